@@ -1,0 +1,433 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms (Stromgren radius and I-front, optically thin 1/r^2, opaque source
+cell, split-count powers of 4), exact invariants (photon ledger, deposited =
+absorbed, linearity in sources, symmetry), an independent brute-force tracer
+with exact rational geometry, textbook chemistry limits, and brute-force
+graph components for source merging.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import brute_trace as bt
+import oracle
+from paper_2512_12466_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def relerr(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+# ------------------------------------------------------------------ hashing / HEALPix
+
+def test_mix64_splitmix_vector():
+    # splitmix64 seeded with 0: first state 0x9e3779b97f4a7c15, first output 0xe220a8397b1dcdaf.
+    assert oracle.mix64(0x9E3779B97F4A7C15) == 0xE220A8397B1DCDAF
+
+
+def test_healpix_level0_centres():
+    """12 base pixels: z = 2/3 (faces 0-3), 0 (4-7), -2/3 (8-11); phi as in Gorski et al."""
+    for p in range(12):
+        v = oracle.pix2vec(0, p)
+        row, col = divmod(p, 4)
+        z = [2.0 / 3.0, 0.0, -2.0 / 3.0][row]
+        phi = (math.pi / 4 + col * math.pi / 2) if row != 1 else col * math.pi / 2
+        s = math.sqrt(1 - z * z)
+        np.testing.assert_allclose(v, [s * math.cos(phi), s * math.sin(phi), z], atol=1e-15)
+
+
+@pytest.mark.parametrize("level", [1, 2, 3, 4])
+def test_healpix_structure(level):
+    nside = 2 ** level
+    npix = 12 * nside * nside
+    vs = np.array([oracle.pix2vec(level, p) for p in range(npix)])
+    np.testing.assert_allclose(np.linalg.norm(vs, axis=1), 1.0, atol=2e-16)
+    # rings: 4 nside - 1 distinct z; polar ring i has 4i pixels, belt rings 4 nside
+    zs, counts = np.unique(np.round(vs[:, 2], 12), return_counts=True)
+    assert len(zs) == 4 * nside - 1
+    expect = {}
+    for i in range(1, 4 * nside):
+        if i < nside:
+            z, c = 1 - i * i / (3 * nside * nside), 4 * i
+        elif i > 3 * nside:
+            j = 4 * nside - i
+            z, c = -(1 - j * j / (3 * nside * nside)), 4 * j
+        else:
+            z, c = (2 * nside - i) * 2 / (3 * nside), 4 * nside
+        expect[round(z, 12)] = c
+    assert dict(zip(zs.tolist(), counts.tolist())) == expect
+    # nested children 4p..4p+3 lie around the parent (within the parent's pixel radius)
+    parents = np.array([oracle.pix2vec(level - 1, p) for p in range(npix // 4)])
+    ang_parent = math.sqrt(4 * math.pi / (npix // 4))
+    for p in range(npix // 4):
+        for q in range(4):
+            cosang = float(np.dot(parents[p], vs[4 * p + q]))
+            assert math.acos(min(1.0, cosang)) < ang_parent
+    # the set of quantised directions is symmetric under z -> -z and 90 deg about z
+    q = {tuple(oracle.direction(level, p)[0]) for p in range(npix)}
+    assert {(x, y, -z) for x, y, z in q} == q
+    assert {(-y, x, z) for x, y, z in q} == q
+
+
+def test_two_healpix_implementations_agree():
+    for level in range(6):
+        for p in range(12 * 4 ** level):
+            assert list(oracle.direction(level, p)[0]) == bt.quantise(bt.healpix_nest_vec(level, p))
+
+
+# ------------------------------------------------------------------ split criterion (Eq. 4)
+
+@pytest.mark.parametrize("n_min", [1.0, 2.0, 4.0, 8.0])
+def test_split_radius_matches_eq4(n_min):
+    """Omega_c / Omega(l) = N_min exactly at R_l (Omega_c = 1/R^2, Omega(l) = 4pi/(12 4^l))."""
+    rq = oracle.split_rq(n_min)
+    for lvl in range(8):
+        r = rq * 2.0 ** (lvl - 24)
+        ratio = (1.0 / r ** 2) / (4 * math.pi / (12 * 4 ** lvl))
+        assert abs(ratio / n_min - 1) < 1e-6
+
+
+def test_default_level_max_never_binds():
+    for n, nmin in [(64, 4.0), (128, 4.0), (256, 2.0)]:
+        lm = oracle.default_level_max(n, nmin)
+        rq = oracle.split_rq(nmin)
+        assert rq * 2.0 ** (lm - 1 - 24) >= math.sqrt(3) * n
+        assert rq * 2.0 ** (lm - 2 - 24) < math.sqrt(3) * n
+
+
+# ------------------------------------------------------------------ brute force (P5)
+
+@pytest.mark.parametrize("seed,mode,n_th_frac,xmode", [
+    (5, 0, 0.01, "mixed"), (6, 3, 0.01, "mixed"), (7, 3, 0.8, "mixed"), (8, 2, 0.8, "mixed"),
+    (9, 1, 0.01, "thin"), (10, 3, 0.5, "patchy"), (11, 4, 0.01, "thin")])
+def test_oracle_matches_brute_force(seed, mode, n_th_frac, xmode):
+    n = 6 if seed % 2 else 8
+    w = I.random_small(n, 3, seed=seed, x_mode=xmode, box_cm=n * 3e21)
+    # the catalog both sides trace: lexicographically sorted, duplicates summed
+    uc, inv = np.unique(w.cells, axis=0, return_inverse=True)
+    w.ndot = np.bincount(inv.reshape(-1), weights=w.ndot)
+    w.cells = uc.astype(np.int32)
+    n_th = n_th_frac * float(w.n_h.mean())
+    bmode = 1 if mode == 4 else mode
+    g, vis, cnt = bt.trace(w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, overlap_mode=bmode, n_th=n_th)
+    r = oracle.run_workload(w, record=400000, overlap_mode=bmode, n_th_cm3=n_th)
+    v = r["visits"]
+    assert v["total"] == len(vis)
+    ov = sorted(zip(v["ray"].tolist(), v["seq"].tolist(), v["cell"].tolist()))
+    bv = sorted((a, b, c) for a, b, c, _ in vis)
+    assert ov == bv
+    ds_o = dict(((a, b), d) for a, b, d in zip(v["ray"].tolist(), v["seq"].tolist(), v["ds"].tolist()))
+    for a, b, c, d in vis:
+        assert abs(ds_o[(a, b)] - d) <= 4e-16 * max(1.0, abs(d))
+    assert relerr(r["gamma"].reshape(-1), g.reshape(-1)) < 1e-12
+    st = r["stats"]
+    assert sum(st["secondary"]) == sum(cnt["secondary"].values())
+    for lvl, c in cnt["rays"].items():
+        assert st["rays"][lvl] == c
+    for lvl, c in cnt["splits"].items():
+        assert st["splits"][lvl] == c
+
+
+# ------------------------------------------------------------------ closed forms
+
+def test_opaque_source_cell_closed_form():
+    """Neutral dense gas: every level-0 ray is spent in the source cell, so
+    Gamma_src = Ndot / (n_HI V) and nothing else is touched (P1)."""
+    w = I.cosmo_box(32, 20.0 * 32 / 128, 1.0, 5, config=2, x_mode="neutral")
+    r = oracle.run_workload(w)
+    st = r["stats"]
+    assert st["rays"][0] == 12 * st["n_src_emit"] and st["segments"][0] == 12 * st["n_src_emit"]
+    assert sum(st["splits"]) == 0 and st["dropped_tau"][0] == 12 * st["n_src_emit"]
+    vol = w.dx_cm ** 3
+    g = r["gamma"]
+    expect = np.zeros_like(g)
+    for (ix, iy, iz), nd in zip(r["emit_cells"], r["emit_ndot"]):
+        expect[iz, iy, ix] += nd / (w.n_h[iz, iy, ix] * vol)
+    assert relerr(g, expect) < 1e-14
+
+
+def _thin_uniform(n=64, level_max=5):
+    n_h = np.full((n, n, n), 2e-4)
+    x = np.ones((n, n, n))                    # n_HI = 0: optically thin limit
+    c = n // 2 - 1                            # origin 31.5: 31.5 cells to the nearest face
+    return n_h, x, np.array([[c, c, c]], np.int32), np.array([1e52]), n * 7.117e23, level_max
+
+
+def test_thin_limit_split_counts_and_path_sum():
+    """Infinite thin medium: 12*4^l rays per level (P7) and
+    sum(Gamma) = Ndot sigma R_L / dx^2 up to direction quantisation (P2)."""
+    n_h, x, cells, ndot, box, lm = _thin_uniform()
+    r = oracle.run(n_h, x, cells, ndot, box, level_max=lm, overlap_mode=0)
+    st = r["stats"]
+    for lvl in range(lm + 1):
+        assert st["rays"][lvl] == 12 * 4 ** lvl
+        assert st["escaped"][lvl] == 0
+    for lvl in range(lm):
+        assert st["splits"][lvl] == 12 * 4 ** lvl
+    assert st["dropped_level"][lm] == 12 * 4 ** lm
+    dx = box / n_h.shape[0]
+    r_l = oracle.split_rq(4.0) * 2.0 ** (lm - 24)
+    expect = ndot[0] * 6.3e-18 * r_l / dx ** 2
+    assert abs(r["gamma"].sum() / expect - 1) < 2e-6
+
+
+def test_thin_limit_inverse_square():
+    """Shell-averaged Gamma r^2 = Ndot sigma / (4 pi dx^2) in a thin medium (P2)."""
+    n_h, x, cells, ndot, box, lm = _thin_uniform(level_max=5)
+    r = oracle.run(n_h, x, cells, ndot, box, level_max=lm, overlap_mode=0)
+    n = n_h.shape[0]
+    dx = box / n
+    o = cells[0] + 0.5
+    zz, yy, xx = np.meshgrid(*(np.arange(n) + 0.5,) * 3, indexing="ij")
+    rr = np.sqrt((xx - o[0]) ** 2 + (yy - o[1]) ** 2 + (zz - o[2]) ** 2)
+    norm = ndot[0] * 6.3e-18 / (4 * math.pi * dx ** 2)
+    for r0 in range(4, 14):
+        m = (rr >= r0) & (rr < r0 + 1)
+        ratio = (r["gamma"][m] * rr[m] ** 2).mean() / norm
+        assert abs(ratio - 1) < 0.02, (r0, ratio)
+
+
+def test_stromgren_front_test_a():
+    """Table 1 Test A, one 0.1 Myr step with the C2-Ray iteration: the I-front
+    radius matches r_I(t) = r_s (1 - exp(-t/t_rec))^(1/3) to 1 cell (P3)."""
+    g = json.load(open(os.path.join(GOLDEN, "table1_stromgren.json")))
+    a = g["tests"]["A"]
+    alpha = g["alpha_B_cm3_s"]
+    w = I.stromgren_test_a(64)
+    assert np.all(w.n_h == a["n_H_cm3"]) and w.ndot[0] == a["Ndot_s"]
+    assert abs(w.box_cm / (a["L_box_Mpc"] * I.MPC_CM) - 1) < 1e-12
+    t = 0.1 * I.MYR_S
+    r = oracle.run_workload(w, chem_iterate=1, dt_s=t, alpha_B=alpha, clumping=a["C"])
+    dx = w.dx_cm
+    rs = (3 * a["Ndot_s"] / (4 * math.pi * alpha * a["C"] * a["n_H_cm3"] ** 2)) ** (1 / 3)
+    trec = 1 / (a["C"] * alpha * a["n_H_cm3"])
+    assert abs(rs / (5.393 * I.KPC_CM) - 1) < 1e-3           # 5.393 kpc
+    assert abs(trec / I.MYR_S - 122.35) < 0.01
+    r_i = rs * (1 - math.exp(-t / trec)) ** (1 / 3) / dx
+    r_n = (3 * r["x"].sum() / (4 * math.pi)) ** (1 / 3)
+    assert abs(r_n - r_i) < 1.0, (r_n, r_i)
+    st = r["stats"]
+    assert st["chem_residual"] < 1e-6 and st["chem_iters"] < 100
+    # photon budget: ionizations <= photons emitted, and close to it (t << t_rec)
+    ionized = (r["x"].sum() * a["n_H_cm3"]) * dx ** 3
+    assert ionized <= a["Ndot_s"] * t * (1 + 1e-9)
+    assert ionized > 0.99 * a["Ndot_s"] * t
+
+
+# ------------------------------------------------------------------ invariants
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_photon_ledger(prec, mode):
+    """emitted = absorbed + escaped + dropped; deposited (sum Gamma n_HI V) =
+    absorbed for the photon-conserving modes; mode 1 (Eq. 5 alone) loses."""
+    w = I.random_small(24, 6, seed=21 + mode, x_mode="patchy", box_cm=24 * 7e22)
+    r = oracle.run_workload(w, precision=prec, overlap_mode=mode, n_th_cm3=0.5 * float(w.n_h.mean()))
+    st = r["stats"]
+    e = st["emitted_ph"]
+    tol = 1e-12 if prec == 0 else 1e-6
+    assert abs(st["absorbed_ph"] + st["escaped_ph"] + st["dropped_ph"] - e) / e < tol
+    assert st["emitted_ph"] == pytest.approx(float(np.sum(r["emit_ndot"])), rel=1e-15)
+    if mode in (0, 2, 3):
+        assert abs(st["deposited_ph"] - st["absorbed_ph"]) / e < tol
+    else:
+        assert st["deposited_ph"] < st["absorbed_ph"] * (1 - 1e-6)
+
+
+def test_linearity_in_sources():
+    """At fixed x, Gamma of the union of two source sets is the sum (P6)."""
+    w = I.random_small(16, 6, seed=31, x_mode="mixed", box_cm=16 * 5e22)
+    # distinct cells so dedup does not merge across the two sets
+    cells = np.array([[1, 2, 3], [10, 4, 7], [15, 15, 0], [5, 5, 5], [8, 1, 13], [3, 12, 9]], np.int32)
+    a = oracle.run(w.n_h, w.x_ion, cells[:3], w.ndot[:3], w.box_cm)
+    b = oracle.run(w.n_h, w.x_ion, cells[3:], w.ndot[3:], w.box_cm)
+    ab = oracle.run(w.n_h, w.x_ion, cells, w.ndot, w.box_cm)
+    assert relerr(ab["gamma"], a["gamma"] + b["gamma"]) < 1e-13
+    # duplicates are exactly a summed source
+    dup = oracle.run(w.n_h, w.x_ion, np.array([[5, 5, 5], [5, 5, 5]], np.int32), np.array([2e50, 3e50]),
+                     w.box_cm)
+    one = oracle.run(w.n_h, w.x_ion, np.array([[5, 5, 5]], np.int32), np.array([5e50]), w.box_cm)
+    assert dup["stats"]["n_src_emit"] == 1
+    assert relerr(dup["gamma"], one["gamma"]) < 1e-15
+
+
+def test_symmetry_centred_source():
+    """Odd grid, source at the centre cell, uniform gas: Gamma is invariant
+    under z -> -z, x -> -x and 90 degree rotations about z (P8)."""
+    n = 21
+    c = n // 2
+    n_h = np.full((n, n, n), 1e-3)
+    x = np.full((n, n, n), 0.9)
+    r = oracle.run(n_h, x, np.array([[c, c, c]], np.int32), np.array([5e48]), n * 3.182e20,
+                   overlap_mode=0)
+    g = r["gamma"]
+    assert relerr(g[::-1, :, :], g) < 1e-12
+    assert relerr(g[:, :, ::-1], g) < 1e-12
+    assert relerr(np.rot90(g, 1, axes=(1, 2)), g) < 1e-12
+
+
+def test_fp32_physics_close_to_fp64():
+    w = I.random_small(24, 5, seed=41, x_mode="patchy", box_cm=24 * 7e22)
+    r64 = oracle.run_workload(w, precision=0)
+    r32 = oracle.run_workload(w, precision=1)
+    assert relerr(r32["gamma"], r64["gamma"]) < 1e-5
+    assert relerr(r32["heat"], r64["heat"]) < 1e-5
+
+
+def test_level_max_drops_budget():
+    w = I.random_small(16, 2, seed=51, x_mode="thin", box_cm=16 * 7e20)
+    r = oracle.run_workload(w, level_max=2)
+    st = r["stats"]
+    assert sum(st["rays"][3:]) == 0 and st["dropped_level"][2] > 0
+    e = st["emitted_ph"]
+    assert abs(st["absorbed_ph"] + st["escaped_ph"] + st["dropped_ph"] - e) / e < 1e-12
+
+
+def test_invalid_inputs_rejected():
+    n = 8
+    n_h = np.full((n, n, n), 1e-3)
+    x = np.zeros((n, n, n))
+    with pytest.raises(ValueError):
+        oracle.run(n_h, x, np.array([[8, 0, 0]], np.int32), np.array([1e50]), 1e22)
+    with pytest.raises(ValueError):
+        oracle.run(n_h, x, np.array([[0, 0, 0]], np.int32), np.array([-1.0]), 1e22)
+    bad = n_h.copy()
+    bad[0, 0, 0] = np.nan
+    with pytest.raises(ValueError):
+        oracle.run(bad, x, np.array([[0, 0, 0]], np.int32), np.array([1e50]), 1e22)
+
+
+# ------------------------------------------------------------------ chemistry (Eq. 3, C2-Ray average)
+
+def test_chem_pure_photoionization():
+    """n_e = 0 (first iterate from a neutral start): x(t) = 1 - (1 - x0) e^{-Gamma t}."""
+    g = np.array([1e-12, 3e-14, 0.0])
+    x0 = np.array([0.0, 0.2, 0.3])
+    xa, xe, _ = oracle.chem_update(np.full(3, 1e-3), x0, np.zeros(3), g, 3e12, 2.59e-13)
+    np.testing.assert_allclose(xe[:2], 1 - (1 - x0[:2]) * np.exp(-g[:2] * 3e12), rtol=1e-13)
+    assert xe[2] == 0.3 and xa[2] == 0.3
+
+
+def test_chem_pure_recombination():
+    """Gamma = 0, fixed n_e: x(t) = x0 exp(-n_e C alpha t)."""
+    n_h = np.full(2, 1e-2)
+    x0 = np.array([0.9, 0.5])
+    xa_prev = np.array([0.7, 0.4])
+    xa, xe, _ = oracle.chem_update(n_h, x0, xa_prev, np.zeros(2), 1e13, 2.59e-13, clump=2.0)
+    rate = xa_prev * n_h * 2.0 * 2.59e-13
+    np.testing.assert_allclose(xe, x0 * np.exp(-rate * 1e13), rtol=1e-13)
+
+
+def test_chem_time_average_is_mean_of_trajectory():
+    """<x> returned equals (1/dt) integral of x(t) for the constant-rate solution."""
+    n_h = np.full(3, 1e-3)
+    x0 = np.array([0.1, 0.6, 0.95])
+    xprev = np.array([0.3, 0.5, 0.9])
+    gam = np.array([2e-14, 1e-15, 5e-13])
+    dt = 4e13
+    xa, xe, _ = oracle.chem_update(n_h, x0, xprev, gam, dt, 2.59e-13, C_H=1e-12, clump=1.5)
+    ne = xprev * n_h
+    ion = gam + ne * 1e-12
+    rec = ne * 1.5 * 2.59e-13
+    xeq = ion / (ion + rec)
+    ts = np.linspace(0, dt, 20001)
+    traj = xeq[:, None] + (x0 - xeq)[:, None] * np.exp(-(ion + rec)[:, None] * ts[None, :])
+    avg = np.trapezoid(traj, ts, axis=1) / dt
+    np.testing.assert_allclose(xa, avg, rtol=1e-8)
+    np.testing.assert_allclose(xe, traj[:, -1], rtol=1e-13)
+
+
+# ------------------------------------------------------------------ sources: dedup, radius, merge (Alg. 3)
+
+def test_dedup_sorted_and_summed():
+    cells = np.array([[3, 1, 2], [0, 5, 5], [3, 1, 2], [0, 5, 4], [3, 1, 2]], np.int32)
+    nd = np.array([1.0, 2.0, 4.0, 8.0, 16.0])
+    c, n = oracle.sources_dedup(cells, nd)
+    assert c.tolist() == [[0, 5, 4], [0, 5, 5], [3, 1, 2]]
+    assert n.tolist() == [8.0, 2.0, 21.0]
+
+
+def test_max_radius_cases():
+    n = 48
+    x = np.zeros((n, n, n))
+    assert oracle.max_radius(x, [24, 24, 24]) == 0.0                    # neutral source cell
+    x[:] = 1.0
+    assert oracle.max_radius(x, [24, 24, 24], rmax=16.0) == 16.0         # fully ionized: R_max
+    # ionized ball of radius 9 around the source (cell centres)
+    zz, yy, xx = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    d = np.sqrt((xx - 24) ** 2 + (yy - 24) ** 2 + (zz - 24) ** 2)
+    x = (d <= 9.0).astype(float)
+    rad = oracle.max_radius(x, [24, 24, 24], dr=2.0, rmax=16.0)
+    assert rad == 8.0
+
+
+def _components(nsrc, edges):
+    adj = {i: set() for i in range(nsrc)}
+    for a, b in edges:
+        adj[a].add(b)
+        adj[b].add(a)
+    seen, comps = set(), []
+    for s in range(nsrc):
+        if s in seen:
+            continue
+        stack, comp = [s], set()
+        while stack:
+            u = stack.pop()
+            if u in comp:
+                continue
+            comp.add(u)
+            stack.extend(adj[u] - comp)
+        seen |= comp
+        comps.append(comp)
+    return comps
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_merge_components_match_dfs(seed):
+    rng = np.random.default_rng(seed)
+    n = 40
+    x = np.clip(I.lognormal(n, 1.0, 1.5, seed + 100), 0, 1)
+    cells = rng.integers(0, n, size=(60, 3)).astype(np.int32)
+    c, nd = oracle.sources_dedup(cells, rng.uniform(1e50, 1e52, size=60))
+    mc, mn, rad, lab = oracle.merge_sources(x, c, nd, rmax=8.0)
+    edges = []
+    for a, b in itertools.combinations(range(len(nd)), 2):
+        if rad[a] > 0 and rad[b] > 0:
+            d2 = float(np.sum((c[a].astype(np.int64) - c[b]) ** 2))
+            if d2 <= (rad[a] + rad[b]) ** 2 + 1e-6:
+                edges.append((a, b))
+    comps = _components(len(nd), edges)
+    groups = {}
+    for i, l in enumerate(lab):
+        groups.setdefault(int(l), set()).add(i)
+    assert sorted(map(sorted, groups.values())) == sorted(map(sorted, comps))
+    assert len(mn) == len(comps)
+    assert abs(mn.sum() / nd.sum() - 1) < 1e-14
+    member_cells = {tuple(v) for v in c.tolist()}
+    assert all(tuple(v) in member_cells for v in mc.tolist())
+    keys = [tuple(v) for v in mc.tolist()]
+    assert keys == sorted(keys)
+
+
+def test_merge_two_sources_in_one_bubble():
+    n = 48
+    zz, yy, xx = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    d = np.sqrt((xx - 24) ** 2 + (yy - 24) ** 2 + (zz - 24) ** 2)
+    x = (d <= 10.0).astype(float)
+    cells = np.array([[22, 24, 24], [26, 24, 24], [2, 2, 2]], np.int32)
+    c, nd = oracle.sources_dedup(cells, np.array([1e51, 3e51, 1e51]))
+    mc, mn, rad, lab = oracle.merge_sources(x, c, nd, rmax=16.0)
+    assert len(mn) == 2
+    merged = mn.max()
+    assert merged == 4e51
+    # flux-weighted centroid (25, 24, 24) snaps to the nearest member (26, 24, 24)
+    assert [26, 24, 24] in mc.tolist() and [2, 2, 2] in mc.tolist()
