@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark: ray-cell segments per second of the adaptive ray march.
+
+A step is one full radiative-transfer step through the C ABI (rt_step):
+source dedup/sort, optical-depth field, the level-by-level fused march +
+split over every ray of every source, heating and ledger. Workload: the
+128^3 lognormal box (20 Mpc/h, sigma_ln = 1, mean n_H = 2e-4) with 1024
+power-law sources in the densest 1% of cells, in its optically thin variant
+(uniform residual x_HI = 1e-4, so rays cross the box). The headline march is
+FP32 with Kahan-compensated budgets (FP64 deposits); the FP64 march is
+measured beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nyx|reference]
+Under torchrun (N > 1) each rank runs its own replica of the workload
+(independent solves, no collective on the data path); the value is the
+segments of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2512_12466_gb300 import inputs as I  # noqa: E402
+
+METRIC = "ray-cell segments/s"
+WORKLOAD = "128^3 lognormal box, 1024 power-law sources, thin (x_HI=1e-4)"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def load_peaks():
+    try:
+        p = json.load(open(PEAKS))
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def workload():
+    w = I.config2("thin")
+    return w, 0.01 * float(w.n_h.mean())
+
+
+def algorithmic_bytes(st: dict, precision: int) -> float:
+    """Algorithmic bytes of the march kernels of one trace: per primary segment
+    and per secondary deposit one kappa read (8 B FP64 / 4 B FP32) and one FP64
+    read-modify-write of Gamma (16 B); per ray its 16-B direction entry and a
+    quarter of its parent record; per split one parent record written."""
+    rec = 24  # src 4 + pix 4 + P + tau (8+8) or P, tau, cP, ctau (4 x 4)
+    seg_b = (8 if precision == 0 else 4) + 16
+    segs = sum(st["segments"])
+    sec = sum(st["secondary"])
+    rays = sum(st["rays"])
+    splits = sum(st["splits"])
+    return seg_b * (segs + sec) + 16 * rays + rec / 4.0 * rays + rec * splits
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The CPU oracle as it stands, single-threaded, on a bounded sample of the
+    same workload: sources of the 1024 taken in order until ~budget_s of work."""
+    import oracle
+    w, n_th = workload()
+    segs, t_total, used = 0, 0.0, 0
+    while t_total < budget_s and used < len(w.ndot):
+        t0 = time.perf_counter()
+        r = oracle.run(w.n_h, w.x_ion, w.cells[used:used + 1], w.ndot[used:used + 1], w.box_cm, n_th_cm3=n_th,
+                       precision=0, n_min_ray=4.0, tau_max=30.0)
+        t_total += time.perf_counter() - t0
+        segs += sum(r["stats"]["segments"])
+        used += 1
+    return {"value": segs / t_total, "unit": "segments/s", "cores": 1, "kind": "oracle",
+            "sample": f"{used} of 1024 sources of the same 128^3 thin workload, FP64 oracle, single thread, "
+                      f"{segs} segments in {t_total:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle on the same workload, each step a bounded
+    sample (a fixed set of sources), on the host cores."""
+    if rank != 0:
+        return 0
+    import oracle
+    w, n_th = workload()
+    k = 2
+    times, segs = [], 0
+    for i in range(args.warmup + args.steps):
+        lo = (i * k) % len(w.ndot)
+        t0 = time.perf_counter()
+        r = oracle.run(w.n_h, w.x_ion, w.cells[lo:lo + k], w.ndot[lo:lo + k], w.box_cm, n_th_cm3=n_th,
+                       precision=0, n_min_ray=4.0, tau_max=30.0)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            segs += sum(r["stats"]["segments"])
+    total = sum(times)
+    value = segs / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "segments/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": 128, "sources": 1024, "step_sample": f"{k} sources per step"},
+            "cpu_baseline": {"value": value, "unit": "segments/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{k} sources of the 1024 per step, FP64 oracle, single thread"},
+            "e2e": {"value": value, "unit": "segments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def time_steps(solver, steps, flush, g, h, torch):
+    """Per-step CUDA-event timing on the solver's stream, L2 flushed before each step."""
+    stream = torch.cuda.current_stream()
+    ms, stats = [], []
+    for _ in range(steps):
+        flush.add_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, st = solver.step(0.0, g, h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    return ms, stats
+
+
+def run_nyx(args, world, rank, local):
+    import torch
+    import paper_2512_12466_gb300 as nyx
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w, n_th = workload()
+    n3 = w.n ** 3
+    d_nh = torch.from_numpy(w.n_h.ravel()).to(dev)
+    d_x = torch.from_numpy(w.x_ion.ravel()).to(dev)
+    d_cells = torch.from_numpy(w.cells.ravel()).to(dev)
+    d_ndot = torch.from_numpy(w.ndot).to(dev)
+    g = torch.empty(n3, dtype=torch.float64, device=dev)
+    h = torch.empty_like(g)
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    results = {}
+    for prec, label in ((nyx.RT_FP32, "fp32"), (nyx.RT_FP64, "fp64")):
+        s = nyx.Solver(w.n, w.box_cm, precision=prec, n_th_cm3=n_th, n_min_ray=4.0, tau_max=30.0)
+        s.set_fields(d_nh, d_x)
+        s.add_sources(d_cells, d_ndot)
+        steps = args.steps if prec == nyx.RT_FP32 else max(1, min(args.steps, 3))
+        for _ in range(args.warmup if prec == nyx.RT_FP32 else 1):
+            s.step(0.0, g, h)
+        torch.cuda.synchronize()
+        clocks = None
+        if prec == nyx.RT_FP32:
+            sampler = ClockSampler(torch.cuda.current_device())
+            sampler.start()
+            time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize()
+        ms, stats = time_steps(s, steps, flush, g, h, torch)
+        torch.cuda.synchronize()
+        barrier(world)
+        if prec == nyx.RT_FP32:
+            clocks = sampler.stop()
+        total_ms = max_over_ranks(sum(ms), world)
+        segs = sum(sum(st["segments"]) for st in stats)
+        segs_all = sum_over_ranks(float(segs), world)
+        st0 = stats[-1]
+        march_ms = sum(st["ms_march"] for st in stats)
+        alg = sum(algorithmic_bytes(st, prec) for st in stats)
+        results[label] = dict(value=segs_all / (total_ms / 1e3), ms_per_step=total_ms / steps, steps=steps,
+                              segments_per_step=sum(st0["segments"]), secondary_per_step=sum(st0["secondary"]),
+                              rays_per_step=sum(st0["rays"]), march_ms_per_step=march_ms / steps,
+                              march_launches_per_step=st0["march_launches"],
+                              launches=sum(st["launches"] for st in stats),
+                              achieved_gbs=alg / (march_ms / 1e3) / 1e9, clocks=clocks, stats=st0)
+        s.close()
+
+    # end to end: pinned host inputs copied in and Gamma read back every step, through the public API
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hn, hx, hc, hd = pin(w.n_h.ravel()), pin(w.x_ion.ravel()), pin(w.cells.ravel()), pin(w.ndot)
+    hg, hh = torch.empty(n3, dtype=torch.float64).pin_memory(), torch.empty(n3, dtype=torch.float64).pin_memory()
+    s = nyx.Solver(w.n, w.box_cm, precision=nyx.RT_FP32, n_th_cm3=n_th, n_min_ray=4.0, tau_max=30.0)
+    e2e_steps = max(1, min(args.steps, 5))
+    for i in range(1 + e2e_steps):
+        if i == 1:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        s.set_fields(hn, hx)
+        s.clear_sources()
+        s.add_sources(hc, hd)
+        _, _, st = s.step(0.0, hg, hh)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_val = sum_over_ranks(float(sum(st["segments"]) * e2e_steps), world) / e2e_s
+    s.close()
+    h2d = 2 * 8 * n3 + w.cells.nbytes + w.ndot.nbytes
+    d2h = 2 * 8 * n3
+
+    if rank != 0:
+        return 0
+    hbm, peak_kind = load_peaks()
+    f32 = results["fp32"]
+    f64 = results["fp64"]
+    line = {
+        "metric": METRIC, "value": f32["value"], "unit": "segments/s", "n_gpus": world, "steps": f32["steps"],
+        "warmup": args.warmup, "ms_per_step": f32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": 128, "box_mpc_h": 20.0, "sigma_ln": 1.0, "mean_nH": 2e-4,
+                   "sources": 1024, "n_min_ray": 4, "tau_max": 30, "overlap": "conservative (Eqs. 7-8)",
+                   "march": "FP32 physics, Kahan-compensated budgets, FP64 deposits and ledger",
+                   "l2": "flushed before every timed step (512 MB write)", "parallelism": f"replicas x{world}"},
+        "segments_per_step": f32["segments_per_step"], "secondary_per_step": f32["secondary_per_step"],
+        "rays_per_step": f32["rays_per_step"],
+        "gpu_launches": f32["launches"],
+        "roofline": {"bound": "hbm", "achieved": f32["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                     "frac": f32["achieved_gbs"] / hbm, "traffic": None,
+                     "kernel": "march_kernel<float>", "peak_kind": peak_kind,
+                     "march_ms_per_step": f32["march_ms_per_step"],
+                     "march_launches_per_step": f32["march_launches_per_step"]},
+        "fp64": {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "steps": f64["steps"],
+                 "roofline": {"achieved": f64["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                              "frac": f64["achieved_gbs"] / hbm, "kernel": "march_kernel<double>"}},
+        "e2e": {"value": e2e_val, "unit": "segments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "clocks": f32["clocks"],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nyx", choices=["nyx", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_nyx(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

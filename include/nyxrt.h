@@ -1,0 +1,185 @@
+/*
+ * nyxrt.h -- C ABI of the GB300 adaptive ray-march library (libnyxrt.so).
+ *
+ * The library computes one radiative-transfer step of the adaptive ray
+ * tracer of "Nyx-RT: Adaptive Ray Tracing in the Nyx Hydrodynamical Code"
+ * (arXiv 2512.12466, Sec. 2.2-2.8): point sources emit rays on HEALPix
+ * directions, rays split 4-way where a cell would be covered by fewer than
+ * N_min rays (Eq. 4), march cell by cell accumulating optical depth (Eq. 2),
+ * and deposit a photon-conserving photoionization rate (Eq. 1, V_box = h^3)
+ * with the geometric overlap correction and conservative thresholding
+ * (Eqs. 5-8). Sources sharing a cell are merged, sorted, and optionally
+ * merged by bubble overlap (Alg. 3). Optionally the step iterates Gamma and
+ * the C2-Ray time-averaged ionization update (Eq. 3, Sec. 2.3-2.4).
+ *
+ * Conventions for every call:
+ *   - Grids are cubic, n^3 cells, flat index (iz*n + iy)*n + ix (x fastest),
+ *     float64. Cell size dx = box_cm / n; cell volume dx^3.
+ *   - `where` says whether a pointer is host memory (RT_HOST) or device
+ *     memory of the handle's GPU (RT_DEVICE).
+ *   - All device work is enqueued on the CUDA stream given to rt_create.
+ *   - Return values: RT_OK (0) or a negative RT_E* code; no exception or
+ *     abort crosses the ABI. rt_last_error() describes the last failure.
+ *     A device-side error (RT_EDEVICE, RT_ETIMEOUT, RT_ECUDA) is sticky:
+ *     later calls on the handle return RT_ESTATE until rt_destroy.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - The library owns the device memory it allocates; inputs are copied.
+ */
+#ifndef NYXRT_H
+#define NYXRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_MAX_LEVELS 16
+
+enum {
+    RT_OK = 0,
+    RT_EINVAL = -1,    /* invalid argument or input value */
+    RT_ENOMEM = -2,    /* device or host allocation failed */
+    RT_ECUDA = -3,     /* a CUDA runtime call failed */
+    RT_EDEVICE = -4,   /* a kernel reported an internal error (e.g. buffer overflow) */
+    RT_ETIMEOUT = -5,  /* a bounded device wait gave up */
+    RT_ESTATE = -6     /* call not valid in the handle's state (missing fields, sticky error) */
+};
+enum { RT_FP64 = 0, RT_FP32 = 1 };
+enum { RT_HOST = 0, RT_DEVICE = 1 };
+enum {
+    RT_OVERLAP_NONE = 0,          /* deposit the whole segment rate in the current cell */
+    RT_OVERLAP_LINEAR = 1,        /* Eq. 5 only (f_c < 1 near faces; photons lost) */
+    RT_OVERLAP_ARC = 2,           /* Eqs. 5-6: secondary deposit into the nearest neighbour */
+    RT_OVERLAP_CONSERVATIVE = 3,  /* Eqs. 7-8: secondary only if n'_H >= n_th (default) */
+    RT_OVERLAP_SQUARED = 4        /* f_c = (1/2 + D_edge/L_pix)^2 (Sec. 2.6.1 alternative) */
+};
+enum { RT_MERGE_OFF = 0, RT_MERGE_FORCED = 1, RT_MERGE_AUTO = 2 };
+
+/* Step configuration. Fill with rt_config_default() and override. */
+typedef struct rt_config {
+    int32_t n;                 /* grid cells per side, 1..1024 */
+    int32_t precision;         /* RT_FP64: FP64 march physics; RT_FP32: FP32 march physics with
+                                  Kahan-compensated photon and optical-depth budgets. Deposits and
+                                  the photon ledger are FP64 in both. */
+    double box_cm;             /* box side length, cm */
+    double sigma_cm2;          /* gray HI cross-section, cm^2 (Eq. 2) */
+    double n_min_ray;          /* N_min^ray >= 1, minimum rays per cell (Eq. 4) */
+    int32_t level_max;         /* maximum HEALPix level (RAY_FLTR, Alg. 1); -1: smallest l with
+                                  R_l >= sqrt(3) n plus one, which never binds */
+    int32_t overlap_mode;      /* RT_OVERLAP_* */
+    double tau_max;            /* optical depth at which a ray's remaining photons are dropped */
+    double n_th_cm3;           /* Eq. 7-8 threshold on the neighbour's n_H; < 0: 0.01 x mean(n_H) */
+    double e_heat_erg;         /* heating per photoionization: heat = e_heat * Gamma * n_HI */
+    int32_t merge_mode;        /* RT_MERGE_*: Alg. 3 source merging off / every step / once mean x
+                                  exceeds automerge_xbar (Sec. 2.8) */
+    int32_t merge_samp_level;  /* HEALPix level of the shell samples (12 * 4^level samples) */
+    double automerge_xbar;     /* automerge threshold on the mean ionized fraction */
+    double merge_x_th;         /* a sample counts as ionized if x >= merge_x_th */
+    double merge_f_req;        /* a shell passes if N_ion / N_tot >= merge_f_req */
+    double merge_dr_cells;     /* shell radius increment, cells */
+    double merge_rmax_cells;   /* hard cap on the bubble radius, cells */
+    double merge_f_ov;         /* overlap factor f_ov */
+    double merge_eps;          /* tolerance epsilon in d^2 <= (f_ov (r_a + r_b))^2 + epsilon */
+    int32_t merge_n_min;       /* below this many samples every sample must be ionized */
+    int32_t chem_iterate;      /* 1: iterate trace <-> C2-Ray update to convergence (Sec. 2.4) */
+    double alpha_B;            /* case-B recombination coefficient, cm^3/s */
+    double C_H;                /* collisional ionization coefficient, cm^3/s */
+    double clumping;           /* clumping factor C */
+    double chem_tol;           /* convergence: max |<x>_new - <x>_old| < chem_tol */
+    int32_t chem_max_iter;     /* iteration cap */
+    int32_t flags;             /* RT_FLAG_* bits */
+} rt_config;
+
+#define RT_FLAG_VISIT_HASH 1   /* accumulate the visit-list hash in rt_stats (bookkeeping check) */
+
+/* Step statistics, filled by rt_step (host memory, valid on return). */
+typedef struct rt_stats {
+    int64_t n_src_in;          /* sources added */
+    int64_t n_src_dedup;       /* after merging sources that share a cell */
+    int64_t n_src_emit;        /* after Alg. 3 merging (= n_src_dedup when merging is off) */
+    int32_t merged;            /* 1 if Alg. 3 merging ran this step */
+    int32_t chem_iters;        /* traces performed (1 without chemistry) */
+    int32_t level_max;         /* level cap in effect */
+    int32_t launches;          /* kernel launches of the last trace */
+    /* per HEALPix level, for the last trace: */
+    int64_t rays[RT_MAX_LEVELS];           /* rays marched */
+    int64_t splits[RT_MAX_LEVELS];         /* rays that reached R_l and split into 4 */
+    int64_t escaped[RT_MAX_LEVELS];        /* rays that left the grid */
+    int64_t dropped_tau[RT_MAX_LEVELS];    /* rays stopped at tau >= tau_max */
+    int64_t dropped_level[RT_MAX_LEVELS];  /* rays stopped at level_max */
+    int64_t segments[RT_MAX_LEVELS];       /* ray-cell segments (primary deposits) */
+    int64_t secondary[RT_MAX_LEVELS];      /* secondary (neighbour) deposits, Eqs. 6/8 */
+    uint64_t visit_hash;       /* sum over segments of a hash of (ray id, segment index, cell);
+                                  0 unless RT_FLAG_VISIT_HASH */
+    double emitted_ph;         /* photons/s emitted */
+    double absorbed_ph;        /* photons/s absorbed along rays */
+    double escaped_ph;         /* photons/s leaving the grid */
+    double dropped_ph;         /* photons/s dropped at tau_max or level_max */
+    double deposited_ph;       /* sum over cells of Gamma n_HI dx^3 */
+    double chem_residual;      /* last max |<x>_new - <x>_old| */
+    double ms_trace;           /* device time of the last trace, first to last march launch */
+    double ms_step;            /* device time of the whole step */
+    double ms_march;           /* sum of the march kernels' own durations in the last trace
+                                  (CUDA events around each launch, on the handle's stream) */
+    int64_t march_launches;    /* march kernel launches in the last trace */
+} rt_stats;
+
+typedef struct rt_handle rt_handle;
+
+/* Fill `cfg` with the library defaults for an n^3 grid of side box_cm:
+ * FP64, sigma = 6.3e-18, N_min = 4, level_max = -1, conservative overlap,
+ * tau_max = 30, n_th = -1, e_heat = 1 eV, merging off (Alg. 3 parameters
+ * x_th = 0.9, f_req = 0.9, dr = 2, R_max = 16, f_ov = 1, eps = 1e-6,
+ * N_min = 8, samples at level 3), chemistry off (alpha_B = 2.59e-13,
+ * C_H = 0, C = 1, tol = 1e-6, 100 iterations). */
+void rt_config_default(rt_config* cfg, int32_t n, double box_cm);
+
+/* Create a solver for one grid (Sec. 2.5 ray-tracing state). `cuda_stream`
+ * is a cudaStream_t (NULL = legacy default stream) on the current device.
+ * Allocates the field and ray buffers on that device. */
+int rt_create(const rt_config* cfg, void* cuda_stream, rt_handle** out);
+
+/* Copy the hydrogen density n_H (cm^-3, >= 0, finite) and the ionized
+ * fraction x in [0, 1] (n^3 float64 each) into the handle. The absorber
+ * density is n_HI = (1 - x) n_H (Sec. 2.6). Device pointers must stay valid
+ * until the stream reaches this call's copies. Values are validated on the
+ * device during rt_step (RT_EINVAL). */
+int rt_set_fields(rt_handle* h, const double* n_H, const double* x_ion, int where);
+
+/* Append n point sources: cell_ijk is n x 3 int32 (ix, iy, iz) integer
+ * cell coordinates (the ray origin is the cell centre), ndot is n float64
+ * photon rates in photons/s (> 0). Copied; validated here for host input
+ * and during rt_step for device input. */
+int rt_add_sources(rt_handle* h, const int32_t* cell_ijk, const double* ndot, int64_t n, int where);
+
+/* Remove all sources. */
+int rt_clear_sources(rt_handle* h);
+
+/* One radiative-transfer step (Alg. 2 with the Sec. 2.8 source handling):
+ * dedup/sort (and merge) sources, trace all rays, write Gamma (s^-1 per H
+ * atom, Eq. 1) and heating (erg s^-1 cm^-3) into caller buffers of n^3
+ * float64 (either may be NULL). With chem_iterate the trace and the
+ * C2-Ray update of Eq. 3 are iterated over a step of dt_s seconds and the
+ * handle's x becomes x(t + dt) (read it with rt_get_x). `st` may be NULL.
+ * Synchronises the stream before returning. */
+int rt_step(rt_handle* h, double dt_s, double* gamma_out, double* heat_out, int where, rt_stats* st);
+
+/* Copy the handle's current ionized fraction (n^3 float64) out. */
+int rt_get_x(rt_handle* h, double* x_out, int where);
+
+/* Free the handle and its device memory. NULL is accepted. */
+int rt_destroy(rt_handle* h);
+
+/* Text of the handle's last error ("" if none); for h == NULL, the last
+ * error of a failed rt_create on this thread. */
+const char* rt_last_error(const rt_handle* h);
+
+/* Library version string. */
+const char* rt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NYXRT_H */

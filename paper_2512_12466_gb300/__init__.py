@@ -1,0 +1,257 @@
+"""GB300-native adaptive ray march of Nyx-RT (arXiv 2512.12466).
+
+Thin ctypes binding over the C ABI of ``libnyxrt.so`` (``include/nyxrt.h``):
+the functions below carry the same names as the C entry points and only
+marshal arguments; every step of the computation runs in the library's CUDA
+kernels. ``Solver`` wraps a handle for convenience, taking torch CUDA tensors
+(zero-copy device pointers on the current torch stream) or numpy arrays (host
+pointers).
+
+The library must be built first (``paper_2512_12466_gb300._build.build()`` or
+``__graft_entry__.build()``); loading fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnyxrt.so")
+
+RT_MAX_LEVELS = 16
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_EDEVICE, RT_ETIMEOUT, RT_ESTATE = 0, -1, -2, -3, -4, -5, -6
+RT_FP64, RT_FP32 = 0, 1
+RT_HOST, RT_DEVICE = 0, 1
+RT_OVERLAP_NONE, RT_OVERLAP_LINEAR, RT_OVERLAP_ARC, RT_OVERLAP_CONSERVATIVE, RT_OVERLAP_SQUARED = 0, 1, 2, 3, 4
+RT_MERGE_OFF, RT_MERGE_FORCED, RT_MERGE_AUTO = 0, 1, 2
+RT_FLAG_VISIT_HASH = 1
+
+_ERRNAMES = {RT_EINVAL: "RT_EINVAL", RT_ENOMEM: "RT_ENOMEM", RT_ECUDA: "RT_ECUDA", RT_EDEVICE: "RT_EDEVICE",
+             RT_ETIMEOUT: "RT_ETIMEOUT", RT_ESTATE: "RT_ESTATE"}
+
+
+class rt_config(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32), ("precision", C.c_int32), ("box_cm", C.c_double), ("sigma_cm2", C.c_double),
+        ("n_min_ray", C.c_double), ("level_max", C.c_int32), ("overlap_mode", C.c_int32),
+        ("tau_max", C.c_double), ("n_th_cm3", C.c_double), ("e_heat_erg", C.c_double),
+        ("merge_mode", C.c_int32), ("merge_samp_level", C.c_int32), ("automerge_xbar", C.c_double),
+        ("merge_x_th", C.c_double), ("merge_f_req", C.c_double), ("merge_dr_cells", C.c_double),
+        ("merge_rmax_cells", C.c_double), ("merge_f_ov", C.c_double), ("merge_eps", C.c_double),
+        ("merge_n_min", C.c_int32), ("chem_iterate", C.c_int32), ("alpha_B", C.c_double), ("C_H", C.c_double),
+        ("clumping", C.c_double), ("chem_tol", C.c_double), ("chem_max_iter", C.c_int32), ("flags", C.c_int32),
+    ]
+
+
+_L = C.c_int64 * RT_MAX_LEVELS
+
+
+class rt_stats(C.Structure):
+    _fields_ = [
+        ("n_src_in", C.c_int64), ("n_src_dedup", C.c_int64), ("n_src_emit", C.c_int64),
+        ("merged", C.c_int32), ("chem_iters", C.c_int32), ("level_max", C.c_int32), ("launches", C.c_int32),
+        ("rays", _L), ("splits", _L), ("escaped", _L), ("dropped_tau", _L), ("dropped_level", _L),
+        ("segments", _L), ("secondary", _L), ("visit_hash", C.c_uint64),
+        ("emitted_ph", C.c_double), ("absorbed_ph", C.c_double), ("escaped_ph", C.c_double),
+        ("dropped_ph", C.c_double), ("deposited_ph", C.c_double), ("chem_residual", C.c_double),
+        ("ms_trace", C.c_double), ("ms_step", C.c_double), ("ms_march", C.c_double),
+        ("march_launches", C.c_int64),
+    ]
+
+
+class NyxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libnyxrt.so. Raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                              "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        P, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.rt_config_default.argtypes = [C.POINTER(rt_config), i32, d]
+        L.rt_config_default.restype = None
+        L.rt_create.argtypes = [C.POINTER(rt_config), P, C.POINTER(P)]
+        L.rt_set_fields.argtypes = [P, P, P, C.c_int]
+        L.rt_add_sources.argtypes = [P, P, P, i64, C.c_int]
+        L.rt_clear_sources.argtypes = [P]
+        L.rt_step.argtypes = [P, d, P, P, C.c_int, C.POINTER(rt_stats)]
+        L.rt_get_x.argtypes = [P, P, C.c_int]
+        L.rt_destroy.argtypes = [P]
+        L.rt_last_error.argtypes = [P]
+        L.rt_last_error.restype = C.c_char_p
+        L.rt_version.restype = C.c_char_p
+        for f in ("rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_step", "rt_get_x",
+                  "rt_destroy"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_step",
+            "rt_get_x", "rt_destroy", "rt_last_error", "rt_version"]
+
+
+def _check(rc: int, h=None):
+    if rc != RT_OK:
+        msg = lib().rt_last_error(h).decode(errors="replace")
+        raise NyxError(rc, msg)
+
+
+# ------------------------------------------------------------ C entry points (same names)
+
+def rt_config_default(n: int, box_cm: float, **overrides) -> rt_config:
+    cfg = rt_config()
+    lib().rt_config_default(C.byref(cfg), int(n), float(box_cm))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def rt_create(cfg: rt_config, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(lib().rt_create(C.byref(cfg), C.c_void_p(stream), C.byref(h)))
+    return h.value
+
+
+def _ptr(a):
+    """(pointer, where) of a torch tensor or numpy array, without copies."""
+    if a is None:
+        return None, RT_HOST
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr()), (RT_DEVICE if a.is_cuda else RT_HOST)
+    return a.ctypes.data_as(C.c_void_p), RT_HOST
+
+
+def rt_set_fields(h: int, n_H, x_ion, where: int) -> None:
+    _check(lib().rt_set_fields(h, n_H, x_ion, where), h)
+
+
+def rt_add_sources(h: int, cells, ndot, n: int, where: int) -> None:
+    _check(lib().rt_add_sources(h, cells, ndot, int(n), where), h)
+
+
+def rt_clear_sources(h: int) -> None:
+    _check(lib().rt_clear_sources(h), h)
+
+
+def rt_step(h: int, dt_s: float, gamma_out, heat_out, where: int, stats: rt_stats | None = None) -> rt_stats:
+    st = stats if stats is not None else rt_stats()
+    _check(lib().rt_step(h, float(dt_s), gamma_out, heat_out, where, C.byref(st)), h)
+    return st
+
+
+def rt_get_x(h: int, x_out, where: int) -> None:
+    _check(lib().rt_get_x(h, x_out, where), h)
+
+
+def rt_destroy(h: int) -> None:
+    _check(lib().rt_destroy(h))
+
+
+def rt_version() -> str:
+    return lib().rt_version().decode()
+
+
+def stats_dict(st: rt_stats) -> dict:
+    out = {}
+    for name, _ in rt_stats._fields_:
+        v = getattr(st, name)
+        out[name] = list(v) if hasattr(v, "__len__") else v
+    return out
+
+
+# ------------------------------------------------------------ convenience wrapper
+
+class Solver:
+    """One grid's ray-march state on the current CUDA device.
+
+    Arrays may be torch CUDA tensors (float64 / int32, contiguous; used in
+    place on ``stream``) or numpy arrays (host, copied by the library).
+    """
+
+    def __init__(self, n: int, box_cm: float, stream: int | None = None, **cfg):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.cfg = rt_config_default(n, box_cm, **cfg)
+        self.n = int(n)
+        self.h = rt_create(self.cfg, stream)
+
+    def set_fields(self, n_H, x_ion):
+        for a in (n_H, x_ion):
+            self._check_array(a, np.float64, self.n ** 3)
+        pn, w1 = _ptr(n_H)
+        px, w2 = _ptr(x_ion)
+        if w1 != w2:
+            raise ValueError("n_H and x_ion must both be host or both be device arrays")
+        rt_set_fields(self.h, pn, px, w1)
+        self._keep = (n_H, x_ion)
+
+    def add_sources(self, cells, ndot):
+        k = len(ndot)
+        self._check_array(cells, np.int32, 3 * k)
+        self._check_array(ndot, np.float64, k)
+        pc, w1 = _ptr(cells)
+        pn, w2 = _ptr(ndot)
+        if w1 != w2:
+            raise ValueError("cells and ndot must both be host or both be device arrays")
+        rt_add_sources(self.h, pc, pn, k, w1)
+        self._keep_src = (cells, ndot)
+
+    def clear_sources(self):
+        rt_clear_sources(self.h)
+
+    def step(self, dt_s: float = 0.0, gamma=None, heat=None):
+        """Run one step; returns (gamma, heat, stats). Output arrays are
+        allocated (numpy) if not given."""
+        if gamma is None and heat is None:
+            gamma = np.empty((self.n,) * 3)
+            heat = np.empty((self.n,) * 3)
+        pg, w1 = _ptr(gamma)
+        ph, w2 = _ptr(heat)
+        where = w1 if gamma is not None else w2
+        st = rt_step(self.h, dt_s, pg, ph, where)
+        return gamma, heat, stats_dict(st)
+
+    def get_x(self, out=None):
+        if out is None:
+            out = np.empty((self.n,) * 3)
+        p, w = _ptr(out)
+        rt_get_x(self.h, p, w)
+        return out
+
+    def close(self):
+        if self.h:
+            rt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _check_array(a, dtype, size):
+        if hasattr(a, "data_ptr"):
+            import torch
+            want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+            if a.dtype != want or not a.is_contiguous() or a.numel() != size:
+                raise ValueError(f"expected a contiguous {want} tensor of {size} elements")
+        else:
+            if a.dtype != dtype or not a.flags["C_CONTIGUOUS"] or a.size != size:
+                raise ValueError(f"expected a C-contiguous {np.dtype(dtype)} array of {size} elements")

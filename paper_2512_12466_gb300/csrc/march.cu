@@ -1,0 +1,433 @@
+// The hot loop of the adaptive ray tracer (Sec. 2.5, Alg. 1 RAYMARCH +
+// RAY_FLTR + FILTERCOPYTRANSFORM<3>, fused): one thread marches one ray of
+// level l from its start sphere R_{l-1} to its split sphere R_l, cell by cell
+// (Amanatides-Woo), depositing the photon-conserving photoionization rate
+// (Eq. 1, gray, V_box) with the overlap correction (Eqs. 5-8) into an FP64
+// grid with atomic adds, and appends the rays that reach R_l to the next
+// level's buffer through a warp-aggregated counter. Children are implicit:
+// a parent record (source, pixel p, budget P, tau) stands for the four
+// HEALPix children 4p..4p+3 with budget P/4 (S_COPY), so splitting writes one
+// record instead of four.
+//
+// Traversal is exact integer arithmetic on quantised directions: the k-th
+// face crossing along axis a is at ray parameter T_a(k) = (2k+1) 2^20 / D_a
+// and the split radius is R_l = Rq 2^l / 2^24, so which face comes next,
+// where a ray starts and whether it reaches R_l are integer comparisons.
+// Segment lengths are exact integers times one per-ray constant. Every
+// floating-point operation that feeds a decision (tau against tau_max, the
+// D_edge < L_pix/2 test) is an explicit round-to-nearest intrinsic, so the
+// bookkeeping is reproducible operation by operation.
+#include <cstdint>
+
+#include "rt_internal.h"
+
+namespace nyx {
+namespace {
+
+constexpr int S = kDirBits;
+constexpr int F = kRadBits;
+constexpr long long kB = 1LL << (S - 1 + F);
+
+template <class R>
+struct Ieee;
+
+template <>
+struct Ieee<double> {
+    __device__ __forceinline__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ __forceinline__ static double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ __forceinline__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+    __device__ __forceinline__ static double div(double a, double b) { return __ddiv_rn(a, b); }
+    __device__ __forceinline__ static double of(long long v) { return __ll2double_rn(v); }
+    __device__ __forceinline__ static double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+    __device__ __forceinline__ static double em1(double x) { return expm1(x); }
+    __device__ __forceinline__ static double qdiv(double a, double b) { return a / b; }
+    __device__ __forceinline__ static bool neg(double x) { return __double_as_longlong(x) < 0; }
+    __device__ __forceinline__ static double mag(double x) { return fabs(x); }
+};
+
+template <>
+struct Ieee<float> {
+    __device__ __forceinline__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ __forceinline__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+    __device__ __forceinline__ static float div(float a, float b) { return __fdiv_rn(a, b); }
+    __device__ __forceinline__ static float of(long long v) { return __ll2float_rn(v); }
+    __device__ __forceinline__ static float pow2(int e) { return __int_as_float((127 + e) << 23); }
+    __device__ __forceinline__ static float em1(float x) { return expm1f(x); }
+    __device__ __forceinline__ static float qdiv(float a, float b) { return __fdividef(a, b); }
+    __device__ __forceinline__ static bool neg(float x) { return __float_as_int(x) < 0; }
+    __device__ __forceinline__ static float mag(float x) { return fabsf(x); }
+};
+
+// splitmix64 output function (Steele, Lea & Flood 2014), for the visit hash.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z ^= z >> 30;
+    z *= 0xbf58476d1ce4e5b9ULL;
+    z ^= z >> 27;
+    z *= 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    return z;
+}
+
+// T_a(ka) < T_b(kb) with T(k) = (2k+1)/D (infinite for D = 0).
+__device__ __forceinline__ bool t_less(int ka, int da, int kb, int db)
+{
+    return (long long)(2 * ka + 1) * db < (long long)(2 * kb + 1) * da;
+}
+
+template <class T>
+__device__ __forceinline__ T pick3(int i, T a, T b, T c)
+{
+    return i == 0 ? a : (i == 1 ? b : c);
+}
+
+// s += v with Kahan compensation c (FP32 march) or plain (FP64 march).
+template <class R>
+__device__ __forceinline__ void budget_add(R& s, R& c, R v)
+{
+    using I = Ieee<R>;
+    if constexpr (sizeof(R) == 4) {
+        const R y = I::sub(v, c);
+        const R t = I::add(s, y);
+        c = I::sub(I::sub(t, s), y);
+        s = t;
+    } else {
+        s = I::add(s, v);
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
+{
+    using I = Ieee<R>;
+    const int l = A.level;
+    const int n = A.n;
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = (long long)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarp = (long long)(gridDim.x * blockDim.x) >> 5;
+
+    unsigned long long c_rays = 0, c_split = 0, c_esc = 0, c_dtau = 0, c_dlev = 0, c_seg = 0, c_sec = 0,
+                       c_hash = 0;
+    double c_abs = 0.0, c_escph = 0.0, c_dropph = 0.0;
+
+    const long long rq_end = A.rq << l;
+    const long long rq_start = l > 0 ? (A.rq << (l - 1)) : 0;
+
+    for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
+        const long long j = base + lane;
+        bool split = false;
+        uint32_t o_src = 0, o_pix = 0;
+        R o_P = 0, o_tau = 0;
+        float o_cP = 0.f, o_ctau = 0.f;
+        if (j < A.c1) {
+            // ---- the ray: level-0 emission (12 per source) or a child of a parent record
+            uint32_t si, pix;
+            R P, tau, cP = 0, ctau = 0;
+            if (l == 0) {
+                si = (uint32_t)(j / 12);
+                pix = (uint32_t)(j - 12LL * si);
+                P = (R)1;
+                tau = (R)0;
+            } else {
+                const long long q = j >> 2;
+                si = A.in.src[q];
+                pix = 4u * A.in.pix[q] + (uint32_t)(j & 3);
+                P = I::mul(A.in.P[q], (R)0.25);
+                tau = A.in.tau[q];
+                if constexpr (sizeof(R) == 4) {
+                    cP = I::mul(A.in.cP[q], 0.25f);
+                    ctau = A.in.ctau[q];
+                }
+            }
+            const SrcEntry se = A.src[si];
+            const int4 dv = A.dirs[pix];
+            const int D0 = abs(dv.x), D1 = abs(dv.y), D2 = abs(dv.z);
+            const int s0 = dv.x < 0 ? -1 : 1, s1 = dv.y < 0 ? -1 : 1, s2 = dv.z < 0 ? -1 : 1;
+
+            // ---- integer event bookkeeping
+            const long long ge0 = rq_end * D0, ge1 = rq_end * D1, ge2 = rq_end * D2;
+            int k0 = 0, k1 = 0, k2 = 0;
+            long long gs0 = 0, gs1 = 0, gs2 = 0;
+            if (l > 0) {
+                gs0 = rq_start * D0;
+                gs1 = rq_start * D1;
+                gs2 = rq_start * D2;
+                k0 = (int)((gs0 + kB) >> (S + F));
+                k1 = (int)((gs1 + kB) >> (S + F));
+                k2 = (int)((gs2 + kB) >> (S + F));
+            }
+            const int ke0 = (int)(((ge0 + kB - 1) >> (S - 1 + F)) >> 1);
+            const int ke1 = (int)(((ge1 + kB - 1) >> (S - 1 + F)) >> 1);
+            const int ke2 = (int)(((ge2 + kB - 1) >> (S - 1 + F)) >> 1);
+            int i0 = se.cx + s0 * k0, i1 = se.cy + s1 * k1, i2 = se.cz + s2 * k2;
+
+            // ---- per-ray constants
+            R nrm;
+            if constexpr (sizeof(R) == 4) {
+                nrm = __int_as_float(dv.w);
+            } else {
+                const long long nn = (long long)D0 * D0 + (long long)D1 * D1 + (long long)D2 * D2;
+                nrm = __dmul_rn(__dsqrt_rn(__ll2double_rn(nn)), I::pow2(-S));
+            }
+            const R two20 = (R)(1 << (S - 1));
+            const R h0 = D0 ? I::div(two20, (R)D0) : (R)0;
+            const R h1 = D1 ? I::div(two20, (R)D1) : (R)0;
+            const R h2 = D2 ? I::div(two20, (R)D2) : (R)0;
+            const R pV = I::pow2(-(S - 1 + F)), pI = I::pow2(-S), pU = I::pow2(-(S + 1));
+            const R W01 = (D0 && D1) ? I::div(h0, (R)D1) : (R)0;
+            const R W02 = (D0 && D2) ? I::div(h0, (R)D2) : (R)0;
+            const R W12 = (D1 && D2) ? I::div(h1, (R)D2) : (R)0;
+            const R u0 = I::mul((R)D0, pU), u1 = I::mul((R)D1, pU), u2 = I::mul((R)D2, pU);
+            const R Lc = I::mul(I::mul(nrm, (R)kSqrtPiOver3), I::pow2(-l));
+            R G;
+            if constexpr (sizeof(R) == 4) G = se.gf; else G = se.gd;
+            const double ph = se.ph;
+            const R taumax = A.tau_max;
+            const unsigned long long rbase =
+                mix64(((unsigned long long)si << 36) | ((unsigned long long)l << 31) | pix);
+
+            R Ab = 0, cA = 0;           // photons absorbed by this ray (units of ph)
+            ++c_rays;
+            bool inside = (unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n;
+            if (!inside) {
+                ++c_esc;
+                c_escph += ph * ((double)P - (double)cP);
+            }
+            int prev = -1, kprev = 0;
+            unsigned seq = 0;
+            while (inside) {
+                // next face crossing (ties x, y, z), or the split sphere
+                int w = 0, kw = k0, Dw = D0;
+                if (t_less(k1, D1, kw, Dw)) { w = 1; kw = k1; Dw = D1; }
+                if (t_less(k2, D2, kw, Dw)) { w = 2; kw = k2; Dw = D2; }
+                const bool is_end = !(kw < pick3(w, ke0, ke1, ke2));
+                const R hw = pick3(w, h0, h1, h2);
+
+                R ds_p;
+                if (!is_end) {
+                    if (prev < 0) {
+                        const long long num = (long long)(2 * kw + 1) * kB - pick3(w, gs0, gs1, gs2);
+                        ds_p = I::mul(I::of(num), I::mul(hw, pV));
+                    } else if (prev == w) {
+                        ds_p = I::add(hw, hw);
+                    } else {
+                        const int Dp = pick3(prev, D0, D1, D2);
+                        const long long num = (long long)(2 * kw + 1) * Dp - (long long)(2 * kprev + 1) * Dw;
+                        const int pair = prev + w;
+                        ds_p = I::mul(I::of(num), pair == 1 ? W01 : (pair == 2 ? W02 : W12));
+                    }
+                } else {
+                    if (prev < 0) {
+                        ds_p = I::mul((R)A.rq, I::pow2(l > 0 ? l - 1 - F : -F));
+                    } else {
+                        const long long num = pick3(prev, ge0, ge1, ge2) - (long long)(2 * kprev + 1) * kB;
+                        ds_p = I::mul(I::of(num), I::mul(pick3(prev, h0, h1, h2), pV));
+                    }
+                }
+                const R ds = I::mul(ds_p, nrm);
+
+                const int cell = (i2 * n + i1) * n + i0;
+                const R kraw = A.kap[cell];
+                const R kap = I::mag(kraw);
+                const R dtau = I::mul(kap, ds);
+                R a, gseg;
+                if (kap > (R)0) {
+                    a = P * (-I::em1(-dtau));
+                    gseg = I::qdiv(a * G, kap);
+                } else {
+                    a = (R)0;
+                    gseg = (P * G) * ds;
+                }
+
+                // ---- overlap correction (Eqs. 5-8)
+                R f = (R)1, g2 = (R)0;
+                int nbcell = -1;
+                if (A.overlap_mode != RT_OVERLAP_NONE) {
+                    R dl[6];
+                    #pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        const int kb_ = pick3(b, k0, k1, k2), Db = pick3(b, D0, D1, D2), sb = pick3(b, s0, s1, s2);
+                        R dn;
+                        if (!is_end) {
+                            dn = (b == w) ? (R)0
+                                          : I::mul(I::of((long long)(2 * kb_ + 1) * Dw - (long long)(2 * kw + 1) * Db),
+                                                   I::mul(hw, pI));
+                        } else {
+                            dn = I::mul(I::of((long long)(2 * kb_ + 1) * kB - pick3(b, ge0, ge1, ge2)),
+                                        I::pow2(-(S + F)));
+                        }
+                        const R delta = I::add(dn, I::mul(ds_p, pick3(b, u0, u1, u2)));
+                        const R other = I::sub((R)1, delta);
+                        dl[2 * b] = sb > 0 ? other : delta;
+                        dl[2 * b + 1] = sb > 0 ? delta : other;
+                    }
+                    int face = 0;
+                    R De = dl[0];
+                    #pragma unroll
+                    for (int q = 1; q < 6; ++q) {
+                        if (dl[q] < De) { De = dl[q]; face = q; }
+                    }
+                    const R tnext = is_end ? I::mul((R)A.rq, I::pow2(l - F)) : I::mul(I::of(2 * kw + 1), hw);
+                    const R tm = I::sub(tnext, I::mul(ds_p, (R)0.5));
+                    const R Lpix = I::mul(tm, Lc);
+                    if (I::add(De, De) < Lpix) {
+                        if (A.overlap_mode == RT_OVERLAP_LINEAR) {
+                            f = (R)0.5 + I::qdiv(De, Lpix);
+                        } else if (A.overlap_mode == RT_OVERLAP_SQUARED) {
+                            f = (R)0.5 + I::qdiv(De, Lpix);
+                            f = f * f;
+                        } else {
+                            int j0 = i0, j1 = i1, j2 = i2;
+                            const int step = (face & 1) ? 1 : -1;
+                            if ((face >> 1) == 0) j0 += step; else if ((face >> 1) == 1) j1 += step; else j2 += step;
+                            if ((unsigned)j0 < (unsigned)n && (unsigned)j1 < (unsigned)n && (unsigned)j2 < (unsigned)n) {
+                                const int c2 = (j2 * n + j1) * n + j0;
+                                const R kn_raw = A.kap[c2];
+                                const R kn = I::mag(kn_raw);
+                                const bool elig = (A.overlap_mode == RT_OVERLAP_CONSERVATIVE) ? (!I::neg(kn_raw) && kn > (R)0)
+                                                                                               : (kn > (R)0);
+                                if (elig) {
+                                    f = (R)0.5 + I::qdiv(De, Lpix);
+                                    g2 = (((R)1 - f) * gseg) * I::qdiv(kap, kn);
+                                    nbcell = c2;
+                                }
+                            }
+                        }
+                    }
+                }
+                atomicAdd(&A.gamma[cell], (double)(f * gseg));
+                if (nbcell >= 0) {
+                    atomicAdd(&A.gamma[nbcell], (double)g2);
+                    ++c_sec;
+                }
+
+                budget_add(tau, ctau, dtau);
+                budget_add(P, cP, -a);
+                budget_add(Ab, cA, a);
+                ++c_seg;
+                if (A.hash) c_hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
+                ++seq;
+
+                if (tau >= taumax) {                     // photons spent
+                    ++c_dtau;
+                    c_dropph += ph * ((double)P - (double)cP);
+                    c_abs += ph * ((double)Ab - (double)cA);
+                    break;
+                }
+                if (is_end) {                            // reached the split sphere R_l
+                    c_abs += ph * ((double)Ab - (double)cA);
+                    if (l + 1 > A.level_max) {
+                        ++c_dlev;
+                        c_dropph += ph * ((double)P - (double)cP);
+                    } else {
+                        ++c_split;
+                        split = true;
+                        o_src = si;
+                        o_pix = pix;
+                        o_P = P;
+                        o_tau = tau;
+                        if constexpr (sizeof(R) == 4) {
+                            o_cP = cP;
+                            o_ctau = ctau;
+                        }
+                    }
+                    break;
+                }
+                // step every axis whose crossing coincides with the winner's
+                const bool t0 = (w == 0) || ((long long)(2 * k0 + 1) * Dw == (long long)(2 * kw + 1) * D0);
+                const bool t1 = (w == 1) || ((long long)(2 * k1 + 1) * Dw == (long long)(2 * kw + 1) * D1);
+                const bool t2 = (w == 2) || ((long long)(2 * k2 + 1) * Dw == (long long)(2 * kw + 1) * D2);
+                if (t0) { ++k0; i0 += s0; }
+                if (t1) { ++k1; i1 += s1; }
+                if (t2) { ++k2; i2 += s2; }
+                prev = w;
+                kprev = kw;
+                if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
+                    ++c_esc;
+                    c_escph += ph * ((double)P - (double)cP);
+                    c_abs += ph * ((double)Ab - (double)cA);
+                    break;
+                }
+            }
+        }
+        // ---- warp-aggregated append of the rays that split (Alg. 1 FILTERCOPYTRANSFORM<3>)
+        const unsigned m = __ballot_sync(0xffffffffu, split);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long pos0 = 0;
+            if (lane == leader) pos0 = atomicAdd(A.out_count, (unsigned long long)__popc(m));
+            pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+            if (split) {
+                const unsigned long long pos = pos0 + __popc(m & ((1u << lane) - 1u));
+                if (pos < (unsigned long long)A.out.cap) {
+                    A.out.src[pos] = o_src;
+                    A.out.pix[pos] = o_pix;
+                    A.out.P[pos] = o_P;
+                    A.out.tau[pos] = o_tau;
+                    if constexpr (sizeof(R) == 4) {
+                        A.out.cP[pos] = o_cP;
+                        A.out.ctau[pos] = o_ctau;
+                    }
+                } else {
+                    atomicOr(&A.st->err, kErrRayOverflow);
+                }
+            }
+        }
+    }
+
+    // ---- statistics and photon ledger: one atomic per warp and counter
+    c_rays = warp_sum(c_rays);
+    c_split = warp_sum(c_split);
+    c_esc = warp_sum(c_esc);
+    c_dtau = warp_sum(c_dtau);
+    c_dlev = warp_sum(c_dlev);
+    c_seg = warp_sum(c_seg);
+    c_sec = warp_sum(c_sec);
+    c_hash = warp_sum(c_hash);
+    c_abs = warp_sum(c_abs);
+    c_escph = warp_sum(c_escph);
+    c_dropph = warp_sum(c_dropph);
+    if (lane == 0 && c_rays) {
+        DevStats* st = A.st;
+        atomicAdd(&st->rays[l], c_rays);
+        if (c_split) atomicAdd(&st->splits[l], c_split);
+        if (c_esc) atomicAdd(&st->escaped[l], c_esc);
+        if (c_dtau) atomicAdd(&st->dropped_tau[l], c_dtau);
+        if (c_dlev) atomicAdd(&st->dropped_level[l], c_dlev);
+        atomicAdd(&st->segments[l], c_seg);
+        if (c_sec) atomicAdd(&st->secondary[l], c_sec);
+        if (c_hash) atomicAdd(&st->visit_hash, c_hash);
+        atomicAdd(&st->absorbed, c_abs);
+        atomicAdd(&st->escaped_ph, c_escph);
+        atomicAdd(&st->dropped_ph, c_dropph);
+    }
+}
+
+}  // namespace
+
+int launch_march_f64(const MarchArgs<double>& a, int grid, int block, cudaStream_t s)
+{
+    march_kernel<double><<<grid, block, 0, s>>>(a);
+    return 1;
+}
+
+int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_t s)
+{
+    march_kernel<float><<<grid, block, 0, s>>>(a);
+    return 1;
+}
+
+}  // namespace nyx

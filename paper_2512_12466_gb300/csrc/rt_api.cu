@@ -1,0 +1,705 @@
+// Host runtime of libnyxrt and its C ABI (include/nyxrt.h).
+//
+// One rt_handle owns one grid's device state: n_H and x, the optical-depth
+// field, the Gamma accumulator, the source catalog and one ray buffer per
+// HEALPix level. rt_step runs the Sec. 2.8 source pipeline, then the ray
+// tracing loop of Alg. 2 as one fused march+split launch per level (and per
+// slice when a level's rays exceed the per-launch bound), then the heating
+// and ledger reduction; with chemistry it iterates trace and the C2-Ray
+// update (Sec. 2.4). The host reads back one counter per launch to size the
+// next level; everything else stays on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rt_internal.h"
+
+using namespace nyx;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Children marched per launch; a level with more is processed in slices, each
+// followed by its whole sub-tree, which bounds every ray buffer to this many
+// records.
+constexpr int64_t kMaxChildrenPerLaunch = int64_t(1) << 27;
+constexpr int kMarchBlock = 256;
+
+struct DirTable {
+    int level = -1;
+    int4* dev = nullptr;
+};
+std::mutex g_dir_mu;
+std::map<int, DirTable> g_dirs;          // per device; superseded tables stay allocated (handles may use them)
+
+int ensure_directions(int device, int level, const int4** out, std::string& err)
+{
+    std::lock_guard<std::mutex> lk(g_dir_mu);
+    DirTable& t = g_dirs[device];
+    if (t.level < level) {
+        const int64_t count = healpix_level_offset(level + 1);
+        std::vector<int4> host;
+        try {
+            host.resize((size_t)count);
+        } catch (const std::bad_alloc&) {
+            err = "host allocation of the direction table failed";
+            return RT_ENOMEM;
+        }
+        healpix_direction_table(level, host.data());
+        int4* d = nullptr;
+        if (cudaMalloc(&d, sizeof(int4) * (size_t)count) != cudaSuccess) {
+            cudaGetLastError();
+            err = "device allocation of the direction table failed";
+            return RT_ENOMEM;
+        }
+        if (cudaMemcpy(d, host.data(), sizeof(int4) * (size_t)count, cudaMemcpyHostToDevice) != cudaSuccess) {
+            err = "copy of the direction table failed";
+            cudaFree(d);
+            return RT_ECUDA;
+        }
+        t.dev = d;
+        t.level = level;
+    }
+    *out = t.dev;
+    return RT_OK;
+}
+
+struct DeviceGuard {
+    int old = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&old);
+        if (old != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (old >= 0 && cur != old) cudaSetDevice(old);
+    }
+};
+
+// One level's ray records, allocated as one block.
+struct RayStore {
+    void* base = nullptr;
+    int64_t cap = 0;
+};
+
+template <class T>
+T* carve(char*& p, int64_t count)
+{
+    T* r = reinterpret_cast<T*>(p);
+    p += ((sizeof(T) * (size_t)count + 255) / 256) * 256;
+    return r;
+}
+
+size_t ray_bytes(int64_t cap, int real_size)
+{
+    auto pad = [](size_t b) { return ((b + 255) / 256) * 256; };
+    size_t b = 2 * pad(4 * (size_t)cap) + 2 * pad((size_t)real_size * (size_t)cap);
+    if (real_size == 4) b += 2 * pad(4 * (size_t)cap);
+    return b;
+}
+
+template <class R>
+RayBuf<R> ray_view(const RayStore& s)
+{
+    RayBuf<R> b;
+    if (!s.base) return b;
+    char* p = static_cast<char*>(s.base);
+    b.src = carve<uint32_t>(p, s.cap);
+    b.pix = carve<uint32_t>(p, s.cap);
+    b.P = carve<R>(p, s.cap);
+    b.tau = carve<R>(p, s.cap);
+    if (sizeof(R) == 4) {
+        b.cP = carve<float>(p, s.cap);
+        b.ctau = carve<float>(p, s.cap);
+    }
+    b.cap = s.cap;
+    return b;
+}
+
+}  // namespace
+
+struct rt_handle {
+    rt_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 152;
+    int64_t ncell = 0;
+    double dx = 0, vol = 0, sdx = 0, s_over_dx2 = 0;
+    int64_t rq = 0;
+    int level_max = 0;
+    int table_level = 0;
+    const int4* dirs = nullptr;
+
+    double* d_nh = nullptr;
+    double* d_x = nullptr;
+    double* d_xavg = nullptr;
+    double* d_xend = nullptr;
+    double* d_gamma = nullptr;
+    double* d_heat = nullptr;
+    void* d_kap = nullptr;
+    double* d_scalar = nullptr;           // reduction scratch
+
+    SourceWork sw;
+    int64_t nsrc = 0;
+    SrcEntry* d_emit = nullptr;
+    int64_t n_emit = 0;
+
+    RayStore rays[RT_MAX_LEVELS + 1];
+    unsigned long long* d_count = nullptr;   // one per level
+    DevStats* d_st = nullptr;
+    DevStats* h_st = nullptr;                // pinned
+    unsigned long long* h_count = nullptr;   // pinned
+    int32_t* h_i32 = nullptr;                // pinned scratch
+    double* h_f64 = nullptr;                 // pinned scratch
+
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double ms_march = 0.0;
+    bool fields_set = false;
+    bool sticky = false;
+    int launches = 0;
+    int march_launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(rt_handle* h, int code, const std::string& msg)
+{
+    h->err = msg;
+    if (code == RT_ECUDA || code == RT_EDEVICE || code == RT_ETIMEOUT) h->sticky = true;
+    return code;
+}
+
+int cuda_fail(rt_handle* h, cudaError_t e, const char* what)
+{
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return fail(h, RT_ENOMEM, std::string(what) + ": out of device memory");
+    return fail(h, RT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RT_CUDA(h, call, what)                                \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+#define RT_LAUNCHED(h, what)                                              \
+    do {                                                                  \
+        cudaError_t e_ = cudaGetLastError();                              \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what);             \
+    } while (0)
+
+int grow_sources(rt_handle* h, int64_t need)
+{
+    if (need <= h->sw.cap) return RT_OK;
+    int64_t cap = std::max<int64_t>(need, std::max<int64_t>(1024, 2 * h->sw.cap));
+    SourceWork nw;
+    nw.cap = cap;
+    auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes); };
+    cudaError_t e = cudaSuccess;
+    e = e ? e : alloc((void**)&nw.cells_raw, 12 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.ndot_raw, 8 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.keys, 8 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.order, 4 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.flag, 4 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.head_pos, 4 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.cells_a, 12 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.ndot_a, 8 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.cells_b, 12 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.ndot_b, 8 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.label, 4 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.parent, 4 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.radius, 8 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.count, 16);
+    SrcEntry* emit = nullptr;
+    e = e ? e : alloc((void**)&emit, sizeof(SrcEntry) * (size_t)cap);
+    auto release = [](SourceWork& w) {
+        cudaFree(w.cells_raw); cudaFree(w.ndot_raw); cudaFree(w.keys); cudaFree(w.order); cudaFree(w.flag);
+        cudaFree(w.head_pos); cudaFree(w.cells_a); cudaFree(w.ndot_a); cudaFree(w.cells_b); cudaFree(w.ndot_b);
+        cudaFree(w.label); cudaFree(w.parent); cudaFree(w.radius); cudaFree(w.count);
+    };
+    if (e != cudaSuccess) {
+        release(nw);
+        cudaFree(emit);
+        return cuda_fail(h, e, "source buffers");
+    }
+    if (h->nsrc > 0) {
+        RT_CUDA(h, cudaMemcpyAsync(nw.cells_raw, h->sw.cells_raw, 12 * (size_t)h->nsrc, cudaMemcpyDeviceToDevice, h->stream),
+                "source copy");
+        RT_CUDA(h, cudaMemcpyAsync(nw.ndot_raw, h->sw.ndot_raw, 8 * (size_t)h->nsrc, cudaMemcpyDeviceToDevice, h->stream),
+                "source copy");
+    }
+    RT_CUDA(h, cudaStreamSynchronize(h->stream), "source copy");
+    release(h->sw);
+    cudaFree(h->d_emit);
+    h->sw = nw;
+    h->d_emit = emit;
+    return RT_OK;
+}
+
+template <class R>
+int ensure_rays(rt_handle* h, int level, int64_t need)
+{
+    RayStore& s = h->rays[level];
+    if (s.cap >= need) return RT_OK;
+    int64_t cap = std::max<int64_t>(need, std::min<int64_t>(kMaxChildrenPerLaunch, std::max<int64_t>(4096, 2 * s.cap)));
+    RT_CUDA(h, cudaStreamSynchronize(h->stream), "ray buffer");
+    cudaFree(s.base);
+    s.base = nullptr;
+    s.cap = 0;
+    void* p = nullptr;
+    RT_CUDA(h, cudaMalloc(&p, ray_bytes(cap, (int)sizeof(R))), "ray buffer");
+    s.base = p;
+    s.cap = cap;
+    return RT_OK;
+}
+
+// March all rays of `level` whose parents are the first n records of the
+// level's buffer (level 0: the emitted sources), then recurse into the
+// next level, one slice of children at a time.
+template <class R>
+int run_level(rt_handle* h, int level, int64_t nparents)
+{
+    const int64_t total = level == 0 ? 12 * h->n_emit : 4 * nparents;
+    if (total <= 0) return RT_OK;
+    if (level > h->table_level || level > kMaxLevel)
+        return fail(h, RT_EDEVICE, "ray level beyond the direction table");
+    const bool can_split = level + 1 <= h->level_max;
+    for (int64_t c0 = 0; c0 < total; c0 += kMaxChildrenPerLaunch) {
+        const int64_t c1 = std::min(total, c0 + kMaxChildrenPerLaunch);
+        if (can_split) {
+            int rc = ensure_rays<R>(h, level + 1, c1 - c0);
+            if (rc) return rc;
+        }
+        RT_CUDA(h, cudaMemsetAsync(h->d_count + level + 1, 0, sizeof(unsigned long long), h->stream), "counter");
+        MarchArgs<R> a;
+        a.level = level;
+        a.n = h->cfg.n;
+        a.c0 = c0;
+        a.c1 = c1;
+        a.dirs = h->dirs + healpix_level_offset(level);
+        a.src = h->d_emit;
+        a.in = ray_view<R>(h->rays[level]);
+        a.out = can_split ? ray_view<R>(h->rays[level + 1]) : RayBuf<R>();
+        a.out_count = h->d_count + level + 1;
+        a.kap = static_cast<const R*>(h->d_kap);
+        a.gamma = h->d_gamma;
+        a.rq = h->rq;
+        a.level_max = h->level_max;
+        a.tau_max = (R)h->cfg.tau_max;
+        a.overlap_mode = h->cfg.overlap_mode;
+        a.hash = (h->cfg.flags & RT_FLAG_VISIT_HASH) ? 1 : 0;
+        a.st = h->d_st;
+        const int64_t warps = (c1 - c0 + 31) / 32;
+        const int64_t want = (warps + kMarchBlock / 32 - 1) / (kMarchBlock / 32);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->sm_count * 8));
+        RT_CUDA(h, cudaEventRecord(h->ev[4], h->stream), "event");
+        if constexpr (sizeof(R) == 8) launch_march_f64(a, grid, kMarchBlock, h->stream);
+        else launch_march_f32(a, grid, kMarchBlock, h->stream);
+        RT_LAUNCHED(h, "march launch");
+        RT_CUDA(h, cudaEventRecord(h->ev[5], h->stream), "event");
+        h->launches++;
+        h->march_launches++;
+        RT_CUDA(h, cudaMemcpyAsync(h->h_count + level + 1, h->d_count + level + 1, sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToHost, h->stream), "counter read");
+        RT_CUDA(h, cudaMemcpyAsync(h->h_i32, &h->d_st->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream),
+                "error read");
+        RT_CUDA(h, cudaStreamSynchronize(h->stream), "march");
+        if (h->h_i32[0]) return fail(h, RT_EDEVICE, "march kernel reported an internal error");
+        float ms = 0.f;
+        RT_CUDA(h, cudaEventElapsedTime(&ms, h->ev[4], h->ev[5]), "event");
+        h->ms_march += ms;
+        const int64_t next = (int64_t)h->h_count[level + 1];
+        if (next > 0) {
+            int rc = run_level<R>(h, level + 1, next);
+            if (rc) return rc;
+        }
+    }
+    return RT_OK;
+}
+
+int trace(rt_handle* h, const double* xuse)
+{
+    RT_CUDA(h, cudaMemsetAsync(h->d_gamma, 0, sizeof(double) * (size_t)h->ncell, h->stream), "gamma clear");
+    // per-trace part of the statistics: per-level counters, hash and ledger
+    RT_CUDA(h, cudaMemsetAsync(h->d_st, 0, offsetof(DevStats, deposited), h->stream), "stats clear");
+    double n_th = h->cfg.n_th_cm3;
+    if (n_th < 0) n_th = 0.01 * h->h_f64[1];
+    if (h->cfg.precision == RT_FP32)
+        launch_prepare_kappa_f32(h->d_nh, xuse, h->ncell, h->sdx, n_th, static_cast<float*>(h->d_kap), h->stream);
+    else
+        launch_prepare_kappa_f64(h->d_nh, xuse, h->ncell, h->sdx, n_th, static_cast<double*>(h->d_kap), h->stream);
+    RT_LAUNCHED(h, "kappa launch");
+    h->launches++;
+    h->march_launches = 0;
+    h->ms_march = 0.0;
+    RT_CUDA(h, cudaEventRecord(h->ev[1], h->stream), "event");
+    int rc = h->cfg.precision == RT_FP32 ? run_level<float>(h, 0, 0) : run_level<double>(h, 0, 0);
+    if (rc) return rc;
+    RT_CUDA(h, cudaEventRecord(h->ev[2], h->stream), "event");
+    return RT_OK;
+}
+
+bool valid_config(const rt_config* c, std::string& why)
+{
+    if (c->n < 1 || c->n > 1024) { why = "n must be in 1..1024"; return false; }
+    if (!(c->box_cm > 0) || !std::isfinite(c->box_cm)) { why = "box_cm must be positive"; return false; }
+    if (c->precision != RT_FP64 && c->precision != RT_FP32) { why = "precision must be RT_FP64 or RT_FP32"; return false; }
+    if (!(c->sigma_cm2 > 0)) { why = "sigma_cm2 must be positive"; return false; }
+    if (!(c->n_min_ray >= 1.0)) { why = "n_min_ray must be >= 1"; return false; }
+    if (!(c->tau_max > 0)) { why = "tau_max must be positive"; return false; }
+    if (c->overlap_mode < 0 || c->overlap_mode > 4) { why = "overlap_mode must be 0..4"; return false; }
+    if (c->merge_mode < 0 || c->merge_mode > 2) { why = "merge_mode must be 0..2"; return false; }
+    if (c->merge_samp_level < 0 || c->merge_samp_level > 4) { why = "merge_samp_level must be 0..4"; return false; }
+    if (!(c->merge_dr_cells > 0)) { why = "merge_dr_cells must be positive"; return false; }
+    if (c->level_max > kMaxLevel) { why = "level_max must be <= 13"; return false; }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rt_config_default(rt_config* c, int32_t n, double box_cm)
+{
+    std::memset(c, 0, sizeof(*c));
+    c->n = n;
+    c->box_cm = box_cm;
+    c->precision = RT_FP64;
+    c->sigma_cm2 = 6.3e-18;
+    c->n_min_ray = 4.0;
+    c->level_max = -1;
+    c->overlap_mode = RT_OVERLAP_CONSERVATIVE;
+    c->tau_max = 30.0;
+    c->n_th_cm3 = -1.0;
+    c->e_heat_erg = 1.602176634e-12;
+    c->merge_mode = RT_MERGE_OFF;
+    c->merge_samp_level = 3;
+    c->automerge_xbar = 0.018;
+    c->merge_x_th = 0.9;
+    c->merge_f_req = 0.9;
+    c->merge_dr_cells = 2.0;
+    c->merge_rmax_cells = 16.0;
+    c->merge_f_ov = 1.0;
+    c->merge_eps = 1e-6;
+    c->merge_n_min = 8;
+    c->chem_iterate = 0;
+    c->alpha_B = 2.59e-13;
+    c->C_H = 0.0;
+    c->clumping = 1.0;
+    c->chem_tol = 1e-6;
+    c->chem_max_iter = 100;
+    c->flags = 0;
+}
+
+const char* rt_version(void) { return "nyxrt 0.1 (sm_103a)"; }
+
+const char* rt_last_error(const rt_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int rt_destroy(rt_handle* h)
+{
+    if (!h) return RT_OK;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_nh); cudaFree(h->d_x); cudaFree(h->d_xavg); cudaFree(h->d_xend);
+    cudaFree(h->d_gamma); cudaFree(h->d_heat); cudaFree(h->d_kap); cudaFree(h->d_scalar);
+    SourceWork& w = h->sw;
+    cudaFree(w.cells_raw); cudaFree(w.ndot_raw); cudaFree(w.keys); cudaFree(w.order); cudaFree(w.flag);
+    cudaFree(w.head_pos); cudaFree(w.cells_a); cudaFree(w.ndot_a); cudaFree(w.cells_b); cudaFree(w.ndot_b);
+    cudaFree(w.label); cudaFree(w.parent); cudaFree(w.radius); cudaFree(w.count);
+    cudaFree(h->d_emit);
+    for (auto& r : h->rays) cudaFree(r.base);
+    cudaFree(h->d_count);
+    cudaFree(h->d_st);
+    cudaFreeHost(h->h_st);
+    cudaFreeHost(h->h_count);
+    cudaFreeHost(h->h_i32);
+    cudaFreeHost(h->h_f64);
+    for (auto& e : h->ev) if (e) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete h;
+    return RT_OK;
+}
+
+int rt_create(const rt_config* cfg, void* cuda_stream, rt_handle** out)
+{
+    if (!out) return RT_EINVAL;
+    *out = nullptr;
+    g_create_error.clear();
+    if (!cfg) { g_create_error = "cfg is NULL"; return RT_EINVAL; }
+    std::string why;
+    if (!valid_config(cfg, why)) { g_create_error = why; return RT_EINVAL; }
+    rt_handle* h = new (std::nothrow) rt_handle();
+    if (!h) { g_create_error = "host allocation failed"; return RT_ENOMEM; }
+    h->cfg = *cfg;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    const int64_t n = cfg->n;
+    h->ncell = n * n * n;
+    // the same IEEE operations as the problem statement: dx = L / n
+    h->dx = cfg->box_cm / (double)n;
+    h->vol = h->dx * h->dx * h->dx;
+    h->sdx = cfg->sigma_cm2 * h->dx;
+    h->s_over_dx2 = cfg->sigma_cm2 / (h->dx * h->dx);
+    // R_0 = sqrt(3 / (pi N_min)) in units of 2^-24 cells (Eq. 4 with Omega_c = dx^2 / R^2)
+    h->rq = (int64_t)std::floor(std::sqrt(3.0 / (3.141592653589793 * cfg->n_min_ray)) * (double)(1 << kRadBits) + 0.5);
+    // smallest level whose split sphere encloses the grid from any cell centre
+    int reach = 0;
+    while (std::ldexp((double)h->rq, reach - kRadBits) < std::sqrt(3.0) * (double)n) ++reach;
+    h->level_max = cfg->level_max >= 0 ? cfg->level_max : std::min(reach + 1, kMaxLevel);
+    h->table_level = std::min(h->level_max, reach);
+    const int need_level = std::max(h->table_level, cfg->merge_samp_level);
+    int rc = ensure_directions(h->device, need_level, &h->dirs, why);
+    if (rc) { g_create_error = why; rt_destroy(h); return rc; }
+
+    cudaError_t e = cudaSuccess;
+    const size_t fb = sizeof(double) * (size_t)h->ncell;
+    e = e ? e : cudaMalloc(&h->d_nh, fb);
+    e = e ? e : cudaMalloc(&h->d_x, fb);
+    e = e ? e : cudaMalloc(&h->d_gamma, fb);
+    e = e ? e : cudaMalloc(&h->d_heat, fb);
+    e = e ? e : cudaMalloc(&h->d_kap, cfg->precision == RT_FP32 ? fb / 2 : fb);
+    if (cfg->chem_iterate) {
+        e = e ? e : cudaMalloc(&h->d_xavg, fb);
+        e = e ? e : cudaMalloc(&h->d_xend, fb);
+    }
+    e = e ? e : cudaMalloc(&h->d_scalar, 64);
+    e = e ? e : cudaMalloc(&h->d_count, sizeof(unsigned long long) * (RT_MAX_LEVELS + 1));
+    e = e ? e : cudaMalloc(&h->d_st, sizeof(DevStats));
+    e = e ? e : cudaMallocHost(&h->h_st, sizeof(DevStats));
+    e = e ? e : cudaMallocHost(&h->h_count, sizeof(unsigned long long) * (RT_MAX_LEVELS + 1));
+    e = e ? e : cudaMallocHost(&h->h_i32, 64);
+    e = e ? e : cudaMallocHost(&h->h_f64, 64);
+    for (auto& ev : h->ev) e = e ? e : cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = std::string("allocation failed: ") + cudaGetErrorString(e);
+        rt_destroy(h);
+        return e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;
+    }
+    *out = h;
+    return RT_OK;
+}
+
+int rt_set_fields(rt_handle* h, const double* n_H, const double* x_ion, int where)
+{
+    if (!h || !n_H || !x_ion || (where != RT_HOST && where != RT_DEVICE)) return h ? fail(h, RT_EINVAL, "bad arguments") : RT_EINVAL;
+    if (h->sticky) return RT_ESTATE;
+    DeviceGuard g(h->device);
+    const size_t fb = sizeof(double) * (size_t)h->ncell;
+    const cudaMemcpyKind k = where == RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    RT_CUDA(h, cudaMemcpyAsync(h->d_nh, n_H, fb, k, h->stream), "field copy");
+    RT_CUDA(h, cudaMemcpyAsync(h->d_x, x_ion, fb, k, h->stream), "field copy");
+    if (where == RT_HOST) RT_CUDA(h, cudaStreamSynchronize(h->stream), "field copy");
+    h->fields_set = true;
+    return RT_OK;
+}
+
+int rt_add_sources(rt_handle* h, const int32_t* cell_ijk, const double* ndot, int64_t n, int where)
+{
+    if (!h) return RT_EINVAL;
+    if (n < 0 || (n > 0 && (!cell_ijk || !ndot)) || (where != RT_HOST && where != RT_DEVICE))
+        return fail(h, RT_EINVAL, "bad arguments");
+    if (h->sticky) return RT_ESTATE;
+    if (n == 0) return RT_OK;
+    if (h->nsrc + n > (int64_t(1) << 30)) return fail(h, RT_EINVAL, "too many sources");
+    if (where == RT_HOST) {
+        for (int64_t i = 0; i < n; ++i) {
+            for (int a = 0; a < 3; ++a)
+                if (cell_ijk[3 * i + a] < 0 || cell_ijk[3 * i + a] >= h->cfg.n) return fail(h, RT_EINVAL, "source cell outside the grid");
+            if (!(ndot[i] > 0) || !std::isfinite(ndot[i])) return fail(h, RT_EINVAL, "source rate must be positive and finite");
+        }
+    }
+    DeviceGuard g(h->device);
+    int rc = grow_sources(h, h->nsrc + n);
+    if (rc) return rc;
+    const cudaMemcpyKind k = where == RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    RT_CUDA(h, cudaMemcpyAsync(h->sw.cells_raw + 3 * h->nsrc, cell_ijk, 12 * (size_t)n, k, h->stream), "source copy");
+    RT_CUDA(h, cudaMemcpyAsync(h->sw.ndot_raw + h->nsrc, ndot, 8 * (size_t)n, k, h->stream), "source copy");
+    if (where == RT_HOST) RT_CUDA(h, cudaStreamSynchronize(h->stream), "source copy");
+    h->nsrc += n;
+    return RT_OK;
+}
+
+int rt_clear_sources(rt_handle* h)
+{
+    if (!h) return RT_EINVAL;
+    if (h->sticky) return RT_ESTATE;
+    h->nsrc = 0;
+    return RT_OK;
+}
+
+int rt_get_x(rt_handle* h, double* x_out, int where)
+{
+    if (!h || !x_out || (where != RT_HOST && where != RT_DEVICE)) return h ? fail(h, RT_EINVAL, "bad arguments") : RT_EINVAL;
+    if (h->sticky) return RT_ESTATE;
+    DeviceGuard g(h->device);
+    RT_CUDA(h, cudaMemcpyAsync(x_out, h->d_x, sizeof(double) * (size_t)h->ncell,
+                               where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream), "x copy");
+    RT_CUDA(h, cudaStreamSynchronize(h->stream), "x copy");
+    return RT_OK;
+}
+
+int rt_step(rt_handle* h, double dt_s, double* gamma_out, double* heat_out, int where, rt_stats* st)
+{
+    if (!h) return RT_EINVAL;
+    if (h->sticky) return RT_ESTATE;
+    if (where != RT_HOST && where != RT_DEVICE) return fail(h, RT_EINVAL, "bad where");
+    if (!h->fields_set) return fail(h, RT_ESTATE, "rt_set_fields has not been called");
+    if (h->cfg.chem_iterate && !(dt_s > 0)) return fail(h, RT_EINVAL, "dt_s must be positive with chem_iterate");
+    DeviceGuard g(h->device);
+    cudaStream_t s = h->stream;
+    h->launches = 0;
+    h->err.clear();
+    RT_CUDA(h, cudaMemsetAsync(h->d_st, 0, sizeof(DevStats), s), "stats clear");
+    RT_CUDA(h, cudaEventRecord(h->ev[0], s), "event");
+
+    // ---- validation of device-resident inputs
+    h->launches += launch_validate_fields(h->d_nh, h->d_x, h->ncell, h->d_st, s);
+    h->launches += launch_validate_sources(h->sw.cells_raw, h->sw.ndot_raw, h->nsrc, h->cfg.n, h->d_st, s);
+    RT_LAUNCHED(h, "validation launch");
+
+    // ---- sources: dedup + sort (Sec. 2.8)
+    h->launches += launch_dedup_sort(h->sw, h->nsrc, s);
+    RT_LAUNCHED(h, "source launch");
+    bool want_mean_nh = h->cfg.n_th_cm3 < 0;
+    if (want_mean_nh) {
+        RT_CUDA(h, cudaMemsetAsync(h->d_scalar, 0, sizeof(double), s), "scalar clear");
+        h->launches += launch_mean_nh(h->d_nh, h->ncell, h->d_scalar, s);
+    }
+    if (h->cfg.merge_mode == RT_MERGE_AUTO) h->launches += launch_sum_x(h->d_x, h->ncell, h->d_st, s);
+    RT_LAUNCHED(h, "reduction launch");
+    RT_CUDA(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "stats read");
+    if (h->nsrc > 0)
+        RT_CUDA(h, cudaMemcpyAsync(h->h_i32, h->sw.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count read");
+    if (want_mean_nh)
+        RT_CUDA(h, cudaMemcpyAsync(h->h_f64, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s), "mean read");
+    RT_CUDA(h, cudaStreamSynchronize(s), "source stage");
+    if (h->h_st->bad_input) return fail(h, RT_EINVAL, "invalid field or source values (n_H < 0, x outside [0,1], non-finite, bad source)");
+    h->h_f64[1] = want_mean_nh ? h->h_f64[0] / (double)h->ncell : 0.0;
+    int64_t m = h->nsrc > 0 ? h->h_i32[0] : 0;
+    const int64_t n_dedup = m;
+    const double xbar = h->h_st->xsum / (double)h->ncell;
+
+    // ---- Alg. 3 source merging
+    bool merged = false;
+    if (m > 0 && (h->cfg.merge_mode == RT_MERGE_FORCED ||
+                  (h->cfg.merge_mode == RT_MERGE_AUTO && xbar > h->cfg.automerge_xbar))) {
+        const int Ls = h->cfg.merge_samp_level;
+        h->launches += launch_merge(h->sw, m, h->cfg.n, h->d_x, h->dirs + healpix_level_offset(Ls),
+                                    (int)(12 * (int64_t(1) << (2 * Ls))), h->cfg.merge_x_th, h->cfg.merge_f_req,
+                                    h->cfg.merge_n_min, h->cfg.merge_dr_cells, h->cfg.merge_rmax_cells,
+                                    h->cfg.merge_f_ov, h->cfg.merge_eps, h->d_st, s);
+        RT_LAUNCHED(h, "merge launch");
+        RT_CUDA(h, cudaMemcpyAsync(h->h_i32, h->sw.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count read");
+        RT_CUDA(h, cudaMemcpyAsync(h->h_i32 + 1, &h->d_st->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "err read");
+        RT_CUDA(h, cudaStreamSynchronize(s), "merge");
+        if (h->h_i32[1]) return fail(h, RT_EDEVICE, "source merge reported an internal error");
+        m = h->h_i32[0];
+        merged = true;
+    }
+    h->launches += launch_build_emit(h->sw, m, h->s_over_dx2, h->d_emit, h->d_st, s);
+    RT_LAUNCHED(h, "emit launch");
+    h->n_emit = m;
+
+    // ---- trace, optionally iterated with the C2-Ray update (Sec. 2.4)
+    int iters = 0;
+    double resid = 0.0;
+    const double* xuse = h->d_x;
+    if (h->cfg.chem_iterate) {
+        RT_CUDA(h, cudaMemcpyAsync(h->d_xavg, h->d_x, sizeof(double) * (size_t)h->ncell, cudaMemcpyDeviceToDevice, s), "x copy");
+        xuse = h->d_xavg;
+        const int maxit = h->cfg.chem_max_iter > 0 ? h->cfg.chem_max_iter : 100;
+        for (;;) {
+            int rc = trace(h, h->d_xavg);
+            if (rc) return rc;
+            ++iters;
+            // the update overwrites <x>; keep the traced one for heating until convergence is known
+            RT_CUDA(h, cudaMemcpyAsync(h->d_heat, h->d_xavg, sizeof(double) * (size_t)h->ncell, cudaMemcpyDeviceToDevice, s),
+                    "x copy");
+            RT_CUDA(h, cudaMemsetAsync(&h->d_st->maxdiff, 0, sizeof(double), s), "clear");
+            h->launches += launch_chem_update(h->d_nh, h->d_x, h->d_xavg, h->d_xend, h->d_gamma, h->ncell, dt_s,
+                                              h->cfg.alpha_B, h->cfg.C_H, h->cfg.clumping, h->d_st, s);
+            RT_LAUNCHED(h, "chemistry launch");
+            RT_CUDA(h, cudaMemcpyAsync(h->h_f64 + 2, &h->d_st->maxdiff, sizeof(double), cudaMemcpyDeviceToHost, s),
+                    "residual read");
+            RT_CUDA(h, cudaStreamSynchronize(s), "chemistry");
+            resid = h->h_f64[2];
+            if (resid < h->cfg.chem_tol || iters >= maxit) break;
+        }
+        // heating uses the <x> the last trace used (saved in d_heat); new x = x(t + dt)
+        std::swap(h->d_xavg, h->d_heat);
+        xuse = h->d_xavg;
+    } else {
+        int rc = trace(h, h->d_x);
+        if (rc) return rc;
+        iters = 1;
+    }
+
+    // ---- heating, deposited photons
+    RT_CUDA(h, cudaMemsetAsync(&h->d_st->deposited, 0, sizeof(double), s), "clear");
+    h->launches += launch_finalize(h->d_gamma, h->d_nh, xuse, h->ncell, h->cfg.e_heat_erg, h->vol, h->d_heat, h->d_st, s);
+    RT_LAUNCHED(h, "finalize launch");
+    if (h->cfg.chem_iterate)
+        RT_CUDA(h, cudaMemcpyAsync(h->d_x, h->d_xend, sizeof(double) * (size_t)h->ncell, cudaMemcpyDeviceToDevice, s),
+                "x update");
+    const size_t fb = sizeof(double) * (size_t)h->ncell;
+    const cudaMemcpyKind k = where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (gamma_out) RT_CUDA(h, cudaMemcpyAsync(gamma_out, h->d_gamma, fb, k, s), "gamma copy");
+    if (heat_out) RT_CUDA(h, cudaMemcpyAsync(heat_out, h->d_heat, fb, k, s), "heat copy");
+    RT_CUDA(h, cudaEventRecord(h->ev[3], s), "event");
+    RT_CUDA(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "stats read");
+    RT_CUDA(h, cudaStreamSynchronize(s), "step");
+    if (h->h_st->err) return fail(h, RT_EDEVICE, "a kernel reported an internal error");
+
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        const DevStats& d = *h->h_st;
+        st->n_src_in = h->nsrc;
+        st->n_src_dedup = n_dedup;
+        st->n_src_emit = m;
+        st->merged = merged ? 1 : 0;
+        st->chem_iters = iters;
+        st->level_max = h->level_max;
+        st->launches = h->launches;
+        for (int l = 0; l < RT_MAX_LEVELS; ++l) {
+            st->rays[l] = (int64_t)d.rays[l];
+            st->splits[l] = (int64_t)d.splits[l];
+            st->escaped[l] = (int64_t)d.escaped[l];
+            st->dropped_tau[l] = (int64_t)d.dropped_tau[l];
+            st->dropped_level[l] = (int64_t)d.dropped_level[l];
+            st->segments[l] = (int64_t)d.segments[l];
+            st->secondary[l] = (int64_t)d.secondary[l];
+        }
+        st->emitted_ph = d.emitted;
+        st->visit_hash = d.visit_hash;
+        st->absorbed_ph = d.absorbed;
+        st->escaped_ph = d.escaped_ph;
+        st->dropped_ph = d.dropped_ph;
+        st->deposited_ph = d.deposited;
+        st->chem_residual = resid;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]);
+        st->ms_trace = ms;
+        cudaEventElapsedTime(&ms, h->ev[0], h->ev[3]);
+        st->ms_step = ms;
+        st->ms_march = h->ms_march;
+        st->march_launches = h->march_launches;
+    }
+    return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,417 @@
+// Source handling before the march (Sec. 2.8): sources that share a cell
+// are merged by summing their rates, the catalog is sorted lexicographically
+// by (ix, iy, iz), and optionally sources whose ionized bubbles overlap are
+// merged (Alg. 3: MAX_RADIUS by shell sampling, union-find over overlapping
+// pairs, one source per group at the member nearest the flux-weighted
+// centroid). Catalogs are at most tens of thousands of entries, so the sorts
+// are exact O(S^2) rank computations tiled through shared memory and the
+// pair test is a dense O(S^2) sweep; every per-group sum runs sequentially
+// in member order, so the emitted catalog is deterministic.
+#include <cstdint>
+
+#include "rt_internal.h"
+
+namespace nyx {
+namespace {
+
+constexpr int kBlock = 256;
+
+int blocks_for(int64_t count)
+{
+    const int64_t g = (count + kBlock - 1) / kBlock;
+    return g < 1 ? 1 : (int)g;
+}
+
+__device__ __forceinline__ uint64_t cell_key(int x, int y, int z)
+{
+    return ((uint64_t)x << 42) | ((uint64_t)y << 21) | (uint64_t)z;
+}
+
+__global__ void validate_sources_kernel(const int32_t* __restrict__ cells, const double* __restrict__ ndot,
+                                        int64_t nsrc, int n, DevStats* st)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nsrc; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = cells[3 * i], y = cells[3 * i + 1], z = cells[3 * i + 2];
+        const double v = ndot[i];
+        if ((unsigned)x >= (unsigned)n || (unsigned)y >= (unsigned)n || (unsigned)z >= (unsigned)n || !(v > 0.0) ||
+            !isfinite(v))
+            atomicAdd(&st->bad_input, 1u);
+    }
+}
+
+__global__ void cell_keys_kernel(const int32_t* __restrict__ cells, int64_t m, uint64_t* __restrict__ keys)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = cell_key(cells[3 * i], cells[3 * i + 1], cells[3 * i + 2]);
+}
+
+// order[rank(i)] = i with rank(i) = #{j : key_j < key_i or (key_j = key_i and j < i)}: a stable sort.
+__global__ void __launch_bounds__(kBlock) rank_kernel(const uint64_t* __restrict__ keys, int64_t m,
+                                                      int32_t* __restrict__ order)
+{
+    __shared__ uint64_t tile[kBlock];
+    const int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+    const bool valid = i < m;
+    const uint64_t ki = valid ? keys[i] : 0;
+    int64_t rank = 0;
+    for (int64_t t0 = 0; t0 < m; t0 += kBlock) {
+        const int64_t jl = t0 + threadIdx.x;
+        tile[threadIdx.x] = jl < m ? keys[jl] : ~0ULL;
+        __syncthreads();
+        const int lim = (int)((m - t0) < kBlock ? (m - t0) : kBlock);
+        for (int jj = 0; jj < lim; ++jj) {
+            const uint64_t kj = tile[jj];
+            rank += (kj < ki) || (kj == ki && t0 + jj < i);
+        }
+        __syncthreads();
+    }
+    if (valid) order[rank] = (int32_t)i;
+}
+
+// flag[p] = 1 where sorted entry p starts a run of equal keys.
+__global__ void run_heads_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ order, int64_t m,
+                                 uint64_t mask, int32_t* __restrict__ flag)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x)
+        flag[p] = (p == 0) || ((keys[order[p]] & mask) != (keys[order[p - 1]] & mask));
+}
+
+// Exclusive prefix sum of flag[0..m) into pos, total into *total (one block).
+__global__ void __launch_bounds__(1024) scan_kernel(const int32_t* __restrict__ flag, int64_t m,
+                                                    int32_t* __restrict__ pos, int32_t* __restrict__ total)
+{
+    __shared__ int32_t sh[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (m + 1023) / 1024;
+    const int64_t b = t * per, e = (b + per < m) ? b + per : m;
+    int32_t local = 0;
+    for (int64_t p = b; p < e; ++p) local += flag[p];
+    sh[t] = local;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int32_t v = t >= o ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += v;
+        __syncthreads();
+    }
+    int32_t off = sh[t] - local;
+    for (int64_t p = b; p < e; ++p) {
+        pos[p] = off;
+        off += flag[p];
+    }
+    if (t == 1023) *total = sh[1023];
+}
+
+// For each run head: sum the rates of the run in sorted (= input) order.
+__global__ void dedup_sum_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ order,
+                                 const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t m,
+                                 const int32_t* __restrict__ cells, const double* __restrict__ ndot,
+                                 int32_t* __restrict__ out_cells, double* __restrict__ out_ndot)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[p]) continue;
+        const int32_t i = order[p];
+        double s = ndot[i];
+        for (int64_t q = p + 1; q < m && !flag[q]; ++q) s = __dadd_rn(s, ndot[order[q]]);
+        const int32_t u = pos[p];
+        out_cells[3 * u] = cells[3 * i];
+        out_cells[3 * u + 1] = cells[3 * i + 1];
+        out_cells[3 * u + 2] = cells[3 * i + 2];
+        out_ndot[u] = s;
+    }
+}
+
+// ---------------------------------------------------------------- Alg. 3
+
+// MAX_RADIUS: one block per source. Shells r = dr, 2 dr, ... <= R_max are
+// sampled at the HEALPix directions of the sample level; a sample is the
+// cell floor(c + 1/2 + r d); the shell's point set is the distinct in-grid
+// sample cells (bitonic sort in shared memory, then run heads).
+template <int NP2>
+__global__ void __launch_bounds__(kBlock) radius_kernel(const int32_t* __restrict__ cells, int64_t m, int n,
+                                                        const double* __restrict__ x, const int4* __restrict__ dirs,
+                                                        int ns, double x_th, double f_req, int n_min, double dr,
+                                                        double rmax, double* __restrict__ radius)
+{
+    __shared__ long long key[NP2];
+    __shared__ int red[2];
+    const int64_t si = blockIdx.x;
+    if (si >= m) return;
+    const int c[3] = {cells[3 * si], cells[3 * si + 1], cells[3 * si + 2]};
+    const int64_t nn = n;
+    if (x[((int64_t)c[2] * nn + c[1]) * nn + c[0]] < x_th) {
+        if (threadIdx.x == 0) radius[si] = 0.0;
+        return;
+    }
+    const double inv = 1.0 / (double)(1 << kDirBits);
+    double result = rmax;
+    for (double r = dr; r <= rmax; r = __dadd_rn(r, dr)) {
+        for (int p = threadIdx.x; p < NP2; p += blockDim.x) {
+            long long k = 0x7fffffffffffffffLL;
+            if (p < ns) {
+                const int4 d = dirs[p];
+                const int dd[3] = {d.x, d.y, d.z};
+                long long q[3];
+                bool inside = true;
+                for (int a = 0; a < 3; ++a) {
+                    const double pos = __dadd_rn(__dadd_rn((double)c[a], 0.5), __dmul_rn(r, __dmul_rn((double)dd[a], inv)));
+                    q[a] = (long long)floor(pos);
+                    if (q[a] < 0 || q[a] >= nn) inside = false;
+                }
+                if (inside) k = (q[2] * nn + q[1]) * nn + q[0];
+            }
+            key[p] = k;
+        }
+        __syncthreads();
+        for (int size = 2; size <= NP2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = threadIdx.x; t < NP2 / 2; t += blockDim.x) {
+                    const int lo = 2 * t - (t & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = ((lo & size) == 0);
+                    const long long a = key[lo], b = key[hi];
+                    if ((a > b) == up) { key[lo] = b; key[hi] = a; }
+                }
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x < 2) red[threadIdx.x] = 0;
+        __syncthreads();
+        int ntot = 0, nion = 0;
+        for (int p = threadIdx.x; p < NP2; p += blockDim.x) {
+            const long long k = key[p];
+            if (k != 0x7fffffffffffffffLL && (p == 0 || key[p - 1] != k)) {
+                ++ntot;
+                if (x[k] >= x_th) ++nion;
+            }
+        }
+        atomicAdd(&red[0], ntot);
+        atomicAdd(&red[1], nion);
+        __syncthreads();
+        ntot = red[0];
+        nion = red[1];
+        bool fail;
+        if (ntot < n_min) fail = nion < ntot;
+        else fail = __ddiv_rn((double)nion, (double)ntot) < f_req;
+        __syncthreads();
+        if (fail) {
+            result = __dsub_rn(r, dr);
+            break;
+        }
+    }
+    if (threadIdx.x == 0) radius[si] = result;
+}
+
+__device__ __forceinline__ int uf_find(int* parent, int a)
+{
+    int p = atomicAdd(&parent[a], 0);
+    while (p != a) {
+        a = p;
+        p = atomicAdd(&parent[a], 0);
+    }
+    return a;
+}
+
+// Pairs (a, b > a) whose bubbles overlap (both radii > 0,
+// d^2 <= (f_ov (r_a + r_b))^2 + eps) are united; the larger root is hooked
+// under the smaller, so each component's root is its smallest index.
+__global__ void pair_union_kernel(const int32_t* __restrict__ cells, const double* __restrict__ radius, int64_t m,
+                                  double f_ov, double eps, int* parent, DevStats* st)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
+        const double ra = radius[a];
+        if (!(ra > 0.0)) continue;
+        const int ax = cells[3 * a], ay = cells[3 * a + 1], az = cells[3 * a + 2];
+        for (int64_t b = a + 1; b < m; ++b) {
+            const double rb = radius[b];
+            if (!(rb > 0.0)) continue;
+            const long long dx = ax - cells[3 * b], dy = ay - cells[3 * b + 1], dz = az - cells[3 * b + 2];
+            const long long d2 = dx * dx + dy * dy + dz * dz;
+            const double rs = __dmul_rn(f_ov, __dadd_rn(ra, rb));
+            if ((double)d2 <= __dadd_rn(__dmul_rn(rs, rs), eps)) {
+                int u = (int)a, v = (int)b;
+                for (int tries = 0;; ++tries) {
+                    u = uf_find(parent, u);
+                    v = uf_find(parent, v);
+                    if (u == v) break;
+                    if (u > v) { const int t = u; u = v; v = t; }
+                    if (atomicCAS(&parent[v], v, u) == v) break;
+                    if (tries > (1 << 20)) { atomicOr(&st->err, kErrUnionFind); break; }
+                }
+            }
+        }
+    }
+}
+
+__global__ void label_keys_kernel(int* parent, int64_t m, int32_t* __restrict__ label, uint64_t* __restrict__ keys)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = uf_find(parent, (int)i);
+        label[i] = r;
+        keys[i] = ((uint64_t)(uint32_t)r << 32) | (uint64_t)i;
+    }
+}
+
+// One merged source per group (members contiguous in `order`, by index):
+// summed rate, flux-weighted centroid rounded and clamped into the grid,
+// snapped to the nearest member (first in order on ties).
+__global__ void group_kernel(const int32_t* __restrict__ order, const int32_t* __restrict__ flag,
+                             const int32_t* __restrict__ pos, int64_t m, int n, const int32_t* __restrict__ cells,
+                             const double* __restrict__ ndot, int32_t* __restrict__ out_cells,
+                             double* __restrict__ out_ndot)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[p]) continue;
+        int64_t e = p + 1;
+        while (e < m && !flag[e]) ++e;
+        const int32_t g = order[p];
+        double ftot = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int64_t q = p; q < e; ++q) {
+            const int32_t j = order[q];
+            const double v = ndot[j];
+            ftot = __dadd_rn(ftot, v);
+            sx = __dadd_rn(sx, __dmul_rn(v, (double)cells[3 * j]));
+            sy = __dadd_rn(sy, __dmul_rn(v, (double)cells[3 * j + 1]));
+            sz = __dadd_rn(sz, __dmul_rn(v, (double)cells[3 * j + 2]));
+        }
+        const int32_t u = pos[p];
+        if (e - p == 1) {
+            out_cells[3 * u] = cells[3 * g];
+            out_cells[3 * u + 1] = cells[3 * g + 1];
+            out_cells[3 * u + 2] = cells[3 * g + 2];
+            out_ndot[u] = ndot[g];
+            continue;
+        }
+        long long rc[3];
+        const double cs[3] = {sx, sy, sz};
+        for (int a = 0; a < 3; ++a) {
+            long long v = (long long)floor(__dadd_rn(__ddiv_rn(cs[a], ftot), 0.5));
+            v = v < 0 ? 0 : (v > n - 1 ? n - 1 : v);
+            rc[a] = v;
+        }
+        int32_t best = -1;
+        long long bestd = 0;
+        for (int64_t q = p; q < e; ++q) {
+            const int32_t j = order[q];
+            long long d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                const long long d = (long long)cells[3 * j + a] - rc[a];
+                d2 += d * d;
+            }
+            if (best < 0 || d2 < bestd) { best = j; bestd = d2; }
+        }
+        out_cells[3 * u] = cells[3 * best];
+        out_cells[3 * u + 1] = cells[3 * best + 1];
+        out_cells[3 * u + 2] = cells[3 * best + 2];
+        out_ndot[u] = ftot;
+    }
+}
+
+__global__ void gather_kernel(const int32_t* __restrict__ order, int64_t m, const int32_t* __restrict__ cells,
+                              const double* __restrict__ ndot, int32_t* __restrict__ out_cells,
+                              double* __restrict__ out_ndot)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = order[p];
+        out_cells[3 * p] = cells[3 * i];
+        out_cells[3 * p + 1] = cells[3 * i + 1];
+        out_cells[3 * p + 2] = cells[3 * i + 2];
+        out_ndot[p] = ndot[i];
+    }
+}
+
+// Entries at or beyond *count sort last.
+__global__ void mask_tail_kernel(uint64_t* __restrict__ keys, int64_t m, const int32_t* __restrict__ count)
+{
+    const int64_t c = *count;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        if (i >= c) keys[i] = ~0ULL;
+}
+
+__global__ void iota_kernel(int* parent, int64_t m)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        parent[i] = (int)i;
+}
+
+__global__ void build_emit_kernel(const int32_t* __restrict__ cells, const double* __restrict__ ndot, int64_t m,
+                                  double s_over_dx2, SrcEntry* __restrict__ out, DevStats* st)
+{
+    double emitted = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        SrcEntry e;
+        e.cx = cells[3 * i];
+        e.cy = cells[3 * i + 1];
+        e.cz = cells[3 * i + 2];
+        e.pad = 0;
+        e.ph = __ddiv_rn(ndot[i], 12.0);
+        e.gd = __dmul_rn(e.ph, s_over_dx2);
+        e.gf = __double2float_rn(e.gd);
+        e.pad2 = 0.f;
+        out[i] = e;
+        emitted += ndot[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) emitted += __shfl_down_sync(0xffffffffu, emitted, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&st->emitted, emitted);
+}
+
+}  // namespace
+
+int launch_validate_sources(const int32_t* cells, const double* ndot, int64_t nsrc, int n, DevStats* st,
+                             cudaStream_t s)
+{
+    if (nsrc <= 0) return 0;
+    validate_sources_kernel<<<blocks_for(nsrc), kBlock, 0, s>>>(cells, ndot, nsrc, n, st);
+    return 1;
+}
+
+int launch_dedup_sort(SourceWork& w, int64_t nsrc, cudaStream_t s)
+{
+    if (nsrc <= 0) return 0;
+    const int b = blocks_for(nsrc);
+    cell_keys_kernel<<<b, kBlock, 0, s>>>(w.cells_raw, nsrc, w.keys);
+    rank_kernel<<<b, kBlock, 0, s>>>(w.keys, nsrc, w.order);
+    run_heads_kernel<<<b, kBlock, 0, s>>>(w.keys, w.order, nsrc, ~0ULL, w.flag);
+    scan_kernel<<<1, 1024, 0, s>>>(w.flag, nsrc, w.head_pos, w.count);
+    dedup_sum_kernel<<<b, kBlock, 0, s>>>(w.keys, w.order, w.flag, w.head_pos, nsrc, w.cells_raw, w.ndot_raw,
+                                          w.cells_a, w.ndot_a);
+    return 5;
+}
+
+int launch_merge(SourceWork& w, int64_t m, int n, const double* x, const int4* samp_dirs, int samp_count,
+                  double x_th, double f_req, int n_min, double dr, double rmax, double f_ov, double eps,
+                  DevStats* st, cudaStream_t s)
+{
+    if (m <= 0) return 0;
+    const int b = blocks_for(m);
+    const int grid_r = (int)m;
+    if (samp_count <= 1024)
+        radius_kernel<1024><<<grid_r, kBlock, 0, s>>>(w.cells_a, m, n, x, samp_dirs, samp_count, x_th, f_req, n_min,
+                                                      dr, rmax, w.radius);
+    else
+        radius_kernel<4096><<<grid_r, kBlock, 0, s>>>(w.cells_a, m, n, x, samp_dirs, samp_count, x_th, f_req, n_min,
+                                                      dr, rmax, w.radius);
+    iota_kernel<<<b, kBlock, 0, s>>>(w.parent, m);
+    pair_union_kernel<<<b, kBlock, 0, s>>>(w.cells_a, w.radius, m, f_ov, eps, w.parent, st);
+    label_keys_kernel<<<b, kBlock, 0, s>>>(w.parent, m, w.label, w.keys);
+    rank_kernel<<<b, kBlock, 0, s>>>(w.keys, m, w.order);
+    run_heads_kernel<<<b, kBlock, 0, s>>>(w.keys, w.order, m, 0xffffffff00000000ULL, w.flag);
+    scan_kernel<<<1, 1024, 0, s>>>(w.flag, m, w.head_pos, w.count);
+    group_kernel<<<b, kBlock, 0, s>>>(w.order, w.flag, w.head_pos, m, n, w.cells_a, w.ndot_a, w.cells_b, w.ndot_b);
+    // final lexicographic order of the merged catalog (its size is count[0] <= m; unused tail keys sort last)
+    cell_keys_kernel<<<b, kBlock, 0, s>>>(w.cells_b, m, w.keys);
+    mask_tail_kernel<<<b, kBlock, 0, s>>>(w.keys, m, w.count);
+    rank_kernel<<<b, kBlock, 0, s>>>(w.keys, m, w.order);
+    gather_kernel<<<b, kBlock, 0, s>>>(w.order, m, w.cells_b, w.ndot_b, w.cells_a, w.ndot_a);
+    return 12;
+}
+
+int launch_build_emit(const SourceWork& w, int64_t m, double s_over_dx2, SrcEntry* out, DevStats* st,
+                      cudaStream_t s)
+{
+    if (m <= 0) return 0;
+    build_emit_kernel<<<blocks_for(m), kBlock, 0, s>>>(w.cells_a, w.ndot_a, m, s_over_dx2, out, st);
+    return 1;
+}
+
+}  // namespace nyx

@@ -1,0 +1,87 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads,
+exports every entry point include/nyxrt.h declares, and the ctypes binding's
+struct layouts match the C header (checked with a gcc-compiled probe)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2512_12466_gb300 as nyx
+from paper_2512_12466_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nyxrt.h")
+
+
+@pytest.fixture(scope="module")
+def built():
+    return _build.build()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_\w+)\s*\(", text)))
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    for f in ["rt_create", "rt_set_fields", "rt_add_sources", "rt_step", "rt_destroy"]:
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(rt_\w+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    lib = C.CDLL(built)
+    for f in declared_functions():
+        getattr(lib, f)
+    assert set(nyx.exported_symbols()) == set(declared_functions())
+
+
+def test_struct_layout_matches_header(tmp_path):
+    fields_c = [f for f, _ in nyx.rt_config._fields_]
+    fields_s = [f for f, _ in nyx.rt_stats._fields_]
+    prog = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
+    prog.append('printf("config %zu\\n", sizeof(rt_config));')
+    prog.append('printf("stats %zu\\n", sizeof(rt_stats));')
+    for f in fields_c:
+        prog.append(f'printf("c.{f} %zu\\n", offsetof(rt_config, {f}));')
+    for f in fields_s:
+        prog.append(f'printf("s.{f} %zu\\n", offsetof(rt_stats, {f}));')
+    prog.append("return 0; }")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(prog))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-o", str(exe), str(src)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n")
+               if line)
+    assert int(got["config"]) == C.sizeof(nyx.rt_config)
+    assert int(got["stats"]) == C.sizeof(nyx.rt_stats)
+    for f in fields_c:
+        assert int(got["c." + f]) == getattr(nyx.rt_config, f).offset, f
+    for f in fields_s:
+        assert int(got["s." + f]) == getattr(nyx.rt_stats, f).offset, f
+
+
+def test_config_defaults_host_only(built):
+    cfg = nyx.rt_config_default(64, 1e22)
+    assert cfg.n == 64 and cfg.box_cm == 1e22
+    assert cfg.precision == nyx.RT_FP64 and cfg.overlap_mode == nyx.RT_OVERLAP_CONSERVATIVE
+    assert cfg.n_min_ray == 4.0 and cfg.tau_max == 30.0 and cfg.level_max == -1
+    assert cfg.merge_dr_cells == 2.0 and cfg.merge_samp_level == 3
+    assert "sm_103a" in nyx.rt_version()
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The binding and the CUDA sources never reference the CPU oracle."""
+    pkg = os.path.join(ROOT, "paper_2512_12466_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text.lower() or f == "inputs.py", f

@@ -1,0 +1,331 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar: ray, split, termination, segment and secondary-deposit counts per level
+and the visit-list hash are bit-exact; Gamma and heating agree within 1e-12
+relative L2 for the FP64 march and within 1e-5 of the FP64 oracle for the
+FP32 march (whose bookkeeping is compared bit-exactly with the oracle's FP32
+variant); the photon ledger closes to 1e-12 (FP64) / 1e-6 (FP32).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_12466_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BOOK = ("rays", "splits", "escaped", "dropped_tau", "dropped_level", "segments", "secondary")
+NYX_KEYS = ("precision", "n_min_ray", "level_max", "overlap_mode", "tau_max", "n_th_cm3", "e_heat_erg",
+            "merge_mode", "merge_samp_level", "automerge_xbar", "merge_x_th", "merge_f_req", "merge_dr_cells",
+            "merge_rmax_cells", "merge_f_ov", "merge_eps", "merge_n_min", "chem_iterate", "alpha_B", "C_H",
+            "clumping", "chem_tol", "chem_max_iter")
+
+
+@pytest.fixture(scope="module")
+def nyx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_12466_gb300 as m
+    m.lib()
+    return m
+
+
+def relerr(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def run_gpu(nyx, n_h, x, cells, ndot, box_cm, dt_s=0.0, device_inputs=True, **kw):
+    cfg = {k: v for k, v in kw.items() if k in NYX_KEYS}
+    cfg.setdefault("flags", nyx.RT_FLAG_VISIT_HASH)
+    n = n_h.shape[0]
+    s = nyx.Solver(n, box_cm, **cfg)
+    dev = torch.device("cuda")
+    if device_inputs:
+        s.set_fields(torch.from_numpy(np.ascontiguousarray(n_h).ravel()).to(dev),
+                     torch.from_numpy(np.ascontiguousarray(x).ravel()).to(dev))
+        if len(ndot):
+            s.add_sources(torch.from_numpy(np.ascontiguousarray(cells, dtype=np.int32).ravel()).to(dev),
+                          torch.from_numpy(np.ascontiguousarray(ndot, dtype=np.float64)).to(dev))
+        g = torch.empty(n ** 3, dtype=torch.float64, device=dev)
+        h = torch.empty_like(g)
+        _, _, st = s.step(dt_s, g, h)
+        g, h = g.cpu().numpy().reshape(n, n, n), h.cpu().numpy().reshape(n, n, n)
+    else:
+        s.set_fields(np.ascontiguousarray(n_h).ravel(), np.ascontiguousarray(x).ravel())
+        if len(ndot):
+            s.add_sources(np.ascontiguousarray(cells, dtype=np.int32).ravel(), np.ascontiguousarray(ndot, dtype=np.float64))
+        g, h, st = s.step(dt_s)
+    xo = s.get_x()
+    s.close()
+    return dict(gamma=g, heat=h, stats=st, x=xo)
+
+
+def run_both(nyx, w, **kw):
+    p = dict(w.params)
+    p.update(kw)
+    if "n_th_cm3" not in p:
+        p["n_th_cm3"] = 0.01 * float(w.n_h.mean())   # same threshold on both sides
+    dt = p.pop("dt_s", 0.0)
+    ref = oracle.run(w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, dt_s=dt, **p)
+    got = run_gpu(nyx, w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, dt_s=dt, **p)
+    return ref, got
+
+
+def assert_bookkeeping(st, rs):
+    for k in BOOK:
+        assert list(st[k]) == list(rs[k]), (k, st[k], rs[k])
+    assert st["visit_hash"] == rs["visit_hash"]
+    assert st["n_src_emit"] == rs["n_src_emit"] and st["n_src_dedup"] == rs["n_src_dedup"]
+
+
+def assert_ledger(st, tol):
+    e = st["emitted_ph"]
+    if e == 0:
+        return
+    assert abs(st["absorbed_ph"] + st["escaped_ph"] + st["dropped_ph"] - e) / e < tol
+
+
+CASES = [
+    # (n, sources, seed, x_mode, box per cell, overlap mode, n_th fraction)
+    (8, 3, 101, "mixed", 3e21, 0, 0.01),
+    (8, 3, 102, "mixed", 3e21, 3, 0.8),
+    (16, 5, 103, "patchy", 7e22, 3, 0.5),
+    (16, 5, 104, "patchy", 7e22, 2, 0.5),
+    (24, 7, 105, "thin", 7e20, 1, 0.01),
+    (24, 7, 106, "thin", 7e20, 4, 0.01),
+    (33, 9, 107, "patchy", 2e22, 3, 0.3),   # odd size: ragged tail of every warp-sized chunk
+    (40, 40, 108, "thin", 2e21, 3, 0.3),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_parity_fp64(nyx, case):
+    n, k, seed, xm, dxc, mode, nth = case
+    w = I.random_small(n, k, seed=seed, x_mode=xm, box_cm=n * dxc)
+    ref, got = run_both(nyx, w, overlap_mode=mode, n_th_cm3=nth * float(w.n_h.mean()), precision=0)
+    assert_bookkeeping(got["stats"], ref["stats"])
+    assert relerr(got["gamma"], ref["gamma"]) < 1e-12
+    assert relerr(got["heat"], ref["heat"]) < 1e-12
+    assert_ledger(got["stats"], 1e-12)
+    st = got["stats"]
+    if mode in (0, 2, 3):
+        assert abs(st["deposited_ph"] - st["absorbed_ph"]) <= 1e-12 * st["emitted_ph"]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_parity_fp32(nyx, case):
+    n, k, seed, xm, dxc, mode, nth = case
+    w = I.random_small(n, k, seed=seed, x_mode=xm, box_cm=n * dxc)
+    n_th = nth * float(w.n_h.mean())
+    ref32, got = run_both(nyx, w, overlap_mode=mode, n_th_cm3=n_th, precision=1)
+    ref64 = oracle.run_workload(w, overlap_mode=mode, n_th_cm3=n_th, precision=0)
+    assert_bookkeeping(got["stats"], ref32["stats"])
+    assert relerr(got["gamma"], ref64["gamma"]) < 1e-5
+    assert relerr(got["heat"], ref64["heat"]) < 1e-5
+    assert relerr(got["gamma"], ref32["gamma"]) < 1e-5
+    assert_ledger(got["stats"], 1e-6)
+
+
+def test_host_and_device_inputs_agree(nyx):
+    w = I.random_small(16, 6, seed=111, x_mode="patchy", box_cm=16 * 7e22)
+    a = run_gpu(nyx, w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, device_inputs=True, n_th_cm3=1e-5)
+    b = run_gpu(nyx, w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, device_inputs=False, n_th_cm3=1e-5)
+    assert_bookkeeping(a["stats"], b["stats"])
+    assert relerr(a["gamma"], b["gamma"]) < 1e-13
+
+
+def test_edge_no_sources(nyx):
+    n = 8
+    got = run_gpu(nyx, np.full((n, n, n), 1e-3), np.zeros((n, n, n)), np.zeros((0, 3), np.int32), np.zeros(0),
+                  n * 3e20)
+    assert not got["gamma"].any() and sum(got["stats"]["rays"]) == 0
+
+
+def test_edge_single_cell_grid(nyx):
+    w = I.Workload("one", 1, 3e20, np.full((1, 1, 1), 1e-3), np.zeros((1, 1, 1)), np.zeros((1, 3), np.int32),
+                   np.array([1e50]), dict(n_min_ray=4.0, tau_max=30.0))
+    ref, got = run_both(nyx, w)
+    assert_bookkeeping(got["stats"], ref["stats"])
+    assert relerr(got["gamma"], ref["gamma"]) < 1e-12
+
+
+@pytest.mark.parametrize("corner", [(0, 0, 0), (15, 15, 15), (0, 15, 7)])
+def test_edge_source_at_faces(nyx, corner):
+    n = 16
+    w = I.random_small(n, 1, seed=121, x_mode="thin", box_cm=n * 7e20)
+    w.cells = np.array([corner], np.int32)
+    ref, got = run_both(nyx, w)
+    assert_bookkeeping(got["stats"], ref["stats"])
+    assert relerr(got["gamma"], ref["gamma"]) < 1e-12
+
+
+@pytest.mark.parametrize("lm", [0, 1, 3])
+def test_edge_level_max(nyx, lm):
+    w = I.random_small(16, 3, seed=131, x_mode="thin", box_cm=16 * 7e20)
+    ref, got = run_both(nyx, w, level_max=lm)
+    assert_bookkeeping(got["stats"], ref["stats"])
+    assert got["stats"]["dropped_level"][lm] > 0
+    assert relerr(got["gamma"], ref["gamma"]) < 1e-12
+    assert_ledger(got["stats"], 1e-12)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_edge_tiny_tau_max_and_opaque(nyx, prec):
+    w = I.cosmo_box(32, 5.0, 1.0, 20, config=2, x_mode="neutral")
+    ref, got = run_both(nyx, w, precision=prec)
+    assert_bookkeeping(got["stats"], ref["stats"])
+    assert got["stats"]["rays"][0] == 12 * got["stats"]["n_src_emit"] and sum(got["stats"]["splits"]) == 0
+    w2 = I.random_small(16, 4, seed=141, x_mode="thin", box_cm=16 * 7e20)
+    ref, got = run_both(nyx, w2, tau_max=1e-3, precision=prec)
+    assert_bookkeeping(got["stats"], ref["stats"])
+
+
+def test_edge_fully_ionized_thin_limit(nyx):
+    n = 16
+    w = I.random_small(n, 3, seed=151, x_mode="thin", box_cm=n * 7e20)
+    w.x_ion = np.ones_like(w.x_ion)
+    ref, got = run_both(nyx, w)
+    assert_bookkeeping(got["stats"], ref["stats"])
+    assert relerr(got["gamma"], ref["gamma"]) < 1e-12
+    assert not got["heat"].any()
+
+
+def test_edge_duplicate_sources(nyx):
+    w = I.random_small(16, 3, seed=161, x_mode="patchy", box_cm=16 * 7e22)
+    w.cells = np.array([[3, 4, 5], [3, 4, 5], [9, 9, 9], [3, 4, 5], [9, 9, 9]], np.int32)
+    w.ndot = np.array([1e50, 2e50, 3e51, 5e49, 1e52])
+    ref, got = run_both(nyx, w)
+    assert got["stats"]["n_src_dedup"] == 2
+    assert_bookkeeping(got["stats"], ref["stats"])
+    assert relerr(got["gamma"], ref["gamma"]) < 1e-12
+
+
+def bubble_workload(n=48, seed=7):
+    """Neutral gas with ionized balls; most sources sit inside the balls so
+    Alg. 3 finds bubbles and merges, the rest are scattered."""
+    rng = np.random.default_rng(seed)
+    n_h = I.lognormal(n, 2e-4, 1.0, seed + 1)
+    x = np.zeros((n, n, n))
+    zz, yy, xx = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    balls = [((12, 12, 12), 7.5), ((30, 30, 20), 9.5), ((40, 10, 35), 5.5)]
+    cells = []
+    for (cx, cy, cz), r in balls:
+        x[(xx - cx) ** 2 + (yy - cy) ** 2 + (zz - cz) ** 2 <= r * r] = 1.0
+        for _ in range(15):
+            d = rng.normal(size=3)
+            d *= rng.uniform(0, r - 1.5) / np.linalg.norm(d)
+            cells.append([int(round(cx + d[0])), int(round(cy + d[1])), int(round(cz + d[2]))])
+    cells += rng.integers(0, n, size=(20, 3)).tolist()
+    cells = np.array(cells, np.int32)
+    ndot = I.power_law_ndot(len(cells), seed + 2)
+    return I.Workload("bubbles", n, n * 7.117e23, n_h, x, cells, ndot, dict(n_min_ray=4.0, tau_max=30.0))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_merge_parity(nyx, prec):
+    w = bubble_workload()
+    ref, got = run_both(nyx, w, merge_mode=1, precision=prec)
+    assert got["stats"]["merged"] == 1
+    assert got["stats"]["n_src_emit"] == ref["stats"]["n_src_emit"] < ref["stats"]["n_src_dedup"] - 10
+    assert_bookkeeping(got["stats"], ref["stats"])
+    tol = 1e-12 if prec == 0 else 1e-5
+    ref64 = ref if prec == 0 else oracle.run_workload(w, merge_mode=1, precision=0,
+                                                      n_th_cm3=0.01 * float(w.n_h.mean()))
+    assert relerr(got["gamma"], ref64["gamma"]) < tol
+
+
+def test_automerge_threshold(nyx):
+    w = bubble_workload(seed=9)
+    xbar = float(w.x_ion.mean())
+    for thr, expect in ((xbar * 0.5, 1), (min(0.999, xbar * 2.0), 0)):
+        ref, got = run_both(nyx, w, merge_mode=2, automerge_xbar=thr)
+        assert got["stats"]["merged"] == expect == ref["stats"]["merged"]
+        assert_bookkeeping(got["stats"], ref["stats"])
+
+
+def test_stromgren_chemistry_parity(nyx):
+    w = I.stromgren_test_a(64)
+    ref, got = run_both(nyx, w, dt_s=0.1 * I.MYR_S)
+    assert abs(got["stats"]["chem_iters"] - ref["stats"]["chem_iters"]) <= 1
+    assert relerr(got["x"], ref["x"]) < 1e-9
+    assert relerr(got["gamma"], ref["gamma"]) < 1e-9
+    r_n = (3 * got["x"].sum() / (4 * np.pi)) ** (1 / 3)
+    assert abs(r_n - 4.889) < 1.0
+
+
+def test_invalid_inputs_rejected(nyx):
+    n = 8
+    s = nyx.Solver(n, n * 3e20)
+    bad = np.full(n ** 3, 1e-3)
+    bad[5] = -1.0
+    s.set_fields(bad, np.zeros(n ** 3))
+    s.add_sources(np.array([1, 2, 3], np.int32), np.array([1e50]))
+    with pytest.raises(nyx.NyxError) as e:
+        s.step()
+    assert e.value.code == nyx.RT_EINVAL
+    with pytest.raises(nyx.NyxError):
+        s.add_sources(np.array([1, 2, 8], np.int32), np.array([1e50]))
+    s.close()
+    s = nyx.Solver(n, n * 3e20)
+    with pytest.raises(nyx.NyxError) as e:
+        s.step()
+    assert e.value.code == nyx.RT_ESTATE
+    s.close()
+    with pytest.raises(nyx.NyxError):
+        nyx.Solver(0, 1.0)
+    # device-side source validation
+    s = nyx.Solver(n, n * 3e20)
+    s.set_fields(np.full(n ** 3, 1e-3), np.zeros(n ** 3))
+    s.add_sources(torch.tensor([1, 2, 99], dtype=torch.int32, device="cuda"),
+                  torch.tensor([1e50], dtype=torch.float64, device="cuda"))
+    with pytest.raises(nyx.NyxError) as e:
+        s.step()
+    assert e.value.code == nyx.RT_EINVAL
+    s.close()
+
+
+def test_repeat_steps_are_reproducible(nyx):
+    w = I.random_small(24, 8, seed=171, x_mode="patchy", box_cm=24 * 7e22)
+    s = nyx.Solver(w.n, w.box_cm, flags=nyx.RT_FLAG_VISIT_HASH, n_th_cm3=1e-5)
+    s.set_fields(w.n_h.ravel(), w.x_ion.ravel())
+    s.add_sources(w.cells.ravel(), w.ndot)
+    g1, _, st1 = s.step()
+    g2, _, st2 = s.step()
+    s.close()
+    assert_bookkeeping(st1, st2)
+    assert relerr(g1, g2) < 1e-14
+
+
+# ---------------------------------------------------------------- workload-size cases
+
+def test_config2_thin_source_subset_parity(nyx):
+    """128^3 lognormal box at full size; a seeded subset of its sources
+    (Gamma is additive over sources at fixed x)."""
+    w = I.config2("thin")
+    sub = np.random.default_rng(2024).choice(len(w.ndot), size=6, replace=False)
+    w.cells, w.ndot = w.cells[sub], w.ndot[sub]
+    for prec in (0, 1):
+        ref, got = run_both(nyx, w, precision=prec)
+        assert_bookkeeping(got["stats"], ref["stats"])
+        if prec == 0:
+            assert relerr(got["gamma"], ref["gamma"]) < 1e-12
+        else:
+            ref64 = oracle.run_workload(w, precision=0, n_th_cm3=0.01 * float(w.n_h.mean()))
+            assert relerr(got["gamma"], ref64["gamma"]) < 1e-5
+
+
+def test_config2_full_invariants(nyx):
+    """All 1024 sources of the 128^3 thin box: ledger closure, deposited =
+    absorbed, FP32 vs FP64 fields, reproducible bookkeeping."""
+    w = I.config2("thin")
+    a = run_gpu(nyx, w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, precision=0, n_th_cm3=0.01 * float(w.n_h.mean()))
+    b = run_gpu(nyx, w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, precision=1, n_th_cm3=0.01 * float(w.n_h.mean()))
+    for r, tol in ((a, 1e-12), (b, 1e-6)):
+        st = r["stats"]
+        assert_ledger(st, tol)
+        assert abs(st["deposited_ph"] - st["absorbed_ph"]) <= tol * st["emitted_ph"]
+        assert (r["gamma"] >= 0).all()
+    assert relerr(b["gamma"], a["gamma"]) < 1e-5
+    assert sum(a["stats"]["segments"]) > 1e9
