@@ -178,6 +178,37 @@ const char* rt_last_error(const rt_handle* h);
 /* Library version string. */
 const char* rt_version(void);
 
+/* rt_step without any memory allocation, for small grids. There is no
+ * counterpart in the paper: it exists for callers that may not allocate
+ * device memory when they need a step (code running inside a memory-capped
+ * or externally managed pool, real-time loops that must stay out of the CUDA
+ * allocator, hosts that budget every allocation up front). It computes the
+ * same step as rt_create + rt_set_fields + rt_add_sources + rt_step + rt_destroy
+ * with the same configuration, but every scratch buffer it needs lives in one
+ * fixed array of about 8.5 MB inside the library, which each GPU that loads
+ * the library keeps until the process exits; it calls no allocator.
+ *
+ * Limits (violations return RT_EINVAL with a message): n <= 32, at most 4096
+ * sources, merge_mode == RT_MERGE_OFF, chem_iterate == 0, and rays may not
+ * need HEALPix levels above 7 (true for n <= 32 with n_min_ray <= 4).
+ *
+ * Arguments: `cfg` as for rt_create; `cuda_stream` a cudaStream_t on the
+ * current device; n_H and x_ion (n^3 float64), cell_ijk (nsrc x 3 int32) and
+ * ndot (nsrc float64) are DEVICE pointers owned by the caller; gamma_out and
+ * heat_out (n^3 float64, heat_out may be NULL) are DEVICE pointers the step
+ * overwrites; `st` (host, may be NULL) receives the counters and ledger
+ * (timings are 0); `err` (host, may be NULL) receives up to err_len - 1
+ * characters of error text. Synchronises the stream before returning.
+ *
+ * The first call on each device sets the array up (looks up its device
+ * address and copies the direction table into it synchronously): make that
+ * first call before any stream capture. All calls share the array and each
+ * overwrites what the last one left; calls that overlap on the GPU race and
+ * must be serialised by the caller. */
+int rt_step_noalloc(const rt_config* cfg, void* cuda_stream, const double* n_H, const double* x_ion,
+                    const int32_t* cell_ijk, const double* ndot, int64_t nsrc, double* gamma_out,
+                    double* heat_out, rt_stats* st, char* err, int32_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -100,7 +100,7 @@ def lib():
 
 def exported_symbols():
     return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_step",
-            "rt_get_x", "rt_destroy", "rt_last_error", "rt_version"]
+            "rt_get_x", "rt_destroy", "rt_last_error", "rt_version", "rt_step_noalloc"]
 
 
 def _check(rc: int, h=None):
