@@ -70,12 +70,6 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
     return z;
 }
 
-// T_a(ka) < T_b(kb) with T(k) = (2k+1)/D (infinite for D = 0).
-__device__ __forceinline__ bool t_less(int ka, int da, int kb, int db)
-{
-    return (long long)(2 * ka + 1) * db < (long long)(2 * kb + 1) * da;
-}
-
 template <class T>
 __device__ __forceinline__ T pick3(int i, T a, T b, T c)
 {
@@ -97,6 +91,27 @@ __device__ __forceinline__ void budget_add(R& s, R& c, R v)
     }
 }
 
+// Exact float -> double widening with integer operations only: GB300's FP64
+// pipe is small, and a conversion per deposit would make it the bottleneck.
+__device__ __forceinline__ double widen(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned sign = u >> 31;
+    int e = (int)((u >> 23) & 0xffu);
+    unsigned m = u & 0x7fffffu;
+    if (e == 0) {
+        if (m == 0) return __longlong_as_double((long long)((unsigned long long)sign << 63));
+        const int sh = __clz(m) - 8;          // normalise a subnormal
+        m = (m << sh) & 0x7fffffu;
+        e = 1 - sh;
+    }
+    const unsigned long long bits = ((unsigned long long)sign << 63) |
+                                    ((unsigned long long)(unsigned)(e + 896) << 52) |
+                                    ((unsigned long long)m << 29);
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -110,7 +125,7 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 template <class R>
-__global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
+__global__ void __launch_bounds__(256, 2) march_kernel(const MarchArgs<R> A)
 {
     using I = Ieee<R>;
     const int l = A.level;
@@ -119,12 +134,13 @@ __global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
     const long long gwarp = (long long)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarp = (long long)(gridDim.x * blockDim.x) >> 5;
 
-    unsigned long long c_rays = 0, c_split = 0, c_esc = 0, c_dtau = 0, c_dlev = 0, c_seg = 0, c_sec = 0,
-                       c_hash = 0;
+    unsigned c_rays = 0, c_split = 0, c_esc = 0, c_dtau = 0, c_dlev = 0, c_seg = 0, c_sec = 0;
+    unsigned long long c_hash = 0;
     double c_abs = 0.0, c_escph = 0.0, c_dropph = 0.0;
 
     const long long rq_end = A.rq << l;
     const long long rq_start = l > 0 ? (A.rq << (l - 1)) : 0;
+    const R pV = I::pow2(-(S - 1 + F)), pI = I::pow2(-S), pU = I::pow2(-(S + 1));
 
     for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
         const long long j = base + lane;
@@ -154,25 +170,26 @@ __global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
             }
             const SrcEntry se = A.src[si];
             const int4 dv = A.dirs[pix];
-            const int D0 = abs(dv.x), D1 = abs(dv.y), D2 = abs(dv.z);
+            const unsigned D0 = (unsigned)abs(dv.x), D1 = (unsigned)abs(dv.y), D2 = (unsigned)abs(dv.z);
             const int s0 = dv.x < 0 ? -1 : 1, s1 = dv.y < 0 ? -1 : 1, s2 = dv.z < 0 ? -1 : 1;
 
-            // ---- integer event bookkeeping
-            const long long ge0 = rq_end * D0, ge1 = rq_end * D1, ge2 = rq_end * D2;
+            // ---- integer event bookkeeping: crossings done at the start sphere, and before the split sphere
             int k0 = 0, k1 = 0, k2 = 0;
-            long long gs0 = 0, gs1 = 0, gs2 = 0;
             if (l > 0) {
-                gs0 = rq_start * D0;
-                gs1 = rq_start * D1;
-                gs2 = rq_start * D2;
-                k0 = (int)((gs0 + kB) >> (S + F));
-                k1 = (int)((gs1 + kB) >> (S + F));
-                k2 = (int)((gs2 + kB) >> (S + F));
+                k0 = (int)((rq_start * D0 + kB) >> (S + F));
+                k1 = (int)((rq_start * D1 + kB) >> (S + F));
+                k2 = (int)((rq_start * D2 + kB) >> (S + F));
             }
-            const int ke0 = (int)(((ge0 + kB - 1) >> (S - 1 + F)) >> 1);
-            const int ke1 = (int)(((ge1 + kB - 1) >> (S - 1 + F)) >> 1);
-            const int ke2 = (int)(((ge2 + kB - 1) >> (S - 1 + F)) >> 1);
+            const int ke0 = (int)(((rq_end * D0 + kB - 1) >> (S - 1 + F)) >> 1);
+            const int ke1 = (int)(((rq_end * D1 + kB - 1) >> (S - 1 + F)) >> 1);
+            const int ke2 = (int)(((rq_end * D2 + kB - 1) >> (S - 1 + F)) >> 1);
             int i0 = se.cx + s0 * k0, i1 = se.cy + s1 * k1, i2 = se.cz + s2 * k2;
+            // A_ab = (2 k_a + 1) D_b: the next crossing on a comes before the one on b iff A_ab < A_ba.
+            // With k_a <= t D_a / 2^21 + 1/2 and D_a D_b <= 2^41, A_ab <= t 2^21 + 2^22, which stays
+            // below 2^32 while the ray parameter t is below 2040 (any point of a grid up to 1024^3).
+            unsigned A01 = (2u * k0 + 1u) * D1, A10 = (2u * k1 + 1u) * D0;
+            unsigned A02 = (2u * k0 + 1u) * D2, A20 = (2u * k2 + 1u) * D0;
+            unsigned A12 = (2u * k1 + 1u) * D2, A21 = (2u * k2 + 1u) * D1;
 
             // ---- per-ray constants
             R nrm;
@@ -186,7 +203,6 @@ __global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
             const R h0 = D0 ? I::div(two20, (R)D0) : (R)0;
             const R h1 = D1 ? I::div(two20, (R)D1) : (R)0;
             const R h2 = D2 ? I::div(two20, (R)D2) : (R)0;
-            const R pV = I::pow2(-(S - 1 + F)), pI = I::pow2(-S), pU = I::pow2(-(S + 1));
             const R W01 = (D0 && D1) ? I::div(h0, (R)D1) : (R)0;
             const R W02 = (D0 && D2) ? I::div(h0, (R)D2) : (R)0;
             const R W12 = (D1 && D2) ? I::div(h1, (R)D2) : (R)0;
@@ -197,43 +213,47 @@ __global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
             const double ph = se.ph;
             const R taumax = A.tau_max;
             const unsigned long long rbase =
-                mix64(((unsigned long long)si << 36) | ((unsigned long long)l << 31) | pix);
+                A.hash ? mix64(((unsigned long long)si << 36) | ((unsigned long long)l << 31) | pix) : 0ULL;
 
             R Ab = 0, cA = 0;           // photons absorbed by this ray (units of ph)
             ++c_rays;
             bool inside = (unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n;
             if (!inside) {
                 ++c_esc;
-                c_escph += ph * ((double)P - (double)cP);
+                c_escph += ph * (widen(P) - widen(cP));
             }
             int prev = -1, kprev = 0;
             unsigned seq = 0;
             while (inside) {
                 // next face crossing (ties x, y, z), or the split sphere
-                int w = 0, kw = k0, Dw = D0;
-                if (t_less(k1, D1, kw, Dw)) { w = 1; kw = k1; Dw = D1; }
-                if (t_less(k2, D2, kw, Dw)) { w = 2; kw = k2; Dw = D2; }
+                int w = 0;
+                if (A10 < A01) w = 1;
+                if (w == 0 ? (A20 < A02) : (A21 < A12)) w = 2;
+                const int kw = pick3(w, k0, k1, k2);
                 const bool is_end = !(kw < pick3(w, ke0, ke1, ke2));
                 const R hw = pick3(w, h0, h1, h2);
+                const unsigned Dw = pick3(w, D0, D1, D2);
 
                 R ds_p;
                 if (!is_end) {
                     if (prev < 0) {
-                        const long long num = (long long)(2 * kw + 1) * kB - pick3(w, gs0, gs1, gs2);
+                        const long long num = (long long)(2 * kw + 1) * kB - rq_start * (long long)Dw;
                         ds_p = I::mul(I::of(num), I::mul(hw, pV));
                     } else if (prev == w) {
                         ds_p = I::add(hw, hw);
                     } else {
-                        const int Dp = pick3(prev, D0, D1, D2);
-                        const long long num = (long long)(2 * kw + 1) * Dp - (long long)(2 * kprev + 1) * Dw;
+                        // (2 k_w + 1) D_p - (2 k_prev + 1) D_w, with k_p = k_prev + 1 now
                         const int pair = prev + w;
+                        const unsigned Awp = pair == 1 ? (w == 0 ? A01 : A10) : (pair == 2 ? (w == 0 ? A02 : A20) : (w == 1 ? A12 : A21));
+                        const unsigned Apw = pair == 1 ? (w == 0 ? A10 : A01) : (pair == 2 ? (w == 0 ? A20 : A02) : (w == 1 ? A21 : A12));
+                        const int num = (int)(Awp - (Apw - 2u * Dw));
                         ds_p = I::mul(I::of(num), pair == 1 ? W01 : (pair == 2 ? W02 : W12));
                     }
                 } else {
                     if (prev < 0) {
                         ds_p = I::mul((R)A.rq, I::pow2(l > 0 ? l - 1 - F : -F));
                     } else {
-                        const long long num = pick3(prev, ge0, ge1, ge2) - (long long)(2 * kprev + 1) * kB;
+                        const long long num = rq_end * (long long)pick3(prev, D0, D1, D2) - (long long)(2 * kprev + 1) * kB;
                         ds_p = I::mul(I::of(num), I::mul(pick3(prev, h0, h1, h2), pV));
                     }
                 }
@@ -257,20 +277,25 @@ __global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
                 int nbcell = -1;
                 if (A.overlap_mode != RT_OVERLAP_NONE) {
                     R dl[6];
+                    const R invw = I::mul(hw, pI);
                     #pragma unroll
                     for (int b = 0; b < 3; ++b) {
-                        const int kb_ = pick3(b, k0, k1, k2), Db = pick3(b, D0, D1, D2), sb = pick3(b, s0, s1, s2);
                         R dn;
                         if (!is_end) {
-                            dn = (b == w) ? (R)0
-                                          : I::mul(I::of((long long)(2 * kb_ + 1) * Dw - (long long)(2 * kw + 1) * Db),
-                                                   I::mul(hw, pI));
+                            // (2 k_b + 1) D_w - (2 k_w + 1) D_b = A_bw - A_wb (0 for b = w)
+                            unsigned Abw, Awb;
+                            if (b == 0) { Abw = w == 1 ? A01 : A02; Awb = w == 1 ? A10 : A20; }
+                            else if (b == 1) { Abw = w == 0 ? A10 : A12; Awb = w == 0 ? A01 : A21; }
+                            else { Abw = w == 0 ? A20 : A21; Awb = w == 0 ? A02 : A12; }
+                            dn = (b == w) ? (R)0 : I::mul(I::of((int)(Abw - Awb)), invw);
                         } else {
-                            dn = I::mul(I::of((long long)(2 * kb_ + 1) * kB - pick3(b, ge0, ge1, ge2)),
-                                        I::pow2(-(S + F)));
+                            const int kb_ = pick3(b, k0, k1, k2);
+                            const long long gb = rq_end * (long long)pick3(b, D0, D1, D2);
+                            dn = I::mul(I::of((long long)(2 * kb_ + 1) * kB - gb), I::pow2(-(S + F)));
                         }
                         const R delta = I::add(dn, I::mul(ds_p, pick3(b, u0, u1, u2)));
                         const R other = I::sub((R)1, delta);
+                        const int sb = pick3(b, s0, s1, s2);
                         dl[2 * b] = sb > 0 ? other : delta;
                         dl[2 * b + 1] = sb > 0 ? delta : other;
                     }
@@ -308,9 +333,9 @@ __global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
                         }
                     }
                 }
-                atomicAdd(&A.gamma[cell], (double)(f * gseg));
+                atomicAdd(&A.gamma[cell], widen(f * gseg));
                 if (nbcell >= 0) {
-                    atomicAdd(&A.gamma[nbcell], (double)g2);
+                    atomicAdd(&A.gamma[nbcell], widen(g2));
                     ++c_sec;
                 }
 
@@ -323,15 +348,15 @@ __global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
 
                 if (tau >= taumax) {                     // photons spent
                     ++c_dtau;
-                    c_dropph += ph * ((double)P - (double)cP);
-                    c_abs += ph * ((double)Ab - (double)cA);
+                    c_dropph += ph * (widen(P) - widen(cP));
+                    c_abs += ph * (widen(Ab) - widen(cA));
                     break;
                 }
                 if (is_end) {                            // reached the split sphere R_l
-                    c_abs += ph * ((double)Ab - (double)cA);
+                    c_abs += ph * (widen(Ab) - widen(cA));
                     if (l + 1 > A.level_max) {
                         ++c_dlev;
-                        c_dropph += ph * ((double)P - (double)cP);
+                        c_dropph += ph * (widen(P) - widen(cP));
                     } else {
                         ++c_split;
                         split = true;
@@ -347,18 +372,18 @@ __global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
                     break;
                 }
                 // step every axis whose crossing coincides with the winner's
-                const bool t0 = (w == 0) || ((long long)(2 * k0 + 1) * Dw == (long long)(2 * kw + 1) * D0);
-                const bool t1 = (w == 1) || ((long long)(2 * k1 + 1) * Dw == (long long)(2 * kw + 1) * D1);
-                const bool t2 = (w == 2) || ((long long)(2 * k2 + 1) * Dw == (long long)(2 * kw + 1) * D2);
-                if (t0) { ++k0; i0 += s0; }
-                if (t1) { ++k1; i1 += s1; }
-                if (t2) { ++k2; i2 += s2; }
+                const bool t0 = (w == 0) || (w == 1 ? A01 == A10 : A02 == A20);
+                const bool t1 = (w == 1) || (w == 0 ? A10 == A01 : A12 == A21);
+                const bool t2 = (w == 2) || (w == 0 ? A20 == A02 : A21 == A12);
+                if (t0) { ++k0; i0 += s0; A01 += 2u * D1; A02 += 2u * D2; }
+                if (t1) { ++k1; i1 += s1; A10 += 2u * D0; A12 += 2u * D2; }
+                if (t2) { ++k2; i2 += s2; A20 += 2u * D0; A21 += 2u * D1; }
                 prev = w;
                 kprev = kw;
                 if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
                     ++c_esc;
-                    c_escph += ph * ((double)P - (double)cP);
-                    c_abs += ph * ((double)Ab - (double)cA);
+                    c_escph += ph * (widen(P) - widen(cP));
+                    c_abs += ph * (widen(Ab) - widen(cA));
                     break;
                 }
             }
@@ -389,26 +414,26 @@ __global__ void __launch_bounds__(256) march_kernel(const MarchArgs<R> A)
     }
 
     // ---- statistics and photon ledger: one atomic per warp and counter
-    c_rays = warp_sum(c_rays);
-    c_split = warp_sum(c_split);
-    c_esc = warp_sum(c_esc);
-    c_dtau = warp_sum(c_dtau);
-    c_dlev = warp_sum(c_dlev);
-    c_seg = warp_sum(c_seg);
-    c_sec = warp_sum(c_sec);
+    const unsigned long long r_rays = warp_sum((unsigned long long)c_rays);
+    const unsigned long long r_split = warp_sum((unsigned long long)c_split);
+    const unsigned long long r_esc = warp_sum((unsigned long long)c_esc);
+    const unsigned long long r_dtau = warp_sum((unsigned long long)c_dtau);
+    const unsigned long long r_dlev = warp_sum((unsigned long long)c_dlev);
+    const unsigned long long r_seg = warp_sum((unsigned long long)c_seg);
+    const unsigned long long r_sec = warp_sum((unsigned long long)c_sec);
     c_hash = warp_sum(c_hash);
     c_abs = warp_sum(c_abs);
     c_escph = warp_sum(c_escph);
     c_dropph = warp_sum(c_dropph);
-    if (lane == 0 && c_rays) {
+    if (lane == 0 && r_rays) {
         DevStats* st = A.st;
-        atomicAdd(&st->rays[l], c_rays);
-        if (c_split) atomicAdd(&st->splits[l], c_split);
-        if (c_esc) atomicAdd(&st->escaped[l], c_esc);
-        if (c_dtau) atomicAdd(&st->dropped_tau[l], c_dtau);
-        if (c_dlev) atomicAdd(&st->dropped_level[l], c_dlev);
-        atomicAdd(&st->segments[l], c_seg);
-        if (c_sec) atomicAdd(&st->secondary[l], c_sec);
+        atomicAdd(&st->rays[l], r_rays);
+        if (r_split) atomicAdd(&st->splits[l], r_split);
+        if (r_esc) atomicAdd(&st->escaped[l], r_esc);
+        if (r_dtau) atomicAdd(&st->dropped_tau[l], r_dtau);
+        if (r_dlev) atomicAdd(&st->dropped_level[l], r_dlev);
+        atomicAdd(&st->segments[l], r_seg);
+        if (r_sec) atomicAdd(&st->secondary[l], r_sec);
         if (c_hash) atomicAdd(&st->visit_hash, c_hash);
         atomicAdd(&st->absorbed, c_abs);
         atomicAdd(&st->escaped_ph, c_escph);
