@@ -38,6 +38,7 @@ struct Ieee<double> {
     __device__ __forceinline__ static double sub(double a, double b) { return __dsub_rn(a, b); }
     __device__ __forceinline__ static double div(double a, double b) { return __ddiv_rn(a, b); }
     __device__ __forceinline__ static double of(long long v) { return __ll2double_rn(v); }
+    __device__ __forceinline__ static double small(unsigned v) { return __uint2double_rn(v); }
     __device__ __forceinline__ static double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
     __device__ __forceinline__ static double em1(double x) { return expm1(x); }
     __device__ __forceinline__ static double qdiv(double a, double b) { return a / b; }
@@ -52,6 +53,11 @@ struct Ieee<float> {
     __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
     __device__ __forceinline__ static float div(float a, float b) { return __fdiv_rn(a, b); }
     __device__ __forceinline__ static float of(long long v) { return __ll2float_rn(v); }
+    // exact for 0 <= v < 2^23: 2^23 + v is representable, so (2^23 | v) - 2^23 = v
+    __device__ __forceinline__ static float small(unsigned v)
+    {
+        return __fsub_rn(__uint_as_float(0x4b000000u | v), 8388608.0f);
+    }
     __device__ __forceinline__ static float pow2(int e) { return __int_as_float((127 + e) << 23); }
     __device__ __forceinline__ static float em1(float x) { return expm1f(x); }
     __device__ __forceinline__ static float qdiv(float a, float b) { return __fdividef(a, b); }
@@ -217,48 +223,18 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const MarchArgs<R> A)
 
             R Ab = 0, cA = 0;           // photons absorbed by this ray (units of ph)
             ++c_rays;
-            bool inside = (unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n;
-            if (!inside) {
+            const bool inside0 = (unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n;
+            if (!inside0) {
                 ++c_esc;
                 c_escph += ph * (widen(P) - widen(cP));
             }
-            int prev = -1, kprev = 0;
             unsigned seq = 0;
-            while (inside) {
-                // next face crossing (ties x, y, z), or the split sphere
-                int w = 0;
-                if (A10 < A01) w = 1;
-                if (w == 0 ? (A20 < A02) : (A21 < A12)) w = 2;
-                const int kw = pick3(w, k0, k1, k2);
-                const bool is_end = !(kw < pick3(w, ke0, ke1, ke2));
-                const R hw = pick3(w, h0, h1, h2);
-                const unsigned Dw = pick3(w, D0, D1, D2);
 
-                R ds_p;
-                if (!is_end) {
-                    if (prev < 0) {
-                        const long long num = (long long)(2 * kw + 1) * kB - rq_start * (long long)Dw;
-                        ds_p = I::mul(I::of(num), I::mul(hw, pV));
-                    } else if (prev == w) {
-                        ds_p = I::add(hw, hw);
-                    } else {
-                        // (2 k_w + 1) D_p - (2 k_prev + 1) D_w, with k_p = k_prev + 1 now
-                        const int pair = prev + w;
-                        const unsigned Awp = pair == 1 ? (w == 0 ? A01 : A10) : (pair == 2 ? (w == 0 ? A02 : A20) : (w == 1 ? A12 : A21));
-                        const unsigned Apw = pair == 1 ? (w == 0 ? A10 : A01) : (pair == 2 ? (w == 0 ? A20 : A02) : (w == 1 ? A21 : A12));
-                        const int num = (int)(Awp - (Apw - 2u * Dw));
-                        ds_p = I::mul(I::of(num), pair == 1 ? W01 : (pair == 2 ? W02 : W12));
-                    }
-                } else {
-                    if (prev < 0) {
-                        ds_p = I::mul((R)A.rq, I::pow2(l > 0 ? l - 1 - F : -F));
-                    } else {
-                        const long long num = rq_end * (long long)pick3(prev, D0, D1, D2) - (long long)(2 * kprev + 1) * kB;
-                        ds_p = I::mul(I::of(num), I::mul(pick3(prev, h0, h1, h2), pV));
-                    }
-                }
+            // One segment of length ds_p (ray parameter) in the current cell, ending at parameter
+            // tnext, where the distance to the exit face along axis b is dn_b: deposit Gamma (Eq. 1,
+            // gray, V_box) with the overlap correction (Eqs. 5-8), then update the budgets.
+            auto segment = [&](R ds_p, R dn0, R dn1, R dn2, R tnext) {
                 const R ds = I::mul(ds_p, nrm);
-
                 const int cell = (i2 * n + i1) * n + i0;
                 const R kraw = A.kap[cell];
                 const R kap = I::mag(kraw);
@@ -271,41 +247,27 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const MarchArgs<R> A)
                     a = (R)0;
                     gseg = (P * G) * ds;
                 }
-
-                // ---- overlap correction (Eqs. 5-8)
                 R f = (R)1, g2 = (R)0;
                 int nbcell = -1;
                 if (A.overlap_mode != RT_OVERLAP_NONE) {
+                    // distances from the segment midpoint to the six faces, order x-, x+, y-, y+, z-, z+
+                    const R d0 = I::add(dn0, I::mul(ds_p, u0));
+                    const R d1 = I::add(dn1, I::mul(ds_p, u1));
+                    const R d2 = I::add(dn2, I::mul(ds_p, u2));
+                    const R o0 = I::sub((R)1, d0), o1 = I::sub((R)1, d1), o2 = I::sub((R)1, d2);
                     R dl[6];
-                    const R invw = I::mul(hw, pI);
-                    #pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        R dn;
-                        if (!is_end) {
-                            // (2 k_b + 1) D_w - (2 k_w + 1) D_b = A_bw - A_wb (0 for b = w)
-                            unsigned Abw, Awb;
-                            if (b == 0) { Abw = w == 1 ? A01 : A02; Awb = w == 1 ? A10 : A20; }
-                            else if (b == 1) { Abw = w == 0 ? A10 : A12; Awb = w == 0 ? A01 : A21; }
-                            else { Abw = w == 0 ? A20 : A21; Awb = w == 0 ? A02 : A12; }
-                            dn = (b == w) ? (R)0 : I::mul(I::of((int)(Abw - Awb)), invw);
-                        } else {
-                            const int kb_ = pick3(b, k0, k1, k2);
-                            const long long gb = rq_end * (long long)pick3(b, D0, D1, D2);
-                            dn = I::mul(I::of((long long)(2 * kb_ + 1) * kB - gb), I::pow2(-(S + F)));
-                        }
-                        const R delta = I::add(dn, I::mul(ds_p, pick3(b, u0, u1, u2)));
-                        const R other = I::sub((R)1, delta);
-                        const int sb = pick3(b, s0, s1, s2);
-                        dl[2 * b] = sb > 0 ? other : delta;
-                        dl[2 * b + 1] = sb > 0 ? delta : other;
-                    }
+                    dl[0] = s0 > 0 ? o0 : d0;
+                    dl[1] = s0 > 0 ? d0 : o0;
+                    dl[2] = s1 > 0 ? o1 : d1;
+                    dl[3] = s1 > 0 ? d1 : o1;
+                    dl[4] = s2 > 0 ? o2 : d2;
+                    dl[5] = s2 > 0 ? d2 : o2;
                     int face = 0;
                     R De = dl[0];
                     #pragma unroll
                     for (int q = 1; q < 6; ++q) {
                         if (dl[q] < De) { De = dl[q]; face = q; }
                     }
-                    const R tnext = is_end ? I::mul((R)A.rq, I::pow2(l - F)) : I::mul(I::of(2 * kw + 1), hw);
                     const R tm = I::sub(tnext, I::mul(ds_p, (R)0.5));
                     const R Lpix = I::mul(tm, Lc);
                     if (I::add(De, De) < Lpix) {
@@ -338,53 +300,124 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const MarchArgs<R> A)
                     atomicAdd(&A.gamma[nbcell], widen(g2));
                     ++c_sec;
                 }
-
                 budget_add(tau, ctau, dtau);
                 budget_add(P, cP, -a);
                 budget_add(Ab, cA, a);
                 ++c_seg;
                 if (A.hash) c_hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
                 ++seq;
+            };
 
-                if (tau >= taumax) {                     // photons spent
-                    ++c_dtau;
-                    c_dropph += ph * (widen(P) - widen(cP));
-                    c_abs += ph * (widen(Ab) - widen(cA));
-                    break;
+            if (inside0) {
+                // first event: the smallest next crossing (ties x, y, z), or the split sphere
+                int w = 0;
+                if (A10 < A01) w = 1;
+                if (w == 0 ? (A20 < A02) : (A21 < A12)) w = 2;
+                int kw = pick3(w, k0, k1, k2);
+                bool is_end = !(kw < pick3(w, ke0, ke1, ke2));
+                int prev = -1, kprev = 0;
+                R ds_p = (R)0;
+                if (!is_end) {               // from the start sphere to the first crossing
+                    const unsigned Dw = pick3(w, D0, D1, D2);
+                    const long long num = (long long)(2 * kw + 1) * kB - rq_start * (long long)Dw;
+                    ds_p = I::mul(I::of(num), I::mul(pick3(w, h0, h1, h2), pV));
                 }
-                if (is_end) {                            // reached the split sphere R_l
-                    c_abs += ph * (widen(Ab) - widen(cA));
-                    if (l + 1 > A.level_max) {
-                        ++c_dlev;
-                        c_dropph += ph * (widen(P) - widen(cP));
+                bool alive = true;
+                // ---- segments that end on a face crossing
+                while (!is_end) {
+                    const R hw = pick3(w, h0, h1, h2);
+                    const R invw = I::mul(hw, pI);
+                    // exit-point distance to the exit face along b: (A_bw - A_wb) / (2 D_w), 0 on b = w
+                    R dn0 = (R)0, dn1 = (R)0, dn2 = (R)0;
+                    if (w == 0) {
+                        dn1 = I::mul(I::small(A10 - A01), invw);
+                        dn2 = I::mul(I::small(A20 - A02), invw);
+                    } else if (w == 1) {
+                        dn0 = I::mul(I::small(A01 - A10), invw);
+                        dn2 = I::mul(I::small(A21 - A12), invw);
                     } else {
-                        ++c_split;
-                        split = true;
-                        o_src = si;
-                        o_pix = pix;
-                        o_P = P;
-                        o_tau = tau;
-                        if constexpr (sizeof(R) == 4) {
-                            o_cP = cP;
-                            o_ctau = ctau;
+                        dn0 = I::mul(I::small(A02 - A20), invw);
+                        dn1 = I::mul(I::small(A12 - A21), invw);
+                    }
+                    segment(ds_p, dn0, dn1, dn2, I::mul(I::small(2u * kw + 1u), hw));
+                    if (tau >= taumax) {             // photons spent
+                        ++c_dtau;
+                        c_dropph += ph * (widen(P) - widen(cP));
+                        c_abs += ph * (widen(Ab) - widen(cA));
+                        alive = false;
+                        break;
+                    }
+                    // step every axis whose crossing coincides with the winner's
+                    const bool t0 = (w == 0) || (w == 1 ? A01 == A10 : A02 == A20);
+                    const bool t1 = (w == 1) || (w == 0 ? A10 == A01 : A12 == A21);
+                    const bool t2 = (w == 2) || (w == 0 ? A20 == A02 : A21 == A12);
+                    if (t0) { ++k0; i0 += s0; A01 += 2u * D1; A02 += 2u * D2; }
+                    if (t1) { ++k1; i1 += s1; A10 += 2u * D0; A12 += 2u * D2; }
+                    if (t2) { ++k2; i2 += s2; A20 += 2u * D0; A21 += 2u * D1; }
+                    prev = w;
+                    kprev = kw;
+                    if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
+                        ++c_esc;
+                        c_escph += ph * (widen(P) - widen(cP));
+                        c_abs += ph * (widen(Ab) - widen(cA));
+                        alive = false;
+                        break;
+                    }
+                    // next event
+                    w = 0;
+                    if (A10 < A01) w = 1;
+                    if (w == 0 ? (A20 < A02) : (A21 < A12)) w = 2;
+                    kw = pick3(w, k0, k1, k2);
+                    is_end = !(kw < pick3(w, ke0, ke1, ke2));
+                    if (!is_end) {
+                        if (prev == w) {
+                            const R h = pick3(w, h0, h1, h2);
+                            ds_p = I::add(h, h);
+                        } else {
+                            // (2 k_w + 1) D_p - (2 k_prev + 1) D_w, with k_p = k_prev + 1 now; in [1, 2^22]
+                            const int pair = prev + w;
+                            const unsigned Dw = pick3(w, D0, D1, D2);
+                            const unsigned Awp = pair == 1 ? (w == 0 ? A01 : A10) : (pair == 2 ? (w == 0 ? A02 : A20) : (w == 1 ? A12 : A21));
+                            const unsigned Apw = pair == 1 ? (w == 0 ? A10 : A01) : (pair == 2 ? (w == 0 ? A20 : A02) : (w == 1 ? A21 : A12));
+                            ds_p = I::mul(I::small(Awp - (Apw - 2u * Dw)), pair == 1 ? W01 : (pair == 2 ? W02 : W12));
                         }
                     }
-                    break;
                 }
-                // step every axis whose crossing coincides with the winner's
-                const bool t0 = (w == 0) || (w == 1 ? A01 == A10 : A02 == A20);
-                const bool t1 = (w == 1) || (w == 0 ? A10 == A01 : A12 == A21);
-                const bool t2 = (w == 2) || (w == 0 ? A20 == A02 : A21 == A12);
-                if (t0) { ++k0; i0 += s0; A01 += 2u * D1; A02 += 2u * D2; }
-                if (t1) { ++k1; i1 += s1; A10 += 2u * D0; A12 += 2u * D2; }
-                if (t2) { ++k2; i2 += s2; A20 += 2u * D0; A21 += 2u * D1; }
-                prev = w;
-                kprev = kw;
-                if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
-                    ++c_esc;
-                    c_escph += ph * (widen(P) - widen(cP));
-                    c_abs += ph * (widen(Ab) - widen(cA));
-                    break;
+                if (alive) {
+                    // ---- the last segment ends on the split sphere R_l, where k_b = kend_b on every axis
+                    if (prev < 0) {
+                        ds_p = I::mul((R)A.rq, I::pow2(l > 0 ? l - 1 - F : -F));
+                    } else {
+                        const long long num = rq_end * (long long)pick3(prev, D0, D1, D2) - (long long)(2 * kprev + 1) * kB;
+                        ds_p = I::mul(I::of(num), I::mul(pick3(prev, h0, h1, h2), pV));
+                    }
+                    const R pE = I::pow2(-(S + F));
+                    const R e0 = I::mul(I::of((long long)(2 * ke0 + 1) * kB - rq_end * (long long)D0), pE);
+                    const R e1 = I::mul(I::of((long long)(2 * ke1 + 1) * kB - rq_end * (long long)D1), pE);
+                    const R e2 = I::mul(I::of((long long)(2 * ke2 + 1) * kB - rq_end * (long long)D2), pE);
+                    segment(ds_p, e0, e1, e2, I::mul((R)A.rq, I::pow2(l - F)));
+                    if (tau >= taumax) {
+                        ++c_dtau;
+                        c_dropph += ph * (widen(P) - widen(cP));
+                        c_abs += ph * (widen(Ab) - widen(cA));
+                    } else {
+                        c_abs += ph * (widen(Ab) - widen(cA));
+                        if (l + 1 > A.level_max) {
+                            ++c_dlev;
+                            c_dropph += ph * (widen(P) - widen(cP));
+                        } else {
+                            ++c_split;
+                            split = true;
+                            o_src = si;
+                            o_pix = pix;
+                            o_P = P;
+                            o_tau = tau;
+                            if constexpr (sizeof(R) == 4) {
+                                o_cP = cP;
+                                o_ctau = ctau;
+                            }
+                        }
+                    }
                 }
             }
         }
