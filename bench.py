@@ -221,6 +221,66 @@ def time_steps(solver, steps, flush, g, h, torch):
     return ms, stats
 
 
+def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int | None = None):
+    """64 independent solves (grid sizes from {32,64,96,128}^3, log-uniform source counts on
+    [1, 4096], per-solve seeds), FP32: one persistent graph-captured launch for all solves vs
+    one rt_step per solve. Returns timings, segments and the largest field difference."""
+    ws = I.batch_solves(64, config=3, x_mode=x_mode)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+    solvers, outs = [], []
+    for w in ws:
+        s = nyx.Solver(w.n, w.box_cm, precision=nyx.RT_FP32, n_th_cm3=0.01 * float(w.n_h.mean()),
+                       n_min_ray=4.0, tau_max=30.0)
+        s.set_fields(dev(w.n_h), dev(w.x_ion))
+        s.add_sources(dev(w.cells), dev(w.ndot))
+        solvers.append(s)
+        outs.append(torch.empty(w.n ** 3, dtype=torch.float64, device="cuda"))
+    plain_out = [torch.empty_like(o) for o in outs]
+
+    def plain_step():
+        segs = 0
+        for s, o in zip(solvers, plain_out):
+            _, _, st = s.step(0.0, o, None)
+            segs += sum(st["segments"])
+        return segs
+
+    plain_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        segs = plain_step()
+    torch.cuda.synchronize()
+    plain_s = (time.perf_counter() - t0) / steps
+    b = nyx.Batch(solvers)
+    if slice_:
+        b.set_params(slice=slice_)
+    tuned = None
+    if tune:
+        p, ms = b.tune(repeats=1)
+        tuned = {"block": p.block, "blocks_per_sm": p.blocks_per_sm, "tile": p.tile, "slice": p.slice,
+                 "group_bytes": p.group_bytes, "ms": ms}
+    p_final = b.params()
+    b.capture()
+    b.run(outs, None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = b.run(outs, None)
+    torch.cuda.synchronize()
+    batch_s = (time.perf_counter() - t0) / steps
+    bsegs = sum(sum(x["segments"]) for x in st)
+    diff = max(float(torch.linalg.norm(a - c) / max(float(torch.linalg.norm(c)), 1e-300))
+               for a, c in zip(outs, plain_out))
+    b.close()
+    for s in solvers:
+        s.close()
+    return {"x_variant": x_mode, "solves": 64, "segments_per_step": bsegs, "plain_segments_per_step": segs,
+            "plain_ms_per_step": plain_s * 1e3, "batched_ms_per_step": batch_s * 1e3,
+            "plain_value": segs / plain_s, "batched_value": bsegs / batch_s, "factor": plain_s / batch_s,
+            "max_rel_l2_batched_vs_plain": diff, "steps": steps, "graph": True, "tuned": tuned,
+            "params": {k: getattr(p_final, k) for k in ("block", "blocks_per_sm", "tile", "slice", "group_bytes")}}
+
+
 def run_nyx(args, world, rank, local):
     import torch
     import paper_2512_12466_gb300 as nyx
@@ -325,6 +385,9 @@ def run_nyx(args, world, rank, local):
                 "steps": e2e_steps},
         "clocks": f32["clocks"],
     }
+    if not args.no_batched:
+        line["batched"] = {"neutral": bench_batched(nyx, torch, "neutral", steps=5, tune=True),
+                           "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 25)}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -338,6 +401,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nyx", choices=["nyx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":

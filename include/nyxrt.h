@@ -178,6 +178,66 @@ const char* rt_last_error(const rt_handle* h);
 /* Library version string. */
 const char* rt_version(void);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent solves in one persistent launch.
+ *
+ * A batch groups handles (each with its own grid size, fields, sources and
+ * configuration; all with the same precision, on one device, chemistry off)
+ * and traces all their rays together: the ray-tracing loop of Alg. 2 runs in
+ * one cooperative launch whose warps claim tiles of work from a device queue,
+ * level by level and slice by slice, over all solves at once. This fills the
+ * GPU when single solves are small and removes the per-level host round trips
+ * of rt_step. Results equal those of rt_step on each handle (the same
+ * kernels' arithmetic; only the order of FP64 atomic deposits differs).
+ */
+typedef struct rt_batch rt_batch;
+
+/* Launch shape of the batch kernel (see rt_batch_tune). */
+typedef struct rt_batch_params {
+    int32_t block;          /* threads per block: 128 or 256 */
+    int32_t blocks_per_sm;  /* co-resident blocks per SM, 1 .. the occupancy limit */
+    int32_t tile;           /* children a warp claims from the work queue at once (multiple of 32) */
+    int32_t pad_;
+    int64_t slice;          /* children per slice; also the record capacity of each level's buffer */
+    int64_t group_bytes;    /* solves run in consecutive groups whose kappa + Gamma bytes stay within
+                               this budget (one launch per group, keeping each group's fields in
+                               L2); 0: all solves in one launch */
+} rt_batch_params;
+
+/* Create a batch over `count` handles (fields set, sources added). Runs each
+ * handle's source stage now (dedup, sort, Alg. 3 merging, the n_th default):
+ * later rt_add_sources calls do not affect the batch, later rt_set_fields
+ * calls do (kappa is rebuilt on every run). `cuda_stream` is unused (the
+ * batch runs on a private stream and waits for the handles' streams). The
+ * handles must outlive the batch. */
+int rt_batch_create(rt_handle* const* handles, int32_t count, void* cuda_stream, rt_batch** out);
+
+/* Set / read the launch shape. Changing `slice` reallocates the ray buffers. */
+int rt_batch_set_params(rt_batch* b, const rt_batch_params* p);
+int rt_batch_get_params(const rt_batch* b, rt_batch_params* p);
+
+/* Autotuner: time the batch under candidate launch shapes (block 128/256,
+ * 1..occupancy blocks per SM, tiles 64/256/1024, slices 2^21/2^23/2^25, group
+ * budgets of 48 MB and unlimited), each `repeats` times, keep the fastest and
+ * return it with its time in ms. */
+int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best, double* best_ms);
+
+/* Capture one run (kappa rebuild, trace, finalize, statistics copy) into a
+ * CUDA graph; rt_batch_run then replays it. */
+int rt_batch_capture(rt_batch* b);
+
+/* Run the batch: write solve i's Gamma and heating into gamma_out[i] and
+ * heat_out[i] (n_i^3 float64, host or device by `where`; arrays or entries may
+ * be NULL) and its statistics into stats[i] (host array of `count`, may be
+ * NULL; timings are the whole batch's). Synchronous. */
+int rt_batch_run(rt_batch* b, double* const* gamma_out, double* const* heat_out, int where, rt_stats* stats);
+
+/* Free the batch (not its handles). NULL is accepted. */
+int rt_batch_destroy(rt_batch* b);
+
+/* Text of the batch's last error. */
+const char* rt_batch_last_error(const rt_batch* b);
+
 /* rt_step without any memory allocation, for small grids. There is no
  * counterpart in the paper: it exists for callers that may not allocate
  * device memory when they need a step (code running inside a memory-capped

@@ -61,6 +61,11 @@ class rt_stats(C.Structure):
     ]
 
 
+class rt_batch_params(C.Structure):
+    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("tile", C.c_int32), ("pad_", C.c_int32),
+                ("slice", C.c_int64), ("group_bytes", C.c_int64)]
+
+
 class NyxError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
@@ -91,8 +96,18 @@ def lib():
         L.rt_last_error.argtypes = [P]
         L.rt_last_error.restype = C.c_char_p
         L.rt_version.restype = C.c_char_p
+        L.rt_batch_create.argtypes = [C.POINTER(P), i32, P, C.POINTER(P)]
+        L.rt_batch_set_params.argtypes = [P, C.POINTER(rt_batch_params)]
+        L.rt_batch_get_params.argtypes = [P, C.POINTER(rt_batch_params)]
+        L.rt_batch_tune.argtypes = [P, i32, C.POINTER(rt_batch_params), C.POINTER(d)]
+        L.rt_batch_capture.argtypes = [P]
+        L.rt_batch_run.argtypes = [P, C.POINTER(P), C.POINTER(P), C.c_int, C.POINTER(rt_stats)]
+        L.rt_batch_destroy.argtypes = [P]
+        L.rt_batch_last_error.argtypes = [P]
+        L.rt_batch_last_error.restype = C.c_char_p
         for f in ("rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_step", "rt_get_x",
-                  "rt_destroy"):
+                  "rt_destroy", "rt_batch_create", "rt_batch_set_params", "rt_batch_get_params", "rt_batch_tune",
+                  "rt_batch_capture", "rt_batch_run", "rt_batch_destroy"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -100,7 +115,9 @@ def lib():
 
 def exported_symbols():
     return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_step",
-            "rt_get_x", "rt_destroy", "rt_last_error", "rt_version", "rt_step_noalloc"]
+            "rt_get_x", "rt_destroy", "rt_last_error", "rt_version", "rt_batch_create", "rt_batch_set_params",
+            "rt_batch_get_params", "rt_batch_tune", "rt_batch_capture", "rt_batch_run", "rt_batch_destroy",
+            "rt_batch_last_error", "rt_step_noalloc"]
 
 
 def _check(rc: int, h=None):
@@ -164,6 +181,56 @@ def rt_destroy(h: int) -> None:
 
 def rt_version() -> str:
     return lib().rt_version().decode()
+
+
+def _bcheck(rc: int, b):
+    if rc != RT_OK:
+        raise NyxError(rc, lib().rt_batch_last_error(b).decode(errors="replace"))
+
+
+def rt_batch_create(handles, stream: int = 0) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    b = C.c_void_p()
+    rc = lib().rt_batch_create(arr, len(handles), C.c_void_p(stream), C.byref(b))
+    if rc != RT_OK:
+        msg = lib().rt_batch_last_error(b).decode(errors="replace") if b.value else ""
+        if b.value:
+            lib().rt_batch_destroy(b)
+        raise NyxError(rc, msg)
+    return b.value
+
+
+def rt_batch_set_params(b: int, p: rt_batch_params) -> None:
+    _bcheck(lib().rt_batch_set_params(b, C.byref(p)), b)
+
+
+def rt_batch_get_params(b: int) -> rt_batch_params:
+    p = rt_batch_params()
+    _bcheck(lib().rt_batch_get_params(b, C.byref(p)), b)
+    return p
+
+
+def rt_batch_tune(b: int, repeats: int = 2):
+    p = rt_batch_params()
+    ms = C.c_double()
+    _bcheck(lib().rt_batch_tune(b, int(repeats), C.byref(p), C.byref(ms)), b)
+    return p, ms.value
+
+
+def rt_batch_capture(b: int) -> None:
+    _bcheck(lib().rt_batch_capture(b), b)
+
+
+def rt_batch_run(b: int, gamma_outs, heat_outs, where: int, count: int):
+    g = (C.c_void_p * count)(*gamma_outs) if gamma_outs is not None else None
+    h = (C.c_void_p * count)(*heat_outs) if heat_outs is not None else None
+    st = (rt_stats * count)()
+    _bcheck(lib().rt_batch_run(b, g, h, where, st), b)
+    return [stats_dict(x) for x in st]
+
+
+def rt_batch_destroy(b: int) -> None:
+    lib().rt_batch_destroy(b)
 
 
 def stats_dict(st: rt_stats) -> dict:
@@ -246,7 +313,7 @@ class Solver:
             pass
 
     @staticmethod
-    def _check_array(a, dtype, size):
+    def _check_array(a, dtype, size):  # noqa: D401
         if hasattr(a, "data_ptr"):
             import torch
             want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
@@ -255,3 +322,54 @@ class Solver:
         else:
             if a.dtype != dtype or not a.flags["C_CONTIGUOUS"] or a.size != size:
                 raise ValueError(f"expected a C-contiguous {np.dtype(dtype)} array of {size} elements")
+
+
+class Batch:
+    """Many solvers traced together by one persistent launch (rt_batch_*)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.b = rt_batch_create([s.h for s in self.solvers])
+
+    def params(self) -> rt_batch_params:
+        return rt_batch_get_params(self.b)
+
+    def set_params(self, block=None, blocks_per_sm=None, tile=None, slice=None, group_bytes=None):
+        p = rt_batch_get_params(self.b)
+        for k, v in dict(block=block, blocks_per_sm=blocks_per_sm, tile=tile, slice=slice,
+                         group_bytes=group_bytes).items():
+            if v is not None:
+                setattr(p, k, v)
+        rt_batch_set_params(self.b, p)
+
+    def tune(self, repeats: int = 2):
+        return rt_batch_tune(self.b, repeats)
+
+    def capture(self):
+        rt_batch_capture(self.b)
+
+    def run(self, gammas=None, heats=None):
+        """Run once. gammas / heats: lists of per-solve output tensors or arrays
+        (all device or all host), or None. Returns per-solve stats dicts."""
+        where = RT_HOST
+        gp = hp = None
+        if gammas is not None:
+            ptrs = [_ptr(g) for g in gammas]
+            gp = [p for p, _ in ptrs]
+            where = ptrs[0][1]
+        if heats is not None:
+            ptrs = [_ptr(h) for h in heats]
+            hp = [p for p, _ in ptrs]
+            where = ptrs[0][1]
+        return rt_batch_run(self.b, gp, hp, where, len(self.solvers))
+
+    def close(self):
+        if self.b:
+            rt_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -17,6 +17,8 @@
 // floating-point operation that feeds a decision (tau against tau_max, the
 // D_edge < L_pix/2 test) is an explicit round-to-nearest intrinsic, so the
 // bookkeeping is reproducible operation by operation.
+#include <cooperative_groups.h>
+
 #include <cstdint>
 
 #include "rt_internal.h"
@@ -130,347 +132,522 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Per-thread tallies for one (solve, level).
+struct Tally {
+    unsigned rays, split, esc, dtau, dlev, seg, sec;
+    unsigned long long hash;
+    double abs, escph, dropph;
+    __device__ __forceinline__ void clear()
+    {
+        rays = split = esc = dtau = dlev = seg = sec = 0u;
+        hash = 0ULL;
+        abs = escph = dropph = 0.0;
+    }
+};
+
+// What a ray needs from the solve it belongs to.
 template <class R>
-__global__ void __launch_bounds__(256, 2) march_kernel(const MarchArgs<R> A)
+struct SolveView {
+    const R* kap;
+    double* gamma;
+    int n;
+    int level_max;
+    int overlap_mode;
+    int hash;
+    long long rq;
+    R tau_max;
+    uint32_t src_off;        // first catalog index of this solve (ray ids are solve-local)
+};
+
+// March one ray of level l (source entry se, quantised direction dv, budget
+// P with compensation cP, optical depth tau with compensation ctau) from its
+// start sphere to its split sphere, depositing into V.gamma and counting into
+// T. Returns true if the ray reached R_l and splits; its final P, tau (and
+// compensations) are then in oP, otau, ocP, octau.
+template <class R>
+__device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, const uint32_t si, const uint32_t pix,
+                                          R P, R tau, R cP, R ctau, const SrcEntry& se, const int4 dv, Tally& T,
+                                          R& oP, R& otau, float& ocP, float& octau)
 {
     using I = Ieee<R>;
-    const int l = A.level;
-    const int n = A.n;
-    const int lane = threadIdx.x & 31;
-    const long long gwarp = (long long)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarp = (long long)(gridDim.x * blockDim.x) >> 5;
-
-    unsigned c_rays = 0, c_split = 0, c_esc = 0, c_dtau = 0, c_dlev = 0, c_seg = 0, c_sec = 0;
-    unsigned long long c_hash = 0;
-    double c_abs = 0.0, c_escph = 0.0, c_dropph = 0.0;
-
-    const long long rq_end = A.rq << l;
-    const long long rq_start = l > 0 ? (A.rq << (l - 1)) : 0;
+    const int n = V.n;
+    const long long rq_end = V.rq << l;
+    const long long rq_start = l > 0 ? (V.rq << (l - 1)) : 0;
     const R pV = I::pow2(-(S - 1 + F)), pI = I::pow2(-S), pU = I::pow2(-(S + 1));
+    bool split = false;
+    const unsigned D0 = (unsigned)abs(dv.x), D1 = (unsigned)abs(dv.y), D2 = (unsigned)abs(dv.z);
+    const int s0 = dv.x < 0 ? -1 : 1, s1 = dv.y < 0 ? -1 : 1, s2 = dv.z < 0 ? -1 : 1;
 
-    for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
-        const long long j = base + lane;
-        bool split = false;
-        uint32_t o_src = 0, o_pix = 0;
-        R o_P = 0, o_tau = 0;
-        float o_cP = 0.f, o_ctau = 0.f;
-        if (j < A.c1) {
-            // ---- the ray: level-0 emission (12 per source) or a child of a parent record
-            uint32_t si, pix;
-            R P, tau, cP = 0, ctau = 0;
-            if (l == 0) {
-                si = (uint32_t)(j / 12);
-                pix = (uint32_t)(j - 12LL * si);
-                P = (R)1;
-                tau = (R)0;
-            } else {
-                const long long q = j >> 2;
-                si = A.in.src[q];
-                pix = 4u * A.in.pix[q] + (uint32_t)(j & 3);
-                P = I::mul(A.in.P[q], (R)0.25);
-                tau = A.in.tau[q];
-                if constexpr (sizeof(R) == 4) {
-                    cP = I::mul(A.in.cP[q], 0.25f);
-                    ctau = A.in.ctau[q];
-                }
+    // ---- integer event bookkeeping: crossings done at the start sphere, and before the split sphere
+    int k0 = 0, k1 = 0, k2 = 0;
+    if (l > 0) {
+        k0 = (int)((rq_start * D0 + kB) >> (S + F));
+        k1 = (int)((rq_start * D1 + kB) >> (S + F));
+        k2 = (int)((rq_start * D2 + kB) >> (S + F));
+    }
+    const int ke0 = (int)(((rq_end * D0 + kB - 1) >> (S - 1 + F)) >> 1);
+    const int ke1 = (int)(((rq_end * D1 + kB - 1) >> (S - 1 + F)) >> 1);
+    const int ke2 = (int)(((rq_end * D2 + kB - 1) >> (S - 1 + F)) >> 1);
+    int i0 = se.cx + s0 * k0, i1 = se.cy + s1 * k1, i2 = se.cz + s2 * k2;
+    // A_ab = (2 k_a + 1) D_b: the next crossing on a comes before the one on b iff A_ab < A_ba.
+    // With k_a <= t D_a / 2^21 + 1/2 and D_a D_b <= 2^41, A_ab <= t 2^21 + 2^22, which stays
+    // below 2^32 while the ray parameter t is below 2040 (any point of a grid up to 1024^3).
+    unsigned A01 = (2u * k0 + 1u) * D1, A10 = (2u * k1 + 1u) * D0;
+    unsigned A02 = (2u * k0 + 1u) * D2, A20 = (2u * k2 + 1u) * D0;
+    unsigned A12 = (2u * k1 + 1u) * D2, A21 = (2u * k2 + 1u) * D1;
+
+    // ---- per-ray constants
+    R nrm;
+    if constexpr (sizeof(R) == 4) {
+        nrm = __int_as_float(dv.w);
+    } else {
+        const long long nn = (long long)D0 * D0 + (long long)D1 * D1 + (long long)D2 * D2;
+        nrm = __dmul_rn(__dsqrt_rn(__ll2double_rn(nn)), I::pow2(-S));
+    }
+    const R two20 = (R)(1 << (S - 1));
+    const R h0 = D0 ? I::div(two20, (R)D0) : (R)0;
+    const R h1 = D1 ? I::div(two20, (R)D1) : (R)0;
+    const R h2 = D2 ? I::div(two20, (R)D2) : (R)0;
+    const R W01 = (D0 && D1) ? I::div(h0, (R)D1) : (R)0;
+    const R W02 = (D0 && D2) ? I::div(h0, (R)D2) : (R)0;
+    const R W12 = (D1 && D2) ? I::div(h1, (R)D2) : (R)0;
+    const R u0 = I::mul((R)D0, pU), u1 = I::mul((R)D1, pU), u2 = I::mul((R)D2, pU);
+    const R Lc = I::mul(I::mul(nrm, (R)kSqrtPiOver3), I::pow2(-l));
+    R G;
+    if constexpr (sizeof(R) == 4) G = se.gf; else G = se.gd;
+    const double ph = se.ph;
+    const R taumax = V.tau_max;
+    const unsigned long long rbase =
+        V.hash ? mix64(((unsigned long long)(si - V.src_off) << 36) | ((unsigned long long)l << 31) | pix) : 0ULL;
+
+    R Ab = 0, cA = 0;           // photons absorbed by this ray (units of ph)
+    ++T.rays;
+    const bool inside0 = (unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n;
+    if (!inside0) {
+        ++T.esc;
+        T.escph += ph * (widen(P) - widen(cP));
+    }
+    unsigned seq = 0;
+
+    // One segment of length ds_p (ray parameter) in the current cell, ending at parameter
+    // tnext, where the distance to the exit face along axis b is dn_b: deposit Gamma (Eq. 1,
+    // gray, V_box) with the overlap correction (Eqs. 5-8), then update the budgets.
+    auto segment = [&](R ds_p, R dn0, R dn1, R dn2, R tnext) {
+        const R ds = I::mul(ds_p, nrm);
+        const int cell = (i2 * n + i1) * n + i0;
+        const R kraw = V.kap[cell];
+        const R kap = I::mag(kraw);
+        const R dtau = I::mul(kap, ds);
+        R a, gseg;
+        if (kap > (R)0) {
+            a = P * (-I::em1(-dtau));
+            gseg = I::qdiv(a * G, kap);
+        } else {
+            a = (R)0;
+            gseg = (P * G) * ds;
+        }
+        R f = (R)1, g2 = (R)0;
+        int nbcell = -1;
+        if (V.overlap_mode != RT_OVERLAP_NONE) {
+            // distances from the segment midpoint to the six faces, order x-, x+, y-, y+, z-, z+
+            const R d0 = I::add(dn0, I::mul(ds_p, u0));
+            const R d1 = I::add(dn1, I::mul(ds_p, u1));
+            const R d2 = I::add(dn2, I::mul(ds_p, u2));
+            const R o0 = I::sub((R)1, d0), o1 = I::sub((R)1, d1), o2 = I::sub((R)1, d2);
+            R dl[6];
+            dl[0] = s0 > 0 ? o0 : d0;
+            dl[1] = s0 > 0 ? d0 : o0;
+            dl[2] = s1 > 0 ? o1 : d1;
+            dl[3] = s1 > 0 ? d1 : o1;
+            dl[4] = s2 > 0 ? o2 : d2;
+            dl[5] = s2 > 0 ? d2 : o2;
+            int face = 0;
+            R De = dl[0];
+            #pragma unroll
+            for (int q = 1; q < 6; ++q) {
+                if (dl[q] < De) { De = dl[q]; face = q; }
             }
-            const SrcEntry se = A.src[si];
-            const int4 dv = A.dirs[pix];
-            const unsigned D0 = (unsigned)abs(dv.x), D1 = (unsigned)abs(dv.y), D2 = (unsigned)abs(dv.z);
-            const int s0 = dv.x < 0 ? -1 : 1, s1 = dv.y < 0 ? -1 : 1, s2 = dv.z < 0 ? -1 : 1;
-
-            // ---- integer event bookkeeping: crossings done at the start sphere, and before the split sphere
-            int k0 = 0, k1 = 0, k2 = 0;
-            if (l > 0) {
-                k0 = (int)((rq_start * D0 + kB) >> (S + F));
-                k1 = (int)((rq_start * D1 + kB) >> (S + F));
-                k2 = (int)((rq_start * D2 + kB) >> (S + F));
-            }
-            const int ke0 = (int)(((rq_end * D0 + kB - 1) >> (S - 1 + F)) >> 1);
-            const int ke1 = (int)(((rq_end * D1 + kB - 1) >> (S - 1 + F)) >> 1);
-            const int ke2 = (int)(((rq_end * D2 + kB - 1) >> (S - 1 + F)) >> 1);
-            int i0 = se.cx + s0 * k0, i1 = se.cy + s1 * k1, i2 = se.cz + s2 * k2;
-            // A_ab = (2 k_a + 1) D_b: the next crossing on a comes before the one on b iff A_ab < A_ba.
-            // With k_a <= t D_a / 2^21 + 1/2 and D_a D_b <= 2^41, A_ab <= t 2^21 + 2^22, which stays
-            // below 2^32 while the ray parameter t is below 2040 (any point of a grid up to 1024^3).
-            unsigned A01 = (2u * k0 + 1u) * D1, A10 = (2u * k1 + 1u) * D0;
-            unsigned A02 = (2u * k0 + 1u) * D2, A20 = (2u * k2 + 1u) * D0;
-            unsigned A12 = (2u * k1 + 1u) * D2, A21 = (2u * k2 + 1u) * D1;
-
-            // ---- per-ray constants
-            R nrm;
-            if constexpr (sizeof(R) == 4) {
-                nrm = __int_as_float(dv.w);
-            } else {
-                const long long nn = (long long)D0 * D0 + (long long)D1 * D1 + (long long)D2 * D2;
-                nrm = __dmul_rn(__dsqrt_rn(__ll2double_rn(nn)), I::pow2(-S));
-            }
-            const R two20 = (R)(1 << (S - 1));
-            const R h0 = D0 ? I::div(two20, (R)D0) : (R)0;
-            const R h1 = D1 ? I::div(two20, (R)D1) : (R)0;
-            const R h2 = D2 ? I::div(two20, (R)D2) : (R)0;
-            const R W01 = (D0 && D1) ? I::div(h0, (R)D1) : (R)0;
-            const R W02 = (D0 && D2) ? I::div(h0, (R)D2) : (R)0;
-            const R W12 = (D1 && D2) ? I::div(h1, (R)D2) : (R)0;
-            const R u0 = I::mul((R)D0, pU), u1 = I::mul((R)D1, pU), u2 = I::mul((R)D2, pU);
-            const R Lc = I::mul(I::mul(nrm, (R)kSqrtPiOver3), I::pow2(-l));
-            R G;
-            if constexpr (sizeof(R) == 4) G = se.gf; else G = se.gd;
-            const double ph = se.ph;
-            const R taumax = A.tau_max;
-            const unsigned long long rbase =
-                A.hash ? mix64(((unsigned long long)si << 36) | ((unsigned long long)l << 31) | pix) : 0ULL;
-
-            R Ab = 0, cA = 0;           // photons absorbed by this ray (units of ph)
-            ++c_rays;
-            const bool inside0 = (unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n;
-            if (!inside0) {
-                ++c_esc;
-                c_escph += ph * (widen(P) - widen(cP));
-            }
-            unsigned seq = 0;
-
-            // One segment of length ds_p (ray parameter) in the current cell, ending at parameter
-            // tnext, where the distance to the exit face along axis b is dn_b: deposit Gamma (Eq. 1,
-            // gray, V_box) with the overlap correction (Eqs. 5-8), then update the budgets.
-            auto segment = [&](R ds_p, R dn0, R dn1, R dn2, R tnext) {
-                const R ds = I::mul(ds_p, nrm);
-                const int cell = (i2 * n + i1) * n + i0;
-                const R kraw = A.kap[cell];
-                const R kap = I::mag(kraw);
-                const R dtau = I::mul(kap, ds);
-                R a, gseg;
-                if (kap > (R)0) {
-                    a = P * (-I::em1(-dtau));
-                    gseg = I::qdiv(a * G, kap);
+            const R tm = I::sub(tnext, I::mul(ds_p, (R)0.5));
+            const R Lpix = I::mul(tm, Lc);
+            if (I::add(De, De) < Lpix) {
+                if (V.overlap_mode == RT_OVERLAP_LINEAR) {
+                    f = (R)0.5 + I::qdiv(De, Lpix);
+                } else if (V.overlap_mode == RT_OVERLAP_SQUARED) {
+                    f = (R)0.5 + I::qdiv(De, Lpix);
+                    f = f * f;
                 } else {
-                    a = (R)0;
-                    gseg = (P * G) * ds;
-                }
-                R f = (R)1, g2 = (R)0;
-                int nbcell = -1;
-                if (A.overlap_mode != RT_OVERLAP_NONE) {
-                    // distances from the segment midpoint to the six faces, order x-, x+, y-, y+, z-, z+
-                    const R d0 = I::add(dn0, I::mul(ds_p, u0));
-                    const R d1 = I::add(dn1, I::mul(ds_p, u1));
-                    const R d2 = I::add(dn2, I::mul(ds_p, u2));
-                    const R o0 = I::sub((R)1, d0), o1 = I::sub((R)1, d1), o2 = I::sub((R)1, d2);
-                    R dl[6];
-                    dl[0] = s0 > 0 ? o0 : d0;
-                    dl[1] = s0 > 0 ? d0 : o0;
-                    dl[2] = s1 > 0 ? o1 : d1;
-                    dl[3] = s1 > 0 ? d1 : o1;
-                    dl[4] = s2 > 0 ? o2 : d2;
-                    dl[5] = s2 > 0 ? d2 : o2;
-                    int face = 0;
-                    R De = dl[0];
-                    #pragma unroll
-                    for (int q = 1; q < 6; ++q) {
-                        if (dl[q] < De) { De = dl[q]; face = q; }
-                    }
-                    const R tm = I::sub(tnext, I::mul(ds_p, (R)0.5));
-                    const R Lpix = I::mul(tm, Lc);
-                    if (I::add(De, De) < Lpix) {
-                        if (A.overlap_mode == RT_OVERLAP_LINEAR) {
+                    int j0 = i0, j1 = i1, j2 = i2;
+                    const int step = (face & 1) ? 1 : -1;
+                    if ((face >> 1) == 0) j0 += step; else if ((face >> 1) == 1) j1 += step; else j2 += step;
+                    if ((unsigned)j0 < (unsigned)n && (unsigned)j1 < (unsigned)n && (unsigned)j2 < (unsigned)n) {
+                        const int c2 = (j2 * n + j1) * n + j0;
+                        const R kn_raw = V.kap[c2];
+                        const R kn = I::mag(kn_raw);
+                        const bool elig = (V.overlap_mode == RT_OVERLAP_CONSERVATIVE) ? (!I::neg(kn_raw) && kn > (R)0)
+                                                                                       : (kn > (R)0);
+                        if (elig) {
                             f = (R)0.5 + I::qdiv(De, Lpix);
-                        } else if (A.overlap_mode == RT_OVERLAP_SQUARED) {
-                            f = (R)0.5 + I::qdiv(De, Lpix);
-                            f = f * f;
-                        } else {
-                            int j0 = i0, j1 = i1, j2 = i2;
-                            const int step = (face & 1) ? 1 : -1;
-                            if ((face >> 1) == 0) j0 += step; else if ((face >> 1) == 1) j1 += step; else j2 += step;
-                            if ((unsigned)j0 < (unsigned)n && (unsigned)j1 < (unsigned)n && (unsigned)j2 < (unsigned)n) {
-                                const int c2 = (j2 * n + j1) * n + j0;
-                                const R kn_raw = A.kap[c2];
-                                const R kn = I::mag(kn_raw);
-                                const bool elig = (A.overlap_mode == RT_OVERLAP_CONSERVATIVE) ? (!I::neg(kn_raw) && kn > (R)0)
-                                                                                               : (kn > (R)0);
-                                if (elig) {
-                                    f = (R)0.5 + I::qdiv(De, Lpix);
-                                    g2 = (((R)1 - f) * gseg) * I::qdiv(kap, kn);
-                                    nbcell = c2;
-                                }
-                            }
-                        }
-                    }
-                }
-                atomicAdd(&A.gamma[cell], widen(f * gseg));
-                if (nbcell >= 0) {
-                    atomicAdd(&A.gamma[nbcell], widen(g2));
-                    ++c_sec;
-                }
-                budget_add(tau, ctau, dtau);
-                budget_add(P, cP, -a);
-                budget_add(Ab, cA, a);
-                ++c_seg;
-                if (A.hash) c_hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
-                ++seq;
-            };
-
-            if (inside0) {
-                // first event: the smallest next crossing (ties x, y, z), or the split sphere
-                int w = 0;
-                if (A10 < A01) w = 1;
-                if (w == 0 ? (A20 < A02) : (A21 < A12)) w = 2;
-                int kw = pick3(w, k0, k1, k2);
-                bool is_end = !(kw < pick3(w, ke0, ke1, ke2));
-                int prev = -1, kprev = 0;
-                R ds_p = (R)0;
-                if (!is_end) {               // from the start sphere to the first crossing
-                    const unsigned Dw = pick3(w, D0, D1, D2);
-                    const long long num = (long long)(2 * kw + 1) * kB - rq_start * (long long)Dw;
-                    ds_p = I::mul(I::of(num), I::mul(pick3(w, h0, h1, h2), pV));
-                }
-                bool alive = true;
-                // ---- segments that end on a face crossing
-                while (!is_end) {
-                    const R hw = pick3(w, h0, h1, h2);
-                    const R invw = I::mul(hw, pI);
-                    // exit-point distance to the exit face along b: (A_bw - A_wb) / (2 D_w), 0 on b = w
-                    R dn0 = (R)0, dn1 = (R)0, dn2 = (R)0;
-                    if (w == 0) {
-                        dn1 = I::mul(I::small(A10 - A01), invw);
-                        dn2 = I::mul(I::small(A20 - A02), invw);
-                    } else if (w == 1) {
-                        dn0 = I::mul(I::small(A01 - A10), invw);
-                        dn2 = I::mul(I::small(A21 - A12), invw);
-                    } else {
-                        dn0 = I::mul(I::small(A02 - A20), invw);
-                        dn1 = I::mul(I::small(A12 - A21), invw);
-                    }
-                    segment(ds_p, dn0, dn1, dn2, I::mul(I::small(2u * kw + 1u), hw));
-                    if (tau >= taumax) {             // photons spent
-                        ++c_dtau;
-                        c_dropph += ph * (widen(P) - widen(cP));
-                        c_abs += ph * (widen(Ab) - widen(cA));
-                        alive = false;
-                        break;
-                    }
-                    // step every axis whose crossing coincides with the winner's
-                    const bool t0 = (w == 0) || (w == 1 ? A01 == A10 : A02 == A20);
-                    const bool t1 = (w == 1) || (w == 0 ? A10 == A01 : A12 == A21);
-                    const bool t2 = (w == 2) || (w == 0 ? A20 == A02 : A21 == A12);
-                    if (t0) { ++k0; i0 += s0; A01 += 2u * D1; A02 += 2u * D2; }
-                    if (t1) { ++k1; i1 += s1; A10 += 2u * D0; A12 += 2u * D2; }
-                    if (t2) { ++k2; i2 += s2; A20 += 2u * D0; A21 += 2u * D1; }
-                    prev = w;
-                    kprev = kw;
-                    if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
-                        ++c_esc;
-                        c_escph += ph * (widen(P) - widen(cP));
-                        c_abs += ph * (widen(Ab) - widen(cA));
-                        alive = false;
-                        break;
-                    }
-                    // next event
-                    w = 0;
-                    if (A10 < A01) w = 1;
-                    if (w == 0 ? (A20 < A02) : (A21 < A12)) w = 2;
-                    kw = pick3(w, k0, k1, k2);
-                    is_end = !(kw < pick3(w, ke0, ke1, ke2));
-                    if (!is_end) {
-                        if (prev == w) {
-                            const R h = pick3(w, h0, h1, h2);
-                            ds_p = I::add(h, h);
-                        } else {
-                            // (2 k_w + 1) D_p - (2 k_prev + 1) D_w, with k_p = k_prev + 1 now; in [1, 2^22]
-                            const int pair = prev + w;
-                            const unsigned Dw = pick3(w, D0, D1, D2);
-                            const unsigned Awp = pair == 1 ? (w == 0 ? A01 : A10) : (pair == 2 ? (w == 0 ? A02 : A20) : (w == 1 ? A12 : A21));
-                            const unsigned Apw = pair == 1 ? (w == 0 ? A10 : A01) : (pair == 2 ? (w == 0 ? A20 : A02) : (w == 1 ? A21 : A12));
-                            ds_p = I::mul(I::small(Awp - (Apw - 2u * Dw)), pair == 1 ? W01 : (pair == 2 ? W02 : W12));
-                        }
-                    }
-                }
-                if (alive) {
-                    // ---- the last segment ends on the split sphere R_l, where k_b = kend_b on every axis
-                    if (prev < 0) {
-                        ds_p = I::mul((R)A.rq, I::pow2(l > 0 ? l - 1 - F : -F));
-                    } else {
-                        const long long num = rq_end * (long long)pick3(prev, D0, D1, D2) - (long long)(2 * kprev + 1) * kB;
-                        ds_p = I::mul(I::of(num), I::mul(pick3(prev, h0, h1, h2), pV));
-                    }
-                    const R pE = I::pow2(-(S + F));
-                    const R e0 = I::mul(I::of((long long)(2 * ke0 + 1) * kB - rq_end * (long long)D0), pE);
-                    const R e1 = I::mul(I::of((long long)(2 * ke1 + 1) * kB - rq_end * (long long)D1), pE);
-                    const R e2 = I::mul(I::of((long long)(2 * ke2 + 1) * kB - rq_end * (long long)D2), pE);
-                    segment(ds_p, e0, e1, e2, I::mul((R)A.rq, I::pow2(l - F)));
-                    if (tau >= taumax) {
-                        ++c_dtau;
-                        c_dropph += ph * (widen(P) - widen(cP));
-                        c_abs += ph * (widen(Ab) - widen(cA));
-                    } else {
-                        c_abs += ph * (widen(Ab) - widen(cA));
-                        if (l + 1 > A.level_max) {
-                            ++c_dlev;
-                            c_dropph += ph * (widen(P) - widen(cP));
-                        } else {
-                            ++c_split;
-                            split = true;
-                            o_src = si;
-                            o_pix = pix;
-                            o_P = P;
-                            o_tau = tau;
-                            if constexpr (sizeof(R) == 4) {
-                                o_cP = cP;
-                                o_ctau = ctau;
-                            }
+                            g2 = (((R)1 - f) * gseg) * I::qdiv(kap, kn);
+                            nbcell = c2;
                         }
                     }
                 }
             }
         }
-        // ---- warp-aggregated append of the rays that split (Alg. 1 FILTERCOPYTRANSFORM<3>)
-        const unsigned m = __ballot_sync(0xffffffffu, split);
-        if (m) {
-            const int leader = __ffs(m) - 1;
-            unsigned long long pos0 = 0;
-            if (lane == leader) pos0 = atomicAdd(A.out_count, (unsigned long long)__popc(m));
-            pos0 = __shfl_sync(0xffffffffu, pos0, leader);
-            if (split) {
-                const unsigned long long pos = pos0 + __popc(m & ((1u << lane) - 1u));
-                if (pos < (unsigned long long)A.out.cap) {
-                    A.out.src[pos] = o_src;
-                    A.out.pix[pos] = o_pix;
-                    A.out.P[pos] = o_P;
-                    A.out.tau[pos] = o_tau;
-                    if constexpr (sizeof(R) == 4) {
-                        A.out.cP[pos] = o_cP;
-                        A.out.ctau[pos] = o_ctau;
-                    }
+        atomicAdd(&V.gamma[cell], widen(f * gseg));
+        if (nbcell >= 0) {
+            atomicAdd(&V.gamma[nbcell], widen(g2));
+            ++T.sec;
+        }
+        budget_add(tau, ctau, dtau);
+        budget_add(P, cP, -a);
+        budget_add(Ab, cA, a);
+        ++T.seg;
+        if (V.hash) T.hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
+        ++seq;
+    };
+
+    if (inside0) {
+        // first event: the smallest next crossing (ties x, y, z), or the split sphere
+        int w = 0;
+        if (A10 < A01) w = 1;
+        if (w == 0 ? (A20 < A02) : (A21 < A12)) w = 2;
+        int kw = pick3(w, k0, k1, k2);
+        bool is_end = !(kw < pick3(w, ke0, ke1, ke2));
+        int prev = -1, kprev = 0;
+        R ds_p = (R)0;
+        if (!is_end) {               // from the start sphere to the first crossing
+            const unsigned Dw = pick3(w, D0, D1, D2);
+            const long long num = (long long)(2 * kw + 1) * kB - rq_start * (long long)Dw;
+            ds_p = I::mul(I::of(num), I::mul(pick3(w, h0, h1, h2), pV));
+        }
+        bool alive = true;
+        // ---- segments that end on a face crossing
+        while (!is_end) {
+            const R hw = pick3(w, h0, h1, h2);
+            const R invw = I::mul(hw, pI);
+            // exit-point distance to the exit face along b: (A_bw - A_wb) / (2 D_w), 0 on b = w
+            R dn0 = (R)0, dn1 = (R)0, dn2 = (R)0;
+            if (w == 0) {
+                dn1 = I::mul(I::small(A10 - A01), invw);
+                dn2 = I::mul(I::small(A20 - A02), invw);
+            } else if (w == 1) {
+                dn0 = I::mul(I::small(A01 - A10), invw);
+                dn2 = I::mul(I::small(A21 - A12), invw);
+            } else {
+                dn0 = I::mul(I::small(A02 - A20), invw);
+                dn1 = I::mul(I::small(A12 - A21), invw);
+            }
+            segment(ds_p, dn0, dn1, dn2, I::mul(I::small(2u * kw + 1u), hw));
+            if (tau >= taumax) {             // photons spent
+                ++T.dtau;
+                T.dropph += ph * (widen(P) - widen(cP));
+                T.abs += ph * (widen(Ab) - widen(cA));
+                alive = false;
+                break;
+            }
+            // step every axis whose crossing coincides with the winner's
+            const bool t0 = (w == 0) || (w == 1 ? A01 == A10 : A02 == A20);
+            const bool t1 = (w == 1) || (w == 0 ? A10 == A01 : A12 == A21);
+            const bool t2 = (w == 2) || (w == 0 ? A20 == A02 : A21 == A12);
+            if (t0) { ++k0; i0 += s0; A01 += 2u * D1; A02 += 2u * D2; }
+            if (t1) { ++k1; i1 += s1; A10 += 2u * D0; A12 += 2u * D2; }
+            if (t2) { ++k2; i2 += s2; A20 += 2u * D0; A21 += 2u * D1; }
+            prev = w;
+            kprev = kw;
+            if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
+                ++T.esc;
+                T.escph += ph * (widen(P) - widen(cP));
+                T.abs += ph * (widen(Ab) - widen(cA));
+                alive = false;
+                break;
+            }
+            // next event
+            w = 0;
+            if (A10 < A01) w = 1;
+            if (w == 0 ? (A20 < A02) : (A21 < A12)) w = 2;
+            kw = pick3(w, k0, k1, k2);
+            is_end = !(kw < pick3(w, ke0, ke1, ke2));
+            if (!is_end) {
+                if (prev == w) {
+                    const R h = pick3(w, h0, h1, h2);
+                    ds_p = I::add(h, h);
                 } else {
-                    atomicOr(&A.st->err, kErrRayOverflow);
+                    // (2 k_w + 1) D_p - (2 k_prev + 1) D_w, with k_p = k_prev + 1 now; in [1, 2^22]
+                    const int pair = prev + w;
+                    const unsigned Dw = pick3(w, D0, D1, D2);
+                    const unsigned Awp = pair == 1 ? (w == 0 ? A01 : A10) : (pair == 2 ? (w == 0 ? A02 : A20) : (w == 1 ? A12 : A21));
+                    const unsigned Apw = pair == 1 ? (w == 0 ? A10 : A01) : (pair == 2 ? (w == 0 ? A20 : A02) : (w == 1 ? A21 : A12));
+                    ds_p = I::mul(I::small(Awp - (Apw - 2u * Dw)), pair == 1 ? W01 : (pair == 2 ? W02 : W12));
+                }
+            }
+        }
+        if (alive) {
+            // ---- the last segment ends on the split sphere R_l, where k_b = kend_b on every axis
+            if (prev < 0) {
+                ds_p = I::mul((R)V.rq, I::pow2(l > 0 ? l - 1 - F : -F));
+            } else {
+                const long long num = rq_end * (long long)pick3(prev, D0, D1, D2) - (long long)(2 * kprev + 1) * kB;
+                ds_p = I::mul(I::of(num), I::mul(pick3(prev, h0, h1, h2), pV));
+            }
+            const R pE = I::pow2(-(S + F));
+            const R e0 = I::mul(I::of((long long)(2 * ke0 + 1) * kB - rq_end * (long long)D0), pE);
+            const R e1 = I::mul(I::of((long long)(2 * ke1 + 1) * kB - rq_end * (long long)D1), pE);
+            const R e2 = I::mul(I::of((long long)(2 * ke2 + 1) * kB - rq_end * (long long)D2), pE);
+            segment(ds_p, e0, e1, e2, I::mul((R)V.rq, I::pow2(l - F)));
+            if (tau >= taumax) {
+                ++T.dtau;
+                T.dropph += ph * (widen(P) - widen(cP));
+                T.abs += ph * (widen(Ab) - widen(cA));
+            } else {
+                T.abs += ph * (widen(Ab) - widen(cA));
+                if (l + 1 > V.level_max) {
+                    ++T.dlev;
+                    T.dropph += ph * (widen(P) - widen(cP));
+                } else {
+                    ++T.split;
+                    split = true;
+                    oP = P;
+                    otau = tau;
+                    if constexpr (sizeof(R) == 4) {
+                        ocP = cP;
+                        octau = ctau;
+                    }
                 }
             }
         }
     }
+    return split;
+}
 
-    // ---- statistics and photon ledger: one atomic per warp and counter
-    const unsigned long long r_rays = warp_sum((unsigned long long)c_rays);
-    const unsigned long long r_split = warp_sum((unsigned long long)c_split);
-    const unsigned long long r_esc = warp_sum((unsigned long long)c_esc);
-    const unsigned long long r_dtau = warp_sum((unsigned long long)c_dtau);
-    const unsigned long long r_dlev = warp_sum((unsigned long long)c_dlev);
-    const unsigned long long r_seg = warp_sum((unsigned long long)c_seg);
-    const unsigned long long r_sec = warp_sum((unsigned long long)c_sec);
-    c_hash = warp_sum(c_hash);
-    c_abs = warp_sum(c_abs);
-    c_escph = warp_sum(c_escph);
-    c_dropph = warp_sum(c_dropph);
-    if (lane == 0 && r_rays) {
-        DevStats* st = A.st;
-        atomicAdd(&st->rays[l], r_rays);
-        if (r_split) atomicAdd(&st->splits[l], r_split);
-        if (r_esc) atomicAdd(&st->escaped[l], r_esc);
-        if (r_dtau) atomicAdd(&st->dropped_tau[l], r_dtau);
-        if (r_dlev) atomicAdd(&st->dropped_level[l], r_dlev);
-        atomicAdd(&st->segments[l], r_seg);
-        if (r_sec) atomicAdd(&st->secondary[l], r_sec);
-        if (c_hash) atomicAdd(&st->visit_hash, c_hash);
-        atomicAdd(&st->absorbed, c_abs);
-        atomicAdd(&st->escaped_ph, c_escph);
-        atomicAdd(&st->dropped_ph, c_dropph);
+// Warp-aggregated append of the rays that split (Alg. 1 FILTERCOPYTRANSFORM<3>): one
+// atomic per warp reserves the records; each splitting lane writes its parent record.
+template <class R>
+__device__ __forceinline__ void append_split(bool split, uint32_t si, uint32_t pix, R P, R tau, float cP, float ctau,
+                                             const RayBuf<R>& out, unsigned long long* count, unsigned* err)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, split);
+    if (!m) return;
+    const int leader = __ffs(m) - 1;
+    unsigned long long pos0 = 0;
+    if (lane == leader) pos0 = atomicAdd(count, (unsigned long long)__popc(m));
+    pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+    if (split) {
+        const unsigned long long pos = pos0 + __popc(m & ((1u << lane) - 1u));
+        if (pos < (unsigned long long)out.cap) {
+            out.src[pos] = si;
+            out.pix[pos] = pix;
+            out.P[pos] = P;
+            out.tau[pos] = tau;
+            if constexpr (sizeof(R) == 4) {
+                out.cP[pos] = cP;
+                out.ctau[pos] = ctau;
+            }
+        } else {
+            atomicOr(err, kErrRayOverflow);
+        }
+    }
+}
+
+// Load child j of the level-l parents (level 0: ray j of the emission, 12 per source).
+template <class R>
+__device__ __forceinline__ void load_ray(int l, long long j, const RayBuf<R>& in, uint32_t& si, uint32_t& pix, R& P,
+                                         R& tau, R& cP, R& ctau)
+{
+    using I = Ieee<R>;
+    if (l == 0) {
+        si = (uint32_t)(j / 12);
+        pix = (uint32_t)(j - 12LL * si);
+        P = (R)1;
+        tau = (R)0;
+        cP = (R)0;
+        ctau = (R)0;
+    } else {
+        const long long q = j >> 2;
+        si = in.src[q];
+        pix = 4u * in.pix[q] + (uint32_t)(j & 3);
+        P = I::mul(in.P[q], (R)0.25);
+        tau = in.tau[q];
+        cP = (R)0;
+        ctau = (R)0;
+        if constexpr (sizeof(R) == 4) {
+            cP = I::mul(in.cP[q], 0.25f);
+            ctau = in.ctau[q];
+        }
+    }
+}
+
+// Sum a tally over the warp lanes in `mask` that carry the same solve, and add
+// it into that solve's statistics (one atomic per group and counter).
+__device__ __forceinline__ void flush_tally(Tally& T, unsigned mask, DevStats* const* st_of_lane, int l)
+{
+    const int lane = threadIdx.x & 31;
+    DevStats* mine = *st_of_lane;
+    while (mask) {
+        const int leader = __ffs(mask) - 1;
+        const unsigned long long key = __shfl_sync(mask, (unsigned long long)mine, leader);
+        const unsigned grp = __ballot_sync(mask, (unsigned long long)mine == key);
+        if ((grp >> lane) & 1u) {
+            const unsigned rays = __reduce_add_sync(grp, T.rays), split = __reduce_add_sync(grp, T.split);
+            const unsigned esc = __reduce_add_sync(grp, T.esc), dtau = __reduce_add_sync(grp, T.dtau);
+            const unsigned dlev = __reduce_add_sync(grp, T.dlev), seg = __reduce_add_sync(grp, T.seg);
+            const unsigned sec = __reduce_add_sync(grp, T.sec);
+            unsigned long long hash = 0ULL;
+            double ab = 0.0, ep = 0.0, dp = 0.0;
+            for (unsigned g = grp; g; g &= g - 1) {
+                const int b = __ffs(g) - 1;
+                hash += __shfl_sync(grp, T.hash, b);
+                ab += __shfl_sync(grp, T.abs, b);
+                ep += __shfl_sync(grp, T.escph, b);
+                dp += __shfl_sync(grp, T.dropph, b);
+            }
+            if (lane == leader && rays) {
+                DevStats* st = mine;
+                atomicAdd(&st->rays[l], (unsigned long long)rays);
+                if (split) atomicAdd(&st->splits[l], (unsigned long long)split);
+                if (esc) atomicAdd(&st->escaped[l], (unsigned long long)esc);
+                if (dtau) atomicAdd(&st->dropped_tau[l], (unsigned long long)dtau);
+                if (dlev) atomicAdd(&st->dropped_level[l], (unsigned long long)dlev);
+                atomicAdd(&st->segments[l], (unsigned long long)seg);
+                if (sec) atomicAdd(&st->secondary[l], (unsigned long long)sec);
+                if (hash) atomicAdd(&st->visit_hash, hash);
+                atomicAdd(&st->absorbed, ab);
+                atomicAdd(&st->escaped_ph, ep);
+                atomicAdd(&st->dropped_ph, dp);
+            }
+            T.clear();
+        }
+        mask &= ~grp;
+    }
+}
+
+// One level (or one slice of it) of one solve: thread j marches child j.
+template <class R>
+__global__ void __launch_bounds__(256, 2) march_kernel(const MarchArgs<R> A)
+{
+    const int l = A.level;
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = (long long)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarp = (long long)(gridDim.x * blockDim.x) >> 5;
+    SolveView<R> V;
+    V.kap = A.kap;
+    V.gamma = A.gamma;
+    V.n = A.n;
+    V.level_max = A.level_max;
+    V.overlap_mode = A.overlap_mode;
+    V.hash = A.hash;
+    V.rq = A.rq;
+    V.tau_max = A.tau_max;
+    V.src_off = 0;
+    Tally T;
+    T.clear();
+    for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
+        const long long j = base + lane;
+        bool split = false;
+        uint32_t si = 0, pix = 0;
+        R oP = 0, otau = 0;
+        float ocP = 0.f, octau = 0.f;
+        if (j < A.c1) {
+            R P, tau, cP, ctau;
+            load_ray<R>(l, j, A.in, si, pix, P, tau, cP, ctau);
+            split = march_ray<R>(V, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T, oP, otau, ocP, octau);
+        }
+        append_split<R>(split, si, pix, oP, otau, ocP, octau, A.out, A.out_count, &A.st->err);
+    }
+    DevStats* st = A.st;
+    flush_tally(T, 0xffffffffu, &st, l);
+}
+
+// All solves of a batch in one cooperative launch. Every block runs the same
+// depth-first schedule over (level, slice of children): a slice's children are
+// claimed in tiles by warps through a device counter (the work queue), the
+// parents that split go to the next level's buffer, and grid.sync() separates
+// slices; the next level's slices run before the current level's remaining ones,
+// so no buffer ever holds more than one slice's output. Only CUDA's grid barrier
+// is waited on: no block spins on another's flag.
+template <class R>
+__global__ void __launch_bounds__(256, 2) batch_kernel(const BatchArgs<R> A)
+{
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    const int lane = threadIdx.x & 31;
+    int lev[RT_MAX_LEVELS + 1];
+    long long tot[RT_MAX_LEVELS + 1], nxt[RT_MAX_LEVELS + 1];
+    int depth = 0;
+    lev[0] = 0;
+    tot[0] = 12LL * A.nsrc;
+    nxt[0] = 0;
+    int sid = 0;
+    while (depth >= 0) {
+        if (nxt[depth] >= tot[depth]) {
+            --depth;
+            continue;
+        }
+        const int l = lev[depth];
+        const long long c0 = nxt[depth];
+        const long long c1 = min(tot[depth], c0 + A.slice);
+        nxt[depth] = c1;
+        if (sid >= A.max_slices || l > A.table_level || depth >= RT_MAX_LEVELS) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, kErrLevel);
+            break;
+        }
+        const int4* dirs = A.dirs + 4LL * ((1LL << (2 * l)) - 1);
+        Tally T;
+        T.clear();
+        DevStats* cur = nullptr;
+        for (;;) {
+            long long t = 0;
+            if (lane == 0) t = (long long)atomicAdd(&A.tiles[sid], 1ULL);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            const long long s0 = c0 + t * A.tile;
+            if (s0 >= c1) break;
+            const long long s1 = min(c1, s0 + (long long)A.tile);
+            for (long long base = s0; base < s1; base += 32) {
+                const long long j = base + lane;
+                bool split = false;
+                uint32_t si = 0, pix = 0;
+                R oP = 0, otau = 0;
+                float ocP = 0.f, octau = 0.f;
+                DevStats* st = cur;
+                SrcEntry se;
+                R P = 0, tau = 0, cP = 0, ctau = 0;
+                if (j < s1) {
+                    load_ray<R>(l, j, A.buf[l], si, pix, P, tau, cP, ctau);
+                    se = A.src[si];
+                    st = A.solves[se.pad].st;
+                }
+                // a lane whose solve changes hands its tally over first
+                const unsigned chg = __ballot_sync(0xffffffffu, cur != nullptr && st != cur);
+                if (chg) flush_tally(T, chg, &cur, l);
+                if (j < s1) {
+                    cur = st;
+                    const BatchSolve& bs = A.solves[se.pad];
+                    SolveView<R> V;
+                    V.kap = static_cast<const R*>(bs.kap);
+                    V.gamma = bs.gamma;
+                    V.n = bs.n;
+                    V.level_max = bs.level_max;
+                    V.overlap_mode = bs.overlap_mode;
+                    V.hash = bs.hash;
+                    V.rq = bs.rq;
+                    V.tau_max = (R)bs.tau_max;
+                    V.src_off = bs.src_off - A.src_base;
+                    split = march_ray<R>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau, ocP, octau);
+                }
+                append_split<R>(split, si, pix, oP, otau, ocP, octau, A.buf[l + 1], &A.counts[sid], A.err);
+            }
+        }
+        const unsigned have = __ballot_sync(0xffffffffu, cur != nullptr);
+        if (have) flush_tally(T, have, &cur, l);
+        grid.sync();
+        const unsigned long long nn = *((volatile unsigned long long*)&A.counts[sid]);
+        ++sid;
+        if (nn > 0) {
+            ++depth;
+            lev[depth] = l + 1;
+            tot[depth] = 4LL * (long long)nn;
+            nxt[depth] = 0;
+        }
     }
 }
 
@@ -486,6 +663,33 @@ int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_
 {
     march_kernel<float><<<grid, block, 0, s>>>(a);
     return 1;
+}
+
+template <class R>
+static cudaError_t launch_batch_impl(const BatchArgs<R>& a, int grid, int block, cudaStream_t s)
+{
+    void* args[] = {const_cast<BatchArgs<R>*>(&a)};
+    return cudaLaunchCooperativeKernel((const void*)batch_kernel<R>, dim3(grid), dim3(block), args, 0, s);
+}
+
+cudaError_t launch_batch_f64(const BatchArgs<double>& a, int grid, int block, cudaStream_t s)
+{
+    return launch_batch_impl<double>(a, grid, block, s);
+}
+
+cudaError_t launch_batch_f32(const BatchArgs<float>& a, int grid, int block, cudaStream_t s)
+{
+    return launch_batch_impl<float>(a, grid, block, s);
+}
+
+int batch_blocks_per_sm(int precision, int block)
+{
+    int nb = 0;
+    if (precision == RT_FP32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_kernel<float>, block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_kernel<double>, block, 0);
+    return nb;
 }
 
 }  // namespace nyx

@@ -20,7 +20,7 @@
 #include <string>
 #include <vector>
 
-#include "rt_internal.h"
+#include "rt_handle.h"
 
 using namespace nyx;
 
@@ -41,7 +41,12 @@ struct DirTable {
 std::mutex g_dir_mu;
 std::map<int, DirTable> g_dirs;          // per device; superseded tables stay allocated (handles may use them)
 
-int ensure_directions(int device, int level, const int4** out, std::string& err)
+
+
+
+}  // namespace
+
+int nyx::ensure_directions(int device, int level, const int4** out, std::string& err)
 {
     std::lock_guard<std::mutex> lk(g_dir_mu);
     DirTable& t = g_dirs[device];
@@ -73,107 +78,8 @@ int ensure_directions(int device, int level, const int4** out, std::string& err)
     return RT_OK;
 }
 
-struct DeviceGuard {
-    int old = -1;
-    explicit DeviceGuard(int dev)
-    {
-        cudaGetDevice(&old);
-        if (old != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (old >= 0 && cur != old) cudaSetDevice(old);
-    }
-};
 
-// One level's ray records, allocated as one block.
-struct RayStore {
-    void* base = nullptr;
-    int64_t cap = 0;
-};
-
-template <class T>
-T* carve(char*& p, int64_t count)
-{
-    T* r = reinterpret_cast<T*>(p);
-    p += ((sizeof(T) * (size_t)count + 255) / 256) * 256;
-    return r;
-}
-
-size_t ray_bytes(int64_t cap, int real_size)
-{
-    auto pad = [](size_t b) { return ((b + 255) / 256) * 256; };
-    size_t b = 2 * pad(4 * (size_t)cap) + 2 * pad((size_t)real_size * (size_t)cap);
-    if (real_size == 4) b += 2 * pad(4 * (size_t)cap);
-    return b;
-}
-
-template <class R>
-RayBuf<R> ray_view(const RayStore& s)
-{
-    RayBuf<R> b;
-    if (!s.base) return b;
-    char* p = static_cast<char*>(s.base);
-    b.src = carve<uint32_t>(p, s.cap);
-    b.pix = carve<uint32_t>(p, s.cap);
-    b.P = carve<R>(p, s.cap);
-    b.tau = carve<R>(p, s.cap);
-    if (sizeof(R) == 4) {
-        b.cP = carve<float>(p, s.cap);
-        b.ctau = carve<float>(p, s.cap);
-    }
-    b.cap = s.cap;
-    return b;
-}
-
-}  // namespace
-
-struct rt_handle {
-    rt_config cfg{};
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    int sm_count = 152;
-    int64_t ncell = 0;
-    double dx = 0, vol = 0, sdx = 0, s_over_dx2 = 0;
-    int64_t rq = 0;
-    int level_max = 0;
-    int table_level = 0;
-    const int4* dirs = nullptr;
-
-    double* d_nh = nullptr;
-    double* d_x = nullptr;
-    double* d_xavg = nullptr;
-    double* d_xend = nullptr;
-    double* d_gamma = nullptr;
-    double* d_heat = nullptr;
-    void* d_kap = nullptr;
-    double* d_scalar = nullptr;           // reduction scratch
-
-    SourceWork sw;
-    int64_t nsrc = 0;
-    SrcEntry* d_emit = nullptr;
-    int64_t n_emit = 0;
-
-    RayStore rays[RT_MAX_LEVELS + 1];
-    unsigned long long* d_count = nullptr;   // one per level
-    DevStats* d_st = nullptr;
-    DevStats* h_st = nullptr;                // pinned
-    unsigned long long* h_count = nullptr;   // pinned
-    int32_t* h_i32 = nullptr;                // pinned scratch
-    double* h_f64 = nullptr;                 // pinned scratch
-
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    double ms_march = 0.0;
-    bool fields_set = false;
-    bool sticky = false;
-    int launches = 0;
-    int march_launches = 0;
-    std::string err;
-};
-
-namespace {
+namespace nyx {
 
 int fail(rt_handle* h, int code, const std::string& msg)
 {
@@ -188,18 +94,6 @@ int cuda_fail(rt_handle* h, cudaError_t e, const char* what)
     if (e == cudaErrorMemoryAllocation) return fail(h, RT_ENOMEM, std::string(what) + ": out of device memory");
     return fail(h, RT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
-
-#define RT_CUDA(h, call, what)                                \
-    do {                                                      \
-        cudaError_t e_ = (call);                              \
-        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
-    } while (0)
-
-#define RT_LAUNCHED(h, what)                                              \
-    do {                                                                  \
-        cudaError_t e_ = cudaGetLastError();                              \
-        if (e_ != cudaSuccess) return cuda_fail(h, e_, what);             \
-    } while (0)
 
 int grow_sources(rt_handle* h, int64_t need)
 {
@@ -349,6 +243,63 @@ int trace(rt_handle* h, const double* xuse)
     int rc = h->cfg.precision == RT_FP32 ? run_level<float>(h, 0, 0) : run_level<double>(h, 0, 0);
     if (rc) return rc;
     RT_CUDA(h, cudaEventRecord(h->ev[2], h->stream), "event");
+    return RT_OK;
+}
+
+// Sec. 2.8 source stage of a step: validation of device-resident inputs,
+// dedup + sort, the n_th default, Alg. 3 merging when on, and the emitted
+// catalog (h->d_emit, h->n_emit). Leaves h->h_f64[1] = mean n_H (default n_th).
+int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out)
+{
+    cudaStream_t s = h->stream;
+    *merged_out = false;
+    // ---- validation of device-resident inputs
+    h->launches += launch_validate_fields(h->d_nh, h->d_x, h->ncell, h->d_st, s);
+    h->launches += launch_validate_sources(h->sw.cells_raw, h->sw.ndot_raw, h->nsrc, h->cfg.n, h->d_st, s);
+    RT_LAUNCHED(h, "validation launch");
+
+    // ---- sources: dedup + sort (Sec. 2.8)
+    h->launches += launch_dedup_sort(h->sw, h->nsrc, s);
+    RT_LAUNCHED(h, "source launch");
+    bool want_mean_nh = h->cfg.n_th_cm3 < 0;
+    if (want_mean_nh) {
+        RT_CUDA(h, cudaMemsetAsync(h->d_scalar, 0, sizeof(double), s), "scalar clear");
+        h->launches += launch_mean_nh(h->d_nh, h->ncell, h->d_scalar, s);
+    }
+    if (h->cfg.merge_mode == RT_MERGE_AUTO) h->launches += launch_sum_x(h->d_x, h->ncell, h->d_st, s);
+    RT_LAUNCHED(h, "reduction launch");
+    RT_CUDA(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "stats read");
+    if (h->nsrc > 0)
+        RT_CUDA(h, cudaMemcpyAsync(h->h_i32, h->sw.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count read");
+    if (want_mean_nh)
+        RT_CUDA(h, cudaMemcpyAsync(h->h_f64, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s), "mean read");
+    RT_CUDA(h, cudaStreamSynchronize(s), "source stage");
+    if (h->h_st->bad_input) return fail(h, RT_EINVAL, "invalid field or source values (n_H < 0, x outside [0,1], non-finite, bad source)");
+    h->h_f64[1] = want_mean_nh ? h->h_f64[0] / (double)h->ncell : 0.0;
+    int64_t m = h->nsrc > 0 ? h->h_i32[0] : 0;
+    *n_dedup_out = m;
+    const double xbar = h->h_st->xsum / (double)h->ncell;
+
+    // ---- Alg. 3 source merging
+    if (m > 0 && (h->cfg.merge_mode == RT_MERGE_FORCED ||
+                  (h->cfg.merge_mode == RT_MERGE_AUTO && xbar > h->cfg.automerge_xbar))) {
+        const int Ls = h->cfg.merge_samp_level;
+        h->launches += launch_merge(h->sw, m, h->cfg.n, h->d_x, h->dirs + healpix_level_offset(Ls),
+                                    (int)(12 * (int64_t(1) << (2 * Ls))), h->cfg.merge_x_th, h->cfg.merge_f_req,
+                                    h->cfg.merge_n_min, h->cfg.merge_dr_cells, h->cfg.merge_rmax_cells,
+                                    h->cfg.merge_f_ov, h->cfg.merge_eps, h->d_st, s);
+        RT_LAUNCHED(h, "merge launch");
+        RT_CUDA(h, cudaMemcpyAsync(h->h_i32, h->sw.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count read");
+        RT_CUDA(h, cudaMemcpyAsync(h->h_i32 + 1, &h->d_st->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "err read");
+        RT_CUDA(h, cudaStreamSynchronize(s), "merge");
+        if (h->h_i32[1]) return fail(h, RT_EDEVICE, "source merge reported an internal error");
+        m = h->h_i32[0];
+        *merged_out = true;
+    }
+    h->launches += launch_build_emit(h->sw, m, h->s_over_dx2, h->d_emit, h->d_st, s);
+    RT_LAUNCHED(h, "emit launch");
+    h->n_emit = m;
+
     return RT_OK;
 }
 
@@ -567,53 +518,13 @@ int rt_step(rt_handle* h, double dt_s, double* gamma_out, double* heat_out, int 
     RT_CUDA(h, cudaMemsetAsync(h->d_st, 0, sizeof(DevStats), s), "stats clear");
     RT_CUDA(h, cudaEventRecord(h->ev[0], s), "event");
 
-    // ---- validation of device-resident inputs
-    h->launches += launch_validate_fields(h->d_nh, h->d_x, h->ncell, h->d_st, s);
-    h->launches += launch_validate_sources(h->sw.cells_raw, h->sw.ndot_raw, h->nsrc, h->cfg.n, h->d_st, s);
-    RT_LAUNCHED(h, "validation launch");
-
-    // ---- sources: dedup + sort (Sec. 2.8)
-    h->launches += launch_dedup_sort(h->sw, h->nsrc, s);
-    RT_LAUNCHED(h, "source launch");
-    bool want_mean_nh = h->cfg.n_th_cm3 < 0;
-    if (want_mean_nh) {
-        RT_CUDA(h, cudaMemsetAsync(h->d_scalar, 0, sizeof(double), s), "scalar clear");
-        h->launches += launch_mean_nh(h->d_nh, h->ncell, h->d_scalar, s);
-    }
-    if (h->cfg.merge_mode == RT_MERGE_AUTO) h->launches += launch_sum_x(h->d_x, h->ncell, h->d_st, s);
-    RT_LAUNCHED(h, "reduction launch");
-    RT_CUDA(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "stats read");
-    if (h->nsrc > 0)
-        RT_CUDA(h, cudaMemcpyAsync(h->h_i32, h->sw.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count read");
-    if (want_mean_nh)
-        RT_CUDA(h, cudaMemcpyAsync(h->h_f64, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s), "mean read");
-    RT_CUDA(h, cudaStreamSynchronize(s), "source stage");
-    if (h->h_st->bad_input) return fail(h, RT_EINVAL, "invalid field or source values (n_H < 0, x outside [0,1], non-finite, bad source)");
-    h->h_f64[1] = want_mean_nh ? h->h_f64[0] / (double)h->ncell : 0.0;
-    int64_t m = h->nsrc > 0 ? h->h_i32[0] : 0;
-    const int64_t n_dedup = m;
-    const double xbar = h->h_st->xsum / (double)h->ncell;
-
-    // ---- Alg. 3 source merging
     bool merged = false;
-    if (m > 0 && (h->cfg.merge_mode == RT_MERGE_FORCED ||
-                  (h->cfg.merge_mode == RT_MERGE_AUTO && xbar > h->cfg.automerge_xbar))) {
-        const int Ls = h->cfg.merge_samp_level;
-        h->launches += launch_merge(h->sw, m, h->cfg.n, h->d_x, h->dirs + healpix_level_offset(Ls),
-                                    (int)(12 * (int64_t(1) << (2 * Ls))), h->cfg.merge_x_th, h->cfg.merge_f_req,
-                                    h->cfg.merge_n_min, h->cfg.merge_dr_cells, h->cfg.merge_rmax_cells,
-                                    h->cfg.merge_f_ov, h->cfg.merge_eps, h->d_st, s);
-        RT_LAUNCHED(h, "merge launch");
-        RT_CUDA(h, cudaMemcpyAsync(h->h_i32, h->sw.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count read");
-        RT_CUDA(h, cudaMemcpyAsync(h->h_i32 + 1, &h->d_st->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "err read");
-        RT_CUDA(h, cudaStreamSynchronize(s), "merge");
-        if (h->h_i32[1]) return fail(h, RT_EDEVICE, "source merge reported an internal error");
-        m = h->h_i32[0];
-        merged = true;
+    int64_t n_dedup = 0;
+    {
+        const int rc = prepare_sources(h, &merged, &n_dedup);
+        if (rc) return rc;
     }
-    h->launches += launch_build_emit(h->sw, m, h->s_over_dx2, h->d_emit, h->d_st, s);
-    RT_LAUNCHED(h, "emit launch");
-    h->n_emit = m;
+    const int64_t m = h->n_emit;
 
     // ---- trace, optionally iterated with the C2-Ray update (Sec. 2.4)
     int iters = 0;

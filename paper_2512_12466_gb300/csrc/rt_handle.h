@@ -1,0 +1,132 @@
+// The rt_handle struct and host-runtime helpers shared by the translation
+// units behind the C ABI (rt_api.cu, batch.cu). Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "rt_internal.h"
+
+namespace nyx {
+
+struct DeviceGuard {
+    int old = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&old);
+        if (old != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (old >= 0 && cur != old) cudaSetDevice(old);
+    }
+};
+
+// One level's ray records, allocated as one block.
+struct RayStore {
+    void* base = nullptr;
+    int64_t cap = 0;
+};
+
+template <class T>
+inline T* carve(char*& p, int64_t count)
+{
+    T* r = reinterpret_cast<T*>(p);
+    p += ((sizeof(T) * (size_t)count + 255) / 256) * 256;
+    return r;
+}
+
+inline size_t ray_bytes(int64_t cap, int real_size)
+{
+    auto pad = [](size_t b) { return ((b + 255) / 256) * 256; };
+    size_t b = 2 * pad(4 * (size_t)cap) + 2 * pad((size_t)real_size * (size_t)cap);
+    if (real_size == 4) b += 2 * pad(4 * (size_t)cap);
+    return b;
+}
+
+template <class R>
+inline RayBuf<R> ray_view(const RayStore& s)
+{
+    RayBuf<R> b;
+    if (!s.base) return b;
+    char* p = static_cast<char*>(s.base);
+    b.src = carve<uint32_t>(p, s.cap);
+    b.pix = carve<uint32_t>(p, s.cap);
+    b.P = carve<R>(p, s.cap);
+    b.tau = carve<R>(p, s.cap);
+    if (sizeof(R) == 4) {
+        b.cP = carve<float>(p, s.cap);
+        b.ctau = carve<float>(p, s.cap);
+    }
+    b.cap = s.cap;
+    return b;
+}
+
+}  // namespace nyx
+
+struct rt_handle {
+    rt_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 152;
+    int64_t ncell = 0;
+    double dx = 0, vol = 0, sdx = 0, s_over_dx2 = 0;
+    int64_t rq = 0;
+    int level_max = 0;
+    int table_level = 0;
+    const int4* dirs = nullptr;
+
+    double* d_nh = nullptr;
+    double* d_x = nullptr;
+    double* d_xavg = nullptr;
+    double* d_xend = nullptr;
+    double* d_gamma = nullptr;
+    double* d_heat = nullptr;
+    void* d_kap = nullptr;
+    double* d_scalar = nullptr;           // reduction scratch
+
+    nyx::SourceWork sw;
+    int64_t nsrc = 0;
+    nyx::SrcEntry* d_emit = nullptr;
+    int64_t n_emit = 0;
+
+    nyx::RayStore rays[RT_MAX_LEVELS + 1];
+    unsigned long long* d_count = nullptr;   // one per level
+    nyx::DevStats* d_st = nullptr;
+    nyx::DevStats* h_st = nullptr;                // pinned
+    unsigned long long* h_count = nullptr;   // pinned
+    int32_t* h_i32 = nullptr;                // pinned scratch
+    double* h_f64 = nullptr;                 // pinned scratch
+
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double ms_march = 0.0;
+    bool fields_set = false;
+    bool sticky = false;
+    int launches = 0;
+    int march_launches = 0;
+    std::string err;
+};
+
+namespace nyx {
+
+int fail(rt_handle* h, int code, const std::string& msg);
+int cuda_fail(rt_handle* h, cudaError_t e, const char* what);
+int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out);
+int ensure_directions(int device, int level, const int4** out, std::string& err);
+
+}  // namespace nyx
+
+#define RT_CUDA(h, call, what)                                      \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return nyx::cuda_fail(h, e_, what);  \
+    } while (0)
+
+#define RT_LAUNCHED(h, what)                                        \
+    do {                                                            \
+        cudaError_t e_ = cudaGetLastError();                        \
+        if (e_ != cudaSuccess) return nyx::cuda_fail(h, e_, what);  \
+    } while (0)

@@ -87,9 +87,44 @@ struct MarchArgs {
     DevStats* st;
 };
 
+// One solve of a batch, as the batch kernel sees it.
+struct BatchSolve {
+    const void* kap;         // float or double kappa of this solve
+    double* gamma;
+    DevStats* st;
+    int n;
+    int level_max;
+    int overlap_mode;
+    int hash;
+    long long rq;
+    double tau_max;
+    uint32_t src_off;        // index of this solve's first source in the batch catalog
+    uint32_t pad_;
+};
+
+template <class R>
+struct BatchArgs {
+    const BatchSolve* solves;
+    const SrcEntry* src;             // the launch's emitted sources; SrcEntry::pad = solve index
+    long long nsrc;
+    unsigned src_base;               // batch-catalog index of src[0]
+    const int4* dirs;                // direction table from level 0
+    int table_level;
+    RayBuf<R> buf[RT_MAX_LEVELS + 1];  // parents of level l live in buf[l]
+    long long slice;                 // children per slice (<= every buffer's capacity)
+    int tile;                        // children per claimed tile (multiple of 32)
+    unsigned long long* counts;      // per slice: next-level records written (zeroed)
+    unsigned long long* tiles;       // per slice: tiles claimed (zeroed)
+    int max_slices;
+    unsigned* err;
+};
+
 // march.cu
 int launch_march_f64(const MarchArgs<double>& a, int grid, int block, cudaStream_t s);
 int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_t s);
+cudaError_t launch_batch_f64(const BatchArgs<double>& a, int grid, int block, cudaStream_t s);
+cudaError_t launch_batch_f32(const BatchArgs<float>& a, int grid, int block, cudaStream_t s);
+int batch_blocks_per_sm(int precision, int block);
 
 // fields.cu
 int launch_validate_fields(const double* nh, const double* x, int64_t ncell, DevStats* st, cudaStream_t s);
