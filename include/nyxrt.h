@@ -43,7 +43,8 @@ enum {
     RT_ECUDA = -3,     /* a CUDA runtime call failed */
     RT_EDEVICE = -4,   /* a kernel reported an internal error (e.g. buffer overflow) */
     RT_ETIMEOUT = -5,  /* a bounded device wait gave up */
-    RT_ESTATE = -6     /* call not valid in the handle's state (missing fields, sticky error) */
+    RT_ESTATE = -6,    /* call not valid in the handle's state (missing fields, sticky error) */
+    RT_EPENDING = -7   /* a served request has not finished yet */
 };
 enum { RT_FP64 = 0, RT_FP32 = 1 };
 enum { RT_HOST = 0, RT_DEVICE = 1 };
@@ -237,6 +238,67 @@ int rt_batch_destroy(rt_batch* b);
 
 /* Text of the batch's last error. */
 const char* rt_batch_last_error(const rt_batch* b);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop with admission by device memory and continuous
+ * batching. Requests (one solve each: configuration, fields, sources) are
+ * submitted as they arrive. A loader thread admits them in arrival order while
+ * their device bytes fit the budget and loads them (handle, fields, sources,
+ * source stage) while the GPU traces the previous batch; a worker thread forms
+ * a batch from every loaded request (up to max_batch) and traces it in one
+ * persistent launch (the batched form above), so requests that arrive while
+ * a batch runs join the next one. Results go to the caller's host buffers and
+ * the request's device memory is released.
+ */
+typedef struct rt_server rt_server;
+
+typedef struct rt_server_config {
+    int32_t precision;      /* RT_FP32 or RT_FP64; every request must match */
+    int32_t max_batch;      /* requests per batch launch */
+    int64_t hbm_budget;     /* device bytes admitted requests may hold; 0: free memory at creation
+                               minus the batch workspace and a 4 GB margin */
+    int64_t slice;          /* batch kernel slice (rt_batch_params.slice) */
+    int64_t group_bytes;    /* batch group budget (rt_batch_params.group_bytes) */
+} rt_server_config;
+
+typedef struct rt_server_stats {
+    int64_t submitted, completed, failed, batches;
+    int64_t queued;         /* submitted, not yet traced */
+    int64_t mem_budget, mem_in_use, mem_peak;   /* admitted-request device bytes */
+    int64_t segments;       /* ray-cell segments of completed requests */
+    double busy_ms;         /* GPU time of all batches */
+    double elapsed_ms;      /* since rt_server_create */
+    double p50_ms, p99_ms, mean_ms, max_ms;     /* latency submit -> done, completed requests */
+} rt_server_stats;
+
+/* Defaults: FP32, max_batch 64, hbm_budget 0, slice 2^23, group 48 MB. */
+void rt_server_config_default(rt_server_config* cfg);
+
+/* Start a server on the current device (two host threads). */
+int rt_server_create(const rt_server_config* cfg, rt_server** out);
+
+/* Submit one solve: `cfg` as for rt_create (chem_iterate 0, the server's
+ * precision); n_H and x_ion (n^3), cell_ijk (nsrc x 3) and ndot (nsrc) are
+ * HOST arrays that must stay valid until the request finishes; gamma_out and
+ * heat_out (n^3 float64 host buffers, either may be NULL) receive the result.
+ * Returns RT_ENOMEM at once if the request alone exceeds the budget. */
+int rt_server_submit(rt_server* s, const rt_config* cfg, const double* n_H, const double* x_ion,
+                     const int32_t* cell_ijk, const double* ndot, int64_t nsrc, double* gamma_out,
+                     double* heat_out, int64_t* id_out);
+
+/* Wait up to wait_s seconds for request `id`. On completion returns its status
+ * (RT_OK or the error), fills `st` and `latency_ms` (either may be NULL) and
+ * forgets the request; returns RT_EPENDING if it has not finished. */
+int rt_server_poll(rt_server* s, int64_t id, double wait_s, rt_stats* st, double* latency_ms);
+
+/* Counters and latency percentiles so far. */
+int rt_server_stats_get(rt_server* s, rt_server_stats* out);
+
+/* Stop the threads and free everything (unfinished requests are dropped). */
+int rt_server_destroy(rt_server* s);
+
+/* Text of the server's last error. */
+const char* rt_server_last_error(const rt_server* s);
 
 /* rt_step without any memory allocation, for small grids. There is no
  * counterpart in the paper: it exists for callers that may not allocate

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libnyxrt.so")
 
 RT_MAX_LEVELS = 16
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_EDEVICE, RT_ETIMEOUT, RT_ESTATE = 0, -1, -2, -3, -4, -5, -6
+RT_EPENDING = -7
 RT_FP64, RT_FP32 = 0, 1
 RT_HOST, RT_DEVICE = 0, 1
 RT_OVERLAP_NONE, RT_OVERLAP_LINEAR, RT_OVERLAP_ARC, RT_OVERLAP_CONSERVATIVE, RT_OVERLAP_SQUARED = 0, 1, 2, 3, 4
@@ -29,7 +30,7 @@ RT_MERGE_OFF, RT_MERGE_FORCED, RT_MERGE_AUTO = 0, 1, 2
 RT_FLAG_VISIT_HASH = 1
 
 _ERRNAMES = {RT_EINVAL: "RT_EINVAL", RT_ENOMEM: "RT_ENOMEM", RT_ECUDA: "RT_ECUDA", RT_EDEVICE: "RT_EDEVICE",
-             RT_ETIMEOUT: "RT_ETIMEOUT", RT_ESTATE: "RT_ESTATE"}
+             RT_ETIMEOUT: "RT_ETIMEOUT", RT_ESTATE: "RT_ESTATE", RT_EPENDING: "RT_EPENDING"}
 
 
 class rt_config(C.Structure):
@@ -64,6 +65,17 @@ class rt_stats(C.Structure):
 class rt_batch_params(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("tile", C.c_int32), ("pad_", C.c_int32),
                 ("slice", C.c_int64), ("group_bytes", C.c_int64)]
+
+
+class rt_server_config(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_batch", C.c_int32), ("hbm_budget", C.c_int64),
+                ("slice", C.c_int64), ("group_bytes", C.c_int64)]
+
+
+class rt_server_stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("submitted", "completed", "failed", "batches", "queued", "mem_budget",
+                                         "mem_in_use", "mem_peak", "segments")] + \
+               [(k, C.c_double) for k in ("busy_ms", "elapsed_ms", "p50_ms", "p99_ms", "mean_ms", "max_ms")]
 
 
 class NyxError(RuntimeError):
@@ -105,9 +117,19 @@ def lib():
         L.rt_batch_destroy.argtypes = [P]
         L.rt_batch_last_error.argtypes = [P]
         L.rt_batch_last_error.restype = C.c_char_p
+        L.rt_server_config_default.argtypes = [C.POINTER(rt_server_config)]
+        L.rt_server_config_default.restype = None
+        L.rt_server_create.argtypes = [C.POINTER(rt_server_config), C.POINTER(P)]
+        L.rt_server_submit.argtypes = [P, C.POINTER(rt_config), P, P, P, P, i64, P, P, C.POINTER(i64)]
+        L.rt_server_poll.argtypes = [P, i64, d, C.POINTER(rt_stats), C.POINTER(d)]
+        L.rt_server_stats_get.argtypes = [P, C.POINTER(rt_server_stats)]
+        L.rt_server_destroy.argtypes = [P]
+        L.rt_server_last_error.argtypes = [P]
+        L.rt_server_last_error.restype = C.c_char_p
         for f in ("rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_step", "rt_get_x",
                   "rt_destroy", "rt_batch_create", "rt_batch_set_params", "rt_batch_get_params", "rt_batch_tune",
-                  "rt_batch_capture", "rt_batch_run", "rt_batch_destroy"):
+                  "rt_batch_capture", "rt_batch_run", "rt_batch_destroy", "rt_server_create", "rt_server_submit",
+                  "rt_server_poll", "rt_server_stats_get", "rt_server_destroy"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -117,7 +139,8 @@ def exported_symbols():
     return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_step",
             "rt_get_x", "rt_destroy", "rt_last_error", "rt_version", "rt_batch_create", "rt_batch_set_params",
             "rt_batch_get_params", "rt_batch_tune", "rt_batch_capture", "rt_batch_run", "rt_batch_destroy",
-            "rt_batch_last_error", "rt_step_noalloc"]
+            "rt_batch_last_error", "rt_server_config_default", "rt_server_create", "rt_server_submit",
+            "rt_server_poll", "rt_server_stats_get", "rt_server_destroy", "rt_server_last_error", "rt_step_noalloc"]
 
 
 def _check(rc: int, h=None):
@@ -367,6 +390,76 @@ class Batch:
         if self.b:
             rt_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (rt_server_*). Inputs are host numpy
+    arrays kept alive here until their request is polled."""
+
+    def __init__(self, precision: int = RT_FP32, max_batch: int = 64, hbm_budget: int = 0,
+                 slice: int | None = None, group_bytes: int | None = None):
+        c = rt_server_config()
+        lib().rt_server_config_default(C.byref(c))
+        c.precision = precision
+        c.max_batch = max_batch
+        c.hbm_budget = hbm_budget
+        if slice is not None:
+            c.slice = slice
+        if group_bytes is not None:
+            c.group_bytes = group_bytes
+        h = C.c_void_p()
+        rc = lib().rt_server_create(C.byref(c), C.byref(h))
+        if rc != RT_OK:
+            raise NyxError(rc, "server creation failed")
+        self.s = h.value
+        self.precision = precision
+        self._live = {}
+
+    def submit(self, n: int, box_cm: float, n_h, x_ion, cells, ndot, gamma=None, heat=None, **cfg) -> int:
+        cfg.setdefault("precision", self.precision)
+        c = rt_config_default(n, box_cm, **cfg)
+        arrs = [np.ascontiguousarray(n_h, dtype=np.float64), np.ascontiguousarray(x_ion, dtype=np.float64),
+                np.ascontiguousarray(cells, dtype=np.int32), np.ascontiguousarray(ndot, dtype=np.float64)]
+        if gamma is None:
+            gamma = np.empty(n ** 3)
+        if heat is None:
+            heat = np.empty(n ** 3)
+        rid = C.c_int64()
+        rc = lib().rt_server_submit(self.s, C.byref(c), *[a.ctypes.data_as(C.c_void_p) for a in arrs], len(arrs[3]),
+                                    gamma.ctypes.data_as(C.c_void_p), heat.ctypes.data_as(C.c_void_p), C.byref(rid))
+        if rc != RT_OK:
+            raise NyxError(rc, lib().rt_server_last_error(self.s).decode(errors="replace"))
+        self._live[rid.value] = (arrs, gamma, heat)
+        return rid.value
+
+    def poll(self, rid: int, wait_s: float = 0.0):
+        """None if the request is still running, else (gamma, heat, stats, latency_ms)."""
+        st = rt_stats()
+        lat = C.c_double()
+        rc = lib().rt_server_poll(self.s, rid, float(wait_s), C.byref(st), C.byref(lat))
+        if rc == RT_EPENDING:
+            return None
+        _, gamma, heat = self._live.pop(rid)
+        if rc != RT_OK:
+            raise NyxError(rc, lib().rt_server_last_error(self.s).decode(errors="replace"))
+        return gamma, heat, stats_dict(st), lat.value
+
+    def stats(self) -> dict:
+        st = rt_server_stats()
+        lib().rt_server_stats_get(self.s, C.byref(st))
+        return {k: getattr(st, k) for k, _ in rt_server_stats._fields_}
+
+    def close(self):
+        if self.s:
+            lib().rt_server_destroy(self.s)
+            self.s = None
+            self._live.clear()
 
     def __del__(self):
         try:

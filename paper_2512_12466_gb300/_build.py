@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libnyxrt.so")
 BUILD = os.path.join(ROOT, "_build", "nyxrt")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["march.cu", "fields.cu", "sources.cu", "rt_api.cu", "batch.cu", "noalloc.cu"]
+CUDA_SOURCES = ["march.cu", "fields.cu", "sources.cu", "rt_api.cu", "batch.cu", "server.cu", "noalloc.cu"]
 CXX_SOURCES = ["directions.cpp"]
 
 

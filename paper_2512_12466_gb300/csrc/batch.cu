@@ -46,6 +46,8 @@ struct rt_batch {
     std::vector<double> n_th, emitted;
     std::vector<int64_t> n_src_in, n_dedup, n_emit;
     std::vector<int> merged;
+    std::vector<BatchSolve> hsolve;
+    int64_t cap_src = 0, cap_solves = 0;
     int table_level = 0;
     const int4* dirs = nullptr;
     BatchSolve* d_solves = nullptr;
@@ -261,6 +263,161 @@ int apply_params(rt_batch* b, const rt_batch_params& p)
 
 }  // namespace
 
+void nyx::batch_fill_stats(const rt_batch* b, size_t i, float ms, rt_stats* st)
+{
+    std::memset(st, 0, sizeof(*st));
+    const DevStats& d = b->h_stats[i];
+    st->n_src_in = b->n_src_in[i];
+    st->n_src_dedup = b->n_dedup[i];
+    st->n_src_emit = b->n_emit[i];
+    st->merged = b->merged[i];
+    st->chem_iters = 1;
+    st->level_max = b->hs[i]->level_max;
+    st->launches = b->launches;
+    for (int l = 0; l < RT_MAX_LEVELS; ++l) {
+        st->rays[l] = (int64_t)d.rays[l];
+        st->splits[l] = (int64_t)d.splits[l];
+        st->escaped[l] = (int64_t)d.escaped[l];
+        st->dropped_tau[l] = (int64_t)d.dropped_tau[l];
+        st->dropped_level[l] = (int64_t)d.dropped_level[l];
+        st->segments[l] = (int64_t)d.segments[l];
+        st->secondary[l] = (int64_t)d.secondary[l];
+    }
+    st->visit_hash = d.visit_hash;
+    st->emitted_ph = b->emitted[i];
+    st->absorbed_ph = d.absorbed;
+    st->escaped_ph = d.escaped_ph;
+    st->dropped_ph = d.dropped_ph;
+    st->deposited_ph = d.deposited;
+    st->ms_trace = ms;
+    st->ms_step = ms;
+    st->ms_march = ms;
+    st->march_launches = 1;
+}
+
+cudaStream_t nyx::batch_stream(const rt_batch* b) { return b->stream; }
+
+int nyx::batch_run_direct(rt_batch* b, float* ms) { return run_once(b, ms); }
+
+// (Re)bind a batch to a set of handles: run each handle's source stage, build
+// the tagged catalog and the solve table. Allocations are kept and grown only
+// when too small, so a long-lived batch (the server's) can be re-targeted every
+// iteration without touching the allocator in steady state.
+int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
+{
+    drop_graph(b);
+    b->hs.assign(handles, handles + count);
+    b->n_th.clear();
+    b->emitted.clear();
+    b->n_src_in.clear();
+    b->n_dedup.clear();
+    b->n_emit.clear();
+    b->merged.clear();
+    b->nsrc = 0;
+    int table_level = 0;
+    for (rt_handle* h : b->hs) {
+        if (h->device != b->device) return bfail(b, RT_EINVAL, "all handles of a batch must be on one device");
+        if (h->cfg.precision != b->precision) return bfail(b, RT_EINVAL, "all handles of a batch must share the precision");
+        if (!h->fields_set) return bfail(b, RT_ESTATE, "rt_set_fields has not been called on a handle");
+        if (h->cfg.chem_iterate) return bfail(b, RT_EINVAL, "the batched form traces at fixed x (chem_iterate must be 0)");
+        if (h->sticky) return bfail(b, RT_ESTATE, "a handle is in an error state");
+    }
+    DeviceGuard g(b->device);
+    // ---- each solve's source stage (Sec. 2.8), unless a loader ran it ahead
+    for (rt_handle* h : b->hs) {
+        if (!h->src_ready) {
+            const int rc = handle_prepare_sources(h);
+            if (rc) return bfail(b, rc, std::string("source stage: ") + h->err);
+        }
+        h->src_ready = false;
+        b->n_th.push_back(h->src_nth);
+        b->emitted.push_back(h->src_emitted);
+        b->n_src_in.push_back(h->nsrc);
+        b->n_dedup.push_back(h->src_dedup);
+        b->n_emit.push_back(h->n_emit);
+        b->merged.push_back(h->src_merged ? 1 : 0);
+        table_level = std::max(table_level, h->table_level);
+        b->nsrc += h->n_emit;
+    }
+    {   // the device's direction table, grown to the deepest level any solve reaches
+        std::string why;
+        const int rc = ensure_directions(b->device, table_level, &b->dirs, why);
+        if (rc) return bfail(b, rc, why);
+    }
+    if (!b->stream) {
+        B_CUDA(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "stream");
+        B_CUDA(b, cudaEventCreate(&b->ev0), "event");
+        B_CUDA(b, cudaEventCreate(&b->ev1), "event");
+        B_CUDA(b, cudaMalloc(&b->d_counts, sizeof(unsigned long long) * kMaxSlices), "counters");
+        B_CUDA(b, cudaMalloc(&b->d_tiles, sizeof(unsigned long long) * kMaxSlices), "counters");
+        B_CUDA(b, cudaMalloc(&b->d_err, sizeof(unsigned)), "error word");
+        B_CUDA(b, cudaMallocHost(&b->h_err, sizeof(unsigned)), "error word");
+        *b->h_err = 0;
+    }
+    // ---- all solves' emitted sources in one catalog, tagged with their solve index
+    if (b->nsrc > b->cap_src || !b->d_src) {
+        B_CUDA(b, cudaStreamSynchronize(b->stream), "batch stream");
+        cudaFree(b->d_src);
+        b->d_src = nullptr;
+        b->cap_src = std::max<int64_t>(b->nsrc, 1024);
+        B_CUDA(b, cudaMalloc(&b->d_src, sizeof(SrcEntry) * (size_t)b->cap_src), "catalog");
+    }
+    int64_t off = 0;
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        const int64_t m = b->n_emit[i];
+        if (m > 0) {
+            const int grid = (int)std::min<int64_t>((m + 255) / 256, 1024);
+            tag_sources_kernel<<<grid, 256, 0, b->stream>>>(b->hs[i]->d_emit, m, (int32_t)i, b->d_src + off);
+            B_CUDA(b, cudaGetLastError(), "catalog launch");
+        }
+        off += m;
+    }
+    // ---- solve table and per-solve statistics
+    const int64_t ns = (int64_t)b->hs.size();
+    if (ns > b->cap_solves) {
+        B_CUDA(b, cudaStreamSynchronize(b->stream), "batch stream");
+        cudaFree(b->d_stats);
+        cudaFreeHost(b->h_stats);
+        cudaFree(b->d_solves);
+        b->d_stats = nullptr;
+        b->h_stats = nullptr;
+        b->d_solves = nullptr;
+        b->cap_solves = std::max<int64_t>(ns, 64);
+        B_CUDA(b, cudaMalloc(&b->d_stats, sizeof(DevStats) * (size_t)b->cap_solves), "stats");
+        B_CUDA(b, cudaMallocHost(&b->h_stats, sizeof(DevStats) * (size_t)b->cap_solves), "stats");
+        B_CUDA(b, cudaMalloc(&b->d_solves, sizeof(BatchSolve) * (size_t)b->cap_solves), "solve table");
+    }
+    b->hsolve.assign(b->hs.size(), BatchSolve{});
+    int64_t first = 0;
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        rt_handle* h = b->hs[i];
+        BatchSolve& s = b->hsolve[i];
+        s.kap = h->d_kap;
+        s.gamma = h->d_gamma;
+        s.st = b->d_stats + i;
+        s.n = h->cfg.n;
+        s.level_max = h->level_max;
+        s.overlap_mode = h->cfg.overlap_mode;
+        s.hash = (h->cfg.flags & RT_FLAG_VISIT_HASH) ? 1 : 0;
+        s.rq = h->rq;
+        s.tau_max = h->cfg.tau_max;
+        s.src_off = (uint32_t)first;
+        s.pad_ = 0;
+        first += b->n_emit[i];
+    }
+    B_CUDA(b, cudaMemcpyAsync(b->d_solves, b->hsolve.data(), sizeof(BatchSolve) * b->hsolve.size(),
+                              cudaMemcpyHostToDevice, b->stream), "solve table");
+    B_CUDA(b, cudaStreamSynchronize(b->stream), "batch setup");
+    if (table_level > b->table_level || !b->rays[1].base) {
+        b->table_level = std::max(b->table_level, table_level);
+        if (b->params.slice > 0) {
+            const int rc = alloc_rays(b, b->params.slice);
+            if (rc) return rc;
+        }
+    }
+    return RT_OK;
+}
+
 extern "C" {
 
 const char* rt_batch_last_error(const rt_batch* b) { return b ? b->err.c_str() : ""; }
@@ -293,93 +450,15 @@ int rt_batch_create(rt_handle* const* handles, int32_t count, void* cuda_stream,
     (void)cuda_stream;
     if (!out || !handles || count < 1) return RT_EINVAL;
     *out = nullptr;
+    for (int32_t i = 0; i < count; ++i)
+        if (!handles[i]) return RT_EINVAL;
     rt_batch* b = new rt_batch();
-    b->hs.assign(handles, handles + count);
-    for (rt_handle* h : b->hs) {
-        if (!h) { rt_batch_destroy(b); return RT_EINVAL; }
-    }
-    rt_handle* h0 = b->hs[0];
-    b->precision = h0->cfg.precision;
-    b->device = h0->device;
-    b->sm_count = h0->sm_count;
+    b->precision = handles[0]->cfg.precision;
+    b->device = handles[0]->device;
+    b->sm_count = handles[0]->sm_count;
     *out = b;
-    for (rt_handle* h : b->hs) {
-        if (h->device != b->device) return bfail(b, RT_EINVAL, "all handles of a batch must be on one device");
-        if (h->cfg.precision != b->precision) return bfail(b, RT_EINVAL, "all handles of a batch must share the precision");
-        if (!h->fields_set) return bfail(b, RT_ESTATE, "rt_set_fields has not been called on a handle");
-        if (h->cfg.chem_iterate) return bfail(b, RT_EINVAL, "the batched form traces at fixed x (chem_iterate must be 0)");
-        if (h->sticky) return bfail(b, RT_ESTATE, "a handle is in an error state");
-    }
-    DeviceGuard g(b->device);
-    // ---- each solve's source stage (Sec. 2.8) on its own stream
-    for (rt_handle* h : b->hs) {
-        h->launches = 0;
-        RT_CUDA(h, cudaMemsetAsync(h->d_st, 0, sizeof(DevStats), h->stream), "stats clear");
-        bool merged = false;
-        int64_t nd = 0;
-        const int rc = prepare_sources(h, &merged, &nd);
-        if (rc) return bfail(b, rc, std::string("source stage: ") + h->err);
-        RT_CUDA(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream), "stats");
-        RT_CUDA(h, cudaStreamSynchronize(h->stream), "source stage");
-        b->n_th.push_back(h->cfg.n_th_cm3 >= 0 ? h->cfg.n_th_cm3 : 0.01 * h->h_f64[1]);
-        b->emitted.push_back(h->h_st->emitted);
-        b->n_src_in.push_back(h->nsrc);
-        b->n_dedup.push_back(nd);
-        b->n_emit.push_back(h->n_emit);
-        b->merged.push_back(merged ? 1 : 0);
-        b->table_level = std::max(b->table_level, h->table_level);
-        b->nsrc += h->n_emit;
-    }
-    {   // the device's direction table, grown to the deepest level any solve reaches
-        std::string why;
-        const int rc = ensure_directions(b->device, b->table_level, &b->dirs, why);
-        if (rc) return bfail(b, rc, why);
-    }
-    B_CUDA(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "stream");
-    B_CUDA(b, cudaEventCreate(&b->ev0), "event");
-    B_CUDA(b, cudaEventCreate(&b->ev1), "event");
-    // ---- all solves' emitted sources in one catalog, tagged with their solve index
-    B_CUDA(b, cudaMalloc(&b->d_src, sizeof(SrcEntry) * (size_t)std::max<int64_t>(1, b->nsrc)), "catalog");
-    int64_t off = 0;
-    for (size_t i = 0; i < b->hs.size(); ++i) {
-        const int64_t m = b->n_emit[i];
-        if (m > 0) {
-            const int grid = (int)std::min<int64_t>((m + 255) / 256, 1024);
-            tag_sources_kernel<<<grid, 256, 0, b->stream>>>(b->hs[i]->d_emit, m, (int32_t)i, b->d_src + off);
-            B_CUDA(b, cudaGetLastError(), "catalog launch");
-        }
-        off += m;
-    }
-    // ---- solve table and per-solve statistics
-    B_CUDA(b, cudaMalloc(&b->d_stats, sizeof(DevStats) * b->hs.size()), "stats");
-    B_CUDA(b, cudaMallocHost(&b->h_stats, sizeof(DevStats) * b->hs.size()), "stats");
-    std::vector<BatchSolve> hsolve(b->hs.size());
-    int64_t first = 0;
-    for (size_t i = 0; i < b->hs.size(); ++i) {
-        rt_handle* h = b->hs[i];
-        BatchSolve& s = hsolve[i];
-        s.kap = h->d_kap;
-        s.gamma = h->d_gamma;
-        s.st = b->d_stats + i;
-        s.n = h->cfg.n;
-        s.level_max = h->level_max;
-        s.overlap_mode = h->cfg.overlap_mode;
-        s.hash = (h->cfg.flags & RT_FLAG_VISIT_HASH) ? 1 : 0;
-        s.rq = h->rq;
-        s.tau_max = h->cfg.tau_max;
-        s.src_off = (uint32_t)first;
-        s.pad_ = 0;
-        first += b->n_emit[i];
-    }
-    B_CUDA(b, cudaMalloc(&b->d_solves, sizeof(BatchSolve) * hsolve.size()), "solve table");
-    B_CUDA(b, cudaMemcpyAsync(b->d_solves, hsolve.data(), sizeof(BatchSolve) * hsolve.size(), cudaMemcpyHostToDevice,
-                              b->stream), "solve table");
-    B_CUDA(b, cudaMalloc(&b->d_counts, sizeof(unsigned long long) * kMaxSlices), "counters");
-    B_CUDA(b, cudaMalloc(&b->d_tiles, sizeof(unsigned long long) * kMaxSlices), "counters");
-    B_CUDA(b, cudaMalloc(&b->d_err, sizeof(unsigned)), "error word");
-    B_CUDA(b, cudaMallocHost(&b->h_err, sizeof(unsigned)), "error word");
-    *b->h_err = 0;
-    B_CUDA(b, cudaStreamSynchronize(b->stream), "batch setup");
+    int rc = batch_bind(b, handles, count);
+    if (rc) return rc;
     rt_batch_params p{};
     p.block = 256;
     p.blocks_per_sm = std::max(1, std::min(2, max_blocks_per_sm(b, 256)));
@@ -387,9 +466,7 @@ int rt_batch_create(rt_handle* const* handles, int32_t count, void* cuda_stream,
     p.slice = int64_t(1) << 22;
     p.group_bytes = int64_t(48) << 20;
     b->params.slice = 0;
-    const int rc = apply_params(b, p);
-    if (rc) return rc;
-    return RT_OK;
+    return apply_params(b, p);
 }
 
 int rt_batch_set_params(rt_batch* b, const rt_batch_params* p)
@@ -486,39 +563,8 @@ int rt_batch_run(rt_batch* b, double* const* gamma_out, double* const* heat_out,
         if (heat_out && heat_out[i]) B_CUDA(b, cudaMemcpyAsync(heat_out[i], h->d_heat, fb, k, b->stream), "heat copy");
     }
     B_CUDA(b, cudaStreamSynchronize(b->stream), "output copy");
-    if (stats) {
-        for (size_t i = 0; i < b->hs.size(); ++i) {
-            rt_stats* st = stats + i;
-            std::memset(st, 0, sizeof(*st));
-            const DevStats& d = b->h_stats[i];
-            st->n_src_in = b->n_src_in[i];
-            st->n_src_dedup = b->n_dedup[i];
-            st->n_src_emit = b->n_emit[i];
-            st->merged = b->merged[i];
-            st->chem_iters = 1;
-            st->level_max = b->hs[i]->level_max;
-            st->launches = b->launches;
-            for (int l = 0; l < RT_MAX_LEVELS; ++l) {
-                st->rays[l] = (int64_t)d.rays[l];
-                st->splits[l] = (int64_t)d.splits[l];
-                st->escaped[l] = (int64_t)d.escaped[l];
-                st->dropped_tau[l] = (int64_t)d.dropped_tau[l];
-                st->dropped_level[l] = (int64_t)d.dropped_level[l];
-                st->segments[l] = (int64_t)d.segments[l];
-                st->secondary[l] = (int64_t)d.secondary[l];
-            }
-            st->visit_hash = d.visit_hash;
-            st->emitted_ph = b->emitted[i];
-            st->absorbed_ph = d.absorbed;
-            st->escaped_ph = d.escaped_ph;
-            st->dropped_ph = d.dropped_ph;
-            st->deposited_ph = d.deposited;
-            st->ms_trace = ms;
-            st->ms_step = ms;
-            st->ms_march = ms;
-            st->march_launches = 1;
-        }
-    }
+    if (stats)
+        for (size_t i = 0; i < b->hs.size(); ++i) batch_fill_stats(b, i, ms, stats + i);
     return RT_OK;
 }
 

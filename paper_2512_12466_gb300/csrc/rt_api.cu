@@ -81,6 +81,14 @@ int nyx::ensure_directions(int device, int level, const int4** out, std::string&
 
 namespace nyx {
 
+// Handle memory is stream-ordered: allocating or freeing it never waits for
+// work on other streams (a server creates and frees handles while batches run).
+cudaError_t dalloc(rt_handle* h, void** p, size_t bytes) { return cudaMallocAsync(p, bytes, h->stream); }
+void dfree(rt_handle* h, void* p)
+{
+    if (p) cudaFreeAsync(p, h->stream);
+}
+
 int fail(rt_handle* h, int code, const std::string& msg)
 {
     h->err = msg;
@@ -101,7 +109,7 @@ int grow_sources(rt_handle* h, int64_t need)
     int64_t cap = std::max<int64_t>(need, std::max<int64_t>(1024, 2 * h->sw.cap));
     SourceWork nw;
     nw.cap = cap;
-    auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes); };
+    auto alloc = [&](void** p, size_t bytes) { return dalloc(h, p, bytes); };
     cudaError_t e = cudaSuccess;
     e = e ? e : alloc((void**)&nw.cells_raw, 12 * (size_t)cap);
     e = e ? e : alloc((void**)&nw.ndot_raw, 8 * (size_t)cap);
@@ -119,14 +127,14 @@ int grow_sources(rt_handle* h, int64_t need)
     e = e ? e : alloc((void**)&nw.count, 16);
     SrcEntry* emit = nullptr;
     e = e ? e : alloc((void**)&emit, sizeof(SrcEntry) * (size_t)cap);
-    auto release = [](SourceWork& w) {
-        cudaFree(w.cells_raw); cudaFree(w.ndot_raw); cudaFree(w.keys); cudaFree(w.order); cudaFree(w.flag);
-        cudaFree(w.head_pos); cudaFree(w.cells_a); cudaFree(w.ndot_a); cudaFree(w.cells_b); cudaFree(w.ndot_b);
-        cudaFree(w.label); cudaFree(w.parent); cudaFree(w.radius); cudaFree(w.count);
+    auto release = [h](SourceWork& w) {
+        void* ps[] = {w.cells_raw, w.ndot_raw, w.keys, w.order, w.flag, w.head_pos, w.cells_a, w.ndot_a,
+                      w.cells_b, w.ndot_b, w.label, w.parent, w.radius, w.count};
+        for (void* q : ps) dfree(h, q);
     };
     if (e != cudaSuccess) {
         release(nw);
-        cudaFree(emit);
+        dfree(h, emit);
         return cuda_fail(h, e, "source buffers");
     }
     if (h->nsrc > 0) {
@@ -135,9 +143,8 @@ int grow_sources(rt_handle* h, int64_t need)
         RT_CUDA(h, cudaMemcpyAsync(nw.ndot_raw, h->sw.ndot_raw, 8 * (size_t)h->nsrc, cudaMemcpyDeviceToDevice, h->stream),
                 "source copy");
     }
-    RT_CUDA(h, cudaStreamSynchronize(h->stream), "source copy");
     release(h->sw);
-    cudaFree(h->d_emit);
+    dfree(h, h->d_emit);
     h->sw = nw;
     h->d_emit = emit;
     return RT_OK;
@@ -149,12 +156,11 @@ int ensure_rays(rt_handle* h, int level, int64_t need)
     RayStore& s = h->rays[level];
     if (s.cap >= need) return RT_OK;
     int64_t cap = std::max<int64_t>(need, std::min<int64_t>(kMaxChildrenPerLaunch, std::max<int64_t>(4096, 2 * s.cap)));
-    RT_CUDA(h, cudaStreamSynchronize(h->stream), "ray buffer");
-    cudaFree(s.base);
+    dfree(h, s.base);
     s.base = nullptr;
     s.cap = 0;
     void* p = nullptr;
-    RT_CUDA(h, cudaMalloc(&p, ray_bytes(cap, (int)sizeof(R))), "ray buffer");
+    RT_CUDA(h, dalloc(h, &p, ray_bytes(cap, (int)sizeof(R))), "ray buffer");
     s.base = p;
     s.cap = cap;
     return RT_OK;
@@ -303,6 +309,26 @@ int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out)
     return RT_OK;
 }
 
+// Run the source stage ahead of a batch (a server's loader does this while the
+// GPU traces the previous batch); batch_bind then uses the recorded results.
+int handle_prepare_sources(rt_handle* h)
+{
+    h->launches = 0;
+    RT_CUDA(h, cudaMemsetAsync(h->d_st, 0, sizeof(DevStats), h->stream), "stats clear");
+    bool merged = false;
+    int64_t nd = 0;
+    const int rc = prepare_sources(h, &merged, &nd);
+    if (rc) return rc;
+    RT_CUDA(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream), "stats");
+    RT_CUDA(h, cudaStreamSynchronize(h->stream), "source stage");
+    h->src_ready = true;
+    h->src_merged = merged;
+    h->src_dedup = nd;
+    h->src_nth = h->cfg.n_th_cm3 >= 0 ? h->cfg.n_th_cm3 : 0.01 * h->h_f64[1];
+    h->src_emitted = h->h_st->emitted;
+    return RT_OK;
+}
+
 bool valid_config(const rt_config* c, std::string& why)
 {
     if (c->n < 1 || c->n > 1024) { why = "n must be in 1..1024"; return false; }
@@ -364,20 +390,20 @@ int rt_destroy(rt_handle* h)
     if (!h) return RT_OK;
     DeviceGuard g(h->device);
     cudaStreamSynchronize(h->stream);
-    cudaFree(h->d_nh); cudaFree(h->d_x); cudaFree(h->d_xavg); cudaFree(h->d_xend);
-    cudaFree(h->d_gamma); cudaFree(h->d_heat); cudaFree(h->d_kap); cudaFree(h->d_scalar);
-    SourceWork& w = h->sw;
-    cudaFree(w.cells_raw); cudaFree(w.ndot_raw); cudaFree(w.keys); cudaFree(w.order); cudaFree(w.flag);
-    cudaFree(w.head_pos); cudaFree(w.cells_a); cudaFree(w.ndot_a); cudaFree(w.cells_b); cudaFree(w.ndot_b);
-    cudaFree(w.label); cudaFree(w.parent); cudaFree(w.radius); cudaFree(w.count);
-    cudaFree(h->d_emit);
-    for (auto& r : h->rays) cudaFree(r.base);
-    cudaFree(h->d_count);
-    cudaFree(h->d_st);
-    cudaFreeHost(h->h_st);
-    cudaFreeHost(h->h_count);
-    cudaFreeHost(h->h_i32);
-    cudaFreeHost(h->h_f64);
+    {
+        void* ps[] = {h->d_nh, h->d_x, h->d_xavg, h->d_xend, h->d_gamma, h->d_heat, h->d_kap, h->d_scalar,
+                      h->d_emit, h->d_count, h->d_st};
+        for (void* q : ps) dfree(h, q);
+        SourceWork& w = h->sw;
+        void* ws[] = {w.cells_raw, w.ndot_raw, w.keys, w.order, w.flag, w.head_pos, w.cells_a, w.ndot_a,
+                      w.cells_b, w.ndot_b, w.label, w.parent, w.radius, w.count};
+        for (void* q : ws) dfree(h, q);
+        for (auto& r : h->rays) dfree(h, r.base);
+    }
+    delete[] h->h_st;
+    delete[] h->h_count;
+    delete[] h->h_i32;
+    delete[] h->h_f64;
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
     cudaGetLastError();
     delete h;
@@ -418,23 +444,25 @@ int rt_create(const rt_config* cfg, void* cuda_stream, rt_handle** out)
 
     cudaError_t e = cudaSuccess;
     const size_t fb = sizeof(double) * (size_t)h->ncell;
-    e = e ? e : cudaMalloc(&h->d_nh, fb);
-    e = e ? e : cudaMalloc(&h->d_x, fb);
-    e = e ? e : cudaMalloc(&h->d_gamma, fb);
-    e = e ? e : cudaMalloc(&h->d_heat, fb);
-    e = e ? e : cudaMalloc(&h->d_kap, cfg->precision == RT_FP32 ? fb / 2 : fb);
+    e = e ? e : dalloc(h, (void**)&h->d_nh, fb);
+    e = e ? e : dalloc(h, (void**)&h->d_x, fb);
+    e = e ? e : dalloc(h, (void**)&h->d_gamma, fb);
+    e = e ? e : dalloc(h, (void**)&h->d_heat, fb);
+    e = e ? e : dalloc(h, &h->d_kap, cfg->precision == RT_FP32 ? fb / 2 : fb);
     if (cfg->chem_iterate) {
-        e = e ? e : cudaMalloc(&h->d_xavg, fb);
-        e = e ? e : cudaMalloc(&h->d_xend, fb);
+        e = e ? e : dalloc(h, (void**)&h->d_xavg, fb);
+        e = e ? e : dalloc(h, (void**)&h->d_xend, fb);
     }
-    e = e ? e : cudaMalloc(&h->d_scalar, 64);
-    e = e ? e : cudaMalloc(&h->d_count, sizeof(unsigned long long) * (RT_MAX_LEVELS + 1));
-    e = e ? e : cudaMalloc(&h->d_st, sizeof(DevStats));
-    e = e ? e : cudaMallocHost(&h->h_st, sizeof(DevStats));
-    e = e ? e : cudaMallocHost(&h->h_count, sizeof(unsigned long long) * (RT_MAX_LEVELS + 1));
-    e = e ? e : cudaMallocHost(&h->h_i32, 64);
-    e = e ? e : cudaMallocHost(&h->h_f64, 64);
+    e = e ? e : dalloc(h, (void**)&h->d_scalar, 64);
+    e = e ? e : dalloc(h, (void**)&h->d_count, sizeof(unsigned long long) * (RT_MAX_LEVELS + 1));
+    e = e ? e : dalloc(h, (void**)&h->d_st, sizeof(DevStats));
+    h->h_st = new (std::nothrow) DevStats[1];
+    h->h_count = new (std::nothrow) unsigned long long[RT_MAX_LEVELS + 1];
+    h->h_i32 = new (std::nothrow) int32_t[16];
+    h->h_f64 = new (std::nothrow) double[8];
+    if (!h->h_st || !h->h_count || !h->h_i32 || !h->h_f64) e = cudaErrorMemoryAllocation;
     for (auto& ev : h->ev) e = e ? e : cudaEventCreate(&ev);
+    e = e ? e : cudaStreamSynchronize(h->stream);   // the allocations are usable from any stream after this
     if (e != cudaSuccess) {
         cudaGetLastError();
         g_create_error = std::string("allocation failed: ") + cudaGetErrorString(e);

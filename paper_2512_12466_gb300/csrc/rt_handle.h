@@ -108,6 +108,12 @@ struct rt_handle {
     int launches = 0;
     int march_launches = 0;
     std::string err;
+    // source stage run ahead of a batch (handle_prepare_sources)
+    bool src_ready = false;
+    bool src_merged = false;
+    int64_t src_dedup = 0;
+    double src_nth = 0.0;
+    double src_emitted = 0.0;
 };
 
 namespace nyx {
@@ -116,6 +122,11 @@ int fail(rt_handle* h, int code, const std::string& msg);
 int cuda_fail(rt_handle* h, cudaError_t e, const char* what);
 int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out);
 int ensure_directions(int device, int level, const int4** out, std::string& err);
+int handle_prepare_sources(rt_handle* h);
+int batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count);
+int batch_run_direct(rt_batch* b, float* ms);
+void batch_fill_stats(const rt_batch* b, size_t i, float ms, rt_stats* st);
+cudaStream_t batch_stream(const rt_batch* b);
 
 }  // namespace nyx
 

@@ -1,0 +1,128 @@
+"""Serving loop: continuous batching with admission by device memory.
+
+Each request's result must be the same alone (rt_step on its own handle) and
+in the mix (traced in a batch with whatever else was loaded at the time):
+bookkeeping and visit hash equal, fields within 1e-10 relative L2 (only the
+order of FP64 atomic deposits differs). The admitted device bytes never exceed
+the budget, and requests submitted while batches run are served by later
+batches.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2512_12466_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BOOK = ("rays", "splits", "escaped", "dropped_tau", "dropped_level", "segments", "secondary", "visit_hash")
+
+
+@pytest.fixture(scope="module")
+def nyx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_12466_gb300 as m
+    m.lib()
+    return m
+
+
+def relerr(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def requests(count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        n = int(rng.choice([16, 24, 32, 48]))
+        k = int(rng.integers(1, 40))
+        xm = ["thin", "patchy", "mixed", "neutral"][j % 4]
+        out.append(I.random_small(n, k, seed=seed * 1000 + j, x_mode=xm, box_cm=n * [7e20, 2e22, 7e22, 1e21][j % 4]))
+    return out
+
+
+def alone(nyx, w, precision, n_th):
+    s = nyx.Solver(w.n, w.box_cm, precision=precision, n_th_cm3=n_th, flags=nyx.RT_FLAG_VISIT_HASH)
+    s.set_fields(w.n_h.ravel(), w.x_ion.ravel())
+    s.add_sources(w.cells.ravel(), w.ndot)
+    g, h, st = s.step()
+    s.close()
+    return g.ravel(), h.ravel(), st
+
+
+def check_same(nyx, got, ref):
+    g, h, st, lat = got
+    gr, hr, sr = ref
+    for k in BOOK:
+        assert st[k] == sr[k], k
+    assert relerr(g, gr) < 1e-10 and relerr(h, hr) < 1e-10
+    assert lat > 0
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_each_result_same_alone_and_in_the_mix(nyx, precision):
+    ws = requests(12, seed=3 + precision)
+    srv = nyx.Server(precision=precision, max_batch=8)
+    ids = []
+    for w in ws:
+        n_th = 0.3 * float(w.n_h.mean())
+        ids.append(srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot, n_th_cm3=n_th,
+                              flags=nyx.RT_FLAG_VISIT_HASH))
+    got = [srv.poll(i, wait_s=120.0) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(ws) and st["failed"] == 0 and st["batches"] >= 2
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    for w, r in zip(ws, got):
+        assert r is not None
+        check_same(nyx, r, alone(nyx, w, precision, 0.3 * float(w.n_h.mean())))
+
+
+def test_admission_respects_the_memory_budget(nyx):
+    ws = requests(6, seed=9)
+    budget = max(w.n ** 3 * 36 + 160 * 1024 + (1 << 16) for w in ws) * 2   # two of the largest at a time
+    srv = nyx.Server(precision=1, max_batch=64, hbm_budget=budget)
+    ids = [srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot, n_th_cm3=0.3 * float(w.n_h.mean()),
+                      flags=nyx.RT_FLAG_VISIT_HASH) for w in ws]
+    got = [srv.poll(i, wait_s=120.0) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(ws) and st["mem_peak"] <= budget and st["batches"] >= 2
+    for w, r in zip(ws, got):
+        check_same(nyx, r, alone(nyx, w, 1, 0.3 * float(w.n_h.mean())))
+
+
+def test_requests_arriving_during_batches_are_served(nyx):
+    ws = requests(16, seed=21)
+    srv = nyx.Server(precision=1, max_batch=4)
+    ids = []
+    for j, w in enumerate(ws):
+        ids.append(srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot, n_th_cm3=0.3 * float(w.n_h.mean()),
+                              flags=nyx.RT_FLAG_VISIT_HASH))
+        if j % 4 == 3:
+            time.sleep(0.02)                     # later requests arrive while earlier ones run
+    got = [srv.poll(i, wait_s=120.0) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(ws) and st["batches"] >= 4
+    for w, r in zip(ws, got):
+        check_same(nyx, r, alone(nyx, w, 1, 0.3 * float(w.n_h.mean())))
+
+
+def test_oversize_request_and_poll_states(nyx):
+    srv = nyx.Server(precision=1, hbm_budget=1 << 20)
+    w = requests(1, seed=31)[0]
+    with pytest.raises(nyx.NyxError) as e:
+        srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot)
+    assert e.value.code == nyx.RT_ENOMEM
+    srv.close()
+    srv = nyx.Server(precision=1)
+    with pytest.raises(nyx.NyxError):                  # precision must match the server's
+        srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot, precision=0)
+    rid = srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot)
+    assert srv.poll(rid, wait_s=120.0) is not None
+    srv.close()
