@@ -281,6 +281,149 @@ def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int |
             "params": {k: getattr(p_final, k) for k in ("block", "blocks_per_sm", "tile", "slice", "group_bytes")}}
 
 
+def serving_requests(n_req: int, torch):
+    """Config 5 request stream: Poisson arrivals at 200/s (seeded), grids from {64,128,256}^3
+    (constant cell size of the 128^3 / 20 Mpc/h box), source counts log-uniform on
+    [16, 32768], density per the 128^3 recipe (lognormal sigma_ln 1, mean 2e-4) and x per the
+    256^3 recipe (x = clip(v, 0, 1), v a mean-1 lognormal, sigma_ln 1.5). Fields come from a
+    pool of 2 seeded realizations per size in pinned memory; sources are drawn per request."""
+    rng = np.random.default_rng(I.seed_for(5, 5))
+    arrivals = I.poisson_arrivals(200.0, n_req, I.seed_for(5, 5))
+    pool = {}
+    for n in (64, 128, 256):
+        for r in range(2):
+            n_h = I.lognormal(n, 2e-4, 1.0, I.seed_for(5, 1, solve=10 * n + r))
+            x = np.clip(I.lognormal(n, 1.0, 1.5, I.seed_for(5, 2, solve=10 * n + r)), 0.0, 1.0)
+            flat = n_h.reshape(-1)
+            k = int(round(0.01 * flat.size))
+            top = np.sort(np.argpartition(flat, flat.size - k)[flat.size - k:])
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).pin_memory().numpy()
+            pool[(n, r)] = (pin(n_h), pin(x), top, float(n_h.mean()))
+    reqs = []
+    for j in range(n_req):
+        n = int((64, 128, 256)[rng.integers(0, 3)])
+        r = int(rng.integers(0, 2))
+        k = int(np.clip(np.floor(np.exp(rng.uniform(np.log(16), np.log(32769)))), 16, 32768))
+        n_h, x, top, mean = pool[(n, r)]
+        pick = top[rng.integers(0, len(top), size=k)]
+        cells = np.stack([pick % n, (pick // n) % n, pick // (n * n)], axis=1).astype(np.int32)
+        ndot = I.power_law_ndot(k, I.seed_for(5, 4, solve=j))
+        reqs.append(dict(t=float(arrivals[j]), n=n, box=20.0 * n / 128.0 / I.HUBBLE_H * I.MPC_CM, n_h=n_h, x=x,
+                         cells=np.ascontiguousarray(cells.ravel()), ndot=ndot, n_th=0.01 * mean))
+    return reqs
+
+
+def bench_serving(nyx, torch, n_req: int):
+    """FP32 continuous-batching server vs a plain FIFO server running rt_step (FP64) per request,
+    on the same arrival stream; latency = done - arrival."""
+    reqs = serving_requests(n_req, torch)
+    ring = {n: [torch.empty(n ** 3, dtype=torch.float64).pin_memory().numpy() for _ in range(96)]
+            for n in (64, 128, 256)}
+    # warm-up, identical for both paths: one request of each grid size through each
+    warm = {}
+    for q in reqs:
+        warm.setdefault(q["n"], q)
+    srv = nyx.Server(precision=nyx.RT_FP32, max_batch=64)
+    for q in warm.values():
+        g = np.empty(q["n"] ** 3)
+        srv.poll(srv.submit(q["n"], q["box"], q["n_h"], q["x"], q["cells"], q["ndot"], gamma=g, heat=None,
+                            n_th_cm3=q["n_th"], n_min_ray=4.0, tau_max=30.0), wait_s=600.0)
+        s = nyx.Solver(q["n"], q["box"], precision=nyx.RT_FP64, n_th_cm3=q["n_th"], n_min_ray=4.0, tau_max=30.0)
+        s.set_fields(q["n_h"], q["x"])
+        s.add_sources(q["cells"], q["ndot"])
+        s.step(0.0, g, None)
+        s.close()
+    srv.close()
+    # ---- served (FP32, batched)
+    srv = nyx.Server(precision=nyx.RT_FP32, max_batch=64)
+    ids = []
+    t0 = time.perf_counter()
+    for j, q in enumerate(reqs):
+        delay = q["t"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(srv.submit(q["n"], q["box"], q["n_h"], q["x"], q["cells"], q["ndot"],
+                              gamma=ring[q["n"]][j % 96], heat=None, n_th_cm3=q["n_th"], n_min_ray=4.0,
+                              tau_max=30.0))
+        # keep the output ring safe: never more than 96 requests of a size in flight
+        if j >= 64:
+            srv.poll(ids[j - 64], wait_s=600.0) if ids[j - 64] is not None else None
+            ids[j - 64] = None
+    for i in ids:
+        if i is not None:
+            srv.poll(i, wait_s=600.0)
+    t_end = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    served = {"achieved_rps": st["completed"] / t_end, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+              "mean_ms": st["mean_ms"], "max_ms": st["max_ms"], "segments_per_s": st["segments"] / t_end,
+              "segments": st["segments"], "batches": st["batches"], "mem_peak_bytes": st["mem_peak"],
+              "gpu_busy_ms": st["busy_ms"], "wall_s": t_end, "completed": st["completed"], "failed": st["failed"],
+              "host_phase_ms": {k: st[k] for k in ("load_ms", "bind_ms", "run_ms", "finish_ms")}}
+    # ---- plain per-request FP64, first-come first-served
+    lat, segs = [], 0
+    t0 = time.perf_counter()
+    check = []
+    for j, q in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if q["t"] > now:
+            time.sleep(q["t"] - now)
+        s = nyx.Solver(q["n"], q["box"], precision=nyx.RT_FP64, n_th_cm3=q["n_th"], n_min_ray=4.0, tau_max=30.0)
+        s.set_fields(q["n_h"], q["x"])
+        s.add_sources(q["cells"], q["ndot"])
+        out = ring[q["n"]][j % 96]
+        _, _, stp = s.step(0.0, out, None)
+        s.close()
+        lat.append(1e3 * (time.perf_counter() - t0 - q["t"]))
+        segs += sum(stp["segments"])
+        if j < 4:
+            check.append((j, out.copy()))
+    t_end_p = time.perf_counter() - t0
+    lat_s = sorted(lat)
+    q_ = lambda p: lat_s[min(len(lat_s) - 1, int(round(p * (len(lat_s) - 1))))]
+    plain = {"achieved_rps": len(reqs) / t_end_p, "p50_ms": q_(0.5), "p99_ms": q_(0.99),
+             "mean_ms": float(np.mean(lat)), "max_ms": lat_s[-1], "segments_per_s": segs / t_end_p,
+             "segments": segs, "wall_s": t_end_p}
+    # accuracy: the first requests served again in FP32 through the server vs their FP64 plain results
+    srv = nyx.Server(precision=nyx.RT_FP32)
+    errs = []
+    for j, ref in check:
+        q = reqs[j]
+        g = np.empty(q["n"] ** 3)
+        rid = srv.submit(q["n"], q["box"], q["n_h"], q["x"], q["cells"], q["ndot"], gamma=g, heat=None,
+                         n_th_cm3=q["n_th"], n_min_ray=4.0, tau_max=30.0)
+        srv.poll(rid, wait_s=600.0)
+        errs.append(float(np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-300)))
+    srv.close()
+    # ---- capacity: every request submitted at once, each path as fast as it goes
+    srv = nyx.Server(precision=nyx.RT_FP32, max_batch=64)
+    t0 = time.perf_counter()
+    ids = [srv.submit(q["n"], q["box"], q["n_h"], q["x"], q["cells"], q["ndot"], gamma=np.empty(q["n"] ** 3) if q["n"] < 256 else ring[256][j % 96],
+                      heat=None, n_th_cm3=q["n_th"], n_min_ray=4.0, tau_max=30.0) for j, q in enumerate(reqs[:96])]
+    for i in ids:
+        srv.poll(i, wait_s=600.0)
+    cap_served = 96 / (time.perf_counter() - t0)
+    cst = srv.stats()
+    srv.close()
+    t0 = time.perf_counter()
+    for j, q in enumerate(reqs[:96]):
+        s = nyx.Solver(q["n"], q["box"], precision=nyx.RT_FP64, n_th_cm3=q["n_th"], n_min_ray=4.0, tau_max=30.0)
+        s.set_fields(q["n_h"], q["x"])
+        s.add_sources(q["cells"], q["ndot"])
+        s.step(0.0, ring[q["n"]][j % 96], None)
+        s.close()
+    cap_plain = 96 / (time.perf_counter() - t0)
+    offered = n_req / reqs[-1]["t"]
+    return {"requests": n_req, "offered_rps": offered,
+            "capacity_rps": {"served_fp32_batched": cap_served, "plain_fp64_per_request": cap_plain,
+                             "factor": cap_served / cap_plain, "requests": 96, "batches": cst["batches"]},
+            "served_fp32_batched": served,
+            "plain_fp64_per_request": plain, "throughput_factor": served["achieved_rps"] / plain["achieved_rps"],
+            "saturated_served": served["achieved_rps"] < 0.95 * offered,
+            "saturated_plain": plain["achieved_rps"] < 0.95 * offered,
+            "max_rel_l2_fp32_served_vs_fp64_plain": max(errs)}
+
+
 def run_nyx(args, world, rank, local):
     import torch
     import paper_2512_12466_gb300 as nyx
@@ -388,6 +531,8 @@ def run_nyx(args, world, rank, local):
     if not args.no_batched:
         line["batched"] = {"neutral": bench_batched(nyx, torch, "neutral", steps=5, tune=True),
                            "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 25)}
+    if args.serve_requests > 0:
+        line["serving"] = bench_serving(nyx, torch, args.serve_requests)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -402,6 +547,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="nyx", choices=["nyx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=400)
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":

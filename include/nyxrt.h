@@ -259,6 +259,8 @@ typedef struct rt_server_config {
                                minus the batch workspace and a 4 GB margin */
     int64_t slice;          /* batch kernel slice (rt_batch_params.slice) */
     int64_t group_bytes;    /* batch group budget (rt_batch_params.group_bytes) */
+    int32_t loaders;        /* loader threads (admission + host-to-device copies + source stage) */
+    int32_t max_n;          /* largest grid expected: its HEALPix directions are built at creation */
 } rt_server_config;
 
 typedef struct rt_server_stats {
@@ -269,12 +271,17 @@ typedef struct rt_server_stats {
     double busy_ms;         /* GPU time of all batches */
     double elapsed_ms;      /* since rt_server_create */
     double p50_ms, p99_ms, mean_ms, max_ms;     /* latency submit -> done, completed requests */
+    double load_ms, bind_ms, run_ms, finish_ms; /* host time summed per phase: loading requests,
+                                                   forming batches, running them, returning results */
 } rt_server_stats;
 
-/* Defaults: FP32, max_batch 64, hbm_budget 0, slice 2^23, group 48 MB. */
+/* Defaults: FP32, max_batch 64, hbm_budget 0, slice 2^23, group 48 MB, 4 loaders, max_n 256.
+ * The server sets the device's default stream-ordered memory pool to keep up
+ * to the budget cached between requests (process-local; the pool is shared
+ * with other cudaMallocAsync users of the process). */
 void rt_server_config_default(rt_server_config* cfg);
 
-/* Start a server on the current device (two host threads). */
+/* Start a server on the current device (loader, worker and finisher threads). */
 int rt_server_create(const rt_server_config* cfg, rt_server** out);
 
 /* Submit one solve: `cfg` as for rt_create (chem_iterate 0, the server's

@@ -69,13 +69,14 @@ class rt_batch_params(C.Structure):
 
 class rt_server_config(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_batch", C.c_int32), ("hbm_budget", C.c_int64),
-                ("slice", C.c_int64), ("group_bytes", C.c_int64)]
+                ("slice", C.c_int64), ("group_bytes", C.c_int64), ("loaders", C.c_int32), ("max_n", C.c_int32)]
 
 
 class rt_server_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("submitted", "completed", "failed", "batches", "queued", "mem_budget",
                                          "mem_in_use", "mem_peak", "segments")] + \
-               [(k, C.c_double) for k in ("busy_ms", "elapsed_ms", "p50_ms", "p99_ms", "mean_ms", "max_ms")]
+               [(k, C.c_double) for k in ("busy_ms", "elapsed_ms", "p50_ms", "p99_ms", "mean_ms", "max_ms",
+                                          "load_ms", "bind_ms", "run_ms", "finish_ms")]
 
 
 class NyxError(RuntimeError):
@@ -403,7 +404,7 @@ class Server:
     arrays kept alive here until their request is polled."""
 
     def __init__(self, precision: int = RT_FP32, max_batch: int = 64, hbm_budget: int = 0,
-                 slice: int | None = None, group_bytes: int | None = None):
+                 slice: int | None = None, group_bytes: int | None = None, loaders: int | None = None):
         c = rt_server_config()
         lib().rt_server_config_default(C.byref(c))
         c.precision = precision
@@ -413,6 +414,8 @@ class Server:
             c.slice = slice
         if group_bytes is not None:
             c.group_bytes = group_bytes
+        if loaders is not None:
+            c.loaders = loaders
         h = C.c_void_p()
         rc = lib().rt_server_create(C.byref(c), C.byref(h))
         if rc != RT_OK:

@@ -1,11 +1,12 @@
 // Serving loop: solves arrive as requests, are admitted while their device
 // memory fits a budget, are loaded onto the GPU (handle, fields, sources,
-// source stage) by a loader thread while the previous batch runs, and are
+// source stage) by loader threads while the previous batch runs, and are
 // traced by a worker thread that forms a new batch from every loaded request
 // at each iteration (continuous batching: a request arriving during a batch
-// joins the next one as soon as memory allows). Each request's Gamma and
-// heating are written to the caller's host buffers when its batch finishes,
-// its device memory is released, and its latency (submit to done) recorded.
+// joins the next one as soon as memory allows). A finisher thread copies each
+// request's Gamma and heating to the caller's host buffers, releases its
+// device memory and records its latency (submit to done), off the worker's
+// path, so the next batch starts as soon as the previous one ends.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,12 +72,16 @@ struct rt_server {
     int64_t next_id = 1;
     int64_t budget = 0, in_use = 0, peak = 0;
     bool stop = false;
-    std::thread loader, worker;
+    std::vector<std::thread> loaders;
+    std::thread worker;
+    std::vector<std::thread> finishers;
+    std::deque<std::pair<std::vector<SrvReq*>, int>> finished;   // traced batches and their status
+    std::condition_variable cv_fin;
     std::vector<cudaStream_t> streams;          // free streams for request handles
     rt_batch* batch = nullptr;
     std::vector<double> lat;
     int64_t submitted = 0, completed = 0, failed = 0, batches = 0, segments = 0;
-    double busy_ms = 0.0;
+    double busy_ms = 0.0, load_ms = 0.0, bind_ms = 0.0, run_ms = 0.0, finish_ms = 0.0;
     Clock::time_point t0;
     std::string err;
 };
@@ -98,13 +103,10 @@ cudaStream_t take_stream(rt_server* s)
     return st;
 }
 
-// Release a request's device state and mark it finished (lock held).
+// Mark a request finished and account for it (lock held; its handle is
+// already destroyed).
 void finish_locked(rt_server* s, SrvReq* r, int rc, const std::string& err)
 {
-    if (r->h) {
-        rt_destroy(r->h);
-        r->h = nullptr;
-    }
     if (r->stream) s->streams.push_back(r->stream);
     r->stream = nullptr;
     s->in_use -= r->mem;
@@ -140,6 +142,7 @@ void loader_main(rt_server* s)
             stream = take_stream(s);
             r->stream = stream;
         }
+        const Clock::time_point tl = Clock::now();
         int rc = stream ? RT_OK : RT_ECUDA;
         std::string err = stream ? "" : "stream creation failed";
         if (rc == RT_OK) {
@@ -150,7 +153,12 @@ void loader_main(rt_server* s)
         if (rc == RT_OK && r->nsrc > 0) rc = rt_add_sources(r->h, r->cells, r->ndot, r->nsrc, RT_HOST);
         if (rc == RT_OK) rc = handle_prepare_sources(r->h);
         if (rc != RT_OK && r->h && err.empty()) err = r->h->err;
+        if (rc != RT_OK && r->h) {
+            rt_destroy(r->h);
+            r->h = nullptr;
+        }
         std::lock_guard<std::mutex> lk(s->mu);
+        s->load_ms += ms_since(tl);
         if (rc != RT_OK) {
             finish_locked(s, r, rc, err);
             s->cv_done.notify_all();
@@ -182,6 +190,7 @@ void worker_main(rt_server* s)
         for (SrvReq* r : take) hs.push_back(r->h);
         int rc = RT_OK;
         std::string err;
+        const Clock::time_point tb = Clock::now();
         if (!s->batch) {
             rc = rt_batch_create(hs.data(), (int32_t)hs.size(), nullptr, &s->batch);
             if (rc == RT_OK) {
@@ -194,26 +203,17 @@ void worker_main(rt_server* s)
         } else {
             rc = batch_bind(s->batch, hs.data(), (int32_t)hs.size());
         }
+        const double bind_ms = ms_since(tb);
         float ms = 0.f;
+        const Clock::time_point tr = Clock::now();
         if (rc == RT_OK) rc = batch_run_direct(s->batch, &ms);
-        if (rc == RT_OK) {
-            cudaStream_t bs = batch_stream(s->batch);
-            for (size_t i = 0; i < take.size() && rc == RT_OK; ++i) {
-                SrvReq* r = take[i];
-                const size_t fb = sizeof(double) * (size_t)r->h->ncell;
-                if (r->gamma_out && cudaMemcpyAsync(r->gamma_out, r->h->d_gamma, fb, cudaMemcpyDeviceToHost, bs) != cudaSuccess)
-                    rc = RT_ECUDA;
-                if (r->heat_out && cudaMemcpyAsync(r->heat_out, r->h->d_heat, fb, cudaMemcpyDeviceToHost, bs) != cudaSuccess)
-                    rc = RT_ECUDA;
-                batch_fill_stats(s->batch, i, ms, &r->st);
-            }
-            if (cudaStreamSynchronize(bs) != cudaSuccess) rc = RT_ECUDA;
-            if (rc != RT_OK) {
-                cudaGetLastError();
-                err = "result copy failed";
-            }
+        const double run_ms = ms_since(tr);
+        if (rc == RT_OK)
+            for (size_t i = 0; i < take.size(); ++i) batch_fill_stats(s->batch, i, ms, &take[i]->st);
+        if (rc != RT_OK) {
+            err = s->batch ? rt_batch_last_error(s->batch) : "batch creation failed";
+            for (SrvReq* r : take) r->err = err;
         }
-        if (rc != RT_OK && err.empty()) err = s->batch ? rt_batch_last_error(s->batch) : "batch creation failed";
         std::lock_guard<std::mutex> lk(s->mu);
         if (rc != RT_OK && s->batch) {       // a failed batch is rebuilt from scratch next time
             rt_batch_destroy(s->batch);
@@ -221,13 +221,52 @@ void worker_main(rt_server* s)
         }
         ++s->batches;
         s->busy_ms += ms;
-        for (SrvReq* r : take) {
-            if (rc == RT_OK)
-                for (int l = 0; l < RT_MAX_LEVELS; ++l) s->segments += r->st.segments[l];
-            finish_locked(s, r, rc, err);
+        s->bind_ms += bind_ms;
+        s->run_ms += run_ms;
+        s->finished.emplace_back(std::move(take), rc);
+        s->cv_fin.notify_one();
+    }
+}
+
+// Copy results out, release each request's device memory, mark it done
+// (two finisher threads share the queue of traced batches).
+void finisher_main(rt_server* s)
+{
+    cudaSetDevice(s->device);
+    for (;;) {
+        std::pair<std::vector<SrvReq*>, int> job;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_fin.wait(lk, [&] { return s->stop || !s->finished.empty(); });
+            if (s->finished.empty()) return;
+            job = std::move(s->finished.front());
+            s->finished.pop_front();
         }
-        s->cv_done.notify_all();
-        s->cv_load.notify_all();
+        int rc = job.second;
+        for (SrvReq* r : job.first) {
+            const Clock::time_point tf = Clock::now();
+            int rrc = rc;
+            std::string err = rrc != RT_OK ? r->err : std::string();
+            if (rrc == RT_OK) {
+                const size_t fb = sizeof(double) * (size_t)r->h->ncell;
+                if ((r->gamma_out && cudaMemcpyAsync(r->gamma_out, r->h->d_gamma, fb, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess) ||
+                    (r->heat_out && cudaMemcpyAsync(r->heat_out, r->h->d_heat, fb, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess) ||
+                    cudaStreamSynchronize(r->stream) != cudaSuccess) {
+                    cudaGetLastError();
+                    rrc = RT_ECUDA;
+                    err = "result copy failed";
+                }
+            }
+            rt_destroy(r->h);
+            r->h = nullptr;
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->finish_ms += ms_since(tf);
+            if (rrc == RT_OK)
+                for (int l = 0; l < RT_MAX_LEVELS; ++l) s->segments += r->st.segments[l];
+            finish_locked(s, r, rrc, err);
+            s->cv_done.notify_all();
+            s->cv_load.notify_all();
+        }
     }
 }
 
@@ -243,13 +282,16 @@ void rt_server_config_default(rt_server_config* c)
     c->hbm_budget = 0;
     c->slice = int64_t(1) << 23;
     c->group_bytes = int64_t(48) << 20;
+    c->loaders = 4;
+    c->max_n = 256;
 }
 
 int rt_server_create(const rt_server_config* cfg, rt_server** out)
 {
     if (!out || !cfg) return RT_EINVAL;
     *out = nullptr;
-    if ((cfg->precision != RT_FP32 && cfg->precision != RT_FP64) || cfg->max_batch < 1 || cfg->hbm_budget < 0)
+    if ((cfg->precision != RT_FP32 && cfg->precision != RT_FP64) || cfg->max_batch < 1 || cfg->hbm_budget < 0 ||
+        cfg->loaders < 1 || cfg->loaders > 64)
         return RT_EINVAL;
     rt_server* s = new rt_server();
     s->cfg = *cfg;
@@ -263,9 +305,24 @@ int rt_server_create(const rt_server_config* cfg, rt_server** out)
     // reserve the shared batch workspace (one slice per level) and a margin
     const int64_t reserve = (int64_t)24 * std::max<int64_t>(cfg->slice, int64_t(1) << 22) * 14 + (int64_t(4) << 30);
     s->budget = cfg->hbm_budget > 0 ? cfg->hbm_budget : std::max<int64_t>(0, (int64_t)free_b - reserve);
+    {   // build the direction table up to the deepest level a grid of max_n cells can need
+        rt_config probe;
+        rt_config_default(&probe, std::max(1, std::min(1024, cfg->max_n)), 1.0);
+        probe.precision = cfg->precision;
+        rt_handle* h = nullptr;
+        if (rt_create(&probe, nullptr, &h) == RT_OK) rt_destroy(h);
+    }
     s->t0 = Clock::now();
-    s->loader = std::thread(loader_main, s);
+    // keep memory freed by finished requests in the stream-ordered pool for the next ones
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+        uint64_t keep = (uint64_t)s->budget;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    for (int i = 0; i < std::max(1, cfg->loaders); ++i) s->loaders.emplace_back(loader_main, s);
     s->worker = std::thread(worker_main, s);
+    for (int i = 0; i < 2; ++i) s->finishers.emplace_back(finisher_main, s);
     *out = s;
     return RT_OK;
 }
@@ -335,6 +392,10 @@ int rt_server_stats_get(rt_server* s, rt_server_stats* out)
     out->mem_peak = s->peak;
     out->segments = s->segments;
     out->busy_ms = s->busy_ms;
+    out->load_ms = s->load_ms;
+    out->bind_ms = s->bind_ms;
+    out->run_ms = s->run_ms;
+    out->finish_ms = s->finish_ms;
     out->elapsed_ms = ms_since(s->t0);
     if (!s->lat.empty()) {
         std::vector<double> v = s->lat;
@@ -361,8 +422,12 @@ int rt_server_destroy(rt_server* s)
     }
     s->cv_load.notify_all();
     s->cv_work.notify_all();
-    if (s->loader.joinable()) s->loader.join();
+    s->cv_fin.notify_all();
+    for (auto& t : s->loaders)
+        if (t.joinable()) t.join();
     if (s->worker.joinable()) s->worker.join();
+    for (auto& t : s->finishers)
+        if (t.joinable()) t.join();
     for (auto& kv : s->reqs) {
         SrvReq* r = kv.second;
         if (r->h) rt_destroy(r->h);
