@@ -157,6 +157,15 @@ int rt_add_sources(rt_handle* h, const int32_t* cell_ijk, const double* ndot, in
 /* Remove all sources. */
 int rt_clear_sources(rt_handle* h);
 
+/* Re-target a handle to another configuration with the same n, precision
+ * and chem_iterate setting (box size, threshold, ray and merge parameters
+ * may all change), keeping its device allocations so that a long-lived
+ * caller that serves many grids of one size allocates nothing per grid.
+ * Sources are cleared and the fields must be set again before rt_step.
+ * Returns RT_EINVAL, leaving the handle as it was, for an invalid
+ * configuration or a different n, precision or chemistry setting. */
+int rt_reconfigure(rt_handle* h, const rt_config* cfg);
+
 /* One radiative-transfer step (Alg. 2 with the Sec. 2.8 source handling):
  * dedup/sort (and merge) sources, trace all rays, write Gamma (s^-1 per H
  * atom, Eq. 1) and heating (erg s^-1 cm^-3) into caller buffers of n^3
@@ -273,6 +282,9 @@ typedef struct rt_server_stats {
     double p50_ms, p99_ms, mean_ms, max_ms;     /* latency submit -> done, completed requests */
     double load_ms, bind_ms, run_ms, finish_ms; /* host time summed per phase: loading requests,
                                                    forming batches, running them, returning results */
+    double src_ms;          /* host time of the batched source stage (part of bind_ms) */
+    double wait_admit_ms, wait_batch_ms, wait_finish_ms;  /* summed over requests: submit -> admitted,
+                                                   loaded -> taken into a batch, traced -> result copy */
 } rt_server_stats;
 
 /* Defaults: FP32, max_batch 64, hbm_budget 0, slice 2^23, group 48 MB, 4 loaders, max_n 256.
@@ -281,7 +293,12 @@ typedef struct rt_server_stats {
  * with other cudaMallocAsync users of the process). */
 void rt_server_config_default(rt_server_config* cfg);
 
-/* Start a server on the current device (loader, worker and finisher threads). */
+/* Start a server on the current device (loader, worker and finisher threads).
+ * Solver handles are pooled by grid size and reused across requests; idle
+ * ones count against the budget and are released, least recently used
+ * first, when a request of another size needs the room. With the
+ * environment variable NYXRT_SERVER_TRACE=<file>, every request's phase
+ * times are appended to that file when the server is destroyed. */
 int rt_server_create(const rt_server_config* cfg, rt_server** out);
 
 /* Submit one solve: `cfg` as for rt_create (chem_iterate 0, the server's

@@ -76,7 +76,8 @@ class rt_server_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("submitted", "completed", "failed", "batches", "queued", "mem_budget",
                                          "mem_in_use", "mem_peak", "segments")] + \
                [(k, C.c_double) for k in ("busy_ms", "elapsed_ms", "p50_ms", "p99_ms", "mean_ms", "max_ms",
-                                          "load_ms", "bind_ms", "run_ms", "finish_ms")]
+                                          "load_ms", "bind_ms", "run_ms", "finish_ms", "src_ms", "wait_admit_ms",
+                                          "wait_batch_ms", "wait_finish_ms")]
 
 
 class NyxError(RuntimeError):
@@ -103,6 +104,7 @@ def lib():
         L.rt_set_fields.argtypes = [P, P, P, C.c_int]
         L.rt_add_sources.argtypes = [P, P, P, i64, C.c_int]
         L.rt_clear_sources.argtypes = [P]
+        L.rt_reconfigure.argtypes = [P, C.POINTER(rt_config)]
         L.rt_step.argtypes = [P, d, P, P, C.c_int, C.POINTER(rt_stats)]
         L.rt_get_x.argtypes = [P, P, C.c_int]
         L.rt_destroy.argtypes = [P]
@@ -127,7 +129,7 @@ def lib():
         L.rt_server_destroy.argtypes = [P]
         L.rt_server_last_error.argtypes = [P]
         L.rt_server_last_error.restype = C.c_char_p
-        for f in ("rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_step", "rt_get_x",
+        for f in ("rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_reconfigure", "rt_step", "rt_get_x",
                   "rt_destroy", "rt_batch_create", "rt_batch_set_params", "rt_batch_get_params", "rt_batch_tune",
                   "rt_batch_capture", "rt_batch_run", "rt_batch_destroy", "rt_server_create", "rt_server_submit",
                   "rt_server_poll", "rt_server_stats_get", "rt_server_destroy"):
@@ -137,7 +139,7 @@ def lib():
 
 
 def exported_symbols():
-    return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_step",
+    return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_reconfigure", "rt_step",
             "rt_get_x", "rt_destroy", "rt_last_error", "rt_version", "rt_batch_create", "rt_batch_set_params",
             "rt_batch_get_params", "rt_batch_tune", "rt_batch_capture", "rt_batch_run", "rt_batch_destroy",
             "rt_batch_last_error", "rt_server_config_default", "rt_server_create", "rt_server_submit",
@@ -187,6 +189,10 @@ def rt_add_sources(h: int, cells, ndot, n: int, where: int) -> None:
 
 def rt_clear_sources(h: int) -> None:
     _check(lib().rt_clear_sources(h), h)
+
+
+def rt_reconfigure(h: int, cfg: rt_config) -> None:
+    _check(lib().rt_reconfigure(h, C.byref(cfg)), h)
 
 
 def rt_step(h: int, dt_s: float, gamma_out, heat_out, where: int, stats: rt_stats | None = None) -> rt_stats:
@@ -305,6 +311,17 @@ class Solver:
 
     def clear_sources(self):
         rt_clear_sources(self.h)
+
+    def reconfigure(self, box_cm: float, **cfg):
+        """Re-target to another configuration of the same n / precision /
+        chemistry setting, keeping the device allocations; sources are
+        cleared and fields must be set again."""
+        cfg.setdefault("precision", self.cfg.precision)
+        cfg.setdefault("chem_iterate", self.cfg.chem_iterate)
+        c = rt_config_default(self.n, box_cm, **cfg)
+        rt_reconfigure(self.h, c)
+        self.cfg = c
+        self._keep = self._keep_src = None
 
     def step(self, dt_s: float = 0.0, gamma=None, heat=None):
         """Run one step; returns (gamma, heat, stats). Output arrays are
@@ -429,13 +446,16 @@ class Server:
         c = rt_config_default(n, box_cm, **cfg)
         arrs = [np.ascontiguousarray(n_h, dtype=np.float64), np.ascontiguousarray(x_ion, dtype=np.float64),
                 np.ascontiguousarray(cells, dtype=np.int32), np.ascontiguousarray(ndot, dtype=np.float64)]
-        if gamma is None:
+        if gamma is None and heat is None:      # neither given: both returned, in new host arrays
             gamma = np.empty(n ** 3)
-        if heat is None:
             heat = np.empty(n ** 3)
+        for a in (gamma, heat):                 # one given: only that one is produced
+            if a is not None and (a.dtype != np.float64 or a.size != n ** 3 or not a.flags.c_contiguous):
+                raise ValueError("result buffers must be contiguous float64 host arrays of n^3 elements")
+        out = [a.ctypes.data_as(C.c_void_p) if a is not None else None for a in (gamma, heat)]
         rid = C.c_int64()
         rc = lib().rt_server_submit(self.s, C.byref(c), *[a.ctypes.data_as(C.c_void_p) for a in arrs], len(arrs[3]),
-                                    gamma.ctypes.data_as(C.c_void_p), heat.ctypes.data_as(C.c_void_p), C.byref(rid))
+                                    out[0], out[1], C.byref(rid))
         if rc != RT_OK:
             raise NyxError(rc, lib().rt_server_last_error(self.s).decode(errors="replace"))
         self._live[rid.value] = (arrs, gamma, heat)

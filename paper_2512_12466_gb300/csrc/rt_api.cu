@@ -81,6 +81,9 @@ int nyx::ensure_directions(int device, int level, const int4** out, std::string&
 
 namespace nyx {
 
+int configure(rt_handle* h, const rt_config* cfg, std::string& why);
+bool valid_config(const rt_config* c, std::string& why);
+
 // Handle memory is stream-ordered: allocating or freeing it never waits for
 // work on other streams (a server creates and frees handles while batches run).
 cudaError_t dalloc(rt_handle* h, void** p, size_t bytes) { return cudaMallocAsync(p, bytes, h->stream); }
@@ -309,6 +312,79 @@ int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out)
     return RT_OK;
 }
 
+// Re-target an idle handle to a new configuration with the same grid size,
+// precision and chemistry setting (its allocations fit as they are).
+int handle_reconfigure(rt_handle* h, const rt_config* cfg)
+{
+    std::string why;
+    if (h->sticky) return RT_ESTATE;
+    if (cfg->n != h->cfg.n || cfg->precision != h->cfg.precision || (cfg->chem_iterate != 0) != (h->cfg.chem_iterate != 0))
+        return fail(h, RT_EINVAL, "reconfiguration needs the same n, precision and chemistry setting");
+    if (!valid_config(cfg, why)) return fail(h, RT_EINVAL, why);
+    const int rc = configure(h, cfg, why);
+    if (rc) return fail(h, rc, why);
+    h->nsrc = 0;
+    h->fields_set = false;
+    h->src_ready = false;
+    h->err.clear();
+    return RT_OK;
+}
+
+// The source stage of many handles at once: for handles without merging, every
+// kernel (validation, dedup + sort, mean n_H, emission with the count read on
+// the device) and the statistics readback are enqueued on all handles' streams
+// before a single wait; handles with merging take the synchronous path.
+// rcs[i] receives handle i's outcome (one bad request fails alone); returns
+// the number of handles that failed.
+int prepare_sources_many(rt_handle* const* hs, int count, int* rcs)
+{
+    auto enqueue = [](rt_handle* h) -> int {
+        cudaStream_t s = h->stream;
+        h->launches = 0;
+        RT_CUDA(h, cudaMemsetAsync(h->d_st, 0, sizeof(DevStats), s), "stats clear");
+        h->launches += launch_validate_fields(h->d_nh, h->d_x, h->ncell, h->d_st, s);
+        h->launches += launch_validate_sources(h->sw.cells_raw, h->sw.ndot_raw, h->nsrc, h->cfg.n, h->d_st, s);
+        h->launches += launch_dedup_sort(h->sw, h->nsrc, s);
+        if (h->cfg.n_th_cm3 < 0) {
+            RT_CUDA(h, cudaMemsetAsync(h->d_scalar, 0, sizeof(double), s), "scalar clear");
+            h->launches += launch_mean_nh(h->d_nh, h->ncell, h->d_scalar, s);
+        }
+        if (h->nsrc > 0) h->launches += launch_build_emit_dev(h->sw, h->nsrc, h->s_over_dx2, h->d_emit, h->d_st, s);
+        RT_LAUNCHED(h, "source stage launch");
+        RT_CUDA(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "stats read");
+        if (h->nsrc > 0)
+            RT_CUDA(h, cudaMemcpyAsync(h->h_i32, h->sw.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count read");
+        if (h->cfg.n_th_cm3 < 0)
+            RT_CUDA(h, cudaMemcpyAsync(h->h_f64, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s), "mean read");
+        return RT_OK;
+    };
+    int failed = 0;
+    for (int i = 0; i < count; ++i) {
+        rt_handle* h = hs[i];
+        rcs[i] = RT_OK;
+        if (h->src_ready) continue;
+        rcs[i] = h->cfg.merge_mode != RT_MERGE_OFF ? handle_prepare_sources(h) : enqueue(h);
+    }
+    for (int i = 0; i < count; ++i) {
+        rt_handle* h = hs[i];
+        if (rcs[i] == RT_OK && !h->src_ready) {
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) rcs[i] = cuda_fail(h, cudaGetLastError(), "source stage");
+            else if (h->h_st->bad_input)
+                rcs[i] = fail(h, RT_EINVAL, "invalid field or source values (n_H < 0, x outside [0,1], non-finite, bad source)");
+        }
+        if (rcs[i] != RT_OK) { ++failed; continue; }
+        if (h->src_ready) continue;
+        const int64_t m = h->nsrc > 0 ? h->h_i32[0] : 0;
+        h->n_emit = m;
+        h->src_ready = true;
+        h->src_merged = false;
+        h->src_dedup = m;
+        h->src_nth = h->cfg.n_th_cm3 >= 0 ? h->cfg.n_th_cm3 : 0.01 * (h->h_f64[0] / (double)h->ncell);
+        h->src_emitted = h->h_st->emitted;
+    }
+    return failed;
+}
+
 // Run the source stage ahead of a batch (a server's loader does this while the
 // GPU traces the previous batch); batch_bind then uses the recorded results.
 int handle_prepare_sources(rt_handle* h)
@@ -327,6 +403,30 @@ int handle_prepare_sources(rt_handle* h)
     h->src_nth = h->cfg.n_th_cm3 >= 0 ? h->cfg.n_th_cm3 : 0.01 * h->h_f64[1];
     h->src_emitted = h->h_st->emitted;
     return RT_OK;
+}
+
+// Derived quantities of a configuration (cell size, split radius, level cap,
+// direction table); allocation-independent, so a pooled handle of the same n
+// and precision can be re-targeted to a new request.
+int configure(rt_handle* h, const rt_config* cfg, std::string& why)
+{
+    h->cfg = *cfg;
+    const int64_t n = cfg->n;
+    h->ncell = n * n * n;
+    // the same IEEE operations as the problem statement: dx = L / n
+    h->dx = cfg->box_cm / (double)n;
+    h->vol = h->dx * h->dx * h->dx;
+    h->sdx = cfg->sigma_cm2 * h->dx;
+    h->s_over_dx2 = cfg->sigma_cm2 / (h->dx * h->dx);
+    // R_0 = sqrt(3 / (pi N_min)) in units of 2^-24 cells (Eq. 4 with Omega_c = dx^2 / R^2)
+    h->rq = (int64_t)std::floor(std::sqrt(3.0 / (3.141592653589793 * cfg->n_min_ray)) * (double)(1 << kRadBits) + 0.5);
+    // smallest level whose split sphere encloses the grid from any cell centre
+    int reach = 0;
+    while (std::ldexp((double)h->rq, reach - kRadBits) < std::sqrt(3.0) * (double)n) ++reach;
+    h->level_max = cfg->level_max >= 0 ? cfg->level_max : std::min(reach + 1, kMaxLevel);
+    h->table_level = std::min(h->level_max, reach);
+    const int need_level = std::max(h->table_level, cfg->merge_samp_level);
+    return ensure_directions(h->device, need_level, &h->dirs, why);
 }
 
 bool valid_config(const rt_config* c, std::string& why)
@@ -400,10 +500,7 @@ int rt_destroy(rt_handle* h)
         for (void* q : ws) dfree(h, q);
         for (auto& r : h->rays) dfree(h, r.base);
     }
-    delete[] h->h_st;
-    delete[] h->h_count;
-    delete[] h->h_i32;
-    delete[] h->h_f64;
+    if (h->h_pin) cudaFreeHost(h->h_pin);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
     cudaGetLastError();
     delete h;
@@ -420,28 +517,11 @@ int rt_create(const rt_config* cfg, void* cuda_stream, rt_handle** out)
     if (!valid_config(cfg, why)) { g_create_error = why; return RT_EINVAL; }
     rt_handle* h = new (std::nothrow) rt_handle();
     if (!h) { g_create_error = "host allocation failed"; return RT_ENOMEM; }
-    h->cfg = *cfg;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
-    const int64_t n = cfg->n;
-    h->ncell = n * n * n;
-    // the same IEEE operations as the problem statement: dx = L / n
-    h->dx = cfg->box_cm / (double)n;
-    h->vol = h->dx * h->dx * h->dx;
-    h->sdx = cfg->sigma_cm2 * h->dx;
-    h->s_over_dx2 = cfg->sigma_cm2 / (h->dx * h->dx);
-    // R_0 = sqrt(3 / (pi N_min)) in units of 2^-24 cells (Eq. 4 with Omega_c = dx^2 / R^2)
-    h->rq = (int64_t)std::floor(std::sqrt(3.0 / (3.141592653589793 * cfg->n_min_ray)) * (double)(1 << kRadBits) + 0.5);
-    // smallest level whose split sphere encloses the grid from any cell centre
-    int reach = 0;
-    while (std::ldexp((double)h->rq, reach - kRadBits) < std::sqrt(3.0) * (double)n) ++reach;
-    h->level_max = cfg->level_max >= 0 ? cfg->level_max : std::min(reach + 1, kMaxLevel);
-    h->table_level = std::min(h->level_max, reach);
-    const int need_level = std::max(h->table_level, cfg->merge_samp_level);
-    int rc = ensure_directions(h->device, need_level, &h->dirs, why);
+    int rc = configure(h, cfg, why);
     if (rc) { g_create_error = why; rt_destroy(h); return rc; }
-
     cudaError_t e = cudaSuccess;
     const size_t fb = sizeof(double) * (size_t)h->ncell;
     e = e ? e : dalloc(h, (void**)&h->d_nh, fb);
@@ -456,11 +536,18 @@ int rt_create(const rt_config* cfg, void* cuda_stream, rt_handle** out)
     e = e ? e : dalloc(h, (void**)&h->d_scalar, 64);
     e = e ? e : dalloc(h, (void**)&h->d_count, sizeof(unsigned long long) * (RT_MAX_LEVELS + 1));
     e = e ? e : dalloc(h, (void**)&h->d_st, sizeof(DevStats));
-    h->h_st = new (std::nothrow) DevStats[1];
-    h->h_count = new (std::nothrow) unsigned long long[RT_MAX_LEVELS + 1];
-    h->h_i32 = new (std::nothrow) int32_t[16];
-    h->h_f64 = new (std::nothrow) double[8];
-    if (!h->h_st || !h->h_count || !h->h_i32 || !h->h_f64) e = cudaErrorMemoryAllocation;
+    {   // one pinned block for every host-side readback
+        const size_t a = (sizeof(DevStats) + 63) & ~size_t(63);
+        const size_t b = (sizeof(unsigned long long) * (RT_MAX_LEVELS + 1) + 63) & ~size_t(63);
+        e = e ? e : cudaMallocHost(&h->h_pin, a + b + 128);
+        if (e == cudaSuccess) {
+            char* q = static_cast<char*>(h->h_pin);
+            h->h_st = reinterpret_cast<DevStats*>(q);
+            h->h_count = reinterpret_cast<unsigned long long*>(q + a);
+            h->h_i32 = reinterpret_cast<int32_t*>(q + a + b);
+            h->h_f64 = reinterpret_cast<double*>(q + a + b + 64);
+        }
+    }
     for (auto& ev : h->ev) e = e ? e : cudaEventCreate(&ev);
     e = e ? e : cudaStreamSynchronize(h->stream);   // the allocations are usable from any stream after this
     if (e != cudaSuccess) {
@@ -511,6 +598,13 @@ int rt_add_sources(rt_handle* h, const int32_t* cell_ijk, const double* ndot, in
     if (where == RT_HOST) RT_CUDA(h, cudaStreamSynchronize(h->stream), "source copy");
     h->nsrc += n;
     return RT_OK;
+}
+
+int rt_reconfigure(rt_handle* h, const rt_config* cfg)
+{
+    if (!h || !cfg) return h ? fail(h, RT_EINVAL, "cfg is NULL") : RT_EINVAL;
+    DeviceGuard g(h->device);
+    return handle_reconfigure(h, cfg);
 }
 
 int rt_clear_sources(rt_handle* h)

@@ -96,10 +96,11 @@ struct rt_handle {
     nyx::RayStore rays[RT_MAX_LEVELS + 1];
     unsigned long long* d_count = nullptr;   // one per level
     nyx::DevStats* d_st = nullptr;
-    nyx::DevStats* h_st = nullptr;                // pinned
-    unsigned long long* h_count = nullptr;   // pinned
-    int32_t* h_i32 = nullptr;                // pinned scratch
-    double* h_f64 = nullptr;                 // pinned scratch
+    void* h_pin = nullptr;                   // one pinned block holding the four below
+    nyx::DevStats* h_st = nullptr;
+    unsigned long long* h_count = nullptr;
+    int32_t* h_i32 = nullptr;                // scratch
+    double* h_f64 = nullptr;                 // scratch
 
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double ms_march = 0.0;
@@ -123,6 +124,8 @@ int cuda_fail(rt_handle* h, cudaError_t e, const char* what);
 int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out);
 int ensure_directions(int device, int level, const int4** out, std::string& err);
 int handle_prepare_sources(rt_handle* h);
+int handle_reconfigure(rt_handle* h, const rt_config* cfg);
+int prepare_sources_many(rt_handle* const* hs, int count, int* rcs);
 int batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count);
 int batch_run_direct(rt_batch* b, float* ms);
 void batch_fill_stats(const rt_batch* b, size_t i, float ms, rt_stats* st);

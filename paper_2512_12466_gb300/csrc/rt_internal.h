@@ -166,6 +166,9 @@ int launch_dedup_sort(SourceWork& w, int64_t nsrc, cudaStream_t s);
 int launch_merge(SourceWork& w, int64_t m, int n, const double* x, const int4* samp_dirs, int samp_count,
                   double x_th, double f_req, int n_min, double dr, double rmax, double f_ov, double eps,
                   DevStats* st, cudaStream_t s);
+// Emitted catalog entries from cells_a/ndot_a[0..*count) with *count read on the device (<= max_m).
+int launch_build_emit_dev(const SourceWork& w, int64_t max_m, double s_over_dx2, SrcEntry* out, DevStats* st,
+                          cudaStream_t s);
 // Emitted catalog entries from cells_a/ndot_a[0..m).
 int launch_build_emit(const SourceWork& w, int64_t m, double s_over_dx2, SrcEntry* out, DevStats* st,
                       cudaStream_t s);

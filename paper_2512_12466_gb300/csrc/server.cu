@@ -1,17 +1,24 @@
 // Serving loop: solves arrive as requests, are admitted while their device
-// memory fits a budget, are loaded onto the GPU (handle, fields, sources,
-// source stage) by loader threads while the previous batch runs, and are
-// traced by a worker thread that forms a new batch from every loaded request
-// at each iteration (continuous batching: a request arriving during a batch
-// joins the next one as soon as memory allows). A finisher thread copies each
-// request's Gamma and heating to the caller's host buffers, releases its
-// device memory and records its latency (submit to done), off the worker's
-// path, so the next batch starts as soon as the previous one ends.
+// memory fits a budget, have their fields and sources copied to the GPU by
+// loader threads while the previous batch runs, and are traced by a worker
+// thread that forms a new batch from every loaded request at each iteration
+// (continuous batching: a request arriving during a batch joins the next one
+// as soon as memory allows). The worker enqueues the source stage of all the
+// batch's requests back to back with one wait, then traces them in one
+// persistent launch. Finisher threads copy each request's Gamma and heating
+// to the caller's host buffers and record its latency (submit to done), off
+// the worker's path. Solver handles are pooled by grid size: a finished
+// request's handle (device arrays, stream, pinned readback block) serves the
+// next request of the same n, so steady-state serving allocates nothing; idle
+// handles count against the budget and the least recently used are released
+// when a request of another size needs the room.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -44,21 +51,44 @@ struct SrvReq {
     double* heat_out = nullptr;
     int64_t mem = 0;
     rt_handle* h = nullptr;
-    cudaStream_t stream = nullptr;
     rt_stats st{};
     int rc = RT_OK;
     std::string err;
     int state = kPending;
-    double t_submit = 0, t_done = 0;
+    double t_submit = 0, t_done = 0, t_ready = 0, t_traced = 0;
 };
 
-// Device bytes a request holds while admitted: n_H, x, Gamma, heating (FP64),
-// kappa, and the source workspace; the shared batch workspace is reserved once.
-int64_t request_bytes(const rt_config& c, int64_t nsrc)
+// Device bytes a handle holds: n_H, x, Gamma, heating (FP64), kappa, and a
+// source workspace of src_cap entries; the shared batch workspace is reserved
+// once for the server.
+int64_t handle_bytes(int n, int precision, int64_t src_cap)
 {
-    const int64_t cells = (int64_t)c.n * c.n * c.n;
-    return cells * (32 + (c.precision == RT_FP32 ? 4 : 8)) + 160 * std::max<int64_t>(nsrc, 1024) + (1 << 16);
+    const int64_t cells = (int64_t)n * n * n;
+    return cells * (32 + (precision == RT_FP32 ? 4 : 8)) + 160 * std::max<int64_t>(src_cap, 1024) + (1 << 16);
 }
+
+// Source capacity a handle with capacity cap has after taking nsrc sources
+// (the growth rule of the handle's source workspace).
+int64_t grown_cap(int64_t cap, int64_t nsrc)
+{
+    return nsrc <= cap ? cap : std::max<int64_t>(nsrc, std::max<int64_t>(1024, 2 * cap));
+}
+
+// Optional event trace (NYXRT_SERVER_TRACE=<file>): one line per event with
+// the time since server start, the event, the request id and a value; written
+// when the server is destroyed. Off by default (one branch per event).
+struct TraceEv {
+    double t;
+    const char* what;
+    int64_t id;
+    double v;
+};
+
+struct Idle {
+    rt_handle* h;
+    int64_t mem;
+    uint64_t used;      // LRU stamp
+};
 
 }  // namespace
 
@@ -77,16 +107,31 @@ struct rt_server {
     std::vector<std::thread> finishers;
     std::deque<std::pair<std::vector<SrvReq*>, int>> finished;   // traced batches and their status
     std::condition_variable cv_fin;
-    std::vector<cudaStream_t> streams;          // free streams for request handles
+    std::vector<cudaStream_t> streams;          // free streams for new request handles
+    std::vector<Idle> idle;                     // pooled handles of finished requests
+    int64_t pooled = 0;                         // device bytes the pooled handles hold
+    uint64_t tick = 0;
     rt_batch* batch = nullptr;
     std::vector<double> lat;
     int64_t submitted = 0, completed = 0, failed = 0, batches = 0, segments = 0;
-    double busy_ms = 0.0, load_ms = 0.0, bind_ms = 0.0, run_ms = 0.0, finish_ms = 0.0;
+    double busy_ms = 0.0, load_ms = 0.0, bind_ms = 0.0, run_ms = 0.0, finish_ms = 0.0, src_ms = 0.0;
+    double wait_admit_ms = 0.0, wait_batch_ms = 0.0, wait_finish_ms = 0.0;
     Clock::time_point t0;
     std::string err;
+    std::string trace_path;
+    std::mutex trace_mu;
+    std::vector<TraceEv> trace;
 };
 
 namespace {
+
+void trace(rt_server* s, const char* what, int64_t id, double v = 0.0)
+{
+    if (s->trace_path.empty()) return;
+    const double t = ms_since(s->t0);
+    std::lock_guard<std::mutex> lk(s->trace_mu);
+    s->trace.push_back({t, what, id, v});
+}
 
 cudaStream_t take_stream(rt_server* s)
 {
@@ -103,12 +148,10 @@ cudaStream_t take_stream(rt_server* s)
     return st;
 }
 
-// Mark a request finished and account for it (lock held; its handle is
-// already destroyed).
+// Mark a request finished and account for it (lock held); its handle has
+// been pooled or destroyed already.
 void finish_locked(rt_server* s, SrvReq* r, int rc, const std::string& err)
 {
-    if (r->stream) s->streams.push_back(r->stream);
-    r->stream = nullptr;
     s->in_use -= r->mem;
     r->rc = rc;
     r->err = err;
@@ -122,39 +165,117 @@ void finish_locked(rt_server* s, SrvReq* r, int rc, const std::string& err)
     }
 }
 
+// Return a request's handle to the pool (lock held). A handle in an error
+// state is destroyed by the caller instead.
+void pool_put_locked(rt_server* s, rt_handle* h)
+{
+    const int64_t mem = handle_bytes(h->cfg.n, h->cfg.precision, h->sw.cap);
+    s->idle.push_back({h, mem, ++s->tick});
+    s->pooled += mem;
+}
+
+// Destroy a handle and keep its stream for later handles.
+void release_handle(rt_server* s, rt_handle* h)
+{
+    cudaStream_t st = h->stream;
+    rt_destroy(h);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (st) s->streams.push_back(st);
+}
+
+// Admission plan for request r: reuse the most recently pooled handle of its
+// grid size when that fits the budget beside the admitted requests (growing
+// only its source workspace), else a fresh handle. Returns the device bytes
+// the request will hold, or -1 while neither fits; *match is the pooled
+// handle to reuse, or -1.
+int64_t plan(const rt_server* s, const SrvReq* r, int* match)
+{
+    *match = -1;
+    int m = -1;
+    for (size_t i = 0; i < s->idle.size(); ++i)
+        if (s->idle[i].h->cfg.n == r->cfg.n && (m < 0 || s->idle[i].used > s->idle[(size_t)m].used)) m = (int)i;
+    if (m >= 0) {
+        const rt_handle* h = s->idle[(size_t)m].h;
+        const int64_t need = handle_bytes(h->cfg.n, h->cfg.precision, grown_cap(h->sw.cap, r->nsrc));
+        if (s->in_use + need <= s->budget) {
+            *match = m;
+            return need;
+        }
+    }
+    const int64_t need = handle_bytes(r->cfg.n, r->cfg.precision, grown_cap(0, r->nsrc));
+    return s->in_use + need <= s->budget ? need : -1;
+}
+
 void loader_main(rt_server* s)
 {
     cudaSetDevice(s->device);
     for (;;) {
         SrvReq* r = nullptr;
+        rt_handle* reuse = nullptr;
+        std::vector<rt_handle*> evict;
         cudaStream_t stream = nullptr;
         {
             std::unique_lock<std::mutex> lk(s->mu);
+            // admissible once the request fits beside the admitted ones: idle
+            // handles of other sizes are released to make room
             s->cv_load.wait(lk, [&] {
-                return s->stop || (!s->pending.empty() && s->in_use + s->pending.front()->mem <= s->budget);
+                if (s->stop) return true;
+                if (s->pending.empty()) return false;
+                int m = -1;
+                return plan(s, s->pending.front(), &m) >= 0;
             });
             if (s->stop) return;
             r = s->pending.front();
             s->pending.pop_front();
+            int m = -1;
+            r->mem = plan(s, r, &m);
+            if (m >= 0) {
+                reuse = s->idle[(size_t)m].h;
+                s->pooled -= s->idle[(size_t)m].mem;
+                s->idle.erase(s->idle.begin() + m);
+            }
+            while (s->in_use + s->pooled + r->mem > s->budget && !s->idle.empty()) {
+                size_t lru = 0;
+                for (size_t i = 1; i < s->idle.size(); ++i)
+                    if (s->idle[i].used < s->idle[lru].used) lru = i;
+                evict.push_back(s->idle[lru].h);
+                s->pooled -= s->idle[lru].mem;
+                s->idle.erase(s->idle.begin() + (long)lru);
+            }
             s->in_use += r->mem;
-            s->peak = std::max(s->peak, s->in_use);
+            s->peak = std::max(s->peak, s->in_use + s->pooled);
             r->state = kLoading;
-            stream = take_stream(s);
-            r->stream = stream;
+            s->wait_admit_ms += ms_since(s->t0) - r->t_submit;
+            if (!reuse) stream = take_stream(s);
         }
         const Clock::time_point tl = Clock::now();
-        int rc = stream ? RT_OK : RT_ECUDA;
-        std::string err = stream ? "" : "stream creation failed";
-        if (rc == RT_OK) {
+        trace(s, reuse ? "load_reuse" : "load_new", r->id, (double)r->mem);
+        for (rt_handle* h : evict) release_handle(s, h);
+        int rc = RT_OK;
+        std::string err;
+        if (reuse) {
+            r->h = reuse;
+            rc = handle_reconfigure(reuse, &r->cfg);
+        } else if (!stream) {
+            rc = RT_ECUDA;
+            err = "stream creation failed";
+        } else {
             rc = rt_create(&r->cfg, stream, &r->h);
-            if (rc) err = rt_last_error(nullptr);
+            if (rc) {
+                err = rt_last_error(nullptr);
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->streams.push_back(stream);
+            }
         }
+        // copies only: the source stage runs for the whole batch in the worker
+        trace(s, "handle_ready", r->id);
         if (rc == RT_OK) rc = rt_set_fields(r->h, r->nh, r->x, RT_HOST);
+        trace(s, "fields_copied", r->id);
         if (rc == RT_OK && r->nsrc > 0) rc = rt_add_sources(r->h, r->cells, r->ndot, r->nsrc, RT_HOST);
-        if (rc == RT_OK) rc = handle_prepare_sources(r->h);
+        trace(s, "loaded", r->id, (double)r->nsrc);
         if (rc != RT_OK && r->h && err.empty()) err = r->h->err;
         if (rc != RT_OK && r->h) {
-            rt_destroy(r->h);
+            release_handle(s, r->h);
             r->h = nullptr;
         }
         std::lock_guard<std::mutex> lk(s->mu);
@@ -165,6 +286,7 @@ void loader_main(rt_server* s)
             s->cv_load.notify_all();
         } else {
             r->state = kReady;
+            r->t_ready = ms_since(s->t0);
             s->ready.push_back(r);
             s->cv_work.notify_one();
         }
@@ -184,51 +306,84 @@ void worker_main(rt_server* s)
                 take.push_back(s->ready.front());
                 s->ready.pop_front();
             }
-            for (SrvReq* r : take) r->state = kRunning;
+            const double now = ms_since(s->t0);
+            for (SrvReq* r : take) {
+                r->state = kRunning;
+                s->wait_batch_ms += now - r->t_ready;
+            }
         }
+        const Clock::time_point tb = Clock::now();
+        for (SrvReq* r : take) trace(s, "batch_take", r->id, (double)take.size());
+        // ---- every request's source stage, enqueued back to back, one wait
+        std::vector<rt_handle*> all;
+        for (SrvReq* r : take) all.push_back(r->h);
+        std::vector<int> rcs(all.size(), RT_OK);
+        prepare_sources_many(all.data(), (int)all.size(), rcs.data());
+        const double src_ms = ms_since(tb);
+        trace(s, "src_done", -1, src_ms);
+        std::vector<SrvReq*> run, bad;
         std::vector<rt_handle*> hs;
-        for (SrvReq* r : take) hs.push_back(r->h);
+        for (size_t i = 0; i < take.size(); ++i) {
+            take[i]->rc = rcs[i];
+            if (rcs[i] != RT_OK) {
+                take[i]->err = take[i]->h->err;
+                bad.push_back(take[i]);
+            } else {
+                run.push_back(take[i]);
+                hs.push_back(take[i]->h);
+            }
+        }
         int rc = RT_OK;
         std::string err;
-        const Clock::time_point tb = Clock::now();
-        if (!s->batch) {
-            rc = rt_batch_create(hs.data(), (int32_t)hs.size(), nullptr, &s->batch);
-            if (rc == RT_OK) {
-                rt_batch_params p{};
-                rt_batch_get_params(s->batch, &p);
-                if (s->cfg.slice > 0) p.slice = s->cfg.slice;
-                if (s->cfg.group_bytes >= 0) p.group_bytes = s->cfg.group_bytes;
-                rc = rt_batch_set_params(s->batch, &p);
+        if (!hs.empty()) {
+            if (!s->batch) {
+                rc = rt_batch_create(hs.data(), (int32_t)hs.size(), nullptr, &s->batch);
+                if (rc == RT_OK) {
+                    rt_batch_params p{};
+                    rt_batch_get_params(s->batch, &p);
+                    if (s->cfg.slice > 0) p.slice = s->cfg.slice;
+                    if (s->cfg.group_bytes >= 0) p.group_bytes = s->cfg.group_bytes;
+                    rc = rt_batch_set_params(s->batch, &p);
+                }
+            } else {
+                rc = batch_bind(s->batch, hs.data(), (int32_t)hs.size());
             }
-        } else {
-            rc = batch_bind(s->batch, hs.data(), (int32_t)hs.size());
         }
         const double bind_ms = ms_since(tb);
         float ms = 0.f;
         const Clock::time_point tr = Clock::now();
-        if (rc == RT_OK) rc = batch_run_direct(s->batch, &ms);
+        if (rc == RT_OK && !hs.empty()) rc = batch_run_direct(s->batch, &ms);
         const double run_ms = ms_since(tr);
+        trace(s, "bind_done", -1, bind_ms);
+        trace(s, "run_done", -1, (double)ms);
         if (rc == RT_OK)
-            for (size_t i = 0; i < take.size(); ++i) batch_fill_stats(s->batch, i, ms, &take[i]->st);
+            for (size_t i = 0; i < run.size(); ++i) batch_fill_stats(s->batch, i, ms, &run[i]->st);
         if (rc != RT_OK) {
             err = s->batch ? rt_batch_last_error(s->batch) : "batch creation failed";
-            for (SrvReq* r : take) r->err = err;
+            for (SrvReq* r : run) {
+                r->rc = rc;
+                r->err = err;
+            }
         }
+        run.insert(run.end(), bad.begin(), bad.end());
         std::lock_guard<std::mutex> lk(s->mu);
         if (rc != RT_OK && s->batch) {       // a failed batch is rebuilt from scratch next time
             rt_batch_destroy(s->batch);
             s->batch = nullptr;
         }
-        ++s->batches;
+        if (!hs.empty()) ++s->batches;
         s->busy_ms += ms;
         s->bind_ms += bind_ms;
+        s->src_ms += src_ms;
         s->run_ms += run_ms;
-        s->finished.emplace_back(std::move(take), rc);
+        const double now = ms_since(s->t0);
+        for (SrvReq* r : run) r->t_traced = now;
+        s->finished.emplace_back(std::move(run), rc);
         s->cv_fin.notify_one();
     }
 }
 
-// Copy results out, release each request's device memory, mark it done
+// Copy results out, return each request's handle to the pool, mark it done
 // (two finisher threads share the queue of traced batches).
 void finisher_main(rt_server* s)
 {
@@ -241,31 +396,38 @@ void finisher_main(rt_server* s)
             if (s->finished.empty()) return;
             job = std::move(s->finished.front());
             s->finished.pop_front();
+            const double now = ms_since(s->t0);
+            for (SrvReq* r : job.first) s->wait_finish_ms += now - r->t_traced;
         }
-        int rc = job.second;
         for (SrvReq* r : job.first) {
             const Clock::time_point tf = Clock::now();
-            int rrc = rc;
+            trace(s, "fin_begin", r->id);
+            int rrc = r->rc;
             std::string err = rrc != RT_OK ? r->err : std::string();
+            rt_handle* h = r->h;
+            r->h = nullptr;
             if (rrc == RT_OK) {
-                const size_t fb = sizeof(double) * (size_t)r->h->ncell;
-                if ((r->gamma_out && cudaMemcpyAsync(r->gamma_out, r->h->d_gamma, fb, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess) ||
-                    (r->heat_out && cudaMemcpyAsync(r->heat_out, r->h->d_heat, fb, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess) ||
-                    cudaStreamSynchronize(r->stream) != cudaSuccess) {
+                const size_t fb = sizeof(double) * (size_t)h->ncell;
+                if ((r->gamma_out && cudaMemcpyAsync(r->gamma_out, h->d_gamma, fb, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) ||
+                    (r->heat_out && cudaMemcpyAsync(r->heat_out, h->d_heat, fb, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) ||
+                    cudaStreamSynchronize(h->stream) != cudaSuccess) {
                     cudaGetLastError();
                     rrc = RT_ECUDA;
                     err = "result copy failed";
                 }
             }
-            rt_destroy(r->h);
-            r->h = nullptr;
+            trace(s, "fin_copied", r->id);
+            const bool keep = rrc == RT_OK && !h->sticky;
+            if (!keep) release_handle(s, h);
             std::lock_guard<std::mutex> lk(s->mu);
+            if (keep) pool_put_locked(s, h);
             s->finish_ms += ms_since(tf);
             if (rrc == RT_OK)
                 for (int l = 0; l < RT_MAX_LEVELS; ++l) s->segments += r->st.segments[l];
             finish_locked(s, r, rrc, err);
             s->cv_done.notify_all();
             s->cv_load.notify_all();
+            trace(s, "done", r->id);
         }
     }
 }
@@ -295,6 +457,7 @@ int rt_server_create(const rt_server_config* cfg, rt_server** out)
         return RT_EINVAL;
     rt_server* s = new rt_server();
     s->cfg = *cfg;
+    if (const char* tp = std::getenv("NYXRT_SERVER_TRACE")) s->trace_path = tp;
     cudaGetDevice(&s->device);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
@@ -341,7 +504,7 @@ int rt_server_submit(rt_server* s, const rt_config* cfg, const double* n_H, cons
     r->nsrc = nsrc;
     r->gamma_out = gamma_out;
     r->heat_out = heat_out;
-    r->mem = request_bytes(*cfg, nsrc);
+    r->mem = handle_bytes(cfg->n, cfg->precision, grown_cap(0, nsrc));
     std::lock_guard<std::mutex> lk(s->mu);
     if (r->mem > s->budget) {
         delete r;
@@ -350,6 +513,7 @@ int rt_server_submit(rt_server* s, const rt_config* cfg, const double* n_H, cons
     }
     r->id = s->next_id++;
     r->t_submit = ms_since(s->t0);
+    trace(s, "submit", r->id, (double)cfg->n);
     s->reqs[r->id] = r;
     s->pending.push_back(r);
     ++s->submitted;
@@ -396,6 +560,10 @@ int rt_server_stats_get(rt_server* s, rt_server_stats* out)
     out->bind_ms = s->bind_ms;
     out->run_ms = s->run_ms;
     out->finish_ms = s->finish_ms;
+    out->src_ms = s->src_ms;
+    out->wait_admit_ms = s->wait_admit_ms;
+    out->wait_batch_ms = s->wait_batch_ms;
+    out->wait_finish_ms = s->wait_finish_ms;
     out->elapsed_ms = ms_since(s->t0);
     if (!s->lat.empty()) {
         std::vector<double> v = s->lat;
@@ -430,12 +598,25 @@ int rt_server_destroy(rt_server* s)
         if (t.joinable()) t.join();
     for (auto& kv : s->reqs) {
         SrvReq* r = kv.second;
-        if (r->h) rt_destroy(r->h);
-        if (r->stream) s->streams.push_back(r->stream);
+        if (r->h) {
+            s->streams.push_back(r->h->stream);
+            rt_destroy(r->h);
+        }
         delete r;
+    }
+    for (Idle& e : s->idle) {
+        s->streams.push_back(e.h->stream);
+        rt_destroy(e.h);
     }
     if (s->batch) rt_batch_destroy(s->batch);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    if (!s->trace_path.empty()) {
+        if (FILE* f = std::fopen(s->trace_path.c_str(), "a")) {
+            for (const TraceEv& e : s->trace) std::fprintf(f, "%.4f %s %lld %.6g\n", e.t, e.what, (long long)e.id, e.v);
+            std::fprintf(f, "---\n");
+            std::fclose(f);
+        }
+    }
     delete s;
     return RT_OK;
 }

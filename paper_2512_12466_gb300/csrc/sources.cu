@@ -7,6 +7,7 @@
 // are exact O(S^2) rank computations tiled through shared memory and the
 // pair test is a dense O(S^2) sweep; every per-group sum runs sequentially
 // in member order, so the emitted catalog is deterministic.
+#include <algorithm>
 #include <cstdint>
 
 #include "rt_internal.h"
@@ -355,6 +356,31 @@ __global__ void build_emit_kernel(const int32_t* __restrict__ cells, const doubl
     if ((threadIdx.x & 31) == 0) atomicAdd(&st->emitted, emitted);
 }
 
+// As build_emit_kernel, with the catalog size read from the device (after
+// dedup) so no host round trip is needed between dedup and emission.
+__global__ void build_emit_dev_kernel(const int32_t* __restrict__ cells, const double* __restrict__ ndot,
+                                      const int32_t* __restrict__ count, double s_over_dx2, SrcEntry* __restrict__ out,
+                                      DevStats* st)
+{
+    const int64_t m = *count;
+    double emitted = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        SrcEntry e;
+        e.cx = cells[3 * i];
+        e.cy = cells[3 * i + 1];
+        e.cz = cells[3 * i + 2];
+        e.pad = 0;
+        e.ph = __ddiv_rn(ndot[i], 12.0);
+        e.gd = __dmul_rn(e.ph, s_over_dx2);
+        e.gf = __double2float_rn(e.gd);
+        e.pad2 = 0.f;
+        out[i] = e;
+        emitted += ndot[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) emitted += __shfl_down_sync(0xffffffffu, emitted, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&st->emitted, emitted);
+}
+
 }  // namespace
 
 int launch_validate_sources(const int32_t* cells, const double* ndot, int64_t nsrc, int n, DevStats* st,
@@ -404,6 +430,15 @@ int launch_merge(SourceWork& w, int64_t m, int n, const double* x, const int4* s
     rank_kernel<<<b, kBlock, 0, s>>>(w.keys, m, w.order);
     gather_kernel<<<b, kBlock, 0, s>>>(w.order, m, w.cells_b, w.ndot_b, w.cells_a, w.ndot_a);
     return 12;
+}
+
+int launch_build_emit_dev(const SourceWork& w, int64_t max_m, double s_over_dx2, SrcEntry* out, DevStats* st,
+                          cudaStream_t s)
+{
+    if (max_m <= 0) return 0;
+    const int64_t g = std::min<int64_t>((max_m + kBlock - 1) / kBlock, 1024);
+    build_emit_dev_kernel<<<(int)g, kBlock, 0, s>>>(w.cells_a, w.ndot_a, w.count, s_over_dx2, out, st);
+    return 1;
 }
 
 int launch_build_emit(const SourceWork& w, int64_t m, double s_over_dx2, SrcEntry* out, DevStats* st,

@@ -298,6 +298,31 @@ def test_repeat_steps_are_reproducible(nyx):
     assert relerr(g1, g2) < 1e-14
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_reconfigured_handle_matches_the_oracle(nyx, prec):
+    # one handle re-targeted across boxes, thresholds, ray parameters and
+    # sources; each step against the oracle as a fresh handle would be
+    w0 = I.random_small(24, 6, seed=181, x_mode="mixed", box_cm=24 * 3e21)
+    s = nyx.Solver(w0.n, w0.box_cm, precision=prec, flags=nyx.RT_FLAG_VISIT_HASH, n_th_cm3=1e-4)
+    for j, (xm, dxc, kw) in enumerate([("patchy", 7e22, dict(overlap_mode=3, n_min_ray=8.0)),
+                                       ("thin", 7e20, dict(overlap_mode=1, tau_max=5.0)),
+                                       ("mixed", 3e21, dict(level_max=3))]):
+        w = I.random_small(24, 4 + 3 * j, seed=190 + j, x_mode=xm, box_cm=24 * dxc)
+        n_th = 0.3 * float(w.n_h.mean())
+        s.reconfigure(w.box_cm, flags=nyx.RT_FLAG_VISIT_HASH, n_th_cm3=n_th, **kw)
+        s.set_fields(w.n_h.ravel(), w.x_ion.ravel())
+        s.add_sources(w.cells.ravel(), w.ndot)
+        g, _, st = s.step()
+        ref = oracle.run(w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, n_th_cm3=n_th, precision=prec, **kw)
+        assert_bookkeeping(st, ref["stats"])
+        assert relerr(g, ref["gamma"]) < (1e-12 if prec == 0 else 1e-5)
+    with pytest.raises(nyx.NyxError):                # a different grid size does not fit the allocations
+        nyx.rt_reconfigure(s.h, nyx.rt_config_default(32, w0.box_cm, precision=prec))
+    with pytest.raises(nyx.NyxError):
+        s.reconfigure(w0.box_cm, precision=1 - prec)
+    s.close()
+
+
 # ---------------------------------------------------------------- workload-size cases
 
 def test_config2_thin_source_subset_parity(nyx):

@@ -126,3 +126,50 @@ def test_oversize_request_and_poll_states(nyx):
     rid = srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot)
     assert srv.poll(rid, wait_s=120.0) is not None
     srv.close()
+
+
+def test_bad_request_fails_alone_and_pooled_handles_are_reused(nyx):
+    # one request with x outside [0, 1] (caught by the device-side validation of
+    # the batched source stage) fails by itself; the others of its batch, and the
+    # later requests that reuse pooled handles of the same sizes, are unaffected
+    ws = requests(10, seed=41)
+    srv = nyx.Server(precision=1, max_batch=16)
+    ids = []
+    bad = 3
+    for j, w in enumerate(ws):
+        x = w.x_ion.copy()
+        if j == bad:
+            x.flat[5] = 1.5
+        ids.append(srv.submit(w.n, w.box_cm, w.n_h, x, w.cells, w.ndot, n_th_cm3=0.3 * float(w.n_h.mean()),
+                              flags=nyx.RT_FLAG_VISIT_HASH))
+    for j, (w, i) in enumerate(zip(ws, ids)):
+        if j == bad:
+            with pytest.raises(nyx.NyxError) as e:
+                srv.poll(i, wait_s=120.0)
+            assert e.value.code == nyx.RT_EINVAL
+        else:
+            check_same(nyx, srv.poll(i, wait_s=120.0), alone(nyx, w, 1, 0.3 * float(w.n_h.mean())))
+    again = requests(10, seed=43)                      # same size mix: served from the pool
+    ids = [srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot, n_th_cm3=0.3 * float(w.n_h.mean()),
+                      flags=nyx.RT_FLAG_VISIT_HASH) for w in again]
+    for w, i in zip(again, ids):
+        check_same(nyx, srv.poll(i, wait_s=120.0), alone(nyx, w, 1, 0.3 * float(w.n_h.mean())))
+    st = srv.stats()
+    srv.close()
+    assert st["failed"] == 1 and st["completed"] == 19
+
+
+def test_pool_evicts_under_a_tight_budget(nyx):
+    # a budget of about two of the largest requests with sizes alternating:
+    # idle handles of the other size must be released for each admission
+    ws = [I.random_small(n, 8, seed=500 + j, x_mode="patchy", box_cm=n * 2e22) for j, n in enumerate([48, 16, 48, 24, 16, 48, 24])]
+    budget = (48 ** 3 * 36 + 160 * 1024 + (1 << 16)) * 2
+    srv = nyx.Server(precision=1, max_batch=8, hbm_budget=budget)
+    ids = [srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot, n_th_cm3=0.3 * float(w.n_h.mean()),
+                      flags=nyx.RT_FLAG_VISIT_HASH) for w in ws]
+    got = [srv.poll(i, wait_s=120.0) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(ws) and st["mem_peak"] <= budget
+    for w, r in zip(ws, got):
+        check_same(nyx, r, alone(nyx, w, 1, 0.3 * float(w.n_h.mean())))
