@@ -560,7 +560,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="nyx", choices=["nyx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()
     if args.impl == "reference":

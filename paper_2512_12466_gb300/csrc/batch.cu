@@ -461,7 +461,7 @@ int rt_batch_create(rt_handle* const* handles, int32_t count, void* cuda_stream,
     if (rc) return rc;
     rt_batch_params p{};
     p.block = 256;
-    p.blocks_per_sm = std::max(1, std::min(2, max_blocks_per_sm(b, 256)));
+    p.blocks_per_sm = std::max(1, max_blocks_per_sm(b, 256));   // every block the kernel was built to fit
     p.tile = 256;
     p.slice = int64_t(1) << 22;
     p.group_bytes = int64_t(48) << 20;
@@ -510,7 +510,10 @@ int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best_out, doubl
     for (int64_t gb : groups)
     for (int bl : blocks) {
         const int occ = max_blocks_per_sm(b, bl);
-        for (int bps = 1; bps <= std::min(occ, 4); bps *= 2) {
+        std::vector<int> bpss;                       // 1, 2, 4 and full occupancy, each once
+        for (int v : {1, 2, 4, occ})
+            if (v <= occ && std::find(bpss.begin(), bpss.end(), v) == bpss.end()) bpss.push_back(v);
+        for (int bps : bpss) {
             for (int64_t sl : slices) {
                 for (int ti : tiles) {
                     rt_batch_params p{};

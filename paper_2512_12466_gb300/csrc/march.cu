@@ -522,9 +522,18 @@ __device__ __forceinline__ void flush_tally(Tally& T, unsigned mask, DevStats* c
     }
 }
 
+// Resident blocks of 256 threads per SM the march kernels are compiled for:
+// the FP32 march fits 80 registers without spilling, so three blocks (24
+// warps) hide more of its dependency latency than two; the FP64 march is held
+// by the FP64 pipe and would spill at that size.
+template <class R>
+struct MarchOccupancy {
+    static constexpr int blocks = sizeof(R) == 4 ? 3 : 2;
+};
+
 // One level (or one slice of it) of one solve: thread j marches child j.
 template <class R>
-__global__ void __launch_bounds__(256, 2) march_kernel(const MarchArgs<R> A)
+__global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(const MarchArgs<R> A)
 {
     const int l = A.level;
     const int lane = threadIdx.x & 31;
@@ -567,7 +576,7 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const MarchArgs<R> A)
 // so no buffer ever holds more than one slice's output. Only CUDA's grid barrier
 // is waited on: no block spins on another's flag.
 template <class R>
-__global__ void __launch_bounds__(256, 2) batch_kernel(const BatchArgs<R> A)
+__global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) batch_kernel(const BatchArgs<R> A)
 {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     const int lane = threadIdx.x & 31;
