@@ -41,6 +41,26 @@ FALLBACK_HBM = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 
 
+# DRAM traffic of the FP32 march from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over
+# all march launches of one step of the same box with its first 64 sources; profiles/march_fp32_config2_dram.md),
+# scaled to the full workload by primary segments. Valid only for the kernel sources it was taken on.
+TRAFFIC_CAPTURE = {"kernel": "march_kernel<float>", "bytes_per_segment": 0.37541880566138525,
+                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "38ff3bb0849b3cbb",
+                               "paper_2512_12466_gb300/csrc/rt_internal.h": "6877d171b8eb5677"}}
+
+
+def traffic_per_launch(segments_per_step: float, launches_per_step: float):
+    """Scaled DRAM bytes of the average march launch, or None once the kernel changed since the capture."""
+    import hashlib
+    for rel, h in TRAFFIC_CAPTURE["sources"].items():
+        try:
+            if hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16] != h:
+                return None
+        except OSError:
+            return None
+    return TRAFFIC_CAPTURE["bytes_per_segment"] * segments_per_step / max(1.0, launches_per_step)
+
+
 def load_peaks():
     try:
         p = json.load(open(PEAKS))
@@ -530,7 +550,10 @@ def run_nyx(args, world, rank, local):
         "rays_per_step": f32["rays_per_step"],
         "gpu_launches": f32["launches"],
         "roofline": {"bound": "hbm", "achieved": f32["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                     "frac": f32["achieved_gbs"] / hbm, "traffic": None,
+                     "frac": f32["achieved_gbs"] / hbm,
+                     "traffic": traffic_per_launch(f32["segments_per_step"], f32["march_launches_per_step"]),
+                     "algorithmic_bytes_per_launch": f32["achieved_gbs"] * 1e6 * f32["march_ms_per_step"]
+                     / max(1, f32["march_launches_per_step"]),
                      "kernel": "march_kernel<float>", "peak_kind": peak_kind,
                      "march_ms_per_step": f32["march_ms_per_step"],
                      "march_launches_per_step": f32["march_launches_per_step"]},
