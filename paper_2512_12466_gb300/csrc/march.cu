@@ -220,7 +220,9 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
     const unsigned long long rbase =
         V.hash ? mix64(((unsigned long long)(si - V.src_off) << 36) | ((unsigned long long)l << 31) | pix) : 0ULL;
 
-    R Ab = 0, cA = 0;           // photons absorbed by this ray (units of ph)
+    // photons this ray absorbs (units of ph) are its budget at the start less its budget at the end:
+    // the compensated budget P - cP, differenced in FP64
+    const double B0 = widen(P) - widen(cP);
     ++T.rays;
     const bool inside0 = (unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n;
     if (!inside0) {
@@ -301,8 +303,6 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
         }
         budget_add(tau, ctau, dtau);
         budget_add(P, cP, -a);
-        budget_add(Ab, cA, a);
-        ++T.seg;
         if (V.hash) T.hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
         ++seq;
     };
@@ -342,7 +342,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             if (tau >= taumax) {             // photons spent
                 ++T.dtau;
                 T.dropph += ph * (widen(P) - widen(cP));
-                T.abs += ph * (widen(Ab) - widen(cA));
+                T.abs += ph * (B0 - (widen(P) - widen(cP)));
                 alive = false;
                 break;
             }
@@ -358,7 +358,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
                 ++T.esc;
                 T.escph += ph * (widen(P) - widen(cP));
-                T.abs += ph * (widen(Ab) - widen(cA));
+                T.abs += ph * (B0 - (widen(P) - widen(cP)));
                 alive = false;
                 break;
             }
@@ -398,9 +398,9 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             if (tau >= taumax) {
                 ++T.dtau;
                 T.dropph += ph * (widen(P) - widen(cP));
-                T.abs += ph * (widen(Ab) - widen(cA));
+                T.abs += ph * (B0 - (widen(P) - widen(cP)));
             } else {
-                T.abs += ph * (widen(Ab) - widen(cA));
+                T.abs += ph * (B0 - (widen(P) - widen(cP)));
                 if (l + 1 > V.level_max) {
                     ++T.dlev;
                     T.dropph += ph * (widen(P) - widen(cP));
@@ -417,6 +417,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             }
         }
     }
+    T.seg += seq;
     return split;
 }
 
