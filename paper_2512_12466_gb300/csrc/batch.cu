@@ -127,6 +127,8 @@ int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count)
     a.counts = b->d_counts;
     a.tiles = b->d_tiles;
     a.max_slices = kMaxSlices;
+    a.any_hash = 0;
+    for (const BatchSolve& bs : b->hsolve) a.any_hash |= bs.hash;
     a.err = b->d_err;
     const int grid = b->sm_count * b->params.blocks_per_sm;
     cudaError_t e;

@@ -19,6 +19,8 @@
 // bookkeeping is reproducible operation by operation.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include <cstdint>
 
 #include "rt_internal.h"
@@ -42,7 +44,9 @@ struct Ieee<double> {
     __device__ __forceinline__ static double of(long long v) { return __ll2double_rn(v); }
     __device__ __forceinline__ static double small(unsigned v) { return __uint2double_rn(v); }
     __device__ __forceinline__ static double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
-    __device__ __forceinline__ static double em1(double x) { return expm1(x); }
+    __device__ __forceinline__ static double mn(double a, double b) { return fmin(a, b); }
+    // photons absorbed per unit budget over optical depth x >= 0: 1 - e^{-x}
+    __device__ __forceinline__ static double absorb(double x) { return -expm1(-x); }
     __device__ __forceinline__ static double qdiv(double a, double b) { return a / b; }
     __device__ __forceinline__ static bool neg(double x) { return __double_as_longlong(x) < 0; }
     __device__ __forceinline__ static double mag(double x) { return fabs(x); }
@@ -61,7 +65,24 @@ struct Ieee<float> {
         return __fsub_rn(__uint_as_float(0x4b000000u | v), 8388608.0f);
     }
     __device__ __forceinline__ static float pow2(int e) { return __int_as_float((127 + e) << 23); }
-    __device__ __forceinline__ static float em1(float x) { return expm1f(x); }
+    __device__ __forceinline__ static float mn(float a, float b) { return fminf(a, b); }
+    // 1 - e^{-x} for x >= 0. Below x = 1/4 the Taylor series of 1 - e^{-x} to x^7 (the
+    // alternating tail is below x^8/8! < 4e-10, i.e. < 2e-9 relative); above it
+    // 1 - __expf(-x), whose error (a few ulp of e^{-x} < 0.78) is below 1e-6 of the
+    // result. Both are evaluated and one selected, so lanes do not diverge.
+    __device__ __forceinline__ static float absorb(float x)
+    {
+        float p = 1.0f / 5040.0f;
+        p = fmaf(p, x, -1.0f / 720.0f);
+        p = fmaf(p, x, 1.0f / 120.0f);
+        p = fmaf(p, x, -1.0f / 24.0f);
+        p = fmaf(p, x, 1.0f / 6.0f);
+        p = fmaf(p, x, -0.5f);
+        p = fmaf(p, x, 1.0f);
+        const float series = p * x;
+        const float direct = 1.0f - __expf(-x);
+        return x < 0.25f ? series : direct;
+    }
     __device__ __forceinline__ static float qdiv(float a, float b) { return __fdividef(a, b); }
     __device__ __forceinline__ static bool neg(float x) { return __float_as_int(x) < 0; }
     __device__ __forceinline__ static float mag(float x) { return fabsf(x); }
@@ -99,24 +120,19 @@ __device__ __forceinline__ void budget_add(R& s, R& c, R v)
     }
 }
 
-// Exact float -> double widening with integer operations only: GB300's FP64
-// pipe is small, and a conversion per deposit would make it the bottleneck.
+// Exact float -> double widening with integer operations for normal numbers
+// (the deposits' case): GB300's FP64 pipe is small, and a conversion per
+// deposit there costs more than re-biasing the exponent and shifting the
+// mantissa. Zero, subnormals, infinities and NaN take the conversion.
 __device__ __forceinline__ double widen(float x)
 {
     const unsigned u = __float_as_uint(x);
-    const unsigned sign = u >> 31;
-    int e = (int)((u >> 23) & 0xffu);
-    unsigned m = u & 0x7fffffu;
-    if (e == 0) {
-        if (m == 0) return __longlong_as_double((long long)((unsigned long long)sign << 63));
-        const int sh = __clz(m) - 8;          // normalise a subnormal
-        m = (m << sh) & 0x7fffffu;
-        e = 1 - sh;
+    const unsigned mag = u & 0x7fffffffu;
+    if (mag - 0x00800000u < 0x7f000000u) {            // normal and finite
+        const unsigned hi = ((mag >> 3) + (896u << 20)) | (u & 0x80000000u);
+        return __hiloint2double((int)hi, (int)(u << 29));
     }
-    const unsigned long long bits = ((unsigned long long)sign << 63) |
-                                    ((unsigned long long)(unsigned)(e + 896) << 52) |
-                                    ((unsigned long long)m << 29);
-    return __longlong_as_double((long long)bits);
+    return (double)x;
 }
 __device__ __forceinline__ double widen(double x) { return x; }
 
@@ -164,7 +180,7 @@ struct SolveView {
 // start sphere to its split sphere, depositing into V.gamma and counting into
 // T. Returns true if the ray reached R_l and splits; its final P, tau (and
 // compensations) are then in oP, otau, ocP, octau.
-template <class R>
+template <class R, bool kHash>
 __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, const uint32_t si, const uint32_t pix,
                                           R P, R tau, R cP, R ctau, const SrcEntry& se, const int4 dv, Tally& T,
                                           R& oP, R& otau, float& ocP, float& octau)
@@ -218,7 +234,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
     const double ph = se.ph;
     const R taumax = V.tau_max;
     const unsigned long long rbase =
-        V.hash ? mix64(((unsigned long long)(si - V.src_off) << 36) | ((unsigned long long)l << 31) | pix) : 0ULL;
+        (kHash && V.hash) ? mix64(((unsigned long long)(si - V.src_off) << 36) | ((unsigned long long)l << 31) | pix) : 0ULL;
 
     // photons this ray absorbs (units of ph) are its budget at the start less its budget at the end:
     // the compensated budget P - cP, differenced in FP64
@@ -242,7 +258,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
         const R dtau = I::mul(kap, ds);
         R a, gseg;
         if (kap > (R)0) {
-            a = P * (-I::em1(-dtau));
+            a = P * I::absorb(dtau);
             gseg = I::qdiv(a * G, kap);
         } else {
             a = (R)0;
@@ -256,19 +272,10 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             const R d1 = I::add(dn1, I::mul(ds_p, u1));
             const R d2 = I::add(dn2, I::mul(ds_p, u2));
             const R o0 = I::sub((R)1, d0), o1 = I::sub((R)1, d1), o2 = I::sub((R)1, d2);
-            R dl[6];
-            dl[0] = s0 > 0 ? o0 : d0;
-            dl[1] = s0 > 0 ? d0 : o0;
-            dl[2] = s1 > 0 ? o1 : d1;
-            dl[3] = s1 > 0 ? d1 : o1;
-            dl[4] = s2 > 0 ? o2 : d2;
-            dl[5] = s2 > 0 ? d2 : o2;
-            int face = 0;
-            R De = dl[0];
-            #pragma unroll
-            for (int q = 1; q < 6; ++q) {
-                if (dl[q] < De) { De = dl[q]; face = q; }
-            }
+            // D_edge: the smallest of the six distances (a minimum is exact, so its value does
+            // not depend on the order); which face attains it is resolved below, only when needed
+            const R m0 = I::mn(d0, o0), m1 = I::mn(d1, o1), m2 = I::mn(d2, o2);
+            const R De = I::mn(I::mn(m0, m1), m2);
             const R tm = I::sub(tnext, I::mul(ds_p, (R)0.5));
             const R Lpix = I::mul(tm, Lc);
             if (I::add(De, De) < Lpix) {
@@ -278,9 +285,14 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
                     f = (R)0.5 + I::qdiv(De, Lpix);
                     f = f * f;
                 } else {
+                    // the first face, in the order x-, x+, y-, y+, z-, z+, at distance D_edge: the first
+                    // axis whose minimum is D_edge, and on it the upper face only if strictly nearer
+                    const int ax = m0 == De ? 0 : (m1 == De ? 1 : 2);
+                    const R dax = pick3(ax, d0, d1, d2), oax = pick3(ax, o0, o1, o2);
+                    const bool up = pick3(ax, s0, s1, s2) > 0;
+                    const int step = (up ? dax : oax) < (up ? oax : dax) ? 1 : -1;
                     int j0 = i0, j1 = i1, j2 = i2;
-                    const int step = (face & 1) ? 1 : -1;
-                    if ((face >> 1) == 0) j0 += step; else if ((face >> 1) == 1) j1 += step; else j2 += step;
+                    if (ax == 0) j0 += step; else if (ax == 1) j1 += step; else j2 += step;
                     if ((unsigned)j0 < (unsigned)n && (unsigned)j1 < (unsigned)n && (unsigned)j2 < (unsigned)n) {
                         const int c2 = (j2 * n + j1) * n + j0;
                         const R kn_raw = V.kap[c2];
@@ -303,7 +315,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
         }
         budget_add(tau, ctau, dtau);
         budget_add(P, cP, -a);
-        if (V.hash) T.hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
+        if (kHash && V.hash) T.hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
         ++seq;
     };
 
@@ -533,7 +545,8 @@ struct MarchOccupancy {
 };
 
 // One level (or one slice of it) of one solve: thread j marches child j.
-template <class R>
+// kHash: compiled with the visit hash (only launched when it is asked for).
+template <class R, bool kHash>
 __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(const MarchArgs<R> A)
 {
     const int l = A.level;
@@ -561,7 +574,7 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
         if (j < A.c1) {
             R P, tau, cP, ctau;
             load_ray<R>(l, j, A.in, si, pix, P, tau, cP, ctau);
-            split = march_ray<R>(V, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T, oP, otau, ocP, octau);
+            split = march_ray<R, kHash>(V, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T, oP, otau, ocP, octau);
         }
         append_split<R>(split, si, pix, oP, otau, ocP, octau, A.out, A.out_count, &A.st->err);
     }
@@ -576,7 +589,7 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
 // slices; the next level's slices run before the current level's remaining ones,
 // so no buffer ever holds more than one slice's output. Only CUDA's grid barrier
 // is waited on: no block spins on another's flag.
-template <class R>
+template <class R, bool kHash>
 __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) batch_kernel(const BatchArgs<R> A)
 {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
@@ -642,7 +655,7 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) batch_kernel(c
                     V.rq = bs.rq;
                     V.tau_max = (R)bs.tau_max;
                     V.src_off = bs.src_off - A.src_base;
-                    split = march_ray<R>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau, ocP, octau);
+                    split = march_ray<R, kHash>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau, ocP, octau);
                 }
                 append_split<R>(split, si, pix, oP, otau, ocP, octau, A.buf[l + 1], &A.counts[sid], A.err);
             }
@@ -665,13 +678,15 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) batch_kernel(c
 
 int launch_march_f64(const MarchArgs<double>& a, int grid, int block, cudaStream_t s)
 {
-    march_kernel<double><<<grid, block, 0, s>>>(a);
+    if (a.hash) march_kernel<double, true><<<grid, block, 0, s>>>(a);
+    else march_kernel<double, false><<<grid, block, 0, s>>>(a);
     return 1;
 }
 
 int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_t s)
 {
-    march_kernel<float><<<grid, block, 0, s>>>(a);
+    if (a.hash) march_kernel<float, true><<<grid, block, 0, s>>>(a);
+    else march_kernel<float, false><<<grid, block, 0, s>>>(a);
     return 1;
 }
 
@@ -679,7 +694,8 @@ template <class R>
 static cudaError_t launch_batch_impl(const BatchArgs<R>& a, int grid, int block, cudaStream_t s)
 {
     void* args[] = {const_cast<BatchArgs<R>*>(&a)};
-    return cudaLaunchCooperativeKernel((const void*)batch_kernel<R>, dim3(grid), dim3(block), args, 0, s);
+    const void* k = a.any_hash ? (const void*)batch_kernel<R, true> : (const void*)batch_kernel<R, false>;
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(block), args, 0, s);
 }
 
 cudaError_t launch_batch_f64(const BatchArgs<double>& a, int grid, int block, cudaStream_t s)
@@ -692,14 +708,19 @@ cudaError_t launch_batch_f32(const BatchArgs<float>& a, int grid, int block, cud
     return launch_batch_impl<float>(a, grid, block, s);
 }
 
+// Co-resident blocks per SM of the batch kernel: the smaller of its two
+// instantiations, so that a cooperative launch sized by it fits either.
 int batch_blocks_per_sm(int precision, int block)
 {
-    int nb = 0;
-    if (precision == RT_FP32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_kernel<float>, block, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_kernel<double>, block, 0);
-    return nb;
+    int a = 0, b = 0;
+    if (precision == RT_FP32) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, (const void*)batch_kernel<float, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)batch_kernel<float, true>, block, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, (const void*)batch_kernel<double, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)batch_kernel<double, true>, block, 0);
+    }
+    return std::min(a, b);
 }
 
 }  // namespace nyx

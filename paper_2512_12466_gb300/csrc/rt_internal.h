@@ -116,6 +116,7 @@ struct BatchArgs {
     unsigned long long* counts;      // per slice: next-level records written (zeroed)
     unsigned long long* tiles;       // per slice: tiles claimed (zeroed)
     int max_slices;
+    int any_hash;                    // some solve asks for the visit hash
     unsigned* err;
 };
 
