@@ -254,6 +254,39 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
         const R ds = I::mul(ds_p, nrm);
         const int cell = (i2 * n + i1) * n + i0;
         const R kraw = V.kap[cell];
+        // ---- geometry of the overlap correction first (it needs no kappa), so that the
+        // neighbour's kappa is requested while this cell's is still in flight
+        R De = (R)0, Lpix = (R)1;
+        bool near = false;
+        int c2 = -1;            // the cell across the nearest face (Arc / conservative modes), if in the domain
+        if (V.overlap_mode != RT_OVERLAP_NONE) {
+            // distances from the segment midpoint to the six faces, order x-, x+, y-, y+, z-, z+
+            const R d0 = I::add(dn0, I::mul(ds_p, u0));
+            const R d1 = I::add(dn1, I::mul(ds_p, u1));
+            const R d2 = I::add(dn2, I::mul(ds_p, u2));
+            const R o0 = I::sub((R)1, d0), o1 = I::sub((R)1, d1), o2 = I::sub((R)1, d2);
+            // D_edge: the smallest of the six distances (a minimum is exact, so its value does
+            // not depend on the order); which face attains it is resolved below, only when needed
+            const R m0 = I::mn(d0, o0), m1 = I::mn(d1, o1), m2 = I::mn(d2, o2);
+            De = I::mn(I::mn(m0, m1), m2);
+            const R tm = I::sub(tnext, I::mul(ds_p, (R)0.5));
+            Lpix = I::mul(tm, Lc);
+            near = I::add(De, De) < Lpix;
+            if (near && V.overlap_mode != RT_OVERLAP_LINEAR && V.overlap_mode != RT_OVERLAP_SQUARED) {
+                // the first face, in the order x-, x+, y-, y+, z-, z+, at distance D_edge: the first
+                // axis whose minimum is D_edge, and on it the upper face only if strictly nearer
+                const int ax = m0 == De ? 0 : (m1 == De ? 1 : 2);
+                const R dax = pick3(ax, d0, d1, d2), oax = pick3(ax, o0, o1, o2);
+                const bool up = pick3(ax, s0, s1, s2) > 0;
+                const int step = (up ? dax : oax) < (up ? oax : dax) ? 1 : -1;
+                int j0 = i0, j1 = i1, j2 = i2;
+                if (ax == 0) j0 += step; else if (ax == 1) j1 += step; else j2 += step;
+                if ((unsigned)j0 < (unsigned)n && (unsigned)j1 < (unsigned)n && (unsigned)j2 < (unsigned)n)
+                    c2 = (j2 * n + j1) * n + j0;
+            }
+        }
+        const R kn_raw = c2 >= 0 ? V.kap[c2] : (R)0;
+        // ---- Eq. 1 for this segment
         const R kap = I::mag(kraw);
         const R dtau = I::mul(kap, ds);
         R a, gseg;
@@ -264,47 +297,23 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             a = (R)0;
             gseg = (P * G) * ds;
         }
+        // ---- Eqs. 5-8: the share f kept in this cell and the neighbour's deposit
         R f = (R)1, g2 = (R)0;
         int nbcell = -1;
-        if (V.overlap_mode != RT_OVERLAP_NONE) {
-            // distances from the segment midpoint to the six faces, order x-, x+, y-, y+, z-, z+
-            const R d0 = I::add(dn0, I::mul(ds_p, u0));
-            const R d1 = I::add(dn1, I::mul(ds_p, u1));
-            const R d2 = I::add(dn2, I::mul(ds_p, u2));
-            const R o0 = I::sub((R)1, d0), o1 = I::sub((R)1, d1), o2 = I::sub((R)1, d2);
-            // D_edge: the smallest of the six distances (a minimum is exact, so its value does
-            // not depend on the order); which face attains it is resolved below, only when needed
-            const R m0 = I::mn(d0, o0), m1 = I::mn(d1, o1), m2 = I::mn(d2, o2);
-            const R De = I::mn(I::mn(m0, m1), m2);
-            const R tm = I::sub(tnext, I::mul(ds_p, (R)0.5));
-            const R Lpix = I::mul(tm, Lc);
-            if (I::add(De, De) < Lpix) {
-                if (V.overlap_mode == RT_OVERLAP_LINEAR) {
+        if (near) {
+            if (V.overlap_mode == RT_OVERLAP_LINEAR) {
+                f = (R)0.5 + I::qdiv(De, Lpix);
+            } else if (V.overlap_mode == RT_OVERLAP_SQUARED) {
+                f = (R)0.5 + I::qdiv(De, Lpix);
+                f = f * f;
+            } else if (c2 >= 0) {
+                const R kn = I::mag(kn_raw);
+                const bool elig = (V.overlap_mode == RT_OVERLAP_CONSERVATIVE) ? (!I::neg(kn_raw) && kn > (R)0)
+                                                                               : (kn > (R)0);
+                if (elig) {
                     f = (R)0.5 + I::qdiv(De, Lpix);
-                } else if (V.overlap_mode == RT_OVERLAP_SQUARED) {
-                    f = (R)0.5 + I::qdiv(De, Lpix);
-                    f = f * f;
-                } else {
-                    // the first face, in the order x-, x+, y-, y+, z-, z+, at distance D_edge: the first
-                    // axis whose minimum is D_edge, and on it the upper face only if strictly nearer
-                    const int ax = m0 == De ? 0 : (m1 == De ? 1 : 2);
-                    const R dax = pick3(ax, d0, d1, d2), oax = pick3(ax, o0, o1, o2);
-                    const bool up = pick3(ax, s0, s1, s2) > 0;
-                    const int step = (up ? dax : oax) < (up ? oax : dax) ? 1 : -1;
-                    int j0 = i0, j1 = i1, j2 = i2;
-                    if (ax == 0) j0 += step; else if (ax == 1) j1 += step; else j2 += step;
-                    if ((unsigned)j0 < (unsigned)n && (unsigned)j1 < (unsigned)n && (unsigned)j2 < (unsigned)n) {
-                        const int c2 = (j2 * n + j1) * n + j0;
-                        const R kn_raw = V.kap[c2];
-                        const R kn = I::mag(kn_raw);
-                        const bool elig = (V.overlap_mode == RT_OVERLAP_CONSERVATIVE) ? (!I::neg(kn_raw) && kn > (R)0)
-                                                                                       : (kn > (R)0);
-                        if (elig) {
-                            f = (R)0.5 + I::qdiv(De, Lpix);
-                            g2 = (((R)1 - f) * gseg) * I::qdiv(kap, kn);
-                            nbcell = c2;
-                        }
-                    }
+                    g2 = (((R)1 - f) * gseg) * I::qdiv(kap, kn);
+                    nbcell = c2;
                 }
             }
         }
