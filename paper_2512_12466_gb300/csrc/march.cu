@@ -250,10 +250,9 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
     // One segment of length ds_p (ray parameter) in the current cell, ending at parameter
     // tnext, where the distance to the exit face along axis b is dn_b: deposit Gamma (Eq. 1,
     // gray, V_box) with the overlap correction (Eqs. 5-8), then update the budgets.
-    auto segment = [&](R ds_p, R dn0, R dn1, R dn2, R tnext) {
+    auto segment = [&](const R kraw, R ds_p, R dn0, R dn1, R dn2, R tnext) {
         const R ds = I::mul(ds_p, nrm);
         const int cell = (i2 * n + i1) * n + i0;
-        const R kraw = V.kap[cell];
         // ---- geometry of the overlap correction first (it needs no kappa), so that the
         // neighbour's kappa is requested while this cell's is still in flight
         R De = (R)0, Lpix = (R)1;
@@ -343,6 +342,8 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             ds_p = I::mul(I::of(num), I::mul(pick3(w, h0, h1, h2), pV));
         }
         bool alive = true;
+        // kappa of the current cell; the loop requests the next cell's one iteration ahead
+        R kcur = V.kap[(i2 * n + i1) * n + i0];
         // ---- segments that end on a face crossing
         while (!is_end) {
             const R hw = pick3(w, h0, h1, h2);
@@ -359,7 +360,15 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
                 dn0 = I::mul(I::small(A02 - A20), invw);
                 dn1 = I::mul(I::small(A12 - A21), invw);
             }
-            segment(ds_p, dn0, dn1, dn2, I::mul(I::small(2u * kw + 1u), hw));
+            // the step after this segment: every axis whose crossing coincides with the winner's;
+            // the cell it leads to is known now, so its kappa is requested before the segment's work
+            const bool t0 = (w == 0) || (w == 1 ? A01 == A10 : A02 == A20);
+            const bool t1 = (w == 1) || (w == 0 ? A10 == A01 : A12 == A21);
+            const bool t2 = (w == 2) || (w == 0 ? A20 == A02 : A21 == A12);
+            const int ni0 = t0 ? i0 + s0 : i0, ni1 = t1 ? i1 + s1 : i1, ni2 = t2 ? i2 + s2 : i2;
+            const bool next_in = (unsigned)ni0 < (unsigned)n && (unsigned)ni1 < (unsigned)n && (unsigned)ni2 < (unsigned)n;
+            const R knext = next_in ? V.kap[(ni2 * n + ni1) * n + ni0] : (R)0;
+            segment(kcur, ds_p, dn0, dn1, dn2, I::mul(I::small(2u * kw + 1u), hw));
             if (tau >= taumax) {             // photons spent
                 ++T.dtau;
                 T.dropph += ph * (widen(P) - widen(cP));
@@ -367,16 +376,16 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
                 alive = false;
                 break;
             }
-            // step every axis whose crossing coincides with the winner's
-            const bool t0 = (w == 0) || (w == 1 ? A01 == A10 : A02 == A20);
-            const bool t1 = (w == 1) || (w == 0 ? A10 == A01 : A12 == A21);
-            const bool t2 = (w == 2) || (w == 0 ? A20 == A02 : A21 == A12);
-            if (t0) { ++k0; i0 += s0; A01 += 2u * D1; A02 += 2u * D2; }
-            if (t1) { ++k1; i1 += s1; A10 += 2u * D0; A12 += 2u * D2; }
-            if (t2) { ++k2; i2 += s2; A20 += 2u * D0; A21 += 2u * D1; }
+            if (t0) { ++k0; A01 += 2u * D1; A02 += 2u * D2; }
+            if (t1) { ++k1; A10 += 2u * D0; A12 += 2u * D2; }
+            if (t2) { ++k2; A20 += 2u * D0; A21 += 2u * D1; }
+            i0 = ni0;
+            i1 = ni1;
+            i2 = ni2;
+            kcur = knext;
             prev = w;
             kprev = kw;
-            if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
+            if (!next_in) {
                 ++T.esc;
                 T.escph += ph * (widen(P) - widen(cP));
                 T.abs += ph * (B0 - (widen(P) - widen(cP)));
@@ -415,7 +424,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             const R e0 = I::mul(I::of((long long)(2 * ke0 + 1) * kB - rq_end * (long long)D0), pE);
             const R e1 = I::mul(I::of((long long)(2 * ke1 + 1) * kB - rq_end * (long long)D1), pE);
             const R e2 = I::mul(I::of((long long)(2 * ke2 + 1) * kB - rq_end * (long long)D2), pE);
-            segment(ds_p, e0, e1, e2, I::mul((R)V.rq, I::pow2(l - F)));
+            segment(kcur, ds_p, e0, e1, e2, I::mul((R)V.rq, I::pow2(l - F)));
             if (tau >= taumax) {
                 ++T.dtau;
                 T.dropph += ph * (widen(P) - widen(cP));
