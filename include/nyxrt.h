@@ -93,6 +93,8 @@ typedef struct rt_config {
 } rt_config;
 
 #define RT_FLAG_VISIT_HASH 1   /* accumulate the visit-list hash in rt_stats (bookkeeping check) */
+#define RT_FLAG_NO_GEOMETRY_TABLE 2  /* FP32: walk every ray's cells instead of reading them from the
+                                        per-device geometry tables (same results; for comparison) */
 
 /* Step statistics, filled by rt_step (host memory, valid on return). */
 typedef struct rt_stats {

@@ -28,6 +28,7 @@ RT_HOST, RT_DEVICE = 0, 1
 RT_OVERLAP_NONE, RT_OVERLAP_LINEAR, RT_OVERLAP_ARC, RT_OVERLAP_CONSERVATIVE, RT_OVERLAP_SQUARED = 0, 1, 2, 3, 4
 RT_MERGE_OFF, RT_MERGE_FORCED, RT_MERGE_AUTO = 0, 1, 2
 RT_FLAG_VISIT_HASH = 1
+RT_FLAG_NO_GEOMETRY_TABLE = 2
 
 _ERRNAMES = {RT_EINVAL: "RT_EINVAL", RT_ENOMEM: "RT_ENOMEM", RT_ECUDA: "RT_ECUDA", RT_EDEVICE: "RT_EDEVICE",
              RT_ETIMEOUT: "RT_ETIMEOUT", RT_ESTATE: "RT_ESTATE", RT_EPENDING: "RT_EPENDING"}

@@ -301,16 +301,16 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
         int nbcell = -1;
         if (near) {
             if (V.overlap_mode == RT_OVERLAP_LINEAR) {
-                f = (R)0.5 + I::qdiv(De, Lpix);
+                f = I::add((R)0.5, I::qdiv(De, Lpix));
             } else if (V.overlap_mode == RT_OVERLAP_SQUARED) {
-                f = (R)0.5 + I::qdiv(De, Lpix);
+                f = I::add((R)0.5, I::qdiv(De, Lpix));
                 f = f * f;
             } else if (c2 >= 0) {
                 const R kn = I::mag(kn_raw);
                 const bool elig = (V.overlap_mode == RT_OVERLAP_CONSERVATIVE) ? (!I::neg(kn_raw) && kn > (R)0)
                                                                                : (kn > (R)0);
                 if (elig) {
-                    f = (R)0.5 + I::qdiv(De, Lpix);
+                    f = I::add((R)0.5, I::qdiv(De, Lpix));
                     g2 = (((R)1 - f) * gseg) * I::qdiv(kap, kn);
                     nbcell = c2;
                 }
@@ -451,6 +451,247 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
     return split;
 }
 
+// ---------------------------------------------------------------------------
+// Geometry tables. A ray's cells, segment lengths and overlap-correction
+// geometry relative to its source depend only on its level and pixel (every
+// source sits at a cell centre), so they are walked once per (level, pixel)
+// and stored; the table-driven march then does only what depends on the
+// data. The walker below takes the same integer steps and the same rounded
+// operations as march_ray, so both produce the same segments bit for bit.
+
+// One segment of a walk: its length ds_p (ray parameter), the exit point's distances dn_b to
+// the exit faces, the ray parameter where it ends, and the step that follows it (bit a: axis
+// a steps; none after the last segment) with the cell it leads to.
+template <class R>
+struct SegGeo {
+    R ds_p, dn0, dn1, dn2, tnext;
+    unsigned steps;
+    int ni0, ni1, ni2;
+    bool next_in;
+};
+
+enum { kWalkEnd = 0, kWalkEscaped = 1, kWalkStopped = 2 };
+
+// Exact integer traversal of one ray of level l (Amanatides-Woo on quantised
+// directions) from its start sphere R_{l-1} to its split sphere R_l, or out of
+// the grid [0, n)^3. The k-th face crossing along axis a is at ray parameter
+// T_a(k) = (2k+1) 2^20 / D_a, the split radius is R_l = Rq 2^l / 2^24, and the
+// next crossing on a comes before the one on b iff A_ab = (2 k_a + 1) D_b is
+// below A_ba, so every decision is an integer comparison and every segment
+// length an exact integer times a per-ray constant.
+template <class R>
+struct Walk {
+    unsigned D0, D1, D2;
+    int s0, s1, s2;
+    int k0, k1, k2, ke0, ke1, ke2;
+    unsigned A01, A10, A02, A20, A12, A21;
+    R nrm, h0, h1, h2, W01, W02, W12, u0, u1, u2, Lc;
+    int i0, i1, i2;          // the current cell
+
+    // Start cell of the ray from cell (c0, c1, c2): the cell holding its point on R_{l-1}.
+    __device__ __forceinline__ void init(const long long rq, const int l, const int4 dv, const int c0, const int c1,
+                                         const int c2)
+    {
+        using I = Ieee<R>;
+        const long long rq_end = rq << l;
+        const long long rq_start = l > 0 ? (rq << (l - 1)) : 0;
+        D0 = (unsigned)abs(dv.x);
+        D1 = (unsigned)abs(dv.y);
+        D2 = (unsigned)abs(dv.z);
+        s0 = dv.x < 0 ? -1 : 1;
+        s1 = dv.y < 0 ? -1 : 1;
+        s2 = dv.z < 0 ? -1 : 1;
+        // crossings done at the start sphere, and before the split sphere
+        k0 = k1 = k2 = 0;
+        if (l > 0) {
+            k0 = (int)((rq_start * D0 + kB) >> (S + F));
+            k1 = (int)((rq_start * D1 + kB) >> (S + F));
+            k2 = (int)((rq_start * D2 + kB) >> (S + F));
+        }
+        ke0 = (int)(((rq_end * D0 + kB - 1) >> (S - 1 + F)) >> 1);
+        ke1 = (int)(((rq_end * D1 + kB - 1) >> (S - 1 + F)) >> 1);
+        ke2 = (int)(((rq_end * D2 + kB - 1) >> (S - 1 + F)) >> 1);
+        i0 = c0 + s0 * k0;
+        i1 = c1 + s1 * k1;
+        i2 = c2 + s2 * k2;
+        // With k_a <= t D_a / 2^21 + 1/2 and D_a D_b <= 2^41, A_ab <= t 2^21 + 2^22, which stays
+        // below 2^32 while the ray parameter t is below 2040 (any point of a grid up to 1024^3).
+        A01 = (2u * k0 + 1u) * D1;
+        A10 = (2u * k1 + 1u) * D0;
+        A02 = (2u * k0 + 1u) * D2;
+        A20 = (2u * k2 + 1u) * D0;
+        A12 = (2u * k1 + 1u) * D2;
+        A21 = (2u * k2 + 1u) * D1;
+        // per-ray constants
+        if constexpr (sizeof(R) == 4) {
+            nrm = __int_as_float(dv.w);
+        } else {
+            const long long nn = (long long)D0 * D0 + (long long)D1 * D1 + (long long)D2 * D2;
+            nrm = __dmul_rn(__dsqrt_rn(__ll2double_rn(nn)), I::pow2(-S));
+        }
+        const R two20 = (R)(1 << (S - 1));
+        h0 = D0 ? I::div(two20, (R)D0) : (R)0;
+        h1 = D1 ? I::div(two20, (R)D1) : (R)0;
+        h2 = D2 ? I::div(two20, (R)D2) : (R)0;
+        W01 = (D0 && D1) ? I::div(h0, (R)D1) : (R)0;
+        W02 = (D0 && D2) ? I::div(h0, (R)D2) : (R)0;
+        W12 = (D1 && D2) ? I::div(h1, (R)D2) : (R)0;
+        const R pU = I::pow2(-(S + 1));
+        u0 = I::mul((R)D0, pU);
+        u1 = I::mul((R)D1, pU);
+        u2 = I::mul((R)D2, pU);
+        Lc = I::mul(I::mul(nrm, (R)kSqrtPiOver3), I::pow2(-l));
+    }
+
+    __device__ __forceinline__ bool inside(const int n) const
+    {
+        return (unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n;
+    }
+
+    // Walk from the (in-grid) start cell (rq and l as given to init). seg(g) is called for every
+    // segment of positive length, in order, with the walker's current cell being the segment's
+    // cell; it returns false to stop the ray. Returns kWalkEnd (R_l reached), kWalkEscaped (left
+    // the grid) or kWalkStopped.
+    template <class Seg>
+    __device__ __forceinline__ int run(const int n, const long long rq, const int l, Seg&& seg)
+    {
+        using I = Ieee<R>;
+        const long long rq_end = rq << l;
+        const long long rq_start = l > 0 ? (rq << (l - 1)) : 0;
+        const R pV = I::pow2(-(S - 1 + F)), pI = I::pow2(-S);
+        // first event: the smallest next crossing (ties x, y, z), or the split sphere
+        int w = 0;
+        if (A10 < A01) w = 1;
+        if (w == 0 ? (A20 < A02) : (A21 < A12)) w = 2;
+        int kw = pick3(w, k0, k1, k2);
+        bool is_end = !(kw < pick3(w, ke0, ke1, ke2));
+        int prev = -1, kprev = 0;
+        R ds_p = (R)0;
+        if (!is_end) {               // from the start sphere to the first crossing
+            const unsigned Dw = pick3(w, D0, D1, D2);
+            const long long num = (long long)(2 * kw + 1) * kB - rq_start * (long long)Dw;
+            ds_p = I::mul(I::of(num), I::mul(pick3(w, h0, h1, h2), pV));
+        }
+        // ---- segments that end on a face crossing
+        while (!is_end) {
+            const R hw = pick3(w, h0, h1, h2);
+            const R invw = I::mul(hw, pI);
+            SegGeo<R> g;
+            g.ds_p = ds_p;
+            // exit-point distance to the exit face along b: (A_bw - A_wb) / (2 D_w), 0 on b = w
+            g.dn0 = g.dn1 = g.dn2 = (R)0;
+            if (w == 0) {
+                g.dn1 = I::mul(I::small(A10 - A01), invw);
+                g.dn2 = I::mul(I::small(A20 - A02), invw);
+            } else if (w == 1) {
+                g.dn0 = I::mul(I::small(A01 - A10), invw);
+                g.dn2 = I::mul(I::small(A21 - A12), invw);
+            } else {
+                g.dn0 = I::mul(I::small(A02 - A20), invw);
+                g.dn1 = I::mul(I::small(A12 - A21), invw);
+            }
+            g.tnext = I::mul(I::small(2u * kw + 1u), hw);
+            // the step after this segment: every axis whose crossing coincides with the winner's
+            const bool t0 = (w == 0) || (w == 1 ? A01 == A10 : A02 == A20);
+            const bool t1 = (w == 1) || (w == 0 ? A10 == A01 : A12 == A21);
+            const bool t2 = (w == 2) || (w == 0 ? A20 == A02 : A21 == A12);
+            g.steps = (t0 ? 1u : 0u) | (t1 ? 2u : 0u) | (t2 ? 4u : 0u);
+            g.ni0 = t0 ? i0 + s0 : i0;
+            g.ni1 = t1 ? i1 + s1 : i1;
+            g.ni2 = t2 ? i2 + s2 : i2;
+            g.next_in = (unsigned)g.ni0 < (unsigned)n && (unsigned)g.ni1 < (unsigned)n && (unsigned)g.ni2 < (unsigned)n;
+            if (!seg(g)) return kWalkStopped;
+            if (t0) { ++k0; A01 += 2u * D1; A02 += 2u * D2; }
+            if (t1) { ++k1; A10 += 2u * D0; A12 += 2u * D2; }
+            if (t2) { ++k2; A20 += 2u * D0; A21 += 2u * D1; }
+            i0 = g.ni0;
+            i1 = g.ni1;
+            i2 = g.ni2;
+            prev = w;
+            kprev = kw;
+            if (!g.next_in) return kWalkEscaped;
+            // next event
+            w = 0;
+            if (A10 < A01) w = 1;
+            if (w == 0 ? (A20 < A02) : (A21 < A12)) w = 2;
+            kw = pick3(w, k0, k1, k2);
+            is_end = !(kw < pick3(w, ke0, ke1, ke2));
+            if (!is_end) {
+                if (prev == w) {
+                    const R h = pick3(w, h0, h1, h2);
+                    ds_p = I::add(h, h);
+                } else {
+                    // (2 k_w + 1) D_p - (2 k_prev + 1) D_w, with k_p = k_prev + 1 now; in [1, 2^22]
+                    const int pair = prev + w;
+                    const unsigned Dw = pick3(w, D0, D1, D2);
+                    const unsigned Awp = pair == 1 ? (w == 0 ? A01 : A10) : (pair == 2 ? (w == 0 ? A02 : A20) : (w == 1 ? A12 : A21));
+                    const unsigned Apw = pair == 1 ? (w == 0 ? A10 : A01) : (pair == 2 ? (w == 0 ? A20 : A02) : (w == 1 ? A21 : A12));
+                    ds_p = I::mul(I::small(Awp - (Apw - 2u * Dw)), pair == 1 ? W01 : (pair == 2 ? W02 : W12));
+                }
+            }
+        }
+        // ---- the last segment ends on the split sphere R_l, where k_b = kend_b on every axis
+        SegGeo<R> g;
+        if (prev < 0) {
+            g.ds_p = I::mul((R)rq, I::pow2(l > 0 ? l - 1 - F : -F));
+        } else {
+            const long long num = rq_end * (long long)pick3(prev, D0, D1, D2) - (long long)(2 * kprev + 1) * kB;
+            g.ds_p = I::mul(I::of(num), I::mul(pick3(prev, h0, h1, h2), pV));
+        }
+        const R pE = I::pow2(-(S + F));
+        g.dn0 = I::mul(I::of((long long)(2 * ke0 + 1) * kB - rq_end * (long long)D0), pE);
+        g.dn1 = I::mul(I::of((long long)(2 * ke1 + 1) * kB - rq_end * (long long)D1), pE);
+        g.dn2 = I::mul(I::of((long long)(2 * ke2 + 1) * kB - rq_end * (long long)D2), pE);
+        g.tnext = I::mul((R)rq, I::pow2(l - F));
+        g.steps = 0u;
+        g.ni0 = i0;
+        g.ni1 = i1;
+        g.ni2 = i2;
+        g.next_in = false;
+        if (!seg(g)) return kWalkStopped;
+        return kWalkEnd;
+    }
+};
+
+// The nearest face to a segment's midpoint (Eqs. 5-6 geometry): D_edge, L_pix, whether
+// 2 D_edge < L_pix, and (if face) the axis and side of the first face, in the order x-, x+,
+// y-, y+, z-, z+, at distance D_edge.
+template <class R>
+struct Edge {
+    R De, Lpix;
+    bool near;
+    int ax, step;
+};
+
+template <class R>
+__device__ __forceinline__ Edge<R> edge(const Walk<R>& W, const SegGeo<R>& g, const bool face)
+{
+    using I = Ieee<R>;
+    Edge<R> e;
+    // distances from the segment midpoint to the six faces, order x-, x+, y-, y+, z-, z+
+    const R d0 = I::add(g.dn0, I::mul(g.ds_p, W.u0));
+    const R d1 = I::add(g.dn1, I::mul(g.ds_p, W.u1));
+    const R d2 = I::add(g.dn2, I::mul(g.ds_p, W.u2));
+    const R o0 = I::sub((R)1, d0), o1 = I::sub((R)1, d1), o2 = I::sub((R)1, d2);
+    // D_edge: the smallest of the six distances (a minimum is exact, so its value does
+    // not depend on the order); which face attains it is resolved only when needed
+    const R m0 = I::mn(d0, o0), m1 = I::mn(d1, o1), m2 = I::mn(d2, o2);
+    e.De = I::mn(I::mn(m0, m1), m2);
+    const R tm = I::sub(g.tnext, I::mul(g.ds_p, (R)0.5));
+    e.Lpix = I::mul(tm, W.Lc);
+    e.near = I::add(e.De, e.De) < e.Lpix;
+    e.ax = 0;
+    e.step = 0;
+    if (face && e.near) {
+        // the first axis whose minimum is D_edge, and on it the upper face only if strictly nearer
+        e.ax = m0 == e.De ? 0 : (m1 == e.De ? 1 : 2);
+        const R dax = pick3(e.ax, d0, d1, d2), oax = pick3(e.ax, o0, o1, o2);
+        const bool up = pick3(e.ax, W.s0, W.s1, W.s2) > 0;
+        e.step = (up ? dax : oax) < (up ? oax : dax) ? 1 : -1;
+    }
+    return e;
+}
+
 // Warp-aggregated append of the rays that split (Alg. 1 FILTERCOPYTRANSFORM<3>): one
 // atomic per warp reserves the records; each splitting lane writes its parent record.
 template <class R>
@@ -479,6 +720,213 @@ __device__ __forceinline__ void append_split(bool split, uint32_t si, uint32_t p
             atomicOr(err, kErrRayOverflow);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Geometry-table generation and the table-driven FP32 march.
+//
+// Entry of segment s of pixel p (8 bytes): x = the FP32 segment length ds (ds_p times the
+// direction norm, rounded as in march_ray); y = bits 0-23: the share f kept in the cell when the
+// segment is near an edge (Eq. 6), as its float bit pattern less that of 0.5 - 2^-21 (f is
+// 0.5 + D_edge / L_pix, in [0.5 - 2^-21, 1] including rounding); bits 24-26: the axes that step
+// after the segment (none after the one ending on R_l); bit 27: 2 D_edge < L_pix; bits 28-29:
+// axis of the nearest face; bit 30: the nearest face is the upper one; bit 31: the pixel's last
+// entry. Entries are stored by blocks of 32 consecutive pixels, segment-major within a block, so
+// the four children of a parent (adjacent lanes) read one 32-byte sector per segment.
+
+constexpr unsigned kFBase = 0x3efffff0u;     // float bits of 0.5 - 2^-21
+
+// Walk pixel p of level l from a source at the centre of a virtual grid of 2 n_cover - 1
+// cells: a cell offset of n_cover or more along any axis lies outside every n_cover^3 grid
+// for every source cell, so that is where the table of the pixel may stop.
+__device__ __forceinline__ void geom_walk_init(Walk<float>& W, const long long rq, const int l, const int4 dv,
+                                               const int n_cover)
+{
+    W.init(rq, l, dv, n_cover - 1, n_cover - 1, n_cover - 1);
+}
+
+__global__ void __launch_bounds__(256) geom_count_kernel(const long long rq, const int l, const int4* __restrict__ dirs,
+                                                         const long long npix, const int n_cover,
+                                                         unsigned* __restrict__ rows)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    unsigned cnt = 0;
+    if (p < npix) {
+        Walk<float> W;
+        geom_walk_init(W, rq, l, dirs[p], n_cover);
+        const int nv = 2 * n_cover - 1;
+        if (W.inside(nv)) W.run(nv, rq, l, [&](const SegGeo<float>&) -> bool { ++cnt; return true; });
+    }
+    // rows of a 32-pixel block: the longest column in it
+    for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(0xffffffffu, cnt, o));
+    if ((threadIdx.x & 31) == 0 && p < npix) rows[p >> 5] = cnt;
+}
+
+__global__ void __launch_bounds__(256) geom_fill_kernel(const long long rq, const int l, const int4* __restrict__ dirs,
+                                                        const long long npix, const int n_cover,
+                                                        const unsigned long long* __restrict__ row0,
+                                                        uint2* __restrict__ ent, unsigned* err)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    Walk<float> W;
+    geom_walk_init(W, rq, l, dirs[p], n_cover);
+    const int nv = 2 * n_cover - 1;
+    if (!W.inside(nv)) return;
+    uint2* col = ent + row0[p >> 5] * 32 + (p & 31);
+    unsigned long long s = 0;
+    W.run(nv, rq, l, [&](const SegGeo<float>& g) -> bool {
+        const Edge<float> e = edge<float>(W, g, true);
+        unsigned y = g.steps << 24;
+        if (e.near) {
+            const float f = __fadd_rn(0.5f, __fdividef(e.De, e.Lpix));
+            const unsigned code = __float_as_uint(f) - kFBase;
+            if (code > 0xffffffu) atomicOr(err, kErrGeometry);
+            y |= (code & 0xffffffu) | (1u << 27) | ((unsigned)e.ax << 28) | (e.step > 0 ? (1u << 30) : 0u);
+        }
+        if (g.steps == 0u || !g.next_in) y |= 1u << 31;
+        col[s * 32] = make_uint2(__float_as_uint(__fmul_rn(g.ds_p, W.nrm)), y);
+        ++s;
+        return true;
+    });
+}
+
+// march_ray with the geometry read from the level's table (FP32 physics).
+template <bool kHash>
+__device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const GeomLevel& GL, unsigned* err, const int l,
+                                                const uint32_t si, const uint32_t pix, float P, float tau, float cP,
+                                                float ctau, const SrcEntry& se, const int4 dv, Tally& T, float& oP,
+                                                float& otau, float& ocP, float& octau)
+{
+    using I = Ieee<float>;
+    const int n = V.n;
+    const int s0 = dv.x < 0 ? -1 : 1, s1 = dv.y < 0 ? -1 : 1, s2 = dv.z < 0 ? -1 : 1;
+    int i0 = se.cx, i1 = se.cy, i2 = se.cz;
+    if (l > 0) {                    // the start cell: crossings done at the start sphere
+        const long long rq_start = V.rq << (l - 1);
+        i0 += s0 * (int)((rq_start * (unsigned)abs(dv.x) + kB) >> (S + F));
+        i1 += s1 * (int)((rq_start * (unsigned)abs(dv.y) + kB) >> (S + F));
+        i2 += s2 * (int)((rq_start * (unsigned)abs(dv.z) + kB) >> (S + F));
+    }
+    const float G = se.gf;
+    const double ph = se.ph;
+    const float taumax = V.tau_max;
+    const unsigned long long rbase =
+        (kHash && V.hash) ? mix64(((unsigned long long)(si - V.src_off) << 36) | ((unsigned long long)l << 31) | pix) : 0ULL;
+    const bool face = V.overlap_mode == RT_OVERLAP_ARC || V.overlap_mode == RT_OVERLAP_CONSERVATIVE;
+    const bool corr = V.overlap_mode != RT_OVERLAP_NONE;
+    const long long nn = (long long)n * n;
+    const double B0 = widen(P) - widen(cP);
+    ++T.rays;
+    if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
+        ++T.esc;
+        T.escph += ph * (widen(P) - widen(cP));
+        return false;
+    }
+    const uint2* col = GL.ent + GL.row0[pix >> 5] * 32 + (pix & 31);
+    uint2 e = col[0];
+    int cell = (i2 * n + i1) * n + i0;
+    float kcur = V.kap[cell];
+    unsigned seq = 0;
+    bool split = false;
+    for (;;) {
+        // the next entry and the next cell's kappa are requested before this segment's work
+        const bool last = (e.y >> 31) != 0u;
+        const uint2 en = last ? make_uint2(0u, 0u) : col[(unsigned long long)(seq + 1) * 32];
+        const unsigned steps = (e.y >> 24) & 7u;
+        const int ni0 = (steps & 1u) ? i0 + s0 : i0;
+        const int ni1 = (steps & 2u) ? i1 + s1 : i1;
+        const int ni2 = (steps & 4u) ? i2 + s2 : i2;
+        const bool next_in = (unsigned)ni0 < (unsigned)n && (unsigned)ni1 < (unsigned)n && (unsigned)ni2 < (unsigned)n;
+        const int ncell = (ni2 * n + ni1) * n + ni0;
+        const float knext = (steps && next_in) ? V.kap[ncell] : 0.f;
+        const bool near = corr && ((e.y >> 27) & 1u);
+        int c2 = -1;
+        if (face && near) {
+            const int ax = (int)((e.y >> 28) & 3u);
+            const int step = ((e.y >> 30) & 1u) ? 1 : -1;
+            const int jc = pick3(ax, i0, i1, i2) + step;
+            if ((unsigned)jc < (unsigned)n) c2 = cell + step * (ax == 0 ? 1 : (ax == 1 ? n : (int)nn));
+        }
+        const float kn_raw = c2 >= 0 ? V.kap[c2] : 0.f;
+        // ---- Eq. 1 for this segment
+        const float ds = __uint_as_float(e.x);
+        const float kap = I::mag(kcur);
+        const float dtau = I::mul(kap, ds);
+        float a, gseg;
+        if (kap > 0.f) {
+            a = P * I::absorb(dtau);
+            gseg = I::qdiv(a * G, kap);
+        } else {
+            a = 0.f;
+            gseg = (P * G) * ds;
+        }
+        // ---- Eqs. 5-8
+        float f = 1.f, g2 = 0.f;
+        int nbcell = -1;
+        if (near) {
+            const float fn = __uint_as_float((e.y & 0xffffffu) + kFBase);
+            if (V.overlap_mode == RT_OVERLAP_LINEAR) {
+                f = fn;
+            } else if (V.overlap_mode == RT_OVERLAP_SQUARED) {
+                f = fn * fn;
+            } else if (c2 >= 0) {
+                const float kn = I::mag(kn_raw);
+                const bool elig = (V.overlap_mode == RT_OVERLAP_CONSERVATIVE) ? (!I::neg(kn_raw) && kn > 0.f) : (kn > 0.f);
+                if (elig) {
+                    f = fn;
+                    g2 = ((1.f - f) * gseg) * I::qdiv(kap, kn);
+                    nbcell = c2;
+                }
+            }
+        }
+        atomicAdd(&V.gamma[cell], widen(f * gseg));
+        if (nbcell >= 0) {
+            atomicAdd(&V.gamma[nbcell], widen(g2));
+            ++T.sec;
+        }
+        budget_add(tau, ctau, dtau);
+        budget_add(P, cP, -a);
+        if (kHash && V.hash) T.hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
+        ++seq;
+        if (tau >= taumax) {             // photons spent
+            ++T.dtau;
+            T.dropph += ph * (widen(P) - widen(cP));
+            break;
+        }
+        if (!steps) {                    // the segment ended on R_l
+            if (l + 1 > V.level_max) {
+                ++T.dlev;
+                T.dropph += ph * (widen(P) - widen(cP));
+            } else {
+                ++T.split;
+                split = true;
+                oP = P;
+                otau = tau;
+                ocP = cP;
+                octau = ctau;
+            }
+            break;
+        }
+        if (!next_in) {
+            ++T.esc;
+            T.escph += ph * (widen(P) - widen(cP));
+            break;
+        }
+        if (last) {                      // cannot happen: a table ends where every grid is left
+            atomicOr(err, kErrGeometry);
+            break;
+        }
+        i0 = ni0;
+        i1 = ni1;
+        i2 = ni2;
+        cell = ncell;
+        kcur = knext;
+        e = en;
+    }
+    T.seg += seq;
+    T.abs += ph * (B0 - (widen(P) - widen(cP)));
+    return split;
 }
 
 // Load child j of the level-l parents (level 0: ray j of the emission, 12 per source).
@@ -600,6 +1048,44 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
     flush_tally(T, 0xffffffffu, &st, l);
 }
 
+// One level (or one slice of it) of one solve, FP32, geometry from the level's table.
+template <bool kHash>
+__global__ void __launch_bounds__(256, MarchOccupancy<float>::blocks) march_table_kernel(const MarchArgs<float> A,
+                                                                                       const GeomLevel GL)
+{
+    const int l = A.level;
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = (long long)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarp = (long long)(gridDim.x * blockDim.x) >> 5;
+    SolveView<float> V;
+    V.kap = A.kap;
+    V.gamma = A.gamma;
+    V.n = A.n;
+    V.level_max = A.level_max;
+    V.overlap_mode = A.overlap_mode;
+    V.hash = A.hash;
+    V.rq = A.rq;
+    V.tau_max = A.tau_max;
+    V.src_off = 0;
+    Tally T;
+    T.clear();
+    for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
+        const long long j = base + lane;
+        bool split = false;
+        uint32_t si = 0, pix = 0;
+        float oP = 0.f, otau = 0.f, ocP = 0.f, octau = 0.f;
+        if (j < A.c1) {
+            float P, tau, cP, ctau;
+            load_ray<float>(l, j, A.in, si, pix, P, tau, cP, ctau);
+            split = march_ray_table<kHash>(V, GL, &A.st->err, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T,
+                                           oP, otau, ocP, octau);
+        }
+        append_split<float>(split, si, pix, oP, otau, ocP, octau, A.out, A.out_count, &A.st->err);
+    }
+    DevStats* st = A.st;
+    flush_tally(T, 0xffffffffu, &st, l);
+}
+
 // All solves of a batch in one cooperative launch. Every block runs the same
 // depth-first schedule over (level, slice of children): a slice's children are
 // claimed in tiles by warps through a device counter (the work queue), the
@@ -706,6 +1192,27 @@ int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_
     if (a.hash) march_kernel<float, true><<<grid, block, 0, s>>>(a);
     else march_kernel<float, false><<<grid, block, 0, s>>>(a);
     return 1;
+}
+
+int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int grid, int block, cudaStream_t s)
+{
+    if (a.hash) march_table_kernel<true><<<grid, block, 0, s>>>(a, g);
+    else march_table_kernel<false><<<grid, block, 0, s>>>(a, g);
+    return 1;
+}
+
+void launch_geom_count(long long rq, int l, const int4* dirs, long long npix, int n_cover, unsigned* rows,
+                       cudaStream_t s)
+{
+    const long long grid = (npix + 255) / 256;
+    geom_count_kernel<<<(unsigned)grid, 256, 0, s>>>(rq, l, dirs, npix, n_cover, rows);
+}
+
+void launch_geom_fill(long long rq, int l, const int4* dirs, long long npix, int n_cover,
+                      const unsigned long long* row0, uint2* ent, unsigned* err, cudaStream_t s)
+{
+    const long long grid = (npix + 255) / 256;
+    geom_fill_kernel<<<(unsigned)grid, 256, 0, s>>>(rq, l, dirs, npix, n_cover, row0, ent, err);
 }
 
 template <class R>

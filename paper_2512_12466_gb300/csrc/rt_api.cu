@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -78,6 +79,108 @@ int nyx::ensure_directions(int device, int level, const int4** out, std::string&
     return RT_OK;
 }
 
+
+namespace {
+
+// Geometry tables (FP32 march): one per (device, split radius, level, grid size covered). A
+// table is never freed while the process runs (handles on other streams may be reading it);
+// a larger grid gets a new one. Their total per device stays within a budget, by default an
+// eighth of the device's memory (NYXRT_GEOMETRY_BUDGET_MB overrides it); a level that does
+// not fit is marched by walking its rays instead.
+struct GeomTable {
+    long long rq;
+    int level;
+    int n_cover;
+    bool complete;            // no pixel cut short: serves every grid size
+    bool usable;
+    nyx::GeomLevel g;
+};
+std::mutex g_geom_mu;
+std::map<int, std::vector<GeomTable>> g_geom;
+std::map<int, size_t> g_geom_bytes;
+
+size_t geometry_budget(int device)
+{
+    if (const char* e = std::getenv("NYXRT_GEOMETRY_BUDGET_MB")) return (size_t)std::strtoull(e, nullptr, 10) << 20;
+    size_t free_b = 0, total_b = 0;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != device) cudaSetDevice(device);
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        total_b = 0;
+    }
+    if (cur != device) cudaSetDevice(cur);
+    return total_b / 8;
+}
+
+}  // namespace
+
+bool nyx::geometry_level(int device, long long rq, int level, int n, const int4* dirs_level, cudaStream_t s,
+                         GeomLevel* out)
+{
+    std::lock_guard<std::mutex> lk(g_geom_mu);
+    std::vector<GeomTable>& list = g_geom[device];
+    for (const GeomTable& t : list)
+        if (t.rq == rq && t.level == level && (t.complete || t.n_cover >= n)) {
+            if (t.usable) *out = t.g;
+            return t.usable;
+        }
+    GeomTable t{rq, level, n, false, false, GeomLevel()};
+    // every ray reaches R_l inside the virtual grid of 2n - 1 cells when R_l + 1 < n
+    t.complete = std::ldexp((double)rq, level - kRadBits) + 2.0 < (double)n;
+    const long long npix = 12LL << (2 * level);
+    const long long nb = (npix + 31) / 32;
+    unsigned* d_rows = nullptr;
+    unsigned* d_err = nullptr;
+    uint2* ent = nullptr;
+    unsigned long long* row0 = nullptr;
+    std::vector<unsigned> rows((size_t)nb);
+    std::vector<unsigned long long> off((size_t)nb);
+    unsigned herr = 0;
+    bool ok = cudaMalloc(&d_rows, sizeof(unsigned) * (size_t)nb) == cudaSuccess &&
+              cudaMalloc(&d_err, sizeof(unsigned)) == cudaSuccess;
+    if (ok) {
+        launch_geom_count(rq, level, dirs_level, npix, n, d_rows, s);
+        ok = cudaMemcpyAsync(rows.data(), d_rows, sizeof(unsigned) * (size_t)nb, cudaMemcpyDeviceToHost, s) ==
+                 cudaSuccess &&
+             cudaStreamSynchronize(s) == cudaSuccess;
+    }
+    unsigned long long total = 0;
+    for (long long b = 0; ok && b < nb; ++b) {
+        off[(size_t)b] = total;
+        total += rows[(size_t)b];
+    }
+    const size_t bytes = (size_t)total * 32 * sizeof(uint2) + sizeof(unsigned long long) * (size_t)nb;
+    ok = ok && g_geom_bytes[device] + bytes <= geometry_budget(device);
+    if (ok) {
+        ok = cudaMalloc(&ent, std::max<size_t>(16, (size_t)total * 32 * sizeof(uint2))) == cudaSuccess &&
+             cudaMalloc(&row0, sizeof(unsigned long long) * (size_t)nb) == cudaSuccess &&
+             cudaMemcpyAsync(row0, off.data(), sizeof(unsigned long long) * (size_t)nb, cudaMemcpyHostToDevice, s) ==
+                 cudaSuccess &&
+             cudaMemsetAsync(d_err, 0, sizeof(unsigned), s) == cudaSuccess;
+    }
+    if (ok) {
+        launch_geom_fill(rq, level, dirs_level, npix, n, row0, ent, d_err, s);
+        ok = cudaMemcpyAsync(&herr, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+             cudaStreamSynchronize(s) == cudaSuccess && herr == 0;
+    }
+    cudaGetLastError();
+    cudaFree(d_rows);
+    cudaFree(d_err);
+    if (ok) {
+        t.usable = true;
+        t.g.ent = ent;
+        t.g.row0 = row0;
+        g_geom_bytes[device] += bytes;
+        *out = t.g;
+    } else {
+        cudaFree(ent);
+        cudaFree(row0);
+    }
+    list.push_back(t);
+    return t.usable;
+}
 
 namespace nyx {
 
@@ -208,9 +311,17 @@ int run_level(rt_handle* h, int level, int64_t nparents)
         const int64_t warps = (c1 - c0 + 31) / 32;
         const int64_t want = (warps + kMarchBlock / 32 - 1) / (kMarchBlock / 32);
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->sm_count * 8));
+        // FP32: the level's geometry table (built once per device, outside the timed launch)
+        GeomLevel gl;
+        const bool table = sizeof(R) == 4 && !(h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE) &&
+                           geometry_level(h->device, h->rq, level, h->cfg.n, a.dirs, h->stream, &gl);
         RT_CUDA(h, cudaEventRecord(h->ev[4], h->stream), "event");
-        if constexpr (sizeof(R) == 8) launch_march_f64(a, grid, kMarchBlock, h->stream);
-        else launch_march_f32(a, grid, kMarchBlock, h->stream);
+        if constexpr (sizeof(R) == 8) {
+            launch_march_f64(a, grid, kMarchBlock, h->stream);
+        } else {
+            if (table) launch_march_table_f32(a, gl, grid, kMarchBlock, h->stream);
+            else launch_march_f32(a, grid, kMarchBlock, h->stream);
+        }
         RT_LAUNCHED(h, "march launch");
         RT_CUDA(h, cudaEventRecord(h->ev[5], h->stream), "event");
         h->launches++;

@@ -123,6 +123,10 @@ int fail(rt_handle* h, int code, const std::string& msg);
 int cuda_fail(rt_handle* h, cudaError_t e, const char* what);
 int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out);
 int ensure_directions(int device, int level, const int4** out, std::string& err);
+// The geometry table of a level for grids of n cells (FP32 march), built on stream s if needed;
+// false if the level has none (over the device's table budget), so its rays are walked.
+bool geometry_level(int device, long long rq, int level, int n, const int4* dirs_level, cudaStream_t s,
+                    GeomLevel* out);
 int handle_prepare_sources(rt_handle* h);
 int handle_reconfigure(rt_handle* h, const rt_config* cfg);
 int prepare_sources_many(rt_handle* const* hs, int count, int* rcs);

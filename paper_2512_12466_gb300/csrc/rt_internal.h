@@ -51,6 +51,7 @@ enum : unsigned {
     kErrRayOverflow = 1u,            // next-level ray buffer too small
     kErrUnionFind = 2u,              // union-find retry cap reached
     kErrLevel = 4u,                  // a ray exceeded the direction table
+    kErrGeometry = 8u,               // a geometry-table entry could not be encoded or ran out
 };
 
 // Ray records between levels (structure of arrays). A record is a parent
@@ -85,6 +86,13 @@ struct MarchArgs {
     int overlap_mode;
     int hash;
     DevStats* st;
+};
+
+// Geometry table of one level (FP32 march): 8-byte entries, entry s of pixel p at
+// ent[(row0[p / 32] + s) * 32 + p % 32].
+struct GeomLevel {
+    const uint2* ent = nullptr;
+    const unsigned long long* row0 = nullptr;
 };
 
 // One solve of a batch, as the batch kernel sees it.
@@ -126,6 +134,14 @@ int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_
 cudaError_t launch_batch_f64(const BatchArgs<double>& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_batch_f32(const BatchArgs<float>& a, int grid, int block, cudaStream_t s);
 int batch_blocks_per_sm(int precision, int block);
+// The FP32 march of one level with its geometry from a table.
+int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int grid, int block, cudaStream_t s);
+// Geometry-table generation for level l of directions dirs (npix pixels), for grids up to
+// n_cover: rows[b] = rows of 32-pixel block b; then the entries at row offsets row0.
+void launch_geom_count(long long rq, int l, const int4* dirs, long long npix, int n_cover, unsigned* rows,
+                       cudaStream_t s);
+void launch_geom_fill(long long rq, int l, const int4* dirs, long long npix, int n_cover,
+                      const unsigned long long* row0, uint2* ent, unsigned* err, cudaStream_t s);
 
 // fields.cu
 int launch_validate_fields(const double* nh, const double* x, int64_t ncell, DevStats* st, cudaStream_t s);

@@ -22,6 +22,7 @@ def main(argv=None) -> int:
     ap.add_argument("--x", choices=["thin", "neutral"], default="thin", help="ionized-fraction variant")
     ap.add_argument("--overlap", type=int, default=3, help="overlap_mode (0 none .. 3 conservative, 4 squared)")
     ap.add_argument("--levels", action="store_true", help="also print segments and rays per level")
+    ap.add_argument("--walk", action="store_true", help="FP32: walk every ray instead of reading geometry tables")
     a = ap.parse_args(argv)
     import torch
     import paper_2512_12466_gb300 as nyx
@@ -31,7 +32,8 @@ def main(argv=None) -> int:
     dev = torch.device("cuda")
     d = lambda v: torch.from_numpy(np.ascontiguousarray(v).ravel()).to(dev)
     s = nyx.Solver(w.n, w.box_cm, precision=nyx.RT_FP32 if a.precision == "fp32" else nyx.RT_FP64,
-                   n_th_cm3=0.01 * float(w.n_h.mean()), overlap_mode=a.overlap)
+                   n_th_cm3=0.01 * float(w.n_h.mean()), overlap_mode=a.overlap,
+                   flags=nyx.RT_FLAG_NO_GEOMETRY_TABLE if a.walk else 0)
     s.set_fields(d(w.n_h), d(w.x_ion))
     if k:
         s.add_sources(d(w.cells[:k].astype(np.int32)), d(w.ndot[:k]))

@@ -19,7 +19,7 @@ BOOK = ("rays", "splits", "escaped", "dropped_tau", "dropped_level", "segments",
 NYX_KEYS = ("precision", "n_min_ray", "level_max", "overlap_mode", "tau_max", "n_th_cm3", "e_heat_erg",
             "merge_mode", "merge_samp_level", "automerge_xbar", "merge_x_th", "merge_f_req", "merge_dr_cells",
             "merge_rmax_cells", "merge_f_ov", "merge_eps", "merge_n_min", "chem_iterate", "alpha_B", "C_H",
-            "clumping", "chem_tol", "chem_max_iter")
+            "clumping", "chem_tol", "chem_max_iter", "flags")
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +38,7 @@ def relerr(a, b):
 
 def run_gpu(nyx, n_h, x, cells, ndot, box_cm, dt_s=0.0, device_inputs=True, **kw):
     cfg = {k: v for k, v in kw.items() if k in NYX_KEYS}
-    cfg.setdefault("flags", nyx.RT_FLAG_VISIT_HASH)
+    cfg["flags"] = cfg.get("flags", 0) | nyx.RT_FLAG_VISIT_HASH
     n = n_h.shape[0]
     s = nyx.Solver(n, box_cm, **cfg)
     dev = torch.device("cuda")
@@ -114,18 +114,50 @@ def test_parity_fp64(nyx, case):
         assert abs(st["deposited_ph"] - st["absorbed_ph"]) <= 1e-12 * st["emitted_ph"]
 
 
+@pytest.mark.parametrize("walk", [False, True], ids=["table", "walk"])
 @pytest.mark.parametrize("case", CASES)
-def test_parity_fp32(nyx, case):
+def test_parity_fp32(nyx, case, walk):
+    # FP32 march with its geometry read from the per-device tables (default) and walked per ray
     n, k, seed, xm, dxc, mode, nth = case
     w = I.random_small(n, k, seed=seed, x_mode=xm, box_cm=n * dxc)
     n_th = nth * float(w.n_h.mean())
-    ref32, got = run_both(nyx, w, overlap_mode=mode, n_th_cm3=n_th, precision=1)
+    ref32, got = run_both(nyx, w, overlap_mode=mode, n_th_cm3=n_th, precision=1,
+                          flags=nyx.RT_FLAG_NO_GEOMETRY_TABLE if walk else 0)
     ref64 = oracle.run_workload(w, overlap_mode=mode, n_th_cm3=n_th, precision=0)
     assert_bookkeeping(got["stats"], ref32["stats"])
     assert relerr(got["gamma"], ref64["gamma"]) < 1e-5
     assert relerr(got["heat"], ref64["heat"]) < 1e-5
     assert relerr(got["gamma"], ref32["gamma"]) < 1e-5
     assert_ledger(got["stats"], 1e-6)
+
+
+@pytest.mark.parametrize("case", [
+    # (n, sources, seed, x mode, box per cell, overlap mode, tau_max, level_max, n_min_ray)
+    (1, 1, 301, "thin", 7e20, 3, 30.0, -1, 4.0),          # one-cell grid
+    (7, 4, 302, "mixed", 3e21, 3, 0.5, -1, 4.0),          # drops by tau_max
+    (20, 6, 303, "thin", 7e20, 1, 30.0, 2, 4.0),          # drops at level_max, Eq. 5 only
+    (31, 9, 304, "patchy", 2e22, 4, 30.0, -1, 2.0),       # squared correction, N_min = 2
+    (40, 12, 305, "thin", 2e21, 2, 30.0, -1, 8.0),        # Arc, N_min = 8
+    (64, 16, 306, "mixed", 3e21, 3, 30.0, -1, 4.0),
+])
+def test_geometry_table_equals_walk(nyx, case):
+    """The table-driven FP32 march and the walked one: the same bookkeeping bit
+    for bit, the same fields to rounding (f may be contracted differently)."""
+    n, k, seed, xm, dxc, mode, tmax, lmax, nmin = case
+    w = I.random_small(n, k, seed=seed, x_mode=xm, box_cm=n * dxc)
+    kw = dict(precision=1, overlap_mode=mode, tau_max=tmax, level_max=lmax, n_min_ray=nmin,
+              n_th_cm3=0.3 * float(w.n_h.mean()))
+    a = run_gpu(nyx, w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, **kw)
+    b = run_gpu(nyx, w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, flags=nyx.RT_FLAG_NO_GEOMETRY_TABLE, **kw)
+    assert_bookkeeping(a["stats"], b["stats"])
+    assert relerr(a["gamma"], b["gamma"]) < 1e-6 and relerr(a["heat"], b["heat"]) < 1e-6
+    # faces and corners: rays that start outside the grid at every level
+    cells = np.array([[0, 0, 0], [n - 1, n - 1, n - 1], [0, n - 1, n // 2]], dtype=np.int32)
+    ndot = np.array([1e52, 2e52, 3e52])
+    a = run_gpu(nyx, w.n_h, w.x_ion, cells, ndot, w.box_cm, **kw)
+    b = run_gpu(nyx, w.n_h, w.x_ion, cells, ndot, w.box_cm, flags=nyx.RT_FLAG_NO_GEOMETRY_TABLE, **kw)
+    assert_bookkeeping(a["stats"], b["stats"])
+    assert relerr(a["gamma"], b["gamma"]) < 1e-6
 
 
 def test_host_and_device_inputs_agree(nyx):
