@@ -1048,10 +1048,10 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
     flush_tally(T, 0xffffffffu, &st, l);
 }
 
-// One level (or one slice of it) of one solve, FP32, geometry from the level's table.
+// One level (or one slice of it) of one solve, FP32, geometry from the level's table. Without
+// the walk it fits 64 registers, so four blocks (32 warps) per SM.
 template <bool kHash>
-__global__ void __launch_bounds__(256, MarchOccupancy<float>::blocks) march_table_kernel(const MarchArgs<float> A,
-                                                                                       const GeomLevel GL)
+__global__ void __launch_bounds__(256, 4) march_table_kernel(const MarchArgs<float> A, const GeomLevel GL)
 {
     const int l = A.level;
     const int lane = threadIdx.x & 31;
