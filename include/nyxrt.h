@@ -183,6 +183,16 @@ int rt_get_x(rt_handle* h, double* x_out, int where);
 /* Free the handle and its device memory. NULL is accepted. */
 int rt_destroy(rt_handle* h);
 
+/* Device memory held by the FP32 geometry tables of CUDA device `device`, in
+ * bytes. A ray's cells, segment lengths and overlap-correction geometry
+ * relative to its source depend only on its HEALPix level and pixel (every
+ * source sits at a cell centre: Sec. 2.5 with the source convention of
+ * Alg. 3), so the FP32 march reads them from tables built on first use for
+ * each (split radius, level, grid size) and kept until the process exits,
+ * within a budget of an eighth of the device's memory (environment variable
+ * NYXRT_GEOMETRY_BUDGET_MB overrides it); levels over budget walk their rays. */
+int64_t rt_geometry_table_bytes(int32_t device);
+
 /* Text of the handle's last error ("" if none); for h == NULL, the last
  * error of a failed rt_create on this thread. */
 const char* rt_last_error(const rt_handle* h);
@@ -207,7 +217,9 @@ typedef struct rt_batch rt_batch;
 /* Launch shape of the batch kernel (see rt_batch_tune). */
 typedef struct rt_batch_params {
     int32_t block;          /* threads per block: 128 or 256 */
-    int32_t blocks_per_sm;  /* co-resident blocks per SM, 1 .. the occupancy limit */
+    int32_t blocks_per_sm;  /* co-resident blocks per SM, 1 .. the occupancy limit; 0: as many as fit
+                               (a batch whose solves share N_min reads the FP32 geometry tables, with
+                               a higher limit than the walking kernel) */
     int32_t tile;           /* children a warp claims from the work queue at once (multiple of 32) */
     int32_t pad_;
     int64_t slice;          /* children per slice; also the record capacity of each level's buffer */
@@ -229,7 +241,7 @@ int rt_batch_set_params(rt_batch* b, const rt_batch_params* p);
 int rt_batch_get_params(const rt_batch* b, rt_batch_params* p);
 
 /* Autotuner: time the batch under candidate launch shapes (block 128/256,
- * 1..occupancy blocks per SM, tiles 64/256/1024, slices 2^21/2^23/2^25, group
+ * 1, 2 and as many blocks per SM as fit, tiles 64/256/1024, slices 2^21/2^23/2^25, group
  * budgets of 48 MB and unlimited), each `repeats` times, keep the fastest and
  * return it with its time in ms. */
 int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best, double* best_ms);

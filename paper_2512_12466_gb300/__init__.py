@@ -106,6 +106,8 @@ def lib():
         L.rt_add_sources.argtypes = [P, P, P, i64, C.c_int]
         L.rt_clear_sources.argtypes = [P]
         L.rt_reconfigure.argtypes = [P, C.POINTER(rt_config)]
+        L.rt_geometry_table_bytes.argtypes = [i32]
+        L.rt_geometry_table_bytes.restype = i64
         L.rt_step.argtypes = [P, d, P, P, C.c_int, C.POINTER(rt_stats)]
         L.rt_get_x.argtypes = [P, P, C.c_int]
         L.rt_destroy.argtypes = [P]
@@ -140,7 +142,8 @@ def lib():
 
 
 def exported_symbols():
-    return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_reconfigure", "rt_step",
+    return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_reconfigure",
+            "rt_geometry_table_bytes", "rt_step",
             "rt_get_x", "rt_destroy", "rt_last_error", "rt_version", "rt_batch_create", "rt_batch_set_params",
             "rt_batch_get_params", "rt_batch_tune", "rt_batch_capture", "rt_batch_run", "rt_batch_destroy",
             "rt_batch_last_error", "rt_server_config_default", "rt_server_create", "rt_server_submit",
@@ -190,6 +193,11 @@ def rt_add_sources(h: int, cells, ndot, n: int, where: int) -> None:
 
 def rt_clear_sources(h: int) -> None:
     _check(lib().rt_clear_sources(h), h)
+
+
+def rt_geometry_table_bytes(device: int = 0) -> int:
+    """Device memory held by the FP32 geometry tables of CUDA device `device`."""
+    return int(lib().rt_geometry_table_bytes(int(device)))
 
 
 def rt_reconfigure(h: int, cfg: rt_config) -> None:

@@ -50,6 +50,8 @@ struct rt_batch {
     int64_t cap_src = 0, cap_solves = 0;
     int table_level = 0;
     const int4* dirs = nullptr;
+    bool use_geo = false;                  // FP32 solves sharing one split radius: geometry tables
+    GeomLevel geo[RT_MAX_LEVELS + 1];
     BatchSolve* d_solves = nullptr;
     DevStats* d_stats = nullptr;
     DevStats* h_stats = nullptr;           // pinned
@@ -106,9 +108,17 @@ int alloc_rays(rt_batch* b, int64_t cap)
     return RT_OK;
 }
 
-int max_blocks_per_sm(rt_batch* b, int block)
+int max_blocks_per_sm(rt_batch* b, int block, bool table)
 {
-    return batch_blocks_per_sm(b->precision, block);
+    return batch_blocks_per_sm(b->precision, block, table);
+}
+
+// Blocks per SM of the next launch: the requested number, or (0) all that fit, within the
+// occupancy of the kernel that runs (walking or table-driven).
+int launch_blocks_per_sm(rt_batch* b)
+{
+    const int occ = max_blocks_per_sm(b, b->params.block, b->use_geo);
+    return b->params.blocks_per_sm > 0 ? std::min(b->params.blocks_per_sm, occ) : occ;
 }
 
 template <class R>
@@ -129,8 +139,10 @@ int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count)
     a.max_slices = kMaxSlices;
     a.any_hash = 0;
     for (const BatchSolve& bs : b->hsolve) a.any_hash |= bs.hash;
+    a.use_geo = b->use_geo ? 1 : 0;
+    for (int l = 0; l <= RT_MAX_LEVELS; ++l) a.geo[l] = b->geo[l];
     a.err = b->d_err;
-    const int grid = b->sm_count * b->params.blocks_per_sm;
+    const int grid = b->sm_count * launch_blocks_per_sm(b);
     cudaError_t e;
     if constexpr (sizeof(R) == 4) e = launch_batch_f32(a, grid, b->params.block, b->stream);
     else e = launch_batch_f64(a, grid, b->params.block, b->stream);
@@ -247,10 +259,10 @@ int run_once(rt_batch* b, float* ms)
 int apply_params(rt_batch* b, const rt_batch_params& p)
 {
     if ((p.block != 128 && p.block != 256) || p.tile < 32 || p.tile % 32 || p.slice < 1024 ||
-        p.slice > (int64_t(1) << 28) || p.blocks_per_sm < 1 || p.group_bytes < 0)
+        p.slice > (int64_t(1) << 28) || p.blocks_per_sm < 0 || p.group_bytes < 0)
         return bfail(b, RT_EINVAL,
                      "batch params: block 128|256, tile a multiple of 32, slice in [1024, 2^28], group_bytes >= 0");
-    const int occ = max_blocks_per_sm(b, p.block);
+    const int occ = std::max(max_blocks_per_sm(b, p.block, false), max_blocks_per_sm(b, p.block, b->use_geo));
     if (p.blocks_per_sm > occ) return bfail(b, RT_EINVAL, "batch params: blocks_per_sm above the occupancy limit");
     const bool realloc = p.slice != b->params.slice || !b->rays[1].base;
     b->params = p;
@@ -355,6 +367,20 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
         B_CUDA(b, cudaMalloc(&b->d_err, sizeof(unsigned)), "error word");
         B_CUDA(b, cudaMallocHost(&b->h_err, sizeof(unsigned)), "error word");
         *b->h_err = 0;
+    }
+    {   // FP32 solves that share a split radius read every level's geometry from the tables
+        // (built here, outside any capture, for the largest grid of the batch)
+        b->use_geo = b->precision == RT_FP32 && !b->hs.empty();
+        int nmax = 0;
+        for (rt_handle* h : b->hs) {
+            if (h->rq != b->hs[0]->rq || (h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE)) b->use_geo = false;
+            nmax = std::max(nmax, h->cfg.n);
+        }
+        for (int l = 0; l <= RT_MAX_LEVELS; ++l) b->geo[l] = GeomLevel();
+        for (int l = 0; b->use_geo && l <= table_level; ++l)
+            if (!geometry_level(b->device, b->hs[0]->rq, l, nmax, b->dirs + healpix_level_offset(l), b->stream,
+                                &b->geo[l]))
+                b->use_geo = false;
     }
     // ---- all solves' emitted sources in one catalog, tagged with their solve index
     if (b->nsrc > b->cap_src || !b->d_src) {
@@ -463,7 +489,7 @@ int rt_batch_create(rt_handle* const* handles, int32_t count, void* cuda_stream,
     if (rc) return rc;
     rt_batch_params p{};
     p.block = 256;
-    p.blocks_per_sm = std::max(1, max_blocks_per_sm(b, 256));   // every block the kernel was built to fit
+    p.blocks_per_sm = 0;   // every block the kernel that runs was built to fit
     p.tile = 256;
     p.slice = int64_t(1) << 22;
     p.group_bytes = int64_t(48) << 20;
@@ -511,10 +537,10 @@ int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best_out, doubl
     const int64_t groups[2] = {int64_t(48) << 20, 0};
     for (int64_t gb : groups)
     for (int bl : blocks) {
-        const int occ = max_blocks_per_sm(b, bl);
-        std::vector<int> bpss;                       // 1, 2, 4 and full occupancy, each once
-        for (int v : {1, 2, 4, occ})
-            if (v <= occ && std::find(bpss.begin(), bpss.end(), v) == bpss.end()) bpss.push_back(v);
+        const int occ = max_blocks_per_sm(b, bl, b->use_geo);
+        std::vector<int> bpss{0};                    // all that fit, then 1 and 2 if fewer
+        for (int v : {1, 2})
+            if (v < occ) bpss.push_back(v);
         for (int bps : bpss) {
             for (int64_t sl : slices) {
                 for (int ti : tiles) {

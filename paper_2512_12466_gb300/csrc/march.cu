@@ -1093,8 +1093,8 @@ __global__ void __launch_bounds__(256, 4) march_table_kernel(const MarchArgs<flo
 // slices; the next level's slices run before the current level's remaining ones,
 // so no buffer ever holds more than one slice's output. Only CUDA's grid barrier
 // is waited on: no block spins on another's flag.
-template <class R, bool kHash>
-__global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) batch_kernel(const BatchArgs<R> A)
+template <class R, bool kHash, bool kTable>
+__global__ void __launch_bounds__(256, kTable ? 4 : MarchOccupancy<R>::blocks) batch_kernel(const BatchArgs<R> A)
 {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     const int lane = threadIdx.x & 31;
@@ -1159,7 +1159,14 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) batch_kernel(c
                     V.rq = bs.rq;
                     V.tau_max = (R)bs.tau_max;
                     V.src_off = bs.src_off - A.src_base;
-                    split = march_ray<R, kHash>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau, ocP, octau);
+                    if constexpr (kTable) {
+                        static_assert(sizeof(R) == 4, "geometry tables serve the FP32 march");
+                        split = march_ray_table<kHash>(V, A.geo[l], A.err, l, si, pix, P, tau, cP, ctau, se, dirs[pix],
+                                                       T, oP, otau, ocP, octau);
+                    } else {
+                        split = march_ray<R, kHash>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau, ocP,
+                                                    octau);
+                    }
                 }
                 append_split<R>(split, si, pix, oP, otau, ocP, octau, A.buf[l + 1], &A.counts[sid], A.err);
             }
@@ -1216,11 +1223,22 @@ void launch_geom_fill(long long rq, int l, const int4* dirs, long long npix, int
 }
 
 template <class R>
+static const void* batch_kernel_for(bool hash, bool table)
+{
+    if constexpr (sizeof(R) == 4) {
+        if (table) return hash ? (const void*)batch_kernel<float, true, true> : (const void*)batch_kernel<float, false, true>;
+        return hash ? (const void*)batch_kernel<float, true, false> : (const void*)batch_kernel<float, false, false>;
+    } else {
+        return hash ? (const void*)batch_kernel<double, true, false> : (const void*)batch_kernel<double, false, false>;
+    }
+}
+
+template <class R>
 static cudaError_t launch_batch_impl(const BatchArgs<R>& a, int grid, int block, cudaStream_t s)
 {
     void* args[] = {const_cast<BatchArgs<R>*>(&a)};
-    const void* k = a.any_hash ? (const void*)batch_kernel<R, true> : (const void*)batch_kernel<R, false>;
-    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(block), args, 0, s);
+    return cudaLaunchCooperativeKernel(batch_kernel_for<R>(a.any_hash != 0, a.use_geo != 0), dim3(grid), dim3(block),
+                                       args, 0, s);
 }
 
 cudaError_t launch_batch_f64(const BatchArgs<double>& a, int grid, int block, cudaStream_t s)
@@ -1233,17 +1251,17 @@ cudaError_t launch_batch_f32(const BatchArgs<float>& a, int grid, int block, cud
     return launch_batch_impl<float>(a, grid, block, s);
 }
 
-// Co-resident blocks per SM of the batch kernel: the smaller of its two
-// instantiations, so that a cooperative launch sized by it fits either.
-int batch_blocks_per_sm(int precision, int block)
+// Co-resident blocks per SM of the batch kernel (walking or table-driven): the smaller of its
+// two visit-hash instantiations, so that a cooperative launch sized by it fits either.
+int batch_blocks_per_sm(int precision, int block, bool table)
 {
     int a = 0, b = 0;
     if (precision == RT_FP32) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, (const void*)batch_kernel<float, false>, block, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)batch_kernel<float, true>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel_for<float>(false, table), block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel_for<float>(true, table), block, 0);
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, (const void*)batch_kernel<double, false>, block, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)batch_kernel<double, true>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel_for<double>(false, false), block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel_for<double>(true, false), block, 0);
     }
     return std::min(a, b);
 }

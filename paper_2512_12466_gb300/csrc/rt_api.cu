@@ -711,6 +711,13 @@ int rt_add_sources(rt_handle* h, const int32_t* cell_ijk, const double* ndot, in
     return RT_OK;
 }
 
+int64_t rt_geometry_table_bytes(int32_t device)
+{
+    std::lock_guard<std::mutex> lk(g_geom_mu);
+    auto it = g_geom_bytes.find(device);
+    return it == g_geom_bytes.end() ? 0 : (int64_t)it->second;
+}
+
 int rt_reconfigure(rt_handle* h, const rt_config* cfg)
 {
     if (!h || !cfg) return h ? fail(h, RT_EINVAL, "cfg is NULL") : RT_EINVAL;
