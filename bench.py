@@ -42,11 +42,12 @@ L2_FLUSH_BYTES = 512 << 20
 
 
 # DRAM traffic of the FP32 march from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over
-# all march launches of one step of the same box with its first 64 sources; profiles/march_fp32_config2_dram.md),
-# scaled to the full workload by primary segments. Valid only for the kernel sources it was taken on.
-TRAFFIC_CAPTURE = {"kernel": "march_kernel<float>", "bytes_per_segment": 0.37541880566138525,
-                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "38ff3bb0849b3cbb",
-                               "paper_2512_12466_gb300/csrc/rt_internal.h": "6877d171b8eb5677"}}
+# all march launches of one step of the same box with its first 64 sources;
+# profiles/march_table_config2_dram.md), scaled to the full workload by primary segments. Valid only
+# for the kernel sources it was taken on.
+TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.76592188759445,
+                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "35f1ba1b977d8abd",
+                               "paper_2512_12466_gb300/csrc/rt_internal.h": "2d6ed30287c61a11"}}
 
 
 def traffic_per_launch(segments_per_step: float, launches_per_step: float):
@@ -546,6 +547,7 @@ def run_nyx(args, world, rank, local):
                    "sources": 1024, "n_min_ray": 4, "tau_max": 30, "overlap": "conservative (Eqs. 7-8)",
                    "march": "FP32 physics, Kahan-compensated budgets, FP64 deposits and ledger",
                    "l2": "flushed before every timed step (512 MB write)", "parallelism": f"replicas x{world}"},
+        "geometry_table_bytes": nyx.rt_geometry_table_bytes(torch.cuda.current_device()),
         "segments_per_step": f32["segments_per_step"], "secondary_per_step": f32["secondary_per_step"],
         "rays_per_step": f32["rays_per_step"],
         "gpu_launches": f32["launches"],
@@ -554,7 +556,7 @@ def run_nyx(args, world, rank, local):
                      "traffic": traffic_per_launch(f32["segments_per_step"], f32["march_launches_per_step"]),
                      "algorithmic_bytes_per_launch": f32["achieved_gbs"] * 1e6 * f32["march_ms_per_step"]
                      / max(1, f32["march_launches_per_step"]),
-                     "kernel": "march_kernel<float>", "peak_kind": peak_kind,
+                     "kernel": "march_table_kernel (FP32, geometry tables)", "peak_kind": peak_kind,
                      "march_ms_per_step": f32["march_ms_per_step"],
                      "march_launches_per_step": f32["march_launches_per_step"]},
         "fp64": {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "steps": f64["steps"],

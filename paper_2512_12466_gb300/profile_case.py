@@ -49,6 +49,8 @@ def main(argv=None) -> int:
             for l, (sg, ry, sc) in enumerate(zip(st["segments"], st["rays"], st["secondary"])):
                 if ry:
                     print(f"  level {l}: rays {ry} segments {sg} secondary {sc}", flush=True)
+    print(f"geometry tables on device {torch.cuda.current_device()}: "
+          f"{nyx.rt_geometry_table_bytes(torch.cuda.current_device()) / 2**20:.1f} MiB", flush=True)
     s.close()
     return 0
 
