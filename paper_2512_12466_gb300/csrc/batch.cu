@@ -34,6 +34,9 @@ __global__ void tag_sources_kernel(const SrcEntry* __restrict__ in, int64_t m, i
 }
 
 constexpr int kMaxSlices = 1 << 16;
+// A solve that traced at least this many segments in its last run gets a launch of its own (the
+// single-solve kernel); lighter solves share launches, where batching pays.
+constexpr unsigned long long kHeavySegments = 1ULL << 26;
 
 }  // namespace
 
@@ -47,6 +50,7 @@ struct rt_batch {
     std::vector<int64_t> n_src_in, n_dedup, n_emit;
     std::vector<int> merged;
     std::vector<BatchSolve> hsolve;
+    std::vector<unsigned long long> work;   // segments each solve traced in the last run (0: not run yet)
     int64_t cap_src = 0, cap_solves = 0;
     int table_level = 0;
     const int4* dirs = nullptr;
@@ -108,23 +112,27 @@ int alloc_rays(rt_batch* b, int64_t cap)
     return RT_OK;
 }
 
-int max_blocks_per_sm(rt_batch* b, int block, bool table)
+int max_blocks_per_sm(rt_batch* b, int block, bool table, bool single)
 {
-    return batch_blocks_per_sm(b->precision, block, table);
+    return batch_blocks_per_sm(b->precision, block, table, single);
 }
 
-// Blocks per SM of the next launch: the requested number, or (0) all that fit, within the
-// occupancy of the kernel that runs (walking or table-driven).
-int launch_blocks_per_sm(rt_batch* b)
+// Blocks per SM of a launch: the requested number, or (0) all that fit, within the occupancy of
+// the kernel variant that runs (walking or table-driven, one solve or many).
+int launch_blocks_per_sm(rt_batch* b, bool single)
 {
-    const int occ = max_blocks_per_sm(b, b->params.block, b->use_geo);
+    const int occ = max_blocks_per_sm(b, b->params.block, b->use_geo, single);
     return b->params.blocks_per_sm > 0 ? std::min(b->params.blocks_per_sm, occ) : occ;
 }
 
+// One cooperative launch over the solves whose sources are [src_first, src_first + src_count) of
+// the batch catalog; single >= 0: that is exactly solve `single`.
 template <class R>
-int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count)
+int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count, int single)
 {
     BatchArgs<R> a;
+    a.single = single >= 0 ? 1 : 0;
+    a.one = single >= 0 ? b->hsolve[(size_t)single] : BatchSolve{};
     a.solves = b->d_solves;
     a.src = b->d_src + src_first;
     a.nsrc = src_count;
@@ -142,7 +150,7 @@ int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count)
     a.use_geo = b->use_geo ? 1 : 0;
     for (int l = 0; l <= RT_MAX_LEVELS; ++l) a.geo[l] = b->geo[l];
     a.err = b->d_err;
-    const int grid = b->sm_count * launch_blocks_per_sm(b);
+    const int grid = b->sm_count * launch_blocks_per_sm(b, single >= 0);
     cudaError_t e;
     if constexpr (sizeof(R) == 4) e = launch_batch_f32(a, grid, b->params.block, b->stream);
     else e = launch_batch_f64(a, grid, b->params.block, b->stream);
@@ -168,8 +176,14 @@ int enqueue(rt_batch* b)
     B_CUDA(b, cudaGetLastError(), "kappa launch");
     B_CUDA(b, cudaMemsetAsync(b->d_stats, 0, sizeof(DevStats) * b->hs.size(), s), "stats clear");
     B_CUDA(b, cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), s), "error clear");
-    // consecutive groups of solves whose kappa + Gamma fit the budget, one launch each
+    // consecutive groups of solves whose kappa + Gamma fit the budget, one launch each; a solve
+    // that fills half the budget or more, or traced many segments in the last run, runs alone (the
+    // single-solve kernel, whose solve parameters are kernel parameters rather than per-lane loads)
     const int rbytes = b->precision == RT_FP32 ? 12 : 16;
+    const int64_t gb = b->params.group_bytes;
+    auto big = [&](size_t i) {
+        return (gb > 0 && 2 * rbytes * b->hs[i]->ncell >= gb) || (i < b->work.size() && b->work[i] >= kHeavySegments);
+    };
     size_t i0 = 0;
     int64_t src0 = 0;
     while (i0 < b->hs.size()) {
@@ -177,7 +191,7 @@ int enqueue(rt_batch* b)
         int64_t bytes = 0, srcs = 0;
         while (i1 < b->hs.size()) {
             const int64_t add = rbytes * b->hs[i1]->ncell;
-            if (i1 > i0 && b->params.group_bytes > 0 && bytes + add > b->params.group_bytes) break;
+            if (i1 > i0 && (big(i0) || big(i1) || (gb > 0 && bytes + add > gb))) break;
             bytes += add;
             srcs += b->n_emit[i1];
             ++i1;
@@ -185,7 +199,9 @@ int enqueue(rt_batch* b)
         if (srcs > 0) {
             B_CUDA(b, cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned long long) * kMaxSlices, s), "counter clear");
             B_CUDA(b, cudaMemsetAsync(b->d_tiles, 0, sizeof(unsigned long long) * kMaxSlices, s), "counter clear");
-            const int rc = b->precision == RT_FP32 ? launch_trace<float>(b, src0, srcs) : launch_trace<double>(b, src0, srcs);
+            const int single = i1 == i0 + 1 ? (int)i0 : -1;
+            const int rc = b->precision == RT_FP32 ? launch_trace<float>(b, src0, srcs, single)
+                                                   : launch_trace<double>(b, src0, srcs, single);
             if (rc) return rc;
             b->launches += 1;
         }
@@ -253,6 +269,9 @@ int run_once(rt_batch* b, float* ms)
     B_CUDA(b, cudaStreamSynchronize(b->stream), "batch run");
     if (*b->h_err) return bfail(b, RT_EDEVICE, "batch kernel reported an internal error (buffer, slice or level limit)");
     if (ms) B_CUDA(b, cudaEventElapsedTime(ms, b->ev0, b->ev1), "event");
+    b->work.assign(b->hs.size(), 0ULL);           // the next launches' grouping (a graph keeps its own)
+    for (size_t i = 0; i < b->hs.size(); ++i)
+        for (int l = 0; l < RT_MAX_LEVELS; ++l) b->work[i] += b->h_stats[i].segments[l];
     return RT_OK;
 }
 
@@ -262,7 +281,8 @@ int apply_params(rt_batch* b, const rt_batch_params& p)
         p.slice > (int64_t(1) << 28) || p.blocks_per_sm < 0 || p.group_bytes < 0)
         return bfail(b, RT_EINVAL,
                      "batch params: block 128|256, tile a multiple of 32, slice in [1024, 2^28], group_bytes >= 0");
-    const int occ = std::max(max_blocks_per_sm(b, p.block, false), max_blocks_per_sm(b, p.block, b->use_geo));
+    int occ = 0;
+    for (int v = 0; v < 4; ++v) occ = std::max(occ, max_blocks_per_sm(b, p.block, v & 1, v & 2));
     if (p.blocks_per_sm > occ) return bfail(b, RT_EINVAL, "batch params: blocks_per_sm above the occupancy limit");
     const bool realloc = p.slice != b->params.slice || !b->rays[1].base;
     b->params = p;
@@ -321,6 +341,7 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
 {
     drop_graph(b);
     b->hs.assign(handles, handles + count);
+    b->work.clear();                               // grouping history belongs to the previous solves
     b->n_th.clear();
     b->emitted.clear();
     b->n_src_in.clear();
@@ -537,7 +558,7 @@ int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best_out, doubl
     const int64_t groups[2] = {int64_t(48) << 20, 0};
     for (int64_t gb : groups)
     for (int bl : blocks) {
-        const int occ = max_blocks_per_sm(b, bl, b->use_geo);
+        const int occ = max_blocks_per_sm(b, bl, b->use_geo, false);
         std::vector<int> bpss{0};                    // all that fit, then 1 and 2 if fewer
         for (int v : {1, 2})
             if (v < occ) bpss.push_back(v);

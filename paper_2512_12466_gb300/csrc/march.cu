@@ -136,18 +136,6 @@ __device__ __forceinline__ double widen(float x)
 }
 __device__ __forceinline__ double widen(double x) { return x; }
 
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // Per-thread tallies for one (solve, level).
 struct Tally {
     unsigned rays, split, esc, dtau, dlev, seg, sec;
@@ -1093,8 +1081,11 @@ __global__ void __launch_bounds__(256, 4) march_table_kernel(const MarchArgs<flo
 // slices; the next level's slices run before the current level's remaining ones,
 // so no buffer ever holds more than one slice's output. Only CUDA's grid barrier
 // is waited on: no block spins on another's flag.
-template <class R, bool kHash, bool kTable>
-__global__ void __launch_bounds__(256, kTable ? 4 : MarchOccupancy<R>::blocks) batch_kernel(const BatchArgs<R> A)
+// kSingle: the launch holds one solve, passed by value in A.one, so its parameters are the same
+// for every lane (kernel parameters, not per-lane loads) and no tally changes hands. Only then does
+// the table-driven kernel fit four blocks per SM; with per-lane solve parameters it takes three.
+template <class R, bool kHash, bool kTable, bool kSingle>
+__global__ void __launch_bounds__(256, (kTable && kSingle) ? 4 : MarchOccupancy<R>::blocks) batch_kernel(const BatchArgs<R> A)
 {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     const int lane = threadIdx.x & 31;
@@ -1141,14 +1132,16 @@ __global__ void __launch_bounds__(256, kTable ? 4 : MarchOccupancy<R>::blocks) b
                 if (j < s1) {
                     load_ray<R>(l, j, A.buf[l], si, pix, P, tau, cP, ctau);
                     se = A.src[si];
-                    st = A.solves[se.pad].st;
+                    st = kSingle ? A.one.st : A.solves[se.pad].st;
                 }
-                // a lane whose solve changes hands its tally over first
-                const unsigned chg = __ballot_sync(0xffffffffu, cur != nullptr && st != cur);
-                if (chg) flush_tally(T, chg, &cur, l);
+                if constexpr (!kSingle) {
+                    // a lane whose solve changes hands its tally over first
+                    const unsigned chg = __ballot_sync(0xffffffffu, cur != nullptr && st != cur);
+                    if (chg) flush_tally(T, chg, &cur, l);
+                }
                 if (j < s1) {
                     cur = st;
-                    const BatchSolve& bs = A.solves[se.pad];
+                    const BatchSolve& bs = kSingle ? A.one : A.solves[se.pad];
                     SolveView<R> V;
                     V.kap = static_cast<const R*>(bs.kap);
                     V.gamma = bs.gamma;
@@ -1222,23 +1215,33 @@ void launch_geom_fill(long long rq, int l, const int4* dirs, long long npix, int
     geom_fill_kernel<<<(unsigned)grid, 256, 0, s>>>(rq, l, dirs, npix, n_cover, row0, ent, err);
 }
 
-template <class R>
-static const void* batch_kernel_for(bool hash, bool table)
+template <class R, bool kSingle>
+static const void* batch_kernel_pick(bool hash, bool table)
 {
     if constexpr (sizeof(R) == 4) {
-        if (table) return hash ? (const void*)batch_kernel<float, true, true> : (const void*)batch_kernel<float, false, true>;
-        return hash ? (const void*)batch_kernel<float, true, false> : (const void*)batch_kernel<float, false, false>;
+        if (table)
+            return hash ? (const void*)batch_kernel<float, true, true, kSingle>
+                        : (const void*)batch_kernel<float, false, true, kSingle>;
+        return hash ? (const void*)batch_kernel<float, true, false, kSingle>
+                    : (const void*)batch_kernel<float, false, false, kSingle>;
     } else {
-        return hash ? (const void*)batch_kernel<double, true, false> : (const void*)batch_kernel<double, false, false>;
+        return hash ? (const void*)batch_kernel<double, true, false, kSingle>
+                    : (const void*)batch_kernel<double, false, false, kSingle>;
     }
+}
+
+template <class R>
+static const void* batch_kernel_for(bool hash, bool table, bool single)
+{
+    return single ? batch_kernel_pick<R, true>(hash, table) : batch_kernel_pick<R, false>(hash, table);
 }
 
 template <class R>
 static cudaError_t launch_batch_impl(const BatchArgs<R>& a, int grid, int block, cudaStream_t s)
 {
     void* args[] = {const_cast<BatchArgs<R>*>(&a)};
-    return cudaLaunchCooperativeKernel(batch_kernel_for<R>(a.any_hash != 0, a.use_geo != 0), dim3(grid), dim3(block),
-                                       args, 0, s);
+    return cudaLaunchCooperativeKernel(batch_kernel_for<R>(a.any_hash != 0, a.use_geo != 0, a.single != 0), dim3(grid),
+                                       dim3(block), args, 0, s);
 }
 
 cudaError_t launch_batch_f64(const BatchArgs<double>& a, int grid, int block, cudaStream_t s)
@@ -1251,19 +1254,20 @@ cudaError_t launch_batch_f32(const BatchArgs<float>& a, int grid, int block, cud
     return launch_batch_impl<float>(a, grid, block, s);
 }
 
-// Co-resident blocks per SM of the batch kernel (walking or table-driven): the smaller of its
-// two visit-hash instantiations, so that a cooperative launch sized by it fits either.
-int batch_blocks_per_sm(int precision, int block, bool table)
+// Co-resident blocks per SM of the batch kernel variant (walking or table-driven, one solve or
+// many): the smaller of its two visit-hash instantiations, so that a cooperative launch sized by
+// it fits either.
+int batch_blocks_per_sm(int precision, int block, bool table, bool single)
 {
-    int a = 0, b = 0;
-    if (precision == RT_FP32) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel_for<float>(false, table), block, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel_for<float>(true, table), block, 0);
-    } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel_for<double>(false, false), block, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel_for<double>(true, false), block, 0);
+    int best = 1 << 30;
+    for (int hash = 0; hash < 2; ++hash) {
+        const void* k = precision == RT_FP32 ? batch_kernel_for<float>(hash, table, single)
+                                             : batch_kernel_for<double>(hash, false, single);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0);
+        best = std::min(best, nb);
     }
-    return std::min(a, b);
+    return best;
 }
 
 }  // namespace nyx

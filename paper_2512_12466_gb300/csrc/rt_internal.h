@@ -127,6 +127,8 @@ struct BatchArgs {
     int any_hash;                    // some solve asks for the visit hash
     int use_geo;                     // FP32, every solve shares rq: geometry from the tables below
     GeomLevel geo[RT_MAX_LEVELS + 1];
+    int single;                      // the launch holds one solve, given in `one`
+    BatchSolve one;
     unsigned* err;
 };
 
@@ -135,7 +137,7 @@ int launch_march_f64(const MarchArgs<double>& a, int grid, int block, cudaStream
 int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_batch_f64(const BatchArgs<double>& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_batch_f32(const BatchArgs<float>& a, int grid, int block, cudaStream_t s);
-int batch_blocks_per_sm(int precision, int block, bool table);
+int batch_blocks_per_sm(int precision, int block, bool table, bool single);
 // The FP32 march of one level with its geometry from a table.
 int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int grid, int block, cudaStream_t s);
 // Geometry-table generation for level l of directions dirs (npix pixels), for grids up to
