@@ -40,7 +40,7 @@ class OrcConfig(C.Structure):
         ("merge_dr_cells", C.c_double), ("merge_rmax_cells", C.c_double), ("merge_f_ov", C.c_double),
         ("merge_eps", C.c_double), ("merge_n_min", C.c_int32), ("chem_iterate", C.c_int32),
         ("dt_s", C.c_double), ("alpha_B", C.c_double), ("C_H", C.c_double), ("clumping", C.c_double),
-        ("chem_tol", C.c_double), ("chem_max_iter", C.c_int32), ("pad_", C.c_int32),
+        ("chem_tol", C.c_double), ("chem_max_iter", C.c_int32), ("periodic", C.c_int32),
     ]
 
 
@@ -80,6 +80,8 @@ def lib():
         L.orc_direction.argtypes = [i32, i64, P, P]
         L.orc_split_rq.argtypes = [d]
         L.orc_split_rq.restype = i64
+        L.orc_periodic_rs.argtypes = [C.c_int32]
+        L.orc_periodic_rs.restype = i64
         L.orc_default_level_max.argtypes = [i32, d]
         L.orc_default_level_max.restype = i32
         L.orc_mix64_export.argtypes = [u64]
@@ -125,6 +127,11 @@ def direction(level: int, pix: int):
 
 def split_rq(n_min_ray: float) -> int:
     return int(lib().orc_split_rq(n_min_ray))
+
+
+def periodic_rs(n: int) -> int:
+    """Travel-distance cutoff sqrt(3) L_box of periodic boundaries (Sec. 2.5.1), in 2^-24 cells."""
+    return int(lib().orc_periodic_rs(int(n)))
 
 
 def default_level_max(n: int, n_min_ray: float) -> int:
@@ -195,7 +202,7 @@ DEFAULTS = dict(precision=0, sigma_cm2=6.3e-18, n_min_ray=4.0, level_max=-1, ove
                 merge_samp_level=3, automerge_xbar=0.018, merge_x_th=0.9, merge_f_req=0.9,
                 merge_dr_cells=2.0, merge_rmax_cells=16.0, merge_f_ov=1.0, merge_eps=1e-6,
                 merge_n_min=8, chem_iterate=0, dt_s=0.0, alpha_B=2.59e-13, C_H=0.0, clumping=1.0,
-                chem_tol=1e-6, chem_max_iter=100)
+                chem_tol=1e-6, chem_max_iter=100, periodic=0)
 
 
 def make_config(n: int, box_cm: float, n_h=None, **kw) -> OrcConfig:

@@ -62,17 +62,27 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
 
     /* Integer event bookkeeping.  Along axis a the k-th face crossing
      * (k = 0, 1, ...) happens at parametric time T_a(k) = (2k+1) 2^(S-1) / D_a;
-     * the split radius is R_l = Rq 2^l / 2^F.  Gend/Gstart are R_l and
-     * R_{l-1} scaled by 2^F D_a. */
+     * the split radius is R_l = Rq 2^l / 2^F.  The ray ends at R_l, or, with
+     * periodic boundaries (Sec. 2.5.1), at the travel distance sqrt(3) L_box
+     * if that comes first or at the same point (RAY_FLTR keeps only rays with
+     * s < sqrt(3) L_box), in which case it stops there without splitting.
+     * Gend/Gstart are the end and start radii scaled by 2^F D_a. */
+    const int64_t Rsplit = C->rq << l;
+    const int split_end = !C->periodic || Rsplit < C->rs;
+    const int64_t Rend = split_end ? Rsplit : C->rs;
+    const int64_t Rstart = l > 0 ? (C->rq << (l - 1)) : 0;
     int64_t Gend[3], Gstart[3], k[3], kend[3];
     for (int a = 0; a < 3; a++) {
-        Gend[a] = (C->rq << l) * D[a];
-        Gstart[a] = l > 0 ? (C->rq << (l - 1)) * D[a] : 0;
+        Gend[a] = Rend * D[a];
+        Gstart[a] = Rstart * D[a];
         k[a] = l > 0 ? (Gstart[a] + B) >> (S + F) : 0;          /* crossings with T <= R_{l-1} */
-        kend[a] = ((Gend[a] + B - 1) >> (S - 1 + F)) >> 1;       /* crossings with T <  R_l     */
+        kend[a] = ((Gend[a] + B - 1) >> (S - 1 + F)) >> 1;       /* crossings with T <  the end */
     }
     int64_t i[3];
-    for (int a = 0; a < 3; a++) i[a] = cell0[a] + s[a] * k[a];
+    for (int a = 0; a < 3; a++) {
+        i[a] = cell0[a] + s[a] * k[a];
+        if (C->periodic) i[a] = ((i[a] % n) + n) % n;           /* wrap into the box */
+    }
 
     /* Per-ray REAL constants (IEEE operations in a fixed order). */
     const REAL nrm = (REAL)nrm_d;
@@ -125,7 +135,8 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
                 ds_p = (REAL)((2 * k[w] + 1) * D[prev] - (2 * kprev + 1) * D[w]) * W[prev][w];
         } else {
             if (prev < 0)
-                ds_p = R_LDEXP((REAL)C->rq, l > 0 ? l - 1 - F : -F);
+                ds_p = split_end ? R_LDEXP((REAL)C->rq, l > 0 ? l - 1 - F : -F)
+                                 : R_LDEXP((REAL)(Rend - Rstart), -F);
             else
                 ds_p = (REAL)(Gend[prev] - (2 * kprev + 1) * B) * V[prev];
         }
@@ -166,7 +177,8 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
             REAL De = dl[0];
             for (int q = 1; q < 6; q++)
                 if (dl[q] < De) { De = dl[q]; face = q; }
-            const REAL tnext = is_end ? R_LDEXP((REAL)C->rq, l - F) : (REAL)(2 * k[w] + 1) * h[w];
+            const REAL tnext = is_end ? (split_end ? R_LDEXP((REAL)C->rq, l - F) : R_LDEXP((REAL)Rend, -F))
+                                      : (REAL)(2 * k[w] + 1) * h[w];
             const REAL tm = tnext - ds_p * (REAL)0.5;
             const REAL Lpix = tm * Lc;                               /* pixel width at the midpoint */
             const int near_edge = (De + De) < Lpix;
@@ -179,6 +191,7 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
                 } else {
                     int64_t j[3] = {i[0], i[1], i[2]};
                     j[face >> 1] += (face & 1) ? 1 : -1;
+                    if (C->periodic) j[face >> 1] = ((j[face >> 1] % n) + n) % n;
                     if (j[0] >= 0 && j[0] < n && j[1] >= 0 && j[1] < n && j[2] >= 0 && j[2] < n) {
                         const int64_t c2 = (j[2] * n + j[1]) * n + j[0];
                         const REAL kn_raw = C->KAPPA_FIELD[c2];
@@ -222,6 +235,12 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
             orc_sum_add(&C->absorbed, ph * ((double)A - (double)cA));
             return 0;
         }
+        if (is_end && !split_end) {                                  /* travelled sqrt(3) L_box (Sec. 2.5.1) */
+            st->escaped[l]++;
+            orc_sum_add(&C->escaped, ph * ((double)P - (double)cP));
+            orc_sum_add(&C->absorbed, ph * ((double)A - (double)cA));
+            return 0;
+        }
         if (is_end) {                                                /* reached the split sphere (Eq. 4) */
             orc_sum_add(&C->absorbed, ph * ((double)A - (double)cA));
             if (l + 1 > C->level_max) {
@@ -247,7 +266,11 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
         for (int b = 0; b < 3; b++)
             tie[b] = (b == w) || ((2 * k[b] + 1) * D[w] == (2 * kw + 1) * D[b]);
         for (int b = 0; b < 3; b++)
-            if (tie[b]) { k[b]++; i[b] += s[b]; }
+            if (tie[b]) {
+                k[b]++;
+                i[b] += s[b];
+                if (C->periodic) i[b] = ((i[b] % n) + n) % n;
+            }
         prev = w;
         kprev = kw;
         if (i[0] < 0 || i[0] >= n || i[1] < 0 || i[1] >= n || i[2] < 0 || i[2] >= n) {

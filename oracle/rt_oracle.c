@@ -82,7 +82,7 @@ typedef struct {
     int32_t chem_iterate;
     double dt_s, alpha_B, C_H, clumping, chem_tol;
     int32_t chem_max_iter;
-    int32_t pad_;
+    int32_t periodic;            /* 1: periodic boundaries (Sec. 2.5.1) */
 } orc_config;
 
 typedef struct {
@@ -118,6 +118,8 @@ typedef struct {
     int level_max;
     double tau_max;
     int overlap_mode;
+    int periodic;                /* Sec. 2.5.1: rays wrap around the box ... */
+    int64_t rs;                  /* ... and stop at travel distance sqrt(3) L_box (2^-F cells) */
     orc_stats* st;
     orc_sum emitted, absorbed, escaped, dropped;
     int64_t* rec_ray;
@@ -224,6 +226,14 @@ int64_t orc_split_rq(double n_min_ray)
 {
     const double r0 = sqrt(3.0 / (3.141592653589793 * n_min_ray));
     return (int64_t)floor(r0 * (double)(1 << ORC_F) + 0.5);
+}
+
+/* Periodic boundaries (Sec. 2.5.1): a ray stops once its travel distance
+ * reaches sqrt(3) L_box, i.e. sqrt(3) n cells; in the split radius's fixed
+ * point (2^-F cells), rounded to nearest. */
+int64_t orc_periodic_rs(int32_t n)
+{
+    return (int64_t)floor(sqrt(3.0) * (double)n * (double)(1 << ORC_F) + 0.5);
 }
 
 /* Default l_max: smallest l with R_l >= sqrt(3) n, plus one, so it never
@@ -559,6 +569,8 @@ static void orc_trace(const orc_config* cfg, int64_t rq, int level_max, const do
     C.level_max = level_max;
     C.tau_max = cfg->tau_max;
     C.overlap_mode = cfg->overlap_mode;
+    C.periodic = cfg->periodic != 0;
+    C.rs = C.periodic ? orc_periodic_rs((int32_t)n) : 0;
     C.st = st;
     C.rec_ray = rec_ray;
     C.rec_seq = rec_seq;

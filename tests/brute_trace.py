@@ -73,14 +73,26 @@ def split_rq(n_min: float) -> int:
     return int(math.floor(math.sqrt(3.0 / (math.pi * n_min)) * 2 ** F + 0.5))
 
 
-def ray_segments(n: int, cell0, sd, level: int, rq: int):
-    """Exact segments of one ray between R_{l-1} and R_l.
+def periodic_rs(n: int) -> int:
+    """Travel-distance cutoff sqrt(3) L_box of periodic boundaries, in 2^-24 cells."""
+    return int(math.floor(math.sqrt(3.0) * n * 2 ** F + 0.5))
+
+
+def ray_segments(n: int, cell0, sd, level: int, rq: int, periodic: bool = False):
+    """Exact segments of one ray between R_{l-1} and R_l (periodic: and at most
+    the travel distance sqrt(3) n, which ends it without a split when it comes
+    first or at the same point).
 
     Returns (segments, outcome) with segments = list of (cell_xyz, t_a, t_b)
-    (Fractions) and outcome in {"split", "escape"}.
+    (Fractions; cells unwrapped, i.e. floor of the position) and outcome in
+    {"split", "escape", "stop"}.
     """
     t0 = Fr(rq * 2 ** (level - 1), 2 ** F) if level > 0 else Fr(0)
     t1 = Fr(rq * 2 ** level, 2 ** F)
+    outcome = "split"
+    if periodic and rq * 2 ** level >= periodic_rs(n):
+        t1 = Fr(periodic_rs(n), 2 ** F)
+        outcome = "stop"
     times = {t0, t1}
     for a in range(3):
         d = abs(sd[a])
@@ -102,10 +114,10 @@ def ray_segments(n: int, cell0, sd, level: int, rq: int):
         for a in range(3):
             pos = Fr(2 * cell0[a] + 1, 2) + tm * Fr(sd[a], 2 ** S)
             cell.append(math.floor(pos))
-        if any(c < 0 or c >= n for c in cell):
+        if not periodic and any(c < 0 or c >= n for c in cell):
             return segs, "escape"
         segs.append((tuple(cell), ta, tb))
-    return segs, "split"
+    return segs, outcome
 
 
 def face_distance(cell, sd, tm, cell0):
@@ -121,8 +133,9 @@ def face_distance(cell, sd, tm, cell0):
 
 
 def trace(n_h, x, cells, ndot, box_cm, sigma=6.3e-18, n_min=4.0, tau_max=30.0, level_max=None,
-          overlap_mode=0, n_th=0.0):
-    """Gamma field and visit list by brute force (FP64 physics)."""
+          overlap_mode=0, n_th=0.0, periodic=False):
+    """Gamma field and visit list by brute force (FP64 physics); periodic:
+    cells wrap around the box and rays stop at travel distance sqrt(3) n."""
     n = n_h.shape[0]
     dx = box_cm / n
     nhi = (1.0 - x) * n_h
@@ -147,10 +160,11 @@ def trace(n_h, x, cells, ndot, box_cm, sigma=6.3e-18, n_min=4.0, tau_max=30.0, l
             counts["rays"][lvl] = counts["rays"].get(lvl, 0) + 1
             sd = quantise(healpix_nest_vec(lvl, pix))
             nrm = math.sqrt(sum(v * v for v in sd)) / 2 ** S
-            segs, outcome = ray_segments(n, c0, sd, lvl, rq)
+            segs, outcome = ray_segments(n, c0, sd, lvl, rq, periodic)
             rid = (j << 36) | (lvl << 31) | pix
             dropped = False
-            for seq, (cell, ta, tb) in enumerate(segs):
+            for seq, (ucell, ta, tb) in enumerate(segs):
+                cell = tuple(c % n for c in ucell)       # the same cell unless periodic
                 ix, iy, iz = cell
                 ds = float(tb - ta) * nrm
                 k = kap[iz, iy, ix]
@@ -165,7 +179,7 @@ def trace(n_h, x, cells, ndot, box_cm, sigma=6.3e-18, n_min=4.0, tau_max=30.0, l
                 nb = None
                 if overlap_mode != 0:
                     tm = (ta + tb) / 2
-                    dist = face_distance(cell, sd, tm, c0)
+                    dist = face_distance(ucell, sd, tm, c0)
                     q = min(range(6), key=lambda i: (dist[i], i))
                     de = float(dist[q])
                     lpix = float(tm) * nrm * math.sqrt(math.pi / 3.0) / 2 ** lvl
@@ -175,6 +189,8 @@ def trace(n_h, x, cells, ndot, box_cm, sigma=6.3e-18, n_min=4.0, tau_max=30.0, l
                         else:
                             nbc = list(cell)
                             nbc[q // 2] += 1 if q % 2 else -1
+                            if periodic:
+                                nbc = [v % n for v in nbc]
                             if all(0 <= v < n for v in nbc):
                                 kn = kap[nbc[2], nbc[1], nbc[0]]
                                 ok = elig[nbc[2], nbc[1], nbc[0]] if overlap_mode == 3 else kn > 0
@@ -192,7 +208,7 @@ def trace(n_h, x, cells, ndot, box_cm, sigma=6.3e-18, n_min=4.0, tau_max=30.0, l
                 if tau >= tau_max:
                     dropped = True
                     break
-            if dropped or outcome == "escape":
+            if dropped or outcome != "split":
                 continue
             if lvl + 1 > level_max:
                 continue

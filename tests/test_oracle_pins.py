@@ -137,6 +137,89 @@ def test_oracle_matches_brute_force(seed, mode, n_th_frac, xmode):
         assert st["splits"][lvl] == c
 
 
+# ------------------------------------------------------------------ periodic boundaries (Sec. 2.5.1)
+
+@pytest.mark.parametrize("seed,mode,xmode", [(21, 0, "thin"), (22, 3, "mixed"), (23, 1, "patchy"), (24, 2, "mixed")])
+def test_periodic_oracle_matches_brute_force(seed, mode, xmode):
+    """Periodic boundaries: cells wrap, rays stop at travel distance sqrt(3) n
+    (and do not split there); the brute force lists the same segments from
+    exact crossing times in the unwrapped frame."""
+    n = 5 if seed % 2 else 4
+    w = I.random_small(n, 2, seed=seed, x_mode=xmode, box_cm=n * 3e21)
+    uc, inv = np.unique(w.cells, axis=0, return_inverse=True)
+    w.ndot = np.bincount(inv.reshape(-1), weights=w.ndot)
+    w.cells = uc.astype(np.int32)
+    n_th = 0.3 * float(w.n_h.mean())
+    g, vis, cnt = bt.trace(w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, overlap_mode=mode, n_th=n_th, periodic=True)
+    r = oracle.run_workload(w, record=2000000, overlap_mode=mode, n_th_cm3=n_th, periodic=1)
+    v = r["visits"]
+    assert v["total"] == len(vis)
+    ov = sorted(zip(v["ray"].tolist(), v["seq"].tolist(), v["cell"].tolist()))
+    bv = sorted((a, b, c) for a, b, c, _ in vis)
+    assert ov == bv
+    assert relerr(r["gamma"].reshape(-1), g.reshape(-1)) < 1e-12
+    st = r["stats"]
+    assert sum(st["secondary"]) == sum(cnt["secondary"].values())
+    for lvl, c in cnt["rays"].items():
+        assert st["rays"][lvl] == c
+    for lvl, c in cnt["splits"].items():
+        assert st["splits"][lvl] == c
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_periodic_translation_invariance(prec):
+    """On a periodic grid, moving the source by v and rolling the fields by v
+    rolls Gamma by v exactly: every ray sees the same cells relative to its
+    source, in the same order, so even the floating-point sums are equal."""
+    n = 12
+    w = I.random_small(n, 1, seed=31, x_mode="mixed", box_cm=n * 3e21)
+    v = (5, -3, 7)
+    c = np.array([[3, 9, 1]], np.int32)
+    cv = ((c + np.array(v)) % n).astype(np.int32)
+    roll = lambda a: np.roll(a, shift=(v[2], v[1], v[0]), axis=(0, 1, 2))   # arrays are [z, y, x]
+    kw = dict(n_th_cm3=0.3 * float(w.n_h.mean()), periodic=1, precision=prec, overlap_mode=3)
+    a = oracle.run(w.n_h, w.x_ion, c, w.ndot[:1], w.box_cm, **kw)
+    b = oracle.run(roll(w.n_h), roll(w.x_ion), cv, w.ndot[:1], w.box_cm, **kw)
+    assert sum(a["stats"]["segments"]) > 10000
+    assert np.array_equal(roll(a["gamma"]), b["gamma"])
+    for k in ("rays", "splits", "segments", "secondary", "escaped", "dropped_tau"):
+        assert a["stats"][k] == b["stats"][k]
+
+
+def test_periodic_thin_path_sum():
+    """Thin periodic medium: every root-to-leaf chain of rays covers exactly
+    the travel distance sqrt(3) n, so sum(Gamma) = Ndot sigma sqrt(3) n / dx^2
+    (up to direction quantisation, 2e-6); rays end there, none escapes earlier."""
+    n = 16
+    n_h = np.full((n, n, n), 2e-4)
+    x = np.ones((n, n, n))
+    box = n * 7.117e23
+    ndot = np.array([1e52])
+    r = oracle.run(n_h, x, np.array([[3, 11, 6]], np.int32), ndot, box, overlap_mode=0, periodic=1)
+    st = r["stats"]
+    rs = oracle.periodic_rs(n)
+    rq = oracle.split_rq(4.0)
+    last = next(l for l in range(20) if (rq << l) >= rs)
+    for lvl in range(last + 1):
+        assert st["rays"][lvl] == 12 * 4 ** lvl
+        assert st["escaped"][lvl] == (12 * 4 ** lvl if lvl == last else 0)
+    dx = box / n
+    expect = ndot[0] * 6.3e-18 * (rs * 2.0 ** -24) / dx ** 2
+    assert abs(r["gamma"].sum() / expect - 1) < 2e-6
+    assert abs(st["absorbed_ph"]) == 0 and abs(st["escaped_ph"] / st["emitted_ph"] - 1) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_periodic_photon_ledger(prec):
+    w = I.random_small(20, 5, seed=41, x_mode="mixed", box_cm=20 * 3e21)
+    r = oracle.run_workload(w, precision=prec, periodic=1, overlap_mode=3)
+    st = r["stats"]
+    e = st["emitted_ph"]
+    tol = 1e-12 if prec == 0 else 1e-6
+    assert abs(st["absorbed_ph"] + st["escaped_ph"] + st["dropped_ph"] - e) / e < tol
+    assert abs(st["deposited_ph"] - st["absorbed_ph"]) / e < tol
+
+
 # ------------------------------------------------------------------ closed forms
 
 def test_opaque_source_cell_closed_form():
