@@ -90,6 +90,9 @@ typedef struct rt_config {
     double chem_tol;           /* convergence: max |<x>_new - <x>_old| < chem_tol */
     int32_t chem_max_iter;     /* iteration cap */
     int32_t flags;             /* RT_FLAG_* bits */
+    int32_t periodic;          /* 1: periodic boundaries (Sec. 2.5.1): rays wrap around the box and
+                                  stop once they have travelled sqrt(3) box lengths (without
+                                  splitting; their remaining photons count as escaped) */
 } rt_config;
 
 #define RT_FLAG_VISIT_HASH 1   /* accumulate the visit-list hash in rt_stats (bookkeeping check) */

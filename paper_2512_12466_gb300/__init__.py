@@ -44,6 +44,7 @@ class rt_config(C.Structure):
         ("merge_rmax_cells", C.c_double), ("merge_f_ov", C.c_double), ("merge_eps", C.c_double),
         ("merge_n_min", C.c_int32), ("chem_iterate", C.c_int32), ("alpha_B", C.c_double), ("C_H", C.c_double),
         ("clumping", C.c_double), ("chem_tol", C.c_double), ("chem_max_iter", C.c_int32), ("flags", C.c_int32),
+        ("periodic", C.c_int32),
     ]
 
 

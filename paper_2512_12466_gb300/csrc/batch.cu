@@ -394,13 +394,14 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
         b->use_geo = b->precision == RT_FP32 && !b->hs.empty();
         int nmax = 0;
         for (rt_handle* h : b->hs) {
-            if (h->rq != b->hs[0]->rq || (h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE)) b->use_geo = false;
+            if (h->rq != b->hs[0]->rq || h->rs != b->hs[0]->rs || (h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE))
+                b->use_geo = false;
             nmax = std::max(nmax, h->cfg.n);
         }
         for (int l = 0; l <= RT_MAX_LEVELS; ++l) b->geo[l] = GeomLevel();
         for (int l = 0; b->use_geo && l <= table_level; ++l)
-            if (!geometry_level(b->device, b->hs[0]->rq, l, nmax, b->dirs + healpix_level_offset(l), b->stream,
-                                &b->geo[l]))
+            if (!geometry_level(b->device, b->hs[0]->rq, l, nmax, b->hs[0]->rs, b->dirs + healpix_level_offset(l),
+                                b->stream, &b->geo[l]))
                 b->use_geo = false;
     }
     // ---- all solves' emitted sources in one catalog, tagged with their solve index
@@ -449,6 +450,7 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
         s.overlap_mode = h->cfg.overlap_mode;
         s.hash = (h->cfg.flags & RT_FLAG_VISIT_HASH) ? 1 : 0;
         s.rq = h->rq;
+        s.rs = h->rs;
         s.tau_max = h->cfg.tau_max;
         s.src_off = (uint32_t)first;
         s.pad_ = 0;

@@ -161,7 +161,21 @@ struct SolveView {
     long long rq;
     R tau_max;
     uint32_t src_off;        // first catalog index of this solve (ray ids are solve-local)
+    long long rs;            // periodic boundaries: travel-distance cutoff sqrt(3) n (2^-24 cells); 0: none
 };
+
+// Periodic boundaries (Sec. 2.5.1): a coordinate moved by one cell wraps around the box.
+__device__ __forceinline__ int wrap1(const int v, const int n)
+{
+    return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+// A coordinate any number of boxes away, wrapped into [0, n).
+__device__ __forceinline__ int wrapn(const int v, const int n)
+{
+    const int r = v % n;
+    return r < 0 ? r + n : r;
+}
 
 // March one ray of level l (source entry se, quantised direction dv, budget
 // P with compensation cP, optical depth tau with compensation ctau) from its
@@ -175,7 +189,12 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
 {
     using I = Ieee<R>;
     const int n = V.n;
-    const long long rq_end = V.rq << l;
+    // the ray ends on its split sphere R_l or, with periodic boundaries, at the travel distance
+    // sqrt(3) L_box if that comes first or at the same point, where it stops without splitting
+    const bool periodic = V.rs != 0;
+    const long long rq_split = V.rq << l;
+    const bool split_end = !periodic || rq_split < V.rs;
+    const long long rq_end = split_end ? rq_split : V.rs;
     const long long rq_start = l > 0 ? (V.rq << (l - 1)) : 0;
     const R pV = I::pow2(-(S - 1 + F)), pI = I::pow2(-S), pU = I::pow2(-(S + 1));
     bool split = false;
@@ -193,6 +212,11 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
     const int ke1 = (int)(((rq_end * D1 + kB - 1) >> (S - 1 + F)) >> 1);
     const int ke2 = (int)(((rq_end * D2 + kB - 1) >> (S - 1 + F)) >> 1);
     int i0 = se.cx + s0 * k0, i1 = se.cy + s1 * k1, i2 = se.cz + s2 * k2;
+    if (periodic) {
+        i0 = wrapn(i0, n);
+        i1 = wrapn(i1, n);
+        i2 = wrapn(i2, n);
+    }
     // A_ab = (2 k_a + 1) D_b: the next crossing on a comes before the one on b iff A_ab < A_ba.
     // With k_a <= t D_a / 2^21 + 1/2 and D_a D_b <= 2^41, A_ab <= t 2^21 + 2^22, which stays
     // below 2^32 while the ray parameter t is below 2040 (any point of a grid up to 1024^3).
@@ -268,6 +292,11 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
                 const int step = (up ? dax : oax) < (up ? oax : dax) ? 1 : -1;
                 int j0 = i0, j1 = i1, j2 = i2;
                 if (ax == 0) j0 += step; else if (ax == 1) j1 += step; else j2 += step;
+                if (periodic) {
+                    j0 = wrap1(j0, n);
+                    j1 = wrap1(j1, n);
+                    j2 = wrap1(j2, n);
+                }
                 if ((unsigned)j0 < (unsigned)n && (unsigned)j1 < (unsigned)n && (unsigned)j2 < (unsigned)n)
                     c2 = (j2 * n + j1) * n + j0;
             }
@@ -353,8 +382,14 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             const bool t0 = (w == 0) || (w == 1 ? A01 == A10 : A02 == A20);
             const bool t1 = (w == 1) || (w == 0 ? A10 == A01 : A12 == A21);
             const bool t2 = (w == 2) || (w == 0 ? A20 == A02 : A21 == A12);
-            const int ni0 = t0 ? i0 + s0 : i0, ni1 = t1 ? i1 + s1 : i1, ni2 = t2 ? i2 + s2 : i2;
-            const bool next_in = (unsigned)ni0 < (unsigned)n && (unsigned)ni1 < (unsigned)n && (unsigned)ni2 < (unsigned)n;
+            int ni0 = t0 ? i0 + s0 : i0, ni1 = t1 ? i1 + s1 : i1, ni2 = t2 ? i2 + s2 : i2;
+            if (periodic) {
+                ni0 = wrap1(ni0, n);
+                ni1 = wrap1(ni1, n);
+                ni2 = wrap1(ni2, n);
+            }
+            const bool next_in =
+                periodic || ((unsigned)ni0 < (unsigned)n && (unsigned)ni1 < (unsigned)n && (unsigned)ni2 < (unsigned)n);
             const R knext = next_in ? V.kap[(ni2 * n + ni1) * n + ni0] : (R)0;
             segment(kcur, ds_p, dn0, dn1, dn2, I::mul(I::small(2u * kw + 1u), hw));
             if (tau >= taumax) {             // photons spent
@@ -401,9 +436,10 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             }
         }
         if (alive) {
-            // ---- the last segment ends on the split sphere R_l, where k_b = kend_b on every axis
+            // ---- the last segment ends on the end sphere, where k_b = kend_b on every axis
             if (prev < 0) {
-                ds_p = I::mul((R)V.rq, I::pow2(l > 0 ? l - 1 - F : -F));
+                ds_p = split_end ? I::mul((R)V.rq, I::pow2(l > 0 ? l - 1 - F : -F))
+                                 : I::mul(I::of(rq_end - rq_start), I::pow2(-F));
             } else {
                 const long long num = rq_end * (long long)pick3(prev, D0, D1, D2) - (long long)(2 * kprev + 1) * kB;
                 ds_p = I::mul(I::of(num), I::mul(pick3(prev, h0, h1, h2), pV));
@@ -412,14 +448,18 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             const R e0 = I::mul(I::of((long long)(2 * ke0 + 1) * kB - rq_end * (long long)D0), pE);
             const R e1 = I::mul(I::of((long long)(2 * ke1 + 1) * kB - rq_end * (long long)D1), pE);
             const R e2 = I::mul(I::of((long long)(2 * ke2 + 1) * kB - rq_end * (long long)D2), pE);
-            segment(kcur, ds_p, e0, e1, e2, I::mul((R)V.rq, I::pow2(l - F)));
+            segment(kcur, ds_p, e0, e1, e2,
+                    split_end ? I::mul((R)V.rq, I::pow2(l - F)) : I::mul(I::of(rq_end), I::pow2(-F)));
             if (tau >= taumax) {
                 ++T.dtau;
                 T.dropph += ph * (widen(P) - widen(cP));
                 T.abs += ph * (B0 - (widen(P) - widen(cP)));
             } else {
                 T.abs += ph * (B0 - (widen(P) - widen(cP)));
-                if (l + 1 > V.level_max) {
+                if (!split_end) {                // travelled sqrt(3) L_box (Sec. 2.5.1)
+                    ++T.esc;
+                    T.escph += ph * (widen(P) - widen(cP));
+                } else if (l + 1 > V.level_max) {
                     ++T.dlev;
                     T.dropph += ph * (widen(P) - widen(cP));
                 } else {
@@ -477,11 +517,13 @@ struct Walk {
     int i0, i1, i2;          // the current cell
 
     // Start cell of the ray from cell (c0, c1, c2): the cell holding its point on R_{l-1}.
+    // rs: travel-distance cutoff of periodic boundaries (0: none), as in march_ray.
     __device__ __forceinline__ void init(const long long rq, const int l, const int4 dv, const int c0, const int c1,
-                                         const int c2)
+                                         const int c2, const long long rs)
     {
         using I = Ieee<R>;
-        const long long rq_end = rq << l;
+        const bool split_end = rs == 0 || (rq << l) < rs;
+        const long long rq_end = split_end ? (rq << l) : rs;
         const long long rq_start = l > 0 ? (rq << (l - 1)) : 0;
         D0 = (unsigned)abs(dv.x);
         D1 = (unsigned)abs(dv.y);
@@ -541,10 +583,11 @@ struct Walk {
     // cell; it returns false to stop the ray. Returns kWalkEnd (R_l reached), kWalkEscaped (left
     // the grid) or kWalkStopped.
     template <class Seg>
-    __device__ __forceinline__ int run(const int n, const long long rq, const int l, Seg&& seg)
+    __device__ __forceinline__ int run(const int n, const long long rq, const int l, const long long rs, Seg&& seg)
     {
         using I = Ieee<R>;
-        const long long rq_end = rq << l;
+        const bool split_end = rs == 0 || (rq << l) < rs;
+        const long long rq_end = split_end ? (rq << l) : rs;
         const long long rq_start = l > 0 ? (rq << (l - 1)) : 0;
         const R pV = I::pow2(-(S - 1 + F)), pI = I::pow2(-S);
         // first event: the smallest next crossing (ties x, y, z), or the split sphere
@@ -618,10 +661,10 @@ struct Walk {
                 }
             }
         }
-        // ---- the last segment ends on the split sphere R_l, where k_b = kend_b on every axis
+        // ---- the last segment ends on the end sphere, where k_b = kend_b on every axis
         SegGeo<R> g;
         if (prev < 0) {
-            g.ds_p = I::mul((R)rq, I::pow2(l > 0 ? l - 1 - F : -F));
+            g.ds_p = split_end ? I::mul((R)rq, I::pow2(l > 0 ? l - 1 - F : -F)) : I::mul(I::of(rq_end - rq_start), I::pow2(-F));
         } else {
             const long long num = rq_end * (long long)pick3(prev, D0, D1, D2) - (long long)(2 * kprev + 1) * kB;
             g.ds_p = I::mul(I::of(num), I::mul(pick3(prev, h0, h1, h2), pV));
@@ -630,7 +673,7 @@ struct Walk {
         g.dn0 = I::mul(I::of((long long)(2 * ke0 + 1) * kB - rq_end * (long long)D0), pE);
         g.dn1 = I::mul(I::of((long long)(2 * ke1 + 1) * kB - rq_end * (long long)D1), pE);
         g.dn2 = I::mul(I::of((long long)(2 * ke2 + 1) * kB - rq_end * (long long)D2), pE);
-        g.tnext = I::mul((R)rq, I::pow2(l - F));
+        g.tnext = split_end ? I::mul((R)rq, I::pow2(l - F)) : I::mul(I::of(rq_end), I::pow2(-F));
         g.steps = 0u;
         g.ni0 = i0;
         g.ni1 = i1;
@@ -724,26 +767,34 @@ __device__ __forceinline__ void append_split(bool split, uint32_t si, uint32_t p
 
 constexpr unsigned kFBase = 0x3efffff0u;     // float bits of 0.5 - 2^-21
 
-// Walk pixel p of level l from a source at the centre of a virtual grid of 2 n_cover - 1
-// cells: a cell offset of n_cover or more along any axis lies outside every n_cover^3 grid
-// for every source cell, so that is where the table of the pixel may stop.
-__device__ __forceinline__ void geom_walk_init(Walk<float>& W, const long long rq, const int l, const int4 dv,
-                                               const int n_cover)
+// Walk pixel p of level l from a source at the centre of a virtual grid. Without periodic
+// boundaries it has 2 n_cover - 1 cells: a cell offset of n_cover or more along any axis lies
+// outside every n_cover^3 grid for every source cell, so that is where the table of the pixel may
+// stop. With them (rs > 0) the ray continues to the travel-distance cutoff, so the virtual grid is
+// wide enough never to be left first (relative cells are what the table stores; the march wraps).
+__device__ __forceinline__ int geom_virtual_grid(const int n_cover, const long long rs)
 {
-    W.init(rq, l, dv, n_cover - 1, n_cover - 1, n_cover - 1);
+    return rs ? 2 * ((int)(rs >> F) + 3) + 1 : 2 * n_cover - 1;
+}
+
+__device__ __forceinline__ void geom_walk_init(Walk<float>& W, const long long rq, const int l, const int4 dv,
+                                               const int nv, const long long rs)
+{
+    const int c = (nv - 1) / 2;
+    W.init(rq, l, dv, c, c, c, rs);
 }
 
 __global__ void __launch_bounds__(256) geom_count_kernel(const long long rq, const int l, const int4* __restrict__ dirs,
-                                                         const long long npix, const int n_cover,
+                                                         const long long npix, const int n_cover, const long long rs,
                                                          unsigned* __restrict__ rows)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     unsigned cnt = 0;
     if (p < npix) {
         Walk<float> W;
-        geom_walk_init(W, rq, l, dirs[p], n_cover);
-        const int nv = 2 * n_cover - 1;
-        if (W.inside(nv)) W.run(nv, rq, l, [&](const SegGeo<float>&) -> bool { ++cnt; return true; });
+        const int nv = geom_virtual_grid(n_cover, rs);
+        geom_walk_init(W, rq, l, dirs[p], nv, rs);
+        if (W.inside(nv)) W.run(nv, rq, l, rs, [&](const SegGeo<float>&) -> bool { ++cnt; return true; });
     }
     // rows of a 32-pixel block: the longest column in it
     for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(0xffffffffu, cnt, o));
@@ -751,19 +802,19 @@ __global__ void __launch_bounds__(256) geom_count_kernel(const long long rq, con
 }
 
 __global__ void __launch_bounds__(256) geom_fill_kernel(const long long rq, const int l, const int4* __restrict__ dirs,
-                                                        const long long npix, const int n_cover,
+                                                        const long long npix, const int n_cover, const long long rs,
                                                         const unsigned long long* __restrict__ row0,
                                                         uint2* __restrict__ ent, unsigned* err)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= npix) return;
     Walk<float> W;
-    geom_walk_init(W, rq, l, dirs[p], n_cover);
-    const int nv = 2 * n_cover - 1;
+    const int nv = geom_virtual_grid(n_cover, rs);
+    geom_walk_init(W, rq, l, dirs[p], nv, rs);
     if (!W.inside(nv)) return;
     uint2* col = ent + row0[p >> 5] * 32 + (p & 31);
     unsigned long long s = 0;
-    W.run(nv, rq, l, [&](const SegGeo<float>& g) -> bool {
+    W.run(nv, rq, l, rs, [&](const SegGeo<float>& g) -> bool {
         const Edge<float> e = edge<float>(W, g, true);
         unsigned y = g.steps << 24;
         if (e.near) {
@@ -796,6 +847,15 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
         i1 += s1 * (int)((rq_start * (unsigned)abs(dv.y) + kB) >> (S + F));
         i2 += s2 * (int)((rq_start * (unsigned)abs(dv.z) + kB) >> (S + F));
     }
+    // periodic boundaries: cells wrap, and the ray's last entry ends at the travel-distance cutoff
+    // instead of R_l when that comes first
+    const bool periodic = V.rs != 0;
+    const bool split_end = !periodic || (V.rq << l) < V.rs;
+    if (periodic) {
+        i0 = wrapn(i0, n);
+        i1 = wrapn(i1, n);
+        i2 = wrapn(i2, n);
+    }
     const float G = se.gf;
     const double ph = se.ph;
     const float taumax = V.tau_max;
@@ -822,10 +882,16 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
         const bool last = (e.y >> 31) != 0u;
         const uint2 en = last ? make_uint2(0u, 0u) : col[(unsigned long long)(seq + 1) * 32];
         const unsigned steps = (e.y >> 24) & 7u;
-        const int ni0 = (steps & 1u) ? i0 + s0 : i0;
-        const int ni1 = (steps & 2u) ? i1 + s1 : i1;
-        const int ni2 = (steps & 4u) ? i2 + s2 : i2;
-        const bool next_in = (unsigned)ni0 < (unsigned)n && (unsigned)ni1 < (unsigned)n && (unsigned)ni2 < (unsigned)n;
+        int ni0 = (steps & 1u) ? i0 + s0 : i0;
+        int ni1 = (steps & 2u) ? i1 + s1 : i1;
+        int ni2 = (steps & 4u) ? i2 + s2 : i2;
+        if (periodic) {
+            ni0 = wrap1(ni0, n);
+            ni1 = wrap1(ni1, n);
+            ni2 = wrap1(ni2, n);
+        }
+        const bool next_in =
+            periodic || ((unsigned)ni0 < (unsigned)n && (unsigned)ni1 < (unsigned)n && (unsigned)ni2 < (unsigned)n);
         const int ncell = (ni2 * n + ni1) * n + ni0;
         const float knext = (steps && next_in) ? V.kap[ncell] : 0.f;
         const bool near = corr && ((e.y >> 27) & 1u);
@@ -834,7 +900,12 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
             const int ax = (int)((e.y >> 28) & 3u);
             const int step = ((e.y >> 30) & 1u) ? 1 : -1;
             const int jc = pick3(ax, i0, i1, i2) + step;
-            if ((unsigned)jc < (unsigned)n) c2 = cell + step * (ax == 0 ? 1 : (ax == 1 ? n : (int)nn));
+            if (periodic) {
+                const int jw = wrap1(jc, n);
+                c2 = cell + (jw - (jc - step)) * (ax == 0 ? 1 : (ax == 1 ? n : (int)nn));
+            } else if ((unsigned)jc < (unsigned)n) {
+                c2 = cell + step * (ax == 0 ? 1 : (ax == 1 ? n : (int)nn));
+            }
         }
         const float kn_raw = c2 >= 0 ? V.kap[c2] : 0.f;
         // ---- Eq. 1 for this segment
@@ -882,8 +953,11 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
             T.dropph += ph * (widen(P) - widen(cP));
             break;
         }
-        if (!steps) {                    // the segment ended on R_l
-            if (l + 1 > V.level_max) {
+        if (!steps) {                    // the segment ended on the end sphere
+            if (!split_end) {            // travelled sqrt(3) L_box (Sec. 2.5.1)
+                ++T.esc;
+                T.escph += ph * (widen(P) - widen(cP));
+            } else if (l + 1 > V.level_max) {
                 ++T.dlev;
                 T.dropph += ph * (widen(P) - widen(cP));
             } else {
@@ -1017,6 +1091,7 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
     V.rq = A.rq;
     V.tau_max = A.tau_max;
     V.src_off = 0;
+    V.rs = A.rs;
     Tally T;
     T.clear();
     for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
@@ -1055,6 +1130,7 @@ __global__ void __launch_bounds__(256, 4) march_table_kernel(const MarchArgs<flo
     V.rq = A.rq;
     V.tau_max = A.tau_max;
     V.src_off = 0;
+    V.rs = A.rs;
     Tally T;
     T.clear();
     for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
@@ -1150,6 +1226,7 @@ __global__ void __launch_bounds__(256, (kTable && kSingle) ? 4 : MarchOccupancy<
                     V.overlap_mode = bs.overlap_mode;
                     V.hash = bs.hash;
                     V.rq = bs.rq;
+                    V.rs = bs.rs;
                     V.tau_max = (R)bs.tau_max;
                     V.src_off = bs.src_off - A.src_base;
                     if constexpr (kTable) {
@@ -1201,18 +1278,18 @@ int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int gr
     return 1;
 }
 
-void launch_geom_count(long long rq, int l, const int4* dirs, long long npix, int n_cover, unsigned* rows,
-                       cudaStream_t s)
+void launch_geom_count(long long rq, int l, const int4* dirs, long long npix, int n_cover, long long rs,
+                       unsigned* rows, cudaStream_t s)
 {
     const long long grid = (npix + 255) / 256;
-    geom_count_kernel<<<(unsigned)grid, 256, 0, s>>>(rq, l, dirs, npix, n_cover, rows);
+    geom_count_kernel<<<(unsigned)grid, 256, 0, s>>>(rq, l, dirs, npix, n_cover, rs, rows);
 }
 
-void launch_geom_fill(long long rq, int l, const int4* dirs, long long npix, int n_cover,
+void launch_geom_fill(long long rq, int l, const int4* dirs, long long npix, int n_cover, long long rs,
                       const unsigned long long* row0, uint2* ent, unsigned* err, cudaStream_t s)
 {
     const long long grid = (npix + 255) / 256;
-    geom_fill_kernel<<<(unsigned)grid, 256, 0, s>>>(rq, l, dirs, npix, n_cover, row0, ent, err);
+    geom_fill_kernel<<<(unsigned)grid, 256, 0, s>>>(rq, l, dirs, npix, n_cover, rs, row0, ent, err);
 }
 
 template <class R, bool kSingle>

@@ -132,6 +132,7 @@ struct Ctx {
     unsigned long long* count;
     int n;
     int64_t rq;
+    int64_t rs;          // periodic boundaries: travel-distance cutoff (2^-24 cells); 0: none
     int level_max;
     int table_level;
     int64_t n_emit;
@@ -169,6 +170,7 @@ int na_level(Ctx& c, int level, int64_t nparents)
         a.kap = static_cast<const R*>(c.kap);
         a.gamma = c.gamma;
         a.rq = c.rq;
+        a.rs = c.rs;
         a.level_max = c.level_max;
         a.tau_max = (R)c.tau_max;
         a.overlap_mode = c.overlap_mode;
@@ -244,6 +246,7 @@ extern "C" int rt_step_noalloc(const rt_config* cfg, void* cuda_stream, const do
     c.count = reinterpret_cast<unsigned long long*>(base + kOffCount);
     c.n = n;
     c.rq = rq;
+    c.rs = cfg->periodic ? (int64_t)std::floor(std::sqrt(3.0) * (double)n * (double)(1 << kRadBits) + 0.5) : 0;
     c.level_max = level_max;
     c.table_level = table_level;
     c.kap = base + kOffKap;

@@ -89,6 +89,7 @@ namespace {
 // not fit is marched by walking its rays instead.
 struct GeomTable {
     long long rq;
+    long long rs;             // periodic travel-distance cutoff; 0: none
     int level;
     int n_cover;
     bool complete;            // no pixel cut short: serves every grid size
@@ -116,19 +117,20 @@ size_t geometry_budget(int device)
 
 }  // namespace
 
-bool nyx::geometry_level(int device, long long rq, int level, int n, const int4* dirs_level, cudaStream_t s,
-                         GeomLevel* out)
+bool nyx::geometry_level(int device, long long rq, int level, int n, long long rs, const int4* dirs_level,
+                         cudaStream_t s, GeomLevel* out)
 {
     std::lock_guard<std::mutex> lk(g_geom_mu);
     std::vector<GeomTable>& list = g_geom[device];
     for (const GeomTable& t : list)
-        if (t.rq == rq && t.level == level && (t.complete || t.n_cover >= n)) {
+        if (t.rq == rq && t.rs == rs && t.level == level && (t.complete || t.n_cover >= n)) {
             if (t.usable) *out = t.g;
             return t.usable;
         }
-    GeomTable t{rq, level, n, false, false, GeomLevel()};
-    // every ray reaches R_l inside the virtual grid of 2n - 1 cells when R_l + 1 < n
-    t.complete = std::ldexp((double)rq, level - kRadBits) + 2.0 < (double)n;
+    GeomTable t{rq, rs, level, n, false, false, GeomLevel()};
+    // every ray reaches R_l inside the virtual grid of 2n - 1 cells when R_l + 1 < n; with periodic
+    // boundaries the table runs to the travel-distance cutoff, fixed by rs alone
+    t.complete = rs != 0 || std::ldexp((double)rq, level - kRadBits) + 2.0 < (double)n;
     const long long npix = 12LL << (2 * level);
     const long long nb = (npix + 31) / 32;
     unsigned* d_rows = nullptr;
@@ -141,7 +143,7 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, const int4*
     bool ok = cudaMalloc(&d_rows, sizeof(unsigned) * (size_t)nb) == cudaSuccess &&
               cudaMalloc(&d_err, sizeof(unsigned)) == cudaSuccess;
     if (ok) {
-        launch_geom_count(rq, level, dirs_level, npix, n, d_rows, s);
+        launch_geom_count(rq, level, dirs_level, npix, n, rs, d_rows, s);
         ok = cudaMemcpyAsync(rows.data(), d_rows, sizeof(unsigned) * (size_t)nb, cudaMemcpyDeviceToHost, s) ==
                  cudaSuccess &&
              cudaStreamSynchronize(s) == cudaSuccess;
@@ -161,7 +163,7 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, const int4*
              cudaMemsetAsync(d_err, 0, sizeof(unsigned), s) == cudaSuccess;
     }
     if (ok) {
-        launch_geom_fill(rq, level, dirs_level, npix, n, row0, ent, d_err, s);
+        launch_geom_fill(rq, level, dirs_level, npix, n, rs, row0, ent, d_err, s);
         ok = cudaMemcpyAsync(&herr, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
              cudaStreamSynchronize(s) == cudaSuccess && herr == 0;
     }
@@ -307,6 +309,7 @@ int run_level(rt_handle* h, int level, int64_t nparents)
         a.tau_max = (R)h->cfg.tau_max;
         a.overlap_mode = h->cfg.overlap_mode;
         a.hash = (h->cfg.flags & RT_FLAG_VISIT_HASH) ? 1 : 0;
+        a.rs = h->rs;
         a.st = h->d_st;
         const int64_t warps = (c1 - c0 + 31) / 32;
         const int64_t want = (warps + kMarchBlock / 32 - 1) / (kMarchBlock / 32);
@@ -314,7 +317,7 @@ int run_level(rt_handle* h, int level, int64_t nparents)
         // FP32: the level's geometry table (built once per device, outside the timed launch)
         GeomLevel gl;
         const bool table = sizeof(R) == 4 && !(h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE) &&
-                           geometry_level(h->device, h->rq, level, h->cfg.n, a.dirs, h->stream, &gl);
+                           geometry_level(h->device, h->rq, level, h->cfg.n, h->rs, a.dirs, h->stream, &gl);
         RT_CUDA(h, cudaEventRecord(h->ev[4], h->stream), "event");
         if constexpr (sizeof(R) == 8) {
             launch_march_f64(a, grid, kMarchBlock, h->stream);
@@ -531,6 +534,9 @@ int configure(rt_handle* h, const rt_config* cfg, std::string& why)
     h->s_over_dx2 = cfg->sigma_cm2 / (h->dx * h->dx);
     // R_0 = sqrt(3 / (pi N_min)) in units of 2^-24 cells (Eq. 4 with Omega_c = dx^2 / R^2)
     h->rq = (int64_t)std::floor(std::sqrt(3.0 / (3.141592653589793 * cfg->n_min_ray)) * (double)(1 << kRadBits) + 0.5);
+    // periodic boundaries (Sec. 2.5.1): rays stop at travel distance sqrt(3) L_box = sqrt(3) n cells,
+    // in the same fixed point as the split radius
+    h->rs = cfg->periodic ? (int64_t)std::floor(std::sqrt(3.0) * (double)n * (double)(1 << kRadBits) + 0.5) : 0;
     // smallest level whose split sphere encloses the grid from any cell centre
     int reach = 0;
     while (std::ldexp((double)h->rq, reach - kRadBits) < std::sqrt(3.0) * (double)n) ++reach;
@@ -553,6 +559,7 @@ bool valid_config(const rt_config* c, std::string& why)
     if (c->merge_samp_level < 0 || c->merge_samp_level > 4) { why = "merge_samp_level must be 0..4"; return false; }
     if (!(c->merge_dr_cells > 0)) { why = "merge_dr_cells must be positive"; return false; }
     if (c->level_max > kMaxLevel) { why = "level_max must be <= 13"; return false; }
+    if (c->periodic != 0 && c->periodic != 1) { why = "periodic must be 0 or 1"; return false; }
     return true;
 }
 

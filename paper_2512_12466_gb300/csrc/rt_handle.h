@@ -75,6 +75,7 @@ struct rt_handle {
     int64_t ncell = 0;
     double dx = 0, vol = 0, sdx = 0, s_over_dx2 = 0;
     int64_t rq = 0;
+    int64_t rs = 0;                          // periodic: travel-distance cutoff sqrt(3) n (2^-24 cells)
     int level_max = 0;
     int table_level = 0;
     const int4* dirs = nullptr;
@@ -125,8 +126,8 @@ int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out);
 int ensure_directions(int device, int level, const int4** out, std::string& err);
 // The geometry table of a level for grids of n cells (FP32 march), built on stream s if needed;
 // false if the level has none (over the device's table budget), so its rays are walked.
-bool geometry_level(int device, long long rq, int level, int n, const int4* dirs_level, cudaStream_t s,
-                    GeomLevel* out);
+bool geometry_level(int device, long long rq, int level, int n, long long rs, const int4* dirs_level,
+                    cudaStream_t s, GeomLevel* out);
 int handle_prepare_sources(rt_handle* h);
 int handle_reconfigure(rt_handle* h, const rt_config* cfg);
 int prepare_sources_many(rt_handle* const* hs, int count, int* rcs);

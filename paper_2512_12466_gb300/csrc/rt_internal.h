@@ -85,6 +85,7 @@ struct MarchArgs {
     R tau_max;
     int overlap_mode;
     int hash;
+    long long rs;                    // periodic boundaries: travel-distance cutoff (2^-24 cells); 0: none
     DevStats* st;
 };
 
@@ -108,6 +109,7 @@ struct BatchSolve {
     double tau_max;
     uint32_t src_off;        // index of this solve's first source in the batch catalog
     uint32_t pad_;
+    long long rs;            // periodic boundaries: travel-distance cutoff (2^-24 cells); 0: none
 };
 
 template <class R>
@@ -142,9 +144,10 @@ int batch_blocks_per_sm(int precision, int block, bool table, bool single);
 int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int grid, int block, cudaStream_t s);
 // Geometry-table generation for level l of directions dirs (npix pixels), for grids up to
 // n_cover: rows[b] = rows of 32-pixel block b; then the entries at row offsets row0.
-void launch_geom_count(long long rq, int l, const int4* dirs, long long npix, int n_cover, unsigned* rows,
-                       cudaStream_t s);
-void launch_geom_fill(long long rq, int l, const int4* dirs, long long npix, int n_cover,
+// rs: travel-distance cutoff of periodic boundaries (0: none).
+void launch_geom_count(long long rq, int l, const int4* dirs, long long npix, int n_cover, long long rs,
+                       unsigned* rows, cudaStream_t s);
+void launch_geom_fill(long long rq, int l, const int4* dirs, long long npix, int n_cover, long long rs,
                       const unsigned long long* row0, uint2* ent, unsigned* err, cudaStream_t s);
 
 // fields.cu

@@ -166,3 +166,23 @@ def test_batch_rejects_mixed_precision_and_chemistry(nyx):
         nyx.Batch([a, d])
     for s in (a, c, d):
         s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_periodic_matches_per_solve(nyx, precision):
+    """Periodic solves (Sec. 2.5.1) in one batch, FP32 with the geometry tables of
+    their shared grid size, against rt_step on each."""
+    ws = [I.random_small(24, 5 + j, seed=700 + j, x_mode=["thin", "mixed", "patchy"][j % 3], box_cm=24 * 3e21)
+          for j in range(4)]
+    solvers = [make_solver(nyx, w, precision, periodic=1) for w in ws]
+    ref = [plain(nyx, s, w.n) for s, w in zip(solvers, ws)]
+    b = nyx.Batch(solvers)
+    gs, hs, stats = run_batch(nyx, b, ws)
+    tol = 1e-12 if precision == 0 else 1e-10
+    for (gr, hr, sr), g, st in zip(ref, gs, stats):
+        for k in BOOK:
+            assert st[k] == sr[k], k
+        assert relerr(g, gr) < tol
+    b.close()
+    for s in solvers:
+        s.close()

@@ -19,7 +19,7 @@ BOOK = ("rays", "splits", "escaped", "dropped_tau", "dropped_level", "segments",
 NYX_KEYS = ("precision", "n_min_ray", "level_max", "overlap_mode", "tau_max", "n_th_cm3", "e_heat_erg",
             "merge_mode", "merge_samp_level", "automerge_xbar", "merge_x_th", "merge_f_req", "merge_dr_cells",
             "merge_rmax_cells", "merge_f_ov", "merge_eps", "merge_n_min", "chem_iterate", "alpha_B", "C_H",
-            "clumping", "chem_tol", "chem_max_iter", "flags")
+            "clumping", "chem_tol", "chem_max_iter", "flags", "periodic")
 
 
 @pytest.fixture(scope="module")
@@ -158,6 +158,38 @@ def test_geometry_table_equals_walk(nyx, case):
     b = run_gpu(nyx, w.n_h, w.x_ion, cells, ndot, w.box_cm, flags=nyx.RT_FLAG_NO_GEOMETRY_TABLE, **kw)
     assert_bookkeeping(a["stats"], b["stats"])
     assert relerr(a["gamma"], b["gamma"]) < 1e-6
+
+
+PERIODIC_CASES = [
+    # (n, sources, seed, x mode, box per cell, overlap mode, n_th fraction)
+    (1, 1, 401, "thin", 7e20, 3, 0.3),          # one cell: every neighbour is the cell itself
+    (2, 2, 402, "mixed", 3e21, 3, 0.3),
+    (9, 4, 403, "thin", 7e20, 3, 0.3),
+    (16, 6, 404, "mixed", 3e21, 2, 0.3),
+    (23, 8, 405, "patchy", 3e21, 1, 0.3),
+    (30, 5, 406, "thin", 2e21, 4, 0.01),
+]
+
+
+@pytest.mark.parametrize("prec,walk", [(0, False), (1, False), (1, True)], ids=["fp64", "fp32-table", "fp32-walk"])
+@pytest.mark.parametrize("case", PERIODIC_CASES)
+def test_periodic_parity(nyx, case, prec, walk):
+    """Periodic boundaries (Sec. 2.5.1) against the oracle: bookkeeping bit for
+    bit, fields within the FP64 / FP32 tolerances."""
+    n, k, seed, xm, dxc, mode, nth = case
+    w = I.random_small(n, k, seed=seed, x_mode=xm, box_cm=n * dxc)
+    n_th = nth * float(w.n_h.mean())
+    kw = dict(overlap_mode=mode, n_th_cm3=n_th, precision=prec, periodic=1)
+    ref, got = run_both(nyx, w, flags=nyx.RT_FLAG_NO_GEOMETRY_TABLE if walk else 0, **kw)
+    assert_bookkeeping(got["stats"], ref["stats"])
+    assert sum(got["stats"]["escaped"]) > 0              # rays that reached sqrt(3) L_box
+    if prec == 0:
+        assert relerr(got["gamma"], ref["gamma"]) < 1e-12
+        assert_ledger(got["stats"], 1e-12)
+    else:
+        ref64 = oracle.run_workload(w, **dict(kw, precision=0))
+        assert relerr(got["gamma"], ref64["gamma"]) < 1e-5
+        assert_ledger(got["stats"], 1e-6)
 
 
 def test_host_and_device_inputs_agree(nyx):
