@@ -89,9 +89,9 @@ def lib():
         L.orc_prepare_kappa.argtypes = [i64, P, P, d, d, P]
         L.orc_sources_dedup.argtypes = [P, P, i64, P, P]
         L.orc_sources_dedup.restype = i64
-        L.orc_max_radius.argtypes = [i32, P, P, i32, d, d, i32, d, d]
+        L.orc_max_radius.argtypes = [i32, P, P, i32, d, d, i32, d, d, i32]
         L.orc_max_radius.restype = d
-        L.orc_merge_sources.argtypes = [i32, P, P, P, i64, i32, d, d, i32, d, d, d, d, P, P, P, P]
+        L.orc_merge_sources.argtypes = [i32, P, P, P, i64, i32, d, d, i32, d, d, d, d, i32, P, P, P, P]
         L.orc_merge_sources.restype = i64
         L.orc_chem_update.argtypes = [i64, P, P, P, P, d, d, d, d, P]
         L.orc_chem_update.restype = d
@@ -159,15 +159,15 @@ def sources_dedup(cells, ndot):
     return oc[:m].copy(), on[:m].copy()
 
 
-def max_radius(x, cell, samp_level=3, x_th=0.9, f_req=0.9, n_min=8, dr=2.0, rmax=16.0) -> float:
+def max_radius(x, cell, samp_level=3, x_th=0.9, f_req=0.9, n_min=8, dr=2.0, rmax=16.0, periodic=0) -> float:
     x = np.ascontiguousarray(x, dtype=np.float64)
     n = x.shape[0]
     c = np.ascontiguousarray(cell, dtype=np.int32)
-    return float(lib().orc_max_radius(n, _ptr(x), _ptr(c), samp_level, x_th, f_req, n_min, dr, rmax))
+    return float(lib().orc_max_radius(n, _ptr(x), _ptr(c), samp_level, x_th, f_req, n_min, dr, rmax, periodic))
 
 
 def merge_sources(x, cells, ndot, samp_level=3, x_th=0.9, f_req=0.9, n_min=8, dr=2.0, rmax=16.0,
-                  f_ov=1.0, eps=1e-6):
+                  f_ov=1.0, eps=1e-6, periodic=0):
     """Alg. 3 on a deduplicated sorted catalog. Returns (cells, ndot, radius, label)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     n = x.shape[0]
@@ -179,7 +179,7 @@ def merge_sources(x, cells, ndot, samp_level=3, x_th=0.9, f_req=0.9, n_min=8, dr
     oc = np.zeros((max(s, 1), 3), dtype=np.int32)
     on = np.zeros(max(s, 1))
     m = lib().orc_merge_sources(n, _ptr(x), _ptr(cells), _ptr(ndot), s, samp_level, x_th, f_req, n_min,
-                                dr, rmax, f_ov, eps, _ptr(rad), _ptr(lab), _ptr(oc), _ptr(on))
+                                dr, rmax, f_ov, eps, periodic, _ptr(rad), _ptr(lab), _ptr(oc), _ptr(on))
     return oc[:m].copy(), on[:m].copy(), rad, lab
 
 

@@ -351,9 +351,20 @@ static int orc_i64_cmp(const void* a, const void* b)
     return x < y ? -1 : (x > y ? 1 : 0);
 }
 
-/* Alg. 3 MAX_RADIUS: grow shells by dr while the sampled shell is ionized. */
+/* Minimum-image component of a cell offset on a periodic grid of n cells:
+ * d mod n in [0, n), less n when above n/2. */
+static int64_t orc_minimg(int64_t d, int64_t n)
+{
+    int64_t r = ((d % n) + n) % n;
+    return 2 * r > n ? r - n : r;
+}
+
+/* Alg. 3 MAX_RADIUS: grow shells by dr while the sampled shell is ionized.
+ * With periodic boundaries a sample outside the grid wraps into it (the
+ * paper computes Alg. 3 under minimum-image geometry); otherwise it is not
+ * evaluated. */
 double orc_max_radius(int32_t n, const double* x, const int32_t c[3], int32_t samp_level,
-                      double x_th, double f_req, int32_t n_min, double dr, double rmax)
+                      double x_th, double f_req, int32_t n_min, double dr, double rmax, int32_t periodic)
 {
     const int64_t nn = n;
     if (x[((int64_t)c[2] * nn + c[1]) * nn + c[0]] < x_th) return 0.0;
@@ -374,6 +385,7 @@ double orc_max_radius(int32_t n, const double* x, const int32_t c[3], int32_t sa
             for (int a = 0; a < 3; a++) {
                 const double pos = ((double)c[a] + 0.5) + r * ((double)dirs[3 * p + a] / (double)(1 << ORC_S));
                 q[a] = (int64_t)floor(pos);
+                if (periodic) q[a] = ((q[a] % nn) + nn) % nn;
                 if (q[a] < 0 || q[a] >= nn) inside = 0;
             }
             if (inside) cellv[m++] = (q[2] * nn + q[1]) * nn + q[0];
@@ -425,11 +437,11 @@ static int orc_msrc_cmp(const void* pa, const void* pb)
  * `radius` receives the per-source bubble radii; `label` the group root. */
 int64_t orc_merge_sources(int32_t n, const double* x, const int32_t* cells, const double* ndot,
                           int64_t nsrc, int32_t samp_level, double x_th, double f_req, int32_t n_min,
-                          double dr, double rmax, double f_ov, double eps,
+                          double dr, double rmax, double f_ov, double eps, int32_t periodic,
                           double* radius, int64_t* label, int32_t* out_cells, double* out_ndot)
 {
     for (int64_t j = 0; j < nsrc; j++)
-        radius[j] = orc_max_radius(n, x, &cells[3 * j], samp_level, x_th, f_req, n_min, dr, rmax);
+        radius[j] = orc_max_radius(n, x, &cells[3 * j], samp_level, x_th, f_req, n_min, dr, rmax, periodic);
     int64_t* parent = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nsrc > 0 ? nsrc : 1));
     for (int64_t j = 0; j < nsrc; j++) parent[j] = j;
     for (int64_t a = 0; a < nsrc; a++) {
@@ -438,7 +450,8 @@ int64_t orc_merge_sources(int32_t n, const double* x, const int32_t* cells, cons
             if (!(radius[b] > 0)) continue;
             int64_t d2 = 0;
             for (int q = 0; q < 3; q++) {
-                const int64_t d = (int64_t)cells[3 * a + q] - cells[3 * b + q];
+                int64_t d = (int64_t)cells[3 * a + q] - cells[3 * b + q];
+                if (periodic) d = orc_minimg(d, n);                  /* minimum-image distance */
                 d2 += d * d;
             }
             const double rs = f_ov * (radius[a] + radius[b]);
@@ -460,10 +473,15 @@ int64_t orc_merge_sources(int32_t n, const double* x, const int32_t* cells, cons
         int64_t count = 0;
         for (int64_t j = g; j < nsrc; j++) {
             if (label[j] != g) continue;
+            /* periodic: each member unwrapped next to the group's first member */
+            double u[3];
+            for (int q = 0; q < 3; q++)
+                u[q] = periodic ? (double)(cells[3 * g + q] + orc_minimg((int64_t)cells[3 * j + q] - cells[3 * g + q], n))
+                                : (double)cells[3 * j + q];
             ftot += ndot[j];
-            sx += ndot[j] * (double)cells[3 * j];
-            sy += ndot[j] * (double)cells[3 * j + 1];
-            sz += ndot[j] * (double)cells[3 * j + 2];
+            sx += ndot[j] * u[0];
+            sy += ndot[j] * u[1];
+            sz += ndot[j] * u[2];
             count++;
         }
         if (count == 1) {
@@ -476,15 +494,20 @@ int64_t orc_merge_sources(int32_t n, const double* x, const int32_t* cells, cons
         int64_t rc[3];
         for (int q = 0; q < 3; q++) {
             rc[q] = (int64_t)floor(cen[q] + 0.5);
-            if (rc[q] < 0) rc[q] = 0;                  /* non-periodic: clamp into the grid */
-            if (rc[q] > n - 1) rc[q] = n - 1;
+            if (periodic) {
+                rc[q] = ((rc[q] % n) + n) % n;         /* wrap back into the grid */
+            } else {
+                if (rc[q] < 0) rc[q] = 0;              /* non-periodic: clamp into the grid */
+                if (rc[q] > n - 1) rc[q] = n - 1;
+            }
         }
         int64_t best = -1, bestd = 0;
         for (int64_t j = g; j < nsrc; j++) {
             if (label[j] != g) continue;
             int64_t d2 = 0;
             for (int q = 0; q < 3; q++) {
-                const int64_t d = (int64_t)cells[3 * j + q] - rc[q];
+                int64_t d = (int64_t)cells[3 * j + q] - rc[q];
+                if (periodic) d = orc_minimg(d, n);
                 d2 += d * d;
             }
             if (best < 0 || d2 < bestd) { best = j; bestd = d2; }
@@ -635,8 +658,8 @@ int orc_run(const orc_config* cfg, const double* n_h, const double* x_in, const 
         double* mn = (double*)malloc(sizeof(double) * (size_t)m);
         int64_t mm = orc_merge_sources(cfg->n, x_in, dc, dn, m, cfg->merge_samp_level, cfg->merge_x_th,
                                        cfg->merge_f_req, cfg->merge_n_min, cfg->merge_dr_cells,
-                                       cfg->merge_rmax_cells, cfg->merge_f_ov, cfg->merge_eps, rad, lab,
-                                       mc, mn);
+                                       cfg->merge_rmax_cells, cfg->merge_f_ov, cfg->merge_eps, cfg->periodic,
+                                       rad, lab, mc, mn);
         memcpy(dc, mc, sizeof(int32_t) * 3 * (size_t)mm);
         memcpy(dn, mn, sizeof(double) * (size_t)mm);
         m = mm;

@@ -501,6 +501,84 @@ def test_merge_components_match_dfs(seed):
     assert keys == sorted(keys)
 
 
+@pytest.mark.parametrize("cell", [[2, 30, 41], [45, 3, 20], [0, 47, 1]])
+def test_max_radius_periodic_equals_translated(cell):
+    """Alg. 3 under periodic (minimum-image) geometry: shell samples wrap. A
+    source near the faces of a periodic grid has the radius of the same
+    configuration translated so that no shell leaves the grid, traced without
+    periodicity."""
+    n = 48
+    x = np.ones((n, n, n))
+    # a neutral slab 3-6 cells beyond the nearer x face, i.e. across the boundary from the source
+    step = -1 if cell[0] < n // 2 else 1
+    for k in range(3, 7):
+        x[:, :, (cell[0] + step * k) % n] = 0.0 if abs(cell[0] + step * k - (n // 2)) > n // 2 - 1 else 1.0
+    v = [24 - c for c in cell]                          # moves the source to the centre
+    xr = np.roll(x, shift=(v[2], v[1], v[0]), axis=(0, 1, 2))
+    rp = oracle.max_radius(x, cell, rmax=16.0, periodic=1)
+    rt = oracle.max_radius(xr, [24, 24, 24], rmax=16.0, periodic=0)
+    assert rp == rt and rp > 0
+    rn = oracle.max_radius(x, cell, rmax=16.0, periodic=0)
+    assert rn != rp                                     # the non-periodic shells differ here
+
+
+def test_merge_periodic_minimum_image_and_unwrapped_centroid():
+    """Two sources across the x faces of a periodic, fully ionized grid are 3
+    cells apart under the minimum image and merge; without periodicity they are
+    45 apart and stay separate. The merged source is placed at the member next
+    to the centroid of the unwrapped pair (near the face), not at the naive
+    centroid in the middle of the box."""
+    n = 48
+    x = np.ones((n, n, n))
+    cells = np.array([[1, 20, 20], [46, 20, 20]], np.int32)
+    nd = np.array([3e52, 2e52])
+    mc, mn, rad, lab = oracle.merge_sources(x, cells, nd, rmax=4.0, periodic=1)
+    assert len(mn) == 1 and mn[0] == 5e52
+    # unwrapped: 1 and -2, centroid (3*1 + 2*(-2))/5 = -0.2 -> 0; nearest member by minimum image: x = 1
+    assert mc[0].tolist() == [1, 20, 20]
+    mc2, mn2, _, _ = oracle.merge_sources(x, cells, nd, rmax=4.0, periodic=0)
+    assert len(mn2) == 2
+    # the naive centroid (3*1 + 2*46)/5 = 19 would snap to x = 1 as well, so weight the far member
+    nd3 = np.array([1e52, 4e52])
+    mc3, _, _, _ = oracle.merge_sources(x, cells, nd3, rmax=4.0, periodic=1)
+    # unwrapped: (1*1 + 4*(-2))/5 = -1.4 -> -1 -> 47; nearest member by minimum image: x = 46
+    assert mc3[0].tolist() == [46, 20, 20]
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_merge_components_match_dfs_periodic(seed):
+    rng = np.random.default_rng(seed)
+    n = 24
+    # ionized balls (minimum-image distance, so they wrap) with sources scattered around their centres
+    zz, yy, xx = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    x = np.zeros((n, n, n))
+    centres = rng.integers(0, n, size=(6, 3))
+    for cx, cy, cz in centres:
+        d = [(a - c) % n for a, c in ((xx, cx), (yy, cy), (zz, cz))]
+        d = [np.where(2 * v > n, v - n, v) for v in d]
+        x[(d[0] ** 2 + d[1] ** 2 + d[2] ** 2) <= rng.uniform(4, 7) ** 2] = 1.0
+    pick = centres[rng.integers(0, 6, size=50)] + rng.integers(-3, 4, size=(50, 3))
+    cells = (pick % n).astype(np.int32)
+    c, nd = oracle.sources_dedup(cells, rng.uniform(1e50, 1e52, size=50))
+    mc, mn, rad, lab = oracle.merge_sources(x, c, nd, rmax=8.0, periodic=1)
+    edges = []
+    for a, b in itertools.combinations(range(len(nd)), 2):
+        if rad[a] > 0 and rad[b] > 0:
+            d = (c[a].astype(np.int64) - c[b]) % n
+            d = np.where(2 * d > n, d - n, d)
+            if float(np.sum(d * d)) <= (rad[a] + rad[b]) ** 2 + 1e-6:
+                edges.append((a, b))
+    comps = _components(len(nd), edges)
+    groups = {}
+    for i, l in enumerate(lab):
+        groups.setdefault(int(l), set()).add(i)
+    assert sorted(map(sorted, groups.values())) == sorted(map(sorted, comps))
+    assert any(len(g) > 1 for g in comps)
+    assert abs(mn.sum() / nd.sum() - 1) < 1e-14
+    member_cells = {tuple(v) for v in c.tolist()}
+    assert all(tuple(v) in member_cells for v in mc.tolist())
+
+
 def test_merge_two_sources_in_one_bubble():
     n = 48
     zz, yy, xx = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
