@@ -407,7 +407,7 @@ int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out)
     if (m > 0 && (h->cfg.merge_mode == RT_MERGE_FORCED ||
                   (h->cfg.merge_mode == RT_MERGE_AUTO && xbar > h->cfg.automerge_xbar))) {
         const int Ls = h->cfg.merge_samp_level;
-        h->launches += launch_merge(h->sw, m, h->cfg.n, h->d_x, h->dirs + healpix_level_offset(Ls),
+        h->launches += launch_merge(h->sw, m, h->cfg.n, h->cfg.periodic, h->d_x, h->dirs + healpix_level_offset(Ls),
                                     (int)(12 * (int64_t(1) << (2 * Ls))), h->cfg.merge_x_th, h->cfg.merge_f_req,
                                     h->cfg.merge_n_min, h->cfg.merge_dr_cells, h->cfg.merge_rmax_cells,
                                     h->cfg.merge_f_ov, h->cfg.merge_eps, h->d_st, s);

@@ -187,9 +187,9 @@ int launch_validate_sources(const int32_t* cells, const double* ndot, int64_t ns
 // Dedup + lexicographic sort; writes cells_a/ndot_a and count[0] = number of unique cells.
 int launch_dedup_sort(SourceWork& w, int64_t nsrc, cudaStream_t s);
 // Alg. 3 on cells_a/ndot_a[0..m): radii, union-find, merged catalog into cells_a/ndot_a, count[0] = size.
-int launch_merge(SourceWork& w, int64_t m, int n, const double* x, const int4* samp_dirs, int samp_count,
-                  double x_th, double f_req, int n_min, double dr, double rmax, double f_ov, double eps,
-                  DevStats* st, cudaStream_t s);
+int launch_merge(SourceWork& w, int64_t m, int n, int periodic, const double* x, const int4* samp_dirs,
+                 int samp_count, double x_th, double f_req, int n_min, double dr, double rmax, double f_ov,
+                 double eps, DevStats* st, cudaStream_t s);
 // Emitted catalog entries from cells_a/ndot_a[0..*count) with *count read on the device (<= max_m).
 int launch_build_emit_dev(const SourceWork& w, int64_t max_m, double s_over_dx2, SrcEntry* out, DevStats* st,
                           cudaStream_t s);

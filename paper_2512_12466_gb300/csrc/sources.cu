@@ -124,15 +124,25 @@ __global__ void dedup_sum_kernel(const uint64_t* __restrict__ keys, const int32_
 
 // ---------------------------------------------------------------- Alg. 3
 
+// Minimum-image component of a cell offset on a periodic grid of n cells
+// (Sec. 2.8 computes Alg. 3 under minimum-image geometry when periodic).
+__device__ __forceinline__ long long minimg(long long d, long long n)
+{
+    long long r = d % n;
+    if (r < 0) r += n;
+    return 2 * r > n ? r - n : r;
+}
+
 // MAX_RADIUS: one block per source. Shells r = dr, 2 dr, ... <= R_max are
 // sampled at the HEALPix directions of the sample level; a sample is the
-// cell floor(c + 1/2 + r d); the shell's point set is the distinct in-grid
-// sample cells (bitonic sort in shared memory, then run heads).
+// cell floor(c + 1/2 + r d), wrapped into the grid when periodic; the shell's
+// point set is the distinct in-grid sample cells (bitonic sort in shared
+// memory, then run heads).
 template <int NP2>
 __global__ void __launch_bounds__(kBlock) radius_kernel(const int32_t* __restrict__ cells, int64_t m, int n,
                                                         const double* __restrict__ x, const int4* __restrict__ dirs,
                                                         int ns, double x_th, double f_req, int n_min, double dr,
-                                                        double rmax, double* __restrict__ radius)
+                                                        double rmax, int periodic, double* __restrict__ radius)
 {
     __shared__ long long key[NP2];
     __shared__ int red[2];
@@ -157,6 +167,7 @@ __global__ void __launch_bounds__(kBlock) radius_kernel(const int32_t* __restric
                 for (int a = 0; a < 3; ++a) {
                     const double pos = __dadd_rn(__dadd_rn((double)c[a], 0.5), __dmul_rn(r, __dmul_rn((double)dd[a], inv)));
                     q[a] = (long long)floor(pos);
+                    if (periodic) q[a] = ((q[a] % nn) + nn) % nn;
                     if (q[a] < 0 || q[a] >= nn) inside = false;
                 }
                 if (inside) k = (q[2] * nn + q[1]) * nn + q[0];
@@ -214,10 +225,11 @@ __device__ __forceinline__ int uf_find(int* parent, int a)
 }
 
 // Pairs (a, b > a) whose bubbles overlap (both radii > 0,
-// d^2 <= (f_ov (r_a + r_b))^2 + eps) are united; the larger root is hooked
-// under the smaller, so each component's root is its smallest index.
+// d^2 <= (f_ov (r_a + r_b))^2 + eps, d minimum-image when periodic) are united;
+// the larger root is hooked under the smaller, so each component's root is
+// its smallest index.
 __global__ void pair_union_kernel(const int32_t* __restrict__ cells, const double* __restrict__ radius, int64_t m,
-                                  double f_ov, double eps, int* parent, DevStats* st)
+                                  int n, int periodic, double f_ov, double eps, int* parent, DevStats* st)
 {
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
         const double ra = radius[a];
@@ -226,7 +238,12 @@ __global__ void pair_union_kernel(const int32_t* __restrict__ cells, const doubl
         for (int64_t b = a + 1; b < m; ++b) {
             const double rb = radius[b];
             if (!(rb > 0.0)) continue;
-            const long long dx = ax - cells[3 * b], dy = ay - cells[3 * b + 1], dz = az - cells[3 * b + 2];
+            long long dx = ax - cells[3 * b], dy = ay - cells[3 * b + 1], dz = az - cells[3 * b + 2];
+            if (periodic) {
+                dx = minimg(dx, n);
+                dy = minimg(dy, n);
+                dz = minimg(dz, n);
+            }
             const long long d2 = dx * dx + dy * dy + dz * dz;
             const double rs = __dmul_rn(f_ov, __dadd_rn(ra, rb));
             if ((double)d2 <= __dadd_rn(__dmul_rn(rs, rs), eps)) {
@@ -255,11 +272,13 @@ __global__ void label_keys_kernel(int* parent, int64_t m, int32_t* __restrict__ 
 
 // One merged source per group (members contiguous in `order`, by index):
 // summed rate, flux-weighted centroid rounded and clamped into the grid,
-// snapped to the nearest member (first in order on ties).
+// snapped to the nearest member (first in order on ties). Periodic: members
+// unwrapped next to the group's first member, centroid wrapped back into the
+// grid, snap by minimum-image distance.
 __global__ void group_kernel(const int32_t* __restrict__ order, const int32_t* __restrict__ flag,
-                             const int32_t* __restrict__ pos, int64_t m, int n, const int32_t* __restrict__ cells,
-                             const double* __restrict__ ndot, int32_t* __restrict__ out_cells,
-                             double* __restrict__ out_ndot)
+                             const int32_t* __restrict__ pos, int64_t m, int n, int periodic,
+                             const int32_t* __restrict__ cells, const double* __restrict__ ndot,
+                             int32_t* __restrict__ out_cells, double* __restrict__ out_ndot)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
         if (!flag[p]) continue;
@@ -270,10 +289,13 @@ __global__ void group_kernel(const int32_t* __restrict__ order, const int32_t* _
         for (int64_t q = p; q < e; ++q) {
             const int32_t j = order[q];
             const double v = ndot[j];
+            long long u[3] = {cells[3 * j], cells[3 * j + 1], cells[3 * j + 2]};
+            if (periodic)
+                for (int a = 0; a < 3; ++a) u[a] = cells[3 * g + a] + minimg(u[a] - cells[3 * g + a], n);
             ftot = __dadd_rn(ftot, v);
-            sx = __dadd_rn(sx, __dmul_rn(v, (double)cells[3 * j]));
-            sy = __dadd_rn(sy, __dmul_rn(v, (double)cells[3 * j + 1]));
-            sz = __dadd_rn(sz, __dmul_rn(v, (double)cells[3 * j + 2]));
+            sx = __dadd_rn(sx, __dmul_rn(v, (double)u[0]));
+            sy = __dadd_rn(sy, __dmul_rn(v, (double)u[1]));
+            sz = __dadd_rn(sz, __dmul_rn(v, (double)u[2]));
         }
         const int32_t u = pos[p];
         if (e - p == 1) {
@@ -287,7 +309,8 @@ __global__ void group_kernel(const int32_t* __restrict__ order, const int32_t* _
         const double cs[3] = {sx, sy, sz};
         for (int a = 0; a < 3; ++a) {
             long long v = (long long)floor(__dadd_rn(__ddiv_rn(cs[a], ftot), 0.5));
-            v = v < 0 ? 0 : (v > n - 1 ? n - 1 : v);
+            if (periodic) v = ((v % n) + n) % n;
+            else v = v < 0 ? 0 : (v > n - 1 ? n - 1 : v);
             rc[a] = v;
         }
         int32_t best = -1;
@@ -296,7 +319,8 @@ __global__ void group_kernel(const int32_t* __restrict__ order, const int32_t* _
             const int32_t j = order[q];
             long long d2 = 0;
             for (int a = 0; a < 3; ++a) {
-                const long long d = (long long)cells[3 * j + a] - rc[a];
+                long long d = (long long)cells[3 * j + a] - rc[a];
+                if (periodic) d = minimg(d, n);
                 d2 += d * d;
             }
             if (best < 0 || d2 < bestd) { best = j; bestd = d2; }
@@ -404,26 +428,27 @@ int launch_dedup_sort(SourceWork& w, int64_t nsrc, cudaStream_t s)
     return 5;
 }
 
-int launch_merge(SourceWork& w, int64_t m, int n, const double* x, const int4* samp_dirs, int samp_count,
-                  double x_th, double f_req, int n_min, double dr, double rmax, double f_ov, double eps,
-                  DevStats* st, cudaStream_t s)
+int launch_merge(SourceWork& w, int64_t m, int n, int periodic, const double* x, const int4* samp_dirs,
+                 int samp_count, double x_th, double f_req, int n_min, double dr, double rmax, double f_ov,
+                 double eps, DevStats* st, cudaStream_t s)
 {
     if (m <= 0) return 0;
     const int b = blocks_for(m);
     const int grid_r = (int)m;
     if (samp_count <= 1024)
         radius_kernel<1024><<<grid_r, kBlock, 0, s>>>(w.cells_a, m, n, x, samp_dirs, samp_count, x_th, f_req, n_min,
-                                                      dr, rmax, w.radius);
+                                                      dr, rmax, periodic, w.radius);
     else
         radius_kernel<4096><<<grid_r, kBlock, 0, s>>>(w.cells_a, m, n, x, samp_dirs, samp_count, x_th, f_req, n_min,
-                                                      dr, rmax, w.radius);
+                                                      dr, rmax, periodic, w.radius);
     iota_kernel<<<b, kBlock, 0, s>>>(w.parent, m);
-    pair_union_kernel<<<b, kBlock, 0, s>>>(w.cells_a, w.radius, m, f_ov, eps, w.parent, st);
+    pair_union_kernel<<<b, kBlock, 0, s>>>(w.cells_a, w.radius, m, n, periodic, f_ov, eps, w.parent, st);
     label_keys_kernel<<<b, kBlock, 0, s>>>(w.parent, m, w.label, w.keys);
     rank_kernel<<<b, kBlock, 0, s>>>(w.keys, m, w.order);
     run_heads_kernel<<<b, kBlock, 0, s>>>(w.keys, w.order, m, 0xffffffff00000000ULL, w.flag);
     scan_kernel<<<1, 1024, 0, s>>>(w.flag, m, w.head_pos, w.count);
-    group_kernel<<<b, kBlock, 0, s>>>(w.order, w.flag, w.head_pos, m, n, w.cells_a, w.ndot_a, w.cells_b, w.ndot_b);
+    group_kernel<<<b, kBlock, 0, s>>>(w.order, w.flag, w.head_pos, m, n, periodic, w.cells_a, w.ndot_a, w.cells_b,
+                                      w.ndot_b);
     // final lexicographic order of the merged catalog (its size is count[0] <= m; unused tail keys sort last)
     cell_keys_kernel<<<b, kBlock, 0, s>>>(w.cells_b, m, w.keys);
     mask_tail_kernel<<<b, kBlock, 0, s>>>(w.keys, m, w.count);

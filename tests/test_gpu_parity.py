@@ -266,21 +266,28 @@ def test_edge_duplicate_sources(nyx):
     assert relerr(got["gamma"], ref["gamma"]) < 1e-12
 
 
-def bubble_workload(n=48, seed=7):
+def bubble_workload(n=48, seed=7, periodic=False):
     """Neutral gas with ionized balls; most sources sit inside the balls so
-    Alg. 3 finds bubbles and merges, the rest are scattered."""
+    Alg. 3 finds bubbles and merges, the rest are scattered. Periodic: the
+    balls sit on the faces and corners and wrap around the box."""
     rng = np.random.default_rng(seed)
     n_h = I.lognormal(n, 2e-4, 1.0, seed + 1)
     x = np.zeros((n, n, n))
     zz, yy, xx = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
     balls = [((12, 12, 12), 7.5), ((30, 30, 20), 9.5), ((40, 10, 35), 5.5)]
+    if periodic:
+        balls = [((1, 24, 24), 7.5), ((46, 46, 2), 9.5), ((24, 0, 40), 5.5)]
     cells = []
     for (cx, cy, cz), r in balls:
-        x[(xx - cx) ** 2 + (yy - cy) ** 2 + (zz - cz) ** 2 <= r * r] = 1.0
+        d = [v - c for v, c in ((xx, cx), (yy, cy), (zz, cz))]
+        if periodic:
+            d = [np.where(2 * (v % n) > n, v % n - n, v % n) for v in d]
+        x[d[0] ** 2 + d[1] ** 2 + d[2] ** 2 <= r * r] = 1.0
         for _ in range(15):
             d = rng.normal(size=3)
             d *= rng.uniform(0, r - 1.5) / np.linalg.norm(d)
-            cells.append([int(round(cx + d[0])), int(round(cy + d[1])), int(round(cz + d[2]))])
+            c = [int(round(cx + d[0])), int(round(cy + d[1])), int(round(cz + d[2]))]
+            cells.append([v % n for v in c] if periodic else c)
     cells += rng.integers(0, n, size=(20, 3)).tolist()
     cells = np.array(cells, np.int32)
     ndot = I.power_law_ndot(len(cells), seed + 2)
@@ -298,6 +305,23 @@ def test_merge_parity(nyx, prec):
     ref64 = ref if prec == 0 else oracle.run_workload(w, merge_mode=1, precision=0,
                                                       n_th_cm3=0.01 * float(w.n_h.mean()))
     assert relerr(got["gamma"], ref64["gamma"]) < tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_merge_parity_periodic(nyx, prec):
+    """Alg. 3 under minimum-image geometry with bubbles across the faces, then the
+    periodic march, against the oracle."""
+    w = bubble_workload(periodic=True)
+    ref, got = run_both(nyx, w, merge_mode=1, precision=prec, periodic=1)
+    assert got["stats"]["merged"] == 1
+    assert got["stats"]["n_src_emit"] == ref["stats"]["n_src_emit"] < ref["stats"]["n_src_dedup"] - 10
+    assert_bookkeeping(got["stats"], ref["stats"])
+    ref64 = ref if prec == 0 else oracle.run_workload(w, merge_mode=1, precision=0, periodic=1,
+                                                      n_th_cm3=0.01 * float(w.n_h.mean()))
+    assert relerr(got["gamma"], ref64["gamma"]) < (1e-12 if prec == 0 else 1e-5)
+    # the same catalog without periodicity merges differently
+    flat = oracle.run_workload(w, merge_mode=1, precision=0, n_th_cm3=0.01 * float(w.n_h.mean()))
+    assert flat["stats"]["n_src_emit"] != ref["stats"]["n_src_emit"]
 
 
 def test_automerge_threshold(nyx):
