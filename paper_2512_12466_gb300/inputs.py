@@ -125,6 +125,22 @@ def stromgren_test_a(n: int = 64) -> Workload:
     )
 
 
+# Table 1 Stromgren test problems: (n_H cm^-3, Ndot s^-1, clumping C, L_box Mpc), all at T = 1e4 K.
+TABLE1 = {"A": (1e-3, 5e48, 1.0, 0.0066), "B": (1.87e-4, 1e54, 5.0, 1.62), "C": (1.87e-4, 1e57, 1.0, 10.0)}
+
+
+def stromgren_test(name: str, n: int = 64) -> Workload:
+    """Table 1 Test A, B or C on an n^3 grid: uniform neutral hydrogen, one
+    source in cell (n/2, n/2, n/2) (centre of the box, to half a cell)."""
+    n_hv, ndot, clump, lbox = TABLE1[name]
+    c = n // 2
+    return Workload(
+        name=f"stromgren_{name}_{n}", n=n, box_cm=lbox * MPC_CM, n_h=np.full((n, n, n), n_hv),
+        x_ion=np.zeros((n, n, n)), cells=np.array([[c, c, c]], dtype=np.int32), ndot=np.array([ndot]),
+        params=dict(n_min_ray=4.0, tau_max=30.0, chem_iterate=1, alpha_B=ALPHA_B_1E4, clumping=clump, C_H=0.0),
+    )
+
+
 def cosmo_box(n: int, box_mpc_h: float, sigma_ln: float, n_sources: int, config: int,
               x_mode: str = "neutral", solve: int = 0, mean_nh: float = 2e-4,
               x_sigma_ln: float = 1.5, thin_xhi: float = 1e-4) -> Workload:

@@ -306,6 +306,44 @@ def test_stromgren_front_test_a():
     assert ionized > 0.99 * a["Ndot_s"] * t
 
 
+def _front_evolution(w, steps_myr, alpha, clump, **kw):
+    """Coupled Gamma <-> x over several steps (each iterated to convergence or
+    the cap); equal-volume front radius in cells after each step."""
+    x = w.x_ion.copy()
+    out, t = [], 0.0
+    for dt in steps_myr:
+        r = oracle.run(w.n_h, x, w.cells, w.ndot, w.box_cm, chem_iterate=1, dt_s=dt * I.MYR_S, alpha_B=alpha,
+                       clumping=clump, n_min_ray=4.0, tau_max=30.0, **kw)
+        x = r["x"]
+        t += dt
+        out.append((t, (3 * x.sum() / (4 * math.pi)) ** (1 / 3), r["stats"]))
+    return out
+
+
+@pytest.mark.parametrize("test,n,steps,tol", [
+    ("A", 64, [1.0, 9.0, 20.0], 0.05),          # to 30 Myr (the front reaches the half-box at 31.8 Myr)
+    ("B", 48, [10.0, 40.0, 150.0], 0.05),       # clumping 5: past t_rec = 131 Myr, towards r_s = 0.563 Mpc
+    ("C", 48, [10.0, 50.0], 0.05),              # r_s = 9.66 Mpc lies beyond the box; front at 60 Myr
+])
+def test_stromgren_front_growth(test, n, steps, tol):
+    """Table 1 Tests A-C over several coupled steps: the equal-volume I-front
+    radius follows r_I(t) = r_s (1 - exp(-t / t_rec))^(1/3) within 5% (P3, f2),
+    with r_s and t_rec from the Table 1 parameters."""
+    g = json.load(open(os.path.join(GOLDEN, "table1_stromgren.json")))
+    a = g["tests"][test]
+    alpha = g["alpha_B_cm3_s"]
+    w = I.stromgren_test(test, n)
+    assert w.n_h.flat[0] == a["n_H_cm3"] and w.ndot[0] == a["Ndot_s"] and w.params["clumping"] == a["C"]
+    rs = (3 * a["Ndot_s"] / (4 * math.pi * alpha * a["C"] * a["n_H_cm3"] ** 2)) ** (1 / 3)
+    trec = 1 / (a["C"] * alpha * a["n_H_cm3"])
+    dx = w.box_cm / n
+    for t, r_n, st in _front_evolution(w, steps, alpha, a["C"]):
+        r_i = rs * (1 - math.exp(-t * I.MYR_S / trec)) ** (1 / 3) / dx
+        assert r_i < n / 2                                  # the analytic front is still inside the box
+        assert abs(r_n / r_i - 1) < tol, (test, t, r_n, r_i)
+        assert st["chem_iters"] >= 1
+
+
 # ------------------------------------------------------------------ invariants
 
 @pytest.mark.parametrize("prec", [0, 1])
