@@ -6,6 +6,8 @@ relative L2 for the FP64 march and within 1e-5 of the FP64 oracle for the
 FP32 march (whose bookkeeping is compared bit-exactly with the oracle's FP32
 variant); the photon ledger closes to 1e-12 (FP64) / 1e-6 (FP32).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -341,6 +343,38 @@ def test_stromgren_chemistry_parity(nyx):
     assert relerr(got["gamma"], ref["gamma"]) < 1e-9
     r_n = (3 * got["x"].sum() / (4 * np.pi)) ** (1 / 3)
     assert abs(r_n - 4.889) < 1.0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("test,n,steps", [("A", 64, [1.0, 9.0, 20.0]), ("B", 48, [10.0, 40.0, 150.0]),
+                                          ("C", 48, [10.0, 50.0])])
+def test_stromgren_evolution_parity(nyx, test, n, steps, prec):
+    """Table 1 Tests A-C evolved through repeated rt_step calls (the handle
+    keeps x(t + dt) between steps) against the same evolution by the oracle:
+    front radii within 0.5% at every step, and within 5% of r_I(t)."""
+    w = I.stromgren_test(test, n)
+    p = w.params
+    s = nyx.Solver(n, w.box_cm, precision=prec, chem_iterate=1, alpha_B=p["alpha_B"], clumping=p["clumping"],
+                   n_min_ray=4.0, tau_max=30.0)
+    s.set_fields(w.n_h.ravel(), w.x_ion.ravel())
+    s.add_sources(w.cells.ravel(), w.ndot)
+    x_ref = w.x_ion.copy()
+    n_hv, ndot, clump, _ = I.TABLE1[test]
+    rs = (3 * ndot / (4 * math.pi * p["alpha_B"] * clump * n_hv ** 2)) ** (1 / 3)
+    trec = 1 / (clump * p["alpha_B"] * n_hv)
+    t = 0.0
+    for dt in steps:
+        s.step(dt * I.MYR_S)
+        x = s.get_x()
+        r = oracle.run(w.n_h, x_ref, w.cells, w.ndot, w.box_cm, chem_iterate=1, dt_s=dt * I.MYR_S,
+                       alpha_B=p["alpha_B"], clumping=clump, n_min_ray=4.0, tau_max=30.0, precision=prec)
+        x_ref = r["x"]
+        t += dt
+        front = lambda a: (3 * a.sum() / (4 * math.pi)) ** (1 / 3)
+        assert abs(front(x) / front(x_ref) - 1) < 5e-3, (test, t)
+        r_i = rs * (1 - math.exp(-t * I.MYR_S / trec)) ** (1 / 3) / (w.box_cm / n)
+        assert abs(front(x) / r_i - 1) < 0.05, (test, t)
+    s.close()
 
 
 def test_invalid_inputs_rejected(nyx):
