@@ -189,6 +189,8 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
                     f = (REAL)0.5 + De / Lpix;
                     f = f * f;
                 } else {
+                    /* naive threshold: the primary share applies whatever the neighbour */
+                    if (C->overlap_mode == ORC_OVERLAP_NAIVE) f = (REAL)0.5 + De / Lpix;
                     int64_t j[3] = {i[0], i[1], i[2]};
                     j[face >> 1] += (face & 1) ? 1 : -1;
                     if (C->periodic) j[face >> 1] = ((j[face >> 1] % n) + n) % n;
@@ -196,8 +198,9 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
                         const int64_t c2 = (j[2] * n + j[1]) * n + j[0];
                         const REAL kn_raw = C->KAPPA_FIELD[c2];
                         const REAL kn = R_FABS(kn_raw);
-                        const int elig = (C->overlap_mode == ORC_OVERLAP_CONSERVATIVE)
-                                             ? (!R_SIGNBIT(kn_raw) && kn > 0)   /* Eq. 7-8: n'_H >= n_th */
+                        const int elig = (C->overlap_mode == ORC_OVERLAP_CONSERVATIVE ||
+                                          C->overlap_mode == ORC_OVERLAP_NAIVE)
+                                             ? (!R_SIGNBIT(kn_raw) && kn > 0)   /* n'_H >= n_th (Eq. 7-8) */
                                              : (kn > 0);                          /* Eq. 5-6 */
                         if (elig) {
                             f = (REAL)0.5 + De / Lpix;

@@ -59,8 +59,12 @@
 #define ORC_STACK 128
 #define ORC_SQRT_PI_3 1.0233267079464885   /* sqrt(pi/3): pixel width = r sqrt(Omega(l)) */
 
+/* Beam-overlap treatments of Sec. 2.6: none; Eq. 5 alone; Eqs. 5-6; Eqs. 7-8
+ * (conservative threshold); the squared f_c; and the naive threshold, which
+ * keeps Eq. 5 but drops the Eq. 6 deposit when n'_H < n_th (the first
+ * remedy the paper tried, which loses photons). */
 enum { ORC_OVERLAP_NONE = 0, ORC_OVERLAP_LINEAR = 1, ORC_OVERLAP_ARC = 2,
-       ORC_OVERLAP_CONSERVATIVE = 3, ORC_OVERLAP_SQUARED = 4 };
+       ORC_OVERLAP_CONSERVATIVE = 3, ORC_OVERLAP_SQUARED = 4, ORC_OVERLAP_NAIVE = 5 };
 
 typedef struct {
     int32_t n;
@@ -621,7 +625,8 @@ int orc_run(const orc_config* cfg, const double* n_h, const double* x_in, const 
             int64_t rec_cap, int64_t* rec_n, int32_t* emit_cells, double* emit_ndot)
 {
     if (cfg->n <= 0 || cfg->n > 1024 || !(cfg->n_min_ray >= 1.0) || !(cfg->box_cm > 0) ||
-        !(cfg->sigma_cm2 > 0) || !(cfg->tau_max > 0))
+        !(cfg->sigma_cm2 > 0) || !(cfg->tau_max > 0) || cfg->overlap_mode < ORC_OVERLAP_NONE ||
+        cfg->overlap_mode > ORC_OVERLAP_NAIVE || (cfg->periodic != 0 && cfg->periodic != 1))
         return -1;
     const int64_t n = cfg->n;
     const int64_t ncell = n * n * n;

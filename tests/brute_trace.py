@@ -187,13 +187,15 @@ def trace(n_h, x, cells, ndot, box_cm, sigma=6.3e-18, n_min=4.0, tau_max=30.0, l
                         if overlap_mode == 1:
                             f = 0.5 + de / lpix
                         else:
+                            if overlap_mode == 5:                # naive threshold: Eq. 5 share regardless
+                                f = 0.5 + de / lpix
                             nbc = list(cell)
                             nbc[q // 2] += 1 if q % 2 else -1
                             if periodic:
                                 nbc = [v % n for v in nbc]
                             if all(0 <= v < n for v in nbc):
                                 kn = kap[nbc[2], nbc[1], nbc[0]]
-                                ok = elig[nbc[2], nbc[1], nbc[0]] if overlap_mode == 3 else kn > 0
+                                ok = elig[nbc[2], nbc[1], nbc[0]] if overlap_mode in (3, 5) else kn > 0
                                 if ok:
                                     f = 0.5 + de / lpix
                                     nb = (nbc, ((1.0 - f) * gseg) * (k / kn))

@@ -108,7 +108,7 @@ def test_default_level_max_never_binds():
 
 @pytest.mark.parametrize("seed,mode,n_th_frac,xmode", [
     (5, 0, 0.01, "mixed"), (6, 3, 0.01, "mixed"), (7, 3, 0.8, "mixed"), (8, 2, 0.8, "mixed"),
-    (9, 1, 0.01, "thin"), (10, 3, 0.5, "patchy"), (11, 4, 0.01, "thin")])
+    (9, 1, 0.01, "thin"), (10, 3, 0.5, "patchy"), (11, 4, 0.01, "thin"), (12, 5, 0.5, "mixed")])
 def test_oracle_matches_brute_force(seed, mode, n_th_frac, xmode):
     n = 6 if seed % 2 else 8
     w = I.random_small(n, 3, seed=seed, x_mode=xmode, box_cm=n * 3e21)
@@ -342,6 +342,40 @@ def test_stromgren_front_growth(test, n, steps, tol):
         assert r_i < n / 2                                  # the analytic front is still inside the box
         assert abs(r_n / r_i - 1) < tol, (test, t, r_n, r_i)
         assert st["chem_iters"] >= 1
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_naive_threshold_identities(prec):
+    """The naive threshold (mode 5) keeps the Eq. 5 share and drops the Eq. 6
+    deposit into neighbours with n'_H < n_th. On a periodic grid (every
+    neighbour in the grid) with n_HI > 0 everywhere: with n_th = 0 every
+    neighbour is eligible and modes 2, 3 and 5 give the same Gamma bit for bit;
+    with n_th above every n_H none is, and mode 5 equals Eq. 5 alone (mode 1)
+    while the conservative threshold equals no correction (mode 0)."""
+    w = I.random_small(14, 3, seed=51, x_mode="thin", box_cm=14 * 7e20)
+    assert (w.x_ion < 1).all()
+    run = lambda mode, nth: oracle.run_workload(w, overlap_mode=mode, n_th_cm3=nth, periodic=1, precision=prec)
+    g = {m: run(m, 0.0)["gamma"] for m in (2, 3, 5)}
+    assert np.array_equal(g[2], g[3]) and np.array_equal(g[3], g[5])
+    big = 10 * float(w.n_h.max())
+    r5, r1, r3, r0 = run(5, big), run(1, big), run(3, big), run(0, big)
+    assert np.array_equal(r5["gamma"], r1["gamma"]) and np.array_equal(r3["gamma"], r0["gamma"])
+    assert sum(r5["stats"]["secondary"]) == 0 and not np.array_equal(r5["gamma"], r3["gamma"])
+
+
+def test_naive_threshold_loses_photons():
+    """With some neighbours below n_th, the naive threshold deposits fewer photons
+    than are absorbed (the loss the paper reports), while the conservative
+    threshold (Eqs. 7-8) deposits all of them."""
+    w = I.random_small(24, 6, seed=52, x_mode="patchy", box_cm=24 * 2e21)
+    nth = 0.8 * float(w.n_h.mean())
+    s5 = oracle.run_workload(w, overlap_mode=5, n_th_cm3=nth)["stats"]
+    s3 = oracle.run_workload(w, overlap_mode=3, n_th_cm3=nth)["stats"]
+    assert s5["deposited_ph"] < s5["absorbed_ph"] * (1 - 1e-4)
+    assert abs(s3["deposited_ph"] / s3["absorbed_ph"] - 1) < 1e-12
+    for st in (s5, s3):
+        e = st["emitted_ph"]
+        assert abs(st["absorbed_ph"] + st["escaped_ph"] + st["dropped_ph"] - e) / e < 1e-12
 
 
 # ------------------------------------------------------------------ invariants
