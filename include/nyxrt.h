@@ -53,7 +53,9 @@ enum {
     RT_OVERLAP_LINEAR = 1,        /* Eq. 5 only (f_c < 1 near faces; photons lost) */
     RT_OVERLAP_ARC = 2,           /* Eqs. 5-6: secondary deposit into the nearest neighbour */
     RT_OVERLAP_CONSERVATIVE = 3,  /* Eqs. 7-8: secondary only if n'_H >= n_th (default) */
-    RT_OVERLAP_SQUARED = 4        /* f_c = (1/2 + D_edge/L_pix)^2 (Sec. 2.6.1 alternative) */
+    RT_OVERLAP_SQUARED = 4,       /* f_c = (1/2 + D_edge/L_pix)^2 (Sec. 2.6.1 alternative) */
+    RT_OVERLAP_NAIVE = 5          /* Eq. 5 always, Eq. 6 deposit only if n'_H >= n_th: the naive
+                                     threshold of Sec. 2.6 (loses photons; for comparison) */
 };
 enum { RT_MERGE_OFF = 0, RT_MERGE_FORCED = 1, RT_MERGE_AUTO = 2 };
 
@@ -250,7 +252,10 @@ int rt_batch_get_params(const rt_batch* b, rt_batch_params* p);
 int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best, double* best_ms);
 
 /* Capture one run (kappa rebuild, trace, finalize, statistics copy) into a
- * CUDA graph; rt_batch_run then replays it. */
+ * CUDA graph; rt_batch_run then replays it. Solves are grouped into launches
+ * by their work in the previous run (a solve that traced 2^26 segments or
+ * more gets a launch of its own), so capturing after one run captures that
+ * grouping; before any run, grouping follows field sizes only. */
 int rt_batch_capture(rt_batch* b);
 
 /* Run the batch: write solve i's Gamma and heating into gamma_out[i] and

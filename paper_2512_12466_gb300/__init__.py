@@ -26,6 +26,7 @@ RT_EPENDING = -7
 RT_FP64, RT_FP32 = 0, 1
 RT_HOST, RT_DEVICE = 0, 1
 RT_OVERLAP_NONE, RT_OVERLAP_LINEAR, RT_OVERLAP_ARC, RT_OVERLAP_CONSERVATIVE, RT_OVERLAP_SQUARED = 0, 1, 2, 3, 4
+RT_OVERLAP_NAIVE = 5
 RT_MERGE_OFF, RT_MERGE_FORCED, RT_MERGE_AUTO = 0, 1, 2
 RT_FLAG_VISIT_HASH = 1
 RT_FLAG_NO_GEOMETRY_TABLE = 2

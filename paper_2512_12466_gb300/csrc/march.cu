@@ -322,10 +322,12 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             } else if (V.overlap_mode == RT_OVERLAP_SQUARED) {
                 f = I::add((R)0.5, I::qdiv(De, Lpix));
                 f = f * f;
-            } else if (c2 >= 0) {
+            } else {
+                // naive threshold: the Eq. 5 share applies whatever the neighbour
+                if (V.overlap_mode == RT_OVERLAP_NAIVE) f = I::add((R)0.5, I::qdiv(De, Lpix));
                 const R kn = I::mag(kn_raw);
-                const bool elig = (V.overlap_mode == RT_OVERLAP_CONSERVATIVE) ? (!I::neg(kn_raw) && kn > (R)0)
-                                                                               : (kn > (R)0);
+                const bool elig = c2 >= 0 && ((V.overlap_mode == RT_OVERLAP_ARC) ? (kn > (R)0)
+                                                                                  : (!I::neg(kn_raw) && kn > (R)0));
                 if (elig) {
                     f = I::add((R)0.5, I::qdiv(De, Lpix));
                     g2 = (((R)1 - f) * gseg) * I::qdiv(kap, kn);
@@ -861,7 +863,8 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
     const float taumax = V.tau_max;
     const unsigned long long rbase =
         (kHash && V.hash) ? mix64(((unsigned long long)(si - V.src_off) << 36) | ((unsigned long long)l << 31) | pix) : 0ULL;
-    const bool face = V.overlap_mode == RT_OVERLAP_ARC || V.overlap_mode == RT_OVERLAP_CONSERVATIVE;
+    const bool face = V.overlap_mode == RT_OVERLAP_ARC || V.overlap_mode == RT_OVERLAP_CONSERVATIVE ||
+                      V.overlap_mode == RT_OVERLAP_NAIVE;
     const bool corr = V.overlap_mode != RT_OVERLAP_NONE;
     const long long nn = (long long)n * n;
     const double B0 = widen(P) - widen(cP);
@@ -929,9 +932,11 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
                 f = fn;
             } else if (V.overlap_mode == RT_OVERLAP_SQUARED) {
                 f = fn * fn;
-            } else if (c2 >= 0) {
+            } else {
+                if (V.overlap_mode == RT_OVERLAP_NAIVE) f = fn;   // the Eq. 5 share whatever the neighbour
                 const float kn = I::mag(kn_raw);
-                const bool elig = (V.overlap_mode == RT_OVERLAP_CONSERVATIVE) ? (!I::neg(kn_raw) && kn > 0.f) : (kn > 0.f);
+                const bool elig =
+                    c2 >= 0 && ((V.overlap_mode == RT_OVERLAP_ARC) ? (kn > 0.f) : (!I::neg(kn_raw) && kn > 0.f));
                 if (elig) {
                     f = fn;
                     g2 = ((1.f - f) * gseg) * I::qdiv(kap, kn);

@@ -214,7 +214,7 @@ extern "C" int rt_step_noalloc(const rt_config* cfg, void* cuda_stream, const do
     if (cfg->merge_mode != RT_MERGE_OFF || cfg->chem_iterate)
         return set_error(RT_EINVAL, "rt_step_noalloc: source merging and chemistry are not available here");
     if ((cfg->precision != RT_FP64 && cfg->precision != RT_FP32) || !(cfg->box_cm > 0) || !(cfg->sigma_cm2 > 0) ||
-        !(cfg->n_min_ray >= 1.0) || !(cfg->tau_max > 0) || cfg->overlap_mode < 0 || cfg->overlap_mode > 4 ||
+        !(cfg->n_min_ray >= 1.0) || !(cfg->tau_max > 0) || cfg->overlap_mode < 0 || cfg->overlap_mode > 5 ||
         cfg->level_max > kMaxLevel)
         return set_error(RT_EINVAL, "rt_step_noalloc: invalid configuration");
     int dev = 0;

@@ -554,7 +554,7 @@ bool valid_config(const rt_config* c, std::string& why)
     if (!(c->sigma_cm2 > 0)) { why = "sigma_cm2 must be positive"; return false; }
     if (!(c->n_min_ray >= 1.0)) { why = "n_min_ray must be >= 1"; return false; }
     if (!(c->tau_max > 0)) { why = "tau_max must be positive"; return false; }
-    if (c->overlap_mode < 0 || c->overlap_mode > 4) { why = "overlap_mode must be 0..4"; return false; }
+    if (c->overlap_mode < 0 || c->overlap_mode > 5) { why = "overlap_mode must be 0..5"; return false; }
     if (c->merge_mode < 0 || c->merge_mode > 2) { why = "merge_mode must be 0..2"; return false; }
     if (c->merge_samp_level < 0 || c->merge_samp_level > 4) { why = "merge_samp_level must be 0..4"; return false; }
     if (!(c->merge_dr_cells > 0)) { why = "merge_dr_cells must be positive"; return false; }

@@ -99,6 +99,7 @@ CASES = [
     (24, 7, 106, "thin", 7e20, 4, 0.01),
     (33, 9, 107, "patchy", 2e22, 3, 0.3),   # odd size: ragged tail of every warp-sized chunk
     (40, 40, 108, "thin", 2e21, 3, 0.3),
+    (26, 7, 109, "mixed", 3e21, 5, 0.5),   # naive threshold
 ]
 
 
@@ -141,6 +142,7 @@ def test_parity_fp32(nyx, case, walk):
     (31, 9, 304, "patchy", 2e22, 4, 30.0, -1, 2.0),       # squared correction, N_min = 2
     (40, 12, 305, "thin", 2e21, 2, 30.0, -1, 8.0),        # Arc, N_min = 8
     (64, 16, 306, "mixed", 3e21, 3, 30.0, -1, 4.0),
+    (28, 8, 307, "patchy", 2e21, 5, 30.0, -1, 4.0),       # naive threshold
 ])
 def test_geometry_table_equals_walk(nyx, case):
     """The table-driven FP32 march and the walked one: the same bookkeeping bit
