@@ -41,6 +41,7 @@ class OrcConfig(C.Structure):
         ("merge_eps", C.c_double), ("merge_n_min", C.c_int32), ("chem_iterate", C.c_int32),
         ("dt_s", C.c_double), ("alpha_B", C.c_double), ("C_H", C.c_double), ("clumping", C.c_double),
         ("chem_tol", C.c_double), ("chem_max_iter", C.c_int32), ("periodic", C.c_int32),
+        ("spectrum", C.c_int32), ("nq", C.c_int32), ("q_s", C.c_void_p), ("q_w", C.c_void_p),
     ]
 
 
@@ -202,7 +203,26 @@ DEFAULTS = dict(precision=0, sigma_cm2=6.3e-18, n_min_ray=4.0, level_max=-1, ove
                 merge_samp_level=3, automerge_xbar=0.018, merge_x_th=0.9, merge_f_req=0.9,
                 merge_dr_cells=2.0, merge_rmax_cells=16.0, merge_f_ov=1.0, merge_eps=1e-6,
                 merge_n_min=8, chem_iterate=0, dt_s=0.0, alpha_B=2.59e-13, C_H=0.0, clumping=1.0,
-                chem_tol=1e-6, chem_max_iter=100, periodic=0)
+                chem_tol=1e-6, chem_max_iter=100, periodic=0, spectrum=0, t_bb_K=1e5)
+
+
+# Hydrogen ionization threshold h nu_0 (13.598 eV) and Boltzmann's constant, cgs.
+H_NU0_ERG = 13.598 * 1.602176634e-12
+K_B_ERG_K = 1.380649e-16
+
+
+def spectrum_nodes(t_bb_K: float, nq: int = 64):
+    """Frequency quadrature for Eq. 1 with a blackbody source at t_bb_K and
+    sigma_nu = sigma_0 (nu_0 / nu)^3 above the threshold: with y = nu / nu_0 and
+    theta = h nu_0 / (k T), the photon-number spectrum is y^2 / (exp(theta y) - 1);
+    substituting y = 1 + z / theta turns its integral over [1, inf) into one with
+    weight exp(-z), done by Gauss-Laguerre. Returns (sigma ratios y^-3, weights
+    normalised to sum 1)."""
+    theta = H_NU0_ERG / (K_B_ERG_K * t_bb_K)
+    z, om = np.polynomial.laguerre.laggauss(nq)
+    y = 1.0 + z / theta
+    wt = om * y ** 2 * np.exp(-theta) / (theta * (-np.expm1(-(theta + z))))
+    return np.ascontiguousarray(y ** -3.0), np.ascontiguousarray(wt / wt.sum())
 
 
 def make_config(n: int, box_cm: float, n_h=None, **kw) -> OrcConfig:
@@ -213,8 +233,17 @@ def make_config(n: int, box_cm: float, n_h=None, **kw) -> OrcConfig:
     cfg = OrcConfig()
     cfg.n = n
     cfg.box_cm = box_cm
+    t_bb = p.pop("t_bb_K")
+    nodes = kw.get("q_nodes")
     for k, v in p.items():
         setattr(cfg, k, v)
+    if cfg.spectrum == 1:
+        qs, qw = spectrum_nodes(t_bb) if nodes is None else (np.ascontiguousarray(nodes[0], dtype=np.float64),
+                                                            np.ascontiguousarray(nodes[1], dtype=np.float64))
+        cfg.nq = len(qs)
+        cfg.q_s = qs.ctypes.data
+        cfg.q_w = qw.ctypes.data
+        cfg._keep = (qs, qw)          # the arrays outlive the call through the config
     return cfg
 
 

@@ -19,6 +19,16 @@ typedef struct {
     REAL tau, ctau;    /* optical depth accumulated from the source, and its compensation */
 } SFX(ray);
 
+/* Photons a ray still carries (units of its budget): the compensated budget
+ * P - cP (gray: P is decremented by every absorption), or, with the
+ * frequency-integrated rate, P Phi(tau): P then stays the geometric budget and
+ * the attenuation lives in Phi. */
+static double SFX(remaining)(const orc_ctx* C, REAL P, REAL cP, REAL tau, REAL ctau)
+{
+    if (C->spectrum) return (double)P * orc_phi(C, (double)tau - (double)ctau);
+    return (double)P - (double)cP;
+}
+
 /* Compensated (Kahan) accumulation s += v, used in FP32 mode. */
 static void SFX(kahan_add)(REAL* s, REAL* c, REAL v)
 {
@@ -110,7 +120,7 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
     st->rays[l]++;
     if (i[0] < 0 || i[0] >= n || i[1] < 0 || i[1] >= n || i[2] < 0 || i[2] >= n) {
         st->escaped[l]++;
-        orc_sum_add(&C->escaped, ph * ((double)P - (double)cP));
+        orc_sum_add(&C->escaped, ph * SFX(remaining)(C, P, cP, tau, ctau));
         return 0;
     }
 
@@ -147,7 +157,16 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
         const REAL kap = R_FABS(kraw);
         const REAL dtau = kap * ds;                                  /* Eq. 2 over the segment */
         REAL a, gseg;
-        if (kap > 0) {
+        if (C->spectrum) {                                           /* Eq. 1 integrated over frequency */
+            const double t0 = (double)tau - (double)ctau;
+            if (kap > 0) {
+                a = (REAL)((double)P * orc_absorbed(C, t0, (double)dtau));
+                gseg = (a * G) / kap;
+            } else {
+                a = 0;
+                gseg = (REAL)((double)P * orc_thin_rate(C, t0)) * G * ds;
+            }
+        } else if (kap > 0) {
             a = P * (-R_EXPM1(-dtau));                               /* photons absorbed */
             gseg = (a * G) / kap;                                    /* Eq. 1, gray, V_box: a/(n_HI V) */
         } else {
@@ -218,7 +237,7 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
         }
 
         SFX(kahan_add)(&tau, &ctau, dtau);
-        SFX(kahan_add)(&P, &cP, -a);
+        if (!C->spectrum) SFX(kahan_add)(&P, &cP, -a);
         SFX(kahan_add)(&A, &cA, a);
 
         st->segments[l]++;
@@ -234,13 +253,13 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
 
         if (tau >= (REAL)C->tau_max) {                               /* photons spent (RAY_FLTR tau test) */
             st->dropped_tau[l]++;
-            orc_sum_add(&C->dropped, ph * ((double)P - (double)cP));
+            orc_sum_add(&C->dropped, ph * SFX(remaining)(C, P, cP, tau, ctau));
             orc_sum_add(&C->absorbed, ph * ((double)A - (double)cA));
             return 0;
         }
         if (is_end && !split_end) {                                  /* travelled sqrt(3) L_box (Sec. 2.5.1) */
             st->escaped[l]++;
-            orc_sum_add(&C->escaped, ph * ((double)P - (double)cP));
+            orc_sum_add(&C->escaped, ph * SFX(remaining)(C, P, cP, tau, ctau));
             orc_sum_add(&C->absorbed, ph * ((double)A - (double)cA));
             return 0;
         }
@@ -248,7 +267,7 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
             orc_sum_add(&C->absorbed, ph * ((double)A - (double)cA));
             if (l + 1 > C->level_max) {
                 st->dropped_level[l]++;
-                orc_sum_add(&C->dropped, ph * ((double)P - (double)cP));
+                orc_sum_add(&C->dropped, ph * SFX(remaining)(C, P, cP, tau, ctau));
                 return 0;
             }
             st->splits[l]++;
@@ -278,7 +297,7 @@ static int SFX(march)(orc_ctx* C, int64_t srcidx, const int32_t cell0[3], double
         kprev = kw;
         if (i[0] < 0 || i[0] >= n || i[1] < 0 || i[1] >= n || i[2] < 0 || i[2] >= n) {
             st->escaped[l]++;
-            orc_sum_add(&C->escaped, ph * ((double)P - (double)cP));
+            orc_sum_add(&C->escaped, ph * SFX(remaining)(C, P, cP, tau, ctau));
             orc_sum_add(&C->absorbed, ph * ((double)A - (double)cA));
             return 0;
         }

@@ -87,6 +87,10 @@ typedef struct {
     double dt_s, alpha_B, C_H, clumping, chem_tol;
     int32_t chem_max_iter;
     int32_t periodic;            /* 1: periodic boundaries (Sec. 2.5.1) */
+    int32_t spectrum;            /* 0: gray sigma; 1: frequency-integrated Eq. 1 (Sec. 2.5) */
+    int32_t nq;                  /* quadrature nodes over frequency (spectrum 1) */
+    const double* q_s;           /* sigma_nu / sigma_0 at each node */
+    const double* q_w;           /* normalised photon-number weight of each node (they sum to 1) */
 } orc_config;
 
 typedef struct {
@@ -122,6 +126,10 @@ typedef struct {
     int level_max;
     double tau_max;
     int overlap_mode;
+    int spectrum;                /* Eq. 1 over frequency: quadrature nodes below */
+    int nq;
+    const double* q_s;
+    const double* q_w;
     int periodic;                /* Sec. 2.5.1: rays wrap around the box ... */
     int64_t rs;                  /* ... and stop at travel distance sqrt(3) L_box (2^-F cells) */
     orc_stats* st;
@@ -253,6 +261,35 @@ int32_t orc_default_level_max(int32_t n, double n_min_ray)
 
 /* ------------------------------------------------------------------ */
 /* The march, in FP64 and FP32 physics.                               */
+
+/* Frequency-integrated photoionization (Eq. 1; Sec. 2.5, after C2-Ray): a
+ * ray's photons are spread over frequency with normalised weights w_k at
+ * cross-section ratios s_k = sigma_nu/sigma_0, so optical depth tau at the
+ * threshold is tau s_k at node k.  Fraction of the ray's photons that
+ * survive tau: Phi(tau) = sum_k w_k exp(-tau s_k).  Fraction absorbed over a
+ * segment of optical depth dtau after tau: sum_k w_k exp(-tau s_k) (1 - exp(-dtau s_k)),
+ * with expm1 so that thin segments keep their precision.  Optically thin
+ * rate per unit dtau: sum_k w_k s_k exp(-tau s_k). */
+static double orc_phi(const orc_ctx* C, double tau)
+{
+    double s = 0.0;
+    for (int k = 0; k < C->nq; k++) s += C->q_w[k] * exp(-tau * C->q_s[k]);
+    return s;
+}
+
+static double orc_absorbed(const orc_ctx* C, double tau, double dtau)
+{
+    double s = 0.0;
+    for (int k = 0; k < C->nq; k++) s += C->q_w[k] * exp(-tau * C->q_s[k]) * (-expm1(-dtau * C->q_s[k]));
+    return s;
+}
+
+static double orc_thin_rate(const orc_ctx* C, double tau)
+{
+    double s = 0.0;
+    for (int k = 0; k < C->nq; k++) s += C->q_w[k] * C->q_s[k] * exp(-tau * C->q_s[k]);
+    return s;
+}
 
 #define REAL double
 #define SFX(x) x##_d
@@ -597,6 +634,10 @@ static void orc_trace(const orc_config* cfg, int64_t rq, int level_max, const do
     C.tau_max = cfg->tau_max;
     C.overlap_mode = cfg->overlap_mode;
     C.periodic = cfg->periodic != 0;
+    C.spectrum = cfg->spectrum;
+    C.nq = cfg->nq;
+    C.q_s = cfg->q_s;
+    C.q_w = cfg->q_w;
     C.rs = C.periodic ? orc_periodic_rs((int32_t)n) : 0;
     C.st = st;
     C.rec_ray = rec_ray;
@@ -626,7 +667,8 @@ int orc_run(const orc_config* cfg, const double* n_h, const double* x_in, const 
 {
     if (cfg->n <= 0 || cfg->n > 1024 || !(cfg->n_min_ray >= 1.0) || !(cfg->box_cm > 0) ||
         !(cfg->sigma_cm2 > 0) || !(cfg->tau_max > 0) || cfg->overlap_mode < ORC_OVERLAP_NONE ||
-        cfg->overlap_mode > ORC_OVERLAP_NAIVE || (cfg->periodic != 0 && cfg->periodic != 1))
+        cfg->overlap_mode > ORC_OVERLAP_NAIVE || (cfg->periodic != 0 && cfg->periodic != 1) ||
+        (cfg->spectrum != 0 && cfg->spectrum != 1) || (cfg->spectrum == 1 && (cfg->nq < 1 || !cfg->q_s || !cfg->q_w)))
         return -1;
     const int64_t n = cfg->n;
     const int64_t ncell = n * n * n;

@@ -378,6 +378,74 @@ def test_naive_threshold_loses_photons():
         assert abs(st["absorbed_ph"] + st["escaped_ph"] + st["dropped_ph"] - e) / e < 1e-12
 
 
+# ------------------------------------------------------------------ frequency-integrated Eq. 1 (f3)
+
+def _bb_moment(t_bb, tau, power):
+    """Defining integral of the blackbody photon spectrum above threshold with
+    sigma_nu / sigma_0 = y^-3: int y^2 / (e^{theta y} - 1) y^{-3 power} e^{-tau y^-3} dy
+    over [1, inf), by adaptive quadrature (scipy), normalised by power 0 at tau 0."""
+    from scipy.integrate import quad
+    theta = oracle.H_NU0_ERG / (oracle.K_B_ERG_K * t_bb)
+    f = lambda y, p, t: (y ** 2 * math.exp(-theta * y) / -math.expm1(-theta * y)) * y ** (-3.0 * p) * math.exp(-t * y ** -3.0)
+    norm = quad(f, 1, np.inf, args=(0, 0.0), epsabs=0, epsrel=1e-13, limit=400)[0]
+    return quad(f, 1, np.inf, args=(power, tau), epsabs=0, epsrel=1e-13, limit=400)[0] / norm
+
+
+@pytest.mark.parametrize("t_bb", [3e4, 1e5])
+def test_spectrum_quadrature_matches_definition(t_bb):
+    """The oracle's frequency nodes reproduce the surviving fraction Phi(tau) and
+    the thin rate Psi(tau) (Eq. 1 integrated over a blackbody photon spectrum with
+    sigma ~ nu^-3) from the defining integrals, to 1e-9 of Phi(0) = 1."""
+    s, w = oracle.spectrum_nodes(t_bb)
+    assert abs(w.sum() - 1) < 1e-14 and (s <= 1).all() and (s > 0).all()
+    for tau in (0.0, 0.03, 0.5, 2.0, 8.0, 30.0):
+        phi = float((w * np.exp(-tau * s)).sum())
+        psi = float((w * s * np.exp(-tau * s)).sum())
+        assert abs(phi - _bb_moment(t_bb, tau, 0)) < 1e-9
+        assert abs(psi - _bb_moment(t_bb, tau, 1)) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_spectrum_one_node_at_threshold_is_gray(prec):
+    """A spectrum with all photons at the threshold (one node, sigma = sigma_0)
+    makes Eq. 1 the gray rate: the same Gamma to rounding, the same bookkeeping."""
+    w = I.random_small(16, 4, seed=62, x_mode="mixed", box_cm=16 * 3e21)
+    kw = dict(overlap_mode=3, n_th_cm3=0.3 * float(w.n_h.mean()), precision=prec)
+    g = oracle.run_workload(w, **kw)
+    f = oracle.run_workload(w, spectrum=1, q_nodes=(np.array([1.0]), np.array([1.0])), **kw)
+    for k in ("rays", "splits", "segments", "secondary", "escaped", "dropped_tau"):
+        assert g["stats"][k] == f["stats"][k]
+    assert relerr(f["gamma"], g["gamma"]) < (1e-13 if prec == 0 else 1e-5)
+    e = g["stats"]["emitted_ph"]
+    for k in ("absorbed_ph", "escaped_ph", "dropped_ph"):
+        assert abs(f["stats"][k] - g["stats"][k]) <= (1e-13 if prec == 0 else 1e-6) * e
+
+
+def test_spectrum_thin_path_sum():
+    """Thin medium with the blackbody spectrum: every photon's share of the rate
+    is weighted by its cross-section, so sum(Gamma) = Ndot sigma_0 <sigma/sigma_0> R_L / dx^2,
+    <sigma/sigma_0> = Psi(0) from the defining integral (direction quantisation: 2e-6)."""
+    n_h, x, cells, ndot, box, lm = _thin_uniform()
+    r = oracle.run(n_h, x, cells, ndot, box, level_max=lm, overlap_mode=0, spectrum=1, t_bb_K=1e5)
+    dx = box / n_h.shape[0]
+    r_l = oracle.split_rq(4.0) * 2.0 ** (lm - 24)
+    expect = ndot[0] * 6.3e-18 * _bb_moment(1e5, 0.0, 1) * r_l / dx ** 2
+    assert abs(r["gamma"].sum() / expect - 1) < 2e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_spectrum_photon_ledger(prec):
+    """emitted = absorbed + escaped + dropped, deposited = absorbed (conservative
+    correction), with the remaining photons of a ray B Phi(tau)."""
+    w = I.random_small(20, 5, seed=63, x_mode="patchy", box_cm=20 * 2e21)
+    st = oracle.run_workload(w, spectrum=1, precision=prec, overlap_mode=3)["stats"]
+    e = st["emitted_ph"]
+    tol = 1e-12 if prec == 0 else 1e-6
+    assert abs(st["absorbed_ph"] + st["escaped_ph"] + st["dropped_ph"] - e) / e < tol
+    assert abs(st["deposited_ph"] - st["absorbed_ph"]) / e < tol
+    assert st["dropped_ph"] > 0            # hard photons outlive tau_max at the threshold
+
+
 # ------------------------------------------------------------------ invariants
 
 @pytest.mark.parametrize("prec", [0, 1])
