@@ -95,7 +95,22 @@ typedef struct rt_config {
     int32_t periodic;          /* 1: periodic boundaries (Sec. 2.5.1): rays wrap around the box and
                                   stop once they have travelled sqrt(3) box lengths (without
                                   splitting; their remaining photons count as escaped) */
+    int32_t spectrum;          /* RT_SPECTRUM_*: gray sigma_cm2, or Eq. 1 integrated over a
+                                  blackbody spectrum (Sec. 2.5) */
+    double t_bb_K;             /* blackbody temperature for RT_SPECTRUM_BLACKBODY */
 } rt_config;
+
+enum {
+    RT_SPECTRUM_GRAY = 0,      /* one cross-section sigma_cm2 for all photons (default) */
+    RT_SPECTRUM_BLACKBODY = 1  /* Eq. 1 over frequency: blackbody photons above the threshold,
+                                  sigma_nu = sigma_cm2 (nu_0 / nu)^3. A ray keeps its geometric
+                                  budget and carries threshold optical depth tau; it absorbs
+                                  Phi(tau) - Phi(tau + dtau) of it per segment, Phi(tau) being the
+                                  fraction of its photons that survive tau (tabulated per
+                                  temperature, cubic interpolation in ln tau). tau_max <= 1e4.
+                                  rt_step only (not the batched, serving or allocation-free forms);
+                                  the FP32 march walks its rays (no geometry tables). */
+};
 
 #define RT_FLAG_VISIT_HASH 1   /* accumulate the visit-list hash in rt_stats (bookkeeping check) */
 #define RT_FLAG_NO_GEOMETRY_TABLE 2  /* FP32: walk every ray's cells instead of reading them from the
@@ -197,6 +212,12 @@ int rt_destroy(rt_handle* h);
  * within a budget of an eighth of the device's memory (environment variable
  * NYXRT_GEOMETRY_BUDGET_MB overrides it); levels over budget walk their rays. */
 int64_t rt_geometry_table_bytes(int32_t device);
+
+/* Phi(tau) and the thin rate Psi(tau) = -dPhi/dtau of RT_SPECTRUM_BLACKBODY at
+ * t_bb_K, from the library's own table and interpolation (what the march uses,
+ * evaluated on the host; for checking). Returns RT_EINVAL for tau outside
+ * [0, 1e4] or t_bb_K <= 0. */
+int rt_spectrum_eval(double t_bb_K, double tau, double* phi, double* psi);
 
 /* Text of the handle's last error ("" if none); for h == NULL, the last
  * error of a failed rt_create on this thread. */
@@ -357,8 +378,9 @@ const char* rt_server_last_error(const rt_server* s);
  * the library keeps until the process exits; it calls no allocator.
  *
  * Limits (violations return RT_EINVAL with a message): n <= 32, at most 4096
- * sources, merge_mode == RT_MERGE_OFF, chem_iterate == 0, and rays may not
- * need HEALPix levels above 7 (true for n <= 32 with n_min_ray <= 4).
+ * sources, merge_mode == RT_MERGE_OFF, chem_iterate == 0, spectrum ==
+ * RT_SPECTRUM_GRAY, and rays may not need HEALPix levels above 7 (true for
+ * n <= 32 with n_min_ray <= 4).
  *
  * Arguments: `cfg` as for rt_create; `cuda_stream` a cudaStream_t on the
  * current device; n_H and x_ion (n^3 float64), cell_ijk (nsrc x 3 int32) and

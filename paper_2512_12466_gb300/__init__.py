@@ -27,6 +27,7 @@ RT_FP64, RT_FP32 = 0, 1
 RT_HOST, RT_DEVICE = 0, 1
 RT_OVERLAP_NONE, RT_OVERLAP_LINEAR, RT_OVERLAP_ARC, RT_OVERLAP_CONSERVATIVE, RT_OVERLAP_SQUARED = 0, 1, 2, 3, 4
 RT_OVERLAP_NAIVE = 5
+RT_SPECTRUM_GRAY, RT_SPECTRUM_BLACKBODY = 0, 1
 RT_MERGE_OFF, RT_MERGE_FORCED, RT_MERGE_AUTO = 0, 1, 2
 RT_FLAG_VISIT_HASH = 1
 RT_FLAG_NO_GEOMETRY_TABLE = 2
@@ -45,7 +46,7 @@ class rt_config(C.Structure):
         ("merge_rmax_cells", C.c_double), ("merge_f_ov", C.c_double), ("merge_eps", C.c_double),
         ("merge_n_min", C.c_int32), ("chem_iterate", C.c_int32), ("alpha_B", C.c_double), ("C_H", C.c_double),
         ("clumping", C.c_double), ("chem_tol", C.c_double), ("chem_max_iter", C.c_int32), ("flags", C.c_int32),
-        ("periodic", C.c_int32),
+        ("periodic", C.c_int32), ("spectrum", C.c_int32), ("t_bb_K", C.c_double),
     ]
 
 
@@ -108,6 +109,8 @@ def lib():
         L.rt_add_sources.argtypes = [P, P, P, i64, C.c_int]
         L.rt_clear_sources.argtypes = [P]
         L.rt_reconfigure.argtypes = [P, C.POINTER(rt_config)]
+        L.rt_spectrum_eval.argtypes = [d, d, C.POINTER(d), C.POINTER(d)]
+        L.rt_spectrum_eval.restype = C.c_int
         L.rt_geometry_table_bytes.argtypes = [i32]
         L.rt_geometry_table_bytes.restype = i64
         L.rt_step.argtypes = [P, d, P, P, C.c_int, C.POINTER(rt_stats)]
@@ -145,7 +148,7 @@ def lib():
 
 def exported_symbols():
     return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_reconfigure",
-            "rt_geometry_table_bytes", "rt_step",
+            "rt_geometry_table_bytes", "rt_spectrum_eval", "rt_step",
             "rt_get_x", "rt_destroy", "rt_last_error", "rt_version", "rt_batch_create", "rt_batch_set_params",
             "rt_batch_get_params", "rt_batch_tune", "rt_batch_capture", "rt_batch_run", "rt_batch_destroy",
             "rt_batch_last_error", "rt_server_config_default", "rt_server_create", "rt_server_submit",
@@ -195,6 +198,15 @@ def rt_add_sources(h: int, cells, ndot, n: int, where: int) -> None:
 
 def rt_clear_sources(h: int) -> None:
     _check(lib().rt_clear_sources(h), h)
+
+
+def rt_spectrum_eval(t_bb_K: float, tau: float):
+    """(Phi(tau), Psi(tau)) of the blackbody spectrum table at t_bb_K (host evaluation)."""
+    phi, psi = C.c_double(), C.c_double()
+    rc = lib().rt_spectrum_eval(float(t_bb_K), float(tau), C.byref(phi), C.byref(psi))
+    if rc != RT_OK:
+        raise NyxError(rc, "rt_spectrum_eval: tau in [0, 1e4], t_bb_K > 0")
+    return phi.value, psi.value
 
 
 def rt_geometry_table_bytes(device: int = 0) -> int:

@@ -355,6 +355,8 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
         if (h->cfg.precision != b->precision) return bfail(b, RT_EINVAL, "all handles of a batch must share the precision");
         if (!h->fields_set) return bfail(b, RT_ESTATE, "rt_set_fields has not been called on a handle");
         if (h->cfg.chem_iterate) return bfail(b, RT_EINVAL, "the batched form traces at fixed x (chem_iterate must be 0)");
+        if (h->cfg.spectrum != RT_SPECTRUM_GRAY)
+            return bfail(b, RT_EINVAL, "the batched form integrates the gray rate (spectrum must be RT_SPECTRUM_GRAY)");
         if (h->sticky) return bfail(b, RT_ESTATE, "a handle is in an error state");
     }
     DeviceGuard g(b->device);

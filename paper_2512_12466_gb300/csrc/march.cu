@@ -162,6 +162,7 @@ struct SolveView {
     R tau_max;
     uint32_t src_off;        // first catalog index of this solve (ray ids are solve-local)
     long long rs;            // periodic boundaries: travel-distance cutoff sqrt(3) n (2^-24 cells); 0: none
+    SpecTable<R> spec;       // RT_SPECTRUM_BLACKBODY (march_ray<..., true> only)
 };
 
 // Periodic boundaries (Sec. 2.5.1): a coordinate moved by one cell wraps around the box.
@@ -182,12 +183,25 @@ __device__ __forceinline__ int wrapn(const int v, const int n)
 // start sphere to its split sphere, depositing into V.gamma and counting into
 // T. Returns true if the ray reached R_l and splits; its final P, tau (and
 // compensations) are then in oP, otau, ocP, octau.
-template <class R, bool kHash>
+// kFreq: Eq. 1 integrated over the blackbody spectrum (V.spec): the budget P stays the ray's
+// geometric share and the photons it still carries are P Phi(tau); otherwise the gray rate, with
+// P decremented by every absorption.
+template <class R, bool kHash, bool kFreq>
 __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, const uint32_t si, const uint32_t pix,
                                           R P, R tau, R cP, R ctau, const SrcEntry& se, const int4 dv, Tally& T,
                                           R& oP, R& otau, float& ocP, float& octau)
 {
     using I = Ieee<R>;
+    // photons the ray still carries, in units of ph
+    auto remaining = [&]() -> double {
+        if constexpr (kFreq) {
+            R phi, psi;
+            spec_eval<R>(V.spec, I::sub(tau, ctau), phi, psi);
+            return widen(P) * widen(phi);
+        } else {
+            return widen(P) - widen(cP);
+        }
+    };
     const int n = V.n;
     // the ray ends on its split sphere R_l or, with periodic boundaries, at the travel distance
     // sqrt(3) L_box if that comes first or at the same point, where it stops without splitting
@@ -250,12 +264,12 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
 
     // photons this ray absorbs (units of ph) are its budget at the start less its budget at the end:
     // the compensated budget P - cP, differenced in FP64
-    const double B0 = widen(P) - widen(cP);
+    const double B0 = remaining();
     ++T.rays;
     const bool inside0 = (unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n;
     if (!inside0) {
         ++T.esc;
-        T.escph += ph * (widen(P) - widen(cP));
+        T.escph += ph * (remaining());
     }
     unsigned seq = 0;
 
@@ -306,7 +320,28 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
         const R kap = I::mag(kraw);
         const R dtau = I::mul(kap, ds);
         R a, gseg;
-        if (kap > (R)0) {
+        if constexpr (kFreq) {
+            // Eq. 1 over frequency: the segment absorbs Phi(tau) - Phi(tau + dtau) of the budget; for
+            // a thin segment the midpoint rate dtau Psi(tau + dtau/2) instead of the difference (error
+            // dtau^2 / 24 against the difference's cancellation, equal near the switch)
+            const R t0 = I::sub(tau, ctau);
+            R phi0, psi0, phi1, psi1;
+            if (kap > (R)0) {
+                if (dtau >= (sizeof(R) == 4 ? (R)1e-2 : (R)1e-6)) {
+                    spec_eval<R>(V.spec, t0, phi0, psi0);
+                    spec_eval<R>(V.spec, t0 + dtau, phi1, psi1);
+                    a = P * (phi0 - phi1);
+                } else {
+                    spec_eval<R>(V.spec, t0 + (R)0.5 * dtau, phi0, psi0);
+                    a = P * (dtau * psi0);
+                }
+                gseg = I::qdiv(a * G, kap);
+            } else {
+                spec_eval<R>(V.spec, t0, phi0, psi0);
+                a = (R)0;
+                gseg = ((P * psi0) * G) * ds;
+            }
+        } else if (kap > (R)0) {
             a = P * I::absorb(dtau);
             gseg = I::qdiv(a * G, kap);
         } else {
@@ -341,7 +376,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             ++T.sec;
         }
         budget_add(tau, ctau, dtau);
-        budget_add(P, cP, -a);
+        if constexpr (!kFreq) budget_add(P, cP, -a);
         if (kHash && V.hash) T.hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
         ++seq;
     };
@@ -396,8 +431,8 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             segment(kcur, ds_p, dn0, dn1, dn2, I::mul(I::small(2u * kw + 1u), hw));
             if (tau >= taumax) {             // photons spent
                 ++T.dtau;
-                T.dropph += ph * (widen(P) - widen(cP));
-                T.abs += ph * (B0 - (widen(P) - widen(cP)));
+                T.dropph += ph * (remaining());
+                T.abs += ph * (B0 - (remaining()));
                 alive = false;
                 break;
             }
@@ -412,8 +447,8 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             kprev = kw;
             if (!next_in) {
                 ++T.esc;
-                T.escph += ph * (widen(P) - widen(cP));
-                T.abs += ph * (B0 - (widen(P) - widen(cP)));
+                T.escph += ph * (remaining());
+                T.abs += ph * (B0 - (remaining()));
                 alive = false;
                 break;
             }
@@ -454,16 +489,16 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
                     split_end ? I::mul((R)V.rq, I::pow2(l - F)) : I::mul(I::of(rq_end), I::pow2(-F)));
             if (tau >= taumax) {
                 ++T.dtau;
-                T.dropph += ph * (widen(P) - widen(cP));
-                T.abs += ph * (B0 - (widen(P) - widen(cP)));
+                T.dropph += ph * (remaining());
+                T.abs += ph * (B0 - (remaining()));
             } else {
-                T.abs += ph * (B0 - (widen(P) - widen(cP)));
+                T.abs += ph * (B0 - (remaining()));
                 if (!split_end) {                // travelled sqrt(3) L_box (Sec. 2.5.1)
                     ++T.esc;
-                    T.escph += ph * (widen(P) - widen(cP));
+                    T.escph += ph * (remaining());
                 } else if (l + 1 > V.level_max) {
                     ++T.dlev;
-                    T.dropph += ph * (widen(P) - widen(cP));
+                    T.dropph += ph * (remaining());
                 } else {
                     ++T.split;
                     split = true;
@@ -1079,7 +1114,7 @@ struct MarchOccupancy {
 
 // One level (or one slice of it) of one solve: thread j marches child j.
 // kHash: compiled with the visit hash (only launched when it is asked for).
-template <class R, bool kHash>
+template <class R, bool kHash, bool kFreq>
 __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(const MarchArgs<R> A)
 {
     const int l = A.level;
@@ -1097,6 +1132,7 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
     V.tau_max = A.tau_max;
     V.src_off = 0;
     V.rs = A.rs;
+    V.spec = A.spec;
     Tally T;
     T.clear();
     for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
@@ -1108,7 +1144,8 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
         if (j < A.c1) {
             R P, tau, cP, ctau;
             load_ray<R>(l, j, A.in, si, pix, P, tau, cP, ctau);
-            split = march_ray<R, kHash>(V, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T, oP, otau, ocP, octau);
+            split = march_ray<R, kHash, kFreq>(V, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T, oP, otau,
+                                               ocP, octau);
         }
         append_split<R>(split, si, pix, oP, otau, ocP, octau, A.out, A.out_count, &A.st->err);
     }
@@ -1239,7 +1276,7 @@ __global__ void __launch_bounds__(256, (kTable && kSingle) ? 4 : MarchOccupancy<
                         split = march_ray_table<kHash>(V, A.geo[l], A.err, l, si, pix, P, tau, cP, ctau, se, dirs[pix],
                                                        T, oP, otau, ocP, octau);
                     } else {
-                        split = march_ray<R, kHash>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau, ocP,
+                        split = march_ray<R, kHash, false>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau, ocP,
                                                     octau);
                     }
                 }
@@ -1262,18 +1299,28 @@ __global__ void __launch_bounds__(256, (kTable && kSingle) ? 4 : MarchOccupancy<
 
 }  // namespace
 
+template <class R>
+static int launch_march_impl(const MarchArgs<R>& a, int grid, int block, cudaStream_t s)
+{
+    const bool freq = a.spec.v != nullptr;
+    if (a.hash) {
+        if (freq) march_kernel<R, true, true><<<grid, block, 0, s>>>(a);
+        else march_kernel<R, true, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (freq) march_kernel<R, false, true><<<grid, block, 0, s>>>(a);
+        else march_kernel<R, false, false><<<grid, block, 0, s>>>(a);
+    }
+    return 1;
+}
+
 int launch_march_f64(const MarchArgs<double>& a, int grid, int block, cudaStream_t s)
 {
-    if (a.hash) march_kernel<double, true><<<grid, block, 0, s>>>(a);
-    else march_kernel<double, false><<<grid, block, 0, s>>>(a);
-    return 1;
+    return launch_march_impl<double>(a, grid, block, s);
 }
 
 int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_t s)
 {
-    if (a.hash) march_kernel<float, true><<<grid, block, 0, s>>>(a);
-    else march_kernel<float, false><<<grid, block, 0, s>>>(a);
-    return 1;
+    return launch_march_impl<float>(a, grid, block, s);
 }
 
 int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int grid, int block, cudaStream_t s)

@@ -211,11 +211,12 @@ extern "C" int rt_step_noalloc(const rt_config* cfg, void* cuda_stream, const do
     const int n = cfg->n;
     if (n < 1 || n > kNaMaxN) return set_error(RT_EINVAL, "rt_step_noalloc: n must be in 1..32");
     if (nsrc > kNaMaxSources) return set_error(RT_EINVAL, "rt_step_noalloc: at most 4096 sources per call");
-    if (cfg->merge_mode != RT_MERGE_OFF || cfg->chem_iterate)
-        return set_error(RT_EINVAL, "rt_step_noalloc: source merging and chemistry are not available here");
+    if (cfg->merge_mode != RT_MERGE_OFF || cfg->chem_iterate || cfg->spectrum != RT_SPECTRUM_GRAY)
+        return set_error(RT_EINVAL,
+                         "rt_step_noalloc: source merging, chemistry and the spectrum table are not available here");
     if ((cfg->precision != RT_FP64 && cfg->precision != RT_FP32) || !(cfg->box_cm > 0) || !(cfg->sigma_cm2 > 0) ||
         !(cfg->n_min_ray >= 1.0) || !(cfg->tau_max > 0) || cfg->overlap_mode < 0 || cfg->overlap_mode > 5 ||
-        cfg->level_max > kMaxLevel)
+        (cfg->periodic != 0 && cfg->periodic != 1) || cfg->level_max > kMaxLevel)
         return set_error(RT_EINVAL, "rt_step_noalloc: invalid configuration");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

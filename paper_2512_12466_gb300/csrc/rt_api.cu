@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <new>
@@ -22,6 +23,7 @@
 #include <vector>
 
 #include "rt_handle.h"
+#include "spectrum.h"
 
 using namespace nyx;
 
@@ -184,6 +186,121 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, long long r
     return t.usable;
 }
 
+namespace {
+
+// Blackbody spectrum tables (RT_SPECTRUM_BLACKBODY), one per (device, temperature), kept until the
+// process exits. Built on the host: with u = nu_0 / nu in (0, 1], s = sigma_nu / sigma_0 = u^3 and
+// the photon-number spectrum y^2 / (exp(theta y) - 1) dy becomes u^-4 / (exp(theta / u) - 1) du
+// (theta = h nu_0 / (k T_bb)); the moments <s^p exp(-tau s)> are integrated by composite Simpson's
+// rule over u (the integrand and its derivatives vanish at u = 0).
+struct SpecEntry {
+    double t_bb;
+    std::vector<double> host;     // the double table (host copy, for rt_spectrum_eval)
+    double psi0, xi0;
+    const double* dev_d;
+    const float* dev_f;
+};
+std::mutex g_spec_mu;
+std::map<int, std::deque<SpecEntry>> g_spec;   // a deque: entries never move once added
+
+constexpr double kHNu0Erg = 13.598 * 1.602176634e-12;   // hydrogen ionization threshold, erg
+constexpr double kKbErgK = 1.380649e-16;
+
+void spectrum_moments(double theta, double tau, double out[3])
+{
+    const int N = 4096;                       // Simpson intervals over u in (0, 1]
+    const double du = 1.0 / N;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = 1; i <= N; ++i) {            // the u = 0 end contributes 0
+        const double u = i * du;
+        const double e = std::exp(-theta / u);
+        const double base = e / (-std::expm1(-theta / u)) / (u * u * u * u);
+        const double s = u * u * u;
+        const double wgt = (i == N) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        const double f0 = base * std::exp(-tau * s);
+        acc[0] += wgt * f0;
+        acc[1] += wgt * f0 * s;
+        acc[2] += wgt * f0 * s * s;
+    }
+    for (int p = 0; p < 3; ++p) out[p] = acc[p] * du / 3.0;
+}
+
+void spectrum_build(double t_bb, std::vector<double>& v, double& psi0, double& xi0)
+{
+    const double theta = kHNu0Erg / (kKbErgK * t_bb);
+    double m0[3];
+    spectrum_moments(theta, 0.0, m0);
+    psi0 = m0[1] / m0[0];
+    xi0 = m0[2] / m0[0];
+    v.assign(4 * (size_t)kSpecPoints, 0.0);
+    for (int j = 0; j < kSpecPoints; ++j) {
+        const double tau = kSpecTauLo * std::pow(10.0, (double)j / kSpecPerDecade);
+        double m[3];
+        spectrum_moments(theta, tau, m);
+        const double phi = m[0] / m0[0], psi = m[1] / m0[0], xi = m[2] / m0[0];
+        v[4 * j] = phi;
+        v[4 * j + 1] = -tau * psi;            // dPhi / dln tau
+        v[4 * j + 2] = psi;
+        v[4 * j + 3] = -tau * xi;             // dPsi / dln tau
+    }
+}
+
+const SpecEntry* spectrum_entry(int device, double t_bb, std::string& why)
+{
+    std::lock_guard<std::mutex> lk(g_spec_mu);
+    std::deque<SpecEntry>& list = g_spec[device];
+    for (const SpecEntry& e : list)
+        if (e.t_bb == t_bb) return &e;
+    SpecEntry e{t_bb, {}, 0.0, 0.0, nullptr, nullptr};
+    spectrum_build(t_bb, e.host, e.psi0, e.xi0);
+    if (device >= 0) {
+        std::vector<float> f(e.host.begin(), e.host.end());
+        double* dd = nullptr;
+        float* df = nullptr;
+        if (cudaMalloc(&dd, sizeof(double) * e.host.size()) != cudaSuccess ||
+            cudaMalloc(&df, sizeof(float) * f.size()) != cudaSuccess ||
+            cudaMemcpy(dd, e.host.data(), sizeof(double) * e.host.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(df, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(dd);
+            cudaFree(df);
+            why = "device allocation of the spectrum table failed";
+            return nullptr;
+        }
+        e.dev_d = dd;
+        e.dev_f = df;
+    }
+    list.push_back(std::move(e));
+    return &list.back();
+}
+
+}  // namespace
+
+// Host evaluation of the table at t_bb (the host copy; entries are immutable once added).
+static void spec_eval_host(double t_bb, double tau, double* phi, double* psi)
+{
+    std::string why;
+    const SpecEntry* e = spectrum_entry(-1, t_bb, why);
+    SpecTable<double> T;
+    T.v = e->host.data();
+    T.psi0 = e->psi0;
+    T.xi0 = e->xi0;
+    nyx::spec_eval<double>(T, tau, *phi, *psi);
+}
+
+int nyx::spectrum_table(int device, double t_bb, SpecTable<double>* d, SpecTable<float>* f, std::string& why)
+{
+    const SpecEntry* e = spectrum_entry(device, t_bb, why);
+    if (!e) return RT_ENOMEM;
+    d->v = e->dev_d;
+    d->psi0 = e->psi0;
+    d->xi0 = e->xi0;
+    f->v = e->dev_f;
+    f->psi0 = (float)e->psi0;
+    f->xi0 = (float)e->xi0;
+    return RT_OK;
+}
+
 namespace nyx {
 
 int configure(rt_handle* h, const rt_config* cfg, std::string& why);
@@ -310,6 +427,8 @@ int run_level(rt_handle* h, int level, int64_t nparents)
         a.overlap_mode = h->cfg.overlap_mode;
         a.hash = (h->cfg.flags & RT_FLAG_VISIT_HASH) ? 1 : 0;
         a.rs = h->rs;
+        if constexpr (sizeof(R) == 8) a.spec = h->spec_d;
+        else a.spec = h->spec_f;
         a.st = h->d_st;
         const int64_t warps = (c1 - c0 + 31) / 32;
         const int64_t want = (warps + kMarchBlock / 32 - 1) / (kMarchBlock / 32);
@@ -317,6 +436,7 @@ int run_level(rt_handle* h, int level, int64_t nparents)
         // FP32: the level's geometry table (built once per device, outside the timed launch)
         GeomLevel gl;
         const bool table = sizeof(R) == 4 && !(h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE) &&
+                           h->cfg.spectrum == RT_SPECTRUM_GRAY &&
                            geometry_level(h->device, h->rq, level, h->cfg.n, h->rs, a.dirs, h->stream, &gl);
         RT_CUDA(h, cudaEventRecord(h->ev[4], h->stream), "event");
         if constexpr (sizeof(R) == 8) {
@@ -543,6 +663,12 @@ int configure(rt_handle* h, const rt_config* cfg, std::string& why)
     h->level_max = cfg->level_max >= 0 ? cfg->level_max : std::min(reach + 1, kMaxLevel);
     h->table_level = std::min(h->level_max, reach);
     const int need_level = std::max(h->table_level, cfg->merge_samp_level);
+    h->spec_d = SpecTable<double>();
+    h->spec_f = SpecTable<float>();
+    if (cfg->spectrum == RT_SPECTRUM_BLACKBODY) {
+        const int rc = spectrum_table(h->device, cfg->t_bb_K, &h->spec_d, &h->spec_f, why);
+        if (rc) return rc;
+    }
     return ensure_directions(h->device, need_level, &h->dirs, why);
 }
 
@@ -560,6 +686,14 @@ bool valid_config(const rt_config* c, std::string& why)
     if (!(c->merge_dr_cells > 0)) { why = "merge_dr_cells must be positive"; return false; }
     if (c->level_max > kMaxLevel) { why = "level_max must be <= 13"; return false; }
     if (c->periodic != 0 && c->periodic != 1) { why = "periodic must be 0 or 1"; return false; }
+    if (c->spectrum != RT_SPECTRUM_GRAY && c->spectrum != RT_SPECTRUM_BLACKBODY) {
+        why = "spectrum must be RT_SPECTRUM_GRAY or RT_SPECTRUM_BLACKBODY";
+        return false;
+    }
+    if (c->spectrum == RT_SPECTRUM_BLACKBODY && (!(c->t_bb_K > 0) || !std::isfinite(c->t_bb_K) || !(c->tau_max <= kSpecTauHi))) {
+        why = "RT_SPECTRUM_BLACKBODY needs t_bb_K > 0 and tau_max <= 1e4";
+        return false;
+    }
     return true;
 }
 
@@ -597,6 +731,9 @@ void rt_config_default(rt_config* c, int32_t n, double box_cm)
     c->chem_tol = 1e-6;
     c->chem_max_iter = 100;
     c->flags = 0;
+    c->periodic = 0;
+    c->spectrum = RT_SPECTRUM_GRAY;
+    c->t_bb_K = 1e5;
 }
 
 const char* rt_version(void) { return "nyxrt 0.1 (sm_103a)"; }
@@ -715,6 +852,13 @@ int rt_add_sources(rt_handle* h, const int32_t* cell_ijk, const double* ndot, in
     RT_CUDA(h, cudaMemcpyAsync(h->sw.ndot_raw + h->nsrc, ndot, 8 * (size_t)n, k, h->stream), "source copy");
     if (where == RT_HOST) RT_CUDA(h, cudaStreamSynchronize(h->stream), "source copy");
     h->nsrc += n;
+    return RT_OK;
+}
+
+int rt_spectrum_eval(double t_bb_K, double tau, double* phi, double* psi)
+{
+    if (!phi || !psi || !(t_bb_K > 0) || !std::isfinite(t_bb_K) || !(tau >= 0) || !(tau <= kSpecTauHi)) return RT_EINVAL;
+    spec_eval_host(t_bb_K, tau, phi, psi);
     return RT_OK;
 }
 

@@ -76,6 +76,8 @@ struct rt_handle {
     double dx = 0, vol = 0, sdx = 0, s_over_dx2 = 0;
     int64_t rq = 0;
     int64_t rs = 0;                          // periodic: travel-distance cutoff sqrt(3) n (2^-24 cells)
+    nyx::SpecTable<double> spec_d;           // RT_SPECTRUM_BLACKBODY tables (device)
+    nyx::SpecTable<float> spec_f;
     int level_max = 0;
     int table_level = 0;
     const int4* dirs = nullptr;
@@ -128,6 +130,8 @@ int ensure_directions(int device, int level, const int4** out, std::string& err)
 // false if the level has none (over the device's table budget), so its rays are walked.
 bool geometry_level(int device, long long rq, int level, int n, long long rs, const int4* dirs_level,
                     cudaStream_t s, GeomLevel* out);
+// The RT_SPECTRUM_BLACKBODY tables at t_bb for `device` (device < 0: host table only).
+int spectrum_table(int device, double t_bb, SpecTable<double>* d, SpecTable<float>* f, std::string& why);
 int handle_prepare_sources(rt_handle* h);
 int handle_reconfigure(rt_handle* h, const rt_config* cfg);
 int prepare_sources_many(rt_handle* const* hs, int count, int* rcs);

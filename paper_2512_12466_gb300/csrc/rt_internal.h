@@ -7,6 +7,8 @@
 
 #include "../../include/nyxrt.h"
 
+#include "spectrum.h"
+
 namespace nyx {
 
 // Ray directions are HEALPix pixel centres quantised to 2^-kDirBits per
@@ -86,6 +88,7 @@ struct MarchArgs {
     int overlap_mode;
     int hash;
     long long rs;                    // periodic boundaries: travel-distance cutoff (2^-24 cells); 0: none
+    SpecTable<R> spec;               // RT_SPECTRUM_BLACKBODY table; spec.v null: gray
     DevStats* st;
 };
 

@@ -21,7 +21,7 @@ BOOK = ("rays", "splits", "escaped", "dropped_tau", "dropped_level", "segments",
 NYX_KEYS = ("precision", "n_min_ray", "level_max", "overlap_mode", "tau_max", "n_th_cm3", "e_heat_erg",
             "merge_mode", "merge_samp_level", "automerge_xbar", "merge_x_th", "merge_f_req", "merge_dr_cells",
             "merge_rmax_cells", "merge_f_ov", "merge_eps", "merge_n_min", "chem_iterate", "alpha_B", "C_H",
-            "clumping", "chem_tol", "chem_max_iter", "flags", "periodic")
+            "clumping", "chem_tol", "chem_max_iter", "flags", "periodic", "spectrum", "t_bb_K")
 
 
 @pytest.fixture(scope="module")
@@ -194,6 +194,53 @@ def test_periodic_parity(nyx, case, prec, walk):
         ref64 = oracle.run_workload(w, **dict(kw, precision=0))
         assert relerr(got["gamma"], ref64["gamma"]) < 1e-5
         assert_ledger(got["stats"], 1e-6)
+
+
+SPECTRUM_CASES = [
+    # (n, sources, seed, x mode, box per cell, overlap mode, T_bb, periodic)
+    (12, 3, 501, "mixed", 3e21, 3, 1e5, 0),
+    (20, 5, 502, "patchy", 2e21, 2, 5e4, 0),
+    (17, 4, 503, "thin", 7e20, 3, 1e5, 1),
+    (24, 6, 504, "mixed", 1e22, 1, 3e4, 0),
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", SPECTRUM_CASES)
+def test_spectrum_parity(nyx, case, prec):
+    """Eq. 1 integrated over a blackbody spectrum: bookkeeping bit for bit (tau
+    decides everything), fields within the table's interpolation accuracy of
+    the oracle's direct quadrature (FP64 1e-7; FP32 2e-5 of the FP64 oracle)."""
+    n, k, seed, xm, dxc, mode, t_bb, per = case
+    w = I.random_small(n, k, seed=seed, x_mode=xm, box_cm=n * dxc)
+    kw = dict(overlap_mode=mode, n_th_cm3=0.3 * float(w.n_h.mean()), spectrum=1, t_bb_K=t_bb, periodic=per)
+    ref, got = run_both(nyx, w, precision=prec, **kw)
+    assert_bookkeeping(got["stats"], ref["stats"])
+    ref64 = ref if prec == 0 else oracle.run_workload(w, precision=0, **kw)
+    assert relerr(got["gamma"], ref64["gamma"]) < (1e-7 if prec == 0 else 2e-5)
+    st = got["stats"]
+    e = st["emitted_ph"]
+    tol = 1e-12 if prec == 0 else 1e-6
+    assert abs(st["absorbed_ph"] + st["escaped_ph"] + st["dropped_ph"] - e) / e < tol
+    assert abs(st["absorbed_ph"] / ref64["stats"]["absorbed_ph"] - 1) < (1e-7 if prec == 0 else 2e-5)
+    if mode in (0, 2, 3):
+        assert abs(st["deposited_ph"] - st["absorbed_ph"]) / e < (1e-10 if prec == 0 else 1e-5)
+
+
+def test_spectrum_rejected_where_not_available(nyx):
+    w = I.random_small(12, 2, seed=505, x_mode="mixed", box_cm=12 * 3e21)
+    s = nyx.Solver(w.n, w.box_cm, precision=1, spectrum=1)
+    s.set_fields(w.n_h.ravel(), w.x_ion.ravel())
+    s.add_sources(w.cells.ravel(), w.ndot)
+    with pytest.raises(nyx.NyxError):
+        nyx.Batch([s])
+    s.close()
+    srv = nyx.Server(precision=1)
+    with pytest.raises(nyx.NyxError):
+        srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot, spectrum=1)
+    srv.close()
+    with pytest.raises(nyx.NyxError):
+        nyx.Solver(w.n, w.box_cm, spectrum=1, tau_max=2e4)       # beyond the table
 
 
 def test_host_and_device_inputs_agree(nyx):
