@@ -45,9 +45,9 @@ L2_FLUSH_BYTES = 512 << 20
 # all march launches of one step of the same box with its first 64 sources;
 # profiles/march_table_config2_dram.md), scaled to the full workload by primary segments. Valid only
 # for the kernel sources it was taken on.
-TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.76592188759445,
-                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "35f1ba1b977d8abd",
-                               "paper_2512_12466_gb300/csrc/rt_internal.h": "2d6ed30287c61a11"}}
+TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.763212646120428,
+                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "4b3a71c57998d3c2",
+                               "paper_2512_12466_gb300/csrc/rt_internal.h": "2308ad8b3588ea45"}}
 
 
 def traffic_per_launch(segments_per_step: float, launches_per_step: float):
@@ -261,6 +261,27 @@ def bench_overlap_modes(nyx, torch, w, n_th):
         out[name] = {"overlap_mode": mode, "deposited_over_absorbed": st["deposited_ph"] / st["absorbed_ph"],
                      "secondary_per_step": sum(st["secondary"]), "march_ms": st["ms_march"],
                      "segments_per_s": sum(st["segments"]) / (st["ms_march"] / 1e3)}
+    return out
+
+
+def bench_spectrum(nyx, torch, w, n_th):
+    """Eq. 1 over a blackbody spectrum (1e5 K) on the same box, FP32 and FP64, one step each,
+    beside the gray rate through the same walked march: throughput and the photons deposited."""
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+    nh, xx, cc, nd = dev(w.n_h), dev(w.x_ion), dev(w.cells), dev(w.ndot)
+    g = torch.empty(w.n ** 3, dtype=torch.float64, device="cuda")
+    out = {}
+    for label, prec, spec in (("fp32_gray_walk", nyx.RT_FP32, 0), ("fp32_blackbody", nyx.RT_FP32, 1),
+                              ("fp64_gray", nyx.RT_FP64, 0), ("fp64_blackbody", nyx.RT_FP64, 1)):
+        s = nyx.Solver(w.n, w.box_cm, precision=prec, n_th_cm3=n_th, n_min_ray=4.0, tau_max=30.0, spectrum=spec,
+                       t_bb_K=1e5, flags=nyx.RT_FLAG_NO_GEOMETRY_TABLE)
+        s.set_fields(nh, xx)
+        s.add_sources(cc[: 3 * 128], nd[:128])          # 128 of the 1024 sources: the FP64 march is slow
+        _, _, st = s.step(0.0, g, None)
+        s.close()
+        out[label] = {"segments_per_s": sum(st["segments"]) / (st["ms_march"] / 1e3), "march_ms": st["ms_march"],
+                      "absorbed_over_emitted": st["absorbed_ph"] / st["emitted_ph"],
+                      "dropped_over_emitted": st["dropped_ph"] / st["emitted_ph"]}
     return out
 
 
@@ -590,6 +611,7 @@ def run_nyx(args, world, rank, local):
         "clocks": f32["clocks"],
     }
     line["overlap_modes"] = bench_overlap_modes(nyx, torch, w, n_th)
+    line["spectrum"] = bench_spectrum(nyx, torch, w, n_th)
     if not args.no_batched:
         line["batched"] = {"neutral": bench_batched(nyx, torch, "neutral", steps=5, tune=True),
                            "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 25)}
