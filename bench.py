@@ -264,6 +264,34 @@ def bench_overlap_modes(nyx, torch, w, n_th):
     return out
 
 
+def bench_config4(nyx, torch):
+    """256^3 patchy box (40 Mpc/h, sigma_ln 1.5), 32768 sources, Alg. 3 merging forced (default f_req 0.9,
+    and 0.5, where groups form), conservative correction, FP32 and FP64: one step each (a second,
+    timed, after a first that builds the geometry tables); catalog sizes, segments, merge and march cost."""
+    w = I.config4()
+    n_th = 0.01 * float(w.n_h.mean())
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+    nh, xx, cc, nd = dev(w.n_h), dev(w.x_ion), dev(w.cells), dev(w.ndot)
+    g = torch.empty(w.n ** 3, dtype=torch.float64, device="cuda")
+    out = {}
+    for label, prec, f_req in (("fp32_f_req_0.9", nyx.RT_FP32, 0.9), ("fp32_f_req_0.5", nyx.RT_FP32, 0.5),
+                               ("fp64_f_req_0.5", nyx.RT_FP64, 0.5)):
+        s = nyx.Solver(w.n, w.box_cm, precision=prec, n_th_cm3=n_th, n_min_ray=4.0, tau_max=30.0, merge_mode=1,
+                       merge_f_req=f_req)
+        s.set_fields(nh, xx)
+        s.add_sources(cc, nd)
+        s.step(0.0, g, None)
+        _, _, st = s.step(0.0, g, None)
+        s.close()
+        seg = sum(st["segments"])
+        out[label] = {"sources_in": st["n_src_in"], "sources_dedup": st["n_src_dedup"],
+                      "sources_traced": st["n_src_emit"], "segments": seg, "secondary": sum(st["secondary"]),
+                      "step_ms": st["ms_step"], "march_ms": st["ms_march"],
+                      "segments_per_s": seg / (st["ms_march"] / 1e3),
+                      "deposited_over_absorbed": st["deposited_ph"] / st["absorbed_ph"]}
+    return out
+
+
 def bench_spectrum(nyx, torch, w, n_th):
     """Eq. 1 over a blackbody spectrum (1e5 K) on the same box, FP32 and FP64, one step each,
     beside the gray rate through the same walked march: throughput and the photons deposited."""
@@ -612,6 +640,7 @@ def run_nyx(args, world, rank, local):
     }
     line["overlap_modes"] = bench_overlap_modes(nyx, torch, w, n_th)
     line["spectrum"] = bench_spectrum(nyx, torch, w, n_th)
+    line["config4"] = bench_config4(nyx, torch)
     if not args.no_batched:
         line["batched"] = {"neutral": bench_batched(nyx, torch, "neutral", steps=5, tune=True),
                            "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 25)}

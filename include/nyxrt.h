@@ -200,6 +200,19 @@ int rt_step(rt_handle* h, double dt_s, double* gamma_out, double* heat_out, int 
 /* Copy the handle's current ionized fraction (n^3 float64) out. */
 int rt_get_x(rt_handle* h, double* x_out, int where);
 
+/* The source catalog that the handle's last step (rt_step or a batched run)
+ * traced, i.e. the sources whose 12 level-0 rays were emitted (Sec. 2.8):
+ * deduplicated by cell, sorted by (ix, iy, iz) and, where that step merged,
+ * replaced by the Alg. 3 groups (a group sits at its snapped centroid and
+ * carries the sum of its members' rates, added in catalog order). Writes
+ * min(catalog size, capacity) entries: cells_out as int32 (ix, iy, iz) triples,
+ * ndot_out as float64 photons/s, both host or device memory per `where`;
+ * *count receives the catalog size. With capacity 0 the two pointers may be
+ * NULL (a size query). RT_ESTATE if sources were added or cleared (or the
+ * handle reconfigured) since the last step, or none has run. */
+int rt_get_sources(rt_handle* h, int32_t* cells_out, double* ndot_out, int64_t capacity, int64_t* count,
+                   int where);
+
 /* Free the handle and its device memory. NULL is accepted. */
 int rt_destroy(rt_handle* h);
 

@@ -115,6 +115,7 @@ def lib():
         L.rt_geometry_table_bytes.restype = i64
         L.rt_step.argtypes = [P, d, P, P, C.c_int, C.POINTER(rt_stats)]
         L.rt_get_x.argtypes = [P, P, C.c_int]
+        L.rt_get_sources.argtypes = [P, P, P, i64, C.POINTER(i64), C.c_int]
         L.rt_destroy.argtypes = [P]
         L.rt_last_error.argtypes = [P]
         L.rt_last_error.restype = C.c_char_p
@@ -138,7 +139,7 @@ def lib():
         L.rt_server_last_error.argtypes = [P]
         L.rt_server_last_error.restype = C.c_char_p
         for f in ("rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_reconfigure", "rt_step", "rt_get_x",
-                  "rt_destroy", "rt_batch_create", "rt_batch_set_params", "rt_batch_get_params", "rt_batch_tune",
+                  "rt_get_sources", "rt_destroy", "rt_batch_create", "rt_batch_set_params", "rt_batch_get_params", "rt_batch_tune",
                   "rt_batch_capture", "rt_batch_run", "rt_batch_destroy", "rt_server_create", "rt_server_submit",
                   "rt_server_poll", "rt_server_stats_get", "rt_server_destroy"):
             getattr(L, f).restype = C.c_int
@@ -149,7 +150,7 @@ def lib():
 def exported_symbols():
     return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_reconfigure",
             "rt_geometry_table_bytes", "rt_spectrum_eval", "rt_step",
-            "rt_get_x", "rt_destroy", "rt_last_error", "rt_version", "rt_batch_create", "rt_batch_set_params",
+            "rt_get_x", "rt_get_sources", "rt_destroy", "rt_last_error", "rt_version", "rt_batch_create", "rt_batch_set_params",
             "rt_batch_get_params", "rt_batch_tune", "rt_batch_capture", "rt_batch_run", "rt_batch_destroy",
             "rt_batch_last_error", "rt_server_config_default", "rt_server_create", "rt_server_submit",
             "rt_server_poll", "rt_server_stats_get", "rt_server_destroy", "rt_server_last_error", "rt_step_noalloc"]
@@ -226,6 +227,13 @@ def rt_step(h: int, dt_s: float, gamma_out, heat_out, where: int, stats: rt_stat
 
 def rt_get_x(h: int, x_out, where: int) -> None:
     _check(lib().rt_get_x(h, x_out, where), h)
+
+
+def rt_get_sources(h: int, cells_out, ndot_out, capacity: int, where: int) -> int:
+    """Copies up to `capacity` entries of the last traced catalog; returns its size."""
+    m = C.c_int64(0)
+    _check(lib().rt_get_sources(h, cells_out, ndot_out, int(capacity), C.byref(m), where), h)
+    return int(m.value)
 
 
 def rt_destroy(h: int) -> None:
@@ -364,6 +372,16 @@ class Solver:
         p, w = _ptr(out)
         rt_get_x(self.h, p, w)
         return out
+
+    def sources(self):
+        """The catalog the last step traced (after dedup, sort and Alg. 3
+        merging) as numpy arrays: cells (m, 3) int32 (ix, iy, iz), ndot (m,)."""
+        m = rt_get_sources(self.h, None, None, 0, RT_HOST)
+        cells = np.empty((m, 3), dtype=np.int32)
+        ndot = np.empty(m)
+        if m:
+            rt_get_sources(self.h, cells.ctypes.data, ndot.ctypes.data, m, RT_HOST)
+        return cells, ndot
 
     def close(self):
         if self.h:

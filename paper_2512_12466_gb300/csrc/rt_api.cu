@@ -542,6 +542,7 @@ int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out)
     h->launches += launch_build_emit(h->sw, m, h->s_over_dx2, h->d_emit, h->d_st, s);
     RT_LAUNCHED(h, "emit launch");
     h->n_emit = m;
+    h->catalog_valid = true;
 
     return RT_OK;
 }
@@ -560,6 +561,7 @@ int handle_reconfigure(rt_handle* h, const rt_config* cfg)
     h->nsrc = 0;
     h->fields_set = false;
     h->src_ready = false;
+    h->catalog_valid = false;
     h->err.clear();
     return RT_OK;
 }
@@ -610,6 +612,7 @@ int prepare_sources_many(rt_handle* const* hs, int count, int* rcs)
         if (h->src_ready) continue;
         const int64_t m = h->nsrc > 0 ? h->h_i32[0] : 0;
         h->n_emit = m;
+        h->catalog_valid = true;
         h->src_ready = true;
         h->src_merged = false;
         h->src_dedup = m;
@@ -845,6 +848,7 @@ int rt_add_sources(rt_handle* h, const int32_t* cell_ijk, const double* ndot, in
         }
     }
     DeviceGuard g(h->device);
+    h->catalog_valid = false;
     int rc = grow_sources(h, h->nsrc + n);
     if (rc) return rc;
     const cudaMemcpyKind k = where == RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -881,6 +885,26 @@ int rt_clear_sources(rt_handle* h)
     if (!h) return RT_EINVAL;
     if (h->sticky) return RT_ESTATE;
     h->nsrc = 0;
+    h->catalog_valid = false;
+    return RT_OK;
+}
+
+int rt_get_sources(rt_handle* h, int32_t* cells_out, double* ndot_out, int64_t capacity, int64_t* count, int where)
+{
+    if (!h) return RT_EINVAL;
+    if (!count || capacity < 0 || (capacity > 0 && (!cells_out || !ndot_out)) || (where != RT_HOST && where != RT_DEVICE))
+        return fail(h, RT_EINVAL, "bad arguments");
+    if (h->sticky) return RT_ESTATE;
+    if (!h->catalog_valid) return fail(h, RT_ESTATE, "no step has traced the current sources");
+    *count = h->n_emit;
+    const int64_t m = std::min(capacity, h->n_emit);
+    if (m > 0) {
+        DeviceGuard g(h->device);
+        const cudaMemcpyKind k = where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        RT_CUDA(h, cudaMemcpyAsync(cells_out, h->sw.cells_a, 12 * (size_t)m, k, h->stream), "catalog copy");
+        RT_CUDA(h, cudaMemcpyAsync(ndot_out, h->sw.ndot_a, 8 * (size_t)m, k, h->stream), "catalog copy");
+        RT_CUDA(h, cudaStreamSynchronize(h->stream), "catalog copy");
+    }
     return RT_OK;
 }
 

@@ -95,6 +95,7 @@ struct rt_handle {
     int64_t nsrc = 0;
     nyx::SrcEntry* d_emit = nullptr;
     int64_t n_emit = 0;
+    bool catalog_valid = false;              // cells_a/ndot_a[0..n_emit) hold the catalog last traced
 
     nyx::RayStore rays[RT_MAX_LEVELS + 1];
     unsigned long long* d_count = nullptr;   // one per level

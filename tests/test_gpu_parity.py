@@ -457,6 +457,46 @@ def test_invalid_inputs_rejected(nyx):
     s.close()
 
 
+def test_traced_catalog_readback(nyx):
+    """rt_get_sources: the deduplicated, sorted catalog of the last step (summed
+    rates of duplicates), host and device outputs, a size query, truncation to
+    the capacity, and RT_ESTATE before a step or once sources changed."""
+    w = I.random_small(12, 6, seed=181, x_mode="mixed", box_cm=12 * 3e21)
+    cells = np.concatenate([w.cells, w.cells[:2]])
+    ndot = np.concatenate([w.ndot, w.ndot[:2] * 0.5])
+    s = nyx.Solver(w.n, w.box_cm)
+    s.set_fields(w.n_h.ravel(), w.x_ion.ravel())
+    s.add_sources(cells.ravel(), ndot)
+    with pytest.raises(nyx.NyxError) as e:
+        s.sources()
+    assert e.value.code == nyx.RT_ESTATE
+    s.step()
+    c, nd = s.sources()
+    rc, rn = oracle.sources_dedup(cells, ndot)
+    assert np.array_equal(c, rc) and np.array_equal(nd, rn)
+    m = nyx.rt_get_sources(s.h, None, None, 0, nyx.RT_HOST)
+    assert m == len(rn)
+    dc = torch.full((3 * m,), -1, dtype=torch.int32, device="cuda")
+    dn = torch.zeros(m, dtype=torch.float64, device="cuda")
+    assert nyx.rt_get_sources(s.h, dc.data_ptr(), dn.data_ptr(), m - 1, nyx.RT_DEVICE) == m
+    torch.cuda.synchronize()
+    assert np.array_equal(dc.cpu().numpy()[: 3 * (m - 1)].reshape(-1, 3), rc[: m - 1])
+    assert (dc.cpu().numpy()[3 * (m - 1):] == -1).all() and dn[m - 1].item() == 0.0
+    s.add_sources(w.cells[:1].ravel(), w.ndot[:1])
+    with pytest.raises(nyx.NyxError) as e:
+        s.sources()
+    assert e.value.code == nyx.RT_ESTATE
+    s.step()
+    assert len(s.sources()[1]) == m
+    s.clear_sources()
+    with pytest.raises(nyx.NyxError):
+        s.sources()
+    with pytest.raises(nyx.NyxError) as e:
+        nyx.rt_get_sources(s.h, None, None, 1, nyx.RT_HOST)
+    assert e.value.code == nyx.RT_EINVAL
+    s.close()
+
+
 def test_repeat_steps_are_reproducible(nyx):
     w = I.random_small(24, 8, seed=171, x_mode="patchy", box_cm=24 * 7e22)
     s = nyx.Solver(w.n, w.box_cm, flags=nyx.RT_FLAG_VISIT_HASH, n_th_cm3=1e-5)
@@ -525,3 +565,94 @@ def test_config2_full_invariants(nyx):
         assert (r["gamma"] >= 0).all()
     assert relerr(b["gamma"], a["gamma"]) < 1e-5
     assert sum(a["stats"]["segments"]) > 1e9
+
+
+@pytest.fixture(scope="module")
+def config4():
+    """256^3, 40 Mpc/h, sigma_ln = 1.5, patchy x, 32768 power-law sources."""
+    return I.config4()
+
+
+def _gpu_solver(nyx, w, cells, ndot, **cfg):
+    dev = torch.device("cuda")
+    cfg["flags"] = cfg.get("flags", 0) | nyx.RT_FLAG_VISIT_HASH
+    s = nyx.Solver(w.n, w.box_cm, **cfg)
+    s.set_fields(torch.from_numpy(w.n_h.ravel()).to(dev), torch.from_numpy(w.x_ion.ravel()).to(dev))
+    s.add_sources(torch.from_numpy(np.ascontiguousarray(cells, dtype=np.int32).ravel()).to(dev),
+                  torch.from_numpy(np.ascontiguousarray(ndot, dtype=np.float64)).to(dev))
+    g = torch.empty(w.n ** 3, dtype=torch.float64, device=dev)
+    _, _, st = s.step(0.0, g, None)
+    return s, g.cpu().numpy().reshape((w.n,) * 3), st
+
+
+@pytest.mark.parametrize("f_req", [0.9, 0.5])
+def test_config4_merged_catalog(nyx, config4, f_req):
+    """256^3 patchy box, all 32768 sources, merging forced: the catalog the GPU
+    traced (rt_get_sources) equals the oracle's dedup + Alg. 3 output exactly,
+    cells and summed rates. With the default f_req = 0.9 no source's shell is
+    ionized enough in this noisy x field and nothing merges; with f_req = 0.5
+    groups form."""
+    w = config4
+    c, nd = oracle.sources_dedup(w.cells, w.ndot)
+    mc, mn, _, _ = oracle.merge_sources(w.x_ion, c, nd, f_req=f_req)
+    s, _, st = _gpu_solver(nyx, w, w.cells, w.ndot, precision=1, merge_mode=1, merge_f_req=f_req,
+                           n_th_cm3=0.01 * float(w.n_h.mean()))
+    cells, ndot = s.sources()
+    s.close()
+    assert st["merged"] == 1 and st["n_src_in"] == 32768
+    assert st["n_src_dedup"] == len(nd) and st["n_src_emit"] == len(mn) == len(ndot)
+    assert np.array_equal(cells, mc) and np.array_equal(ndot, mn)
+    if f_req == 0.9:
+        assert len(mn) == len(nd)
+    else:
+        assert len(mn) < len(nd) - 100
+    assert abs(st["emitted_ph"] / nd.sum() - 1) < 1e-12
+
+
+def test_config4_full_size_parity(nyx, config4):
+    """The full-size merged step (f_req = 0.5) in FP64 and FP32: the ledger
+    closes and deposited = absorbed (Eqs. 7-8); FP32 within 1e-5 of FP64; the
+    traced catalog fed back with merging off gives the same bookkeeping, hash
+    and field (Alg. 3 only changes the catalog). A seeded subset of 256 merged
+    sources against the oracle (bookkeeping bit-exact; Gamma 1e-12, FP32 1e-5),
+    and Gamma is additive over sources: subset plus complement equals the whole
+    (counts exactly, field within 1e-12)."""
+    w = config4
+    nth = 0.01 * float(w.n_h.mean())
+    full = {}
+    for prec in (0, 1):
+        s, g, st = _gpu_solver(nyx, w, w.cells, w.ndot, precision=prec, merge_mode=1, merge_f_req=0.5, n_th_cm3=nth)
+        if prec == 0:
+            mc, mn = s.sources()
+        s.close()
+        tol = 1e-12 if prec == 0 else 1e-6
+        assert_ledger(st, tol)
+        assert abs(st["deposited_ph"] - st["absorbed_ph"]) <= tol * st["emitted_ph"]
+        assert (g >= 0).all() and sum(st["segments"]) > 1e6 and sum(st["secondary"]) > 0
+        full[prec] = (g, st)
+    assert relerr(full[1][0], full[0][0]) < 1e-5
+    s, g_fed, st_fed = _gpu_solver(nyx, w, mc, mn, precision=0, merge_mode=0, n_th_cm3=nth)
+    s.close()
+    for k in BOOK:
+        assert list(st_fed[k]) == list(full[0][1][k]), k
+    assert st_fed["visit_hash"] == full[0][1]["visit_hash"]
+    assert relerr(g_fed, full[0][0]) < 1e-12
+    sub = np.sort(np.random.default_rng(4004).choice(len(mn), size=256, replace=False))
+    rest = np.setdiff1d(np.arange(len(mn)), sub)
+    parts = {}
+    for prec in (0, 1):
+        ref = oracle.run(w.n_h, w.x_ion, mc[sub], mn[sub], w.box_cm, precision=prec, n_th_cm3=nth, **w.params)
+        s, g, st = _gpu_solver(nyx, w, mc[sub], mn[sub], precision=prec, n_th_cm3=nth)
+        s.close()
+        assert_bookkeeping(st, ref["stats"])
+        if prec == 0:
+            assert relerr(g, ref["gamma"]) < 1e-12
+            parts["sub"] = (g, st)
+        else:
+            assert relerr(g, parts["sub"][0]) < 1e-5
+    s, g_rest, st_rest = _gpu_solver(nyx, w, mc[rest], mn[rest], precision=0, n_th_cm3=nth)
+    s.close()
+    g_sub, st_sub = parts["sub"]
+    for k in ("rays", "splits", "escaped", "dropped_tau", "dropped_level", "segments", "secondary"):
+        assert [a + b for a, b in zip(st_sub[k], st_rest[k])] == list(full[0][1][k]), k
+    assert relerr(g_sub + g_rest, full[0][0]) < 1e-12
