@@ -109,11 +109,11 @@ enum {
                                   fraction of its photons that survive tau (tabulated per
                                   temperature, cubic interpolation in ln tau). tau_max <= 1e4.
                                   rt_step only (not the batched, serving or allocation-free forms);
-                                  the FP32 march walks its rays (no geometry tables). */
+                                  the march walks its rays (no geometry tables). */
 };
 
 #define RT_FLAG_VISIT_HASH 1   /* accumulate the visit-list hash in rt_stats (bookkeeping check) */
-#define RT_FLAG_NO_GEOMETRY_TABLE 2  /* FP32: walk every ray's cells instead of reading them from the
+#define RT_FLAG_NO_GEOMETRY_TABLE 2  /* walk every ray's cells instead of reading them from the
                                         per-device geometry tables (same results; for comparison) */
 
 /* Step statistics, filled by rt_step (host memory, valid on return). */
@@ -216,14 +216,17 @@ int rt_get_sources(rt_handle* h, int32_t* cells_out, double* ndot_out, int64_t c
 /* Free the handle and its device memory. NULL is accepted. */
 int rt_destroy(rt_handle* h);
 
-/* Device memory held by the FP32 geometry tables of CUDA device `device`, in
+/* Device memory held by the geometry tables of CUDA device `device`, in
  * bytes. A ray's cells, segment lengths and overlap-correction geometry
  * relative to its source depend only on its HEALPix level and pixel (every
  * source sits at a cell centre: Sec. 2.5 with the source convention of
- * Alg. 3), so the FP32 march reads them from tables built on first use for
- * each (split radius, level, grid size) and kept until the process exits,
- * within a budget of an eighth of the device's memory (environment variable
- * NYXRT_GEOMETRY_BUDGET_MB overrides it); levels over budget walk their rays. */
+ * Alg. 3), so the march reads them from tables built on first use for each
+ * (split radius, level, grid size) and kept until the process exits: row
+ * offsets shared by both precisions, 8-byte entries for the FP32 march and
+ * 16-byte ones for the FP64 march (each built when that precision first
+ * needs the level), within a budget of an eighth of the device's memory
+ * (environment variable NYXRT_GEOMETRY_BUDGET_MB overrides it); levels over
+ * budget walk their rays. The batched form reads the FP32 tables only. */
 int64_t rt_geometry_table_bytes(int32_t device);
 
 /* Phi(tau) and the thin rate Psi(tau) = -dPhi/dtau of RT_SPECTRUM_BLACKBODY at

@@ -403,7 +403,7 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
         for (int l = 0; l <= RT_MAX_LEVELS; ++l) b->geo[l] = GeomLevel();
         for (int l = 0; b->use_geo && l <= table_level; ++l)
             if (!geometry_level(b->device, b->hs[0]->rq, l, nmax, b->hs[0]->rs, b->dirs + healpix_level_offset(l),
-                                b->stream, &b->geo[l]))
+                                b->stream, false, &b->geo[l]))
                 b->use_geo = false;
     }
     // ---- all solves' emitted sources in one catalog, tagged with their solve index

@@ -48,8 +48,56 @@ struct Ieee<double> {
     // photons absorbed per unit budget over optical depth x >= 0: 1 - e^{-x}
     __device__ __forceinline__ static double absorb(double x) { return -expm1(-x); }
     __device__ __forceinline__ static double qdiv(double a, double b) { return a / b; }
+    // Eq. 1 for a segment of optical depth dtau = kap ds, kap > 0: photons absorbed a = P (1 - e^{-dtau})
+    // and rate gseg = a G / kap. Below dtau = 2 both come from g(y) = (1 - e^{-y}) / y, whose
+    // series sum_k (-y)^k / (k+1)! is summed to k = 23 (the first term left out is below
+    // 2^24 / 25! < 1.1e-18, against g(2) > 0.43): a = P dtau g and gseg = P G ds g, with no
+    // exponential and no division on GB300's small FP64 unit; the bound is wide enough that a
+    // warp's lanes seldom split between the two forms. Above it, expm1 and the quotient.
+    __device__ __forceinline__ static void rate(double P, double G, double kap, double ds, double dtau, double& a,
+                                                double& gseg)
+    {
+        if (lt(dtau, 2.0)) {
+            double g = 1.0 / 620448401733239439360000.0;                  // 1 / 24!
+            g = fma(-dtau, g, 1.0 / 25852016738884976640000.0);
+            g = fma(-dtau, g, 1.0 / 1124000727777607680000.0);
+            g = fma(-dtau, g, 1.0 / 51090942171709440000.0);
+            g = fma(-dtau, g, 1.0 / 2432902008176640000.0);
+            g = fma(-dtau, g, 1.0 / 121645100408832000.0);
+            g = fma(-dtau, g, 1.0 / 6402373705728000.0);
+            g = fma(-dtau, g, 1.0 / 355687428096000.0);
+            g = fma(-dtau, g, 1.0 / 20922789888000.0);
+            g = fma(-dtau, g, 1.0 / 1307674368000.0);
+            g = fma(-dtau, g, 1.0 / 87178291200.0);
+            g = fma(-dtau, g, 1.0 / 6227020800.0);
+            g = fma(-dtau, g, 1.0 / 479001600.0);
+            g = fma(-dtau, g, 1.0 / 39916800.0);
+            g = fma(-dtau, g, 1.0 / 3628800.0);
+            g = fma(-dtau, g, 1.0 / 362880.0);
+            g = fma(-dtau, g, 1.0 / 40320.0);
+            g = fma(-dtau, g, 1.0 / 5040.0);
+            g = fma(-dtau, g, 1.0 / 720.0);
+            g = fma(-dtau, g, 1.0 / 120.0);
+            g = fma(-dtau, g, 1.0 / 24.0);
+            g = fma(-dtau, g, 1.0 / 6.0);
+            g = fma(-dtau, g, 0.5);
+            g = fma(-dtau, g, 1.0);
+            a = P * (dtau * g);
+            gseg = ((P * G) * ds) * g;
+        } else {
+            a = P * absorb(dtau);
+            gseg = qdiv(a * G, kap);
+        }
+    }
+    // a < b and a > 0 for a, b >= 0 (not NaN): the order of their bit patterns as integers, which
+    // keeps the comparison off the FP64 pipe
+    __device__ __forceinline__ static bool lt(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+    __device__ __forceinline__ static bool pos(double a) { return __double_as_longlong(a) > 0; }
     __device__ __forceinline__ static bool neg(double x) { return __double_as_longlong(x) < 0; }
-    __device__ __forceinline__ static double mag(double x) { return fabs(x); }
+    __device__ __forceinline__ static double mag(double x)
+    {
+        return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffll);
+    }
 };
 
 template <>
@@ -84,7 +132,15 @@ struct Ieee<float> {
         return x < 0.25f ? series : direct;
     }
     __device__ __forceinline__ static float qdiv(float a, float b) { return __fdividef(a, b); }
+    // Eq. 1 for a segment of optical depth dtau = kap ds, kap > 0 (see the FP64 form)
+    __device__ __forceinline__ static void rate(float P, float G, float kap, float, float dtau, float& a, float& gseg)
+    {
+        a = P * absorb(dtau);
+        gseg = qdiv(a * G, kap);
+    }
     __device__ __forceinline__ static bool neg(float x) { return __float_as_int(x) < 0; }
+    __device__ __forceinline__ static bool lt(float a, float b) { return a < b; }
+    __device__ __forceinline__ static bool pos(float a) { return a > 0.f; }
     __device__ __forceinline__ static float mag(float x) { return fabsf(x); }
 };
 
@@ -326,7 +382,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             // dtau^2 / 24 against the difference's cancellation, equal near the switch)
             const R t0 = I::sub(tau, ctau);
             R phi0, psi0, phi1, psi1;
-            if (kap > (R)0) {
+            if (I::pos(kap)) {
                 if (dtau >= (sizeof(R) == 4 ? (R)1e-2 : (R)1e-6)) {
                     spec_eval<R>(V.spec, t0, phi0, psi0);
                     spec_eval<R>(V.spec, t0 + dtau, phi1, psi1);
@@ -341,9 +397,8 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
                 a = (R)0;
                 gseg = ((P * psi0) * G) * ds;
             }
-        } else if (kap > (R)0) {
-            a = P * I::absorb(dtau);
-            gseg = I::qdiv(a * G, kap);
+        } else if (I::pos(kap)) {
+            I::rate(P, G, kap, ds, dtau, a, gseg);
         } else {
             a = (R)0;
             gseg = (P * G) * ds;
@@ -361,8 +416,8 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
                 // naive threshold: the Eq. 5 share applies whatever the neighbour
                 if (V.overlap_mode == RT_OVERLAP_NAIVE) f = I::add((R)0.5, I::qdiv(De, Lpix));
                 const R kn = I::mag(kn_raw);
-                const bool elig = c2 >= 0 && ((V.overlap_mode == RT_OVERLAP_ARC) ? (kn > (R)0)
-                                                                                  : (!I::neg(kn_raw) && kn > (R)0));
+                const bool elig = c2 >= 0 && ((V.overlap_mode == RT_OVERLAP_ARC) ? (I::pos(kn))
+                                                                                  : (!I::neg(kn_raw) && I::pos(kn)));
                 if (elig) {
                     f = I::add((R)0.5, I::qdiv(De, Lpix));
                     g2 = (((R)1 - f) * gseg) * I::qdiv(kap, kn);
@@ -429,7 +484,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
                 periodic || ((unsigned)ni0 < (unsigned)n && (unsigned)ni1 < (unsigned)n && (unsigned)ni2 < (unsigned)n);
             const R knext = next_in ? V.kap[(ni2 * n + ni1) * n + ni0] : (R)0;
             segment(kcur, ds_p, dn0, dn1, dn2, I::mul(I::small(2u * kw + 1u), hw));
-            if (tau >= taumax) {             // photons spent
+            if (!I::lt(tau, taumax)) {             // photons spent
                 ++T.dtau;
                 T.dropph += ph * (remaining());
                 T.abs += ph * (B0 - (remaining()));
@@ -487,7 +542,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
             const R e2 = I::mul(I::of((long long)(2 * ke2 + 1) * kB - rq_end * (long long)D2), pE);
             segment(kcur, ds_p, e0, e1, e2,
                     split_end ? I::mul((R)V.rq, I::pow2(l - F)) : I::mul(I::of(rq_end), I::pow2(-F)));
-            if (tau >= taumax) {
+            if (!I::lt(tau, taumax)) {
                 ++T.dtau;
                 T.dropph += ph * (remaining());
                 T.abs += ph * (B0 - (remaining()));
@@ -804,6 +859,12 @@ __device__ __forceinline__ void append_split(bool split, uint32_t si, uint32_t p
 
 constexpr unsigned kFBase = 0x3efffff0u;     // float bits of 0.5 - 2^-21
 
+// FP64 entries (16 bytes, same row offsets): x = the bits of the FP64 ds (rounded as in the FP64
+// march_ray); y = bits 0-52: the FP64 share f of a near segment as its bit pattern less that of
+// 0.5, plus 1 (f in [0.5, 1]: 1 .. 2^52 + 1), 0 otherwise; bits 56-63: the flags of bits 24-31 of
+// the FP32 entry (steps, near, face axis and side, last), decided in FP64.
+constexpr unsigned long long kDBase = 0x3fdfffffffffffffull;    // double bits of 0.5, less 1
+
 // Walk pixel p of level l from a source at the centre of a virtual grid. Without periodic
 // boundaries it has 2 n_cover - 1 cells: a cell offset of n_cover or more along any axis lies
 // outside every n_cover^3 grid for every source cell, so that is where the table of the pixel may
@@ -814,7 +875,8 @@ __device__ __forceinline__ int geom_virtual_grid(const int n_cover, const long l
     return rs ? 2 * ((int)(rs >> F) + 3) + 1 : 2 * n_cover - 1;
 }
 
-__device__ __forceinline__ void geom_walk_init(Walk<float>& W, const long long rq, const int l, const int4 dv,
+template <class R>
+__device__ __forceinline__ void geom_walk_init(Walk<R>& W, const long long rq, const int l, const int4 dv,
                                                const int nv, const long long rs)
 {
     const int c = (nv - 1) / 2;
@@ -867,14 +929,81 @@ __global__ void __launch_bounds__(256) geom_fill_kernel(const long long rq, cons
     });
 }
 
-// march_ray with the geometry read from the level's table (FP32 physics).
-template <bool kHash>
-__device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const GeomLevel& GL, unsigned* err, const int l,
-                                                const uint32_t si, const uint32_t pix, float P, float tau, float cP,
-                                                float ctau, const SrcEntry& se, const int4 dv, Tally& T, float& oP,
-                                                float& otau, float& ocP, float& octau)
+__global__ void __launch_bounds__(256) geom_fill64_kernel(const long long rq, const int l, const int4* __restrict__ dirs,
+                                                          const long long npix, const int n_cover, const long long rs,
+                                                          const unsigned long long* __restrict__ row0,
+                                                          const unsigned long long rows_total,
+                                                          ulonglong2* __restrict__ ent, unsigned* err)
 {
-    using I = Ieee<float>;
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    Walk<double> W;
+    const int nv = geom_virtual_grid(n_cover, rs);
+    geom_walk_init(W, rq, l, dirs[p], nv, rs);
+    if (!W.inside(nv)) return;
+    const long long b = p >> 5, nb = (npix + 31) >> 5;
+    const unsigned long long rows = (b + 1 < nb ? row0[b + 1] : rows_total) - row0[b];
+    ulonglong2* col = ent + row0[b] * 32 + (p & 31);
+    unsigned long long s = 0;
+    W.run(nv, rq, l, rs, [&](const SegGeo<double>& g) -> bool {
+        if (s >= rows) {                 // the rows were counted by the same integer traversal
+            atomicOr(err, kErrGeometry);
+            return false;
+        }
+        const Edge<double> e = edge<double>(W, g, true);
+        unsigned long long y = (unsigned long long)g.steps << 56;
+        if (e.near) {
+            const double f = __dadd_rn(0.5, e.De / e.Lpix);
+            const unsigned long long code = (unsigned long long)__double_as_longlong(f) - kDBase;
+            if (code == 0ull || code > (1ull << 52) + 1ull) atomicOr(err, kErrGeometry);
+            y |= (code & ((1ull << 53) - 1ull)) | (1ull << 59) | ((unsigned long long)e.ax << 60) |
+                 (e.step > 0 ? (1ull << 62) : 0ull);
+        }
+        if (g.steps == 0u || !g.next_in) y |= 1ull << 63;
+        col[s * 32] = make_ulonglong2((unsigned long long)__double_as_longlong(__dmul_rn(g.ds_p, W.nrm)), y);
+        ++s;
+        return true;
+    });
+}
+
+// Table entry access by precision: the entry type, its FP32/FP64 segment length, the flag word
+// (steps in bits 24-26, near 27, face axis 28-29, upper face 30, last 31) and the share f.
+template <class R>
+struct TableEntry;
+
+template <>
+struct TableEntry<float> {
+    using E = uint2;
+    __device__ __forceinline__ static const E* ent(const GeomLevel& G) { return G.ent; }
+    __device__ __forceinline__ static E none() { return make_uint2(0u, 0u); }
+    __device__ __forceinline__ static float ds(const E& e) { return __uint_as_float(e.x); }
+    __device__ __forceinline__ static unsigned flags(const E& e) { return e.y; }
+    __device__ __forceinline__ static float f(const E& e) { return __uint_as_float((e.y & 0xffffffu) + kFBase); }
+};
+
+template <>
+struct TableEntry<double> {
+    using E = ulonglong2;
+    __device__ __forceinline__ static const E* ent(const GeomLevel& G) { return G.ent64; }
+    __device__ __forceinline__ static E none() { return make_ulonglong2(0ull, 0ull); }
+    __device__ __forceinline__ static double ds(const E& e) { return __longlong_as_double((long long)e.x); }
+    __device__ __forceinline__ static unsigned flags(const E& e) { return (unsigned)(e.y >> 32); }
+    __device__ __forceinline__ static double f(const E& e)
+    {
+        return __longlong_as_double((long long)((e.y & ((1ull << 53) - 1ull)) + kDBase));
+    }
+};
+
+// march_ray with the geometry read from the level's table (FP32 or FP64 physics).
+template <class R, bool kHash>
+__device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const GeomLevel& GL, unsigned* err, const int l,
+                                                const uint32_t si, const uint32_t pix, R P, R tau, R cP, R ctau,
+                                                const SrcEntry& se, const int4 dv, Tally& T, R& oP, R& otau,
+                                                float& ocP, float& octau)
+{
+    using I = Ieee<R>;
+    using TE = TableEntry<R>;
+    using E = typename TE::E;
     const int n = V.n;
     const int s0 = dv.x < 0 ? -1 : 1, s1 = dv.y < 0 ? -1 : 1, s2 = dv.z < 0 ? -1 : 1;
     int i0 = se.cx, i1 = se.cy, i2 = se.cz;
@@ -893,9 +1022,10 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
         i1 = wrapn(i1, n);
         i2 = wrapn(i2, n);
     }
-    const float G = se.gf;
+    R G;
+    if constexpr (sizeof(R) == 4) G = se.gf; else G = se.gd;
     const double ph = se.ph;
-    const float taumax = V.tau_max;
+    const R taumax = V.tau_max;
     const unsigned long long rbase =
         (kHash && V.hash) ? mix64(((unsigned long long)(si - V.src_off) << 36) | ((unsigned long long)l << 31) | pix) : 0ULL;
     const bool face = V.overlap_mode == RT_OVERLAP_ARC || V.overlap_mode == RT_OVERLAP_CONSERVATIVE ||
@@ -909,17 +1039,18 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
         T.escph += ph * (widen(P) - widen(cP));
         return false;
     }
-    const uint2* col = GL.ent + GL.row0[pix >> 5] * 32 + (pix & 31);
-    uint2 e = col[0];
+    const E* col = TE::ent(GL) + GL.row0[pix >> 5] * 32 + (pix & 31);
+    E e = col[0];
     int cell = (i2 * n + i1) * n + i0;
-    float kcur = V.kap[cell];
+    R kcur = V.kap[cell];
     unsigned seq = 0;
     bool split = false;
     for (;;) {
         // the next entry and the next cell's kappa are requested before this segment's work
-        const bool last = (e.y >> 31) != 0u;
-        const uint2 en = last ? make_uint2(0u, 0u) : col[(unsigned long long)(seq + 1) * 32];
-        const unsigned steps = (e.y >> 24) & 7u;
+        const unsigned fl = TE::flags(e);
+        const bool last = (fl >> 31) != 0u;
+        const E en = last ? TE::none() : col[(unsigned long long)(seq + 1) * 32];
+        const unsigned steps = (fl >> 24) & 7u;
         int ni0 = (steps & 1u) ? i0 + s0 : i0;
         int ni1 = (steps & 2u) ? i1 + s1 : i1;
         int ni2 = (steps & 4u) ? i2 + s2 : i2;
@@ -931,12 +1062,12 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
         const bool next_in =
             periodic || ((unsigned)ni0 < (unsigned)n && (unsigned)ni1 < (unsigned)n && (unsigned)ni2 < (unsigned)n);
         const int ncell = (ni2 * n + ni1) * n + ni0;
-        const float knext = (steps && next_in) ? V.kap[ncell] : 0.f;
-        const bool near = corr && ((e.y >> 27) & 1u);
+        const R knext = (steps && next_in) ? V.kap[ncell] : (R)0;
+        const bool near = corr && ((fl >> 27) & 1u);
         int c2 = -1;
         if (face && near) {
-            const int ax = (int)((e.y >> 28) & 3u);
-            const int step = ((e.y >> 30) & 1u) ? 1 : -1;
+            const int ax = (int)((fl >> 28) & 3u);
+            const int step = ((fl >> 30) & 1u) ? 1 : -1;
             const int jc = pick3(ax, i0, i1, i2) + step;
             if (periodic) {
                 const int jw = wrap1(jc, n);
@@ -945,36 +1076,35 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
                 c2 = cell + step * (ax == 0 ? 1 : (ax == 1 ? n : (int)nn));
             }
         }
-        const float kn_raw = c2 >= 0 ? V.kap[c2] : 0.f;
+        const R kn_raw = c2 >= 0 ? V.kap[c2] : (R)0;
         // ---- Eq. 1 for this segment
-        const float ds = __uint_as_float(e.x);
-        const float kap = I::mag(kcur);
-        const float dtau = I::mul(kap, ds);
-        float a, gseg;
-        if (kap > 0.f) {
-            a = P * I::absorb(dtau);
-            gseg = I::qdiv(a * G, kap);
+        const R ds = TE::ds(e);
+        const R kap = I::mag(kcur);
+        const R dtau = I::mul(kap, ds);
+        R a, gseg;
+        if (I::pos(kap)) {
+            I::rate(P, G, kap, ds, dtau, a, gseg);
         } else {
-            a = 0.f;
+            a = (R)0;
             gseg = (P * G) * ds;
         }
         // ---- Eqs. 5-8
-        float f = 1.f, g2 = 0.f;
+        R f = (R)1, g2 = (R)0;
         int nbcell = -1;
         if (near) {
-            const float fn = __uint_as_float((e.y & 0xffffffu) + kFBase);
+            const R fn = TE::f(e);
             if (V.overlap_mode == RT_OVERLAP_LINEAR) {
                 f = fn;
             } else if (V.overlap_mode == RT_OVERLAP_SQUARED) {
                 f = fn * fn;
             } else {
                 if (V.overlap_mode == RT_OVERLAP_NAIVE) f = fn;   // the Eq. 5 share whatever the neighbour
-                const float kn = I::mag(kn_raw);
+                const R kn = I::mag(kn_raw);
                 const bool elig =
-                    c2 >= 0 && ((V.overlap_mode == RT_OVERLAP_ARC) ? (kn > 0.f) : (!I::neg(kn_raw) && kn > 0.f));
+                    c2 >= 0 && ((V.overlap_mode == RT_OVERLAP_ARC) ? (I::pos(kn)) : (!I::neg(kn_raw) && I::pos(kn)));
                 if (elig) {
                     f = fn;
-                    g2 = ((1.f - f) * gseg) * I::qdiv(kap, kn);
+                    g2 = (((R)1 - f) * gseg) * I::qdiv(kap, kn);
                     nbcell = c2;
                 }
             }
@@ -988,7 +1118,7 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
         budget_add(P, cP, -a);
         if (kHash && V.hash) T.hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
         ++seq;
-        if (tau >= taumax) {             // photons spent
+        if (!I::lt(tau, taumax)) {             // photons spent
             ++T.dtau;
             T.dropph += ph * (widen(P) - widen(cP));
             break;
@@ -1005,8 +1135,8 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<float>& V, const
                 split = true;
                 oP = P;
                 otau = tau;
-                ocP = cP;
-                octau = ctau;
+                ocP = (float)cP;         // compensations: FP32 march only (0 in FP64)
+                octau = (float)ctau;
             }
             break;
         }
@@ -1153,16 +1283,21 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
     flush_tally(T, 0xffffffffu, &st, l);
 }
 
-// One level (or one slice of it) of one solve, FP32, geometry from the level's table. Without
-// the walk it fits 64 registers, so four blocks (32 warps) per SM.
-template <bool kHash>
-__global__ void __launch_bounds__(256, 4) march_table_kernel(const MarchArgs<float> A, const GeomLevel GL)
+// One level (or one slice of it) of one solve, geometry from the level's table. Without the walk
+// the FP32 march fits 64 registers, so four blocks (32 warps) per SM; the FP64 one takes three.
+template <class R>
+struct TableOccupancy {
+    static constexpr int blocks = sizeof(R) == 4 ? 4 : 2;
+};
+
+template <class R, bool kHash>
+__global__ void __launch_bounds__(256, TableOccupancy<R>::blocks) march_table_kernel(const MarchArgs<R> A, const GeomLevel GL)
 {
     const int l = A.level;
     const int lane = threadIdx.x & 31;
     const long long gwarp = (long long)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarp = (long long)(gridDim.x * blockDim.x) >> 5;
-    SolveView<float> V;
+    SolveView<R> V;
     V.kap = A.kap;
     V.gamma = A.gamma;
     V.n = A.n;
@@ -1179,14 +1314,15 @@ __global__ void __launch_bounds__(256, 4) march_table_kernel(const MarchArgs<flo
         const long long j = base + lane;
         bool split = false;
         uint32_t si = 0, pix = 0;
-        float oP = 0.f, otau = 0.f, ocP = 0.f, octau = 0.f;
+        R oP = 0, otau = 0;
+        float ocP = 0.f, octau = 0.f;
         if (j < A.c1) {
-            float P, tau, cP, ctau;
-            load_ray<float>(l, j, A.in, si, pix, P, tau, cP, ctau);
-            split = march_ray_table<kHash>(V, GL, &A.st->err, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T,
+            R P, tau, cP, ctau;
+            load_ray<R>(l, j, A.in, si, pix, P, tau, cP, ctau);
+            split = march_ray_table<R, kHash>(V, GL, &A.st->err, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T,
                                            oP, otau, ocP, octau);
         }
-        append_split<float>(split, si, pix, oP, otau, ocP, octau, A.out, A.out_count, &A.st->err);
+        append_split<R>(split, si, pix, oP, otau, ocP, octau, A.out, A.out_count, &A.st->err);
     }
     DevStats* st = A.st;
     flush_tally(T, 0xffffffffu, &st, l);
@@ -1273,7 +1409,7 @@ __global__ void __launch_bounds__(256, (kTable && kSingle) ? 4 : MarchOccupancy<
                     V.src_off = bs.src_off - A.src_base;
                     if constexpr (kTable) {
                         static_assert(sizeof(R) == 4, "geometry tables serve the FP32 march");
-                        split = march_ray_table<kHash>(V, A.geo[l], A.err, l, si, pix, P, tau, cP, ctau, se, dirs[pix],
+                        split = march_ray_table<float, kHash>(V, A.geo[l], A.err, l, si, pix, P, tau, cP, ctau, se, dirs[pix],
                                                        T, oP, otau, ocP, octau);
                     } else {
                         split = march_ray<R, kHash, false>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau, ocP,
@@ -1325,8 +1461,15 @@ int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_
 
 int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int grid, int block, cudaStream_t s)
 {
-    if (a.hash) march_table_kernel<true><<<grid, block, 0, s>>>(a, g);
-    else march_table_kernel<false><<<grid, block, 0, s>>>(a, g);
+    if (a.hash) march_table_kernel<float, true><<<grid, block, 0, s>>>(a, g);
+    else march_table_kernel<float, false><<<grid, block, 0, s>>>(a, g);
+    return 1;
+}
+
+int launch_march_table_f64(const MarchArgs<double>& a, const GeomLevel& g, int grid, int block, cudaStream_t s)
+{
+    if (a.hash) march_table_kernel<double, true><<<grid, block, 0, s>>>(a, g);
+    else march_table_kernel<double, false><<<grid, block, 0, s>>>(a, g);
     return 1;
 }
 
@@ -1342,6 +1485,14 @@ void launch_geom_fill(long long rq, int l, const int4* dirs, long long npix, int
 {
     const long long grid = (npix + 255) / 256;
     geom_fill_kernel<<<(unsigned)grid, 256, 0, s>>>(rq, l, dirs, npix, n_cover, rs, row0, ent, err);
+}
+
+void launch_geom_fill64(long long rq, int l, const int4* dirs, long long npix, int n_cover, long long rs,
+                        const unsigned long long* row0, unsigned long long rows_total, ulonglong2* ent,
+                        unsigned* err, cudaStream_t s)
+{
+    const long long grid = (npix + 255) / 256;
+    geom_fill64_kernel<<<(unsigned)grid, 256, 0, s>>>(rq, l, dirs, npix, n_cover, rs, row0, rows_total, ent, err);
 }
 
 template <class R, bool kSingle>

@@ -95,11 +95,14 @@ struct GeomTable {
     int level;
     int n_cover;
     bool complete;            // no pixel cut short: serves every grid size
-    bool usable;
-    nyx::GeomLevel g;
+    unsigned long long total; // rows (of 32 entries)
+    unsigned long long* row0; // row offset of each 32-pixel block (device)
+    uint2* ent;               // FP32 entries, built on first use
+    ulonglong2* ent64;        // FP64 entries, built on first use
+    bool failed32, failed64;  // that build was tried and did not fit (or failed)
 };
 std::mutex g_geom_mu;
-std::map<int, std::vector<GeomTable>> g_geom;
+std::map<int, std::vector<GeomTable>> g_geom;   // never shrinks; entries are updated in place
 std::map<int, size_t> g_geom_bytes;
 
 size_t geometry_budget(int device)
@@ -120,70 +123,92 @@ size_t geometry_budget(int device)
 }  // namespace
 
 bool nyx::geometry_level(int device, long long rq, int level, int n, long long rs, const int4* dirs_level,
-                         cudaStream_t s, GeomLevel* out)
+                         cudaStream_t s, bool fp64, GeomLevel* out)
 {
     std::lock_guard<std::mutex> lk(g_geom_mu);
     std::vector<GeomTable>& list = g_geom[device];
-    for (const GeomTable& t : list)
-        if (t.rq == rq && t.rs == rs && t.level == level && (t.complete || t.n_cover >= n)) {
-            if (t.usable) *out = t.g;
-            return t.usable;
+    GeomTable* t = nullptr;
+    for (GeomTable& c : list)
+        if (c.rq == rq && c.rs == rs && c.level == level && (c.complete || c.n_cover >= n)) {
+            t = &c;
+            break;
         }
-    GeomTable t{rq, rs, level, n, false, false, GeomLevel()};
-    // every ray reaches R_l inside the virtual grid of 2n - 1 cells when R_l + 1 < n; with periodic
-    // boundaries the table runs to the travel-distance cutoff, fixed by rs alone
-    t.complete = rs != 0 || std::ldexp((double)rq, level - kRadBits) + 2.0 < (double)n;
     const long long npix = 12LL << (2 * level);
     const long long nb = (npix + 31) / 32;
-    unsigned* d_rows = nullptr;
-    unsigned* d_err = nullptr;
-    uint2* ent = nullptr;
-    unsigned long long* row0 = nullptr;
-    std::vector<unsigned> rows((size_t)nb);
-    std::vector<unsigned long long> off((size_t)nb);
-    unsigned herr = 0;
-    bool ok = cudaMalloc(&d_rows, sizeof(unsigned) * (size_t)nb) == cudaSuccess &&
-              cudaMalloc(&d_err, sizeof(unsigned)) == cudaSuccess;
-    if (ok) {
-        launch_geom_count(rq, level, dirs_level, npix, n, rs, d_rows, s);
-        ok = cudaMemcpyAsync(rows.data(), d_rows, sizeof(unsigned) * (size_t)nb, cudaMemcpyDeviceToHost, s) ==
-                 cudaSuccess &&
+    if (!t) {
+        // the rows of every 32-pixel block: counted once, shared by both precisions' entries
+        GeomTable c{rq, rs, level, n, false, 0ull, nullptr, nullptr, nullptr, false, false};
+        // every ray reaches R_l inside the virtual grid of 2n - 1 cells when R_l + 1 < n; with periodic
+        // boundaries the table runs to the travel-distance cutoff, fixed by rs alone
+        c.complete = rs != 0 || std::ldexp((double)rq, level - kRadBits) + 2.0 < (double)n;
+        unsigned* d_rows = nullptr;
+        std::vector<unsigned> rows((size_t)nb);
+        std::vector<unsigned long long> off((size_t)nb);
+        const size_t row0_bytes = sizeof(unsigned long long) * (size_t)nb;
+        bool ok = g_geom_bytes[device] + row0_bytes <= geometry_budget(device) &&
+                  cudaMalloc(&d_rows, sizeof(unsigned) * (size_t)nb) == cudaSuccess;
+        if (ok) {
+            launch_geom_count(rq, level, dirs_level, npix, n, rs, d_rows, s);
+            ok = cudaMemcpyAsync(rows.data(), d_rows, sizeof(unsigned) * (size_t)nb, cudaMemcpyDeviceToHost, s) ==
+                     cudaSuccess &&
+                 cudaStreamSynchronize(s) == cudaSuccess;
+        }
+        for (long long b = 0; ok && b < nb; ++b) {
+            off[(size_t)b] = c.total;
+            c.total += rows[(size_t)b];
+        }
+        ok = ok && cudaMalloc(&c.row0, row0_bytes) == cudaSuccess &&
+             cudaMemcpyAsync(c.row0, off.data(), row0_bytes, cudaMemcpyHostToDevice, s) == cudaSuccess &&
              cudaStreamSynchronize(s) == cudaSuccess;
+        cudaGetLastError();
+        cudaFree(d_rows);
+        if (ok) {
+            g_geom_bytes[device] += row0_bytes;
+        } else {
+            cudaFree(c.row0);
+            c.row0 = nullptr;
+            c.failed32 = c.failed64 = true;
+        }
+        list.push_back(c);
+        t = &list.back();
     }
-    unsigned long long total = 0;
-    for (long long b = 0; ok && b < nb; ++b) {
-        off[(size_t)b] = total;
-        total += rows[(size_t)b];
+    bool& failed = fp64 ? t->failed64 : t->failed32;
+    const bool have = fp64 ? t->ent64 != nullptr : t->ent != nullptr;
+    if (!have && !failed) {
+        const size_t esz = fp64 ? sizeof(ulonglong2) : sizeof(uint2);
+        const size_t bytes = (size_t)t->total * 32 * esz;
+        void* ent = nullptr;
+        unsigned* d_err = nullptr;
+        unsigned herr = 0;
+        bool ok = g_geom_bytes[device] + bytes <= geometry_budget(device) &&
+                  cudaMalloc(&ent, std::max<size_t>(16, bytes)) == cudaSuccess &&
+                  cudaMalloc(&d_err, sizeof(unsigned)) == cudaSuccess &&
+                  cudaMemsetAsync(d_err, 0, sizeof(unsigned), s) == cudaSuccess;
+        if (ok) {
+            if (fp64)
+                launch_geom_fill64(rq, level, dirs_level, npix, t->n_cover, rs, t->row0, t->total,
+                                   static_cast<ulonglong2*>(ent), d_err, s);
+            else
+                launch_geom_fill(rq, level, dirs_level, npix, t->n_cover, rs, t->row0, static_cast<uint2*>(ent), d_err, s);
+            ok = cudaMemcpyAsync(&herr, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                 cudaStreamSynchronize(s) == cudaSuccess && herr == 0;
+        }
+        cudaGetLastError();
+        cudaFree(d_err);
+        if (ok) {
+            if (fp64) t->ent64 = static_cast<ulonglong2*>(ent);
+            else t->ent = static_cast<uint2*>(ent);
+            g_geom_bytes[device] += bytes;
+        } else {
+            cudaFree(ent);
+            failed = true;
+        }
     }
-    const size_t bytes = (size_t)total * 32 * sizeof(uint2) + sizeof(unsigned long long) * (size_t)nb;
-    ok = ok && g_geom_bytes[device] + bytes <= geometry_budget(device);
-    if (ok) {
-        ok = cudaMalloc(&ent, std::max<size_t>(16, (size_t)total * 32 * sizeof(uint2))) == cudaSuccess &&
-             cudaMalloc(&row0, sizeof(unsigned long long) * (size_t)nb) == cudaSuccess &&
-             cudaMemcpyAsync(row0, off.data(), sizeof(unsigned long long) * (size_t)nb, cudaMemcpyHostToDevice, s) ==
-                 cudaSuccess &&
-             cudaMemsetAsync(d_err, 0, sizeof(unsigned), s) == cudaSuccess;
-    }
-    if (ok) {
-        launch_geom_fill(rq, level, dirs_level, npix, n, rs, row0, ent, d_err, s);
-        ok = cudaMemcpyAsync(&herr, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-             cudaStreamSynchronize(s) == cudaSuccess && herr == 0;
-    }
-    cudaGetLastError();
-    cudaFree(d_rows);
-    cudaFree(d_err);
-    if (ok) {
-        t.usable = true;
-        t.g.ent = ent;
-        t.g.row0 = row0;
-        g_geom_bytes[device] += bytes;
-        *out = t.g;
-    } else {
-        cudaFree(ent);
-        cudaFree(row0);
-    }
-    list.push_back(t);
-    return t.usable;
+    if (fp64 ? t->ent64 == nullptr : t->ent == nullptr) return false;
+    out->ent = t->ent;
+    out->ent64 = t->ent64;
+    out->row0 = t->row0;
+    return true;
 }
 
 namespace {
@@ -433,14 +458,15 @@ int run_level(rt_handle* h, int level, int64_t nparents)
         const int64_t warps = (c1 - c0 + 31) / 32;
         const int64_t want = (warps + kMarchBlock / 32 - 1) / (kMarchBlock / 32);
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->sm_count * 8));
-        // FP32: the level's geometry table (built once per device, outside the timed launch)
+        // the level's geometry table for this precision (built once per device, outside the timed launch)
         GeomLevel gl;
-        const bool table = sizeof(R) == 4 && !(h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE) &&
-                           h->cfg.spectrum == RT_SPECTRUM_GRAY &&
-                           geometry_level(h->device, h->rq, level, h->cfg.n, h->rs, a.dirs, h->stream, &gl);
+        const bool table = !(h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE) && h->cfg.spectrum == RT_SPECTRUM_GRAY &&
+                           geometry_level(h->device, h->rq, level, h->cfg.n, h->rs, a.dirs, h->stream, sizeof(R) == 8,
+                                          &gl);
         RT_CUDA(h, cudaEventRecord(h->ev[4], h->stream), "event");
         if constexpr (sizeof(R) == 8) {
-            launch_march_f64(a, grid, kMarchBlock, h->stream);
+            if (table) launch_march_table_f64(a, gl, grid, kMarchBlock, h->stream);
+            else launch_march_f64(a, grid, kMarchBlock, h->stream);
         } else {
             if (table) launch_march_table_f32(a, gl, grid, kMarchBlock, h->stream);
             else launch_march_f32(a, grid, kMarchBlock, h->stream);

@@ -127,10 +127,11 @@ int fail(rt_handle* h, int code, const std::string& msg);
 int cuda_fail(rt_handle* h, cudaError_t e, const char* what);
 int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out);
 int ensure_directions(int device, int level, const int4** out, std::string& err);
-// The geometry table of a level for grids of n cells (FP32 march), built on stream s if needed;
-// false if the level has none (over the device's table budget), so its rays are walked.
+// The geometry table of a level for grids of n cells, with the entries of the FP32 march (fp64
+// false) or the FP64 one, built on stream s if needed; false if the level has none for that
+// precision (over the device's table budget), so its rays are walked.
 bool geometry_level(int device, long long rq, int level, int n, long long rs, const int4* dirs_level,
-                    cudaStream_t s, GeomLevel* out);
+                    cudaStream_t s, bool fp64, GeomLevel* out);
 // The RT_SPECTRUM_BLACKBODY tables at t_bb for `device` (device < 0: host table only).
 int spectrum_table(int device, double t_bb, SpecTable<double>* d, SpecTable<float>* f, std::string& why);
 int handle_prepare_sources(rt_handle* h);

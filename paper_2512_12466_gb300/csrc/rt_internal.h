@@ -95,7 +95,8 @@ struct MarchArgs {
 // Geometry table of one level (FP32 march): 8-byte entries, entry s of pixel p at
 // ent[(row0[p / 32] + s) * 32 + p % 32].
 struct GeomLevel {
-    const uint2* ent = nullptr;
+    const uint2* ent = nullptr;              // FP32 march: 8-byte entries
+    const ulonglong2* ent64 = nullptr;       // FP64 march: 16-byte entries at the same row offsets
     const unsigned long long* row0 = nullptr;
 };
 
@@ -143,8 +144,9 @@ int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_
 cudaError_t launch_batch_f64(const BatchArgs<double>& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_batch_f32(const BatchArgs<float>& a, int grid, int block, cudaStream_t s);
 int batch_blocks_per_sm(int precision, int block, bool table, bool single);
-// The FP32 march of one level with its geometry from a table.
+// The march of one level with its geometry from a table (FP32: g.ent; FP64: g.ent64).
 int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int grid, int block, cudaStream_t s);
+int launch_march_table_f64(const MarchArgs<double>& a, const GeomLevel& g, int grid, int block, cudaStream_t s);
 // Geometry-table generation for level l of directions dirs (npix pixels), for grids up to
 // n_cover: rows[b] = rows of 32-pixel block b; then the entries at row offsets row0.
 // rs: travel-distance cutoff of periodic boundaries (0: none).
@@ -152,6 +154,10 @@ void launch_geom_count(long long rq, int l, const int4* dirs, long long npix, in
                        unsigned* rows, cudaStream_t s);
 void launch_geom_fill(long long rq, int l, const int4* dirs, long long npix, int n_cover, long long rs,
                       const unsigned long long* row0, uint2* ent, unsigned* err, cudaStream_t s);
+// The FP64 entries of the same level at the same row offsets (total rows: rows_total).
+void launch_geom_fill64(long long rq, int l, const int4* dirs, long long npix, int n_cover, long long rs,
+                        const unsigned long long* row0, unsigned long long rows_total, ulonglong2* ent,
+                        unsigned* err, cudaStream_t s);
 
 // fields.cu
 int launch_validate_fields(const double* nh, const double* x, int64_t ncell, DevStats* st, cudaStream_t s);
