@@ -638,9 +638,10 @@ def run_nyx(args, world, rank, local):
                 "steps": e2e_steps},
         "clocks": f32["clocks"],
     }
-    line["overlap_modes"] = bench_overlap_modes(nyx, torch, w, n_th)
-    line["spectrum"] = bench_spectrum(nyx, torch, w, n_th)
-    line["config4"] = bench_config4(nyx, torch)
+    if not args.no_variants:
+        line["overlap_modes"] = bench_overlap_modes(nyx, torch, w, n_th)
+        line["spectrum"] = bench_spectrum(nyx, torch, w, n_th)
+        line["config4"] = bench_config4(nyx, torch)
     if not args.no_batched:
         line["batched"] = {"neutral": bench_batched(nyx, torch, "neutral", steps=5, tune=True),
                            "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 25)}
@@ -660,6 +661,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="nyx", choices=["nyx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the untimed side measurements (overlap modes, spectrum, 256^3 box)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args(argv)
     world, rank, local = dist_setup()

@@ -265,13 +265,17 @@ extern "C" int rt_step_noalloc(const rt_config* cfg, void* cuda_stream, const do
     w.cells_raw = reinterpret_cast<int32_t*>(const_cast<int32_t*>(cell_ijk));
     w.ndot_raw = const_cast<double*>(ndot);
     w.keys = reinterpret_cast<uint64_t*>(take(8 * kNaMaxSources));
+    w.keys_b = reinterpret_cast<uint64_t*>(take(8 * kNaMaxSources));
+    w.keys_c = reinterpret_cast<uint64_t*>(take(8 * kNaMaxSources));
     w.order = reinterpret_cast<int32_t*>(take(4 * kNaMaxSources));
+    w.order_b = reinterpret_cast<int32_t*>(take(4 * kNaMaxSources));
     w.flag = reinterpret_cast<int32_t*>(take(4 * kNaMaxSources));
     w.head_pos = reinterpret_cast<int32_t*>(take(4 * kNaMaxSources));
     w.cells_a = reinterpret_cast<int32_t*>(take(12 * kNaMaxSources));
     w.ndot_a = reinterpret_cast<double*>(take(8 * kNaMaxSources));
     w.count = reinterpret_cast<int32_t*>(take(16));
     w.cap = kNaMaxSources;
+    if (p > base + kOffEmit) return set_error(RT_EINVAL, "rt_step_noalloc: source workspace layout overflow");
     SrcEntry* emit = reinterpret_cast<SrcEntry*>(base + kOffEmit);
 
     auto cu = [&](cudaError_t e, const char* what) {
@@ -285,7 +289,7 @@ extern "C" int rt_step_noalloc(const rt_config* cfg, void* cuda_stream, const do
     if ((rc = cu(cudaMemsetAsync(c.st, 0, sizeof(DevStats), s), "rt_step_noalloc: statistics clear failed"))) return rc;
     c.launches += launch_validate_fields(n_H, x_ion, ncell, c.st, s);
     c.launches += launch_validate_sources(cell_ijk, ndot, nsrc, n, c.st, s);
-    c.launches += launch_dedup_sort(w, nsrc, s);
+    c.launches += launch_dedup_sort(w, nsrc, n, s);
     const bool want_mean = cfg->n_th_cm3 < 0;
     if (want_mean) {
         if ((rc = cu(cudaMemsetAsync(scalar, 0, sizeof(double), s), "rt_step_noalloc: clear failed"))) return rc;

@@ -364,7 +364,10 @@ int grow_sources(rt_handle* h, int64_t need)
     e = e ? e : alloc((void**)&nw.cells_raw, 12 * (size_t)cap);
     e = e ? e : alloc((void**)&nw.ndot_raw, 8 * (size_t)cap);
     e = e ? e : alloc((void**)&nw.keys, 8 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.keys_b, 8 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.keys_c, 8 * (size_t)cap);
     e = e ? e : alloc((void**)&nw.order, 4 * (size_t)cap);
+    e = e ? e : alloc((void**)&nw.order_b, 4 * (size_t)cap);
     e = e ? e : alloc((void**)&nw.flag, 4 * (size_t)cap);
     e = e ? e : alloc((void**)&nw.head_pos, 4 * (size_t)cap);
     e = e ? e : alloc((void**)&nw.cells_a, 12 * (size_t)cap);
@@ -378,8 +381,8 @@ int grow_sources(rt_handle* h, int64_t need)
     SrcEntry* emit = nullptr;
     e = e ? e : alloc((void**)&emit, sizeof(SrcEntry) * (size_t)cap);
     auto release = [h](SourceWork& w) {
-        void* ps[] = {w.cells_raw, w.ndot_raw, w.keys, w.order, w.flag, w.head_pos, w.cells_a, w.ndot_a,
-                      w.cells_b, w.ndot_b, w.label, w.parent, w.radius, w.count};
+        void* ps[] = {w.cells_raw, w.ndot_raw, w.keys, w.keys_b, w.keys_c, w.order, w.order_b, w.flag, w.head_pos,
+                      w.cells_a, w.ndot_a, w.cells_b, w.ndot_b, w.label, w.parent, w.radius, w.count};
         for (void* q : ps) dfree(h, q);
     };
     if (e != cudaSuccess) {
@@ -528,7 +531,7 @@ int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out)
     RT_LAUNCHED(h, "validation launch");
 
     // ---- sources: dedup + sort (Sec. 2.8)
-    h->launches += launch_dedup_sort(h->sw, h->nsrc, s);
+    h->launches += launch_dedup_sort(h->sw, h->nsrc, h->cfg.n, s);
     RT_LAUNCHED(h, "source launch");
     bool want_mean_nh = h->cfg.n_th_cm3 < 0;
     if (want_mean_nh) {
@@ -606,7 +609,7 @@ int prepare_sources_many(rt_handle* const* hs, int count, int* rcs)
         RT_CUDA(h, cudaMemsetAsync(h->d_st, 0, sizeof(DevStats), s), "stats clear");
         h->launches += launch_validate_fields(h->d_nh, h->d_x, h->ncell, h->d_st, s);
         h->launches += launch_validate_sources(h->sw.cells_raw, h->sw.ndot_raw, h->nsrc, h->cfg.n, h->d_st, s);
-        h->launches += launch_dedup_sort(h->sw, h->nsrc, s);
+        h->launches += launch_dedup_sort(h->sw, h->nsrc, h->cfg.n, s);
         if (h->cfg.n_th_cm3 < 0) {
             RT_CUDA(h, cudaMemsetAsync(h->d_scalar, 0, sizeof(double), s), "scalar clear");
             h->launches += launch_mean_nh(h->d_nh, h->ncell, h->d_scalar, s);

@@ -178,7 +178,10 @@ struct SourceWork {
     int32_t* cells_raw = nullptr;   // cap x 3, appended sources
     double* ndot_raw = nullptr;     // cap
     uint64_t* keys = nullptr;       // scratch, cap
+    uint64_t* keys_b = nullptr;     // sort scratch, cap
+    uint64_t* keys_c = nullptr;     // sort scratch, cap
     int32_t* order = nullptr;       // scratch, cap
+    int32_t* order_b = nullptr;     // sort scratch, cap
     int32_t* flag = nullptr;        // scratch, cap
     int32_t* head_pos = nullptr;    // scratch, cap
     int32_t* cells_a = nullptr;     // cap x 3: deduplicated (then merged) sorted catalog
@@ -193,8 +196,9 @@ struct SourceWork {
 };
 int launch_validate_sources(const int32_t* cells, const double* ndot, int64_t nsrc, int n, DevStats* st,
                              cudaStream_t s);
-// Dedup + lexicographic sort; writes cells_a/ndot_a and count[0] = number of unique cells.
-int launch_dedup_sort(SourceWork& w, int64_t nsrc, cudaStream_t s);
+// Dedup + lexicographic sort (cells of an n^3 grid); writes cells_a/ndot_a and count[0] = number
+// of unique cells.
+int launch_dedup_sort(SourceWork& w, int64_t nsrc, int n, cudaStream_t s);
 // Alg. 3 on cells_a/ndot_a[0..m): radii, union-find, merged catalog into cells_a/ndot_a, count[0] = size.
 int launch_merge(SourceWork& w, int64_t m, int n, int periodic, const double* x, const int4* samp_dirs,
                  int samp_count, double x_th, double f_req, int n_min, double dr, double rmax, double f_ov,

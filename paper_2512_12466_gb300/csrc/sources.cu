@@ -3,10 +3,11 @@
 // by (ix, iy, iz), and optionally sources whose ionized bubbles overlap are
 // merged (Alg. 3: MAX_RADIUS by shell sampling, union-find over overlapping
 // pairs, one source per group at the member nearest the flux-weighted
-// centroid). Catalogs are at most tens of thousands of entries, so the sorts
-// are exact O(S^2) rank computations tiled through shared memory and the
-// pair test is a dense O(S^2) sweep; every per-group sum runs sequentially
-// in member order, so the emitted catalog is deterministic.
+// centroid). Catalogs are tens of thousands of entries: the sorts are stable
+// LSD radix sorts in one block over only the key bits in use, and the pair
+// test sweeps the pairs of the sources whose bubble radius is positive (the
+// only ones that can merge); every per-group sum runs sequentially in member
+// order, so the emitted catalog is deterministic.
 #include <algorithm>
 #include <cstdint>
 
@@ -23,9 +24,18 @@ int blocks_for(int64_t count)
     return g < 1 ? 1 : (int)g;
 }
 
-__device__ __forceinline__ uint64_t cell_key(int x, int y, int z)
+// Bits per axis of a cell coordinate in [0, n).
+int axis_bits(int n)
 {
-    return ((uint64_t)x << 42) | ((uint64_t)y << 21) | (uint64_t)z;
+    int b = 0;
+    while ((1LL << b) < (long long)n) ++b;
+    return b;
+}
+
+// Lexicographic (x, y, z) key of a cell, b bits per axis.
+__device__ __forceinline__ uint64_t cell_key(int x, int y, int z, int b)
+{
+    return ((uint64_t)x << (2 * b)) | ((uint64_t)y << b) | (uint64_t)z;
 }
 
 __global__ void validate_sources_kernel(const int32_t* __restrict__ cells, const double* __restrict__ ndot,
@@ -40,33 +50,109 @@ __global__ void validate_sources_kernel(const int32_t* __restrict__ cells, const
     }
 }
 
-__global__ void cell_keys_kernel(const int32_t* __restrict__ cells, int64_t m, uint64_t* __restrict__ keys)
+__global__ void cell_keys_kernel(const int32_t* __restrict__ cells, int64_t m, int b, uint64_t* __restrict__ keys)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-        keys[i] = cell_key(cells[3 * i], cells[3 * i + 1], cells[3 * i + 2]);
+        keys[i] = cell_key(cells[3 * i], cells[3 * i + 1], cells[3 * i + 2], b);
 }
 
-// order[rank(i)] = i with rank(i) = #{j : key_j < key_i or (key_j = key_i and j < i)}: a stable sort.
-__global__ void __launch_bounds__(kBlock) rank_kernel(const uint64_t* __restrict__ keys, int64_t m,
-                                                      int32_t* __restrict__ order)
+// Stable sort of keys[0..m) by their low `bits` bits: order[p] = the index of the p-th smallest,
+// equal keys in index order (keys itself is left as it is; keys_b and keys_c, order_b: scratch).
+// One block of 1024 threads (32 warps), least significant digit first, 8 bits a pass: warp w owns
+// a contiguous chunk of the sequence; a pass counts each warp's digits, scans the counts in
+// (digit, warp) order and scatters every warp's chunk in sequence order, 32 keys a round, a lane
+// placed after the lower lanes of its round that share its digit (found with 8 ballots) - so
+// every pass is stable and the result is the stable sort.
+constexpr int kSortThreads = 1024;
+
+__global__ void __launch_bounds__(kSortThreads) radix_sort_kernel(const uint64_t* __restrict__ keys, int64_t m,
+                                                                  int bits, uint64_t* keys_b, uint64_t* keys_c,
+                                                                  int32_t* order_b, int32_t* __restrict__ order)
 {
-    __shared__ uint64_t tile[kBlock];
-    const int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x;
-    const bool valid = i < m;
-    const uint64_t ki = valid ? keys[i] : 0;
-    int64_t rank = 0;
-    for (int64_t t0 = 0; t0 < m; t0 += kBlock) {
-        const int64_t jl = t0 + threadIdx.x;
-        tile[threadIdx.x] = jl < m ? keys[jl] : ~0ULL;
+    __shared__ int32_t cnt[256 * 33];      // [digit][warp], rows padded to 33 so a warp's lanes spread over banks
+    __shared__ int32_t wsum[32];
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    const int64_t chunk = (m + 31) / 32;
+    const int64_t c0 = min(m, (int64_t)wp * chunk), c1 = min(m, c0 + chunk);
+    const int passes = (bits + 7) / 8;
+    const uint64_t* kin = keys;
+    const int32_t* iin = nullptr;                   // pass 0 reads the identity
+    uint64_t* kout = keys_b;
+    int32_t* iout = (passes & 1) ? order : order_b; // the last pass writes `order`
+    for (int pass = 0; pass < passes; ++pass) {
+        const int sh = 8 * pass;
+        for (int q = t; q < 256 * 33; q += kSortThreads) cnt[q] = 0;
         __syncthreads();
-        const int lim = (int)((m - t0) < kBlock ? (m - t0) : kBlock);
-        for (int jj = 0; jj < lim; ++jj) {
-            const uint64_t kj = tile[jj];
-            rank += (kj < ki) || (kj == ki && t0 + jj < i);
+        for (int64_t i = c0 + lane; i < c1; i += 128) {   // four independent loads in flight a lane
+            uint64_t kk[4];
+            for (int u = 0; u < 4; ++u) kk[u] = i + 32 * u < c1 ? kin[i + 32 * u] : 0ULL;
+            for (int u = 0; u < 4; ++u)
+                if (i + 32 * u < c1) atomicAdd(&cnt[((int)(kk[u] >> sh) & 255) * 33 + wp], 1);
         }
         __syncthreads();
+        // exclusive scan of the 8192 counters in (digit, warp) order: thread t owns counters
+        // [8t, 8t + 8), i.e. digit t / 4, warps 8 (t % 4) .. 8 (t % 4) + 7
+        const int sd = t >> 2, sw = 8 * (t & 3);
+        int32_t loc[8], run = 0;
+        for (int q = 0; q < 8; ++q) {
+            loc[q] = run;
+            run += cnt[sd * 33 + sw + q];
+        }
+        int32_t incl = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[wp] = incl;
+        __syncthreads();
+        if (wp == 0) {
+            int32_t v = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            wsum[lane] = v;                          // inclusive over warps
+        }
+        __syncthreads();
+        const int32_t base = (incl - run) + (wp > 0 ? wsum[wp - 1] : 0);
+        for (int q = 0; q < 8; ++q) cnt[sd * 33 + sw + q] = base + loc[q];
+        __syncthreads();
+        // scatter, each warp its chunk in order; the next round's key and index are requested
+        // before this round's are placed
+        uint64_t kn = c0 + lane < c1 ? kin[c0 + lane] : 0ULL;
+        int32_t xn = c0 + lane < c1 ? (iin ? iin[c0 + lane] : (int32_t)(c0 + lane)) : 0;
+        for (int64_t r0 = c0; r0 < c1; r0 += 32) {
+            const int64_t i = r0 + lane;
+            const bool v = i < c1;
+            const uint64_t k = kn;
+            const int32_t x = xn;
+            const int64_t inext = i + 32;
+            kn = inext < c1 ? kin[inext] : 0ULL;
+            xn = inext < c1 ? (iin ? iin[inext] : (int32_t)inext) : 0;
+            const int d = (int)(k >> sh) & 255;
+            unsigned peers = __ballot_sync(0xffffffffu, v);
+            for (int b = 0; b < 8; ++b) {
+                const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1);
+                peers &= ((d >> b) & 1) ? bb : ~bb;
+            }
+            int32_t* slot = &cnt[d * 33 + wp];
+            if (v) {
+                const int32_t dst = *slot + __popc(peers & ((1u << lane) - 1u));
+                kout[dst] = k;
+                iout[dst] = x;
+            }
+            __syncwarp();
+            if (v && (peers >> lane) == 1u) *slot += __popc(peers);   // the highest lane of its digit
+            __syncwarp();
+        }
+        __syncthreads();
+        kin = kout;
+        kout = (kout == keys_b) ? keys_c : keys_b;
+        iin = iout;
+        iout = (iout == order) ? order_b : order;
     }
-    if (valid) order[rank] = (int32_t)i;
+    if (passes == 0)
+        for (int64_t i = t; i < m; i += kSortThreads) order[i] = (int32_t)i;
 }
 
 // flag[p] = 1 where sorted entry p starts a run of equal keys.
@@ -214,59 +300,97 @@ __global__ void __launch_bounds__(kBlock) radius_kernel(const int32_t* __restric
     if (threadIdx.x == 0) radius[si] = result;
 }
 
+// Root of a in the union-find forest; parents are read past L1 (they change under concurrent hooks,
+// which are atomicCAS on roots, so a stale read only lengthens the walk or fails a CAS that retries).
 __device__ __forceinline__ int uf_find(int* parent, int a)
 {
-    int p = atomicAdd(&parent[a], 0);
+    int p = __ldcg(&parent[a]);
     while (p != a) {
         a = p;
-        p = atomicAdd(&parent[a], 0);
+        p = __ldcg(&parent[a]);
     }
     return a;
 }
 
-// Pairs (a, b > a) whose bubbles overlap (both radii > 0,
-// d^2 <= (f_ov (r_a + r_b))^2 + eps, d minimum-image when periodic) are united;
-// the larger root is hooked under the smaller, so each component's root is
-// its smallest index.
-__global__ void pair_union_kernel(const int32_t* __restrict__ cells, const double* __restrict__ radius, int64_t m,
-                                  int n, int periodic, double f_ov, double eps, int* parent, DevStats* st)
+// flag[i] = 1 where source i has a positive bubble radius (only such sources can pair).
+__global__ void positive_radius_kernel(const double* __restrict__ radius, int64_t m, int32_t* __restrict__ flag)
 {
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
-        const double ra = radius[a];
-        if (!(ra > 0.0)) continue;
-        const int ax = cells[3 * a], ay = cells[3 * a + 1], az = cells[3 * a + 2];
-        for (int64_t b = a + 1; b < m; ++b) {
-            const double rb = radius[b];
-            if (!(rb > 0.0)) continue;
-            long long dx = ax - cells[3 * b], dy = ay - cells[3 * b + 1], dz = az - cells[3 * b + 2];
-            if (periodic) {
-                dx = minimg(dx, n);
-                dy = minimg(dy, n);
-                dz = minimg(dz, n);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = radius[i] > 0.0 ? 1 : 0;
+}
+
+// list[pos[i]] = i for the flagged sources (in index order).
+__global__ void compact_kernel(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t m,
+                               int32_t* __restrict__ list)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) list[pos[i]] = (int32_t)i;
+}
+
+// Pairs of the *np_dev sources of `list` (positive radii, increasing index) whose bubbles
+// overlap (d^2 <= (f_ov (r_a + r_b))^2 + eps, d minimum-image when periodic) are united; the
+// larger root is hooked under the smaller, so each component's root is its smallest index. The
+// np (np - 1) / 2 pairs (ia < ib) are numbered row by row, row ia holding np - 1 - ia of them,
+// and the grid strides over that numbering.
+__device__ __forceinline__ long long pair_row_start(long long ia, long long np)
+{
+    return ia * np - ia * (ia + 1) / 2;
+}
+
+__global__ void pair_union_kernel(const int32_t* __restrict__ cells, const double* __restrict__ radius,
+                                  const int32_t* __restrict__ list, const int32_t* __restrict__ np_dev, int n,
+                                  int periodic, double f_ov, double eps, int* parent, DevStats* st)
+{
+    const long long np = *np_dev;
+    const long long total = np * (np - 1) / 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    // the row of pair k: the root of ia^2 - (2 np - 1) ia + 2 k = 0, then corrected to be exact
+    const double b2 = (double)(2 * np - 1);
+    long long ia = (long long)floor(0.5 * (b2 - sqrt(fmax(b2 * b2 - 8.0 * (double)k, 0.0))));
+    ia = ia < 0 ? 0 : (ia > np - 2 ? np - 2 : ia);
+    while (ia > 0 && pair_row_start(ia, np) > k) --ia;
+    while (ia < np - 2 && pair_row_start(ia + 1, np) <= k) ++ia;
+    long long ib = k - pair_row_start(ia, np) + ia + 1;
+    for (; k < total; k += stride) {
+        const int a = list[ia], b = list[ib];
+        const double ra = radius[a], rb = radius[b];
+        long long dx = cells[3 * a] - cells[3 * b], dy = cells[3 * a + 1] - cells[3 * b + 1],
+                  dz = cells[3 * a + 2] - cells[3 * b + 2];
+        if (periodic) {
+            dx = minimg(dx, n);
+            dy = minimg(dy, n);
+            dz = minimg(dz, n);
+        }
+        const long long d2 = dx * dx + dy * dy + dz * dz;
+        const double rs = __dmul_rn(f_ov, __dadd_rn(ra, rb));
+        if ((double)d2 <= __dadd_rn(__dmul_rn(rs, rs), eps)) {
+            int u = a, v = b;
+            for (int tries = 0;; ++tries) {
+                u = uf_find(parent, u);
+                v = uf_find(parent, v);
+                if (u == v) break;
+                if (u > v) { const int t = u; u = v; v = t; }
+                if (atomicCAS(&parent[v], v, u) == v) break;
+                if (tries > (1 << 20)) { atomicOr(&st->err, kErrUnionFind); break; }
             }
-            const long long d2 = dx * dx + dy * dy + dz * dz;
-            const double rs = __dmul_rn(f_ov, __dadd_rn(ra, rb));
-            if ((double)d2 <= __dadd_rn(__dmul_rn(rs, rs), eps)) {
-                int u = (int)a, v = (int)b;
-                for (int tries = 0;; ++tries) {
-                    u = uf_find(parent, u);
-                    v = uf_find(parent, v);
-                    if (u == v) break;
-                    if (u > v) { const int t = u; u = v; v = t; }
-                    if (atomicCAS(&parent[v], v, u) == v) break;
-                    if (tries > (1 << 20)) { atomicOr(&st->err, kErrUnionFind); break; }
-                }
-            }
+        }
+        ib += stride;                    // the pair `stride` further on: rows shrink by one each
+        while (ib >= np && ia < np - 2) {
+            ib -= np - ia - 2;
+            ++ia;
         }
     }
 }
 
+// Key of source i: its component's root (a stable sort by it keeps members in index order).
 __global__ void label_keys_kernel(int* parent, int64_t m, int32_t* __restrict__ label, uint64_t* __restrict__ keys)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = uf_find(parent, (int)i);
         label[i] = r;
-        keys[i] = ((uint64_t)(uint32_t)r << 32) | (uint64_t)i;
+        keys[i] = (uint64_t)(uint32_t)r;
     }
 }
 
@@ -415,12 +539,13 @@ int launch_validate_sources(const int32_t* cells, const double* ndot, int64_t ns
     return 1;
 }
 
-int launch_dedup_sort(SourceWork& w, int64_t nsrc, cudaStream_t s)
+int launch_dedup_sort(SourceWork& w, int64_t nsrc, int n, cudaStream_t s)
 {
     if (nsrc <= 0) return 0;
     const int b = blocks_for(nsrc);
-    cell_keys_kernel<<<b, kBlock, 0, s>>>(w.cells_raw, nsrc, w.keys);
-    rank_kernel<<<b, kBlock, 0, s>>>(w.keys, nsrc, w.order);
+    const int ab = axis_bits(n);
+    cell_keys_kernel<<<b, kBlock, 0, s>>>(w.cells_raw, nsrc, ab, w.keys);
+    radix_sort_kernel<<<1, kSortThreads, 0, s>>>(w.keys, nsrc, 3 * ab, w.keys_b, w.keys_c, w.order_b, w.order);
     run_heads_kernel<<<b, kBlock, 0, s>>>(w.keys, w.order, nsrc, ~0ULL, w.flag);
     scan_kernel<<<1, 1024, 0, s>>>(w.flag, nsrc, w.head_pos, w.count);
     dedup_sum_kernel<<<b, kBlock, 0, s>>>(w.keys, w.order, w.flag, w.head_pos, nsrc, w.cells_raw, w.ndot_raw,
@@ -442,19 +567,26 @@ int launch_merge(SourceWork& w, int64_t m, int n, int periodic, const double* x,
         radius_kernel<4096><<<grid_r, kBlock, 0, s>>>(w.cells_a, m, n, x, samp_dirs, samp_count, x_th, f_req, n_min,
                                                       dr, rmax, periodic, w.radius);
     iota_kernel<<<b, kBlock, 0, s>>>(w.parent, m);
-    pair_union_kernel<<<b, kBlock, 0, s>>>(w.cells_a, w.radius, m, n, periodic, f_ov, eps, w.parent, st);
+    // the sources with a positive radius, compacted (label holds the list, count[1] its length)
+    positive_radius_kernel<<<b, kBlock, 0, s>>>(w.radius, m, w.flag);
+    scan_kernel<<<1, 1024, 0, s>>>(w.flag, m, w.head_pos, w.count + 1);
+    compact_kernel<<<b, kBlock, 0, s>>>(w.flag, w.head_pos, m, w.label);
+    pair_union_kernel<<<std::min(b * 64, 152 * 16), kBlock, 0, s>>>(w.cells_a, w.radius, w.label, w.count + 1, n,
+                                                                     periodic, f_ov, eps, w.parent, st);
     label_keys_kernel<<<b, kBlock, 0, s>>>(w.parent, m, w.label, w.keys);
-    rank_kernel<<<b, kBlock, 0, s>>>(w.keys, m, w.order);
-    run_heads_kernel<<<b, kBlock, 0, s>>>(w.keys, w.order, m, 0xffffffff00000000ULL, w.flag);
+    radix_sort_kernel<<<1, kSortThreads, 0, s>>>(w.keys, m, axis_bits((int)std::min<int64_t>(m, 1LL << 30)), w.keys_b,
+                                                 w.keys_c, w.order_b, w.order);
+    run_heads_kernel<<<b, kBlock, 0, s>>>(w.keys, w.order, m, ~0ULL, w.flag);
     scan_kernel<<<1, 1024, 0, s>>>(w.flag, m, w.head_pos, w.count);
     group_kernel<<<b, kBlock, 0, s>>>(w.order, w.flag, w.head_pos, m, n, periodic, w.cells_a, w.ndot_a, w.cells_b,
                                       w.ndot_b);
     // final lexicographic order of the merged catalog (its size is count[0] <= m; unused tail keys sort last)
-    cell_keys_kernel<<<b, kBlock, 0, s>>>(w.cells_b, m, w.keys);
+    const int ab = axis_bits(n);
+    cell_keys_kernel<<<b, kBlock, 0, s>>>(w.cells_b, m, ab, w.keys);
     mask_tail_kernel<<<b, kBlock, 0, s>>>(w.keys, m, w.count);
-    rank_kernel<<<b, kBlock, 0, s>>>(w.keys, m, w.order);
+    radix_sort_kernel<<<1, kSortThreads, 0, s>>>(w.keys, m, 3 * ab, w.keys_b, w.keys_c, w.order_b, w.order);
     gather_kernel<<<b, kBlock, 0, s>>>(w.order, m, w.cells_b, w.ndot_b, w.cells_a, w.ndot_a);
-    return 12;
+    return 15;
 }
 
 int launch_build_emit_dev(const SourceWork& w, int64_t max_m, double s_over_dx2, SrcEntry* out, DevStats* st,
