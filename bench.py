@@ -45,9 +45,9 @@ L2_FLUSH_BYTES = 512 << 20
 # all march launches of one step of the same box with its first 64 sources;
 # profiles/march_table_config2_dram.md), scaled to the full workload by primary segments. Valid only
 # for the kernel sources it was taken on.
-TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.763212646120428,
-                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "4b3a71c57998d3c2",
-                               "paper_2512_12466_gb300/csrc/rt_internal.h": "2308ad8b3588ea45"}}
+TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.804378436268312,
+                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "40ce4c5c9d00b4fc",
+                               "paper_2512_12466_gb300/csrc/rt_internal.h": "632db27dbd2931e9"}}
 
 
 def traffic_per_launch(segments_per_step: float, launches_per_step: float):
@@ -633,7 +633,9 @@ def run_nyx(args, world, rank, local):
                      "march_launches_per_step": f32["march_launches_per_step"]},
         "fp64": {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "steps": f64["steps"],
                  "roofline": {"achieved": f64["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                              "frac": f64["achieved_gbs"] / hbm, "kernel": "march_kernel<double>"}},
+                              "frac": f64["achieved_gbs"] / hbm,
+                              "kernel": "march_table_kernel<double> (FP64, geometry tables)",
+                              "bound": "fp64 pipe (84% of its peak in ncu; HBM fraction shown for the record)"}},
         "e2e": {"value": e2e_val, "unit": "segments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "clocks": f32["clocks"],
@@ -644,7 +646,7 @@ def run_nyx(args, world, rank, local):
         line["config4"] = bench_config4(nyx, torch)
     if not args.no_batched:
         line["batched"] = {"neutral": bench_batched(nyx, torch, "neutral", steps=5, tune=True),
-                           "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 25)}
+                           "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 27)}
     if args.serve_requests > 0:
         line["serving"] = bench_serving(nyx, torch, args.serve_requests)
     if world == 1 and not args.no_cpu_baseline:
