@@ -49,39 +49,31 @@ struct Ieee<double> {
     __device__ __forceinline__ static double absorb(double x) { return -expm1(-x); }
     __device__ __forceinline__ static double qdiv(double a, double b) { return a / b; }
     // Eq. 1 for a segment of optical depth dtau = kap ds, kap > 0: photons absorbed a = P (1 - e^{-dtau})
-    // and rate gseg = a G / kap. Below dtau = 2 both come from g(y) = (1 - e^{-y}) / y, whose
-    // series sum_k (-y)^k / (k+1)! is summed to k = 23 (the first term left out is below
-    // 2^24 / 25! < 1.1e-18, against g(2) > 0.43): a = P dtau g and gseg = P G ds g, with no
-    // exponential and no division on GB300's small FP64 unit; the bound is wide enough that a
-    // warp's lanes seldom split between the two forms. Above it, expm1 and the quotient.
+    // and rate gseg = a G / kap. Below dtau = 2 both come from g(y) = (1 - e^{-y}) / y: a = P dtau g
+    // and gseg = P G ds g, with no exponential and no division on GB300's small FP64 unit. g is the
+    // degree-13 Chebyshev interpolant of g(1 + t) on t in [-1, 1] (coefficients from
+    // gen_rate_poly.py, highest degree first), evaluated by Horner's rule in t = dtau - 1: within
+    // 2.4e-16 of g relative over [0, 2). The bound is wide enough that a warp's lanes seldom split
+    // between the two forms. Above it, expm1 and the quotient.
     __device__ __forceinline__ static void rate(double P, double G, double kap, double ds, double dtau, double& a,
                                                 double& gseg)
     {
         if (lt(dtau, 2.0)) {
-            double g = 1.0 / 620448401733239439360000.0;                  // 1 / 24!
-            g = fma(-dtau, g, 1.0 / 25852016738884976640000.0);
-            g = fma(-dtau, g, 1.0 / 1124000727777607680000.0);
-            g = fma(-dtau, g, 1.0 / 51090942171709440000.0);
-            g = fma(-dtau, g, 1.0 / 2432902008176640000.0);
-            g = fma(-dtau, g, 1.0 / 121645100408832000.0);
-            g = fma(-dtau, g, 1.0 / 6402373705728000.0);
-            g = fma(-dtau, g, 1.0 / 355687428096000.0);
-            g = fma(-dtau, g, 1.0 / 20922789888000.0);
-            g = fma(-dtau, g, 1.0 / 1307674368000.0);
-            g = fma(-dtau, g, 1.0 / 87178291200.0);
-            g = fma(-dtau, g, 1.0 / 6227020800.0);
-            g = fma(-dtau, g, 1.0 / 479001600.0);
-            g = fma(-dtau, g, 1.0 / 39916800.0);
-            g = fma(-dtau, g, 1.0 / 3628800.0);
-            g = fma(-dtau, g, 1.0 / 362880.0);
-            g = fma(-dtau, g, 1.0 / 40320.0);
-            g = fma(-dtau, g, 1.0 / 5040.0);
-            g = fma(-dtau, g, 1.0 / 720.0);
-            g = fma(-dtau, g, 1.0 / 120.0);
-            g = fma(-dtau, g, 1.0 / 24.0);
-            g = fma(-dtau, g, 1.0 / 6.0);
-            g = fma(-dtau, g, 0.5);
-            g = fma(-dtau, g, 1.0);
+            const double t = dtau - 1.0;
+            double g = -4.585677284736203e-12;
+            g = fma(g, t, 6.465596029808311e-11);
+            g = fma(g, t, -8.315200300486033e-10);
+            g = fma(g, t, 1.0046307689376594e-08);
+            g = fma(g, t, -1.1142554025478742e-07);
+            g = fma(g, t, 1.1252035937302869e-06);
+            g = fma(g, t, -1.0249196652958194e-05);
+            g = fma(g, t, 8.324114893927396e-05);
+            g = fma(g, t, -0.0005941848175853081);
+            g = fma(g, t, 0.0036598468274018593);
+            g = fma(g, t, -0.018988156876153583);
+            g = fma(g, t, 0.08030139707139056);
+            g = fma(g, t, -0.26424111765711533);
+            g = fma(g, t, 0.6321205588285577);
             a = P * (dtau * g);
             gseg = ((P * G) * ds) * g;
         } else {
