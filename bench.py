@@ -45,8 +45,8 @@ L2_FLUSH_BYTES = 512 << 20
 # all march launches of one step of the same box with its first 64 sources;
 # profiles/march_table_config2_dram.md), scaled to the full workload by primary segments. Valid only
 # for the kernel sources it was taken on.
-TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.804378436268312,
-                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "40ce4c5c9d00b4fc",
+TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.776468771607432,
+                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "bceb26a80677fcce",
                                "paper_2512_12466_gb300/csrc/rt_internal.h": "632db27dbd2931e9"}}
 
 
