@@ -211,7 +211,7 @@ def rt_spectrum_eval(t_bb_K: float, tau: float):
 
 
 def rt_geometry_table_bytes(device: int = 0) -> int:
-    """Device memory held by the FP32 geometry tables of CUDA device `device`."""
+    """Device memory held by the geometry tables (both precisions) of CUDA device `device`."""
     return int(lib().rt_geometry_table_bytes(int(device)))
 
 
