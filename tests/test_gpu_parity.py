@@ -315,6 +315,64 @@ def test_edge_fully_ionized_thin_limit(nyx):
     assert not got["heat"].any()
 
 
+@pytest.mark.parametrize("prec", [1, 0], ids=["fp32", "fp64"])
+def test_edge_max_grid_thin_path_sum(nyx, prec):
+    """The largest grid rt_create accepts (1024^3; cell indices up to 2^30, the integer crossing
+    products at their largest): a centred source in a fully ionized medium with level_max = 10,
+    whose split sphere R_10 (about 500 cells) lies inside the grid. Every level holds 12 4^l rays,
+    none escapes, the 12 4^10 last are dropped at level_max, and sum(Gamma) = Ndot sigma R_L / dx^2
+    (the thin-limit path sum) to the directions' quantisation. The deepest levels exceed the
+    geometry-table budget here, so the step mixes table-driven and walked levels."""
+    n, lm = 1024, 10
+    dev = torch.device("cuda")
+    box = n * 7.117e23
+    s = nyx.Solver(n, box, precision=prec, level_max=lm, overlap_mode=0, n_min_ray=4.0, tau_max=30.0,
+                   n_th_cm3=1e-4)
+    s.set_fields(torch.full((n ** 3,), 2e-4, dtype=torch.float64, device=dev),
+                 torch.ones(n ** 3, dtype=torch.float64, device=dev))
+    c = n // 2 - 1
+    s.add_sources(np.array([c, c, c], np.int32), np.array([1e52]))
+    g = torch.empty(n ** 3, dtype=torch.float64, device=dev)
+    _, _, st = s.step(0.0, g, None)
+    s.close()
+    for lvl in range(lm + 1):
+        assert st["rays"][lvl] == 12 * 4 ** lvl and st["escaped"][lvl] == 0
+    assert st["dropped_level"][lm] == 12 * 4 ** lm
+    dx = box / n
+    expect = 1e52 * 6.3e-18 * oracle.split_rq(4.0) * 2.0 ** (lm - 24) / dx ** 2
+    assert abs(g.sum().item() / expect - 1) < (2e-6 if prec == 0 else 3e-6)
+    assert (g >= 0).all().item()
+    del g
+    torch.cuda.empty_cache()
+
+
+def test_edge_max_grid_opaque_corners(nyx):
+    """1024^3 of dense neutral gas with a source in each of the 8 corner cells: every level-0 ray
+    is spent in its source cell, so Gamma there is Ndot / (n_HI V) and every other cell stays 0
+    (the opaque closed form), 12 rays a source and no split."""
+    n = 1024
+    dev = torch.device("cuda")
+    box = n * 7.117e23
+    s = nyx.Solver(n, box, precision=0, n_min_ray=4.0, tau_max=30.0, n_th_cm3=1e-2)
+    s.set_fields(torch.ones(n ** 3, dtype=torch.float64, device=dev),
+                 torch.zeros(n ** 3, dtype=torch.float64, device=dev))
+    corners = np.array([[i * (n - 1), j * (n - 1), k * (n - 1)] for i in (0, 1) for j in (0, 1) for k in (0, 1)],
+                       np.int32)
+    ndot = np.linspace(1e50, 8e50, 8)
+    s.add_sources(corners.ravel(), ndot)
+    g = torch.empty(n ** 3, dtype=torch.float64, device=dev)
+    _, _, st = s.step(0.0, g, None)
+    s.close()
+    assert st["rays"][0] == 96 and sum(st["splits"]) == 0 and st["dropped_tau"][0] == 96
+    assert torch.count_nonzero(g).item() == 8
+    vol = (box / n) ** 3
+    for (ix, iy, iz), nd in zip(corners, ndot):
+        got = g[(int(iz) * n + int(iy)) * n + int(ix)].item()
+        assert abs(got / (nd / (1.0 * vol)) - 1) < 1e-14
+    del g
+    torch.cuda.empty_cache()
+
+
 def test_edge_duplicate_sources(nyx):
     w = I.random_small(16, 3, seed=161, x_mode="patchy", box_cm=16 * 7e22)
     w.cells = np.array([[3, 4, 5], [3, 4, 5], [9, 9, 9], [3, 4, 5], [9, 9, 9]], np.int32)
