@@ -108,8 +108,7 @@ enum {
                                   Phi(tau) - Phi(tau + dtau) of it per segment, Phi(tau) being the
                                   fraction of its photons that survive tau (tabulated per
                                   temperature, cubic interpolation in ln tau). tau_max <= 1e4.
-                                  rt_step only (not the batched, serving or allocation-free forms);
-                                  the march walks its rays (no geometry tables). */
+                                  rt_step only (not the batched, serving or allocation-free forms). */
 };
 
 #define RT_FLAG_VISIT_HASH 1   /* accumulate the visit-list hash in rt_stats (bookkeeping check) */

@@ -226,6 +226,57 @@ __device__ __forceinline__ int wrapn(const int v, const int n)
     return r < 0 ? r + n : r;
 }
 
+// Eq. 1 for one segment of optical depth dtau = kap ds (kap = 0: the thin limit): the photons a it
+// absorbs per unit photon rate and its rate gseg. Gray: a = P (1 - e^{-dtau}). kFreq, integrated over
+// the blackbody spectrum (V.spec), the ray's budget P is its geometric share and the photons it still
+// carries are P Phi(tau): the segment absorbs P (Phi(tau) - Phi(tau + dtau)), or for a thin segment
+// the midpoint rate dtau Psi(tau + dtau/2) (error dtau^2 / 24 against the difference's cancellation,
+// equal near the switch), and deposits at the thin rate P Psi(tau) where kap = 0.
+template <class R, bool kFreq>
+__device__ __forceinline__ void segment_eq1(const SolveView<R>& V, R P, R tau, R ctau, R G, R kap, R ds, R dtau, R& a,
+                                            R& gseg)
+{
+    using I = Ieee<R>;
+    if constexpr (kFreq) {
+        const R t0 = I::sub(tau, ctau);
+        R phi0, psi0, phi1, psi1;
+        if (I::pos(kap)) {
+            if (dtau >= (sizeof(R) == 4 ? (R)1e-2 : (R)1e-6)) {
+                spec_eval<R>(V.spec, t0, phi0, psi0);
+                spec_eval<R>(V.spec, t0 + dtau, phi1, psi1);
+                a = P * (phi0 - phi1);
+            } else {
+                spec_eval<R>(V.spec, t0 + (R)0.5 * dtau, phi0, psi0);
+                a = P * (dtau * psi0);
+            }
+            gseg = I::qdiv(a * G, kap);
+        } else {
+            spec_eval<R>(V.spec, t0, phi0, psi0);
+            a = (R)0;
+            gseg = ((P * psi0) * G) * ds;
+        }
+    } else if (I::pos(kap)) {
+        I::rate(P, G, kap, ds, dtau, a, gseg);
+    } else {
+        a = (R)0;
+        gseg = (P * G) * ds;
+    }
+}
+
+// The photons a ray still carries, in units of its source's photon rate per ray: its compensated
+// budget P - cP (gray), or P Phi(tau - ctau) (kFreq).
+template <class R, bool kFreq>
+__device__ __forceinline__ double ray_remaining(const SolveView<R>& V, R P, R tau, R cP, R ctau)
+{
+    if constexpr (kFreq) {
+        R phi, psi;
+        spec_eval<R>(V.spec, Ieee<R>::sub(tau, ctau), phi, psi);
+        return widen(P) * widen(phi);
+    } else {
+        return widen(P) - widen(cP);
+    }
+}
+
 // March one ray of level l (source entry se, quantised direction dv, budget
 // P with compensation cP, optical depth tau with compensation ctau) from its
 // start sphere to its split sphere, depositing into V.gamma and counting into
@@ -241,15 +292,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
 {
     using I = Ieee<R>;
     // photons the ray still carries, in units of ph
-    auto remaining = [&]() -> double {
-        if constexpr (kFreq) {
-            R phi, psi;
-            spec_eval<R>(V.spec, I::sub(tau, ctau), phi, psi);
-            return widen(P) * widen(phi);
-        } else {
-            return widen(P) - widen(cP);
-        }
-    };
+    auto remaining = [&]() -> double { return ray_remaining<R, kFreq>(V, P, tau, cP, ctau); };
     const int n = V.n;
     // the ray ends on its split sphere R_l or, with periodic boundaries, at the travel distance
     // sqrt(3) L_box if that comes first or at the same point, where it stops without splitting
@@ -368,33 +411,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
         const R kap = I::mag(kraw);
         const R dtau = I::mul(kap, ds);
         R a, gseg;
-        if constexpr (kFreq) {
-            // Eq. 1 over frequency: the segment absorbs Phi(tau) - Phi(tau + dtau) of the budget; for
-            // a thin segment the midpoint rate dtau Psi(tau + dtau/2) instead of the difference (error
-            // dtau^2 / 24 against the difference's cancellation, equal near the switch)
-            const R t0 = I::sub(tau, ctau);
-            R phi0, psi0, phi1, psi1;
-            if (I::pos(kap)) {
-                if (dtau >= (sizeof(R) == 4 ? (R)1e-2 : (R)1e-6)) {
-                    spec_eval<R>(V.spec, t0, phi0, psi0);
-                    spec_eval<R>(V.spec, t0 + dtau, phi1, psi1);
-                    a = P * (phi0 - phi1);
-                } else {
-                    spec_eval<R>(V.spec, t0 + (R)0.5 * dtau, phi0, psi0);
-                    a = P * (dtau * psi0);
-                }
-                gseg = I::qdiv(a * G, kap);
-            } else {
-                spec_eval<R>(V.spec, t0, phi0, psi0);
-                a = (R)0;
-                gseg = ((P * psi0) * G) * ds;
-            }
-        } else if (I::pos(kap)) {
-            I::rate(P, G, kap, ds, dtau, a, gseg);
-        } else {
-            a = (R)0;
-            gseg = (P * G) * ds;
-        }
+        segment_eq1<R, kFreq>(V, P, tau, ctau, G, kap, ds, dtau, a, gseg);
         // ---- Eqs. 5-8: the share f kept in this cell and the neighbour's deposit
         R f = (R)1, g2 = (R)0;
         int nbcell = -1;
@@ -987,7 +1004,7 @@ struct TableEntry<double> {
 };
 
 // march_ray with the geometry read from the level's table (FP32 or FP64 physics).
-template <class R, bool kHash>
+template <class R, bool kHash, bool kFreq>
 __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const GeomLevel& GL, unsigned* err, const int l,
                                                 const uint32_t si, const uint32_t pix, R P, R tau, R cP, R ctau,
                                                 const SrcEntry& se, const int4 dv, Tally& T, R& oP, R& otau,
@@ -1024,11 +1041,11 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
                       V.overlap_mode == RT_OVERLAP_NAIVE;
     const bool corr = V.overlap_mode != RT_OVERLAP_NONE;
     const long long nn = (long long)n * n;
-    const double B0 = widen(P) - widen(cP);
+    const double B0 = ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
     ++T.rays;
     if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
         ++T.esc;
-        T.escph += ph * (widen(P) - widen(cP));
+        T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
         return false;
     }
     const E* col = TE::ent(GL) + GL.row0[pix >> 5] * 32 + (pix & 31);
@@ -1074,12 +1091,7 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         const R kap = I::mag(kcur);
         const R dtau = I::mul(kap, ds);
         R a, gseg;
-        if (I::pos(kap)) {
-            I::rate(P, G, kap, ds, dtau, a, gseg);
-        } else {
-            a = (R)0;
-            gseg = (P * G) * ds;
-        }
+        segment_eq1<R, kFreq>(V, P, tau, ctau, G, kap, ds, dtau, a, gseg);
         // ---- Eqs. 5-8
         R f = (R)1, g2 = (R)0;
         int nbcell = -1;
@@ -1107,21 +1119,21 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
             ++T.sec;
         }
         budget_add(tau, ctau, dtau);
-        budget_add(P, cP, -a);
+        if constexpr (!kFreq) budget_add(P, cP, -a);
         if (kHash && V.hash) T.hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
         ++seq;
         if (!I::lt(tau, taumax)) {             // photons spent
             ++T.dtau;
-            T.dropph += ph * (widen(P) - widen(cP));
+            T.dropph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
             break;
         }
         if (!steps) {                    // the segment ended on the end sphere
             if (!split_end) {            // travelled sqrt(3) L_box (Sec. 2.5.1)
                 ++T.esc;
-                T.escph += ph * (widen(P) - widen(cP));
+                T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
             } else if (l + 1 > V.level_max) {
                 ++T.dlev;
-                T.dropph += ph * (widen(P) - widen(cP));
+                T.dropph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
             } else {
                 ++T.split;
                 split = true;
@@ -1134,7 +1146,7 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         }
         if (!next_in) {
             ++T.esc;
-            T.escph += ph * (widen(P) - widen(cP));
+            T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
             break;
         }
         if (last) {                      // cannot happen: a table ends where every grid is left
@@ -1149,7 +1161,7 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         e = en;
     }
     T.seg += seq;
-    T.abs += ph * (B0 - (widen(P) - widen(cP)));
+    T.abs += ph * (B0 - ray_remaining<R, kFreq>(V, P, tau, cP, ctau));
     return split;
 }
 
@@ -1275,14 +1287,15 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
     flush_tally(T, 0xffffffffu, &st, l);
 }
 
-// One level (or one slice of it) of one solve, geometry from the level's table. Without the walk
-// the FP32 march fits 64 registers, so four blocks (32 warps) per SM; the FP64 one takes three.
+// One level (or one slice of it) of one solve, geometry from the level's table (kFreq: Eq. 1 over
+// the blackbody spectrum). Without the walk the FP32 march fits 64 registers, so four blocks (32
+// warps) per SM; the FP64 one takes two.
 template <class R>
 struct TableOccupancy {
     static constexpr int blocks = sizeof(R) == 4 ? 4 : 2;
 };
 
-template <class R, bool kHash>
+template <class R, bool kHash, bool kFreq>
 __global__ void __launch_bounds__(256, TableOccupancy<R>::blocks) march_table_kernel(const MarchArgs<R> A, const GeomLevel GL)
 {
     const int l = A.level;
@@ -1300,6 +1313,7 @@ __global__ void __launch_bounds__(256, TableOccupancy<R>::blocks) march_table_ke
     V.tau_max = A.tau_max;
     V.src_off = 0;
     V.rs = A.rs;
+    V.spec = A.spec;
     Tally T;
     T.clear();
     for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
@@ -1311,7 +1325,7 @@ __global__ void __launch_bounds__(256, TableOccupancy<R>::blocks) march_table_ke
         if (j < A.c1) {
             R P, tau, cP, ctau;
             load_ray<R>(l, j, A.in, si, pix, P, tau, cP, ctau);
-            split = march_ray_table<R, kHash>(V, GL, &A.st->err, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T,
+            split = march_ray_table<R, kHash, kFreq>(V, GL, &A.st->err, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T,
                                            oP, otau, ocP, octau);
         }
         append_split<R>(split, si, pix, oP, otau, ocP, octau, A.out, A.out_count, &A.st->err);
@@ -1401,7 +1415,7 @@ __global__ void __launch_bounds__(256, (kTable && kSingle) ? 4 : MarchOccupancy<
                     V.src_off = bs.src_off - A.src_base;
                     if constexpr (kTable) {
                         static_assert(sizeof(R) == 4, "geometry tables serve the FP32 march");
-                        split = march_ray_table<float, kHash>(V, A.geo[l], A.err, l, si, pix, P, tau, cP, ctau, se, dirs[pix],
+                        split = march_ray_table<float, kHash, false>(V, A.geo[l], A.err, l, si, pix, P, tau, cP, ctau, se, dirs[pix],
                                                        T, oP, otau, ocP, octau);
                     } else {
                         split = march_ray<R, kHash, false>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau, ocP,
@@ -1453,15 +1467,25 @@ int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_
 
 int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int grid, int block, cudaStream_t s)
 {
-    if (a.hash) march_table_kernel<float, true><<<grid, block, 0, s>>>(a, g);
-    else march_table_kernel<float, false><<<grid, block, 0, s>>>(a, g);
+    if (a.spec.v) {
+        if (a.hash) march_table_kernel<float, true, true><<<grid, block, 0, s>>>(a, g);
+        else march_table_kernel<float, false, true><<<grid, block, 0, s>>>(a, g);
+    } else {
+        if (a.hash) march_table_kernel<float, true, false><<<grid, block, 0, s>>>(a, g);
+        else march_table_kernel<float, false, false><<<grid, block, 0, s>>>(a, g);
+    }
     return 1;
 }
 
 int launch_march_table_f64(const MarchArgs<double>& a, const GeomLevel& g, int grid, int block, cudaStream_t s)
 {
-    if (a.hash) march_table_kernel<double, true><<<grid, block, 0, s>>>(a, g);
-    else march_table_kernel<double, false><<<grid, block, 0, s>>>(a, g);
+    if (a.spec.v) {
+        if (a.hash) march_table_kernel<double, true, true><<<grid, block, 0, s>>>(a, g);
+        else march_table_kernel<double, false, true><<<grid, block, 0, s>>>(a, g);
+    } else {
+        if (a.hash) march_table_kernel<double, true, false><<<grid, block, 0, s>>>(a, g);
+        else march_table_kernel<double, false, false><<<grid, block, 0, s>>>(a, g);
+    }
     return 1;
 }
 

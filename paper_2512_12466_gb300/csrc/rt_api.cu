@@ -463,7 +463,7 @@ int run_level(rt_handle* h, int level, int64_t nparents)
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->sm_count * 8));
         // the level's geometry table for this precision (built once per device, outside the timed launch)
         GeomLevel gl;
-        const bool table = !(h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE) && h->cfg.spectrum == RT_SPECTRUM_GRAY &&
+        const bool table = !(h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE) &&
                            geometry_level(h->device, h->rq, level, h->cfg.n, h->rs, a.dirs, h->stream, sizeof(R) == 8,
                                           &gl);
         RT_CUDA(h, cudaEventRecord(h->ev[4], h->stream), "event");

@@ -30,6 +30,7 @@ def main(argv=None) -> int:
     ap.add_argument("--merge", action="store_true", help="256^3 patchy box, Alg. 3 merging forced")
     ap.add_argument("--chem", action="store_true", help="Table 1 Test A (64^3) with the C2-Ray iteration")
     ap.add_argument("--batch", type=int, default=0, help="K solves of the uneven mix through the batched kernel")
+    ap.add_argument("--spectrum", action="store_true", help="Eq. 1 over a 1e5 K blackbody instead of the gray rate")
     a = ap.parse_args(argv)
     import torch
     import paper_2512_12466_gb300 as nyx
@@ -69,6 +70,8 @@ def main(argv=None) -> int:
         w = I.config2(a.x)
         cfg = {}
     k = max(0, min(a.sources, len(w.ndot)))
+    if a.spectrum:
+        cfg.update(spectrum=nyx.RT_SPECTRUM_BLACKBODY, t_bb_K=1e5)
     s = nyx.Solver(w.n, w.box_cm, precision=prec, n_th_cm3=0.01 * float(w.n_h.mean()), overlap_mode=a.overlap,
                    n_min_ray=4.0, tau_max=30.0, flags=flags, **cfg)
     s.set_fields(d(w.n_h), d(w.x_ion))

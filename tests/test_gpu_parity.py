@@ -213,16 +213,18 @@ SPECTRUM_CASES = [
 ]
 
 
+@pytest.mark.parametrize("walk", [False, True], ids=["table", "walk"])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("case", SPECTRUM_CASES)
-def test_spectrum_parity(nyx, case, prec):
-    """Eq. 1 integrated over a blackbody spectrum: bookkeeping bit for bit (tau
-    decides everything), fields within the table's interpolation accuracy of
-    the oracle's direct quadrature (FP64 1e-7; FP32 2e-5 of the FP64 oracle)."""
+def test_spectrum_parity(nyx, case, prec, walk):
+    """Eq. 1 integrated over a blackbody spectrum, on the geometry tables and on the walk:
+    bookkeeping bit for bit (tau decides everything), fields within the spectrum table's
+    interpolation accuracy of the oracle's direct quadrature (FP64 1e-7; FP32 2e-5 of the FP64
+    oracle)."""
     n, k, seed, xm, dxc, mode, t_bb, per = case
     w = I.random_small(n, k, seed=seed, x_mode=xm, box_cm=n * dxc)
     kw = dict(overlap_mode=mode, n_th_cm3=0.3 * float(w.n_h.mean()), spectrum=1, t_bb_K=t_bb, periodic=per)
-    ref, got = run_both(nyx, w, precision=prec, **kw)
+    ref, got = run_both(nyx, w, precision=prec, flags=nyx.RT_FLAG_NO_GEOMETRY_TABLE if walk else 0, **kw)
     assert_bookkeeping(got["stats"], ref["stats"])
     ref64 = ref if prec == 0 else oracle.run_workload(w, precision=0, **kw)
     assert relerr(got["gamma"], ref64["gamma"]) < (1e-7 if prec == 0 else 2e-5)
