@@ -355,7 +355,8 @@ def bench_spectrum(nyx, torch, w, n_th):
     return out
 
 
-def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int | None = None):
+def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int | None = None,
+                  tile: int | None = None):
     """64 independent solves (grid sizes from {32,64,96,128}^3, log-uniform source counts on
     [1, 4096], per-solve seeds), FP32: one persistent graph-captured launch for all solves vs
     one rt_step per solve. Returns timings, segments and the largest field difference."""
@@ -388,6 +389,8 @@ def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int |
     b = nyx.Batch(solvers)
     if slice_:
         b.set_params(slice=slice_)
+    if tile:
+        b.set_params(tile=tile)
     tuned = None
     if tune:
         p, ms = b.tune(repeats=1)
@@ -688,7 +691,8 @@ def run_nyx(args, world, rank, local):
         line["config4"] = bench_config4(nyx, torch)
     if not args.no_batched:
         line["batched"] = {"neutral": bench_batched(nyx, torch, "neutral", steps=5, tune=True),
-                           "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 27)}
+                           "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 27,
+                                                         tile=32)}
     if args.serve_requests > 0:
         line["serving"] = bench_serving(nyx, torch, args.serve_requests)
     if world == 1 and not args.no_cpu_baseline:
