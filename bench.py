@@ -45,8 +45,8 @@ L2_FLUSH_BYTES = 512 << 20
 # all march launches of one step of the same box with its first 64 sources;
 # profiles/march_table_config2_dram.md), scaled to the full workload by primary segments. Valid only
 # for the kernel sources it was taken on.
-TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.776468771607432,
-                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "bceb26a80677fcce",
+TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.760785412388026,
+                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "640aef1bb48de04d",
                                "paper_2512_12466_gb300/csrc/rt_internal.h": "632db27dbd2931e9"}}
 
 
