@@ -525,6 +525,7 @@ int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out)
 {
     cudaStream_t s = h->stream;
     *merged_out = false;
+    h->catalog_valid = false;            // the buffers below are rewritten; valid again once emitted
     // ---- validation of device-resident inputs
     h->launches += launch_validate_fields(h->d_nh, h->d_x, h->ncell, h->d_st, s);
     h->launches += launch_validate_sources(h->sw.cells_raw, h->sw.ndot_raw, h->nsrc, h->cfg.n, h->d_st, s);
@@ -606,6 +607,7 @@ int prepare_sources_many(rt_handle* const* hs, int count, int* rcs)
     auto enqueue = [](rt_handle* h) -> int {
         cudaStream_t s = h->stream;
         h->launches = 0;
+        h->catalog_valid = false;
         RT_CUDA(h, cudaMemsetAsync(h->d_st, 0, sizeof(DevStats), s), "stats clear");
         h->launches += launch_validate_fields(h->d_nh, h->d_x, h->ncell, h->d_st, s);
         h->launches += launch_validate_sources(h->sw.cells_raw, h->sw.ndot_raw, h->nsrc, h->cfg.n, h->d_st, s);

@@ -562,6 +562,19 @@ def test_traced_catalog_readback(nyx):
     with pytest.raises(nyx.NyxError) as e:
         nyx.rt_get_sources(s.h, None, None, 1, nyx.RT_HOST)
     assert e.value.code == nyx.RT_EINVAL
+    # a step that device-side validation rejects leaves no catalog to read
+    s.add_sources(w.cells.ravel(), w.ndot)
+    s.step()
+    assert len(s.sources()[1]) == m
+    s.clear_sources()
+    s.add_sources(torch.tensor([1, 2, 99], dtype=torch.int32, device="cuda"),
+                  torch.tensor([1e50], dtype=torch.float64, device="cuda"))
+    with pytest.raises(nyx.NyxError) as e:
+        s.step()
+    assert e.value.code == nyx.RT_EINVAL
+    with pytest.raises(nyx.NyxError) as e:
+        s.sources()
+    assert e.value.code == nyx.RT_ESTATE
     s.close()
 
 
