@@ -719,6 +719,27 @@ def test_merge_components_match_dfs_periodic(seed):
     assert all(tuple(v) in member_cells for v in mc.tolist())
 
 
+def test_merge_pair_predicate_is_squared():
+    """Alg. 3's pair test compares squared distance with the squared overlap length,
+    d^2 <= (f_ov (r_a + r_b))^2 + eps (the text's form): two bubbles of radius 7.5 whose
+    centres are 10 cells apart give both sources r = 6 (shells 2, 4, 6 fully ionized, the
+    shell at 8 not), so they merge (100 <= 144) where d^2 <= f_ov (r_a + r_b) + eps would
+    not (100 > 12); with f_ov = 0.8 they stay apart (100 > 92.16), so f_ov sits inside the
+    square. The merged source is the member nearest the flux-weighted centroid
+    floor((19 + 2 29) / 3 + 1/2) = 26, i.e. the one at 29."""
+    n = 48
+    zz, yy, xx = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    x = np.zeros((n, n, n))
+    for cx in (19, 29):
+        x[(xx - cx) ** 2 + (yy - 24) ** 2 + (zz - 24) ** 2 <= 7.5 ** 2] = 1.0
+    c, nd = oracle.sources_dedup(np.array([[19, 24, 24], [29, 24, 24]], np.int32), np.array([1e51, 2e51]))
+    mc, mn, rad, lab = oracle.merge_sources(x, c, nd, f_ov=1.0)
+    assert list(rad) == [6.0, 6.0]
+    assert mc.tolist() == [[29, 24, 24]] and list(mn) == [3e51]
+    mc, mn, rad, lab = oracle.merge_sources(x, c, nd, f_ov=0.8)
+    assert len(mn) == 2 and list(mn) == [1e51, 2e51]
+
+
 def test_merge_two_sources_in_one_bubble():
     n = 48
     zz, yy, xx = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
