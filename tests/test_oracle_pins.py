@@ -569,6 +569,35 @@ def test_chem_time_average_is_mean_of_trajectory():
     np.testing.assert_allclose(xe, traj[:, -1], rtol=1e-13)
 
 
+def test_chem_matches_ode_integration():
+    """Eq. 3 at constant rates, dx/dt = (Gamma + n_e C_H)(1 - x) - n_e C alpha_B x with n_e the
+    previous <x> n_H, integrated by classical fourth-order Runge-Kutta in 40000 steps: the
+    oracle's x(t + dt) and time average <x> (its closed form) agree to 1e-10."""
+    rng = np.random.default_rng(33)
+    n_h = 10 ** rng.uniform(-4, -2, 6)
+    x0 = rng.uniform(0, 1, 6)
+    xprev = rng.uniform(0, 1, 6)
+    gam = 10 ** rng.uniform(-16, -12, 6)
+    dt, alpha, c_h, clump = 3e13, 2.59e-13, 3e-13, 2.0
+    xa, xe, _ = oracle.chem_update(n_h, x0, xprev, gam, dt, alpha, C_H=c_h, clump=clump)
+    ne = xprev * n_h
+    f = lambda x: (gam + ne * c_h) * (1 - x) - ne * clump * alpha * x
+    steps = 40000
+    h = dt / steps
+    x = x0.copy()
+    integral = np.zeros_like(x)
+    for _ in range(steps):
+        k1 = f(x)
+        k2 = f(x + 0.5 * h * k1)
+        k3 = f(x + 0.5 * h * k2)
+        k4 = f(x + h * k3)
+        # Simpson's rule over the step with the Runge-Kutta midpoint estimate
+        integral += h / 6 * (x + 4 * (x + 0.5 * h * (k1 + k2) / 2) + (x + h * (k1 + 2 * k2 + 2 * k3 + k4) / 6))
+        x = x + h * (k1 + 2 * k2 + 2 * k3 + k4) / 6
+    np.testing.assert_allclose(xe, x, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(xa, integral / dt, rtol=1e-8, atol=1e-10)
+
+
 # ------------------------------------------------------------------ sources: dedup, radius, merge (Alg. 3)
 
 def test_dedup_sorted_and_summed():
