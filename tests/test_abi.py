@@ -44,28 +44,27 @@ def test_library_exports_every_declared_symbol(built):
 
 
 def test_struct_layout_matches_header(tmp_path):
-    fields_c = [f for f, _ in nyx.rt_config._fields_]
-    fields_s = [f for f, _ in nyx.rt_stats._fields_]
+    """Every struct the binding mirrors has the header's size and field offsets (a gcc probe
+    compiled from the header as C)."""
+    structs = [nyx.rt_config, nyx.rt_stats, nyx.rt_batch_params, nyx.rt_server_config, nyx.rt_server_stats]
     prog = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
-    prog.append('printf("config %zu\\n", sizeof(rt_config));')
-    prog.append('printf("stats %zu\\n", sizeof(rt_stats));')
-    for f in fields_c:
-        prog.append(f'printf("c.{f} %zu\\n", offsetof(rt_config, {f}));')
-    for f in fields_s:
-        prog.append(f'printf("s.{f} %zu\\n", offsetof(rt_stats, {f}));')
+    for st in structs:
+        name = st.__name__
+        prog.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            prog.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
     prog.append("return 0; }")
     src = tmp_path / "probe.c"
     src.write_text("\n".join(prog))
     exe = tmp_path / "probe"
-    subprocess.run(["gcc", "-o", str(exe), str(src)], check=True)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-o", str(exe), str(src)], check=True)
     got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n")
                if line)
-    assert int(got["config"]) == C.sizeof(nyx.rt_config)
-    assert int(got["stats"]) == C.sizeof(nyx.rt_stats)
-    for f in fields_c:
-        assert int(got["c." + f]) == getattr(nyx.rt_config, f).offset, f
-    for f in fields_s:
-        assert int(got["s." + f]) == getattr(nyx.rt_stats, f).offset, f
+    for st in structs:
+        name = st.__name__
+        assert int(got[name]) == C.sizeof(st), name
+        for f, _ in st._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(st, f).offset, (name, f)
 
 
 def test_config_defaults_host_only(built):
