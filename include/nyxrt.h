@@ -212,6 +212,20 @@ int rt_get_x(rt_handle* h, double* x_out, int where);
 int rt_get_sources(rt_handle* h, int32_t* cells_out, double* ndot_out, int64_t capacity, int64_t* count,
                    int where);
 
+/* Checkpoint, to resume a run later or elsewhere: write the handle's configuration, its fields
+ * (n_H and the current ionized fraction x, which rt_step advances under chem_iterate) and the
+ * sources added since the last rt_clear_sources to the file `path` (binary, read back by rt_load).
+ * A handle loaded from it steps exactly as this one would: the same bookkeeping bit for bit and
+ * the same fields. RT_ESTATE before rt_set_fields; RT_EINVAL if the file cannot be written.
+ * Synchronises the handle's stream. */
+int rt_save(rt_handle* h, const char* path);
+
+/* Create a handle on `cuda_stream` (as rt_create) from a file rt_save wrote, holding its
+ * configuration, fields and sources. RT_EINVAL if the file is missing, truncated, of another
+ * format version or holds an invalid configuration (rt_last_error(NULL) says which); otherwise
+ * the codes of rt_create, rt_set_fields and rt_add_sources. */
+int rt_load(const char* path, void* cuda_stream, rt_handle** out);
+
 /* Free the handle and its device memory. NULL is accepted. */
 int rt_destroy(rt_handle* h);
 

@@ -116,6 +116,8 @@ def lib():
         L.rt_step.argtypes = [P, d, P, P, C.c_int, C.POINTER(rt_stats)]
         L.rt_get_x.argtypes = [P, P, C.c_int]
         L.rt_get_sources.argtypes = [P, P, P, i64, C.POINTER(i64), C.c_int]
+        L.rt_save.argtypes = [P, C.c_char_p]
+        L.rt_load.argtypes = [C.c_char_p, P, C.POINTER(P)]
         L.rt_destroy.argtypes = [P]
         L.rt_last_error.argtypes = [P]
         L.rt_last_error.restype = C.c_char_p
@@ -139,7 +141,8 @@ def lib():
         L.rt_server_last_error.argtypes = [P]
         L.rt_server_last_error.restype = C.c_char_p
         for f in ("rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_reconfigure", "rt_step", "rt_get_x",
-                  "rt_get_sources", "rt_destroy", "rt_batch_create", "rt_batch_set_params", "rt_batch_get_params", "rt_batch_tune",
+                  "rt_get_sources", "rt_save", "rt_load", "rt_destroy", "rt_batch_create", "rt_batch_set_params",
+                  "rt_batch_get_params", "rt_batch_tune",
                   "rt_batch_capture", "rt_batch_run", "rt_batch_destroy", "rt_server_create", "rt_server_submit",
                   "rt_server_poll", "rt_server_stats_get", "rt_server_destroy"):
             getattr(L, f).restype = C.c_int
@@ -150,7 +153,7 @@ def lib():
 def exported_symbols():
     return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_reconfigure",
             "rt_geometry_table_bytes", "rt_spectrum_eval", "rt_step",
-            "rt_get_x", "rt_get_sources", "rt_destroy", "rt_last_error", "rt_version", "rt_batch_create", "rt_batch_set_params",
+            "rt_get_x", "rt_get_sources", "rt_save", "rt_load", "rt_destroy", "rt_last_error", "rt_version", "rt_batch_create", "rt_batch_set_params",
             "rt_batch_get_params", "rt_batch_tune", "rt_batch_capture", "rt_batch_run", "rt_batch_destroy",
             "rt_batch_last_error", "rt_server_config_default", "rt_server_create", "rt_server_submit",
             "rt_server_poll", "rt_server_stats_get", "rt_server_destroy", "rt_server_last_error", "rt_step_noalloc"]
@@ -234,6 +237,16 @@ def rt_get_sources(h: int, cells_out, ndot_out, capacity: int, where: int) -> in
     m = C.c_int64(0)
     _check(lib().rt_get_sources(h, cells_out, ndot_out, int(capacity), C.byref(m), where), h)
     return int(m.value)
+
+
+def rt_save(h: int, path: str) -> None:
+    _check(lib().rt_save(h, os.fsencode(path)), h)
+
+
+def rt_load(path: str, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(lib().rt_load(os.fsencode(path), C.c_void_p(stream), C.byref(h)))
+    return h.value
 
 
 def rt_destroy(h: int) -> None:
@@ -372,6 +385,24 @@ class Solver:
         p, w = _ptr(out)
         rt_get_x(self.h, p, w)
         return out
+
+    def save(self, path: str) -> None:
+        """Checkpoint this solver (configuration, fields, sources) to `path`."""
+        rt_save(self.h, path)
+
+    @classmethod
+    def load(cls, path: str, stream: int | None = None) -> "Solver":
+        """A solver restored from a checkpoint written by save(), ready to step."""
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        s = cls.__new__(cls)
+        s.h = rt_load(path, stream)
+        with open(path, "rb") as f:                # the configuration follows the magic and two uint32
+            f.seek(16)
+            s.cfg = rt_config.from_buffer_copy(f.read(C.sizeof(rt_config)))
+        s.n = int(s.cfg.n)
+        return s
 
     def sources(self):
         """The catalog the last step traced (after dedup, sort and Alg. 3

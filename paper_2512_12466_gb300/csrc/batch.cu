@@ -604,6 +604,7 @@ int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best_out, doubl
 
 int rt_batch_run(rt_batch* b, double* const* gamma_out, double* const* heat_out, int where, rt_stats* stats)
 {
+    NvtxRange nvtx("rt_batch_run");
     if (!b) return RT_EINVAL;
     if (b->sticky) return RT_ESTATE;
     if (where != RT_HOST && where != RT_DEVICE) return bfail(b, RT_EINVAL, "bad where");

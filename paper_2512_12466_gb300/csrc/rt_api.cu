@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -331,9 +332,30 @@ namespace nyx {
 int configure(rt_handle* h, const rt_config* cfg, std::string& why);
 bool valid_config(const rt_config* c, std::string& why);
 
+// Host-side fault injection for tests: with NYXRT_FAULT_ALLOC=k (k >= 1) in the environment, the k-th
+// device allocation the library makes through dalloc in this process fails as if the device were out
+// of memory (no device work is involved; every caller must return RT_ENOMEM and stay usable).
+long long fault_alloc_at()
+{
+    static const long long k = [] {
+        const char* e = std::getenv("NYXRT_FAULT_ALLOC");
+        return e ? std::atoll(e) : 0LL;
+    }();
+    return k;
+}
+std::atomic<long long> g_alloc_count{0};
+
 // Handle memory is stream-ordered: allocating or freeing it never waits for
 // work on other streams (a server creates and frees handles while batches run).
-cudaError_t dalloc(rt_handle* h, void** p, size_t bytes) { return cudaMallocAsync(p, bytes, h->stream); }
+cudaError_t dalloc(rt_handle* h, void** p, size_t bytes)
+{
+    const long long k = fault_alloc_at();
+    if (k > 0 && ++g_alloc_count == k) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, h->stream);
+}
 void dfree(rt_handle* h, void* p)
 {
     if (p) cudaFreeAsync(p, h->stream);
@@ -425,6 +447,9 @@ int ensure_rays(rt_handle* h, int level, int64_t need)
 template <class R>
 int run_level(rt_handle* h, int level, int64_t nparents)
 {
+    char range[32];
+    std::snprintf(range, sizeof(range), "march level %d", level);
+    NvtxRange nvtx(range);
     const int64_t total = level == 0 ? 12 * h->n_emit : 4 * nparents;
     if (total <= 0) return RT_OK;
     if (level > h->table_level || level > kMaxLevel)
@@ -523,6 +548,7 @@ int trace(rt_handle* h, const double* xuse)
 // catalog (h->d_emit, h->n_emit). Leaves h->h_f64[1] = mean n_H (default n_th).
 int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out)
 {
+    NvtxRange nvtx("source stage (dedup, sort, Alg. 3)");
     cudaStream_t s = h->stream;
     *merged_out = false;
     h->catalog_valid = false;            // the buffers below are rewritten; valid again once emitted
@@ -784,8 +810,8 @@ int rt_destroy(rt_handle* h)
                       h->d_emit, h->d_count, h->d_st};
         for (void* q : ps) dfree(h, q);
         SourceWork& w = h->sw;
-        void* ws[] = {w.cells_raw, w.ndot_raw, w.keys, w.order, w.flag, w.head_pos, w.cells_a, w.ndot_a,
-                      w.cells_b, w.ndot_b, w.label, w.parent, w.radius, w.count};
+        void* ws[] = {w.cells_raw, w.ndot_raw, w.keys, w.keys_b, w.keys_c, w.order, w.order_b, w.flag, w.head_pos,
+                      w.cells_a, w.ndot_a, w.cells_b, w.ndot_b, w.label, w.parent, w.radius, w.count};
         for (void* q : ws) dfree(h, q);
         for (auto& r : h->rays) dfree(h, r.base);
     }
@@ -939,6 +965,92 @@ int rt_get_sources(rt_handle* h, int32_t* cells_out, double* ndot_out, int64_t c
     return RT_OK;
 }
 
+// Checkpoint file: the 8-byte magic, then uint32 version, uint32 sizeof(rt_config), the rt_config,
+// int64 cell count, n_H and x (float64 each), int64 source count, the sources' cells (int32 x 3)
+// and rates (float64), all little-endian as the host writes them.
+static const char kCkptMagic[8] = {'N', 'Y', 'X', 'R', 'T', 'C', 'K', '1'};
+static const uint32_t kCkptVersion = 1;
+
+int rt_save(rt_handle* h, const char* path)
+{
+    if (!h) return RT_EINVAL;
+    if (!path) return fail(h, RT_EINVAL, "path is NULL");
+    if (h->sticky) return RT_ESTATE;
+    if (!h->fields_set) return fail(h, RT_ESTATE, "rt_set_fields has not been called");
+    DeviceGuard g(h->device);
+    const int64_t nc = h->ncell, ns = h->nsrc;
+    std::vector<double> nh((size_t)nc), x((size_t)nc), nd((size_t)ns);
+    std::vector<int32_t> cells((size_t)(3 * ns));
+    RT_CUDA(h, cudaMemcpyAsync(nh.data(), h->d_nh, 8 * (size_t)nc, cudaMemcpyDeviceToHost, h->stream), "checkpoint copy");
+    RT_CUDA(h, cudaMemcpyAsync(x.data(), h->d_x, 8 * (size_t)nc, cudaMemcpyDeviceToHost, h->stream), "checkpoint copy");
+    if (ns > 0) {
+        RT_CUDA(h, cudaMemcpyAsync(cells.data(), h->sw.cells_raw, 12 * (size_t)ns, cudaMemcpyDeviceToHost, h->stream),
+                "checkpoint copy");
+        RT_CUDA(h, cudaMemcpyAsync(nd.data(), h->sw.ndot_raw, 8 * (size_t)ns, cudaMemcpyDeviceToHost, h->stream),
+                "checkpoint copy");
+    }
+    RT_CUDA(h, cudaStreamSynchronize(h->stream), "checkpoint copy");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(h, RT_EINVAL, std::string("cannot open ") + path + " for writing");
+    const uint32_t hdr[2] = {kCkptVersion, (uint32_t)sizeof(rt_config)};
+    bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 2, f) == 2 &&
+              std::fwrite(&h->cfg, sizeof(rt_config), 1, f) == 1 && std::fwrite(&nc, 8, 1, f) == 1 &&
+              std::fwrite(nh.data(), 8, (size_t)nc, f) == (size_t)nc && std::fwrite(x.data(), 8, (size_t)nc, f) == (size_t)nc &&
+              std::fwrite(&ns, 8, 1, f) == 1;
+    if (ok && ns > 0)
+        ok = std::fwrite(cells.data(), 4, (size_t)(3 * ns), f) == (size_t)(3 * ns) &&
+             std::fwrite(nd.data(), 8, (size_t)ns, f) == (size_t)ns;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(h, RT_EINVAL, std::string("writing ") + path + " failed");
+    return RT_OK;
+}
+
+int rt_load(const char* path, void* cuda_stream, rt_handle** out)
+{
+    if (!out) return RT_EINVAL;
+    *out = nullptr;
+    g_create_error.clear();
+    if (!path) { g_create_error = "path is NULL"; return RT_EINVAL; }
+    FILE* f = std::fopen(path, "rb");
+    if (!f) { g_create_error = std::string("cannot open ") + path; return RT_EINVAL; }
+    char magic[8];
+    uint32_t hdr[2] = {0, 0};
+    rt_config cfg{};
+    int64_t nc = -1, ns = -1;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+              std::fread(hdr, 4, 2, f) == 2 && hdr[0] == kCkptVersion && hdr[1] == sizeof(rt_config) &&
+              std::fread(&cfg, sizeof(rt_config), 1, f) == 1 && std::fread(&nc, 8, 1, f) == 1 &&
+              cfg.n >= 1 && cfg.n <= 1024 && nc == (int64_t)cfg.n * cfg.n * cfg.n;
+    std::vector<double> nh, x, nd;
+    std::vector<int32_t> cells;
+    if (ok) {
+        nh.resize((size_t)nc);
+        x.resize((size_t)nc);
+        ok = std::fread(nh.data(), 8, (size_t)nc, f) == (size_t)nc && std::fread(x.data(), 8, (size_t)nc, f) == (size_t)nc &&
+             std::fread(&ns, 8, 1, f) == 1 && ns >= 0 && ns <= (int64_t(1) << 30);
+    }
+    if (ok && ns > 0) {
+        cells.resize((size_t)(3 * ns));
+        nd.resize((size_t)ns);
+        ok = std::fread(cells.data(), 4, (size_t)(3 * ns), f) == (size_t)(3 * ns) &&
+             std::fread(nd.data(), 8, (size_t)ns, f) == (size_t)ns;
+    }
+    std::fclose(f);
+    if (!ok) { g_create_error = std::string(path) + " is not a complete checkpoint of this library"; return RT_EINVAL; }
+    rt_handle* h = nullptr;
+    int rc = rt_create(&cfg, cuda_stream, &h);
+    if (rc) return rc;
+    rc = rt_set_fields(h, nh.data(), x.data(), RT_HOST);
+    if (!rc && ns > 0) rc = rt_add_sources(h, cells.data(), nd.data(), ns, RT_HOST);
+    if (rc) {
+        g_create_error = h->err;
+        rt_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return RT_OK;
+}
+
 int rt_get_x(rt_handle* h, double* x_out, int where)
 {
     if (!h || !x_out || (where != RT_HOST && where != RT_DEVICE)) return h ? fail(h, RT_EINVAL, "bad arguments") : RT_EINVAL;
@@ -952,6 +1064,7 @@ int rt_get_x(rt_handle* h, double* x_out, int where)
 
 int rt_step(rt_handle* h, double dt_s, double* gamma_out, double* heat_out, int where, rt_stats* st)
 {
+    NvtxRange nvtx("rt_step");
     if (!h) return RT_EINVAL;
     if (h->sticky) return RT_ESTATE;
     if (where != RT_HOST && where != RT_DEVICE) return fail(h, RT_EINVAL, "bad where");

@@ -67,6 +67,22 @@ inline RayBuf<R> ray_view(const RayStore& s)
 
 }  // namespace nyx
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+// A named range on the profiler's timeline for the lifetime of the object (NVTX; free when no tool
+// is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#else
+struct NvtxRange {
+    explicit NvtxRange(const char*) {}
+};
+#endif
+
 struct rt_handle {
     rt_config cfg{};
     cudaStream_t stream = nullptr;

@@ -737,3 +737,63 @@ def test_config4_full_size_parity(nyx, config4):
     for k in ("rays", "splits", "escaped", "dropped_tau", "dropped_level", "segments", "secondary"):
         assert [a + b for a, b in zip(st_sub[k], st_rest[k])] == list(full[0][1][k]), k
     assert relerr(g_sub + g_rest, full[0][0]) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_checkpoint_resume(nyx, tmp_path, prec):
+    """rt_save / rt_load: a solver restored from a checkpoint steps exactly as the saved one: the
+    same bookkeeping and visit hash, Gamma and heating to the order of the FP64 atomics; its
+    configuration comes back with it (the restored step differs from a default-config one)."""
+    w = I.random_small(20, 5, seed=601, x_mode="patchy", box_cm=20 * 2e21)
+    kw = dict(precision=prec, overlap_mode=2, n_th_cm3=0.4 * float(w.n_h.mean()), tau_max=12.0,
+              flags=nyx.RT_FLAG_VISIT_HASH)
+    a = nyx.Solver(w.n, w.box_cm, **kw)
+    a.set_fields(w.n_h.ravel(), w.x_ion.ravel())
+    a.add_sources(w.cells.ravel(), w.ndot)
+    path = str(tmp_path / "solver.ckpt")
+    a.save(path)
+    ga, ha, sta = a.step()
+    a.close()
+    b = nyx.Solver.load(path)
+    assert b.n == w.n and b.cfg.overlap_mode == 2 and b.cfg.tau_max == 12.0
+    gb, hb, stb = b.step()
+    b.close()
+    assert_bookkeeping(stb, sta)
+    assert relerr(gb, ga) < 1e-14 and relerr(hb, ha) < 1e-14
+    # errors: missing or truncated files, and a save before the fields are set
+    with pytest.raises(nyx.NyxError) as e:
+        nyx.Solver.load(str(tmp_path / "missing.ckpt"))
+    assert e.value.code == nyx.RT_EINVAL
+    cut = tmp_path / "cut.ckpt"
+    cut.write_bytes(open(path, "rb").read()[:1000])
+    with pytest.raises(nyx.NyxError) as e:
+        nyx.Solver.load(str(cut))
+    assert e.value.code == nyx.RT_EINVAL
+    c = nyx.Solver(w.n, w.box_cm)
+    with pytest.raises(nyx.NyxError) as e:
+        c.save(str(tmp_path / "empty.ckpt"))
+    assert e.value.code == nyx.RT_ESTATE
+    c.close()
+
+
+def test_checkpoint_resume_with_chemistry(nyx, tmp_path):
+    """Table 1 Test A with the C2-Ray iteration: checkpoint after one step, then the original's
+    second step and the restored solver's first step give the same x(t + dt) and Gamma."""
+    w = I.stromgren_test("A", 32)
+    kw = {k: w.params[k] for k in ("n_min_ray", "tau_max", "chem_iterate", "alpha_B", "clumping", "C_H")}
+    dt = 1.0 * I.MYR_S
+    a = nyx.Solver(w.n, w.box_cm, n_th_cm3=1e-4, **kw)
+    a.set_fields(w.n_h.ravel(), w.x_ion.ravel())
+    a.add_sources(w.cells.ravel(), w.ndot)
+    a.step(dt)
+    path = str(tmp_path / "stromgren.ckpt")
+    a.save(path)
+    ga, _, sta = a.step(dt)
+    xa = a.get_x()
+    a.close()
+    b = nyx.Solver.load(path)
+    gb, _, stb = b.step(dt)
+    xb = b.get_x()
+    b.close()
+    assert abs(stb["chem_iters"] - sta["chem_iters"]) <= 1
+    assert relerr(xb, xa) < 1e-10 and relerr(gb, ga) < 1e-10
