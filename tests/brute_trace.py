@@ -184,8 +184,10 @@ def trace(n_h, x, cells, ndot, box_cm, sigma=6.3e-18, n_min=4.0, tau_max=30.0, l
                     de = float(dist[q])
                     lpix = float(tm) * nrm * math.sqrt(math.pi / 3.0) / 2 ** lvl
                     if 2 * de < lpix:
-                        if overlap_mode == 1:
+                        if overlap_mode == 1:                    # Eq. 5 alone
                             f = 0.5 + de / lpix
+                        elif overlap_mode == 4:                  # squared f_c, nothing to the neighbour
+                            f = (0.5 + de / lpix) ** 2
                         else:
                             if overlap_mode == 5:                # naive threshold: Eq. 5 share regardless
                                 f = 0.5 + de / lpix

@@ -3,15 +3,20 @@
 Each request's result must be the same alone (rt_step on its own handle) and
 in the mix (traced in a batch with whatever else was loaded at the time):
 bookkeeping and visit hash equal, fields within 1e-10 relative L2 (only the
-order of FP64 atomic deposits differs). The admitted device bytes never exceed
-the budget, and requests submitted while batches run are served by later
-batches.
+order of FP64 atomic deposits differs). Each served result is also checked
+against the CPU oracle run on that request alone (the iterative solve of
+Sec. 2.4, Alg. 2 per request): FP32 bookkeeping and visit hash bit-exact with
+the oracle's FP32 variant and fields within 1e-5 of the FP64 oracle; FP64
+bookkeeping bit-exact and fields within 1e-12. The admitted device bytes never
+exceed the budget, and requests submitted while batches run are served by
+later batches.
 """
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2512_12466_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
@@ -80,6 +85,19 @@ def test_each_result_same_alone_and_in_the_mix(nyx, precision):
     for w, r in zip(ws, got):
         assert r is not None
         check_same(nyx, r, alone(nyx, w, precision, 0.3 * float(w.n_h.mean())))
+        check_oracle(w, r, precision, 0.3 * float(w.n_h.mean()))
+
+
+def check_oracle(w, got, precision, n_th):
+    """A served result against the oracle on the same request alone."""
+    g, h, st, _ = got
+    ref64 = oracle.run_workload(w, n_th_cm3=n_th, precision=0)
+    ref = ref64 if precision == 0 else oracle.run_workload(w, n_th_cm3=n_th, precision=1)
+    for k in BOOK:
+        assert st[k] == ref["stats"][k], k
+    tol = 1e-12 if precision == 0 else 1e-5
+    assert relerr(g.ravel(), ref64["gamma"].ravel()) < tol
+    assert relerr(h.ravel(), ref64["heat"].ravel()) < tol
 
 
 def test_admission_respects_the_memory_budget(nyx):

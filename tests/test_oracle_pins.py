@@ -117,9 +117,8 @@ def test_oracle_matches_brute_force(seed, mode, n_th_frac, xmode):
     w.ndot = np.bincount(inv.reshape(-1), weights=w.ndot)
     w.cells = uc.astype(np.int32)
     n_th = n_th_frac * float(w.n_h.mean())
-    bmode = 1 if mode == 4 else mode
-    g, vis, cnt = bt.trace(w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, overlap_mode=bmode, n_th=n_th)
-    r = oracle.run_workload(w, record=400000, overlap_mode=bmode, n_th_cm3=n_th)
+    g, vis, cnt = bt.trace(w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, overlap_mode=mode, n_th=n_th)
+    r = oracle.run_workload(w, record=400000, overlap_mode=mode, n_th_cm3=n_th)
     v = r["visits"]
     assert v["total"] == len(vis)
     ov = sorted(zip(v["ray"].tolist(), v["seq"].tolist(), v["cell"].tolist()))
@@ -139,7 +138,8 @@ def test_oracle_matches_brute_force(seed, mode, n_th_frac, xmode):
 
 # ------------------------------------------------------------------ periodic boundaries (Sec. 2.5.1)
 
-@pytest.mark.parametrize("seed,mode,xmode", [(21, 0, "thin"), (22, 3, "mixed"), (23, 1, "patchy"), (24, 2, "mixed")])
+@pytest.mark.parametrize("seed,mode,xmode", [(21, 0, "thin"), (22, 3, "mixed"), (23, 1, "patchy"), (24, 2, "mixed"),
+                                             (25, 4, "thin"), (26, 5, "mixed")])
 def test_periodic_oracle_matches_brute_force(seed, mode, xmode):
     """Periodic boundaries: cells wrap, rays stop at travel distance sqrt(3) n
     (and do not split there); the brute force lists the same segments from
