@@ -1,0 +1,102 @@
+// Double-float arithmetic for the FP64 table march: a value is the unevaluated sum
+// h + l of two floats (about 48 significant bits), carried on the FP32 pipe, which on
+// GB300 is 64 times wider than the FP64 one. Built from error-free transformations:
+// Knuth's two-sum (TAOCP vol. 2, 4.2.2), Dekker's fast two-sum for |a| >= |b| and
+// Dekker's exact product (Dekker 1971), whose rounding error a fused multiply-add
+// returns exactly. Every operation is an explicit round-to-nearest intrinsic, so
+// nothing is contracted or reassociated by the compiler.
+#pragma once
+
+namespace nyx {
+
+struct dflt {
+    float h, l;
+};
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ dflt df_two_sum(const float a, const float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// s + e = a + b exactly when the exponent of a is at least that of b (Dekker)
+__device__ __forceinline__ dflt df_fast_two_sum(const float a, const float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// a b: the head product, its exact error and the two cross terms. The pair is left
+// unnormalised (|l| up to about 2^-22 |h|), which the next product or sum absorbs;
+// relative error below about 2^-45.
+__device__ __forceinline__ dflt df_mul(const dflt a, const dflt b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return {p, e};
+}
+
+// a - b for a >= b >= 0: heads by Knuth's two-sum, tails added to its error, renormalised
+__device__ __forceinline__ dflt df_sub(const dflt a, const dflt b)
+{
+    const dflt s = df_two_sum(a.h, -b.h);
+    const float t = __fadd_rn(s.l, __fsub_rn(a.l, b.l));
+    return df_fast_two_sum(s.h, t);
+}
+
+// A positive normal double as a double-float mantissa in [1, 2) and its unbiased exponent:
+// the head holds the leading 24 bits, the tail the remaining 29 rounded to 24 (error below
+// 2^-48 of the value). Zero and subnormals are outside its domain (callers test x > 0).
+__device__ __forceinline__ dflt df_mant(const double x, int& ex)
+{
+    const long long b = __double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    ex = (int)(hw >> 20) - 1023;
+    const float h = __uint_as_float(0x3f800000u | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    const float l = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), 2.220446049250313e-16f);   // 2^-52
+    return {h, l};
+}
+
+// A non-negative double below 2^127 as a double-float, head = its leading 24 bits. Values
+// below 2^-74 keep only the head (a relative error up to 2^-24 that the callers tolerate:
+// they pass optical depths, whose error there only enters the rate factor, and segment
+// lengths, which are never that short); values below 2^-126 read as 0.
+__device__ __forceinline__ dflt df_of(const double x)
+{
+    const long long b = __double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const int e = (int)(hw >> 20);
+    if (e < 897) return {0.f, 0.f};
+    const float h = __uint_as_float(((unsigned)(e - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    const float l = e >= 949 ? __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), __uint_as_float((unsigned)(e - 948) << 23))
+                             : 0.f;
+    return {h, l};
+}
+
+// x 2^e2 as a double, exactly: float to double by re-biasing the exponent and shifting the
+// mantissa (no FP64 instruction); zero and subnormal floats take the conversion.
+__device__ __forceinline__ double widen_scaled(const float x, const int e2)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned mag = u & 0x7fffffffu;
+    if (mag - 0x00800000u < 0x7f000000u) {              // normal and finite
+        const unsigned hi = ((mag >> 3) + ((unsigned)(896 + e2) << 20)) | (u & 0x80000000u);
+        return __hiloint2double((int)hi, (int)(u << 29));
+    }
+    if (mag == 0u) return 0.0;
+    const double d = (double)x;
+    return __longlong_as_double(__double_as_longlong(d) + (long long)e2 * (1LL << 52));
+}
+
+// (h + l) 2^e2 rounded to double (one FP64 addition)
+__device__ __forceinline__ double df_to_double(const dflt a, const int e2)
+{
+    return __dadd_rn(widen_scaled(a.h, e2), widen_scaled(a.l, e2));
+}
+
+}  // namespace nyx

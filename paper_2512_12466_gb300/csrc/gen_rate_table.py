@@ -1,0 +1,81 @@
+"""Taylor table of the Eq. 1 factor g(y) = (1 - e^{-y}) / y for the FP64 table march's
+double-float arithmetic; writes ``rate_table.h`` next to this script.
+
+On [0, 2) the factor is expanded about the left end y0 = j / 128 of each of 256 intervals,
+g(y0 + r) = sum_k c_k(y0) r^k with 0 <= r < 1/128, to degree 5. The coefficients are
+c_k(y0) = sum_{n >= k} C(n, k) (-1)^n y0^(n - k) / (n + 1)!, the k-th derivative of the power
+series g(y) = sum_n (-y)^n / (n + 1)! divided by k!, summed in 50-digit arithmetic. c_0..c_2 are
+stored as double-float pairs (head = the value rounded to float, tail = the rest rounded to
+float, about 48 bits together), c_3..c_5 as floats: on |r| < 2^-7 the terms c_3 r^3 and beyond
+are below 2e-8, so float precision there costs under 3e-15 of g. The truncation after r^5 is
+below c_6 r^6 < 2^-42 / 5040 = 5e-17.
+
+Each row: {c0 head, c0 tail, c1 head, c1 tail, c2 head, c2 tail, c3, c4, c5}, written as C99
+hexadecimal float literals, so the header holds the exact float values.
+
+    python paper_2512_12466_gb300/csrc/gen_rate_table.py
+"""
+import os
+import struct
+
+import mpmath as mp
+
+INTERVALS = 256          # over [0, 2): y0 = j / 128
+STEP = mp.mpf(1) / 128
+DEGREE = 5
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def f32(x) -> float:
+    """x rounded to the nearest float (through double; the tail absorbs the double rounding)."""
+    return struct.unpack("<f", struct.pack("<f", float(x)))[0]
+
+
+def coefficient(k: int, y0) -> mp.mpf:
+    """c_k(y0) = g^(k)(y0) / k! from the power series of g about 0."""
+    s = mp.mpf(0)
+    n = k
+    while True:
+        term = mp.binomial(n, k) * (-1) ** n * y0 ** (n - k) / mp.factorial(n + 1)
+        s += term
+        if n > k + 8 and abs(term) < mp.mpf(10) ** -45:
+            return s
+        n += 1
+
+
+def rows():
+    mp.mp.dps = 50
+    out = []
+    for j in range(INTERVALS):
+        y0 = j * STEP
+        c = [coefficient(k, y0) for k in range(DEGREE + 1)]
+        row = []
+        for k in range(3):
+            h = f32(c[k])
+            row += [h, f32(c[k] - mp.mpf(h))]
+        row += [f32(c[3]), f32(c[4]), f32(c[5])]
+        out.append(row)
+    return out
+
+
+def write(path=os.path.join(HERE, "rate_table.h")):
+    lines = [
+        "// Generated by gen_rate_table.py: Taylor coefficients of g(y) = (1 - e^{-y}) / y about",
+        "// y0 = j / 128, j = 0..255 (Eq. 1 rate factor of the FP64 table march). Row j:",
+        "// {c0 head, c0 tail, c1 head, c1 tail, c2 head, c2 tail, c3, c4, c5}.",
+        "#pragma once",
+        "",
+        "namespace nyx {",
+        f"constexpr int kRateIntervals = {INTERVALS};",
+        "constexpr int kRateCoefs = 9;",
+        f"__device__ const float kRateTable[{INTERVALS} * 9] = {{",
+    ]
+    for r in rows():
+        lines.append("    " + ", ".join(v.hex() if v != 0 else "0x0p+0" for v in r) + ",")
+    lines += ["};", "}  // namespace nyx", ""]
+    with open(path, "w") as f:
+        f.write("\n".join(lines))
+
+
+if __name__ == "__main__":
+    write()

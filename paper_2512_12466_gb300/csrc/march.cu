@@ -24,6 +24,8 @@
 #include <cstdint>
 
 #include "rt_internal.h"
+#include "dfloat.h"
+#include "rate_table.h"
 
 namespace nyx {
 namespace {
@@ -1165,6 +1167,274 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
     return split;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 table march in double-float arithmetic. GB300's FP64 unit runs at 1/64 of its FP32
+// rate, and only two FP64 operations per segment decide anything: dtau = kap ds and
+// tau += dtau, whose result is compared with tau_max. Both stay IEEE FP64, so the bookkeeping
+// (rays, splits, segments, terminations, visits) is that of the plain FP64 march bit for bit.
+// What only feeds the fields and the photon ledger runs on the FP32 pipe in double-float
+// pairs (dfloat.h, about 48 significant bits):
+//   - the Eq. 1 factor g(dtau) = (1 - e^{-dtau}) / dtau below dtau = 2, from the Taylor table of
+//     rate_table.h;
+//   - the ray's photon budget, carried as Q = P m_G 2^64, where G = m_G 2^e_G is the source's
+//     rate per unit budget and cell of path (the factor 2^64 keeps Q far inside the float
+//     range): a segment absorbs Q dtau g of it and deposits the rate Q g ds 2^(e_G - 64), which
+//     is Eq. 1 with V_box, P G ds g;
+//   - the Eqs. 5-8 shares and the Eq. 8 ratio kap / kap' (a reciprocal and one correction).
+// Each deposit is rounded to double once (one FP64 addition) for its atomic add. From
+// dtau = 2 on (an opaque cell, where most of the budget goes at once) the segment is evaluated
+// in FP64 with expm1 and a division, as in the FP64 form of march_ray_table.
+
+constexpr int kRateStride = 12;     // floats per row of the rate table in shared memory
+
+// g(x) for 0 <= x < 2 from row j = floor(128 x) of the Taylor table:
+// c0 + r (c1 + r (c2 + r (c3 + r (c4 + r c5)))) with r = x - j/128 in [0, 1/128); the three
+// inner terms in float (below 2e-8 of g together), the three outer ones in double-float.
+__device__ __forceinline__ dflt rate_factor(const float* __restrict__ tab, const dflt x)
+{
+    const int j = min(__float2int_rz(__fmul_rn(x.h, 128.f)), kRateIntervals - 1);
+    const float4 A = *reinterpret_cast<const float4*>(tab + j * kRateStride);       // c0 c0' c1 c1'
+    const float4 B = *reinterpret_cast<const float4*>(tab + j * kRateStride + 4);   // c2 c2' c3 c4
+    const float c5 = tab[j * kRateStride + 8];
+    // r = x - j/128: the head difference is exact (Sterbenz for j >= 1; nothing is subtracted
+    // for j = 0); with x's tail it is renormalised, so that the cross terms below stay small
+    const dflt r = df_two_sum(__fsub_rn(x.h, __fmul_rn(__int2float_rn(j), 0.0078125f)), x.l);
+    const float rh = r.h, rl = r.l;
+    const float t = __fmaf_rn(__fmaf_rn(c5, rh, B.w), rh, B.z);
+    // u = c2 + r t
+    const dflt u = df_fast_two_sum(B.x, __fmaf_rn(rh, t, __fmaf_rn(rl, t, B.y)));
+    // v = c1 + r u
+    float p = __fmul_rn(rh, u.h);
+    float pe = __fmaf_rn(rh, u.h, -p);
+    pe = __fmaf_rn(rh, u.l, pe);
+    pe = __fmaf_rn(rl, u.h, pe);
+    dflt v = df_fast_two_sum(A.z, p);
+    v.l = __fadd_rn(v.l, __fadd_rn(pe, A.w));
+    // g = c0 + r v
+    p = __fmul_rn(rh, v.h);
+    pe = __fmaf_rn(rh, v.h, -p);
+    pe = __fmaf_rn(rh, v.l, pe);
+    pe = __fmaf_rn(rl, v.h, pe);
+    dflt g = df_fast_two_sum(A.x, p);
+    g.l = __fadd_rn(g.l, __fadd_rn(pe, A.y));
+    return g;
+}
+
+// d 2^e for a double d >= 0, by its exponent bits (d = 0 stays 0)
+__device__ __forceinline__ double scale2(const double d, const int e)
+{
+    const long long b = __double_as_longlong(d);
+    return b == 0 ? d : __longlong_as_double(b + (long long)e * (1LL << 52));
+}
+
+// march_ray_table for FP64 physics (gray), in double-float arithmetic as described above.
+template <bool kHash>
+__device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, const float* __restrict__ rtab,
+                                                   const GeomLevel& GL, unsigned* err, const int l,
+                                                   const uint32_t si, const uint32_t pix, const double P0,
+                                                   double tau, const SrcEntry& se, const int4 dv, Tally& T,
+                                                   double& oP, double& otau)
+{
+    using I = Ieee<double>;
+    using TE = TableEntry<double>;
+    using E = typename TE::E;
+    const int n = V.n;
+    const int s0 = dv.x < 0 ? -1 : 1, s1 = dv.y < 0 ? -1 : 1, s2 = dv.z < 0 ? -1 : 1;
+    int i0 = se.cx, i1 = se.cy, i2 = se.cz;
+    if (l > 0) {                    // the start cell: crossings done at the start sphere
+        const long long rq_start = V.rq << (l - 1);
+        i0 += s0 * (int)((rq_start * (unsigned)abs(dv.x) + kB) >> (S + F));
+        i1 += s1 * (int)((rq_start * (unsigned)abs(dv.y) + kB) >> (S + F));
+        i2 += s2 * (int)((rq_start * (unsigned)abs(dv.z) + kB) >> (S + F));
+    }
+    const bool periodic = V.rs != 0;
+    const bool split_end = !periodic || (V.rq << l) < V.rs;
+    if (periodic) {
+        i0 = wrapn(i0, n);
+        i1 = wrapn(i1, n);
+        i2 = wrapn(i2, n);
+    }
+    const double ph = se.ph;
+    const double taumax = V.tau_max;
+    const unsigned long long rbase =
+        (kHash && V.hash) ? mix64(((unsigned long long)(si - V.src_off) << 36) | ((unsigned long long)l << 31) | pix) : 0ULL;
+    const bool face = V.overlap_mode == RT_OVERLAP_ARC || V.overlap_mode == RT_OVERLAP_CONSERVATIVE ||
+                      V.overlap_mode == RT_OVERLAP_NAIVE;
+    const bool corr = V.overlap_mode != RT_OVERLAP_NONE;
+    const long long nn = (long long)n * n;
+    ++T.rays;
+    if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
+        ++T.esc;
+        T.escph += ph * P0;
+        return false;
+    }
+    // G = m_G 2^e_G; the budget Q = P m_G 2^64, and 1 / m_G to read P back
+    int eG;
+    const dflt mG = df_mant(se.gd, eG);
+    const int e_dep = eG - 64;
+    dflt Q = df_mul(df_of(scale2(P0, 64)), mG);
+    dflt mGi;
+    mGi.h = __frcp_rn(mG.h);
+    mGi.l = __fmul_rn(__fmaf_rn(-mG.l, mGi.h, __fmaf_rn(-mG.h, mGi.h, 1.0f)), mGi.h);
+    auto remaining = [&]() -> double { return df_to_double(df_mul(Q, mGi), -64); };
+
+    const E* col = TE::ent(GL) + GL.row0[pix >> 5] * 32 + (pix & 31);
+    E e = col[0];
+    int cell = (i2 * n + i1) * n + i0;
+    double kcur = V.kap[cell];
+    unsigned seq = 0;
+    bool split = false;
+    for (;;) {
+        // the next entry and the next cell's kappa are requested before this segment's work
+        const unsigned fl = TE::flags(e);
+        const bool last = (fl >> 31) != 0u;
+        const E en = last ? TE::none() : col[(unsigned long long)(seq + 1) * 32];
+        const unsigned steps = (fl >> 24) & 7u;
+        int ni0 = (steps & 1u) ? i0 + s0 : i0;
+        int ni1 = (steps & 2u) ? i1 + s1 : i1;
+        int ni2 = (steps & 4u) ? i2 + s2 : i2;
+        if (periodic) {
+            ni0 = wrap1(ni0, n);
+            ni1 = wrap1(ni1, n);
+            ni2 = wrap1(ni2, n);
+        }
+        const bool next_in =
+            periodic || ((unsigned)ni0 < (unsigned)n && (unsigned)ni1 < (unsigned)n && (unsigned)ni2 < (unsigned)n);
+        const int ncell = (ni2 * n + ni1) * n + ni0;
+        const double knext = (steps && next_in) ? V.kap[ncell] : 0.0;
+        const bool near = corr && ((fl >> 27) & 1u);
+        int c2 = -1;
+        if (face && near) {
+            const int ax = (int)((fl >> 28) & 3u);
+            const int step = ((fl >> 30) & 1u) ? 1 : -1;
+            const int jc = pick3(ax, i0, i1, i2) + step;
+            if (periodic) {
+                const int jw = wrap1(jc, n);
+                c2 = cell + (jw - (jc - step)) * (ax == 0 ? 1 : (ax == 1 ? n : (int)nn));
+            } else if ((unsigned)jc < (unsigned)n) {
+                c2 = cell + step * (ax == 0 ? 1 : (ax == 1 ? n : (int)nn));
+            }
+        }
+        const double kn_raw = c2 >= 0 ? V.kap[c2] : 0.0;
+        // ---- the two deciding FP64 operations: dtau = kap ds here, tau += dtau below
+        const double ds = TE::ds(e);
+        const double kap = I::mag(kcur);
+        const double dtau = I::mul(kap, ds);
+        // ---- Eq. 1: w = Q g ds, the segment's rate before the Eq. 5-8 share (double-float),
+        // or its FP64 value wd for an opaque segment
+        dflt w = {0.f, 0.f};
+        double wd = 0.0;
+        const bool opaque = I::pos(kap) && !I::lt(dtau, 2.0);
+        if (!opaque) {
+            const dflt dsf = df_of(ds);
+            if (I::pos(kap)) {
+                const dflt x = df_of(dtau);
+                const dflt u = df_mul(Q, rate_factor(rtab, x));
+                Q = df_sub(Q, df_mul(u, x));
+                w = df_mul(u, dsf);
+            } else {
+                w = df_mul(Q, dsf);                       // optically thin limit
+            }
+        } else {
+            const double Qd = df_to_double(Q, 0);
+            const double aQ = Qd * (-expm1(-dtau));
+            wd = aQ / kap;
+            Q = df_of(Qd - aQ);
+        }
+        // ---- Eqs. 5-8: the cell's deposit and the neighbour's
+        double dep = 0.0, dep2 = 0.0;
+        int nbcell = -1;
+        const int mode = V.overlap_mode;
+        bool keep_all = !near;                           // f = 1
+        bool squared = false, second = false;
+        if (near) {
+            if (mode == RT_OVERLAP_LINEAR) {
+            } else if (mode == RT_OVERLAP_SQUARED) {
+                squared = true;
+            } else {
+                const double kn = I::mag(kn_raw);
+                const bool elig = c2 >= 0 && ((mode == RT_OVERLAP_ARC) ? I::pos(kn) : (!I::neg(kn_raw) && I::pos(kn)));
+                second = elig;
+                keep_all = !elig && mode != RT_OVERLAP_NAIVE;   // naive threshold: the Eq. 5 share regardless
+            }
+        }
+        if (keep_all) {
+            dep = opaque ? scale2(wd, e_dep) : df_to_double(w, e_dep);
+        } else {
+            const double fd = TE::f(e);
+            if (opaque) {
+                dep = scale2(fd * (squared ? fd * wd : wd), e_dep);
+                if (second) dep2 = scale2(((1.0 - fd) * wd) * (kap / I::mag(kn_raw)), e_dep);
+            } else {
+                const dflt f = df_of(fd);
+                const dflt fw = df_mul(f, w);
+                dep = df_to_double(squared ? df_mul(f, fw) : fw, e_dep);
+                if (second && I::pos(kap)) {       // kap = 0 (an ionized cell) sends 0 to c'
+                    // Eq. 8: (1 - f) w kap / kap', the ratio of the mantissas by a float reciprocal
+                    // and one correction, the exponents applied when rounding to double
+                    int ek, en;
+                    const dflt mk = df_mant(kap, ek), mn = df_mant(I::mag(kn_raw), en);
+                    const float r0 = __frcp_rn(mn.h);
+                    const float q0 = __fmul_rn(mk.h, r0);
+                    const float p = __fmul_rn(mn.h, q0);
+                    const float pe = __fmaf_rn(mn.h, q0, -p);
+                    const float rho = __fmaf_rn(-q0, mn.l, __fadd_rn(__fsub_rn(__fsub_rn(mk.h, p), pe), mk.l));
+                    const dflt ratio = {q0, __fmul_rn(rho, r0)};
+                    const dflt om = {__fsub_rn(1.0f, f.h), -f.l};
+                    dep2 = df_to_double(df_mul(df_mul(om, w), ratio), e_dep + ek - en);
+                }
+            }
+        }
+        if (second) nbcell = c2;
+        atomicAdd(&V.gamma[cell], dep);
+        if (nbcell >= 0) {
+            atomicAdd(&V.gamma[nbcell], dep2);
+            ++T.sec;
+        }
+        tau = I::add(tau, dtau);
+        if (kHash && V.hash) T.hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
+        ++seq;
+        if (!I::lt(tau, taumax)) {             // photons spent
+            ++T.dtau;
+            T.dropph += ph * remaining();
+            break;
+        }
+        if (!steps) {                    // the segment ended on the end sphere
+            if (!split_end) {            // travelled sqrt(3) L_box (Sec. 2.5.1)
+                ++T.esc;
+                T.escph += ph * remaining();
+            } else if (l + 1 > V.level_max) {
+                ++T.dlev;
+                T.dropph += ph * remaining();
+            } else {
+                ++T.split;
+                split = true;
+                oP = remaining();
+                otau = tau;
+            }
+            break;
+        }
+        if (!next_in) {
+            ++T.esc;
+            T.escph += ph * remaining();
+            break;
+        }
+        if (last) {                      // cannot happen: a table ends where every grid is left
+            atomicOr(err, kErrGeometry);
+            break;
+        }
+        i0 = ni0;
+        i1 = ni1;
+        i2 = ni2;
+        cell = ncell;
+        kcur = knext;
+        e = en;
+    }
+    T.seg += seq;
+    T.abs += ph * (P0 - remaining());
+    return split;
+}
+
 // Load child j of the level-l parents (level 0: ray j of the emission, 12 per source).
 template <class R>
 __device__ __forceinline__ void load_ray(int l, long long j, const RayBuf<R>& in, uint32_t& si, uint32_t& pix, R& P,
@@ -1267,15 +1537,17 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
     V.src_off = 0;
     V.rs = A.rs;
     V.spec = A.spec;
+    // children of this launch: as given, or bounded by the parents the previous level counted
+    const long long c1 = A.in_count ? min((long long)A.c1, (long long)A.c0 + 4LL * (long long)*A.in_count) : (long long)A.c1;
     Tally T;
     T.clear();
-    for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
+    for (long long base = A.c0 + gwarp * 32; base < c1; base += nwarp * 32) {
         const long long j = base + lane;
         bool split = false;
         uint32_t si = 0, pix = 0;
         R oP = 0, otau = 0;
         float ocP = 0.f, octau = 0.f;
-        if (j < A.c1) {
+        if (j < c1) {
             R P, tau, cP, ctau;
             load_ray<R>(l, j, A.in, si, pix, P, tau, cP, ctau);
             split = march_ray<R, kHash, kFreq>(V, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T, oP, otau,
@@ -1314,19 +1586,36 @@ __global__ void __launch_bounds__(256, TableOccupancy<R>::blocks) march_table_ke
     V.src_off = 0;
     V.rs = A.rs;
     V.spec = A.spec;
+    // children of this launch: as given, or bounded by the parents the previous level counted
+    const long long c1 = A.in_count ? min((long long)A.c1, (long long)A.c0 + 4LL * (long long)*A.in_count) : (long long)A.c1;
     Tally T;
     T.clear();
-    for (long long base = A.c0 + gwarp * 32; base < A.c1; base += nwarp * 32) {
+    // FP64 gray march: the Eq. 1 rate table in shared memory (rows padded to 12 floats, 16-byte aligned)
+    constexpr bool kDf = sizeof(R) == 8 && !kFreq;
+    __shared__ __align__(16) float rtab[kDf ? kRateIntervals * kRateStride : 4];
+    if constexpr (kDf) {
+        for (int i = threadIdx.x; i < kRateIntervals * kRateStride; i += blockDim.x) {
+            const int row = i / kRateStride, c = i - row * kRateStride;
+            rtab[i] = c < kRateCoefs ? kRateTable[row * kRateCoefs + c] : 0.f;
+        }
+        __syncthreads();
+    }
+    for (long long base = A.c0 + gwarp * 32; base < c1; base += nwarp * 32) {
         const long long j = base + lane;
         bool split = false;
         uint32_t si = 0, pix = 0;
         R oP = 0, otau = 0;
         float ocP = 0.f, octau = 0.f;
-        if (j < A.c1) {
+        if (j < c1) {
             R P, tau, cP, ctau;
             load_ray<R>(l, j, A.in, si, pix, P, tau, cP, ctau);
-            split = march_ray_table<R, kHash, kFreq>(V, GL, &A.st->err, l, si, pix, P, tau, cP, ctau, A.src[si], A.dirs[pix], T,
-                                           oP, otau, ocP, octau);
+            if constexpr (kDf) {
+                split = march_ray_table_df<kHash>(V, rtab, GL, &A.st->err, l, si, pix, P, tau, A.src[si], A.dirs[pix],
+                                                  T, oP, otau);
+            } else {
+                split = march_ray_table<R, kHash, kFreq>(V, GL, &A.st->err, l, si, pix, P, tau, cP, ctau, A.src[si],
+                                                         A.dirs[pix], T, oP, otau, ocP, octau);
+            }
         }
         append_split<R>(split, si, pix, oP, otau, ocP, octau, A.out, A.out_count, &A.st->err);
     }

@@ -151,11 +151,12 @@ def test_parity_fp32(nyx, case, walk):
 def test_geometry_table_equals_walk(nyx, case, prec):
     """The table-driven march and the walked one: the same bookkeeping bit for
     bit, the same fields to rounding (FP32: f may be contracted differently;
-    FP64: every deposit is the same IEEE value, so only the order of the
-    atomic additions differs)."""
+    FP64: the table march evaluates what decides nothing in double-float
+    arithmetic, about 1e-14 from the walk's IEEE FP64, so both are held to the
+    FP64 bar of 1e-12)."""
     n, k, seed, xm, dxc, mode, tmax, lmax, nmin = case
     w = I.random_small(n, k, seed=seed, x_mode=xm, box_cm=n * dxc)
-    tol = 1e-14 if prec == 0 else 1e-6
+    tol = 1e-12 if prec == 0 else 1e-6
     kw = dict(precision=prec, overlap_mode=mode, tau_max=tmax, level_max=lmax, n_min_ray=nmin,
               n_th_cm3=0.3 * float(w.n_h.mean()))
     a = run_gpu(nyx, w.n_h, w.x_ion, w.cells, w.ndot, w.box_cm, **kw)
