@@ -333,6 +333,57 @@ def bench_config4(nyx, torch):
     return out
 
 
+def bench_beyond_l2(nyx, torch, n_sources: int = 64):
+    """The 256^3 thin box (40 Mpc/h, sigma_ln = 1.5, x_HI = 1e-4) with its first 64 sources: kappa
+    and Gamma (67 + 134 MB with FP32 physics, 134 + 134 MB with FP64) exceed the 129 MB L2, so
+    the march's own bytes come from HBM. Both precisions, one untimed step that builds the
+    geometry tables, then timed steps with L2 flushed; the roofline of the march kernels in
+    algorithmic bytes, the table bytes this box added and which levels read tables or walked."""
+    w = I.thin256(n_sources)
+    n_th = 0.01 * float(w.n_h.mean())
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).to(dev)
+    d_nh, d_x, d_c, d_nd = d(w.n_h), d(w.x_ion), d(w.cells), d(w.ndot)
+    n3 = w.n ** 3
+    g = torch.empty(n3, dtype=torch.float64, device=dev)
+    h = torch.empty_like(g)
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    hbm, _ = load_peaks()
+    out = {"workload": f"256^3 lognormal box (40 Mpc/h, sigma_ln 1.5), thin (x_HI=1e-4), first {n_sources} of "
+                       "config 4's power-law sources",
+           "l2_bytes": 129 << 20}
+    for prec, label in ((nyx.RT_FP32, "fp32"), (nyx.RT_FP64, "fp64")):
+        before = nyx.rt_geometry_table_bytes(torch.cuda.current_device())
+        s = nyx.Solver(w.n, w.box_cm, precision=prec, n_th_cm3=n_th, n_min_ray=4.0, tau_max=30.0)
+        s.set_fields(d_nh, d_x)
+        s.add_sources(d_c, d_nd)
+        s.step(0.0, g, h)
+        torch.cuda.synchronize()
+        built = nyx.rt_geometry_table_bytes(torch.cuda.current_device()) - before
+        ms, stats = time_steps(s, 2, flush, g, h, torch)
+        s.close()
+        st = stats[-1]
+        march_ms = sum(x["ms_march"] for x in stats) / len(stats)
+        segs = sum(st["segments"])
+        alg = algorithmic_bytes(st, prec)
+        levels = [lv for lv in range(len(st["rays"])) if st["rays"][lv]]
+        out[label] = {
+            "value": segs / (statistics.mean(ms) / 1e3), "unit": "segments/s",
+            "march_segments_per_s": segs / (march_ms / 1e3), "ms_per_step": statistics.mean(ms),
+            "march_ms_per_step": march_ms, "segments_per_step": segs, "secondary_per_step": sum(st["secondary"]),
+            "kappa_gamma_bytes": n3 * ((4 if prec == nyx.RT_FP32 else 8) + 8),
+            "roofline": {"bound": "hbm", "achieved": alg / (march_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (march_ms / 1e3) / 1e9 / hbm,
+                         "algorithmic_bytes_per_step": alg},
+            "table_levels": [lv for lv in levels if (st["table_levels"] >> lv) & 1],
+            "walked_levels": [lv for lv in levels if not (st["table_levels"] >> lv) & 1],
+            "segments_by_level": [st["segments"][lv] for lv in levels],
+            "geometry_table_bytes_added": built,
+        }
+    out["geometry_table_bytes_total"] = nyx.rt_geometry_table_bytes(torch.cuda.current_device())
+    return out
+
+
 def bench_spectrum(nyx, torch, w, n_th):
     """Eq. 1 over a blackbody spectrum (1e5 K) on the same box, FP32 and FP64 (geometry tables), a
     timed step after one that builds the tables, beside the gray rate: throughput and the photons
@@ -690,6 +741,7 @@ def run_nyx(args, world, rank, local):
         line["overlap_modes"] = bench_overlap_modes(nyx, torch, w, n_th)
         line["spectrum"] = bench_spectrum(nyx, torch, w, n_th)
         line["config4"] = bench_config4(nyx, torch)
+        line["beyond_l2"] = bench_beyond_l2(nyx, torch)
     if not args.no_batched:
         line["batched"] = {"neutral": bench_batched(nyx, torch, "neutral", steps=5, tune=True),
                            "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 27,

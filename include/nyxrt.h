@@ -145,6 +145,9 @@ typedef struct rt_stats {
     double ms_march;           /* sum of the march kernels' own durations in the last trace
                                   (CUDA events around each launch, on the handle's stream) */
     int64_t march_launches;    /* march kernel launches in the last trace */
+    int64_t table_levels;      /* bit l set: level l's march read its cells from the per-device
+                                  geometry tables in the last trace; clear: it walked its rays
+                                  (or did not run) */
 } rt_stats;
 
 typedef struct rt_handle rt_handle;
@@ -215,15 +218,19 @@ int rt_get_sources(rt_handle* h, int32_t* cells_out, double* ndot_out, int64_t c
 /* Checkpoint, to resume a run later or elsewhere: write the handle's configuration, its fields
  * (n_H and the current ionized fraction x, which rt_step advances under chem_iterate) and the
  * sources added since the last rt_clear_sources to the file `path` (binary, read back by rt_load).
- * A handle loaded from it steps exactly as this one would: the same bookkeeping bit for bit and
- * the same fields. RT_ESTATE before rt_set_fields; RT_EINVAL if the file cannot be written.
- * Synchronises the handle's stream. */
+ * A handle loaded from it steps as this one would: the same bookkeeping bit for bit, and fields
+ * that agree to the order of the FP64 deposit atomics (about 1e-14 relative); under chem_iterate
+ * the iteration count may differ by one where the convergence test sits at its tolerance.
+ * RT_ESTATE before rt_set_fields; RT_ENOMEM if the host buffers cannot be allocated; RT_EINVAL if
+ * the file cannot be written. Synchronises the handle's stream. */
 int rt_save(rt_handle* h, const char* path);
 
 /* Create a handle on `cuda_stream` (as rt_create) from a file rt_save wrote, holding its
- * configuration, fields and sources. RT_EINVAL if the file is missing, truncated, of another
- * format version or holds an invalid configuration (rt_last_error(NULL) says which); otherwise
- * the codes of rt_create, rt_set_fields and rt_add_sources. */
+ * configuration, fields and sources. RT_EINVAL if the file is missing, truncated or longer than
+ * its header's counts say, of another format version or holds an invalid configuration
+ * (rt_last_error(NULL) says which): the counts are checked against the file's size before any
+ * buffer is sized from them. RT_ENOMEM if the host buffers cannot be allocated; otherwise the
+ * codes of rt_create, rt_set_fields and rt_add_sources. */
 int rt_load(const char* path, void* cuda_stream, rt_handle** out);
 
 /* Free the handle and its device memory. NULL is accepted. */

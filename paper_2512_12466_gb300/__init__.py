@@ -62,7 +62,7 @@ class rt_stats(C.Structure):
         ("emitted_ph", C.c_double), ("absorbed_ph", C.c_double), ("escaped_ph", C.c_double),
         ("dropped_ph", C.c_double), ("deposited_ph", C.c_double), ("chem_residual", C.c_double),
         ("ms_trace", C.c_double), ("ms_step", C.c_double), ("ms_march", C.c_double),
-        ("march_launches", C.c_int64),
+        ("march_launches", C.c_int64), ("table_levels", C.c_int64),
     ]
 
 

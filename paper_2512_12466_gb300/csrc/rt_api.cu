@@ -333,8 +333,10 @@ int configure(rt_handle* h, const rt_config* cfg, std::string& why);
 bool valid_config(const rt_config* c, std::string& why);
 
 // Host-side fault injection for tests: with NYXRT_FAULT_ALLOC=k (k >= 1) in the environment, the k-th
-// device allocation the library makes through dalloc in this process fails as if the device were out
-// of memory (no device work is involved; every caller must return RT_ENOMEM and stay usable).
+// handle allocation the library makes through dalloc in this process fails as if the device were out
+// of memory (no device work is involved; every caller must return RT_ENOMEM and stay usable). With
+// NYXRT_FAULT_ALLOC_TRACE set, every dalloc call writes its ordinal to stderr ("nyxrt-dalloc k"), so
+// a test can find which ordinals a stage makes before it injects one.
 long long fault_alloc_at()
 {
     static const long long k = [] {
@@ -343,6 +345,11 @@ long long fault_alloc_at()
     }();
     return k;
 }
+bool fault_alloc_trace()
+{
+    static const bool t = std::getenv("NYXRT_FAULT_ALLOC_TRACE") != nullptr;
+    return t;
+}
 std::atomic<long long> g_alloc_count{0};
 
 // Handle memory is stream-ordered: allocating or freeing it never waits for
@@ -350,9 +357,16 @@ std::atomic<long long> g_alloc_count{0};
 cudaError_t dalloc(rt_handle* h, void** p, size_t bytes)
 {
     const long long k = fault_alloc_at();
-    if (k > 0 && ++g_alloc_count == k) {
-        *p = nullptr;
-        return cudaErrorMemoryAllocation;
+    if (k > 0 || fault_alloc_trace()) {
+        const long long ord = ++g_alloc_count;
+        if (fault_alloc_trace()) {
+            std::fprintf(stderr, "nyxrt-dalloc %lld\n", ord);
+            std::fflush(stderr);
+        }
+        if (ord == k) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
     }
     return cudaMallocAsync(p, bytes, h->stream);
 }
@@ -503,6 +517,7 @@ int run_level(rt_handle* h, int level, int64_t nparents)
         RT_CUDA(h, cudaEventRecord(h->ev[5], h->stream), "event");
         h->launches++;
         h->march_launches++;
+        if (table) h->table_levels |= int64_t(1) << level;
         RT_CUDA(h, cudaMemcpyAsync(h->h_count + level + 1, h->d_count + level + 1, sizeof(unsigned long long),
                                    cudaMemcpyDeviceToHost, h->stream), "counter read");
         RT_CUDA(h, cudaMemcpyAsync(h->h_i32, &h->d_st->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream),
@@ -535,6 +550,7 @@ int trace(rt_handle* h, const double* xuse)
     RT_LAUNCHED(h, "kappa launch");
     h->launches++;
     h->march_launches = 0;
+    h->table_levels = 0;
     h->ms_march = 0.0;
     RT_CUDA(h, cudaEventRecord(h->ev[1], h->stream), "event");
     int rc = h->cfg.precision == RT_FP32 ? run_level<float>(h, 0, 0) : run_level<double>(h, 0, 0);
@@ -979,8 +995,16 @@ int rt_save(rt_handle* h, const char* path)
     if (!h->fields_set) return fail(h, RT_ESTATE, "rt_set_fields has not been called");
     DeviceGuard g(h->device);
     const int64_t nc = h->ncell, ns = h->nsrc;
-    std::vector<double> nh((size_t)nc), x((size_t)nc), nd((size_t)ns);
-    std::vector<int32_t> cells((size_t)(3 * ns));
+    std::vector<double> nh, x, nd;
+    std::vector<int32_t> cells;
+    try {
+        nh.resize((size_t)nc);
+        x.resize((size_t)nc);
+        nd.resize((size_t)ns);
+        cells.resize((size_t)(3 * ns));
+    } catch (const std::bad_alloc&) {
+        return fail(h, RT_ENOMEM, "out of host memory for the checkpoint buffers");
+    }
     RT_CUDA(h, cudaMemcpyAsync(nh.data(), h->d_nh, 8 * (size_t)nc, cudaMemcpyDeviceToHost, h->stream), "checkpoint copy");
     RT_CUDA(h, cudaMemcpyAsync(x.data(), h->d_x, 8 * (size_t)nc, cudaMemcpyDeviceToHost, h->stream), "checkpoint copy");
     if (ns > 0) {
@@ -1013,28 +1037,42 @@ int rt_load(const char* path, void* cuda_stream, rt_handle** out)
     if (!path) { g_create_error = "path is NULL"; return RT_EINVAL; }
     FILE* f = std::fopen(path, "rb");
     if (!f) { g_create_error = std::string("cannot open ") + path; return RT_EINVAL; }
+    // the file's size first: every count the header claims is checked against it before any
+    // buffer is sized from that count
+    long long fsize = -1;
+    if (std::fseek(f, 0, SEEK_END) == 0) fsize = (long long)std::ftell(f);
+    std::rewind(f);
     char magic[8];
     uint32_t hdr[2] = {0, 0};
     rt_config cfg{};
     int64_t nc = -1, ns = -1;
-    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+    const long long head = 8 + 8 + (long long)sizeof(rt_config) + 8;    // magic, version, config, cell count
+    bool ok = fsize >= head && std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
               std::fread(hdr, 4, 2, f) == 2 && hdr[0] == kCkptVersion && hdr[1] == sizeof(rt_config) &&
               std::fread(&cfg, sizeof(rt_config), 1, f) == 1 && std::fread(&nc, 8, 1, f) == 1 &&
               cfg.n >= 1 && cfg.n <= 1024 && nc == (int64_t)cfg.n * cfg.n * cfg.n;
+    const long long at_ns = head + 16 * (long long)nc;                  // n_H and x, then the source count
+    ok = ok && fsize >= at_ns + 8 && std::fseek(f, (long)at_ns, SEEK_SET) == 0 && std::fread(&ns, 8, 1, f) == 1 &&
+         ns >= 0 && ns <= (int64_t(1) << 30) && fsize == at_ns + 8 + 20 * (long long)ns;
     std::vector<double> nh, x, nd;
     std::vector<int32_t> cells;
     if (ok) {
-        nh.resize((size_t)nc);
-        x.resize((size_t)nc);
-        ok = std::fread(nh.data(), 8, (size_t)nc, f) == (size_t)nc && std::fread(x.data(), 8, (size_t)nc, f) == (size_t)nc &&
-             std::fread(&ns, 8, 1, f) == 1 && ns >= 0 && ns <= (int64_t(1) << 30);
+        try {
+            nh.resize((size_t)nc);
+            x.resize((size_t)nc);
+            cells.resize((size_t)(3 * ns));
+            nd.resize((size_t)ns);
+        } catch (const std::bad_alloc&) {
+            std::fclose(f);
+            g_create_error = "out of host memory reading " + std::string(path);
+            return RT_ENOMEM;
+        }
+        ok = std::fseek(f, (long)head, SEEK_SET) == 0 && std::fread(nh.data(), 8, (size_t)nc, f) == (size_t)nc &&
+             std::fread(x.data(), 8, (size_t)nc, f) == (size_t)nc && std::fseek(f, (long)(at_ns + 8), SEEK_SET) == 0;
     }
-    if (ok && ns > 0) {
-        cells.resize((size_t)(3 * ns));
-        nd.resize((size_t)ns);
+    if (ok && ns > 0)
         ok = std::fread(cells.data(), 4, (size_t)(3 * ns), f) == (size_t)(3 * ns) &&
              std::fread(nd.data(), 8, (size_t)ns, f) == (size_t)ns;
-    }
     std::fclose(f);
     if (!ok) { g_create_error = std::string(path) + " is not a complete checkpoint of this library"; return RT_EINVAL; }
     rt_handle* h = nullptr;
@@ -1168,6 +1206,7 @@ int rt_step(rt_handle* h, double dt_s, double* gamma_out, double* heat_out, int 
         st->ms_step = ms;
         st->ms_march = h->ms_march;
         st->march_launches = h->march_launches;
+        st->table_levels = h->table_levels;
     }
     return RT_OK;
 }

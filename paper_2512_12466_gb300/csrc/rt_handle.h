@@ -128,6 +128,7 @@ struct rt_handle {
     bool sticky = false;
     int launches = 0;
     int march_launches = 0;
+    int64_t table_levels = 0;        // bit l: level l read the geometry tables in the last trace
     std::string err;
     // source stage run ahead of a batch (handle_prepare_sources)
     bool src_ready = false;

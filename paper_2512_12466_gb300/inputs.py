@@ -178,6 +178,16 @@ def config4(n_sources: int = 32768) -> Workload:
     return cosmo_box(256, 40.0, 1.5, n_sources, config=4, x_mode="patchy")
 
 
+def thin256(n_sources: int = 64) -> Workload:
+    """256^3, 40 Mpc/h, sigma_ln = 1.5 (the config-4 density field) in the optically thin
+    variant (uniform residual x_HI = 1e-4), with the first n_sources of config 4's power-law
+    sources: the box whose kappa and Gamma (67 + 134 MB in FP32 physics) exceed the L2 cache."""
+    w = cosmo_box(256, 40.0, 1.5, 32768, config=4, x_mode="thin")
+    w.cells, w.ndot = w.cells[:n_sources].copy(), w.ndot[:n_sources].copy()
+    w.name = f"cosmo_256_{n_sources}_thin"
+    return w
+
+
 def batch_solves(count: int = 64, config: int = 3, x_mode: str = "thin",
                  sizes=(32, 64, 96, 128), max_sources: int = 4096):
     """Batched workload: grid sizes uniform over `sizes`, source counts

@@ -10,7 +10,9 @@ the first step. Prints one line per step (segments, march time, launches).
 --merge adds the Alg. 3 kernels (the 256^3 patchy box with its first k of
 32768 sources, f_req = 0.5), --chem the C2-Ray iteration (Table 1 Test A over
 1 Myr), --batch K the persistent batched kernel over the first K solves of
-the 64-solve uneven mix (one direct run).
+the 64-solve uneven mix (one direct run), --thin256 the 256^3 thin box (40
+Mpc/h, sigma_ln = 1.5, x_HI = 1e-4) with its first k sources, whose kappa and
+Gamma do not fit the L2 cache.
 """
 import argparse
 import sys
@@ -31,6 +33,7 @@ def main(argv=None) -> int:
     ap.add_argument("--chem", action="store_true", help="Table 1 Test A (64^3) with the C2-Ray iteration")
     ap.add_argument("--batch", type=int, default=0, help="K solves of the uneven mix through the batched kernel")
     ap.add_argument("--spectrum", action="store_true", help="Eq. 1 over a 1e5 K blackbody instead of the gray rate")
+    ap.add_argument("--thin256", action="store_true", help="256^3 thin box (kappa and Gamma beyond L2)")
     a = ap.parse_args(argv)
     import torch
     import paper_2512_12466_gb300 as nyx
@@ -62,6 +65,9 @@ def main(argv=None) -> int:
     if a.merge:
         w = I.config4()
         cfg = dict(merge_mode=1, merge_f_req=0.5)
+    elif a.thin256:
+        w = I.thin256(max(1, a.sources))
+        cfg = {}
     elif a.chem:
         w = I.stromgren_test("A", 64)
         cfg = {k: w.params[k] for k in ("chem_iterate", "alpha_B", "clumping", "C_H")}

@@ -84,3 +84,28 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cpp", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower() or f == "inputs.py", f
+
+
+def _checkpoint_bytes(n: int, nc: int, ns: int, payload: int) -> bytes:
+    """A checkpoint header (magic, version, configuration, cell count), `payload` bytes of data
+    and a source count, as rt_save lays them out."""
+    cfg = nyx.rt_config_default(n, 1e22)
+    head = b"NYXRTCK1" + (1).to_bytes(4, "little") + C.sizeof(nyx.rt_config).to_bytes(4, "little")
+    head += bytes(cfg) + nc.to_bytes(8, "little", signed=True)
+    return head + bytes(payload) + ns.to_bytes(8, "little", signed=True) + bytes(64)
+
+
+@pytest.mark.parametrize("n,ns,payload", [
+    (8, 1 << 30, 16 * 512),            # a source count of 2^30 in a file that holds 64 bytes of sources
+    (1024, 0, 4096),                   # a 1024^3 grid (16 GB of fields) in a file of a few kB
+    (8, 3, 16 * 512),                  # 3 sources claimed, 64 bytes present (60 needed): trailing bytes
+])
+def test_load_checks_counts_against_the_file_size(built, tmp_path, n, ns, payload):
+    """rt_load sizes nothing from a count in the header before the file is known to hold that
+    much data: a short or padded file is RT_EINVAL, before any host buffer or CUDA call."""
+    p = tmp_path / "bad.ckpt"
+    p.write_bytes(_checkpoint_bytes(n, n ** 3, ns, payload))
+    with pytest.raises(nyx.NyxError) as e:
+        nyx.rt_load(str(p))
+    assert e.value.code == nyx.RT_EINVAL
+    assert "not a complete checkpoint" in str(e.value)
