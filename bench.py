@@ -410,8 +410,9 @@ def bench_spectrum(nyx, torch, w, n_th):
 def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int | None = None,
                   tile: int | None = None):
     """64 independent solves (grid sizes from {32,64,96,128}^3, log-uniform source counts on
-    [1, 4096], per-solve seeds), FP32: one persistent graph-captured launch for all solves vs
-    one rt_step per solve. Returns timings, segments and the largest field difference."""
+    [1, 4096], per-solve seeds), FP32: the graph-captured batch (light solves in persistent
+    launches, heavy ones in device-sized per-level launches on parallel streams) vs one rt_step
+    per solve. Returns timings, segments and the largest field difference."""
     ws = I.batch_solves(64, config=3, x_mode=x_mode)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
     solvers, outs = [], []
@@ -468,7 +469,9 @@ def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int |
             "plain_ms_per_step": plain_s * 1e3, "batched_ms_per_step": batch_s * 1e3,
             "plain_value": segs / plain_s, "batched_value": bsegs / batch_s, "factor": plain_s / batch_s,
             "max_rel_l2_batched_vs_plain": diff, "steps": steps, "graph": True, "tuned": tuned,
-            "params": {k: getattr(p_final, k) for k in ("block", "blocks_per_sm", "tile", "slice", "group_bytes")}}
+            "params": {k: getattr(p_final, k) for k in ("block", "blocks_per_sm", "tile", "slice", "group_bytes",
+                                                        "heavy_shift")},
+            "heavy_solves": sum(1 for x in st if sum(x["segments"]) >= (1 << 26))}
 
 
 def serving_requests(n_req: int, torch):
@@ -564,46 +567,52 @@ def bench_serving(nyx, torch, n_req: int):
                                              "wait_batch_ms", "wait_finish_ms", "busy_ms")}
     srv.close()
 
-    # ---- plain per-request FP64, first-come first-served; one handle per grid size, re-targeted
-    # to each request (rt_reconfigure), so neither path allocates per request
-    solvers = {}
+    # ---- plain per-request launches, first-come first-served, in FP64 (the benchmark spec's baseline) and
+    # in FP32 (the same precision as the served form, to separate batching's gain from precision's);
+    # one handle per grid size, re-targeted to each request (rt_reconfigure), so no path allocates
+    # per request
+    def plain_arm(precision, keep_check):
+        solvers = {}
 
-    def plain_step(q, out):
-        s = solvers.get(q["n"])
-        if s is None:
-            s = solvers[q["n"]] = nyx.Solver(q["n"], q["box"], precision=nyx.RT_FP64, n_th_cm3=q["n_th"],
-                                             n_min_ray=4.0, tau_max=30.0)
-        else:
-            s.reconfigure(q["box"], n_th_cm3=q["n_th"], n_min_ray=4.0, tau_max=30.0)
-        s.set_fields(q["n_h"], q["x"])
-        s.add_sources(q["cells"], q["ndot"])
-        return s.step(0.0, out, None)[2]
+        def plain_step(q, out):
+            s = solvers.get(q["n"])
+            if s is None:
+                s = solvers[q["n"]] = nyx.Solver(q["n"], q["box"], precision=precision, n_th_cm3=q["n_th"],
+                                                 n_min_ray=4.0, tau_max=30.0)
+            else:
+                s.reconfigure(q["box"], n_th_cm3=q["n_th"], n_min_ray=4.0, tau_max=30.0)
+            s.set_fields(q["n_h"], q["x"])
+            s.add_sources(q["cells"], q["ndot"])
+            return s.step(0.0, out, None)[2]
 
-    lat, segs = [], 0
-    t0 = time.perf_counter()
-    check = []
-    for j, q in enumerate(reqs):
-        now = time.perf_counter() - t0
-        if q["t"] > now:
-            time.sleep(q["t"] - now)
-        out = ring[q["n"]][j % 96]
-        stp = plain_step(q, out)
-        lat.append(1e3 * (time.perf_counter() - t0 - q["t"]))
-        segs += sum(stp["segments"])
-        if j < 4:
-            check.append((j, out.copy()))
-    t_end_p = time.perf_counter() - t0
-    lat_s = sorted(lat)
-    q_ = lambda p: lat_s[min(len(lat_s) - 1, int(round(p * (len(lat_s) - 1))))]
-    plain = {"achieved_rps": len(reqs) / t_end_p, "p50_ms": q_(0.5), "p99_ms": q_(0.99),
-             "mean_ms": float(np.mean(lat)), "max_ms": lat_s[-1], "segments_per_s": segs / t_end_p,
-             "segments": segs, "wall_s": t_end_p}
-    t0 = time.perf_counter()
-    for j, q in enumerate(reqs[:96]):
-        plain_step(q, ring[q["n"]][j % 96])
-    cap_plain = 96 / (time.perf_counter() - t0)
-    for s in solvers.values():
-        s.close()
+        lat, segs, check = [], 0, []
+        t0 = time.perf_counter()
+        for j, q in enumerate(reqs):
+            now = time.perf_counter() - t0
+            if q["t"] > now:
+                time.sleep(q["t"] - now)
+            out = ring[q["n"]][j % 96]
+            stp = plain_step(q, out)
+            lat.append(1e3 * (time.perf_counter() - t0 - q["t"]))
+            segs += sum(stp["segments"])
+            if keep_check and j < 4:
+                check.append((j, out.copy()))
+        t_end_p = time.perf_counter() - t0
+        lat_s = sorted(lat)
+        q_ = lambda p: lat_s[min(len(lat_s) - 1, int(round(p * (len(lat_s) - 1))))]
+        res = {"achieved_rps": len(reqs) / t_end_p, "p50_ms": q_(0.5), "p99_ms": q_(0.99),
+               "mean_ms": float(np.mean(lat)), "max_ms": lat_s[-1], "segments_per_s": segs / t_end_p,
+               "segments": segs, "wall_s": t_end_p}
+        t0 = time.perf_counter()
+        for j, q in enumerate(reqs[:96]):
+            plain_step(q, ring[q["n"]][j % 96])
+        cap = 96 / (time.perf_counter() - t0)
+        for s in solvers.values():
+            s.close()
+        return res, cap, check
+
+    plain, cap_plain, check = plain_arm(nyx.RT_FP64, True)
+    plain32, cap_plain32, _ = plain_arm(nyx.RT_FP32, False)
     # accuracy: the first requests served again in FP32 through the server vs their FP64 plain results
     srv = nyx.Server(precision=nyx.RT_FP32)
     errs = []
@@ -618,12 +627,17 @@ def bench_serving(nyx, torch, n_req: int):
     offered = n_req / reqs[-1]["t"]
     return {"requests": n_req, "offered_rps": offered,
             "capacity_rps": {"served_fp32_batched": cap_served, "plain_fp64_per_request": cap_plain,
-                             "factor": cap_served / cap_plain, "requests": 96, "batches": cap_batches,
+                             "plain_fp32_per_request": cap_plain32,
+                             "factor": cap_served / cap_plain, "factor_same_precision": cap_served / cap_plain32,
+                             "requests": 96, "batches": cap_batches, "wall_ms": 96e3 / cap_served,
+                             "gpu_busy_fraction": cap_phase["busy_ms"] / (96e3 / cap_served),
                              "served_host_phase_ms": cap_phase},
             "served_fp32_batched": served,
-            "plain_fp64_per_request": plain, "throughput_factor": served["achieved_rps"] / plain["achieved_rps"],
+            "plain_fp64_per_request": plain, "plain_fp32_per_request": plain32,
+            "throughput_factor": served["achieved_rps"] / plain["achieved_rps"],
             "saturated_served": served["achieved_rps"] < 0.95 * offered,
             "saturated_plain": plain["achieved_rps"] < 0.95 * offered,
+            "saturated_plain_fp32": plain32["achieved_rps"] < 0.95 * offered,
             "max_rel_l2_fp32_served_vs_fp64_plain": max(errs)}
 
 

@@ -108,7 +108,8 @@ enum {
                                   Phi(tau) - Phi(tau + dtau) of it per segment, Phi(tau) being the
                                   fraction of its photons that survive tau (tabulated per
                                   temperature, cubic interpolation in ln tau). tau_max <= 1e4.
-                                  rt_step only (not the batched, serving or allocation-free forms). */
+                                  rt_step, the batched form (its heavy path) and the server; not
+                                  the allocation-free form. */
 };
 
 #define RT_FLAG_VISIT_HASH 1   /* accumulate the visit-list hash in rt_stats (bookkeeping check) */
@@ -263,16 +264,22 @@ const char* rt_last_error(const rt_handle* h);
 const char* rt_version(void);
 
 /* ---------------------------------------------------------------------------
- * Batched form: many independent solves in one persistent launch.
+ * Batched form: many independent solves traced together.
  *
  * A batch groups handles (each with its own grid size, fields, sources and
  * configuration; all with the same precision, on one device, chemistry off)
- * and traces all their rays together: the ray-tracing loop of Alg. 2 runs in
- * one cooperative launch whose warps claim tiles of work from a device queue,
- * level by level and slice by slice, over all solves at once. This fills the
- * GPU when single solves are small and removes the per-level host round trips
- * of rt_step. Results equal those of rt_step on each handle (the same
- * kernels' arithmetic; only the order of FP64 atomic deposits differs).
+ * and traces all their rays in one run of the ray-tracing loop of Alg. 2.
+ * Light solves share cooperative, persistent launches whose warps claim tiles
+ * of work from a device queue, level by level and slice by slice, over all
+ * their solves at once: this fills the GPU when single solves are small and
+ * removes the per-level host round trips of rt_step. Heavy solves (see
+ * heavy_shift; always those with RT_SPECTRUM_BLACKBODY) are cut into chunks of
+ * sources, each traced by one march launch per level sized on the device from
+ * the parents the previous level counted, on parallel streams whose launches
+ * overlap. Results equal those of rt_step on each handle (bookkeeping bit for
+ * bit; fields to the order of the FP64 atomic deposits, and for FP64 walked
+ * solves to the FP64 bar of 1e-12 against the table march's double-float
+ * arithmetic).
  */
 typedef struct rt_batch rt_batch;
 
@@ -283,7 +290,9 @@ typedef struct rt_batch_params {
                                (a batch whose solves share N_min reads the FP32 geometry tables, with
                                a higher limit than the walking kernel) */
     int32_t tile;           /* children a warp claims from the work queue at once (multiple of 32) */
-    int32_t pad_;
+    int32_t heavy_shift;    /* a solve that traced 2^heavy_shift segments or more in its last run
+                               takes the heavy path (before any run: a grid whose kappa + Gamma fill
+                               half of group_bytes); 0: 26; -1: every solve; at most 62 */
     int64_t slice;          /* children per slice; also the record capacity of each level's buffer */
     int64_t group_bytes;    /* solves run in consecutive groups whose kappa + Gamma bytes stay within
                                this budget (one launch per group, keeping each group's fields in
@@ -309,10 +318,10 @@ int rt_batch_get_params(const rt_batch* b, rt_batch_params* p);
 int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best, double* best_ms);
 
 /* Capture one run (kappa rebuild, trace, finalize, statistics copy) into a
- * CUDA graph; rt_batch_run then replays it. Solves are grouped into launches
- * by their work in the previous run (a solve that traced 2^26 segments or
- * more gets a launch of its own), so capturing after one run captures that
- * grouping; before any run, grouping follows field sizes only. */
+ * CUDA graph; rt_batch_run then replays it. Solves are sorted into the light
+ * and heavy paths by their work in the previous run (heavy_shift), so
+ * capturing after one run captures that split; before any run, it follows
+ * field sizes only. */
 int rt_batch_capture(rt_batch* b);
 
 /* Run the batch: write solve i's Gamma and heating into gamma_out[i] and

@@ -67,7 +67,7 @@ class rt_stats(C.Structure):
 
 
 class rt_batch_params(C.Structure):
-    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("tile", C.c_int32), ("pad_", C.c_int32),
+    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("tile", C.c_int32), ("heavy_shift", C.c_int32),
                 ("slice", C.c_int64), ("group_bytes", C.c_int64)]
 
 
@@ -438,7 +438,8 @@ class Solver:
 
 
 class Batch:
-    """Many solvers traced together by one persistent launch (rt_batch_*)."""
+    """Many solvers traced together (rt_batch_*): light solves in persistent launches, heavy ones
+    in device-sized per-level launches on parallel streams."""
 
     def __init__(self, solvers):
         self.solvers = list(solvers)
@@ -447,10 +448,11 @@ class Batch:
     def params(self) -> rt_batch_params:
         return rt_batch_get_params(self.b)
 
-    def set_params(self, block=None, blocks_per_sm=None, tile=None, slice=None, group_bytes=None):
+    def set_params(self, block=None, blocks_per_sm=None, tile=None, slice=None, group_bytes=None,
+                   heavy_shift=None):
         p = rt_batch_get_params(self.b)
         for k, v in dict(block=block, blocks_per_sm=blocks_per_sm, tile=tile, slice=slice,
-                         group_bytes=group_bytes).items():
+                         group_bytes=group_bytes, heavy_shift=heavy_shift).items():
             if v is not None:
                 setattr(p, k, v)
         rt_batch_set_params(self.b, p)

@@ -1,15 +1,23 @@
 // Batched form of the step: many independent solves (their own grids, fields,
-// sources and parameters, one common precision) traced by one cooperative,
-// persistent launch of batch_kernel fed by a device work queue, optionally
+// sources and parameters, one common precision) traced together, optionally
 // captured in a CUDA graph and replayed, with launch shapes chosen by an
 // autotuner that times candidate shapes on the batch itself.
 //
+// Light solves (where launches and host round trips would dominate) share
+// cooperative, persistent launches of batch_kernel fed by a device work queue.
+// Heavy solves (many segments in the last run, a large grid, or the
+// frequency-integrated rate) are cut into chunks of sources; each chunk is
+// traced by one launch of the per-level march kernel per HEALPix level, every
+// launch sized on the device from the parents the previous level counted, so
+// no host round trip separates the levels. The chunks are spread over parallel
+// lanes (streams forked from the batch stream and joined back), whose launches
+// overlap on the device and fill each other's tails.
+//
 // Per run, on the batch's private stream: for every solve Gamma is cleared and
-// kappa rebuilt from the handle's current n_H and x; the batch kernel traces
-// all rays of all solves; finalize writes every solve's heating and deposited
-// photons; the per-solve statistics come back in one copy. Sources (after
-// dedup, sort and merging) and the n_th default are fixed when the batch is
-// created.
+// kappa rebuilt from the handle's current n_H and x; the light and heavy solves
+// are traced; finalize writes every solve's heating and deposited photons; the
+// per-solve statistics come back in one copy. Sources (after dedup, sort and
+// merging) and the n_th default are fixed when the batch is created.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +42,10 @@ __global__ void tag_sources_kernel(const SrcEntry* __restrict__ in, int64_t m, i
 }
 
 constexpr int kMaxSlices = 1 << 16;
+// Heavy solves: lanes, and the ray-record bytes one lane's chunk may need at most (a chunk holds as
+// many sources as keep every level's parent records within it).
+constexpr int kLanes = 4;
+constexpr int64_t kLaneRecordBytes = int64_t(768) << 20;
 // A solve that traced at least this many segments in its last run gets a launch of its own (the
 // single-solve kernel); lighter solves share launches, where batching pays.
 constexpr unsigned long long kHeavySegments = 1ULL << 26;
@@ -54,8 +66,19 @@ struct rt_batch {
     int64_t cap_src = 0, cap_solves = 0;
     int table_level = 0;
     const int4* dirs = nullptr;
-    bool use_geo = false;                  // FP32 solves sharing one split radius: geometry tables
+    bool use_geo = false;                  // FP32 solves, every level tabled: the persistent kernel reads tables
+    bool geo_shared = false;               // every solve shares one split radius and boundary: tables apply
+    bool geo_ok[RT_MAX_LEVELS + 1] = {};   // level l has a table in the batch's precision
     GeomLevel geo[RT_MAX_LEVELS + 1];
+    // heavy solves: per-level launches over chunks of sources on parallel lanes
+    cudaStream_t lane[kLanes] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kLanes] = {};
+    RayStore lane_rays[kLanes][RT_MAX_LEVELS + 1];  // parents of level l of the lane's current chunk
+    int64_t lane_cap[RT_MAX_LEVELS + 1] = {};       // records per level and lane
+    unsigned long long* d_lane_count = nullptr;     // kLanes x (RT_MAX_LEVELS + 1) parent counters
+    std::vector<int64_t> chunk;                     // sources per chunk of each solve
+    std::vector<int64_t> tlev;                      // per solve: levels that read tables in the last run
     BatchSolve* d_solves = nullptr;
     DevStats* d_stats = nullptr;
     DevStats* h_stats = nullptr;           // pinned
@@ -158,6 +181,110 @@ int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count, int single)
     return RT_OK;
 }
 
+// Parent records a chunk of `count` sources can need at level l >= 1: its level l-1 rays, at most
+// 12 4^(l-1) per source.
+int64_t chunk_records(int64_t count, int l) { return count * 12 * (int64_t(1) << (2 * (l - 1))); }
+
+// Solve i takes the heavy path: the frequency-integrated rate (which the persistent kernel does not
+// integrate), or enough work to fill the device by itself (from its last run; before any run, a grid
+// that fills half the group budget).
+bool heavy_solve(const rt_batch* b, size_t i)
+{
+    const rt_handle* h = b->hs[i];
+    if (h->cfg.spectrum != RT_SPECTRUM_GRAY) return true;
+    const int hs = b->params.heavy_shift;
+    if (hs < 0) return true;
+    if (i < b->work.size()) return b->work[i] >= (hs > 0 ? (1ULL << hs) : kHeavySegments);
+    const int rbytes = b->precision == RT_FP32 ? 12 : 16;
+    return b->params.group_bytes > 0 && 2 * rbytes * h->ncell >= b->params.group_bytes;
+}
+
+// One chunk of a heavy solve: sources [first, first + count) of its catalog, every level traced by one
+// launch on lane k, sized on the device from the parents the previous level counted. Returns the
+// levels that read geometry tables.
+template <class R>
+int enqueue_chunk(rt_batch* b, size_t i, int64_t first, int64_t count, int k, int64_t* tabled)
+{
+    rt_handle* h = b->hs[i];
+    cudaStream_t s = b->lane[k];
+    unsigned long long* cnt = b->d_lane_count + (size_t)k * (RT_MAX_LEVELS + 1);
+    B_CUDA(b, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (RT_MAX_LEVELS + 1), s), "lane counters");
+    const int L = h->table_level;
+    const bool tables = b->geo_shared && !(h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE);
+    for (int l = 0; l <= L; ++l) {
+        MarchArgs<R> a;
+        a.level = l;
+        a.n = h->cfg.n;
+        a.c0 = l == 0 ? 12 * first : 0;
+        a.c1 = l == 0 ? 12 * (first + count) : 4 * chunk_records(count, l);
+        a.in_count = l == 0 ? nullptr : cnt + l;
+        a.dirs = b->dirs + healpix_level_offset(l);
+        a.src = h->d_emit;
+        a.in = l == 0 ? RayBuf<R>() : ray_view<R>(b->lane_rays[k][l]);
+        // rays of the deepest level a solve reaches end before their split sphere or at level_max
+        a.out = (l < L && l + 1 <= h->level_max) ? ray_view<R>(b->lane_rays[k][l + 1]) : RayBuf<R>();
+        a.out_count = cnt + l + 1;
+        a.kap = static_cast<const R*>(h->d_kap);
+        a.gamma = h->d_gamma;
+        a.rq = h->rq;
+        a.level_max = h->level_max;
+        a.tau_max = (R)h->cfg.tau_max;
+        a.overlap_mode = h->cfg.overlap_mode;
+        a.hash = (h->cfg.flags & RT_FLAG_VISIT_HASH) ? 1 : 0;
+        a.rs = h->rs;
+        if constexpr (sizeof(R) == 8) a.spec = h->spec_d;
+        else a.spec = h->spec_f;
+        a.st = b->d_stats + i;
+        const int64_t want = (a.c1 - a.c0 + 255) / 256;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)b->sm_count * 8));
+        const bool table = tables && b->geo_ok[l];
+        if constexpr (sizeof(R) == 8) {
+            if (table) launch_march_table_f64(a, b->geo[l], grid, 256, s);
+            else launch_march_f64(a, grid, 256, s);
+        } else {
+            if (table) launch_march_table_f32(a, b->geo[l], grid, 256, s);
+            else launch_march_f32(a, grid, 256, s);
+        }
+        B_CUDA(b, cudaGetLastError(), "march launch");
+        b->launches += 1;
+        if (table) *tabled |= int64_t(1) << l;
+    }
+    return RT_OK;
+}
+
+// The heavy solves: fork the lanes from the batch stream, give each chunk to the lane with the least
+// estimated work so far (segments of the last run, or cells times sources before any), join back.
+int enqueue_heavy(rt_batch* b, const std::vector<char>& hv)
+{
+    cudaStream_t s = b->stream;
+    B_CUDA(b, cudaEventRecord(b->ev_fork, s), "fork");
+    for (int k = 0; k < kLanes; ++k) B_CUDA(b, cudaStreamWaitEvent(b->lane[k], b->ev_fork, 0), "fork");
+    double load[kLanes] = {};
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        if (!hv[i] || b->n_emit[i] == 0) continue;
+        const int64_t m = b->n_emit[i], c = std::max<int64_t>(1, b->chunk[i]);
+        const double est = (i < b->work.size() && b->work[i] > 0) ? (double)b->work[i]
+                                                                 : (double)b->hs[i]->ncell * (double)m;
+        int64_t tabled = 0;
+        for (int64_t f = 0; f < m; f += c) {
+            const int64_t cc = std::min(c, m - f);
+            int k = 0;
+            for (int q = 1; q < kLanes; ++q)
+                if (load[q] < load[k]) k = q;
+            load[k] += est * (double)cc / (double)m;
+            const int rc = b->precision == RT_FP32 ? enqueue_chunk<float>(b, i, f, cc, k, &tabled)
+                                                   : enqueue_chunk<double>(b, i, f, cc, k, &tabled);
+            if (rc) return rc;
+        }
+        b->tlev[i] = tabled;
+    }
+    for (int k = 0; k < kLanes; ++k) {
+        B_CUDA(b, cudaEventRecord(b->ev_join[k], b->lane[k]), "join");
+        B_CUDA(b, cudaStreamWaitEvent(s, b->ev_join[k], 0), "join");
+    }
+    return RT_OK;
+}
+
 // The device work of one run, enqueued on b->stream (also what a graph captures).
 int enqueue(rt_batch* b)
 {
@@ -181,15 +308,25 @@ int enqueue(rt_batch* b)
     // single-solve kernel, whose solve parameters are kernel parameters rather than per-lane loads)
     const int rbytes = b->precision == RT_FP32 ? 12 : 16;
     const int64_t gb = b->params.group_bytes;
-    auto big = [&](size_t i) {
-        return (gb > 0 && 2 * rbytes * b->hs[i]->ncell >= gb) || (i < b->work.size() && b->work[i] >= kHeavySegments);
-    };
+    auto big = [&](size_t i) { return gb > 0 && 2 * rbytes * b->hs[i]->ncell >= gb; };
+    std::vector<char> hv(b->hs.size());
+    bool any_heavy = false;
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        hv[i] = heavy_solve(b, i) ? 1 : 0;
+        any_heavy = any_heavy || hv[i];
+        b->tlev[i] = 0;
+    }
     size_t i0 = 0;
     int64_t src0 = 0;
     while (i0 < b->hs.size()) {
+        if (hv[i0]) {                               // traced on the lanes below
+            src0 += b->n_emit[i0];
+            ++i0;
+            continue;
+        }
         size_t i1 = i0;
         int64_t bytes = 0, srcs = 0;
-        while (i1 < b->hs.size()) {
+        while (i1 < b->hs.size() && !hv[i1]) {
             const int64_t add = rbytes * b->hs[i1]->ncell;
             if (i1 > i0 && (big(i0) || big(i1) || (gb > 0 && bytes + add > gb))) break;
             bytes += add;
@@ -204,9 +341,15 @@ int enqueue(rt_batch* b)
                                                    : launch_trace<double>(b, src0, srcs, single);
             if (rc) return rc;
             b->launches += 1;
+            if (b->use_geo)
+                for (size_t i = i0; i < i1; ++i) b->tlev[i] = (int64_t(2) << b->table_level) - 1;
         }
         src0 += srcs;
         i0 = i1;
+    }
+    if (any_heavy) {
+        const int rc = enqueue_heavy(b, hv);
+        if (rc) return rc;
     }
     for (size_t i = 0; i < b->hs.size(); ++i) {
         rt_handle* h = b->hs[i];
@@ -268,6 +411,8 @@ int run_once(rt_batch* b, float* ms)
     B_CUDA(b, cudaEventRecord(b->ev1, b->stream), "event");
     B_CUDA(b, cudaStreamSynchronize(b->stream), "batch run");
     if (*b->h_err) return bfail(b, RT_EDEVICE, "batch kernel reported an internal error (buffer, slice or level limit)");
+    for (size_t i = 0; i < b->hs.size(); ++i)
+        if (b->h_stats[i].err) return bfail(b, RT_EDEVICE, "a march launch of a heavy solve reported an internal error");
     if (ms) B_CUDA(b, cudaEventElapsedTime(ms, b->ev0, b->ev1), "event");
     b->work.assign(b->hs.size(), 0ULL);           // the next launches' grouping (a graph keeps its own)
     for (size_t i = 0; i < b->hs.size(); ++i)
@@ -278,9 +423,11 @@ int run_once(rt_batch* b, float* ms)
 int apply_params(rt_batch* b, const rt_batch_params& p)
 {
     if ((p.block != 128 && p.block != 256) || p.tile < 32 || p.tile % 32 || p.slice < 1024 ||
-        p.slice > (int64_t(1) << 28) || p.blocks_per_sm < 0 || p.group_bytes < 0)
+        p.slice > (int64_t(1) << 28) || p.blocks_per_sm < 0 || p.group_bytes < 0 || p.heavy_shift < -1 ||
+        p.heavy_shift > 62)
         return bfail(b, RT_EINVAL,
-                     "batch params: block 128|256, tile a multiple of 32, slice in [1024, 2^28], group_bytes >= 0");
+                     "batch params: block 128|256, tile a multiple of 32, slice in [1024, 2^28], group_bytes >= 0, "
+                     "heavy_shift in [-1, 62]");
     int occ = 0;
     for (int v = 0; v < 4; ++v) occ = std::max(occ, max_blocks_per_sm(b, p.block, v & 1, v & 2));
     if (p.blocks_per_sm > occ) return bfail(b, RT_EINVAL, "batch params: blocks_per_sm above the occupancy limit");
@@ -327,6 +474,7 @@ void nyx::batch_fill_stats(const rt_batch* b, size_t i, float ms, rt_stats* st)
     st->ms_step = ms;
     st->ms_march = ms;
     st->march_launches = 1;
+    st->table_levels = i < b->tlev.size() ? b->tlev[i] : 0;
 }
 
 cudaStream_t nyx::batch_stream(const rt_batch* b) { return b->stream; }
@@ -355,8 +503,6 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
         if (h->cfg.precision != b->precision) return bfail(b, RT_EINVAL, "all handles of a batch must share the precision");
         if (!h->fields_set) return bfail(b, RT_ESTATE, "rt_set_fields has not been called on a handle");
         if (h->cfg.chem_iterate) return bfail(b, RT_EINVAL, "the batched form traces at fixed x (chem_iterate must be 0)");
-        if (h->cfg.spectrum != RT_SPECTRUM_GRAY)
-            return bfail(b, RT_EINVAL, "the batched form integrates the gray rate (spectrum must be RT_SPECTRUM_GRAY)");
         if (h->sticky) return bfail(b, RT_ESTATE, "a handle is in an error state");
     }
     DeviceGuard g(b->device);
@@ -390,21 +536,71 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
         B_CUDA(b, cudaMalloc(&b->d_err, sizeof(unsigned)), "error word");
         B_CUDA(b, cudaMallocHost(&b->h_err, sizeof(unsigned)), "error word");
         *b->h_err = 0;
+        B_CUDA(b, cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event");
+        for (int k = 0; k < kLanes; ++k) {
+            B_CUDA(b, cudaStreamCreateWithFlags(&b->lane[k], cudaStreamNonBlocking), "lane stream");
+            B_CUDA(b, cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming), "event");
+        }
+        B_CUDA(b, cudaMalloc(&b->d_lane_count, sizeof(unsigned long long) * kLanes * (RT_MAX_LEVELS + 1)),
+               "lane counters");
     }
-    {   // FP32 solves that share a split radius read every level's geometry from the tables
-        // (built here, outside any capture, for the largest grid of the batch)
-        b->use_geo = b->precision == RT_FP32 && !b->hs.empty();
+    {   // solves that share a split radius and boundary read the geometry tables of the batch's
+        // precision, built here (outside any capture) for the largest grid of the batch: the
+        // persistent kernel (FP32) when every level has one, the heavy path level by level
+        b->geo_shared = !b->hs.empty();
+        bool any_table = false, every_table = true;
         int nmax = 0;
         for (rt_handle* h : b->hs) {
-            if (h->rq != b->hs[0]->rq || h->rs != b->hs[0]->rs || (h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE))
-                b->use_geo = false;
+            if (h->rq != b->hs[0]->rq || h->rs != b->hs[0]->rs) b->geo_shared = false;
+            if (h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE) every_table = false;
+            else any_table = true;
             nmax = std::max(nmax, h->cfg.n);
         }
-        for (int l = 0; l <= RT_MAX_LEVELS; ++l) b->geo[l] = GeomLevel();
-        for (int l = 0; b->use_geo && l <= table_level; ++l)
-            if (!geometry_level(b->device, b->hs[0]->rq, l, nmax, b->hs[0]->rs, b->dirs + healpix_level_offset(l),
-                                b->stream, false, &b->geo[l]))
-                b->use_geo = false;
+        bool all = b->geo_shared && any_table;
+        for (int l = 0; l <= RT_MAX_LEVELS; ++l) {
+            b->geo[l] = GeomLevel();
+            b->geo_ok[l] = false;
+        }
+        for (int l = 0; b->geo_shared && any_table && l <= table_level; ++l) {
+            b->geo_ok[l] = geometry_level(b->device, b->hs[0]->rq, l, nmax, b->hs[0]->rs,
+                                          b->dirs + healpix_level_offset(l), b->stream, b->precision == RT_FP64,
+                                          &b->geo[l]);
+            all = all && b->geo_ok[l];
+        }
+        b->use_geo = b->precision == RT_FP32 && all && every_table;
+    }
+    {   // heavy-path chunks: as many sources as keep every level's parent records within the lane
+        // budget; the lanes' ray buffers grow to the largest chunk of any level
+        b->chunk.assign(b->hs.size(), 1);
+        b->tlev.assign(b->hs.size(), 0);
+        int64_t need[RT_MAX_LEVELS + 1] = {};
+        for (size_t i = 0; i < b->hs.size(); ++i) {
+            const int L = b->hs[i]->table_level;
+            int64_t per_src = 0;
+            for (int l = 1; l <= L; ++l) per_src += chunk_records(1, l);
+            const int64_t c =
+                std::max<int64_t>(1, std::min<int64_t>(b->n_emit[i], kLaneRecordBytes / (24 * std::max<int64_t>(1, per_src))));
+            b->chunk[i] = c;
+            for (int l = 1; l <= L; ++l) need[l] = std::max(need[l], chunk_records(c, l));
+        }
+        const int real = b->precision == RT_FP32 ? 4 : 8;
+        for (int l = 1; l <= RT_MAX_LEVELS; ++l) {
+            if (need[l] <= b->lane_cap[l]) continue;
+            B_CUDA(b, cudaStreamSynchronize(b->stream), "batch stream");
+            for (int k = 0; k < kLanes; ++k) {
+                B_CUDA(b, cudaStreamSynchronize(b->lane[k]), "lane stream");
+                cudaFree(b->lane_rays[k][l].base);
+                b->lane_rays[k][l] = RayStore();
+            }
+            b->lane_cap[l] = 0;
+            for (int k = 0; k < kLanes; ++k) {
+                void* p = nullptr;
+                B_CUDA(b, cudaMalloc(&p, ray_bytes(need[l], real)), "lane ray buffers");
+                b->lane_rays[k][l].base = p;
+                b->lane_rays[k][l].cap = need[l];
+            }
+            b->lane_cap[l] = need[l];
+        }
     }
     // ---- all solves' emitted sources in one catalog, tagged with their solve index
     if (b->nsrc > b->cap_src || !b->d_src) {
@@ -482,6 +678,14 @@ int rt_batch_destroy(rt_batch* b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
     for (auto& r : b->rays) cudaFree(r.base);
+    for (int k = 0; k < kLanes; ++k) {
+        if (b->lane[k]) cudaStreamSynchronize(b->lane[k]);
+        for (auto& r : b->lane_rays[k]) cudaFree(r.base);
+        if (b->lane[k]) cudaStreamDestroy(b->lane[k]);
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    cudaFree(b->d_lane_count);
     cudaFree(b->d_solves);
     cudaFree(b->d_stats);
     cudaFree(b->d_src);
@@ -575,6 +779,7 @@ int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best_out, doubl
                     p.tile = ti;
                     p.slice = sl;
                     p.group_bytes = gb;
+                    p.heavy_shift = start.heavy_shift;
                     int rc = apply_params(b, p);
                     if (rc) return rc;
                     float t = 0.f, tmin = 1e30f;

@@ -494,8 +494,7 @@ int rt_server_submit(rt_server* s, const rt_config* cfg, const double* n_H, cons
                      const double* ndot, int64_t nsrc, double* gamma_out, double* heat_out, int64_t* id_out)
 {
     if (!s || !cfg || !n_H || !x_ion || !id_out || nsrc < 0 || (nsrc > 0 && (!cell_ijk || !ndot))) return RT_EINVAL;
-    if (cfg->precision != s->cfg.precision || cfg->chem_iterate || cfg->spectrum != RT_SPECTRUM_GRAY || cfg->n < 1 ||
-        cfg->n > 1024)
+    if (cfg->precision != s->cfg.precision || cfg->chem_iterate || cfg->n < 1 || cfg->n > 1024)
         return RT_EINVAL;
     SrvReq* r = new SrvReq();
     r->cfg = *cfg;

@@ -70,12 +70,16 @@ def run_batch(nyx, b, ws):
     return [g.cpu().numpy() for g in gs], [h.cpu().numpy() for h in hs], stats
 
 
+@pytest.mark.parametrize("heavy_shift", [0, -1], ids=["default", "all-heavy"])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batch_matches_per_solve(nyx, precision):
+def test_batch_matches_per_solve(nyx, precision, heavy_shift):
+    # heavy_shift -1: every solve on the heavy path (chunks of sources, device-sized per-level
+    # launches on parallel streams); by default these small solves share persistent launches
     ws = mixed_workloads()
     solvers = [make_solver(nyx, w, precision) for w in ws]
     ref = [plain(nyx, s, w.n) for s, w in zip(solvers, ws)]
     b = nyx.Batch(solvers)
+    b.set_params(heavy_shift=heavy_shift)
     gs, hs, stats = run_batch(nyx, b, ws)
     tol = 1e-12 if precision == 0 else 1e-10
     for (gr, hr, sr), g, h, st in zip(ref, gs, hs, stats):
@@ -100,10 +104,12 @@ def test_batch_matches_per_solve(nyx, precision):
         s.close()
 
 
-def test_batch_matches_oracle(nyx):
+@pytest.mark.parametrize("heavy_shift", [0, -1], ids=["default", "all-heavy"])
+def test_batch_matches_oracle(nyx, heavy_shift):
     ws = mixed_workloads(count=3, seed=5)
     solvers = [make_solver(nyx, w, 0) for w in ws]
     b = nyx.Batch(solvers)
+    b.set_params(heavy_shift=heavy_shift)
     gs, _, stats = run_batch(nyx, b, ws)
     for w, g, st in zip(ws, gs, stats):
         r = oracle.run_workload(w, n_th_cm3=0.3 * float(w.n_h.mean()))
@@ -194,6 +200,61 @@ def test_batch_periodic_matches_per_solve(nyx, precision):
         for k in BOOK:
             assert st[k] == sr[k], k
         assert relerr(g, gr) < tol
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_heavy_path_many_chunks(nyx, precision):
+    """Solves with more sources than one heavy-path chunk holds (24^3 grids, about 1400 distinct
+    source cells against chunks of 512): every chunk's levels sized on the device, chunks spread
+    over the lanes, each solve equal to rt_step on it (bookkeeping bit for bit), graph replay
+    included."""
+    ws = [I.random_small(24, 1500, seed=810 + j, x_mode=["thin", "mixed"][j], box_cm=24 * 7e20) for j in range(2)]
+    solvers = [make_solver(nyx, w, precision) for w in ws]
+    ref = [plain(nyx, s, w.n) for s, w in zip(solvers, ws)]
+    assert all(r[2]["n_src_emit"] > 1024 for r in ref)
+    b = nyx.Batch(solvers)
+    b.set_params(heavy_shift=-1)
+    tol = 1e-12 if precision == 0 else 1e-10
+    for replay in (False, True):
+        if replay:
+            b.capture()
+        gs, hs, stats = run_batch(nyx, b, ws)
+        for (gr, hr, sr), g, h, st in zip(ref, gs, hs, stats):
+            for k in BOOK:
+                assert st[k] == sr[k], k
+            assert relerr(g, gr) < tol and relerr(h, hr) < tol
+            assert st["table_levels"] & 1                     # level 0 read its table
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_blackbody_rate(nyx, precision):
+    """Eq. 1 integrated over a blackbody spectrum in the batched form (its heavy path): each solve
+    equal to rt_step (bookkeeping bit for bit, fields to the atomics' order) and, for one solve, to
+    the oracle's direct quadrature (FP64 1e-7; FP32 2e-5 of the FP64 oracle)."""
+    ws = mixed_workloads(count=4, seed=23)
+    kw = dict(spectrum=1, t_bb_K=1e5)
+    solvers = [make_solver(nyx, w, precision, **kw) for w in ws]
+    ref = [plain(nyx, s, w.n) for s, w in zip(solvers, ws)]
+    b = nyx.Batch(solvers)
+    gs, hs, stats = run_batch(nyx, b, ws)
+    tol = 1e-12 if precision == 0 else 1e-10
+    for (gr, hr, sr), g, st in zip(ref, gs, stats):
+        for k in BOOK:
+            assert st[k] == sr[k], k
+        assert relerr(g, gr) < tol
+    w = ws[0]
+    n_th = 0.3 * float(w.n_h.mean())
+    r = oracle.run_workload(w, n_th_cm3=n_th, precision=precision, **kw)
+    for k in BOOK:
+        assert stats[0][k] == r["stats"][k], k
+    r64 = r if precision == 0 else oracle.run_workload(w, n_th_cm3=n_th, precision=0, **kw)
+    assert relerr(gs[0].reshape(w.n, w.n, w.n), r64["gamma"]) < (1e-7 if precision == 0 else 2e-5)
     b.close()
     for s in solvers:
         s.close()

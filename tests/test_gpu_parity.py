@@ -239,19 +239,8 @@ def test_spectrum_parity(nyx, case, prec, walk):
 
 
 def test_spectrum_rejected_where_not_available(nyx):
-    w = I.random_small(12, 2, seed=505, x_mode="mixed", box_cm=12 * 3e21)
-    s = nyx.Solver(w.n, w.box_cm, precision=1, spectrum=1)
-    s.set_fields(w.n_h.ravel(), w.x_ion.ravel())
-    s.add_sources(w.cells.ravel(), w.ndot)
     with pytest.raises(nyx.NyxError):
-        nyx.Batch([s])
-    s.close()
-    srv = nyx.Server(precision=1)
-    with pytest.raises(nyx.NyxError):
-        srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot, spectrum=1)
-    srv.close()
-    with pytest.raises(nyx.NyxError):
-        nyx.Solver(w.n, w.box_cm, spectrum=1, tau_max=2e4)       # beyond the table
+        nyx.Solver(12, 12 * 3e21, spectrum=1, tau_max=2e4)       # beyond the table
 
 
 def test_host_and_device_inputs_agree(nyx):

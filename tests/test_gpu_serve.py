@@ -191,3 +191,28 @@ def test_pool_evicts_under_a_tight_budget(nyx):
     assert st["completed"] == len(ws) and st["mem_peak"] <= budget
     for w, r in zip(ws, got):
         check_same(nyx, r, alone(nyx, w, 1, 0.3 * float(w.n_h.mean())))
+
+
+def test_blackbody_requests_are_served(nyx):
+    """Requests with Eq. 1 integrated over a blackbody spectrum go to the batch's heavy path:
+    each served result equals rt_step on the request alone and the oracle's bookkeeping."""
+    ws = requests(6, seed=61)
+    srv = nyx.Server(precision=1, max_batch=8)
+    kw = dict(spectrum=1, t_bb_K=1e5)
+    ids = [srv.submit(w.n, w.box_cm, w.n_h, w.x_ion, w.cells, w.ndot, n_th_cm3=0.3 * float(w.n_h.mean()),
+                      flags=nyx.RT_FLAG_VISIT_HASH, **kw) for w in ws]
+    got = [srv.poll(i, wait_s=120.0) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(ws) and st["failed"] == 0
+    for w, r in zip(ws, got):
+        n_th = 0.3 * float(w.n_h.mean())
+        s = nyx.Solver(w.n, w.box_cm, precision=1, n_th_cm3=n_th, flags=nyx.RT_FLAG_VISIT_HASH, **kw)
+        s.set_fields(w.n_h.ravel(), w.x_ion.ravel())
+        s.add_sources(w.cells.ravel(), w.ndot)
+        g, h, sr = s.step()
+        s.close()
+        check_same(nyx, r, (g.ravel(), h.ravel(), sr))
+        ref = oracle.run_workload(w, n_th_cm3=n_th, precision=1, **kw)
+        for k in BOOK:
+            assert r[2][k] == ref["stats"][k], k
