@@ -17,6 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libnyxrt.so")
+PROBE_LIB = os.path.join(HERE, "libnyxrt_probe.so")   # arithmetic-peak probe, beside the library
 BUILD = os.path.join(ROOT, "_build", "nyxrt")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -55,7 +56,22 @@ def _compile(src: str) -> str:
     return obj
 
 
+def build_probe(force: bool = False) -> str:
+    """The FMA-throughput probe (probe_peaks.cu) as its own shared library."""
+    src = os.path.join(CSRC, "probe_peaks.cu")
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(src):
+        return PROBE_LIB
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", src, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    build_probe(force)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
         return LIB
     os.makedirs(BUILD, exist_ok=True)

@@ -1561,10 +1561,11 @@ __global__ void __launch_bounds__(256, MarchOccupancy<R>::blocks) march_kernel(c
 
 // One level (or one slice of it) of one solve, geometry from the level's table (kFreq: Eq. 1 over
 // the blackbody spectrum). Without the walk the FP32 march fits 64 registers, so four blocks (32
-// warps) per SM; the FP64 one takes two.
+// warps) per SM. The FP64 march, latency-bound in its double-float arithmetic, runs three (80
+// registers, a spill of a few dozen bytes): 57 against 50 G segments/s with two.
 template <class R>
 struct TableOccupancy {
-    static constexpr int blocks = sizeof(R) == 4 ? 4 : 2;
+    static constexpr int blocks = sizeof(R) == 4 ? 4 : 3;
 };
 
 template <class R, bool kHash, bool kFreq>
