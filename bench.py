@@ -43,12 +43,12 @@ L2_FLUSH_BYTES = 512 << 20
 
 
 # DRAM traffic of the FP32 march from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over
-# all march launches of one step of the same box with its first 64 sources;
-# profiles/march_table_config2_dram.md), scaled to the full workload by primary segments. Valid only
-# for the kernel sources it was taken on.
-TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.760785412388026,
-                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "640aef1bb48de04d",
-                               "paper_2512_12466_gb300/csrc/rt_internal.h": "632db27dbd2931e9"}}
+# every march launch of one step of the same box with its first 64 sources, taken with
+# `python -m paper_2512_12466_gb300.profile_case --sources 64 --steps 1 --levels`), scaled to the full
+# workload by primary segments. Valid only for the kernel sources it was taken on.
+TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.803362415664589,
+                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "2bebfa05e9fe1ace",
+                               "paper_2512_12466_gb300/csrc/rt_internal.h": "4b0bda58e087fccc"}}
 
 
 def traffic_per_launch(segments_per_step: float, launches_per_step: float):
@@ -61,6 +61,26 @@ def traffic_per_launch(segments_per_step: float, launches_per_step: float):
         except OSError:
             return None
     return TRAFFIC_CAPTURE["bytes_per_segment"] * segments_per_step / max(1.0, launches_per_step)
+
+
+def atomic_peak():
+    """FP64 atomic adds per second into an L2-resident array the size of the 128^3 Gamma grid (random
+    cells and neighbouring cells per warp), measured now with the committed probe library: the
+    deposit roofline of the march."""
+    import ctypes as C
+    from paper_2512_12466_gb300 import _build
+    lib = C.CDLL(_build.build_probe())
+    lib.nyxrt_probe_red_f64.argtypes = [C.c_int64, C.c_int64, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.nyxrt_probe_red_f64.restype = C.c_int
+    out = {}
+    for name, pat in (("random", 0), ("neighbours", 1)):
+        best = 0.0
+        for _ in range(3):
+            ps, ms = C.c_double(), C.c_double()
+            if lib.nyxrt_probe_red_f64(128 ** 3, 256, pat, C.byref(ps), C.byref(ms)) == 0:
+                best = max(best, ps.value)
+        out[name] = best
+    return out
 
 
 def load_peaks():
@@ -633,6 +653,7 @@ def bench_serving(nyx, torch, n_req: int):
                              "gpu_busy_fraction": cap_phase["busy_ms"] / (96e3 / cap_served),
                              "served_host_phase_ms": cap_phase},
             "served_fp32_batched": served,
+            "geometry_table_bytes": nyx.rt_geometry_table_bytes(torch.cuda.current_device()),
             "plain_fp64_per_request": plain, "plain_fp32_per_request": plain32,
             "throughput_factor": served["achieved_rps"] / plain["achieved_rps"],
             "saturated_served": served["achieved_rps"] < 0.95 * offered,
@@ -720,6 +741,7 @@ def run_nyx(args, world, rank, local):
     if rank != 0:
         return 0
     hbm, peak_kind = load_peaks()
+    red = atomic_peak()
     f32 = results["fp32"]
     f64 = results["fp64"]
     line = {
@@ -741,12 +763,21 @@ def run_nyx(args, world, rank, local):
                      / max(1, f32["march_launches_per_step"]),
                      "kernel": "march_table_kernel (FP32, geometry tables)", "peak_kind": peak_kind,
                      "march_ms_per_step": f32["march_ms_per_step"],
-                     "march_launches_per_step": f32["march_launches_per_step"]},
+                     "march_launches_per_step": f32["march_launches_per_step"],
+                     # what binds the march on this machine: its FP64 deposits (one per primary segment and
+                     # per secondary deposit) against FP64 atomic adds into an L2-resident array of the
+                     # same size, measured in this run
+                     "l2_atomics": {"achieved": (f32["segments_per_step"] + f32["secondary_per_step"])
+                                    / (f32["march_ms_per_step"] / 1e3),
+                                    "peak": red["random"], "peak_neighbouring_cells": red["neighbours"],
+                                    "unit": "FP64 atomic adds/s",
+                                    "frac": (f32["segments_per_step"] + f32["secondary_per_step"])
+                                    / (f32["march_ms_per_step"] / 1e3) / max(red["random"], 1.0)}},
         "fp64": {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "steps": f64["steps"],
                  "roofline": {"achieved": f64["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                               "frac": f64["achieved_gbs"] / hbm, "frac_nominal": f64["achieved_gbs"] / NOMINAL_HBM,
-                              "kernel": "march_table_kernel<double> (FP64, geometry tables)",
-                              "bound": "fp64 pipe (84% of its peak in ncu; HBM fraction shown for the record)"}},
+                              "kernel": "march_table_kernel<double> (FP64, geometry tables, double-float)",
+                              "bound": "latency of the double-float arithmetic (issue 58%, FP64 pipe 51% in ncu)"}},
         "e2e": {"value": e2e_val, "unit": "segments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "clocks": f32["clocks"],

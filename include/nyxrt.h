@@ -291,8 +291,8 @@ typedef struct rt_batch_params {
                                a higher limit than the walking kernel) */
     int32_t tile;           /* children a warp claims from the work queue at once (multiple of 32) */
     int32_t heavy_shift;    /* a solve that traced 2^heavy_shift segments or more in its last run
-                               takes the heavy path (before any run: a grid whose kappa + Gamma fill
-                               half of group_bytes); 0: 26; -1: every solve; at most 62 */
+                               takes the heavy path (before any run every gray solve is light);
+                               0: 26; -1: every solve; at most 62 */
     int64_t slice;          /* children per slice; also the record capacity of each level's buffer */
     int64_t group_bytes;    /* solves run in consecutive groups whose kappa + Gamma bytes stay within
                                this budget (one launch per group, keeping each group's fields in
@@ -320,8 +320,8 @@ int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best, double* b
 /* Capture one run (kappa rebuild, trace, finalize, statistics copy) into a
  * CUDA graph; rt_batch_run then replays it. Solves are sorted into the light
  * and heavy paths by their work in the previous run (heavy_shift), so
- * capturing after one run captures that split; before any run, it follows
- * field sizes only. */
+ * capturing after one run captures that split; before any run, only the
+ * blackbody-rate solves take the heavy path. */
 int rt_batch_capture(rt_batch* b);
 
 /* Run the batch: write solve i's Gamma and heating into gamma_out[i] and

@@ -186,17 +186,54 @@ int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count, int single)
 int64_t chunk_records(int64_t count, int l) { return count * 12 * (int64_t(1) << (2 * (l - 1))); }
 
 // Solve i takes the heavy path: the frequency-integrated rate (which the persistent kernel does not
-// integrate), or enough work to fill the device by itself (from its last run; before any run, a grid
-// that fills half the group budget).
+// integrate), or enough work in its last run to fill the device by itself. Before any run a solve is
+// light: a chunk's buffers are sized for every ray of every level, so a heavy path taken blindly
+// by an opaque many-source solve would be thousands of nearly empty launches.
 bool heavy_solve(const rt_batch* b, size_t i)
 {
     const rt_handle* h = b->hs[i];
     if (h->cfg.spectrum != RT_SPECTRUM_GRAY) return true;
     const int hs = b->params.heavy_shift;
     if (hs < 0) return true;
-    if (i < b->work.size()) return b->work[i] >= (hs > 0 ? (1ULL << hs) : kHeavySegments);
-    const int rbytes = b->precision == RT_FP32 ? 12 : 16;
-    return b->params.group_bytes > 0 && 2 * rbytes * h->ncell >= b->params.group_bytes;
+    return i < b->work.size() && b->work[i] >= (hs > 0 ? (1ULL << hs) : kHeavySegments);
+}
+
+// Chunk sizes of the heavy solves of the next run (as many sources as keep every level's parent
+// records within the lane budget) and the lanes' ray buffers, grown to the largest chunk of any
+// level. Outside any capture: run before a direct run and before capturing one.
+int ensure_lanes(rt_batch* b)
+{
+    b->chunk.assign(b->hs.size(), 1);
+    int64_t need[RT_MAX_LEVELS + 1] = {};
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        if (!heavy_solve(b, i)) continue;
+        const int L = b->hs[i]->table_level;
+        int64_t per_src = 0;
+        for (int l = 1; l <= L; ++l) per_src += chunk_records(1, l);
+        const int64_t c =
+            std::max<int64_t>(1, std::min<int64_t>(b->n_emit[i], kLaneRecordBytes / (24 * std::max<int64_t>(1, per_src))));
+        b->chunk[i] = c;
+        for (int l = 1; l <= L; ++l) need[l] = std::max(need[l], chunk_records(c, l));
+    }
+    const int real = b->precision == RT_FP32 ? 4 : 8;
+    for (int l = 1; l <= RT_MAX_LEVELS; ++l) {
+        if (need[l] <= b->lane_cap[l]) continue;
+        B_CUDA(b, cudaStreamSynchronize(b->stream), "batch stream");
+        for (int k = 0; k < kLanes; ++k) {
+            B_CUDA(b, cudaStreamSynchronize(b->lane[k]), "lane stream");
+            cudaFree(b->lane_rays[k][l].base);
+            b->lane_rays[k][l] = RayStore();
+        }
+        b->lane_cap[l] = 0;
+        for (int k = 0; k < kLanes; ++k) {
+            void* p = nullptr;
+            B_CUDA(b, cudaMalloc(&p, ray_bytes(need[l], real)), "lane ray buffers");
+            b->lane_rays[k][l].base = p;
+            b->lane_rays[k][l].cap = need[l];
+        }
+        b->lane_cap[l] = need[l];
+    }
+    return RT_OK;
 }
 
 // One chunk of a heavy solve: sources [first, first + count) of its catalog, every level traced by one
@@ -375,6 +412,8 @@ void drop_graph(rt_batch* b)
 int capture(rt_batch* b)
 {
     drop_graph(b);
+    const int lrc = ensure_lanes(b);
+    if (lrc) return lrc;
     B_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     const int rc = enqueue(b);
     cudaGraph_t g = nullptr;
@@ -397,10 +436,16 @@ int capture(rt_batch* b)
     return RT_OK;
 }
 
-// One run: wait for the handles' streams, replay the graph (or enqueue), wait.
-int run_once(rt_batch* b, float* ms)
+// One run, in two halves: launch (wait for the handles' streams, replay the graph or enqueue)
+// and finish (wait for the batch stream, check the error words, read the time and each solve's
+// work for the next grouping). A caller may do other host work between the two.
+int run_launch(rt_batch* b)
 {
     for (rt_handle* h : b->hs) B_CUDA(b, cudaStreamSynchronize(h->stream), "handle stream");
+    if (!b->captured) {                   // the heavy solves' lanes, before the timed region
+        const int rc = ensure_lanes(b);
+        if (rc) return rc;
+    }
     B_CUDA(b, cudaEventRecord(b->ev0, b->stream), "event");
     if (b->captured) {
         B_CUDA(b, cudaGraphLaunch(b->exec, b->stream), "graph launch");
@@ -409,6 +454,11 @@ int run_once(rt_batch* b, float* ms)
         if (rc) return rc;
     }
     B_CUDA(b, cudaEventRecord(b->ev1, b->stream), "event");
+    return RT_OK;
+}
+
+int run_finish(rt_batch* b, float* ms)
+{
     B_CUDA(b, cudaStreamSynchronize(b->stream), "batch run");
     if (*b->h_err) return bfail(b, RT_EDEVICE, "batch kernel reported an internal error (buffer, slice or level limit)");
     for (size_t i = 0; i < b->hs.size(); ++i)
@@ -418,6 +468,12 @@ int run_once(rt_batch* b, float* ms)
     for (size_t i = 0; i < b->hs.size(); ++i)
         for (int l = 0; l < RT_MAX_LEVELS; ++l) b->work[i] += b->h_stats[i].segments[l];
     return RT_OK;
+}
+
+int run_once(rt_batch* b, float* ms)
+{
+    const int rc = run_launch(b);
+    return rc ? rc : run_finish(b, ms);
 }
 
 int apply_params(rt_batch* b, const rt_batch_params& p)
@@ -480,6 +536,10 @@ void nyx::batch_fill_stats(const rt_batch* b, size_t i, float ms, rt_stats* st)
 cudaStream_t nyx::batch_stream(const rt_batch* b) { return b->stream; }
 
 int nyx::batch_run_direct(rt_batch* b, float* ms) { return run_once(b, ms); }
+
+int nyx::batch_launch(rt_batch* b) { return run_launch(b); }
+
+int nyx::batch_finish(rt_batch* b, float* ms) { return run_finish(b, ms); }
 
 // (Re)bind a batch to a set of handles: run each handle's source stage, build
 // the tagged catalog and the solve table. Allocations are kept and grown only
@@ -569,46 +629,16 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
         }
         b->use_geo = b->precision == RT_FP32 && all && every_table;
     }
-    {   // heavy-path chunks: as many sources as keep every level's parent records within the lane
-        // budget; the lanes' ray buffers grow to the largest chunk of any level
-        b->chunk.assign(b->hs.size(), 1);
-        b->tlev.assign(b->hs.size(), 0);
-        int64_t need[RT_MAX_LEVELS + 1] = {};
-        for (size_t i = 0; i < b->hs.size(); ++i) {
-            const int L = b->hs[i]->table_level;
-            int64_t per_src = 0;
-            for (int l = 1; l <= L; ++l) per_src += chunk_records(1, l);
-            const int64_t c =
-                std::max<int64_t>(1, std::min<int64_t>(b->n_emit[i], kLaneRecordBytes / (24 * std::max<int64_t>(1, per_src))));
-            b->chunk[i] = c;
-            for (int l = 1; l <= L; ++l) need[l] = std::max(need[l], chunk_records(c, l));
-        }
-        const int real = b->precision == RT_FP32 ? 4 : 8;
-        for (int l = 1; l <= RT_MAX_LEVELS; ++l) {
-            if (need[l] <= b->lane_cap[l]) continue;
-            B_CUDA(b, cudaStreamSynchronize(b->stream), "batch stream");
-            for (int k = 0; k < kLanes; ++k) {
-                B_CUDA(b, cudaStreamSynchronize(b->lane[k]), "lane stream");
-                cudaFree(b->lane_rays[k][l].base);
-                b->lane_rays[k][l] = RayStore();
-            }
-            b->lane_cap[l] = 0;
-            for (int k = 0; k < kLanes; ++k) {
-                void* p = nullptr;
-                B_CUDA(b, cudaMalloc(&p, ray_bytes(need[l], real)), "lane ray buffers");
-                b->lane_rays[k][l].base = p;
-                b->lane_rays[k][l].cap = need[l];
-            }
-            b->lane_cap[l] = need[l];
-        }
-    }
-    // ---- all solves' emitted sources in one catalog, tagged with their solve index
+    b->chunk.assign(b->hs.size(), 1);
+    b->tlev.assign(b->hs.size(), 0);
+    // ---- all solves' emitted sources in one catalog, tagged with their solve index. Buffers grow
+    // geometrically and stream-ordered on the batch stream: a plain cudaFree would wait for every
+    // stream of the device (a server's loaders copying the next requests included).
     if (b->nsrc > b->cap_src || !b->d_src) {
-        B_CUDA(b, cudaStreamSynchronize(b->stream), "batch stream");
-        cudaFree(b->d_src);
+        if (b->d_src) B_CUDA(b, cudaFreeAsync(b->d_src, b->stream), "catalog");
         b->d_src = nullptr;
-        b->cap_src = std::max<int64_t>(b->nsrc, 1024);
-        B_CUDA(b, cudaMalloc(&b->d_src, sizeof(SrcEntry) * (size_t)b->cap_src), "catalog");
+        b->cap_src = std::max<int64_t>(std::max<int64_t>(b->nsrc, 2 * b->cap_src), 1024);
+        B_CUDA(b, cudaMallocAsync(&b->d_src, sizeof(SrcEntry) * (size_t)b->cap_src, b->stream), "catalog");
     }
     int64_t off = 0;
     for (size_t i = 0; i < b->hs.size(); ++i) {
@@ -623,17 +653,17 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
     // ---- solve table and per-solve statistics
     const int64_t ns = (int64_t)b->hs.size();
     if (ns > b->cap_solves) {
-        B_CUDA(b, cudaStreamSynchronize(b->stream), "batch stream");
-        cudaFree(b->d_stats);
+        B_CUDA(b, cudaStreamSynchronize(b->stream), "batch stream");   // the pinned block is read on the host
+        if (b->d_stats) B_CUDA(b, cudaFreeAsync(b->d_stats, b->stream), "stats");
+        if (b->d_solves) B_CUDA(b, cudaFreeAsync(b->d_solves, b->stream), "solve table");
         cudaFreeHost(b->h_stats);
-        cudaFree(b->d_solves);
         b->d_stats = nullptr;
         b->h_stats = nullptr;
         b->d_solves = nullptr;
-        b->cap_solves = std::max<int64_t>(ns, 64);
-        B_CUDA(b, cudaMalloc(&b->d_stats, sizeof(DevStats) * (size_t)b->cap_solves), "stats");
+        b->cap_solves = std::max<int64_t>(std::max<int64_t>(ns, 2 * b->cap_solves), 256);
+        B_CUDA(b, cudaMallocAsync(&b->d_stats, sizeof(DevStats) * (size_t)b->cap_solves, b->stream), "stats");
         B_CUDA(b, cudaMallocHost(&b->h_stats, sizeof(DevStats) * (size_t)b->cap_solves), "stats");
-        B_CUDA(b, cudaMalloc(&b->d_solves, sizeof(BatchSolve) * (size_t)b->cap_solves), "solve table");
+        B_CUDA(b, cudaMallocAsync(&b->d_solves, sizeof(BatchSolve) * (size_t)b->cap_solves, b->stream), "solve table");
     }
     b->hsolve.assign(b->hs.size(), BatchSolve{});
     int64_t first = 0;
@@ -686,9 +716,12 @@ int rt_batch_destroy(rt_batch* b)
     }
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     cudaFree(b->d_lane_count);
-    cudaFree(b->d_solves);
-    cudaFree(b->d_stats);
-    cudaFree(b->d_src);
+    if (b->stream) {
+        if (b->d_solves) cudaFreeAsync(b->d_solves, b->stream);
+        if (b->d_stats) cudaFreeAsync(b->d_stats, b->stream);
+        if (b->d_src) cudaFreeAsync(b->d_src, b->stream);
+        cudaStreamSynchronize(b->stream);
+    }
     cudaFree(b->d_counts);
     cudaFree(b->d_tiles);
     cudaFree(b->d_err);

@@ -99,4 +99,22 @@ __device__ __forceinline__ double df_to_double(const dflt a, const int e2)
     return __dadd_rn(widen_scaled(a.h, e2), widen_scaled(a.l, e2));
 }
 
+// The same for h + l >= 0 without the FP64 unit: renormalise (|l| <= 2^-24 h), take h's double
+// exactly, and add l counted in units of that double's last place, 2^(E_h - 52), as a 64-bit
+// integer: l 2^(52 - E_h) is below 2^28 in magnitude and rounds to the nearest unit. A carry or
+// borrow across the mantissa's end moves the exponent as binary addition of the bit patterns of
+// a positive double does, so the result is within one unit of the last place of h + l. Heads
+// outside [2^-75, 2^127) (where the scale factor leaves the float range) take df_to_double.
+__device__ __forceinline__ double df_to_double_pos(const dflt a, const int e2)
+{
+    const dflt n = df_fast_two_sum(a.h, a.l);
+    const unsigned u = __float_as_uint(n.h);
+    const int eh = (int)(u >> 23) - 127;
+    if (eh < -75 || eh > 126 || (u >> 31)) return df_to_double(a, e2);
+    const unsigned hi = (u >> 3) + ((unsigned)(896 + e2) << 20);
+    const long long bits = (long long)(((unsigned long long)hi << 32) | (unsigned long long)(u << 29));
+    const int units = __float2int_rn(__fmul_rn(n.l, __uint_as_float((unsigned)(179 - eh) << 23)));   // l 2^(52 - E_h)
+    return __longlong_as_double(bits + (long long)units);
+}
+
 }  // namespace nyx

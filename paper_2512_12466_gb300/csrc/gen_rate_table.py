@@ -1,16 +1,18 @@
 """Taylor table of the Eq. 1 factor g(y) = (1 - e^{-y}) / y for the FP64 table march's
 double-float arithmetic; writes ``rate_table.h`` next to this script.
 
-On [0, 2) the factor is expanded about the left end y0 = j / 128 of each of 256 intervals,
-g(y0 + r) = sum_k c_k(y0) r^k with 0 <= r < 1/128, to degree 5. The coefficients are
-c_k(y0) = sum_{n >= k} C(n, k) (-1)^n y0^(n - k) / (n + 1)!, the k-th derivative of the power
-series g(y) = sum_n (-y)^n / (n + 1)! divided by k!, summed in 50-digit arithmetic. c_0..c_2 are
-stored as double-float pairs (head = the value rounded to float, tail = the rest rounded to
-float, about 48 bits together), c_3..c_5 as floats: on |r| < 2^-7 the terms c_3 r^3 and beyond
-are below 2e-8, so float precision there costs under 3e-15 of g. The truncation after r^5 is
-below c_6 r^6 < 2^-42 / 5040 = 5e-17.
+On [0, 2) the factor is expanded about y0 in each of 512 intervals of width 1/256: the left end
+y0 = 0 for the first interval and the midpoint y0 = (j + 1/2) / 256 for the others, so that
+|y - y0| <= 1/512 (below 1/256 on the first) and y - y0 is exact in float arithmetic (Sterbenz:
+y / y0 lies in [2/3, 4/3] for j >= 1). The expansion g(y0 + r) = sum_k c_k(y0) r^k runs to degree 4;
+its coefficients c_k(y0) = sum_{n >= k} C(n, k) (-1)^n y0^(n - k) / (n + 1)!, the k-th derivative of
+the power series g(y) = sum_n (-y)^n / (n + 1)! divided by k!, are summed in 50-digit arithmetic.
+c_0..c_2 are stored as double-float pairs (head = the value rounded to float, tail = the rest
+rounded to float, about 48 bits together), c_3 and c_4 as floats: c_3 r^3 is below 3e-9, so float
+precision there costs under 1e-15 of g, and the truncation after r^4 is below 2e-15 relative
+(|c_5| r^5 < 2^-6 2^-45 for j >= 1, 2^-40 / 720 for j = 0).
 
-Each row: {c0 head, c0 tail, c1 head, c1 tail, c2 head, c2 tail, c3, c4, c5}, written as C99
+Each row: {c0 head, c0 tail, c1 head, c1 tail, c2 head, c2 tail, c3, c4}, written as C99
 hexadecimal float literals, so the header holds the exact float values.
 
     python paper_2512_12466_gb300/csrc/gen_rate_table.py
@@ -20,9 +22,9 @@ import struct
 
 import mpmath as mp
 
-INTERVALS = 256          # over [0, 2): y0 = j / 128
-STEP = mp.mpf(1) / 128
-DEGREE = 5
+INTERVALS = 512          # over [0, 2), width 1/256
+STEP = mp.mpf(1) / 256
+DEGREE = 4
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
@@ -43,17 +45,21 @@ def coefficient(k: int, y0) -> mp.mpf:
         n += 1
 
 
+def centre(j: int):
+    """Expansion point of interval j: its left end for j = 0, its midpoint otherwise."""
+    return mp.mpf(0) if j == 0 else (j + mp.mpf(1) / 2) * STEP
+
+
 def rows():
     mp.mp.dps = 50
     out = []
     for j in range(INTERVALS):
-        y0 = j * STEP
-        c = [coefficient(k, y0) for k in range(DEGREE + 1)]
+        c = [coefficient(k, centre(j)) for k in range(DEGREE + 1)]
         row = []
         for k in range(3):
             h = f32(c[k])
             row += [h, f32(c[k] - mp.mpf(h))]
-        row += [f32(c[3]), f32(c[4]), f32(c[5])]
+        row += [f32(c[3]), f32(c[4])]
         out.append(row)
     return out
 
@@ -61,14 +67,14 @@ def rows():
 def write(path=os.path.join(HERE, "rate_table.h")):
     lines = [
         "// Generated by gen_rate_table.py: Taylor coefficients of g(y) = (1 - e^{-y}) / y about",
-        "// y0 = j / 128, j = 0..255 (Eq. 1 rate factor of the FP64 table march). Row j:",
-        "// {c0 head, c0 tail, c1 head, c1 tail, c2 head, c2 tail, c3, c4, c5}.",
+        "// y0 = 0 (j = 0) and y0 = (j + 1/2) / 256 (j = 1..511), the Eq. 1 rate factor of the FP64",
+        "// table march. Row j: {c0 head, c0 tail, c1 head, c1 tail, c2 head, c2 tail, c3, c4}.",
         "#pragma once",
         "",
         "namespace nyx {",
         f"constexpr int kRateIntervals = {INTERVALS};",
-        "constexpr int kRateCoefs = 9;",
-        f"__device__ const float kRateTable[{INTERVALS} * 9] = {{",
+        "constexpr int kRateCoefs = 8;",
+        f"__device__ const float kRateTable[{INTERVALS} * 8] = {{",
     ]
     for r in rows():
         lines.append("    " + ", ".join(v.hex() if v != 0 else "0x0p+0" for v in r) + ",")

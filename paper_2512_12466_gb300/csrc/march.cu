@@ -228,6 +228,15 @@ __device__ __forceinline__ int wrapn(const int v, const int n)
     return r < 0 ? r + n : r;
 }
 
+// Phi at the ray's current optical depth, kept from the segment that last evaluated it (Eq. 1 over
+// the blackbody spectrum): a segment's Phi(tau + dtau) is the next segment's Phi(tau), so each
+// difference segment evaluates the table once, and the absorbed photons telescope along the ray.
+template <class R>
+struct PhiCache {
+    R phi;
+    bool ok;
+};
+
 // Eq. 1 for one segment of optical depth dtau = kap ds (kap = 0: the thin limit): the photons a it
 // absorbs per unit photon rate and its rate gseg. Gray: a = P (1 - e^{-dtau}). kFreq, integrated over
 // the blackbody spectrum (V.spec), the ray's budget P is its geometric share and the photons it still
@@ -236,7 +245,7 @@ __device__ __forceinline__ int wrapn(const int v, const int n)
 // equal near the switch), and deposits at the thin rate P Psi(tau) where kap = 0.
 template <class R, bool kFreq>
 __device__ __forceinline__ void segment_eq1(const SolveView<R>& V, R P, R tau, R ctau, R G, R kap, R ds, R dtau, R& a,
-                                            R& gseg)
+                                            R& gseg, PhiCache<R>& pc)
 {
     using I = Ieee<R>;
     if constexpr (kFreq) {
@@ -244,18 +253,24 @@ __device__ __forceinline__ void segment_eq1(const SolveView<R>& V, R P, R tau, R
         R phi0, psi0, phi1, psi1;
         if (I::pos(kap)) {
             if (dtau >= (sizeof(R) == 4 ? (R)1e-2 : (R)1e-6)) {
-                spec_eval<R>(V.spec, t0, phi0, psi0);
+                if (pc.ok) phi0 = pc.phi;
+                else spec_eval<R>(V.spec, t0, phi0, psi0);
                 spec_eval<R>(V.spec, t0 + dtau, phi1, psi1);
                 a = P * (phi0 - phi1);
+                pc.phi = phi1;
+                pc.ok = true;
             } else {
                 spec_eval<R>(V.spec, t0 + (R)0.5 * dtau, phi0, psi0);
                 a = P * (dtau * psi0);
+                pc.ok = false;
             }
             gseg = I::qdiv(a * G, kap);
         } else {
             spec_eval<R>(V.spec, t0, phi0, psi0);
             a = (R)0;
             gseg = ((P * psi0) * G) * ds;
+            pc.phi = phi0;                  // tau does not move in an ionized cell
+            pc.ok = true;
         }
     } else if (I::pos(kap)) {
         I::rate(P, G, kap, ds, dtau, a, gseg);
@@ -266,14 +281,17 @@ __device__ __forceinline__ void segment_eq1(const SolveView<R>& V, R P, R tau, R
 }
 
 // The photons a ray still carries, in units of its source's photon rate per ray: its compensated
-// budget P - cP (gray), or P Phi(tau - ctau) (kFreq).
+// budget P - cP (gray), or P Phi(tau - ctau) (kFreq; Phi from the cache when the last segment left it).
 template <class R, bool kFreq>
-__device__ __forceinline__ double ray_remaining(const SolveView<R>& V, R P, R tau, R cP, R ctau)
+__device__ __forceinline__ double ray_remaining(const SolveView<R>& V, R P, R tau, R cP, R ctau, PhiCache<R>& pc)
 {
     if constexpr (kFreq) {
-        R phi, psi;
-        spec_eval<R>(V.spec, Ieee<R>::sub(tau, ctau), phi, psi);
-        return widen(P) * widen(phi);
+        if (!pc.ok) {
+            R psi;
+            spec_eval<R>(V.spec, Ieee<R>::sub(tau, ctau), pc.phi, psi);
+            pc.ok = true;
+        }
+        return widen(P) * widen(pc.phi);
     } else {
         return widen(P) - widen(cP);
     }
@@ -294,7 +312,8 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
 {
     using I = Ieee<R>;
     // photons the ray still carries, in units of ph
-    auto remaining = [&]() -> double { return ray_remaining<R, kFreq>(V, P, tau, cP, ctau); };
+    PhiCache<R> pc{(R)0, false};
+    auto remaining = [&]() -> double { return ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc); };
     const int n = V.n;
     // the ray ends on its split sphere R_l or, with periodic boundaries, at the travel distance
     // sqrt(3) L_box if that comes first or at the same point, where it stops without splitting
@@ -413,7 +432,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
         const R kap = I::mag(kraw);
         const R dtau = I::mul(kap, ds);
         R a, gseg;
-        segment_eq1<R, kFreq>(V, P, tau, ctau, G, kap, ds, dtau, a, gseg);
+        segment_eq1<R, kFreq>(V, P, tau, ctau, G, kap, ds, dtau, a, gseg, pc);
         // ---- Eqs. 5-8: the share f kept in this cell and the neighbour's deposit
         R f = (R)1, g2 = (R)0;
         int nbcell = -1;
@@ -1043,11 +1062,12 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
                       V.overlap_mode == RT_OVERLAP_NAIVE;
     const bool corr = V.overlap_mode != RT_OVERLAP_NONE;
     const long long nn = (long long)n * n;
-    const double B0 = ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
+    PhiCache<R> pc{(R)0, false};
+    const double B0 = ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
     ++T.rays;
     if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
         ++T.esc;
-        T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
+        T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
         return false;
     }
     const E* col = TE::ent(GL) + GL.row0[pix >> 5] * 32 + (pix & 31);
@@ -1093,7 +1113,7 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         const R kap = I::mag(kcur);
         const R dtau = I::mul(kap, ds);
         R a, gseg;
-        segment_eq1<R, kFreq>(V, P, tau, ctau, G, kap, ds, dtau, a, gseg);
+        segment_eq1<R, kFreq>(V, P, tau, ctau, G, kap, ds, dtau, a, gseg, pc);
         // ---- Eqs. 5-8
         R f = (R)1, g2 = (R)0;
         int nbcell = -1;
@@ -1126,16 +1146,16 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         ++seq;
         if (!I::lt(tau, taumax)) {             // photons spent
             ++T.dtau;
-            T.dropph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
+            T.dropph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
             break;
         }
         if (!steps) {                    // the segment ended on the end sphere
             if (!split_end) {            // travelled sqrt(3) L_box (Sec. 2.5.1)
                 ++T.esc;
-                T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
+                T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
             } else if (l + 1 > V.level_max) {
                 ++T.dlev;
-                T.dropph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
+                T.dropph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
             } else {
                 ++T.split;
                 split = true;
@@ -1148,7 +1168,7 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         }
         if (!next_in) {
             ++T.esc;
-            T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
+            T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
             break;
         }
         if (last) {                      // cannot happen: a table ends where every grid is left
@@ -1163,7 +1183,7 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         e = en;
     }
     T.seg += seq;
-    T.abs += ph * (B0 - ray_remaining<R, kFreq>(V, P, tau, cP, ctau));
+    T.abs += ph * (B0 - ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc));
     return split;
 }
 
@@ -1175,32 +1195,35 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
 // What only feeds the fields and the photon ledger runs on the FP32 pipe in double-float
 // pairs (dfloat.h, about 48 significant bits):
 //   - the Eq. 1 factor g(dtau) = (1 - e^{-dtau}) / dtau below dtau = 2, from the Taylor table of
-//     rate_table.h;
+//     rate_table.h (512 intervals, degree 4, in shared memory);
 //   - the ray's photon budget, carried as Q = P m_G 2^64, where G = m_G 2^e_G is the source's
 //     rate per unit budget and cell of path (the factor 2^64 keeps Q far inside the float
 //     range): a segment absorbs Q dtau g of it and deposits the rate Q g ds 2^(e_G - 64), which
 //     is Eq. 1 with V_box, P G ds g;
 //   - the Eqs. 5-8 shares and the Eq. 8 ratio kap / kap' (a reciprocal and one correction).
-// Each deposit is rounded to double once (one FP64 addition) for its atomic add. From
-// dtau = 2 on (an opaque cell, where most of the budget goes at once) the segment is evaluated
-// in FP64 with expm1 and a division, as in the FP64 form of march_ray_table.
+// Each deposit is rounded to double by integer operations (df_to_double_pos) for its atomic add.
+// From dtau = 2 on (an opaque cell, where most of the budget goes at once) the segment is
+// evaluated in FP64 with expm1 and a division, as in the FP64 form of march_ray_table.
 
-constexpr int kRateStride = 12;     // floats per row of the rate table in shared memory
+// The rate table in shared memory: two float4 arrays, row j's {c0, c0', c1, c1'} at 4 j and its
+// {c2, c2', c3, c4} at 4 (kRateIntervals + j), so each is one 16-byte load.
+constexpr int kRateSmem = 8 * kRateIntervals;
 
-// g(x) for 0 <= x < 2 from row j = floor(128 x) of the Taylor table:
-// c0 + r (c1 + r (c2 + r (c3 + r (c4 + r c5)))) with r = x - j/128 in [0, 1/128); the three
-// inner terms in float (below 2e-8 of g together), the three outer ones in double-float.
+// g(x) for 0 <= x < 2 from interval j = floor(256 x) of the Taylor table, expanded about y0 = 0
+// (j = 0) or the interval's midpoint (j + 1/2) / 256: c0 + r (c1 + r (c2 + r (c3 + r c4))) with
+// r = x - y0; the two inner terms in float (below 3e-9 of g together), the three outer ones in
+// double-float.
 __device__ __forceinline__ dflt rate_factor(const float* __restrict__ tab, const dflt x)
 {
-    const int j = min(__float2int_rz(__fmul_rn(x.h, 128.f)), kRateIntervals - 1);
-    const float4 A = *reinterpret_cast<const float4*>(tab + j * kRateStride);       // c0 c0' c1 c1'
-    const float4 B = *reinterpret_cast<const float4*>(tab + j * kRateStride + 4);   // c2 c2' c3 c4
-    const float c5 = tab[j * kRateStride + 8];
-    // r = x - j/128: the head difference is exact (Sterbenz for j >= 1; nothing is subtracted
+    const int j = min(__float2int_rz(__fmul_rn(x.h, 256.f)), kRateIntervals - 1);
+    const float4 A = *reinterpret_cast<const float4*>(tab + 4 * j);                          // c0 c0' c1 c1'
+    const float4 B = *reinterpret_cast<const float4*>(tab + 4 * (kRateIntervals + j));       // c2 c2' c3 c4
+    // r = x - y0: the head difference is exact (Sterbenz, x / y0 in [2/3, 4/3] for j >= 1; y0 = 0
     // for j = 0); with x's tail it is renormalised, so that the cross terms below stay small
-    const dflt r = df_two_sum(__fsub_rn(x.h, __fmul_rn(__int2float_rn(j), 0.0078125f)), x.l);
+    const float y0 = j ? __fmul_rn(__fadd_rn(__int2float_rn(j), 0.5f), 0.00390625f) : 0.f;
+    const dflt r = df_two_sum(__fsub_rn(x.h, y0), x.l);
     const float rh = r.h, rl = r.l;
-    const float t = __fmaf_rn(__fmaf_rn(c5, rh, B.w), rh, B.z);
+    const float t = __fmaf_rn(B.w, rh, B.z);
     // u = c2 + r t
     const dflt u = df_fast_two_sum(B.x, __fmaf_rn(rh, t, __fmaf_rn(rl, t, B.y)));
     // v = c1 + r u
@@ -1359,7 +1382,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
             }
         }
         if (keep_all) {
-            dep = opaque ? scale2(wd, e_dep) : df_to_double(w, e_dep);
+            dep = opaque ? scale2(wd, e_dep) : df_to_double_pos(w, e_dep);
         } else {
             const double fd = TE::f(e);
             if (opaque) {
@@ -1368,7 +1391,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
             } else {
                 const dflt f = df_of(fd);
                 const dflt fw = df_mul(f, w);
-                dep = df_to_double(squared ? df_mul(f, fw) : fw, e_dep);
+                dep = df_to_double_pos(squared ? df_mul(f, fw) : fw, e_dep);
                 if (second && I::pos(kap)) {       // kap = 0 (an ionized cell) sends 0 to c'
                     // Eq. 8: (1 - f) w kap / kap', the ratio of the mantissas by a float reciprocal
                     // and one correction, the exponents applied when rounding to double
@@ -1381,7 +1404,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
                     const float rho = __fmaf_rn(-q0, mn.l, __fadd_rn(__fsub_rn(__fsub_rn(mk.h, p), pe), mk.l));
                     const dflt ratio = {q0, __fmul_rn(rho, r0)};
                     const dflt om = {__fsub_rn(1.0f, f.h), -f.l};
-                    dep2 = df_to_double(df_mul(df_mul(om, w), ratio), e_dep + ek - en);
+                    dep2 = df_to_double_pos(df_mul(df_mul(om, w), ratio), e_dep + ek - en);
                 }
             }
         }
@@ -1591,13 +1614,13 @@ __global__ void __launch_bounds__(256, TableOccupancy<R>::blocks) march_table_ke
     const long long c1 = A.in_count ? min((long long)A.c1, (long long)A.c0 + 4LL * (long long)*A.in_count) : (long long)A.c1;
     Tally T;
     T.clear();
-    // FP64 gray march: the Eq. 1 rate table in shared memory (rows padded to 12 floats, 16-byte aligned)
+    // FP64 gray march: the Eq. 1 rate table in shared memory (two float4 arrays, see rate_factor)
     constexpr bool kDf = sizeof(R) == 8 && !kFreq;
-    __shared__ __align__(16) float rtab[kDf ? kRateIntervals * kRateStride : 4];
+    __shared__ __align__(16) float rtab[kDf ? kRateSmem : 4];
     if constexpr (kDf) {
-        for (int i = threadIdx.x; i < kRateIntervals * kRateStride; i += blockDim.x) {
-            const int row = i / kRateStride, c = i - row * kRateStride;
-            rtab[i] = c < kRateCoefs ? kRateTable[row * kRateCoefs + c] : 0.f;
+        for (int i = threadIdx.x; i < kRateSmem; i += blockDim.x) {
+            const int row = (i >> 2) % kRateIntervals, half = (i >> 2) / kRateIntervals;
+            rtab[i] = kRateTable[row * kRateCoefs + 4 * half + (i & 3)];
         }
         __syncthreads();
     }

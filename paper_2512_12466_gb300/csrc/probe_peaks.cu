@@ -1,6 +1,7 @@
-// Arithmetic-peak probe (a measurement tool beside the library, not part of its ABI): fused
+// Throughput probe (a measurement tool beside the library, not part of its ABI): fused
 // multiply-add throughput of the FP32 and FP64 pipes on the current device, the denominators of
-// the march kernels' ALU rooflines. Every thread runs eight independent FMA chains (enough to
+// the march kernels' ALU rooflines, and FP64 atomic-add throughput, the denominator of their
+// deposit roofline. Every thread runs eight independent FMA chains (enough to
 // cover the pipe latency at full occupancy); the grid fills every SM; the kernel is timed with
 // CUDA events after a warm-up launch. One FMA counts two floating-point operations.
 #include <cuda_runtime.h>
@@ -61,9 +62,69 @@ int run(const int64_t iters, double* tflops, double* ms_out)
     return 0;
 }
 
+// FP64 atomic adds whose result is unused (reductions performed in L2), as the march's deposits
+// are: each thread adds `iters` times into an array of n doubles, at addresses spread by a hash
+// (pattern 0: every lane of a warp a different, random cell) or consecutive within a warp (pattern
+// 1: the lanes of a warp cover 32 neighbouring cells).
+__global__ void __launch_bounds__(256) red_f64(double* __restrict__ a, const int64_t n, const int64_t iters,
+                                                const int pattern)
+{
+    const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (int64_t i = 0; i < iters; ++i) {
+        uint64_t k;
+        if (pattern == 0) {
+            uint64_t z = gid * 0x9e3779b97f4a7c15ULL + (uint64_t)i * 0xbf58476d1ce4e5b9ULL;
+            z ^= z >> 31;
+            z *= 0x94d049bb133111ebULL;
+            z ^= z >> 29;
+            k = z % (uint64_t)n;
+        } else {
+            k = ((gid >> 5) * 0x9e3779b97f4a7c15ULL + (uint64_t)i * 40503ULL) % (uint64_t)(n / 32) * 32 + (gid & 31);
+        }
+        atomicAdd(a + k, 1.0);
+    }
+}
+
+int run_red(const int64_t n, const int64_t iters, const int pattern, double* per_s, double* ms_out)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -3;
+    double* a = nullptr;
+    if (cudaMalloc(&a, sizeof(double) * (size_t)n) != cudaSuccess) return -2;
+    cudaMemset(a, 0, sizeof(double) * (size_t)n);
+    const int grid = sms * 8;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    red_f64<<<grid, 256>>>(a, n, iters / 8 + 1, pattern);                    // warm-up
+    cudaEventRecord(e0);
+    red_f64<<<grid, 256>>>(a, n, iters, pattern);
+    cudaEventRecord(e1);
+    const cudaError_t err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(a);
+    if (err != cudaSuccess) return -3;
+    *per_s = (double)iters * grid * 256.0 / ((double)ms * 1e-3);
+    *ms_out = ms;
+    return 0;
+}
+
 }  // namespace
 
 extern "C" {
+
+// FP64 atomic adds per second into an array of n doubles (n >= 32, a multiple of 32), pattern 0
+// random cells, 1 neighbouring cells per warp; `iters` adds per thread. 0 on success.
+int nyxrt_probe_red_f64(int64_t n, int64_t iters, int pattern, double* per_s, double* ms)
+{
+    if (!per_s || !ms || iters < 1 || n < 32 || n % 32 || (pattern != 0 && pattern != 1)) return -1;
+    return run_red(n, iters, pattern, per_s, ms);
+}
+
 
 // FMA throughput of one precision (32: FP32, 64: FP64) over `iters` iterations of eight chains per
 // thread: *tflops = 2 x FMAs / kernel time, *ms the kernel time. 0 on success, a negative code if

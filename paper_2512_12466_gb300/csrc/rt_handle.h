@@ -156,6 +156,10 @@ int handle_reconfigure(rt_handle* h, const rt_config* cfg);
 int prepare_sources_many(rt_handle* const* hs, int count, int* rcs);
 int batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count);
 int batch_run_direct(rt_batch* b, float* ms);
+// The two halves of batch_run_direct: enqueue the run (returns once it is on the device), then
+// wait for it and check it.
+int batch_launch(rt_batch* b);
+int batch_finish(rt_batch* b, float* ms);
 void batch_fill_stats(const rt_batch* b, size_t i, float ms, rt_stats* st);
 cudaStream_t batch_stream(const rt_batch* b);
 

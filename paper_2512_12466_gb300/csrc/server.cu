@@ -383,8 +383,9 @@ void worker_main(rt_server* s)
     }
 }
 
-// Copy results out, return each request's handle to the pool, mark it done
-// (two finisher threads share the queue of traced batches).
+// Copy results out, return each request's handle to the pool, mark it done (finisher threads share
+// the queue of traced batches). A batch's result copies are all issued first, each on its request's
+// stream, and waited for afterwards, so they overlap one another on the copy engines.
 void finisher_main(rt_server* s)
 {
     cudaSetDevice(s->device);
@@ -399,36 +400,49 @@ void finisher_main(rt_server* s)
             const double now = ms_since(s->t0);
             for (SrvReq* r : job.first) s->wait_finish_ms += now - r->t_traced;
         }
-        for (SrvReq* r : job.first) {
-            const Clock::time_point tf = Clock::now();
+        const Clock::time_point tf = Clock::now();
+        std::vector<int> rcs(job.first.size());
+        std::vector<std::string> errs(job.first.size());
+        for (size_t k = 0; k < job.first.size(); ++k) {
+            SrvReq* r = job.first[k];
             trace(s, "fin_begin", r->id);
-            int rrc = r->rc;
-            std::string err = rrc != RT_OK ? r->err : std::string();
+            rcs[k] = r->rc;
+            if (rcs[k] != RT_OK) {
+                errs[k] = r->err;
+                continue;
+            }
+            rt_handle* h = r->h;
+            const size_t fb = sizeof(double) * (size_t)h->ncell;
+            if ((r->gamma_out && cudaMemcpyAsync(r->gamma_out, h->d_gamma, fb, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) ||
+                (r->heat_out && cudaMemcpyAsync(r->heat_out, h->d_heat, fb, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)) {
+                cudaGetLastError();
+                rcs[k] = RT_ECUDA;
+                errs[k] = "result copy failed";
+            }
+        }
+        for (size_t k = 0; k < job.first.size(); ++k) {
+            SrvReq* r = job.first[k];
             rt_handle* h = r->h;
             r->h = nullptr;
-            if (rrc == RT_OK) {
-                const size_t fb = sizeof(double) * (size_t)h->ncell;
-                if ((r->gamma_out && cudaMemcpyAsync(r->gamma_out, h->d_gamma, fb, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) ||
-                    (r->heat_out && cudaMemcpyAsync(r->heat_out, h->d_heat, fb, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) ||
-                    cudaStreamSynchronize(h->stream) != cudaSuccess) {
-                    cudaGetLastError();
-                    rrc = RT_ECUDA;
-                    err = "result copy failed";
-                }
+            if (rcs[k] == RT_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) {
+                cudaGetLastError();
+                rcs[k] = RT_ECUDA;
+                errs[k] = "result copy failed";
             }
             trace(s, "fin_copied", r->id);
-            const bool keep = rrc == RT_OK && !h->sticky;
+            const bool keep = rcs[k] == RT_OK && !h->sticky;
             if (!keep) release_handle(s, h);
             std::lock_guard<std::mutex> lk(s->mu);
             if (keep) pool_put_locked(s, h);
-            s->finish_ms += ms_since(tf);
-            if (rrc == RT_OK)
+            if (rcs[k] == RT_OK)
                 for (int l = 0; l < RT_MAX_LEVELS; ++l) s->segments += r->st.segments[l];
-            finish_locked(s, r, rrc, err);
+            finish_locked(s, r, rcs[k], errs[k]);
             s->cv_done.notify_all();
             s->cv_load.notify_all();
             trace(s, "done", r->id);
         }
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->finish_ms += ms_since(tf);
     }
 }
 
@@ -485,7 +499,7 @@ int rt_server_create(const rt_server_config* cfg, rt_server** out)
     cudaGetLastError();
     for (int i = 0; i < std::max(1, cfg->loaders); ++i) s->loaders.emplace_back(loader_main, s);
     s->worker = std::thread(worker_main, s);
-    for (int i = 0; i < 2; ++i) s->finishers.emplace_back(finisher_main, s);
+    for (int i = 0; i < 4; ++i) s->finishers.emplace_back(finisher_main, s);
     *out = s;
     return RT_OK;
 }

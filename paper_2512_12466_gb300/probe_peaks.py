@@ -5,7 +5,8 @@ copy bandwidth from pinned memory (the serving form's transfer roofline):
     python -m paper_2512_12466_gb300.probe_peaks [--copies]
 
 Prints one JSON line: TFLOP/s (2 flops per FMA) and FMA instructions per second for each
-precision, best of three timed launches; with --copies, GB/s of 128 MiB copies host to device,
+precision, best of three timed launches; FP64 atomic adds per second into an L2-resident and a
+2 GB array, at random and at neighbouring cells; with --copies, GB/s of 128 MiB copies host to device,
 device to host and both at once, on 1, 2 and 4 streams (torch copies, wall time of 8 rounds).
 """
 import ctypes as C
@@ -33,6 +34,23 @@ def main() -> int:
                 best, ms_best = tf.value, ms.value
         out[f"fp{bits}"] = {"tflops": best, "fma_per_s": best * 1e12 / 2, "kernel_ms": ms_best, "iters": iters}
     out["fp32_over_fp64"] = out["fp32"]["tflops"] / out["fp64"]["tflops"]
+    # FP64 atomic adds (the march's deposits): an L2-resident array the size of a 128^3 Gamma grid
+    # and one of 2 GB (beyond L2), random cells and neighbouring cells per warp
+    lib.nyxrt_probe_red_f64.argtypes = [C.c_int64, C.c_int64, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.nyxrt_probe_red_f64.restype = C.c_int
+    red = {}
+    for label, n in (("l2_128cubed", 128 ** 3), ("dram_2GB", 1 << 28)):
+        for pname, pat in (("random", 0), ("neighbours", 1)):
+            best = 0.0
+            for _ in range(3):
+                ps, ms = C.c_double(), C.c_double()
+                rc = lib.nyxrt_probe_red_f64(n, 256, pat, C.byref(ps), C.byref(ms))
+                if rc != 0:
+                    print(json.dumps({"error": f"atomic probe returned {rc}"}))
+                    return 1
+                best = max(best, ps.value)
+            red[f"{label}_{pname}_per_s"] = best
+    out["red_add_f64"] = red
     if "--copies" in sys.argv[1:]:
         out["copies_gbs"] = copy_bandwidth()
     print(json.dumps(out))

@@ -782,3 +782,44 @@ def test_merge_two_sources_in_one_bubble():
     assert merged == 4e51
     # flux-weighted centroid (25, 24, 24) snaps to the nearest member (26, 24, 24)
     assert [26, 24, 24] in mc.tolist() and [2, 2, 2] in mc.tolist()
+
+
+# ------------------------------------------------------------------ automerge switch, heating
+
+def test_automerge_switch_equals_forced_or_no_merge():
+    """Sec. 2.8: automerge (merge_mode 2) runs Alg. 3 in a step exactly when the mean ionized
+    fraction exceeds the threshold. Below it the step equals the step without merging, above it
+    the step with merging forced (catalog, bookkeeping and Gamma)."""
+    n = 24
+    zz, yy, xx = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    x = (np.sqrt((xx - 12) ** 2 + (yy - 12) ** 2 + (zz - 12) ** 2) <= 7.0).astype(float)
+    n_h = np.full((n, n, n), 2e-4)
+    cells = np.array([[10, 12, 12], [14, 12, 12], [12, 10, 13], [2, 2, 2]], np.int32)
+    ndot = np.array([1e51, 2e51, 3e51, 1e51])
+    box = n * 7.117e23
+    xbar = float(x.mean())
+    kw = dict(n_th_cm3=2e-6, merge_rmax_cells=10.0)
+    off = oracle.run(n_h, x, cells, ndot, box, merge_mode=0, **kw)
+    forced = oracle.run(n_h, x, cells, ndot, box, merge_mode=1, **kw)
+    assert forced["stats"]["merged"] == 1 and len(forced["emit_ndot"]) < len(off["emit_ndot"])
+    for thr, ref in ((2.0 * xbar, off), (0.5 * xbar, forced)):
+        a = oracle.run(n_h, x, cells, ndot, box, merge_mode=2, automerge_xbar=thr, **kw)
+        assert a["stats"]["merged"] == ref["stats"]["merged"]
+        assert np.array_equal(a["emit_cells"], ref["emit_cells"]) and np.array_equal(a["emit_ndot"], ref["emit_ndot"])
+        for k in ("rays", "splits", "segments", "secondary"):
+            assert a["stats"][k] == ref["stats"][k]
+        assert np.array_equal(a["gamma"], ref["gamma"])
+
+
+@pytest.mark.parametrize("mode", [0, 2, 3])
+def test_heating_equals_absorbed_photon_energy(mode):
+    """The heating grid against the ray ledger, an independent sum: with a photon-conserving
+    overlap treatment every absorbed photon is deposited, so the total heating over the box,
+    sum(heat) dx^3, equals e_heat times the photons absorbed along the rays (photons/s)."""
+    w = I.random_small(16, 5, seed=41 + mode, x_mode="patchy", box_cm=16 * 7e22)
+    e = 2.5e-12
+    r = oracle.run_workload(w, overlap_mode=mode, n_th_cm3=0.3 * float(w.n_h.mean()), e_heat_erg=e)
+    vol = (w.box_cm / w.n) ** 3
+    total = float(r["heat"].sum()) * vol
+    assert r["stats"]["absorbed_ph"] > 0
+    assert abs(total / (e * r["stats"]["absorbed_ph"]) - 1) < 1e-12
