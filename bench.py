@@ -573,14 +573,21 @@ def bench_serving(nyx, torch, n_req: int):
               "gpu_busy_ms": st["busy_ms"], "wall_s": t_end, "completed": st["completed"], "failed": st["failed"],
               "host_phase_ms": {k: st[k] for k in ("load_ms", "src_ms", "bind_ms", "run_ms", "finish_ms", "wait_admit_ms",
                                                    "wait_batch_ms", "wait_finish_ms")}}
-    # ---- capacity: every request submitted at once, each path as fast as it goes
+    # ---- capacity: every request submitted at once, each path as fast as it goes. The served form's
+    # first burst meets a handle pool sized by the Poisson stream and creates most handles; the timed
+    # burst is the second, the server's steady state (the plain arms reuse one warm handle per size).
+    def burst():
+        t0 = time.perf_counter()
+        ids = [srv.submit(q["n"], q["box"], q["n_h"], q["x"], q["cells"], q["ndot"], gamma=ring[q["n"]][j % 96],
+                          heat=None, n_th_cm3=q["n_th"], n_min_ray=4.0, tau_max=30.0) for j, q in enumerate(reqs[:96])]
+        for i in ids:
+            srv.poll(i, wait_s=600.0)
+        return 96 / (time.perf_counter() - t0)
+
+    cap_first = burst()
+    st = srv.stats()
     b0 = st["batches"]
-    t0 = time.perf_counter()
-    ids = [srv.submit(q["n"], q["box"], q["n_h"], q["x"], q["cells"], q["ndot"], gamma=ring[q["n"]][j % 96],
-                      heat=None, n_th_cm3=q["n_th"], n_min_ray=4.0, tau_max=30.0) for j, q in enumerate(reqs[:96])]
-    for i in ids:
-        srv.poll(i, wait_s=600.0)
-    cap_served = 96 / (time.perf_counter() - t0)
+    cap_served = burst()
     st2 = srv.stats()
     cap_batches = st2["batches"] - b0
     cap_phase = {k: st2[k] - st[k] for k in ("load_ms", "src_ms", "bind_ms", "run_ms", "finish_ms", "wait_admit_ms",
@@ -649,6 +656,7 @@ def bench_serving(nyx, torch, n_req: int):
             "capacity_rps": {"served_fp32_batched": cap_served, "plain_fp64_per_request": cap_plain,
                              "plain_fp32_per_request": cap_plain32,
                              "factor": cap_served / cap_plain, "factor_same_precision": cap_served / cap_plain32,
+                             "served_first_burst": cap_first,
                              "requests": 96, "batches": cap_batches, "wall_ms": 96e3 / cap_served,
                              "gpu_busy_fraction": cap_phase["busy_ms"] / (96e3 / cap_served),
                              "served_host_phase_ms": cap_phase},

@@ -247,7 +247,7 @@ int rt_destroy(rt_handle* h);
  * 16-byte ones for the FP64 march (each built when that precision first
  * needs the level), within a budget of an eighth of the device's memory
  * (environment variable NYXRT_GEOMETRY_BUDGET_MB overrides it); levels over
- * budget walk their rays. The batched form reads the FP32 tables only. */
+ * budget walk their rays. The batched form reads them in both precisions. */
 int64_t rt_geometry_table_bytes(int32_t device);
 
 /* Phi(tau) and the thin rate Psi(tau) = -dPhi/dtau of RT_SPECTRUM_BLACKBODY at
@@ -287,8 +287,8 @@ typedef struct rt_batch rt_batch;
 typedef struct rt_batch_params {
     int32_t block;          /* threads per block: 128 or 256 */
     int32_t blocks_per_sm;  /* co-resident blocks per SM, 1 .. the occupancy limit; 0: as many as fit
-                               (a batch whose solves share N_min reads the FP32 geometry tables, with
-                               a higher limit than the walking kernel) */
+                               (a batch whose solves share N_min reads the geometry tables of its
+                               precision, with a limit of its own) */
     int32_t tile;           /* children a warp claims from the work queue at once (multiple of 32) */
     int32_t heavy_shift;    /* a solve that traced 2^heavy_shift segments or more in its last run
                                takes the heavy path (before any run every gray solve is light);

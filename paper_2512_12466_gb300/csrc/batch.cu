@@ -66,7 +66,7 @@ struct rt_batch {
     int64_t cap_src = 0, cap_solves = 0;
     int table_level = 0;
     const int4* dirs = nullptr;
-    bool use_geo = false;                  // FP32 solves, every level tabled: the persistent kernel reads tables
+    bool use_geo = false;                  // every level tabled: the persistent kernel reads tables
     bool geo_shared = false;               // every solve shares one split radius and boundary: tables apply
     bool geo_ok[RT_MAX_LEVELS + 1] = {};   // level l has a table in the batch's precision
     GeomLevel geo[RT_MAX_LEVELS + 1];
@@ -82,6 +82,7 @@ struct rt_batch {
     BatchSolve* d_solves = nullptr;
     DevStats* d_stats = nullptr;
     DevStats* h_stats = nullptr;           // pinned
+    DevStats* m_stats = nullptr;           // its device address (mapped)
     SrcEntry* d_src = nullptr;
     int64_t nsrc = 0;
     RayStore rays[RT_MAX_LEVELS + 1];
@@ -89,6 +90,7 @@ struct rt_batch {
     unsigned long long* d_tiles = nullptr;
     unsigned* d_err = nullptr;
     unsigned* h_err = nullptr;             // pinned
+    unsigned* m_err = nullptr;             // its device address (mapped)
     rt_batch_params params{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -394,9 +396,13 @@ int enqueue(rt_batch* b)
                                        b->d_stats + i, s);
     }
     B_CUDA(b, cudaGetLastError(), "finalize launch");
-    B_CUDA(b, cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(DevStats) * b->hs.size(), cudaMemcpyDeviceToHost, s),
-           "stats read");
-    B_CUDA(b, cudaMemcpyAsync(b->h_err, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "error read");
+    // statistics and error word written into pinned memory by a kernel, not copied: a server's
+    // result copies of the previous batch may occupy the copy engines
+    ReadbackList rb;
+    rb.add(b->d_stats, b->m_stats, sizeof(DevStats) * b->hs.size());
+    rb.add(b->d_err, b->m_err, sizeof(unsigned));
+    b->launches += launch_readback(rb, s);
+    B_CUDA(b, cudaGetLastError(), "readback launch");
     return RT_OK;
 }
 
@@ -595,6 +601,7 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
         B_CUDA(b, cudaMalloc(&b->d_tiles, sizeof(unsigned long long) * kMaxSlices), "counters");
         B_CUDA(b, cudaMalloc(&b->d_err, sizeof(unsigned)), "error word");
         B_CUDA(b, cudaMallocHost(&b->h_err, sizeof(unsigned)), "error word");
+        B_CUDA(b, cudaHostGetDevicePointer(reinterpret_cast<void**>(&b->m_err), b->h_err, 0), "error word");
         *b->h_err = 0;
         B_CUDA(b, cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event");
         for (int k = 0; k < kLanes; ++k) {
@@ -627,7 +634,7 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
                                           &b->geo[l]);
             all = all && b->geo_ok[l];
         }
-        b->use_geo = b->precision == RT_FP32 && all && every_table;
+        b->use_geo = all && every_table;
     }
     b->chunk.assign(b->hs.size(), 1);
     b->tlev.assign(b->hs.size(), 0);
@@ -659,10 +666,12 @@ int nyx::batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count)
         cudaFreeHost(b->h_stats);
         b->d_stats = nullptr;
         b->h_stats = nullptr;
+        b->m_stats = nullptr;
         b->d_solves = nullptr;
         b->cap_solves = std::max<int64_t>(std::max<int64_t>(ns, 2 * b->cap_solves), 256);
         B_CUDA(b, cudaMallocAsync(&b->d_stats, sizeof(DevStats) * (size_t)b->cap_solves, b->stream), "stats");
         B_CUDA(b, cudaMallocHost(&b->h_stats, sizeof(DevStats) * (size_t)b->cap_solves), "stats");
+        B_CUDA(b, cudaHostGetDevicePointer(reinterpret_cast<void**>(&b->m_stats), b->h_stats, 0), "stats");
         B_CUDA(b, cudaMallocAsync(&b->d_solves, sizeof(BatchSolve) * (size_t)b->cap_solves, b->stream), "solve table");
     }
     b->hsolve.assign(b->hs.size(), BatchSolve{});

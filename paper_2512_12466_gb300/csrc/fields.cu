@@ -180,4 +180,18 @@ int launch_mean_nh(const double* nh, int64_t ncell, double* out, cudaStream_t s)
     return 1;
 }
 
+__global__ void __launch_bounds__(256) readback_kernel(const ReadbackList r)
+{
+    for (int k = 0; k < r.n; ++k)
+        for (int i = threadIdx.x; i < r.words[k]; i += blockDim.x) r.dst[k][i] = r.src[k][i];
+    __threadfence_system();
+}
+
+int launch_readback(const ReadbackList& r, cudaStream_t s)
+{
+    if (r.n == 0) return 0;
+    readback_kernel<<<1, 256, 0, s>>>(r);
+    return 1;
+}
+
 }  // namespace nyx

@@ -250,12 +250,12 @@ __device__ __forceinline__ void segment_eq1(const SolveView<R>& V, R P, R tau, R
     using I = Ieee<R>;
     if constexpr (kFreq) {
         const R t0 = I::sub(tau, ctau);
-        R phi0, psi0, phi1, psi1;
+        R phi0, psi0, phi1;
         if (I::pos(kap)) {
             if (dtau >= (sizeof(R) == 4 ? (R)1e-2 : (R)1e-6)) {
                 if (pc.ok) phi0 = pc.phi;
-                else spec_eval<R>(V.spec, t0, phi0, psi0);
-                spec_eval<R>(V.spec, t0 + dtau, phi1, psi1);
+                else phi0 = spec_phi<R>(V.spec, t0);
+                phi1 = spec_phi<R>(V.spec, t0 + dtau);
                 a = P * (phi0 - phi1);
                 pc.phi = phi1;
                 pc.ok = true;
@@ -287,8 +287,7 @@ __device__ __forceinline__ double ray_remaining(const SolveView<R>& V, R P, R ta
 {
     if constexpr (kFreq) {
         if (!pc.ok) {
-            R psi;
-            spec_eval<R>(V.spec, Ieee<R>::sub(tau, ctau), pc.phi, psi);
+            pc.phi = spec_phi<R>(V.spec, Ieee<R>::sub(tau, ctau));
             pc.ok = true;
         }
         return widen(P) * widen(pc.phi);
@@ -1658,10 +1657,21 @@ __global__ void __launch_bounds__(256, TableOccupancy<R>::blocks) march_table_ke
 // for every lane (kernel parameters, not per-lane loads) and no tally changes hands. Only then does
 // the table-driven kernel fit four blocks per SM; with per-lane solve parameters it takes three.
 template <class R, bool kHash, bool kTable, bool kSingle>
-__global__ void __launch_bounds__(256, (kTable && kSingle) ? 4 : MarchOccupancy<R>::blocks) batch_kernel(const BatchArgs<R> A)
+__global__ void __launch_bounds__(256, (kTable && kSingle) ? TableOccupancy<R>::blocks : MarchOccupancy<R>::blocks)
+    batch_kernel(const BatchArgs<R> A)
 {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     const int lane = threadIdx.x & 31;
+    // FP64 solves on the geometry tables: the Eq. 1 rate table of the double-float march in shared memory
+    constexpr bool kDf = kTable && sizeof(R) == 8;
+    __shared__ __align__(16) float rtab[kDf ? kRateSmem : 4];
+    if constexpr (kDf) {
+        for (int i = threadIdx.x; i < kRateSmem; i += blockDim.x) {
+            const int row = (i >> 2) % kRateIntervals, half = (i >> 2) / kRateIntervals;
+            rtab[i] = kRateTable[row * kRateCoefs + 4 * half + (i & 3)];
+        }
+        __syncthreads();
+    }
     int lev[RT_MAX_LEVELS + 1];
     long long tot[RT_MAX_LEVELS + 1], nxt[RT_MAX_LEVELS + 1];
     int depth = 0;
@@ -1726,8 +1736,10 @@ __global__ void __launch_bounds__(256, (kTable && kSingle) ? 4 : MarchOccupancy<
                     V.rs = bs.rs;
                     V.tau_max = (R)bs.tau_max;
                     V.src_off = bs.src_off - A.src_base;
-                    if constexpr (kTable) {
-                        static_assert(sizeof(R) == 4, "geometry tables serve the FP32 march");
+                    if constexpr (kDf) {
+                        split = march_ray_table_df<kHash>(V, rtab, A.geo[l], A.err, l, si, pix, P, tau, se, dirs[pix], T, oP,
+                                                          otau);
+                    } else if constexpr (kTable) {
                         split = march_ray_table<float, kHash, false>(V, A.geo[l], A.err, l, si, pix, P, tau, cP, ctau, se, dirs[pix],
                                                        T, oP, otau, ocP, octau);
                     } else {
@@ -1834,6 +1846,9 @@ static const void* batch_kernel_pick(bool hash, bool table)
         return hash ? (const void*)batch_kernel<float, true, false, kSingle>
                     : (const void*)batch_kernel<float, false, false, kSingle>;
     } else {
+        if (table)
+            return hash ? (const void*)batch_kernel<double, true, true, kSingle>
+                        : (const void*)batch_kernel<double, false, true, kSingle>;
         return hash ? (const void*)batch_kernel<double, true, false, kSingle>
                     : (const void*)batch_kernel<double, false, false, kSingle>;
     }
@@ -1871,7 +1886,7 @@ int batch_blocks_per_sm(int precision, int block, bool table, bool single)
     int best = 1 << 30;
     for (int hash = 0; hash < 2; ++hash) {
         const void* k = precision == RT_FP32 ? batch_kernel_for<float>(hash, table, single)
-                                             : batch_kernel_for<double>(hash, false, single);
+                                             : batch_kernel_for<double>(hash, table, single);
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0);
         best = std::min(best, nb);

@@ -638,13 +638,13 @@ int handle_reconfigure(rt_handle* h, const rt_config* cfg)
     return RT_OK;
 }
 
-// The source stage of many handles at once: for handles without merging, every
-// kernel (validation, dedup + sort, mean n_H, emission with the count read on
-// the device) and the statistics readback are enqueued on all handles' streams
-// before a single wait; handles with merging take the synchronous path.
-// rcs[i] receives handle i's outcome (one bad request fails alone); returns
-// the number of handles that failed.
-int prepare_sources_many(rt_handle* const* hs, int count, int* rcs)
+// The source stage of many handles at once, in two halves. sources_enqueue_many enqueues, for handles
+// without merging, every kernel (validation, dedup + sort, mean n_H, emission with the count read on
+// the device) and the statistics readback on all handles' streams; handles with merging take the
+// synchronous path there. sources_wait_many then waits once per stream and records the results.
+// rcs[i] receives handle i's outcome (one bad request fails alone); each returns the number of
+// handles that failed so far.
+int sources_enqueue_many(rt_handle* const* hs, int count, int* rcs)
 {
     auto enqueue = [](rt_handle* h) -> int {
         cudaStream_t s = h->stream;
@@ -659,12 +659,14 @@ int prepare_sources_many(rt_handle* const* hs, int count, int* rcs)
             h->launches += launch_mean_nh(h->d_nh, h->ncell, h->d_scalar, s);
         }
         if (h->nsrc > 0) h->launches += launch_build_emit_dev(h->sw, h->nsrc, h->s_over_dx2, h->d_emit, h->d_st, s);
+        // statistics, count and mean written into the pinned block by a kernel (a server's result
+        // copies of other requests may occupy the copy engines)
+        ReadbackList rb;
+        rb.add(h->d_st, pinned_dev(h, h->h_st), sizeof(DevStats));
+        if (h->nsrc > 0) rb.add(h->sw.count, pinned_dev(h, h->h_i32), sizeof(int32_t));
+        if (h->cfg.n_th_cm3 < 0) rb.add(h->d_scalar, pinned_dev(h, h->h_f64), sizeof(double));
+        h->launches += launch_readback(rb, s);
         RT_LAUNCHED(h, "source stage launch");
-        RT_CUDA(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "stats read");
-        if (h->nsrc > 0)
-            RT_CUDA(h, cudaMemcpyAsync(h->h_i32, h->sw.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "count read");
-        if (h->cfg.n_th_cm3 < 0)
-            RT_CUDA(h, cudaMemcpyAsync(h->h_f64, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s), "mean read");
         return RT_OK;
     };
     int failed = 0;
@@ -673,7 +675,14 @@ int prepare_sources_many(rt_handle* const* hs, int count, int* rcs)
         rcs[i] = RT_OK;
         if (h->src_ready) continue;
         rcs[i] = h->cfg.merge_mode != RT_MERGE_OFF ? handle_prepare_sources(h) : enqueue(h);
+        failed += rcs[i] != RT_OK;
     }
+    return failed;
+}
+
+int sources_wait_many(rt_handle* const* hs, int count, int* rcs)
+{
+    int failed = 0;
     for (int i = 0; i < count; ++i) {
         rt_handle* h = hs[i];
         if (rcs[i] == RT_OK && !h->src_ready) {
@@ -871,6 +880,7 @@ int rt_create(const rt_config* cfg, void* cuda_stream, rt_handle** out)
         const size_t a = (sizeof(DevStats) + 63) & ~size_t(63);
         const size_t b = (sizeof(unsigned long long) * (RT_MAX_LEVELS + 1) + 63) & ~size_t(63);
         e = e ? e : cudaMallocHost(&h->h_pin, a + b + 128);
+        e = e ? e : cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->d_pin), h->h_pin, 0);
         if (e == cudaSuccess) {
             char* q = static_cast<char*>(h->h_pin);
             h->h_st = reinterpret_cast<DevStats*>(q);

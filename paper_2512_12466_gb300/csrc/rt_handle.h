@@ -117,6 +117,7 @@ struct rt_handle {
     unsigned long long* d_count = nullptr;   // one per level
     nyx::DevStats* d_st = nullptr;
     void* h_pin = nullptr;                   // one pinned block holding the four below
+    char* d_pin = nullptr;                   // the same block's device address (mapped)
     nyx::DevStats* h_st = nullptr;
     unsigned long long* h_count = nullptr;
     int32_t* h_i32 = nullptr;                // scratch
@@ -142,6 +143,12 @@ namespace nyx {
 
 int fail(rt_handle* h, int code, const std::string& msg);
 int cuda_fail(rt_handle* h, cudaError_t e, const char* what);
+// The device address of a pointer into the handle's pinned block.
+template <class T>
+inline T* pinned_dev(const rt_handle* h, T* host)
+{
+    return reinterpret_cast<T*>(h->d_pin + (reinterpret_cast<char*>(host) - static_cast<char*>(h->h_pin)));
+}
 int prepare_sources(rt_handle* h, bool* merged_out, int64_t* n_dedup_out);
 int ensure_directions(int device, int level, const int4** out, std::string& err);
 // The geometry table of a level for grids of n cells, with the entries of the FP32 march (fp64
@@ -153,7 +160,8 @@ bool geometry_level(int device, long long rq, int level, int n, long long rs, co
 int spectrum_table(int device, double t_bb, SpecTable<double>* d, SpecTable<float>* f, std::string& why);
 int handle_prepare_sources(rt_handle* h);
 int handle_reconfigure(rt_handle* h, const rt_config* cfg);
-int prepare_sources_many(rt_handle* const* hs, int count, int* rcs);
+int sources_enqueue_many(rt_handle* const* hs, int count, int* rcs);
+int sources_wait_many(rt_handle* const* hs, int count, int* rcs);
 int batch_bind(rt_batch* b, rt_handle* const* handles, int32_t count);
 int batch_run_direct(rt_batch* b, float* ms);
 // The two halves of batch_run_direct: enqueue the run (returns once it is on the device), then

@@ -134,7 +134,7 @@ struct BatchArgs {
     unsigned long long* tiles;       // per slice: tiles claimed (zeroed)
     int max_slices;
     int any_hash;                    // some solve asks for the visit hash
-    int use_geo;                     // FP32, every solve shares rq: geometry from the tables below
+    int use_geo;                     // every solve shares rq and every level is tabled: geometry from the tables below
     GeomLevel geo[RT_MAX_LEVELS + 1];
     int single;                      // the launch holds one solve, given in `one`
     BatchSolve one;
@@ -175,6 +175,25 @@ int launch_chem_update(const double* nh, const double* x0, double* xavg, double*
                         cudaStream_t s);
 int launch_sum_x(const double* x, int64_t ncell, DevStats* st, cudaStream_t s);
 int launch_mean_nh(const double* nh, int64_t ncell, double* out, cudaStream_t s);
+
+// Small device-to-host readbacks (statistics, counters), written by one kernel straight into mapped
+// pinned host memory: unlike copies they do not queue on the copy engines behind large transfers
+// that other streams have in flight. Up to four regions, each a whole number of 4-byte words; dst
+// holds device addresses of pinned host memory.
+struct ReadbackList {
+    const unsigned* src[4] = {};
+    unsigned* dst[4] = {};
+    int words[4] = {};
+    int n = 0;
+    void add(const void* from, void* to, size_t bytes)
+    {
+        src[n] = static_cast<const unsigned*>(from);
+        dst[n] = static_cast<unsigned*>(to);
+        words[n] = (int)(bytes / 4);
+        ++n;
+    }
+};
+int launch_readback(const ReadbackList& r, cudaStream_t s);
 
 // sources.cu
 struct SourceWork {

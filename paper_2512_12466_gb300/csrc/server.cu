@@ -318,7 +318,9 @@ void worker_main(rt_server* s)
         std::vector<rt_handle*> all;
         for (SrvReq* r : take) all.push_back(r->h);
         std::vector<int> rcs(all.size(), RT_OK);
-        prepare_sources_many(all.data(), (int)all.size(), rcs.data());
+        sources_enqueue_many(all.data(), (int)all.size(), rcs.data());
+        trace(s, "src_enqueued", -1, ms_since(tb));
+        sources_wait_many(all.data(), (int)all.size(), rcs.data());
         const double src_ms = ms_since(tb);
         trace(s, "src_done", -1, src_ms);
         std::vector<SrvReq*> run, bad;

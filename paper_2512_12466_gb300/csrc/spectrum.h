@@ -62,4 +62,23 @@ __host__ __device__ inline void spec_eval(const SpecTable<R>& T, R tau, R& phi, 
     psi = h00 * a[2] + h10 * h * a[3] + h01 * a[6] + h11 * h * a[7];
 }
 
+// Phi(tau) alone (the same operations as spec_eval's Phi): what a segment that absorbs
+// P (Phi(tau) - Phi(tau + dtau)) needs at its far end.
+template <class R>
+__host__ __device__ inline R spec_phi(const SpecTable<R>& T, R tau)
+{
+    if (tau < (R)kSpecTauLo) return (R)1 - tau * T.psi0;
+    const R inv_h = (R)(kSpecPerDecade / 2.302585092994046);
+    const R h = (R)(2.302585092994046 / kSpecPerDecade);
+    R u = (spec_log<R>(tau) - (R)(-18.420680743952367)) * inv_h;
+    int j = (int)u;
+    if (j >= kSpecPoints - 1) return T.v[4 * (kSpecPoints - 1)];
+    const R t = u - (R)j;
+    const R t2 = t * t, t3 = t2 * t;
+    const R h00 = (R)2 * t3 - (R)3 * t2 + (R)1, h10 = t3 - (R)2 * t2 + t;
+    const R h01 = (R)3 * t2 - (R)2 * t3, h11 = t3 - t2;
+    const R* a = T.v + 4 * j;
+    return h00 * a[0] + h10 * h * a[1] + h01 * a[4] + h11 * h * a[5];
+}
+
 }  // namespace nyx

@@ -185,15 +185,17 @@ def test_batch_rejects_mixed_precision_and_chemistry(nyx):
         s.close()
 
 
+@pytest.mark.parametrize("heavy_shift", [0, -1], ids=["default", "all-heavy"])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batch_periodic_matches_per_solve(nyx, precision):
-    """Periodic solves (Sec. 2.5.1) in one batch, FP32 with the geometry tables of
-    their shared grid size, against rt_step on each."""
+def test_batch_periodic_matches_per_solve(nyx, precision, heavy_shift):
+    """Periodic solves (Sec. 2.5.1) in one batch, with the geometry tables of their shared grid
+    size, against rt_step on each: in the persistent kernel and on the heavy path."""
     ws = [I.random_small(24, 5 + j, seed=700 + j, x_mode=["thin", "mixed", "patchy"][j % 3], box_cm=24 * 3e21)
           for j in range(4)]
     solvers = [make_solver(nyx, w, precision, periodic=1) for w in ws]
     ref = [plain(nyx, s, w.n) for s, w in zip(solvers, ws)]
     b = nyx.Batch(solvers)
+    b.set_params(heavy_shift=heavy_shift)
     gs, hs, stats = run_batch(nyx, b, ws)
     tol = 1e-12 if precision == 0 else 1e-10
     for (gr, hr, sr), g, st in zip(ref, gs, stats):
