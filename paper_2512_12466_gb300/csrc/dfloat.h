@@ -41,6 +41,20 @@ __device__ __forceinline__ dflt df_mul(const dflt a, const dflt b)
     return {p, e};
 }
 
+// a + b for any signs: heads by Knuth's two-sum, tails added to its error, renormalised
+__device__ __forceinline__ dflt df_add(const dflt a, const dflt b)
+{
+    const dflt s = df_two_sum(a.h, b.h);
+    return df_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+
+// a 2^n, exactly while both parts stay normal
+__device__ __forceinline__ dflt df_scale(const dflt a, const int n)
+{
+    const float m = __uint_as_float((unsigned)(127 + n) << 23);
+    return {__fmul_rn(a.h, m), __fmul_rn(a.l, m)};
+}
+
 // a - b for a >= b >= 0: heads by Knuth's two-sum, tails added to its error, renormalised
 __device__ __forceinline__ dflt df_sub(const dflt a, const dflt b)
 {

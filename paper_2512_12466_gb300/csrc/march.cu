@@ -240,15 +240,28 @@ struct PhiCache {
 // Eq. 1 for one segment of optical depth dtau = kap ds (kap = 0: the thin limit): the photons a it
 // absorbs per unit photon rate and its rate gseg. Gray: a = P (1 - e^{-dtau}). kFreq, integrated over
 // the blackbody spectrum (V.spec), the ray's budget P is its geometric share and the photons it still
-// carries are P Phi(tau): the segment absorbs P (Phi(tau) - Phi(tau + dtau)), or for a thin segment
-// the midpoint rate dtau Psi(tau + dtau/2) (error dtau^2 / 24 against the difference's cancellation,
-// equal near the switch), and deposits at the thin rate P Psi(tau) where kap = 0.
+// carries are P Phi(tau): the segment absorbs P (Phi(tau) - Phi(tau + dtau)) and deposits at the thin
+// rate P Psi(tau) where kap = 0. FP64 takes the difference from the cubic pieces in tau as a mean
+// slope (lin_absorb); FP32 from its logarithmic table, or for a thin segment as the midpoint rate
+// dtau Psi(tau + dtau/2) (error dtau^2 / 24 against the difference's cancellation, equal near the
+// switch).
 template <class R, bool kFreq>
 __device__ __forceinline__ void segment_eq1(const SolveView<R>& V, R P, R tau, R ctau, R G, R kap, R ds, R dtau, R& a,
                                             R& gseg, PhiCache<R>& pc)
 {
     using I = Ieee<R>;
-    if constexpr (kFreq) {
+    if constexpr (kFreq && sizeof(R) == 8) {
+        // FP64: the cubic pieces in tau, the absorbed fraction as a mean slope (no cancellation)
+        if (I::pos(kap)) {
+            double frac, per_kap;
+            lin_absorb(V.spec, tau, dtau, kap, ds, frac, per_kap);
+            a = P * frac;
+            gseg = (P * G) * per_kap;
+        } else {
+            a = (R)0;
+            gseg = ((P * lin_psi(V.spec, tau)) * G) * ds;
+        }
+    } else if constexpr (kFreq) {
         const R t0 = I::sub(tau, ctau);
         R phi0, psi0, phi1;
         if (I::pos(kap)) {
@@ -285,7 +298,9 @@ __device__ __forceinline__ void segment_eq1(const SolveView<R>& V, R P, R tau, R
 template <class R, bool kFreq>
 __device__ __forceinline__ double ray_remaining(const SolveView<R>& V, R P, R tau, R cP, R ctau, PhiCache<R>& pc)
 {
-    if constexpr (kFreq) {
+    if constexpr (kFreq && sizeof(R) == 8) {
+        return P * lin_phi(V.spec, tau);
+    } else if constexpr (kFreq) {
         if (!pc.ok) {
             pc.phi = spec_phi<R>(V.spec, Ieee<R>::sub(tau, ctau));
             pc.ok = true;
@@ -1249,8 +1264,93 @@ __device__ __forceinline__ double scale2(const double d, const int e)
     return b == 0 ? d : __longlong_as_double(b + (long long)e * (1LL << 52));
 }
 
-// march_ray_table for FP64 physics (gray), in double-float arithmetic as described above.
-template <bool kHash>
+// ---- the blackbody rate on the FP32 pipe (FP64 march): the cubic pieces of spectrum.h as
+// double-float pairs, evaluated by one code path for every segment between 2^-20 and 2^14.
+
+// Piece and exact position of tau in [2^-20, 2^14) as a double-float (the 47 or 45 fraction bits
+// split over head and tail), and the piece's width exponent.
+__device__ __forceinline__ int lin_locate_df(const double tau, dflt& t, int& wexp)
+{
+    const long long b = __double_as_longlong(tau);
+    const int e = (int)(b >> 52) - 1023;
+    const int hb = e < 0 ? 5 : 7;
+    const int fb = 52 - hb;
+    const unsigned long long m = (unsigned long long)b & ((1ULL << fb) - 1);
+    t.h = __fmul_rn(__uint2float_rn((unsigned)(m >> (fb - 24))), 5.9604644775390625e-08f);           // 2^-24
+    t.l = __fmul_rn(__uint2float_rn((unsigned)(m & ((1ULL << (fb - 24)) - 1))), __uint_as_float((unsigned)(127 - fb) << 23));
+    wexp = e - hb;
+    return e < 0 ? (e - kLinExpLo) * 32 + (int)((b >> 47) & 31) : kLinOmega + (e << 7) + (int)((b >> 45) & 127);
+}
+
+__device__ __forceinline__ dflt df_neg(const dflt a)
+{
+    return {-a.h, -a.l};
+}
+
+// (Phi(t0) - Phi(t0 + T)) / T on the piece {a, b}: -(c1 + c2 s1 + c3 s2), s1 = t0 + t1,
+// s2 = t0 s1 + t1^2 (the mean slope of the cubic, free of cancellation); t0 = 0 in lin_slope0_df.
+__device__ __forceinline__ dflt lin_slope_df(const float4 a, const float4 b, const dflt t0, const dflt T)
+{
+    const dflt t1 = df_add(t0, T);
+    const dflt s1 = df_add(t0, t1);
+    const dflt s2 = df_add(df_mul(t0, s1), df_mul(t1, t1));
+    const dflt D = df_add(dflt{a.z, a.w}, df_add(df_mul(dflt{b.x, b.y}, s1), df_mul(dflt{b.z, b.w}, s2)));
+    return df_neg(D);
+}
+
+__device__ __forceinline__ dflt lin_slope0_df(const float4 a, const float4 b, const dflt T)
+{
+    const dflt D = df_add(dflt{a.z, a.w}, df_mul(T, df_add(dflt{b.x, b.y}, df_mul(T, dflt{b.z, b.w}))));
+    return df_neg(D);
+}
+
+// Phi(tau0) - Phi(tau0 + dtau) for 2^-20 <= tau0 and tau1 = tau0 + dtau (rounded) < 2^14: the part in
+// tau0's piece, the whole pieces after it (node values: Omega below tau = 1, Phi above), and the part
+// in tau1's piece. When tau1 lies in the next piece, the depth past the node is dtau less the first
+// part, so a segment that just crosses a node keeps its precision; further on, tau1's own position.
+__device__ __forceinline__ dflt lin_frac_df(const float4* __restrict__ P, const double tau0, const double tau1,
+                                            const double dtau)
+{
+    dflt t0, t1;
+    int w0, w1;
+    const int k0 = lin_locate_df(tau0, t0, w0);
+    const int k1 = lin_locate_df(tau1, t1, w1);
+    const bool same = k1 == k0;
+    const dflt T = df_of(scale2(dtau, -w0));                   // dtau in units of piece k0's width
+    const dflt T0 = same ? T : df_add(dflt{1.f, 0.f}, df_neg(t0));
+    const dflt f0 = df_mul(T0, lin_slope_df(P[2 * k0], P[2 * k0 + 1], t0, T0));
+    const dflt R = df_add(df_of(dtau), df_neg(df_scale(T0, w0)));
+    const dflt T1 = same ? dflt{0.f, 0.f} : (k1 == k0 + 1 ? df_scale(R, -w1) : t1);
+    const dflt f1 = df_mul(T1, lin_slope0_df(P[2 * k1], P[2 * k1 + 1], T1));
+    // Phi_a - Phi_b over the whole pieces a = k0 + 1 .. b - 1, b = k1 (none unless k1 >= k0 + 2)
+    const int ka = min(k0 + 1, kLinIntervals - 1);
+    const float4 pa = P[2 * ka], pb = P[2 * k1];
+    const dflt va = {pa.x, pa.y}, vb = {pb.x, pb.y};
+    dflt mid;
+    if (k1 < kLinOmega) mid = df_add(vb, df_neg(va));                       // Omega_b - Omega_a
+    else if (ka >= kLinOmega) mid = df_add(va, df_neg(vb));                 // Phi_a - Phi_b
+    else mid = df_add(dflt{1.f, 0.f}, df_neg(df_add(va, vb)));             // 1 - Omega_a - Phi_b
+    if (k1 < k0 + 2) mid = dflt{0.f, 0.f};
+    return df_add(f0, df_add(mid, f1));
+}
+
+// Psi(tau) as a double-float (the optically thin rate), by Horner on tau's piece.
+__device__ __forceinline__ dflt lin_psi_df(const SpecTable<double>& S, const double tau)
+{
+    if (tau < kLinTauLo || tau >= kLinTauHi) return df_of(lin_psi(S, tau));
+    dflt t;
+    int w;
+    const int k = lin_locate_df(tau, t, w);
+    const float4 a = S.lin_bf[2 * k], b = S.lin_bf[2 * k + 1];
+    const dflt c = df_add(dflt{a.z, a.w}, df_mul(t, df_add(dflt{b.x, b.y}, df_mul(t, dflt{b.z, b.w}))));
+    return df_add(dflt{a.x, a.y}, df_mul(t, c));
+}
+
+// march_ray_table for FP64 physics, in double-float arithmetic as described above. kFreq: Eq. 1 over
+// the blackbody spectrum; Q = P m_G 2^64 then stays the ray's geometric share (its photons are
+// P Phi(tau)), and a segment deposits Q 2^64 r 2^(e_G - 128), r its rate per unit budget and G from
+// the FP64 pieces in tau (lin_absorb: Phi(tau) - Phi(tau + dtau) over kap; kap = 0: Psi(tau) ds).
+template <bool kHash, bool kFreq>
 __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, const float* __restrict__ rtab,
                                                    const GeomLevel& GL, unsigned* err, const int l,
                                                    const uint32_t si, const uint32_t pix, const double P0,
@@ -1285,20 +1385,24 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
     const bool corr = V.overlap_mode != RT_OVERLAP_NONE;
     const long long nn = (long long)n * n;
     ++T.rays;
+    const double B0 = kFreq ? P0 * lin_phi(V.spec, tau) : P0;   // the photons the ray starts with
     if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
         ++T.esc;
-        T.escph += ph * P0;
+        T.escph += ph * B0;
         return false;
     }
     // G = m_G 2^e_G; the budget Q = P m_G 2^64, and 1 / m_G to read P back
     int eG;
     const dflt mG = df_mant(se.gd, eG);
-    const int e_dep = eG - 64;
+    const int e_dep = kFreq ? eG - 128 : eG - 64;
     dflt Q = df_mul(df_of(scale2(P0, 64)), mG);
     dflt mGi;
     mGi.h = __frcp_rn(mG.h);
     mGi.l = __fmul_rn(__fmaf_rn(-mG.l, mGi.h, __fmaf_rn(-mG.h, mGi.h, 1.0f)), mGi.h);
-    auto remaining = [&]() -> double { return df_to_double(df_mul(Q, mGi), -64); };
+    auto remaining = [&]() -> double {
+        if constexpr (kFreq) return P0 * lin_phi(V.spec, tau);
+        else return df_to_double(df_mul(Q, mGi), -64);
+    };
 
     const E* col = TE::ent(GL) + GL.row0[pix >> 5] * 32 + (pix & 31);
     E e = col[0];
@@ -1346,8 +1450,32 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
         // or its FP64 value wd for an opaque segment
         dflt w = {0.f, 0.f};
         double wd = 0.0;
-        const bool opaque = I::pos(kap) && !I::lt(dtau, 2.0);
-        if (!opaque) {
+        const bool opaque = !kFreq && I::pos(kap) && !I::lt(dtau, 2.0);
+        const double tau1 = I::add(tau, dtau);
+        int e_seg = e_dep;
+        if constexpr (kFreq) {
+            // w = Q r with r the segment's rate per unit budget and G: (Phi(tau) - Phi(tau1)) / kap,
+            // its 2^-e_kap applied when rounding the deposit; Psi(tau) ds where kap = 0
+            if (I::pos(kap)) {
+                if (tau >= kLinTauLo && I::lt(tau1, kLinTauHi)) {
+                    const dflt frac = lin_frac_df(V.spec.lin_af, tau, tau1, dtau);
+                    int ek;
+                    const dflt mk = df_mant(kap, ek);
+                    dflt inv;
+                    inv.h = __frcp_rn(mk.h);
+                    inv.l = __fmul_rn(__fmaf_rn(-mk.l, inv.h, __fmaf_rn(-mk.h, inv.h, 1.0f)), inv.h);
+                    w = df_mul(Q, df_mul(frac, inv));
+                    e_seg = e_dep + 64 - ek;
+                } else {                                   // below 2^-20 or past 2^14: FP64
+                    double frac, r;
+                    lin_absorb(V.spec, tau, dtau, kap, ds, frac, r);
+                    w = df_mul(Q, df_of(scale2(r, 64)));
+                }
+            } else {
+                w = df_mul(Q, df_mul(lin_psi_df(V.spec, tau), df_of(ds)));   // optically thin limit
+                e_seg = e_dep + 64;
+            }
+        } else if (!opaque) {
             const dflt dsf = df_of(ds);
             if (I::pos(kap)) {
                 const dflt x = df_of(dtau);
@@ -1381,7 +1509,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
             }
         }
         if (keep_all) {
-            dep = opaque ? scale2(wd, e_dep) : df_to_double_pos(w, e_dep);
+            dep = opaque ? scale2(wd, e_dep) : df_to_double_pos(w, e_seg);
         } else {
             const double fd = TE::f(e);
             if (opaque) {
@@ -1390,7 +1518,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
             } else {
                 const dflt f = df_of(fd);
                 const dflt fw = df_mul(f, w);
-                dep = df_to_double_pos(squared ? df_mul(f, fw) : fw, e_dep);
+                dep = df_to_double_pos(squared ? df_mul(f, fw) : fw, e_seg);
                 if (second && I::pos(kap)) {       // kap = 0 (an ionized cell) sends 0 to c'
                     // Eq. 8: (1 - f) w kap / kap', the ratio of the mantissas by a float reciprocal
                     // and one correction, the exponents applied when rounding to double
@@ -1403,7 +1531,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
                     const float rho = __fmaf_rn(-q0, mn.l, __fadd_rn(__fsub_rn(__fsub_rn(mk.h, p), pe), mk.l));
                     const dflt ratio = {q0, __fmul_rn(rho, r0)};
                     const dflt om = {__fsub_rn(1.0f, f.h), -f.l};
-                    dep2 = df_to_double_pos(df_mul(df_mul(om, w), ratio), e_dep + ek - en);
+                    dep2 = df_to_double_pos(df_mul(df_mul(om, w), ratio), e_seg + ek - en);
                 }
             }
         }
@@ -1413,7 +1541,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
             atomicAdd(&V.gamma[nbcell], dep2);
             ++T.sec;
         }
-        tau = I::add(tau, dtau);
+        tau = tau1;
         if (kHash && V.hash) T.hash += mix64(rbase ^ ((unsigned long long)seq << 40) ^ (unsigned long long)cell);
         ++seq;
         if (!I::lt(tau, taumax)) {             // photons spent
@@ -1431,7 +1559,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
             } else {
                 ++T.split;
                 split = true;
-                oP = remaining();
+                oP = kFreq ? P0 : remaining();
                 otau = tau;
             }
             break;
@@ -1453,7 +1581,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
         e = en;
     }
     T.seg += seq;
-    T.abs += ph * (P0 - remaining());
+    T.abs += ph * (B0 - remaining());
     return split;
 }
 
@@ -1613,10 +1741,11 @@ __global__ void __launch_bounds__(256, TableOccupancy<R>::blocks) march_table_ke
     const long long c1 = A.in_count ? min((long long)A.c1, (long long)A.c0 + 4LL * (long long)*A.in_count) : (long long)A.c1;
     Tally T;
     T.clear();
-    // FP64 gray march: the Eq. 1 rate table in shared memory (two float4 arrays, see rate_factor)
-    constexpr bool kDf = sizeof(R) == 8 && !kFreq;
-    __shared__ __align__(16) float rtab[kDf ? kRateSmem : 4];
-    if constexpr (kDf) {
+    // FP64 march in double-float arithmetic; gray: the Eq. 1 rate table in shared memory (two float4
+    // arrays, see rate_factor)
+    constexpr bool kDf = sizeof(R) == 8;
+    __shared__ __align__(16) float rtab[(kDf && !kFreq) ? kRateSmem : 4];
+    if constexpr (kDf && !kFreq) {
         for (int i = threadIdx.x; i < kRateSmem; i += blockDim.x) {
             const int row = (i >> 2) % kRateIntervals, half = (i >> 2) / kRateIntervals;
             rtab[i] = kRateTable[row * kRateCoefs + 4 * half + (i & 3)];
@@ -1633,8 +1762,8 @@ __global__ void __launch_bounds__(256, TableOccupancy<R>::blocks) march_table_ke
             R P, tau, cP, ctau;
             load_ray<R>(l, j, A.in, si, pix, P, tau, cP, ctau);
             if constexpr (kDf) {
-                split = march_ray_table_df<kHash>(V, rtab, GL, &A.st->err, l, si, pix, P, tau, A.src[si], A.dirs[pix],
-                                                  T, oP, otau);
+                split = march_ray_table_df<kHash, kFreq>(V, rtab, GL, &A.st->err, l, si, pix, P, tau, A.src[si],
+                                                         A.dirs[pix], T, oP, otau);
             } else {
                 split = march_ray_table<R, kHash, kFreq>(V, GL, &A.st->err, l, si, pix, P, tau, cP, ctau, A.src[si],
                                                          A.dirs[pix], T, oP, otau, ocP, octau);
@@ -1737,7 +1866,7 @@ __global__ void __launch_bounds__(256, (kTable && kSingle) ? TableOccupancy<R>::
                     V.tau_max = (R)bs.tau_max;
                     V.src_off = bs.src_off - A.src_base;
                     if constexpr (kDf) {
-                        split = march_ray_table_df<kHash>(V, rtab, A.geo[l], A.err, l, si, pix, P, tau, se, dirs[pix], T, oP,
+                        split = march_ray_table_df<kHash, false>(V, rtab, A.geo[l], A.err, l, si, pix, P, tau, se, dirs[pix], T, oP,
                                                           otau);
                     } else if constexpr (kTable) {
                         split = march_ray_table<float, kHash, false>(V, A.geo[l], A.err, l, si, pix, P, tau, cP, ctau, se, dirs[pix],

@@ -21,6 +21,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "rt_handle.h"
@@ -225,6 +226,10 @@ struct SpecEntry {
     double psi0, xi0;
     const double* dev_d;
     const float* dev_f;
+    std::vector<LinPiece> lin_a, lin_b;   // the FP64 march's cubic pieces in tau
+    double zeta0, phi_end, psi_end;
+    const LinPiece* dev_lin;              // lin_a then lin_b
+    const float4* dev_linf;               // the same as double-float pairs, two float4 per piece
 };
 std::mutex g_spec_mu;
 std::map<int, std::deque<SpecEntry>> g_spec;   // a deque: entries never move once added
@@ -271,30 +276,137 @@ void spectrum_build(double t_bb, std::vector<double>& v, double& psi0, double& x
     }
 }
 
+// The FP64 march's pieces (kLinIntervals cubics in tau, laid out as spectrum.h describes), from the same Simpson rule
+// over u as spectrum_moments. At node tau_j (and width w_j = tau_{j+1} - tau_j) it integrates Phi,
+// Psi = <s e^{-tau s}>, Xi = <s^2 e^{-tau s}>, Omega = <1 - e^{-tau s}> and the increments
+// dPhi_j = Phi_j - Phi_{j+1} = <e^{-tau_j s} (1 - e^{-w_j s})> and dPsi_j likewise, each written with
+// expm1 so that no difference of nearly equal values is taken. The cubic of piece j is the Hermite
+// interpolant of the node values and of their tau-derivatives (-Psi for Phi, -Xi for Psi), in
+// t = (tau - tau_j) / w_j; its coefficients follow from the two values and two slopes.
+void spectrum_lin_build(double theta, SpecEntry& e)
+{
+    const int N = 4096;
+    const double du = 1.0 / N;
+    std::vector<double> W(N + 1), sv(N + 1);
+    double M0 = 0.0, M3 = 0.0;
+    for (int i = 1; i <= N; ++i) {
+        const double u = i * du;
+        const double base = std::exp(-theta / u) / (-std::expm1(-theta / u)) / (u * u * u * u);
+        const double wgt = (i == N) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        W[i] = wgt * base * du / 3.0;
+        sv[i] = u * u * u;
+        M0 += W[i];
+        M3 += W[i] * sv[i] * sv[i] * sv[i];
+    }
+    const int J = kLinIntervals;
+    std::vector<double> phi(J + 1), psi(J + 1), xi(J + 1), om(J + 1), dphi(J), dpsi(J), wid(J);
+    auto node = [&](int j) {
+        double tau, w;                                        // node tau_j and piece width
+        if (j < kLinOmega) {
+            tau = std::ldexp(1.0 + (double)(j % 32) / 32.0, kLinExpLo + j / 32);
+            w = std::ldexp(1.0, kLinExpLo + j / 32 - 5);
+        } else {
+            const int q = j - kLinOmega;
+            tau = std::ldexp(1.0 + (double)(q % 128) / 128.0, q / 128);
+            w = std::ldexp(1.0, q / 128 - 7);
+        }
+        double a[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = 1; i <= N; ++i) {
+            const double sx = sv[i];
+            const double E = W[i] * std::exp(-tau * sx);
+            a[0] += E;
+            a[1] += E * sx;
+            a[2] += E * sx * sx;
+            a[3] += W[i] * -std::expm1(-tau * sx);
+            if (j < J) {
+                const double X = E * -std::expm1(-w * sx);
+                a[4] += X;
+                a[5] += X * sx;
+            }
+        }
+        phi[j] = a[0] / M0;
+        psi[j] = a[1] / M0;
+        xi[j] = a[2] / M0;
+        om[j] = a[3] / M0;
+        if (j < J) {
+            dphi[j] = a[4] / M0;
+            dpsi[j] = a[5] / M0;
+            wid[j] = w;
+        }
+    };
+    const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int q = 0; q < nth; ++q)
+        pool.emplace_back([&, q] {
+            for (int j = q; j <= J; j += nth) node(j);
+        });
+    for (auto& t : pool) t.join();
+    e.lin_a.resize(J);
+    e.lin_b.resize(J);
+    for (int j = 0; j < J; ++j) {
+        const double w = wid[j];
+        const double m0 = -w * psi[j], m1 = -w * psi[j + 1];          // t-slopes of Phi at the ends
+        e.lin_a[j] = {j < kLinOmega ? om[j] : phi[j], m0, -3.0 * dphi[j] - 2.0 * m0 - m1, 2.0 * dphi[j] + m0 + m1};
+        const double n0 = -w * xi[j], n1 = -w * xi[j + 1];            // t-slopes of Psi
+        e.lin_b[j] = {psi[j], n0, -3.0 * dpsi[j] - 2.0 * n0 - n1, 2.0 * dpsi[j] + n0 + n1};
+    }
+    e.zeta0 = M3 / M0;
+    e.phi_end = phi[J];
+    e.psi_end = psi[J];
+}
+
 const SpecEntry* spectrum_entry(int device, double t_bb, std::string& why)
 {
     std::lock_guard<std::mutex> lk(g_spec_mu);
     std::deque<SpecEntry>& list = g_spec[device];
     for (const SpecEntry& e : list)
         if (e.t_bb == t_bb) return &e;
-    SpecEntry e{t_bb, {}, 0.0, 0.0, nullptr, nullptr};
+    SpecEntry e{t_bb, {}, 0.0, 0.0, nullptr, nullptr, {}, {}, 0.0, 0.0, 0.0, nullptr, nullptr};
     spectrum_build(t_bb, e.host, e.psi0, e.xi0);
     if (device >= 0) {
+        spectrum_lin_build(kHNu0Erg / (kKbErgK * t_bb), e);
         std::vector<float> f(e.host.begin(), e.host.end());
         double* dd = nullptr;
         float* df = nullptr;
+        LinPiece* dl = nullptr;
+        float4* dlf = nullptr;
+        const size_t nl = e.lin_a.size();
+        // head = the value rounded to float, tail = the rest rounded to float
+        std::vector<float4> lf(4 * nl);
+        auto pair = [](double x, float& h, float& l) {
+            h = (float)x;
+            l = (float)(x - (double)h);
+        };
+        for (size_t q = 0; q < 2 * nl; ++q) {
+            const LinPiece& p = q < nl ? e.lin_a[q] : e.lin_b[q - nl];
+            float4& u = lf[2 * q];
+            float4& v = lf[2 * q + 1];
+            pair(p.v, u.x, u.y);
+            pair(p.c1, u.z, u.w);
+            pair(p.c2, v.x, v.y);
+            pair(p.c3, v.z, v.w);
+        }
         if (cudaMalloc(&dd, sizeof(double) * e.host.size()) != cudaSuccess ||
             cudaMalloc(&df, sizeof(float) * f.size()) != cudaSuccess ||
+            cudaMalloc(&dl, sizeof(LinPiece) * 2 * nl) != cudaSuccess ||
+            cudaMalloc(&dlf, sizeof(float4) * lf.size()) != cudaSuccess ||
+            cudaMemcpy(dlf, lf.data(), sizeof(float4) * lf.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(dd, e.host.data(), sizeof(double) * e.host.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(df, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaMemcpy(df, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(dl, e.lin_a.data(), sizeof(LinPiece) * nl, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(dl + nl, e.lin_b.data(), sizeof(LinPiece) * nl, cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(dd);
             cudaFree(df);
+            cudaFree(dl);
+            cudaFree(dlf);
             why = "device allocation of the spectrum table failed";
             return nullptr;
         }
         e.dev_d = dd;
         e.dev_f = df;
+        e.dev_lin = dl;
+        e.dev_linf = dlf;
     }
     list.push_back(std::move(e));
     return &list.back();
@@ -321,6 +433,13 @@ int nyx::spectrum_table(int device, double t_bb, SpecTable<double>* d, SpecTable
     d->v = e->dev_d;
     d->psi0 = e->psi0;
     d->xi0 = e->xi0;
+    d->lin_a = e->dev_lin;
+    d->lin_b = e->dev_lin ? e->dev_lin + e->lin_a.size() : nullptr;
+    d->zeta0 = e->zeta0;
+    d->phi_end = e->phi_end;
+    d->psi_end = e->psi_end;
+    d->lin_af = e->dev_linf;
+    d->lin_bf = e->dev_linf ? e->dev_linf + 2 * e->lin_a.size() : nullptr;
     f->v = e->dev_f;
     f->psi0 = (float)e->psi0;
     f->xi0 = (float)e->xi0;
