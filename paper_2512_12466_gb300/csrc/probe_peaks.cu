@@ -64,16 +64,19 @@ int run(const int64_t iters, double* tflops, double* ms_out)
 
 // FP64 atomic adds whose result is unused (reductions performed in L2), as the march's deposits
 // are: each thread adds `iters` times into an array of n doubles, at addresses spread by a hash
-// (pattern 0: every lane of a warp a different, random cell) or consecutive within a warp (pattern
-// 1: the lanes of a warp cover 32 neighbouring cells).
+// (pattern 0: every lane of a warp a different, random cell), consecutive within a warp (pattern
+// 1: the lanes of a warp cover 32 neighbouring cells), or shared by groups of lanes (pattern 2:
+// groups of 4 lanes add to one random cell; pattern 3: groups of 16), as rays of one source that
+// cross the same cell in the same step do.
 __global__ void __launch_bounds__(256) red_f64(double* __restrict__ a, const int64_t n, const int64_t iters,
                                                 const int pattern)
 {
     const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     for (int64_t i = 0; i < iters; ++i) {
         uint64_t k;
-        if (pattern == 0) {
-            uint64_t z = gid * 0x9e3779b97f4a7c15ULL + (uint64_t)i * 0xbf58476d1ce4e5b9ULL;
+        if (pattern == 0 || pattern >= 2) {
+            const uint64_t g = pattern == 2 ? gid >> 2 : (pattern == 3 ? gid >> 4 : gid);
+            uint64_t z = g * 0x9e3779b97f4a7c15ULL + (uint64_t)i * 0xbf58476d1ce4e5b9ULL;
             z ^= z >> 31;
             z *= 0x94d049bb133111ebULL;
             z ^= z >> 29;
@@ -118,10 +121,11 @@ int run_red(const int64_t n, const int64_t iters, const int pattern, double* per
 extern "C" {
 
 // FP64 atomic adds per second into an array of n doubles (n >= 32, a multiple of 32), pattern 0
-// random cells, 1 neighbouring cells per warp; `iters` adds per thread. 0 on success.
+// random cells, 1 neighbouring cells per warp, 2 and 3 one random cell per group of 4 and 16 lanes;
+// `iters` adds per thread. 0 on success.
 int nyxrt_probe_red_f64(int64_t n, int64_t iters, int pattern, double* per_s, double* ms)
 {
-    if (!per_s || !ms || iters < 1 || n < 32 || n % 32 || (pattern != 0 && pattern != 1)) return -1;
+    if (!per_s || !ms || iters < 1 || n < 32 || n % 32 || pattern < 0 || pattern > 3) return -1;
     return run_red(n, iters, pattern, per_s, ms);
 }
 

@@ -35,12 +35,13 @@ def main() -> int:
         out[f"fp{bits}"] = {"tflops": best, "fma_per_s": best * 1e12 / 2, "kernel_ms": ms_best, "iters": iters}
     out["fp32_over_fp64"] = out["fp32"]["tflops"] / out["fp64"]["tflops"]
     # FP64 atomic adds (the march's deposits): an L2-resident array the size of a 128^3 Gamma grid
-    # and one of 2 GB (beyond L2), random cells and neighbouring cells per warp
+    # and one of 2 GB (beyond L2), random cells, neighbouring cells per warp, and one random cell per
+    # group of 4 or 16 lanes
     lib.nyxrt_probe_red_f64.argtypes = [C.c_int64, C.c_int64, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.nyxrt_probe_red_f64.restype = C.c_int
     red = {}
     for label, n in (("l2_128cubed", 128 ** 3), ("dram_2GB", 1 << 28)):
-        for pname, pat in (("random", 0), ("neighbours", 1)):
+        for pname, pat in (("random", 0), ("neighbours", 1), ("shared4", 2), ("shared16", 3)):
             best = 0.0
             for _ in range(3):
                 ps, ms = C.c_double(), C.c_double()
