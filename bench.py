@@ -772,9 +772,10 @@ def run_nyx(args, world, rank, local):
                      "kernel": "march_table_kernel (FP32, geometry tables)", "peak_kind": peak_kind,
                      "march_ms_per_step": f32["march_ms_per_step"],
                      "march_launches_per_step": f32["march_launches_per_step"],
-                     # what binds the march on this machine: its FP64 deposits (one per primary segment and
-                     # per secondary deposit) against FP64 atomic adds into an L2-resident array of the
-                     # same size, measured in this run
+                     # the march's FP64 deposits (one per primary segment and per secondary deposit)
+                     # against FP64 atomic adds into an L2-resident array of the same size, measured in
+                     # this run: the rates match, but removing the primary deposits (a timing-only
+                     # variant) leaves the march time unchanged, so they are not what binds it
                      "l2_atomics": {"achieved": (f32["segments_per_step"] + f32["secondary_per_step"])
                                     / (f32["march_ms_per_step"] / 1e3),
                                     "peak": red["random"], "peak_neighbouring_cells": red["neighbours"],
@@ -785,7 +786,7 @@ def run_nyx(args, world, rank, local):
                  "roofline": {"achieved": f64["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                               "frac": f64["achieved_gbs"] / hbm, "frac_nominal": f64["achieved_gbs"] / NOMINAL_HBM,
                               "kernel": "march_table_kernel<double> (FP64, geometry tables, double-float)",
-                              "bound": "latency of the double-float arithmetic (issue 58%, FP64 pipe 51% in ncu)"}},
+                              "bound": "instruction issue of the double-float arithmetic (issue 70% active, 319 thread instructions per segment, FP64 pipe 30% in ncu)"}},
         "e2e": {"value": e2e_val, "unit": "segments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "clocks": f32["clocks"],
