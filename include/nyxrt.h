@@ -106,8 +106,9 @@ enum {
                                   sigma_nu = sigma_cm2 (nu_0 / nu)^3. A ray keeps its geometric
                                   budget and carries threshold optical depth tau; it absorbs
                                   Phi(tau) - Phi(tau + dtau) of it per segment, Phi(tau) being the
-                                  fraction of its photons that survive tau (tabulated per
-                                  temperature, cubic interpolation in ln tau). tau_max <= 1e4.
+                                  fraction of its photons that survive tau (cubic pieces in tau
+                                  per temperature, 32 per octave below tau = 1 and 128 above, indexed
+                                  by the bits of tau). tau_max <= 1e4.
                                   rt_step, the batched form (its heavy path) and the server; not
                                   the allocation-free form. */
 };
@@ -251,9 +252,9 @@ int rt_destroy(rt_handle* h);
 int64_t rt_geometry_table_bytes(int32_t device);
 
 /* Phi(tau) and the thin rate Psi(tau) = -dPhi/dtau of RT_SPECTRUM_BLACKBODY at
- * t_bb_K, from the library's own table and interpolation (what the march uses,
- * evaluated on the host; for checking). Returns RT_EINVAL for tau outside
- * [0, 1e4] or t_bb_K <= 0. */
+ * t_bb_K, from the library's own cubic pieces (the functions the FP64 march runs,
+ * evaluated on the host; the FP32 march reads the same pieces rounded to float; for
+ * checking). Returns RT_EINVAL for tau outside [0, 1e4] or t_bb_K <= 0. */
 int rt_spectrum_eval(double t_bb_K, double tau, double* phi, double* psi);
 
 /* Text of the handle's last error ("" if none); for h == NULL, the last

@@ -228,30 +228,18 @@ __device__ __forceinline__ int wrapn(const int v, const int n)
     return r < 0 ? r + n : r;
 }
 
-// Phi at the ray's current optical depth, kept from the segment that last evaluated it (Eq. 1 over
-// the blackbody spectrum): a segment's Phi(tau + dtau) is the next segment's Phi(tau), so each
-// difference segment evaluates the table once, and the absorbed photons telescope along the ray.
-template <class R>
-struct PhiCache {
-    R phi;
-    bool ok;
-};
-
 // Eq. 1 for one segment of optical depth dtau = kap ds (kap = 0: the thin limit): the photons a it
 // absorbs per unit photon rate and its rate gseg. Gray: a = P (1 - e^{-dtau}). kFreq, integrated over
 // the blackbody spectrum (V.spec), the ray's budget P is its geometric share and the photons it still
-// carries are P Phi(tau): the segment absorbs P (Phi(tau) - Phi(tau + dtau)) and deposits at the thin
-// rate P Psi(tau) where kap = 0. FP64 takes the difference from the cubic pieces in tau as a mean
-// slope (lin_absorb); FP32 from its logarithmic table, or for a thin segment as the midpoint rate
-// dtau Psi(tau + dtau/2) (error dtau^2 / 24 against the difference's cancellation, equal near the
-// switch).
+// carries are P Phi(tau): the segment absorbs P (Phi(tau) - Phi(tau + dtau)), taken from the cubic
+// pieces in tau as a mean slope (no cancellation), and deposits at the thin rate P Psi(tau) where
+// kap = 0.
 template <class R, bool kFreq>
 __device__ __forceinline__ void segment_eq1(const SolveView<R>& V, R P, R tau, R ctau, R G, R kap, R ds, R dtau, R& a,
-                                            R& gseg, PhiCache<R>& pc)
+                                            R& gseg)
 {
     using I = Ieee<R>;
     if constexpr (kFreq && sizeof(R) == 8) {
-        // FP64: the cubic pieces in tau, the absorbed fraction as a mean slope (no cancellation)
         if (I::pos(kap)) {
             double frac, per_kap;
             lin_absorb(V.spec, tau, dtau, kap, ds, frac, per_kap);
@@ -263,27 +251,12 @@ __device__ __forceinline__ void segment_eq1(const SolveView<R>& V, R P, R tau, R
         }
     } else if constexpr (kFreq) {
         const R t0 = I::sub(tau, ctau);
-        R phi0, psi0, phi1;
         if (I::pos(kap)) {
-            if (dtau >= (sizeof(R) == 4 ? (R)1e-2 : (R)1e-6)) {
-                if (pc.ok) phi0 = pc.phi;
-                else phi0 = spec_phi<R>(V.spec, t0);
-                phi1 = spec_phi<R>(V.spec, t0 + dtau);
-                a = P * (phi0 - phi1);
-                pc.phi = phi1;
-                pc.ok = true;
-            } else {
-                spec_eval<R>(V.spec, t0 + (R)0.5 * dtau, phi0, psi0);
-                a = P * (dtau * psi0);
-                pc.ok = false;
-            }
+            a = P * lin_absorb_f(V.spec, t0, dtau);
             gseg = I::qdiv(a * G, kap);
         } else {
-            spec_eval<R>(V.spec, t0, phi0, psi0);
             a = (R)0;
-            gseg = ((P * psi0) * G) * ds;
-            pc.phi = phi0;                  // tau does not move in an ionized cell
-            pc.ok = true;
+            gseg = ((P * lin_psi_f(V.spec, t0)) * G) * ds;
         }
     } else if (I::pos(kap)) {
         I::rate(P, G, kap, ds, dtau, a, gseg);
@@ -294,18 +267,14 @@ __device__ __forceinline__ void segment_eq1(const SolveView<R>& V, R P, R tau, R
 }
 
 // The photons a ray still carries, in units of its source's photon rate per ray: its compensated
-// budget P - cP (gray), or P Phi(tau - ctau) (kFreq; Phi from the cache when the last segment left it).
+// budget P - cP (gray), or P Phi(tau - ctau) (kFreq).
 template <class R, bool kFreq>
-__device__ __forceinline__ double ray_remaining(const SolveView<R>& V, R P, R tau, R cP, R ctau, PhiCache<R>& pc)
+__device__ __forceinline__ double ray_remaining(const SolveView<R>& V, R P, R tau, R cP, R ctau)
 {
     if constexpr (kFreq && sizeof(R) == 8) {
         return P * lin_phi(V.spec, tau);
     } else if constexpr (kFreq) {
-        if (!pc.ok) {
-            pc.phi = spec_phi<R>(V.spec, Ieee<R>::sub(tau, ctau));
-            pc.ok = true;
-        }
-        return widen(P) * widen(pc.phi);
+        return widen(P) * widen(lin_phi_f(V.spec, Ieee<R>::sub(tau, ctau)));
     } else {
         return widen(P) - widen(cP);
     }
@@ -326,8 +295,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
 {
     using I = Ieee<R>;
     // photons the ray still carries, in units of ph
-    PhiCache<R> pc{(R)0, false};
-    auto remaining = [&]() -> double { return ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc); };
+    auto remaining = [&]() -> double { return ray_remaining<R, kFreq>(V, P, tau, cP, ctau); };
     const int n = V.n;
     // the ray ends on its split sphere R_l or, with periodic boundaries, at the travel distance
     // sqrt(3) L_box if that comes first or at the same point, where it stops without splitting
@@ -446,7 +414,7 @@ __device__ __forceinline__ bool march_ray(const SolveView<R>& V, const int l, co
         const R kap = I::mag(kraw);
         const R dtau = I::mul(kap, ds);
         R a, gseg;
-        segment_eq1<R, kFreq>(V, P, tau, ctau, G, kap, ds, dtau, a, gseg, pc);
+        segment_eq1<R, kFreq>(V, P, tau, ctau, G, kap, ds, dtau, a, gseg);
         // ---- Eqs. 5-8: the share f kept in this cell and the neighbour's deposit
         R f = (R)1, g2 = (R)0;
         int nbcell = -1;
@@ -1076,12 +1044,11 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
                       V.overlap_mode == RT_OVERLAP_NAIVE;
     const bool corr = V.overlap_mode != RT_OVERLAP_NONE;
     const long long nn = (long long)n * n;
-    PhiCache<R> pc{(R)0, false};
-    const double B0 = ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
+    const double B0 = ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
     ++T.rays;
     if (!((unsigned)i0 < (unsigned)n && (unsigned)i1 < (unsigned)n && (unsigned)i2 < (unsigned)n)) {
         ++T.esc;
-        T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
+        T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
         return false;
     }
     const E* col = TE::ent(GL) + GL.row0[pix >> 5] * 32 + (pix & 31);
@@ -1127,7 +1094,7 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         const R kap = I::mag(kcur);
         const R dtau = I::mul(kap, ds);
         R a, gseg;
-        segment_eq1<R, kFreq>(V, P, tau, ctau, G, kap, ds, dtau, a, gseg, pc);
+        segment_eq1<R, kFreq>(V, P, tau, ctau, G, kap, ds, dtau, a, gseg);
         // ---- Eqs. 5-8
         R f = (R)1, g2 = (R)0;
         int nbcell = -1;
@@ -1160,16 +1127,16 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         ++seq;
         if (!I::lt(tau, taumax)) {             // photons spent
             ++T.dtau;
-            T.dropph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
+            T.dropph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
             break;
         }
         if (!steps) {                    // the segment ended on the end sphere
             if (!split_end) {            // travelled sqrt(3) L_box (Sec. 2.5.1)
                 ++T.esc;
-                T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
+                T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
             } else if (l + 1 > V.level_max) {
                 ++T.dlev;
-                T.dropph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
+                T.dropph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
             } else {
                 ++T.split;
                 split = true;
@@ -1182,7 +1149,7 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         }
         if (!next_in) {
             ++T.esc;
-            T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc);
+            T.escph += ph * ray_remaining<R, kFreq>(V, P, tau, cP, ctau);
             break;
         }
         if (last) {                      // cannot happen: a table ends where every grid is left
@@ -1197,7 +1164,7 @@ __device__ __forceinline__ bool march_ray_table(const SolveView<R>& V, const Geo
         e = en;
     }
     T.seg += seq;
-    T.abs += ph * (B0 - ray_remaining<R, kFreq>(V, P, tau, cP, ctau, pc));
+    T.abs += ph * (B0 - ray_remaining<R, kFreq>(V, P, tau, cP, ctau));
     return split;
 }
 
@@ -1898,7 +1865,7 @@ __global__ void __launch_bounds__(256, (kTable && kSingle) ? TableOccupancy<R>::
 template <class R>
 static int launch_march_impl(const MarchArgs<R>& a, int grid, int block, cudaStream_t s)
 {
-    const bool freq = a.spec.v != nullptr;
+    const bool freq = a.spec.lin_a != nullptr;
     if (a.hash) {
         if (freq) march_kernel<R, true, true><<<grid, block, 0, s>>>(a);
         else march_kernel<R, true, false><<<grid, block, 0, s>>>(a);
@@ -1921,7 +1888,7 @@ int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_
 
 int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int grid, int block, cudaStream_t s)
 {
-    if (a.spec.v) {
+    if (a.spec.lin_a) {
         if (a.hash) march_table_kernel<float, true, true><<<grid, block, 0, s>>>(a, g);
         else march_table_kernel<float, false, true><<<grid, block, 0, s>>>(a, g);
     } else {
@@ -1933,7 +1900,7 @@ int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int gr
 
 int launch_march_table_f64(const MarchArgs<double>& a, const GeomLevel& g, int grid, int block, cudaStream_t s)
 {
-    if (a.spec.v) {
+    if (a.spec.lin_a) {
         if (a.hash) march_table_kernel<double, true, true><<<grid, block, 0, s>>>(a, g);
         else march_table_kernel<double, false, true><<<grid, block, 0, s>>>(a, g);
     } else {

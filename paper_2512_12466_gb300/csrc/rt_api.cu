@@ -222,14 +222,11 @@ namespace {
 // rule over u (the integrand and its derivatives vanish at u = 0).
 struct SpecEntry {
     double t_bb;
-    std::vector<double> host;     // the double table (host copy, for rt_spectrum_eval)
-    double psi0, xi0;
-    const double* dev_d;
-    const float* dev_f;
-    std::vector<LinPiece> lin_a, lin_b;   // the FP64 march's cubic pieces in tau
-    double zeta0, phi_end, psi_end;
+    std::vector<LinPiece> lin_a, lin_b;   // the cubic pieces in tau (host copy, for rt_spectrum_eval)
+    double psi0, xi0, zeta0, phi_end, psi_end;
     const LinPiece* dev_lin;              // lin_a then lin_b
     const float4* dev_linf;               // the same as double-float pairs, two float4 per piece
+    const float4* dev_linF;               // rounded to float, one float4 per piece
 };
 std::mutex g_spec_mu;
 std::map<int, std::deque<SpecEntry>> g_spec;   // a deque: entries never move once added
@@ -237,47 +234,9 @@ std::map<int, std::deque<SpecEntry>> g_spec;   // a deque: entries never move on
 constexpr double kHNu0Erg = 13.598 * 1.602176634e-12;   // hydrogen ionization threshold, erg
 constexpr double kKbErgK = 1.380649e-16;
 
-void spectrum_moments(double theta, double tau, double out[3])
-{
-    const int N = 4096;                       // Simpson intervals over u in (0, 1]
-    const double du = 1.0 / N;
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int i = 1; i <= N; ++i) {            // the u = 0 end contributes 0
-        const double u = i * du;
-        const double e = std::exp(-theta / u);
-        const double base = e / (-std::expm1(-theta / u)) / (u * u * u * u);
-        const double s = u * u * u;
-        const double wgt = (i == N) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
-        const double f0 = base * std::exp(-tau * s);
-        acc[0] += wgt * f0;
-        acc[1] += wgt * f0 * s;
-        acc[2] += wgt * f0 * s * s;
-    }
-    for (int p = 0; p < 3; ++p) out[p] = acc[p] * du / 3.0;
-}
-
-void spectrum_build(double t_bb, std::vector<double>& v, double& psi0, double& xi0)
-{
-    const double theta = kHNu0Erg / (kKbErgK * t_bb);
-    double m0[3];
-    spectrum_moments(theta, 0.0, m0);
-    psi0 = m0[1] / m0[0];
-    xi0 = m0[2] / m0[0];
-    v.assign(4 * (size_t)kSpecPoints, 0.0);
-    for (int j = 0; j < kSpecPoints; ++j) {
-        const double tau = kSpecTauLo * std::pow(10.0, (double)j / kSpecPerDecade);
-        double m[3];
-        spectrum_moments(theta, tau, m);
-        const double phi = m[0] / m0[0], psi = m[1] / m0[0], xi = m[2] / m0[0];
-        v[4 * j] = phi;
-        v[4 * j + 1] = -tau * psi;            // dPhi / dln tau
-        v[4 * j + 2] = psi;
-        v[4 * j + 3] = -tau * xi;             // dPsi / dln tau
-    }
-}
-
-// The FP64 march's pieces (kLinIntervals cubics in tau, laid out as spectrum.h describes), from the same Simpson rule
-// over u as spectrum_moments. At node tau_j (and width w_j = tau_{j+1} - tau_j) it integrates Phi,
+// The cubic pieces in tau (kLinIntervals of them, laid out as spectrum.h describes), by composite
+// Simpson's rule over u with 4096 intervals. At node tau_j (and width w_j = tau_{j+1} - tau_j) it
+// integrates Phi,
 // Psi = <s e^{-tau s}>, Xi = <s^2 e^{-tau s}>, Omega = <1 - e^{-tau s}> and the increments
 // dPhi_j = Phi_j - Phi_{j+1} = <e^{-tau_j s} (1 - e^{-w_j s})> and dPsi_j likewise, each written with
 // expm1 so that no difference of nearly equal values is taken. The cubic of piece j is the Hermite
@@ -288,7 +247,7 @@ void spectrum_lin_build(double theta, SpecEntry& e)
     const int N = 4096;
     const double du = 1.0 / N;
     std::vector<double> W(N + 1), sv(N + 1);
-    double M0 = 0.0, M3 = 0.0;
+    double M0 = 0.0, M1 = 0.0, M2 = 0.0, M3 = 0.0;
     for (int i = 1; i <= N; ++i) {
         const double u = i * du;
         const double base = std::exp(-theta / u) / (-std::expm1(-theta / u)) / (u * u * u * u);
@@ -296,6 +255,8 @@ void spectrum_lin_build(double theta, SpecEntry& e)
         W[i] = wgt * base * du / 3.0;
         sv[i] = u * u * u;
         M0 += W[i];
+        M1 += W[i] * sv[i];
+        M2 += W[i] * sv[i] * sv[i];
         M3 += W[i] * sv[i] * sv[i] * sv[i];
     }
     const int J = kLinIntervals;
@@ -350,6 +311,8 @@ void spectrum_lin_build(double theta, SpecEntry& e)
         const double n0 = -w * xi[j], n1 = -w * xi[j + 1];            // t-slopes of Psi
         e.lin_b[j] = {psi[j], n0, -3.0 * dpsi[j] - 2.0 * n0 - n1, 2.0 * dpsi[j] + n0 + n1};
     }
+    e.psi0 = M1 / M0;
+    e.xi0 = M2 / M0;
     e.zeta0 = M3 / M0;
     e.phi_end = phi[J];
     e.psi_end = psi[J];
@@ -361,18 +324,15 @@ const SpecEntry* spectrum_entry(int device, double t_bb, std::string& why)
     std::deque<SpecEntry>& list = g_spec[device];
     for (const SpecEntry& e : list)
         if (e.t_bb == t_bb) return &e;
-    SpecEntry e{t_bb, {}, 0.0, 0.0, nullptr, nullptr, {}, {}, 0.0, 0.0, 0.0, nullptr, nullptr};
-    spectrum_build(t_bb, e.host, e.psi0, e.xi0);
+    SpecEntry e{t_bb, {}, {}, 0.0, 0.0, 0.0, 0.0, 0.0, nullptr, nullptr, nullptr};
+    spectrum_lin_build(kHNu0Erg / (kKbErgK * t_bb), e);
     if (device >= 0) {
-        spectrum_lin_build(kHNu0Erg / (kKbErgK * t_bb), e);
-        std::vector<float> f(e.host.begin(), e.host.end());
-        double* dd = nullptr;
-        float* df = nullptr;
         LinPiece* dl = nullptr;
         float4* dlf = nullptr;
+        float4* dlF = nullptr;
         const size_t nl = e.lin_a.size();
-        // head = the value rounded to float, tail = the rest rounded to float
-        std::vector<float4> lf(4 * nl);
+        // double-float pairs: head = the value rounded to float, tail = the rest rounded to float
+        std::vector<float4> lf(4 * nl), lF(2 * nl);
         auto pair = [](double x, float& h, float& l) {
             h = (float)x;
             l = (float)(x - (double)h);
@@ -385,28 +345,25 @@ const SpecEntry* spectrum_entry(int device, double t_bb, std::string& why)
             pair(p.c1, u.z, u.w);
             pair(p.c2, v.x, v.y);
             pair(p.c3, v.z, v.w);
+            lF[q] = make_float4((float)p.v, (float)p.c1, (float)p.c2, (float)p.c3);
         }
-        if (cudaMalloc(&dd, sizeof(double) * e.host.size()) != cudaSuccess ||
-            cudaMalloc(&df, sizeof(float) * f.size()) != cudaSuccess ||
-            cudaMalloc(&dl, sizeof(LinPiece) * 2 * nl) != cudaSuccess ||
+        if (cudaMalloc(&dl, sizeof(LinPiece) * 2 * nl) != cudaSuccess ||
             cudaMalloc(&dlf, sizeof(float4) * lf.size()) != cudaSuccess ||
-            cudaMemcpy(dlf, lf.data(), sizeof(float4) * lf.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(dd, e.host.data(), sizeof(double) * e.host.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(df, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMalloc(&dlF, sizeof(float4) * lF.size()) != cudaSuccess ||
             cudaMemcpy(dl, e.lin_a.data(), sizeof(LinPiece) * nl, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(dl + nl, e.lin_b.data(), sizeof(LinPiece) * nl, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaMemcpy(dl + nl, e.lin_b.data(), sizeof(LinPiece) * nl, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(dlf, lf.data(), sizeof(float4) * lf.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(dlF, lF.data(), sizeof(float4) * lF.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(dd);
-            cudaFree(df);
             cudaFree(dl);
             cudaFree(dlf);
+            cudaFree(dlF);
             why = "device allocation of the spectrum table failed";
             return nullptr;
         }
-        e.dev_d = dd;
-        e.dev_f = df;
         e.dev_lin = dl;
         e.dev_linf = dlf;
+        e.dev_linF = dlF;
     }
     list.push_back(std::move(e));
     return &list.back();
@@ -414,35 +371,52 @@ const SpecEntry* spectrum_entry(int device, double t_bb, std::string& why)
 
 }  // namespace
 
-// Host evaluation of the table at t_bb (the host copy; entries are immutable once added).
+// Host evaluation of the pieces at t_bb (the host copy; entries are immutable once added): the same
+// functions the FP64 march runs.
 static void spec_eval_host(double t_bb, double tau, double* phi, double* psi)
 {
     std::string why;
     const SpecEntry* e = spectrum_entry(-1, t_bb, why);
     SpecTable<double> T;
-    T.v = e->host.data();
+    T.lin_a = e->lin_a.data();
+    T.lin_b = e->lin_b.data();
     T.psi0 = e->psi0;
     T.xi0 = e->xi0;
-    nyx::spec_eval<double>(T, tau, *phi, *psi);
+    T.zeta0 = e->zeta0;
+    T.phi_end = e->phi_end;
+    T.psi_end = e->psi_end;
+    *phi = nyx::lin_phi(T, tau);
+    *psi = nyx::lin_psi(T, tau);
 }
 
 int nyx::spectrum_table(int device, double t_bb, SpecTable<double>* d, SpecTable<float>* f, std::string& why)
 {
     const SpecEntry* e = spectrum_entry(device, t_bb, why);
     if (!e) return RT_ENOMEM;
-    d->v = e->dev_d;
-    d->psi0 = e->psi0;
-    d->xi0 = e->xi0;
-    d->lin_a = e->dev_lin;
-    d->lin_b = e->dev_lin ? e->dev_lin + e->lin_a.size() : nullptr;
-    d->zeta0 = e->zeta0;
-    d->phi_end = e->phi_end;
-    d->psi_end = e->psi_end;
-    d->lin_af = e->dev_linf;
-    d->lin_bf = e->dev_linf ? e->dev_linf + 2 * e->lin_a.size() : nullptr;
-    f->v = e->dev_f;
-    f->psi0 = (float)e->psi0;
-    f->xi0 = (float)e->xi0;
+    SpecTable<double> t;
+    t.lin_a = e->dev_lin;
+    t.lin_b = e->dev_lin ? e->dev_lin + e->lin_a.size() : nullptr;
+    t.lin_af = e->dev_linf;
+    t.lin_bf = e->dev_linf ? e->dev_linf + 2 * e->lin_a.size() : nullptr;
+    t.lin_f = e->dev_linF;
+    t.psi0 = e->psi0;
+    t.xi0 = e->xi0;
+    t.zeta0 = e->zeta0;
+    t.phi_end = e->phi_end;
+    t.psi_end = e->psi_end;
+    *d = t;
+    SpecTable<float> u;
+    u.lin_a = t.lin_a;
+    u.lin_b = t.lin_b;
+    u.lin_af = t.lin_af;
+    u.lin_bf = t.lin_bf;
+    u.lin_f = t.lin_f;
+    u.psi0 = t.psi0;
+    u.xi0 = t.xi0;
+    u.zeta0 = t.zeta0;
+    u.phi_end = t.phi_end;
+    u.psi_end = t.psi_end;
+    *f = u;
     return RT_OK;
 }
 

@@ -88,7 +88,7 @@ struct MarchArgs {
     int overlap_mode;
     int hash;
     long long rs;                    // periodic boundaries: travel-distance cutoff (2^-24 cells); 0: none
-    SpecTable<R> spec;               // RT_SPECTRUM_BLACKBODY table; spec.v null: gray
+    SpecTable<R> spec;               // RT_SPECTRUM_BLACKBODY pieces; spec.lin_a null: gray
     DevStats* st;
     // parents of this level counted on the device (written by the previous level's launch): the
     // launch then covers children [c0, min(c1, c0 + 4 * *in_count)); null: [c0, c1) as given

@@ -6,151 +6,116 @@
 // photons (average over the photon-number spectrum), absorbs
 // Phi(tau) - Phi(tau + dtau) over a segment of optical depth dtau, and in an
 // optically thin cell deposits at the rate Psi(tau) = <s exp(-tau s)> per unit
-// dtau. Phi and Psi are tabulated once per temperature on a logarithmic grid
-// in tau with their derivatives in ln tau, and read back by cubic Hermite
-// interpolation.
+// dtau.
+//
+// Phi and Psi are read from cubic pieces in tau itself, built once per
+// temperature. Below tau = 1, piece k covers [2^e (1 + i/32), 2^e (1 + (i+1)/32))
+// with e = kLinExpLo + k / 32 and i = k % 32; from tau = 1 on the pieces are four
+// times finer, 128 per octave, where a cubic in tau follows Phi less closely. So
+// k and the position t in [0, 1) come exactly from the bits of tau (no
+// logarithm), and a piece's width is a power of two. Below 2^-20 Phi follows its
+// series in tau; above 2^14 it keeps its value there.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 
 namespace nyx {
 
-constexpr double kSpecTauLo = 1e-8;       // first grid point; below it the expansions in tau
-constexpr int kSpecPerDecade = 64;
-constexpr int kSpecDecades = 12;          // up to tau = 1e4
-constexpr int kSpecPoints = kSpecPerDecade * kSpecDecades + 1;
-constexpr double kSpecTauHi = 1e4;
-
-// The FP64 march reads Phi and Psi from cubic pieces in tau itself. Below tau = 1, piece k covers
-// [2^e (1 + i/32), 2^e (1 + (i+1)/32)) with e = kLinExpLo + k / 32 and i = k % 32; from tau = 1 on the
-// pieces are four times finer, 128 per octave, where a cubic in tau follows Phi less closely. So k
-// and the position t in [0, 1) come exactly from the bits of a double tau (no logarithm), and a
-// piece's width is a power of two. Below 2^-20 Phi follows its series in tau; above 2^14 it keeps its
-// value there.
+constexpr double kSpecTauHi = 1e4;                          // largest tau_max with the blackbody rate
 constexpr int kLinExpLo = -20;
 constexpr int kLinOmega = -kLinExpLo * 32;                  // the pieces below tau = 1
 constexpr int kLinIntervals = kLinOmega + 14 * 128;         // up to 2^14
 constexpr double kLinTauLo = 9.5367431640625e-07;           // 2^-20
 constexpr double kLinTauHi = 16384.0;                       // 2^14
 
-// One cubic piece: on interval k, Phi(t) - Phi_k = c1 t + c2 t^2 + c3 t^3 (lin_a) and Psi(t) = v + c1 t
+// One cubic piece: on piece k, Phi(t) - Phi_k = c1 t + c2 t^2 + c3 t^3 (lin_a) and Psi(t) = v + c1 t
 // + c2 t^2 + c3 t^3 (lin_b). In lin_a, v is Phi_k from tau = 1 on and Omega_k = 1 - Phi_k below it,
 // so that small absorbed fractions keep their relative precision.
 struct __align__(32) LinPiece {
     double v, c1, c2, c3;
 };
 
-// Table of one temperature: v[4 j .. 4 j + 3] = Phi, dPhi/dln tau, Psi, dPsi/dln tau at
-// tau_j = kSpecTauLo 10^(j / kSpecPerDecade); psi0 = Psi(0), xi0 = <s^2>. lin_a, lin_b and the
-// values after them: the FP64 march's pieces (double tables only); zeta0 = <s^3>.
+// The pieces of one temperature on one device (or the host). lin_a / lin_b: the FP64 pieces, read by
+// the FP64 walk and, on the host, by rt_spectrum_eval; lin_af / lin_bf: the same as double-float
+// pairs for the FP64 table march, two float4 per piece, {v.h, v.l, c1.h, c1.l}, {c2.h, c2.l, c3.h,
+// c3.l}; lin_f: the FP32 march's pieces rounded to float, one float4 {v, c1, c2, c3} per piece, the
+// Phi pieces then the Psi pieces. psi0 = <s>, xi0 = <s^2>, zeta0 = <s^3> (the series below 2^-20);
+// phi_end and psi_end at 2^14. lin_a null: the gray rate.
 template <class R>
 struct SpecTable {
-    const R* v = nullptr;
-    R psi0 = 0, xi0 = 0;
     const LinPiece* lin_a = nullptr;
     const LinPiece* lin_b = nullptr;
-    double zeta0 = 0, phi_end = 0, psi_end = 0;
-    // the same pieces as double-float pairs for the FP32 pipe, two float4 per piece:
-    // {v.h, v.l, c1.h, c1.l}, {c2.h, c2.l, c3.h, c3.l}
     const float4* lin_af = nullptr;
     const float4* lin_bf = nullptr;
+    const float4* lin_f = nullptr;
+    double psi0 = 0, xi0 = 0, zeta0 = 0, phi_end = 0, psi_end = 0;
 };
 
-template <class R>
-__host__ __device__ inline R spec_log(R x)
+__host__ __device__ __forceinline__ long long lin_bits(const double x)
 {
-    return log(x);
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(x);
+#else
+    long long b;
+    std::memcpy(&b, &x, sizeof b);
+    return b;
+#endif
 }
 
-// Phi(tau) and Psi(tau) from a table; tau >= 0.
-template <class R>
-__host__ __device__ inline void spec_eval(const SpecTable<R>& T, R tau, R& phi, R& psi)
+__host__ __device__ __forceinline__ double lin_double(const long long b)
 {
-    if (tau < (R)kSpecTauLo) {
-        phi = (R)1 - tau * T.psi0;
-        psi = T.psi0 - tau * T.xi0;
-        return;
-    }
-    const R inv_h = (R)(kSpecPerDecade / 2.302585092994046);     // 1 / ln-spacing
-    const R h = (R)(2.302585092994046 / kSpecPerDecade);
-    R u = (spec_log<R>(tau) - (R)(-18.420680743952367)) * inv_h;  // ln(1e-8)
-    int j = (int)u;
-    if (j >= kSpecPoints - 1) {
-        phi = T.v[4 * (kSpecPoints - 1)];
-        psi = T.v[4 * (kSpecPoints - 1) + 2];
-        return;
-    }
-    const R t = u - (R)j;
-    const R t2 = t * t, t3 = t2 * t;
-    const R h00 = (R)2 * t3 - (R)3 * t2 + (R)1, h10 = t3 - (R)2 * t2 + t;
-    const R h01 = (R)3 * t2 - (R)2 * t3, h11 = t3 - t2;
-    const R* a = T.v + 4 * j;
-    phi = h00 * a[0] + h10 * h * a[1] + h01 * a[4] + h11 * h * a[5];
-    psi = h00 * a[2] + h10 * h * a[3] + h01 * a[6] + h11 * h * a[7];
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double x;
+    std::memcpy(&x, &b, sizeof x);
+    return x;
+#endif
 }
 
-// Phi(tau) alone (the same operations as spec_eval's Phi): what a segment that absorbs
-// P (Phi(tau) - Phi(tau + dtau)) needs at its far end.
-template <class R>
-__host__ __device__ inline R spec_phi(const SpecTable<R>& T, R tau)
+// 2^n as a double, for a normal result
+__host__ __device__ __forceinline__ double lin_pow2(const int n)
 {
-    if (tau < (R)kSpecTauLo) return (R)1 - tau * T.psi0;
-    const R inv_h = (R)(kSpecPerDecade / 2.302585092994046);
-    const R h = (R)(2.302585092994046 / kSpecPerDecade);
-    R u = (spec_log<R>(tau) - (R)(-18.420680743952367)) * inv_h;
-    int j = (int)u;
-    if (j >= kSpecPoints - 1) return T.v[4 * (kSpecPoints - 1)];
-    const R t = u - (R)j;
-    const R t2 = t * t, t3 = t2 * t;
-    const R h00 = (R)2 * t3 - (R)3 * t2 + (R)1, h10 = t3 - (R)2 * t2 + t;
-    const R h01 = (R)3 * t2 - (R)2 * t3, h11 = t3 - t2;
-    const R* a = T.v + 4 * j;
-    return h00 * a[0] + h10 * h * a[1] + h01 * a[4] + h11 * h * a[5];
+    return lin_double((long long)(1023 + n) << 52);
 }
 
-#ifdef __CUDACC__
-// Piece, exact position t and width 2^wexp of a double tau in [2^-20, 2^14): k from the exponent
-// and the top five (below 1) or seven mantissa bits, t from the others (exactly representable).
-__device__ __forceinline__ int lin_locate(const double tau, double& t, int& wexp)
+// Piece, exact position t and width 2^wexp of a double tau in [2^-20, 2^14): k from the exponent and
+// the top five (below 1) or seven mantissa bits, t from the others (exactly representable).
+__host__ __device__ __forceinline__ int lin_locate(const double tau, double& t, int& wexp)
 {
-    const long long b = __double_as_longlong(tau);
+    const long long b = lin_bits(tau);
     const int e = (int)(b >> 52) - 1023;
     const int hb = e < 0 ? 5 : 7;
-    t = __longlong_as_double(0x3FF0000000000000LL | ((b & ((1LL << (52 - hb)) - 1)) << hb)) - 1.0;
+    t = lin_double(0x3FF0000000000000LL | ((b & ((1LL << (52 - hb)) - 1)) << hb)) - 1.0;
     wexp = e - hb;
     return e < 0 ? (e - kLinExpLo) * 32 + (int)((b >> 47) & 31) : kLinOmega + (e << 7) + (int)((b >> 45) & 127);
 }
 
-__device__ __forceinline__ int lin_index(const double tau)
+__host__ __device__ __forceinline__ int lin_index(const double tau)
 {
-    const long long b = __double_as_longlong(tau);
-    const int e = (int)(b >> 52) - 1023;
-    return e < 0 ? (e - kLinExpLo) * 32 + (int)((b >> 47) & 31) : kLinOmega + (e << 7) + (int)((b >> 45) & 127);
+    double t;
+    int w;
+    return lin_locate(tau, t, w);
 }
 
 // The width exponent of piece k.
-__device__ __forceinline__ int lin_wexp(const int k)
+__host__ __device__ __forceinline__ int lin_wexp(const int k)
 {
     return k < kLinOmega ? kLinExpLo + k / 32 - 5 : ((k - kLinOmega) >> 7) - 7;
 }
 
-// 2^n for a normal result
-__device__ __forceinline__ double lin_pow2(const int n)
-{
-    return __longlong_as_double((long long)(1023 + n) << 52);
-}
-
 // Omega(tau) = 1 - Phi(tau) below 2^-20: tau <s> - tau^2 <s^2> / 2 + tau^3 <s^3> / 6 (the next
 // term, below 2^-80 / 24, is dropped).
-__device__ __forceinline__ double lin_series(const SpecTable<double>& S, const double tau)
+__host__ __device__ __forceinline__ double lin_series(const SpecTable<double>& S, const double tau)
 {
     return tau * fma(-tau, fma(-tau, S.zeta0 * (1.0 / 6.0), 0.5 * S.xi0), S.psi0);
 }
 
 // Omega(tau) below tau = 1, Phi(tau) from 1 on.
-__device__ __forceinline__ double lin_rep(const SpecTable<double>& S, const double tau)
+__host__ __device__ __forceinline__ double lin_rep(const SpecTable<double>& S, const double tau)
 {
     if (tau < kLinTauLo) return lin_series(S, tau);
     if (tau >= kLinTauHi) return S.phi_end;
@@ -163,14 +128,14 @@ __device__ __forceinline__ double lin_rep(const SpecTable<double>& S, const doub
 }
 
 // Phi(tau): the fraction of a ray's photons left after threshold optical depth tau.
-__device__ __forceinline__ double lin_phi(const SpecTable<double>& S, const double tau)
+__host__ __device__ __forceinline__ double lin_phi(const SpecTable<double>& S, const double tau)
 {
     const double r = lin_rep(S, tau);
     return tau < 1.0 ? 1.0 - r : r;
 }
 
 // Psi(tau): the optically thin deposition rate per unit threshold optical depth.
-__device__ __forceinline__ double lin_psi(const SpecTable<double>& S, const double tau)
+__host__ __device__ __forceinline__ double lin_psi(const SpecTable<double>& S, const double tau)
 {
     if (tau < kLinTauLo) return fma(-tau, fma(-tau, 0.5 * S.zeta0, S.xi0), S.psi0);
     if (tau >= kLinTauHi) return S.psi_end;
@@ -183,7 +148,7 @@ __device__ __forceinline__ double lin_psi(const SpecTable<double>& S, const doub
 
 // (Phi(t0) - Phi(t0 + T)) / T on piece p: minus the mean slope of its cubic, (c1 + c2 s1 + c3 s2)
 // with s1 = t0 + t1, s2 = t0^2 + t0 t1 + t1^2, so a thin segment loses nothing to cancellation.
-__device__ __forceinline__ double lin_slope(const LinPiece& p, const double t0, const double T)
+__host__ __device__ __forceinline__ double lin_slope(const LinPiece& p, const double t0, const double T)
 {
     const double t1 = t0 + T;
     const double s1 = t0 + t1;
@@ -194,11 +159,11 @@ __device__ __forceinline__ double lin_slope(const LinPiece& p, const double t0, 
 // A segment of optical depth dtau = kap ds after tau0 (kap > 0): frac = Phi(tau0) - Phi(tau0 + dtau),
 // the fraction of the ray's photons it absorbs, and per_kap = frac / kap. Within one piece the
 // difference is T = dtau / width times the piece's mean slope in t (and per_kap = ds / width times
-// it, with no division); a segment that ends
-// in the next piece is split at the node; longer ones subtract the two values, in Omega below tau = 1
-// and Phi above, where neither loses its relative precision.
-__device__ __forceinline__ void lin_absorb(const SpecTable<double>& S, const double tau0, const double dtau,
-                                           const double kap, const double ds, double& frac, double& per_kap)
+// it, with no division); a segment that ends in the next piece is split at the node; longer ones
+// subtract the two values, in Omega below tau = 1 and Phi above, where neither loses its relative
+// precision.
+__host__ __device__ __forceinline__ void lin_absorb(const SpecTable<double>& S, const double tau0, const double dtau,
+                                                    const double kap, const double ds, double& frac, double& per_kap)
 {
     const double tau1 = tau0 + dtau;
     if (tau1 < kLinTauLo) {
@@ -235,6 +200,93 @@ __device__ __forceinline__ void lin_absorb(const SpecTable<double>& S, const dou
     const double r0 = lin_rep(S, tau0), r1 = lin_rep(S, tau1);
     frac = tau1 < 1.0 ? r1 - r0 : (tau0 < 1.0 ? (1.0 - r1) - r0 : r0 - r1);
     per_kap = frac / kap;
+}
+
+#ifdef __CUDACC__
+// ---- the FP32 march: the same pieces rounded to float (lin_f), located from the bits of a float tau.
+
+__device__ __forceinline__ float lin_pow2f(const int n)
+{
+    return __uint_as_float((unsigned)(127 + n) << 23);
+}
+
+__device__ __forceinline__ int lin_locate_f(const float tau, float& t, int& wexp)
+{
+    const unsigned b = __float_as_uint(tau);
+    const int e = (int)(b >> 23) - 127;
+    const int hb = e < 0 ? 5 : 7;
+    t = __uint_as_float(0x3F800000u | ((b & ((1u << (23 - hb)) - 1u)) << hb)) - 1.0f;
+    wexp = e - hb;
+    return e < 0 ? (e - kLinExpLo) * 32 + (int)((b >> 18) & 31) : kLinOmega + (e << 7) + (int)((b >> 16) & 127);
+}
+
+__device__ __forceinline__ float lin_slope_f(const float4 p, const float t0, const float T)
+{
+    const float t1 = t0 + T;
+    const float s1 = t0 + t1;
+    const float s2 = fmaf(t0, s1, t1 * t1);
+    return -fmaf(p.w, s2, fmaf(p.z, s1, p.y));
+}
+
+// Omega(tau) below tau = 1, Phi(tau) from 1 on (FP32).
+__device__ __forceinline__ float lin_rep_f(const SpecTable<float>& S, const float tau)
+{
+    if (tau < (float)kLinTauLo) return tau * fmaf(-tau, (float)(0.5 * S.xi0), (float)S.psi0);
+    if (tau >= (float)kLinTauHi) return (float)S.phi_end;
+    float t;
+    int we;
+    const int k = lin_locate_f(tau, t, we);
+    const float4 p = S.lin_f[k];
+    const float c = t * fmaf(t, fmaf(t, p.w, p.z), p.y);
+    return k < kLinOmega ? p.x - c : p.x + c;
+}
+
+__device__ __forceinline__ float lin_phi_f(const SpecTable<float>& S, const float tau)
+{
+    const float r = lin_rep_f(S, tau);
+    return tau < 1.0f ? 1.0f - r : r;
+}
+
+__device__ __forceinline__ float lin_psi_f(const SpecTable<float>& S, const float tau)
+{
+    if (tau < (float)kLinTauLo) return fmaf(-tau, (float)S.xi0, (float)S.psi0);
+    if (tau >= (float)kLinTauHi) return (float)S.psi_end;
+    float t;
+    int we;
+    const int k = lin_locate_f(tau, t, we);
+    const float4 p = S.lin_f[kLinIntervals + k];
+    return fmaf(t, fmaf(t, fmaf(t, p.w, p.z), p.y), p.x);
+}
+
+// Phi(tau0) - Phi(tau0 + dtau) (FP32, kap > 0): as lin_absorb, with the whole pieces between a
+// segment's first and last piece taken from node values.
+__device__ __forceinline__ float lin_absorb_f(const SpecTable<float>& S, const float tau0, const float dtau)
+{
+    const float tau1 = tau0 + dtau;
+    if (tau1 < (float)kLinTauLo) return dtau * fmaf(-0.5f * (float)S.xi0, tau0 + tau1, (float)S.psi0);
+    if (tau0 >= (float)kLinTauLo && tau1 < (float)kLinTauHi) {
+        float t0, t1;
+        int w0, w1;
+        const int k0 = lin_locate_f(tau0, t0, w0);
+        const int k1 = lin_locate_f(tau1, t1, w1);
+        const float4* P = S.lin_f;
+        if (k1 == k0) {
+            const float T = dtau * lin_pow2f(-w0);
+            return T * lin_slope_f(P[k0], t0, T);
+        }
+        const float T0 = 1.0f - t0;
+        const float f0 = T0 * lin_slope_f(P[k0], t0, T0);
+        const float T1 = k1 == k0 + 1 ? fmaf(-T0, lin_pow2f(w0), dtau) * lin_pow2f(-w1) : t1;
+        const float f1 = T1 * lin_slope_f(P[k1], 0.0f, T1);
+        float mid = 0.0f;                                   // Phi_a - Phi_b, a = k0 + 1, b = k1
+        if (k1 >= k0 + 2) {
+            const float va = P[k0 + 1].x, vb = P[k1].x;
+            mid = k1 < kLinOmega ? vb - va : (k0 + 1 >= kLinOmega ? va - vb : (1.0f - vb) - va);
+        }
+        return f0 + (mid + f1);
+    }
+    const float r0 = lin_rep_f(S, tau0), r1 = lin_rep_f(S, tau1);
+    return tau1 < 1.0f ? r1 - r0 : (tau0 < 1.0f ? (1.0f - r1) - r0 : r0 - r1);
 }
 #endif
 

@@ -222,20 +222,21 @@ def test_spectrum_parity(nyx, case, prec, walk):
     bookkeeping bit for bit (tau decides everything), fields within the spectrum table's
     interpolation accuracy of the oracle's direct quadrature. FP64 reads cubic pieces in tau (32 per
     octave below tau = 1, 128 above) whose mean slope over a segment is within about 1e-8 of the
-    quadrature where Phi is not negligible: 1e-9 relative L2 on Gamma and absorbed; FP32 keeps its
-    logarithmic table: 2e-5 of the FP64 oracle."""
+    quadrature where Phi is not negligible: 1e-9 relative L2 on Gamma and absorbed. FP32 reads the
+    same pieces rounded to float (2^-24 on each coefficient) in float arithmetic: 2e-6 of the FP64
+    oracle (measured at most 3.1e-7 on Gamma, 4.5e-9 on absorbed)."""
     n, k, seed, xm, dxc, mode, t_bb, per = case
     w = I.random_small(n, k, seed=seed, x_mode=xm, box_cm=n * dxc)
     kw = dict(overlap_mode=mode, n_th_cm3=0.3 * float(w.n_h.mean()), spectrum=1, t_bb_K=t_bb, periodic=per)
     ref, got = run_both(nyx, w, precision=prec, flags=nyx.RT_FLAG_NO_GEOMETRY_TABLE if walk else 0, **kw)
     assert_bookkeeping(got["stats"], ref["stats"])
     ref64 = ref if prec == 0 else oracle.run_workload(w, precision=0, **kw)
-    assert relerr(got["gamma"], ref64["gamma"]) < (1e-9 if prec == 0 else 2e-5)
+    assert relerr(got["gamma"], ref64["gamma"]) < (1e-9 if prec == 0 else 2e-6)
     st = got["stats"]
     e = st["emitted_ph"]
     tol = 1e-12 if prec == 0 else 1e-6
     assert abs(st["absorbed_ph"] + st["escaped_ph"] + st["dropped_ph"] - e) / e < tol
-    assert abs(st["absorbed_ph"] / ref64["stats"]["absorbed_ph"] - 1) < (1e-9 if prec == 0 else 2e-5)
+    assert abs(st["absorbed_ph"] / ref64["stats"]["absorbed_ph"] - 1) < (1e-9 if prec == 0 else 2e-6)
     if mode in (0, 2, 3):
         assert abs(st["deposited_ph"] - st["absorbed_ph"]) / e < (1e-10 if prec == 0 else 1e-5)
 
