@@ -258,33 +258,37 @@ __device__ __forceinline__ float lin_psi_f(const SpecTable<float>& S, const floa
     return fmaf(t, fmaf(t, fmaf(t, p.w, p.z), p.y), p.x);
 }
 
-// Phi(tau0) - Phi(tau0 + dtau) (FP32, kap > 0): as lin_absorb, with the whole pieces between a
-// segment's first and last piece taken from node values.
+__device__ __forceinline__ float lin_slope0_f(const float4 p, const float T)
+{
+    return -fmaf(T, fmaf(T, p.w, p.z), p.y);
+}
+
+// Phi(tau0) - Phi(tau0 + dtau) (FP32, kap > 0): as lin_absorb, by one code path for every segment
+// between 2^-20 and 2^14 (the part in tau0's piece, the whole pieces between from node values, the
+// part in tau1's piece), so the lanes of a warp do not diverge on where their segments end.
 __device__ __forceinline__ float lin_absorb_f(const SpecTable<float>& S, const float tau0, const float dtau)
 {
     const float tau1 = tau0 + dtau;
-    if (tau1 < (float)kLinTauLo) return dtau * fmaf(-0.5f * (float)S.xi0, tau0 + tau1, (float)S.psi0);
     if (tau0 >= (float)kLinTauLo && tau1 < (float)kLinTauHi) {
         float t0, t1;
         int w0, w1;
         const int k0 = lin_locate_f(tau0, t0, w0);
         const int k1 = lin_locate_f(tau1, t1, w1);
         const float4* P = S.lin_f;
-        if (k1 == k0) {
-            const float T = dtau * lin_pow2f(-w0);
-            return T * lin_slope_f(P[k0], t0, T);
-        }
-        const float T0 = 1.0f - t0;
-        const float f0 = T0 * lin_slope_f(P[k0], t0, T0);
-        const float T1 = k1 == k0 + 1 ? fmaf(-T0, lin_pow2f(w0), dtau) * lin_pow2f(-w1) : t1;
-        const float f1 = T1 * lin_slope_f(P[k1], 0.0f, T1);
-        float mid = 0.0f;                                   // Phi_a - Phi_b, a = k0 + 1, b = k1
-        if (k1 >= k0 + 2) {
-            const float va = P[k0 + 1].x, vb = P[k1].x;
-            mid = k1 < kLinOmega ? vb - va : (k0 + 1 >= kLinOmega ? va - vb : (1.0f - vb) - va);
-        }
+        const float4 p0 = P[k0];
+        const bool same = k1 == k0;
+        const float T0 = same ? dtau * lin_pow2f(-w0) : 1.0f - t0;
+        const float f0 = T0 * lin_slope_f(p0, t0, T0);
+        const float4 p1 = P[k1];
+        const float T1 = same ? 0.0f : (k1 == k0 + 1 ? fmaf(-T0, lin_pow2f(w0), dtau) * lin_pow2f(-w1) : t1);
+        const float f1 = T1 * lin_slope0_f(p1, T1);
+        const int ka = min(k0 + 1, kLinIntervals - 1);     // Phi_a - Phi_b, a = k0 + 1, b = k1
+        const float va = P[ka].x, vb = p1.x;
+        float mid = k1 < kLinOmega ? vb - va : (ka >= kLinOmega ? va - vb : (1.0f - vb) - va);
+        mid = k1 >= k0 + 2 ? mid : 0.0f;
         return f0 + (mid + f1);
     }
+    if (tau1 < (float)kLinTauLo) return dtau * fmaf(-0.5f * (float)S.xi0, tau0 + tau1, (float)S.psi0);
     const float r0 = lin_rep_f(S, tau0), r1 = lin_rep_f(S, tau1);
     return tau1 < 1.0f ? r1 - r0 : (tau0 < 1.0f ? (1.0f - r1) - r0 : r0 - r1);
 }
