@@ -257,6 +257,15 @@ int64_t rt_geometry_table_bytes(int32_t device);
  * checking). Returns RT_EINVAL for tau outside [0, 1e4] or t_bb_K <= 0. */
 int rt_spectrum_eval(double t_bb_K, double tau, double* phi, double* psi);
 
+/* The fraction Phi(tau) - Phi(tau + dtau) of a ray's photons that a segment of
+ * threshold optical depth dtau > 0 absorbs after tau, computed on the host by the
+ * same function the FP64 march runs on the device (the mean slope of the cubic
+ * piece within a piece, split at a node, node values across several pieces;
+ * Eq. 1 over a blackbody spectrum, Sec. 2.5). *frac receives it. Returns
+ * RT_EINVAL for tau outside [0, 1e4], dtau not in (0, 1e4], t_bb_K <= 0 or a
+ * null pointer. For checking. */
+int rt_spectrum_absorb(double t_bb_K, double tau, double dtau, double* frac);
+
 /* Text of the handle's last error ("" if none); for h == NULL, the last
  * error of a failed rt_create on this thread. */
 const char* rt_last_error(const rt_handle* h);

@@ -111,6 +111,8 @@ def lib():
         L.rt_reconfigure.argtypes = [P, C.POINTER(rt_config)]
         L.rt_spectrum_eval.argtypes = [d, d, C.POINTER(d), C.POINTER(d)]
         L.rt_spectrum_eval.restype = C.c_int
+        L.rt_spectrum_absorb.argtypes = [d, d, d, C.POINTER(d)]
+        L.rt_spectrum_absorb.restype = C.c_int
         L.rt_geometry_table_bytes.argtypes = [i32]
         L.rt_geometry_table_bytes.restype = i64
         L.rt_step.argtypes = [P, d, P, P, C.c_int, C.POINTER(rt_stats)]
@@ -152,7 +154,7 @@ def lib():
 
 def exported_symbols():
     return ["rt_config_default", "rt_create", "rt_set_fields", "rt_add_sources", "rt_clear_sources", "rt_reconfigure",
-            "rt_geometry_table_bytes", "rt_spectrum_eval", "rt_step",
+            "rt_geometry_table_bytes", "rt_spectrum_eval", "rt_spectrum_absorb", "rt_step",
             "rt_get_x", "rt_get_sources", "rt_save", "rt_load", "rt_destroy", "rt_last_error", "rt_version", "rt_batch_create", "rt_batch_set_params",
             "rt_batch_get_params", "rt_batch_tune", "rt_batch_capture", "rt_batch_run", "rt_batch_destroy",
             "rt_batch_last_error", "rt_server_config_default", "rt_server_create", "rt_server_submit",
@@ -211,6 +213,15 @@ def rt_spectrum_eval(t_bb_K: float, tau: float):
     if rc != RT_OK:
         raise NyxError(rc, "rt_spectrum_eval: tau in [0, 1e4], t_bb_K > 0")
     return phi.value, psi.value
+
+
+def rt_spectrum_absorb(t_bb_K: float, tau: float, dtau: float) -> float:
+    """Phi(tau) - Phi(tau + dtau) as the FP64 march computes it (host evaluation)."""
+    frac = C.c_double()
+    rc = lib().rt_spectrum_absorb(float(t_bb_K), float(tau), float(dtau), C.byref(frac))
+    if rc != RT_OK:
+        raise NyxError(rc, "rt_spectrum_absorb: tau in [0, 1e4], dtau in (0, 1e4], t_bb_K > 0")
+    return frac.value
 
 
 def rt_geometry_table_bytes(device: int = 0) -> int:

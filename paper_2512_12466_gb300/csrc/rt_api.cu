@@ -389,6 +389,23 @@ static void spec_eval_host(double t_bb, double tau, double* phi, double* psi)
     *psi = nyx::lin_psi(T, tau);
 }
 
+// One segment's absorbed fraction, as the FP64 march computes it (kap = 1, so ds = dtau).
+static void spec_absorb_host(double t_bb, double tau, double dtau, double* frac)
+{
+    std::string why;
+    const SpecEntry* e = spectrum_entry(-1, t_bb, why);
+    SpecTable<double> T;
+    T.lin_a = e->lin_a.data();
+    T.lin_b = e->lin_b.data();
+    T.psi0 = e->psi0;
+    T.xi0 = e->xi0;
+    T.zeta0 = e->zeta0;
+    T.phi_end = e->phi_end;
+    T.psi_end = e->psi_end;
+    double per_kap;
+    nyx::lin_absorb(T, tau, dtau, 1.0, dtau, *frac, per_kap);
+}
+
 int nyx::spectrum_table(int device, double t_bb, SpecTable<double>* d, SpecTable<float>* f, std::string& why)
 {
     const SpecEntry* e = spectrum_entry(device, t_bb, why);
@@ -1039,6 +1056,15 @@ int rt_spectrum_eval(double t_bb_K, double tau, double* phi, double* psi)
 {
     if (!phi || !psi || !(t_bb_K > 0) || !std::isfinite(t_bb_K) || !(tau >= 0) || !(tau <= kSpecTauHi)) return RT_EINVAL;
     spec_eval_host(t_bb_K, tau, phi, psi);
+    return RT_OK;
+}
+
+int rt_spectrum_absorb(double t_bb_K, double tau, double dtau, double* frac)
+{
+    if (!frac || !(t_bb_K > 0) || !std::isfinite(t_bb_K) || !(tau >= 0) || !(tau <= kSpecTauHi) || !(dtau > 0) ||
+        !(dtau <= kSpecTauHi))
+        return RT_EINVAL;
+    spec_absorb_host(t_bb_K, tau, dtau, frac);
     return RT_OK;
 }
 
