@@ -46,9 +46,9 @@ L2_FLUSH_BYTES = 512 << 20
 # every march launch of one step of the same box with its first 64 sources, taken with
 # `python -m paper_2512_12466_gb300.profile_case --sources 64 --steps 1 --levels`), scaled to the full
 # workload by primary segments. Valid only for the kernel sources it was taken on.
-TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.80412666985661,
-                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "5f36b816d983378b",
-                               "paper_2512_12466_gb300/csrc/rt_internal.h": "a715d541f54dc509"}}
+TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.781914413031373,
+                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "f377f4a644a2787a",
+                               "paper_2512_12466_gb300/csrc/rt_internal.h": "669971fcb157da7e"}}
 
 
 def traffic_per_launch(segments_per_step: float, launches_per_step: float):
