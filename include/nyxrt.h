@@ -246,7 +246,7 @@ int rt_destroy(rt_handle* h);
  * (split radius, level, grid size) and kept until the process exits: row
  * offsets shared by both precisions, 8-byte entries for the FP32 march and
  * 16-byte ones for the FP64 march (each built when that precision first
- * needs the level), within a budget of an eighth of the device's memory
+ * needs the level), within a budget of a quarter of the device's memory
  * (environment variable NYXRT_GEOMETRY_BUDGET_MB overrides it); levels over
  * budget walk their rays. The batched form reads them in both precisions. */
 int64_t rt_geometry_table_bytes(int32_t device);

@@ -88,9 +88,10 @@ namespace {
 
 // Geometry tables (FP32 march): one per (device, split radius, level, grid size covered). A
 // table is never freed while the process runs (handles on other streams may be reading it);
-// a larger grid gets a new one. Their total per device stays within a budget, by default an
-// eighth of the device's memory (NYXRT_GEOMETRY_BUDGET_MB overrides it); a level that does
-// not fit is marched by walking its rays instead.
+// a larger grid gets a new one. Their total per device stays within a budget, by default a
+// quarter of the device's memory (NYXRT_GEOMETRY_BUDGET_MB overrides it): on a GB300 that holds
+// every level of a 256^3 box in both precisions (46 GB) beside those of a 128^3 box. A level that
+// does not fit is marched by walking its rays instead.
 struct GeomTable {
     long long rq;
     long long rs;             // periodic travel-distance cutoff; 0: none
@@ -119,7 +120,7 @@ size_t geometry_budget(int device)
         total_b = 0;
     }
     if (cur != device) cudaSetDevice(cur);
-    return total_b / 8;
+    return total_b / 4;
 }
 
 }  // namespace
