@@ -594,7 +594,7 @@ def bench_serving(nyx, torch, n_req: int):
                                              "wait_batch_ms", "wait_finish_ms", "busy_ms")}
     srv.close()
 
-    # ---- plain per-request launches, first-come first-served, in FP64 (the benchmark spec's baseline) and
+    # ---- plain per-request launches, first-come first-served, in FP64 (the per-request baseline) and
     # in FP32 (the same precision as the served form, to separate batching's gain from precision's);
     # one handle per grid size, re-targeted to each request (rt_reconfigure), so no path allocates
     # per request

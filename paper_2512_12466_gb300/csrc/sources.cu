@@ -60,8 +60,8 @@ __global__ void cell_keys_kernel(const int32_t* __restrict__ cells, int64_t m, i
 // equal keys in index order (keys itself is left as it is; keys_b and keys_c, order_b: scratch).
 // One block of 1024 threads (32 warps), least significant digit first, 8 bits a pass: warp w owns
 // a contiguous chunk of the sequence; a pass counts each warp's digits, scans the counts in
-// (digit, warp) order and scatters every warp's chunk in sequence order, 32 keys a round, a lane
-// placed after the lower lanes of its round that share its digit (found with 8 ballots) - so
+// (digit, warp) order and scatters every warp's chunk in sequence order, 32 keys an iteration, a lane
+// placed after the lower lanes of its iteration that share its digit (found with 8 ballots) - so
 // every pass is stable and the result is the stable sort.
 constexpr int kSortThreads = 1024;
 
@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_sort_kernel(const uint64_t
         const int32_t base = (incl - run) + (wp > 0 ? wsum[wp - 1] : 0);
         for (int q = 0; q < 8; ++q) cnt[sd * 33 + sw + q] = base + loc[q];
         __syncthreads();
-        // scatter, each warp its chunk in order; the next round's key and index are requested
-        // before this round's are placed
+        // scatter, each warp its chunk in order; the next iteration's key and index are requested
+        // before this iteration's are placed
         uint64_t kn = c0 + lane < c1 ? kin[c0 + lane] : 0ULL;
         int32_t xn = c0 + lane < c1 ? (iin ? iin[c0 + lane] : (int32_t)(c0 + lane)) : 0;
         for (int64_t r0 = c0; r0 < c1; r0 += 32) {
