@@ -626,6 +626,29 @@ def test_config2_thin_source_subset_parity(nyx):
             assert relerr(got["gamma"], ref64["gamma"]) < 1e-5
 
 
+def test_thin256_source_subset_parity(nyx):
+    """256^3 thin box (kappa and Gamma beyond L2) at full size, two seeded sources of its 64, in
+    both precisions. Every level the rays reach, level 10 included, reads the geometry tables (the
+    FP64 level-10 table alone is 20 GB), and the result equals the oracle's."""
+    w = I.thin256(64)
+    sub = np.sort(np.random.default_rng(2561).choice(len(w.ndot), size=2, replace=False))
+    w.cells, w.ndot = w.cells[sub], w.ndot[sub]
+    n_th = 0.01 * float(w.n_h.mean())
+    ref64 = None
+    for prec in (0, 1):
+        ref, got = run_both(nyx, w, precision=prec, n_th_cm3=n_th)
+        st = got["stats"]
+        assert_bookkeeping(st, ref["stats"])
+        reached = [l for l, r in enumerate(st["rays"]) if r]
+        assert max(reached) >= 10
+        assert all((st["table_levels"] >> l) & 1 for l in reached), (prec, st["table_levels"], reached)
+        if prec == 0:
+            ref64 = ref
+            assert relerr(got["gamma"], ref["gamma"]) < 1e-12
+        else:
+            assert relerr(got["gamma"], ref64["gamma"]) < 1e-5
+
+
 def test_config2_full_invariants(nyx):
     """All 1024 sources of the 128^3 thin box: ledger closure, deposited =
     absorbed, FP32 vs FP64 fields, reproducible bookkeeping."""
