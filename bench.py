@@ -428,16 +428,18 @@ def bench_spectrum(nyx, torch, w, n_th):
 
 
 def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int | None = None,
-                  tile: int | None = None):
+                  tile: int | None = None, precision: int | None = None):
     """64 independent solves (grid sizes from {32,64,96,128}^3, log-uniform source counts on
-    [1, 4096], per-solve seeds), FP32: the graph-captured batch (light solves in persistent
-    launches, heavy ones in device-sized per-level launches on parallel streams) vs one rt_step
-    per solve. Returns timings, segments and the largest field difference."""
+    [1, 4096], per-solve seeds), FP32 unless `precision` says otherwise: the graph-captured batch
+    (light solves in persistent launches, heavy ones in device-sized per-level launches on parallel
+    streams) vs one rt_step per solve. Returns timings, segments and the largest field difference."""
+    if precision is None:
+        precision = nyx.RT_FP32
     ws = I.batch_solves(64, config=3, x_mode=x_mode)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
     solvers, outs = [], []
     for w in ws:
-        s = nyx.Solver(w.n, w.box_cm, precision=nyx.RT_FP32, n_th_cm3=0.01 * float(w.n_h.mean()),
+        s = nyx.Solver(w.n, w.box_cm, precision=precision, n_th_cm3=0.01 * float(w.n_h.mean()),
                        n_min_ray=4.0, tau_max=30.0)
         s.set_fields(dev(w.n_h), dev(w.x_ion))
         s.add_sources(dev(w.cells), dev(w.ndot))
@@ -485,7 +487,8 @@ def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int |
     b.close()
     for s in solvers:
         s.close()
-    return {"x_variant": x_mode, "solves": 64, "segments_per_step": bsegs, "plain_segments_per_step": segs,
+    return {"x_variant": x_mode, "precision": "f64" if precision == nyx.RT_FP64 else "f32", "solves": 64,
+            "segments_per_step": bsegs, "plain_segments_per_step": segs,
             "plain_ms_per_step": plain_s * 1e3, "batched_ms_per_step": batch_s * 1e3,
             "plain_value": segs / plain_s, "batched_value": bsegs / batch_s, "factor": plain_s / batch_s,
             "max_rel_l2_batched_vs_plain": diff, "steps": steps, "graph": True, "tuned": tuned,
@@ -798,8 +801,10 @@ def run_nyx(args, world, rank, local):
         line["beyond_l2"] = bench_beyond_l2(nyx, torch)
     if not args.no_batched:
         line["batched"] = {"neutral": bench_batched(nyx, torch, "neutral", steps=5, tune=True),
+                           "neutral_fp64": bench_batched(nyx, torch, "neutral", steps=5, tune=True,
+                                                         precision=nyx.RT_FP64),
                            "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 27,
-                                                         tile=32)}
+                                                 tile=32)}
     if args.serve_requests > 0:
         line["serving"] = bench_serving(nyx, torch, args.serve_requests)
     if world == 1 and not args.no_cpu_baseline:
