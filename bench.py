@@ -428,10 +428,11 @@ def bench_spectrum(nyx, torch, w, n_th):
 
 
 def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int | None = None,
-                  tile: int | None = None, precision: int | None = None):
+                  tile: int | None = None, precision: int | None = None, spectrum: int = 0):
     """64 independent solves (grid sizes from {32,64,96,128}^3, log-uniform source counts on
-    [1, 4096], per-solve seeds), FP32 unless `precision` says otherwise: the graph-captured batch
-    (light solves in persistent launches, heavy ones in device-sized per-level launches on parallel
+    [1, 4096], per-solve seeds), FP32 unless `precision` says otherwise, gray unless `spectrum` is 1
+    (a 1e5 K blackbody): the graph-captured batch (light
+    solves in persistent launches, heavy ones in device-sized per-level launches on parallel
     streams) vs one rt_step per solve. Returns timings, segments and the largest field difference."""
     if precision is None:
         precision = nyx.RT_FP32
@@ -440,7 +441,7 @@ def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int |
     solvers, outs = [], []
     for w in ws:
         s = nyx.Solver(w.n, w.box_cm, precision=precision, n_th_cm3=0.01 * float(w.n_h.mean()),
-                       n_min_ray=4.0, tau_max=30.0)
+                       n_min_ray=4.0, tau_max=30.0, spectrum=spectrum, t_bb_K=1e5)
         s.set_fields(dev(w.n_h), dev(w.x_ion))
         s.add_sources(dev(w.cells), dev(w.ndot))
         solvers.append(s)
@@ -487,7 +488,8 @@ def bench_batched(nyx, torch, x_mode: str, steps: int, tune: bool, slice_: int |
     b.close()
     for s in solvers:
         s.close()
-    return {"x_variant": x_mode, "precision": "f64" if precision == nyx.RT_FP64 else "f32", "solves": 64,
+    return {"x_variant": x_mode, "precision": "f64" if precision == nyx.RT_FP64 else "f32",
+            "rate": "blackbody 1e5 K" if spectrum else "gray", "solves": 64,
             "segments_per_step": bsegs, "plain_segments_per_step": segs,
             "plain_ms_per_step": plain_s * 1e3, "batched_ms_per_step": batch_s * 1e3,
             "plain_value": segs / plain_s, "batched_value": bsegs / batch_s, "factor": plain_s / batch_s,
@@ -803,6 +805,8 @@ def run_nyx(args, world, rank, local):
         line["batched"] = {"neutral": bench_batched(nyx, torch, "neutral", steps=5, tune=True),
                            "neutral_fp64": bench_batched(nyx, torch, "neutral", steps=5, tune=True,
                                                          precision=nyx.RT_FP64),
+                           "neutral_blackbody": bench_batched(nyx, torch, "neutral", steps=5, tune=False,
+                                                              spectrum=1),
                            "thin": bench_batched(nyx, torch, "thin", steps=1, tune=False, slice_=1 << 27,
                                                  tile=32)}
     if args.serve_requests > 0:

@@ -282,8 +282,9 @@ const char* rt_version(void);
  * Light solves share cooperative, persistent launches whose warps claim tiles
  * of work from a device queue, level by level and slice by slice, over all
  * their solves at once: this fills the GPU when single solves are small and
- * removes the per-level host round trips of rt_step. Heavy solves (see
- * heavy_shift; always those with RT_SPECTRUM_BLACKBODY) are cut into chunks of
+ * removes the per-level host round trips of rt_step (a launch holds solves of
+ * one rate: gray, or the blackbody at one temperature). Heavy solves (see
+ * heavy_shift) are cut into chunks of
  * sources, each traced by one march launch per level sized on the device from
  * the parents the previous level counted, on parallel streams whose launches
  * overlap. Results equal those of rt_step on each handle (bookkeeping bit for
@@ -330,8 +331,8 @@ int rt_batch_tune(rt_batch* b, int32_t repeats, rt_batch_params* best, double* b
 /* Capture one run (kappa rebuild, trace, finalize, statistics copy) into a
  * CUDA graph; rt_batch_run then replays it. Solves are sorted into the light
  * and heavy paths by their work in the previous run (heavy_shift), so
- * capturing after one run captures that split; before any run, only the
- * blackbody-rate solves take the heavy path. */
+ * capturing after one run captures that split; before any run, every solve is
+ * light (unless heavy_shift is -1). */
 int rt_batch_capture(rt_batch* b);
 
 /* Run the batch: write solve i's Gamma and heating into gamma_out[i] and

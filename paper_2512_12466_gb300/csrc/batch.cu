@@ -137,25 +137,30 @@ int alloc_rays(rt_batch* b, int64_t cap)
     return RT_OK;
 }
 
-int max_blocks_per_sm(rt_batch* b, int block, bool table, bool single)
+int max_blocks_per_sm(rt_batch* b, int block, bool table, bool single, bool freq = false)
 {
-    return batch_blocks_per_sm(b->precision, block, table, single);
+    return batch_blocks_per_sm(b->precision, block, table, single, freq);
 }
 
 // Blocks per SM of a launch: the requested number, or (0) all that fit, within the occupancy of
-// the kernel variant that runs (walking or table-driven, one solve or many).
-int launch_blocks_per_sm(rt_batch* b, bool single)
+// the kernel variant that runs (walking or table-driven, one solve or many, gray or blackbody).
+int launch_blocks_per_sm(rt_batch* b, bool single, bool freq)
 {
-    const int occ = max_blocks_per_sm(b, b->params.block, b->use_geo, single);
+    const int occ = max_blocks_per_sm(b, b->params.block, b->use_geo, single, freq);
     return b->params.blocks_per_sm > 0 ? std::min(b->params.blocks_per_sm, occ) : occ;
 }
 
 // One cooperative launch over the solves whose sources are [src_first, src_first + src_count) of
-// the batch catalog; single >= 0: that is exactly solve `single`.
+// the batch catalog; single >= 0: that is exactly solve `single`. Solve `first` stands for the
+// launch's rate: every solve of a launch has the same (gray, or blackbody at one temperature).
 template <class R>
-int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count, int single)
+int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count, int single, size_t first)
 {
     BatchArgs<R> a;
+    const rt_handle* hf = b->hs[first];
+    a.freq = hf->cfg.spectrum != RT_SPECTRUM_GRAY ? 1 : 0;
+    if constexpr (sizeof(R) == 4) a.spec = hf->spec_f;
+    else a.spec = hf->spec_d;
     a.single = single >= 0 ? 1 : 0;
     a.one = single >= 0 ? b->hsolve[(size_t)single] : BatchSolve{};
     a.solves = b->d_solves;
@@ -175,7 +180,7 @@ int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count, int single)
     a.use_geo = b->use_geo ? 1 : 0;
     for (int l = 0; l <= RT_MAX_LEVELS; ++l) a.geo[l] = b->geo[l];
     a.err = b->d_err;
-    const int grid = b->sm_count * launch_blocks_per_sm(b, single >= 0);
+    const int grid = b->sm_count * launch_blocks_per_sm(b, single >= 0, a.freq != 0);
     cudaError_t e;
     if constexpr (sizeof(R) == 4) e = launch_batch_f32(a, grid, b->params.block, b->stream);
     else e = launch_batch_f64(a, grid, b->params.block, b->stream);
@@ -187,14 +192,11 @@ int launch_trace(rt_batch* b, int64_t src_first, int64_t src_count, int single)
 // 12 4^(l-1) per source.
 int64_t chunk_records(int64_t count, int l) { return count * 12 * (int64_t(1) << (2 * (l - 1))); }
 
-// Solve i takes the heavy path: the frequency-integrated rate (which the persistent kernel does not
-// integrate), or enough work in its last run to fill the device by itself. Before any run a solve is
-// light: a chunk's buffers are sized for every ray of every level, so a heavy path taken blindly
-// by an opaque many-source solve would be thousands of nearly empty launches.
+// Solve i takes the heavy path: enough work in its last run to fill the device by itself. Before
+// any run a solve is light: a chunk's buffers are sized for every ray of every level, so a heavy
+// path taken blindly by an opaque many-source solve would be thousands of nearly empty launches.
 bool heavy_solve(const rt_batch* b, size_t i)
 {
-    const rt_handle* h = b->hs[i];
-    if (h->cfg.spectrum != RT_SPECTRUM_GRAY) return true;
     const int hs = b->params.heavy_shift;
     if (hs < 0) return true;
     return i < b->work.size() && b->work[i] >= (hs > 0 ? (1ULL << hs) : kHeavySegments);
@@ -365,9 +367,15 @@ int enqueue(rt_batch* b)
         }
         size_t i1 = i0;
         int64_t bytes = 0, srcs = 0;
+        // one rate per launch: gray, or the blackbody at one temperature
+        auto same_rate = [&](size_t i) {
+            const rt_config& a = b->hs[i0]->cfg;
+            const rt_config& c = b->hs[i]->cfg;
+            return a.spectrum == c.spectrum && (a.spectrum == RT_SPECTRUM_GRAY || a.t_bb_K == c.t_bb_K);
+        };
         while (i1 < b->hs.size() && !hv[i1]) {
             const int64_t add = rbytes * b->hs[i1]->ncell;
-            if (i1 > i0 && (big(i0) || big(i1) || (gb > 0 && bytes + add > gb))) break;
+            if (i1 > i0 && (big(i0) || big(i1) || (gb > 0 && bytes + add > gb) || !same_rate(i1))) break;
             bytes += add;
             srcs += b->n_emit[i1];
             ++i1;
@@ -376,8 +384,8 @@ int enqueue(rt_batch* b)
             B_CUDA(b, cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned long long) * kMaxSlices, s), "counter clear");
             B_CUDA(b, cudaMemsetAsync(b->d_tiles, 0, sizeof(unsigned long long) * kMaxSlices, s), "counter clear");
             const int single = i1 == i0 + 1 ? (int)i0 : -1;
-            const int rc = b->precision == RT_FP32 ? launch_trace<float>(b, src0, srcs, single)
-                                                   : launch_trace<double>(b, src0, srcs, single);
+            const int rc = b->precision == RT_FP32 ? launch_trace<float>(b, src0, srcs, single, i0)
+                                                   : launch_trace<double>(b, src0, srcs, single, i0);
             if (rc) return rc;
             b->launches += 1;
             if (b->use_geo)
@@ -491,7 +499,7 @@ int apply_params(rt_batch* b, const rt_batch_params& p)
                      "batch params: block 128|256, tile a multiple of 32, slice in [1024, 2^28], group_bytes >= 0, "
                      "heavy_shift in [-1, 62]");
     int occ = 0;
-    for (int v = 0; v < 4; ++v) occ = std::max(occ, max_blocks_per_sm(b, p.block, v & 1, v & 2));
+    for (int v = 0; v < 8; ++v) occ = std::max(occ, max_blocks_per_sm(b, p.block, v & 1, v & 2, v & 4));
     if (p.blocks_per_sm > occ) return bfail(b, RT_EINVAL, "batch params: blocks_per_sm above the occupancy limit");
     const bool realloc = p.slice != b->params.slice || !b->rays[1].base;
     b->params = p;

@@ -1752,16 +1752,17 @@ __global__ void __launch_bounds__(256, TableOccupancy<R>::blocks) march_table_ke
 // kSingle: the launch holds one solve, passed by value in A.one, so its parameters are the same
 // for every lane (kernel parameters, not per-lane loads) and no tally changes hands. Only then does
 // the table-driven kernel fit four blocks per SM; with per-lane solve parameters it takes three.
-template <class R, bool kHash, bool kTable, bool kSingle>
+template <class R, bool kHash, bool kTable, bool kSingle, bool kFreq>
 __global__ void __launch_bounds__(256, (kTable && kSingle) ? TableOccupancy<R>::blocks : MarchOccupancy<R>::blocks)
     batch_kernel(const BatchArgs<R> A)
 {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     const int lane = threadIdx.x & 31;
-    // FP64 solves on the geometry tables: the Eq. 1 rate table of the double-float march in shared memory
+    // FP64 solves on the geometry tables: the Eq. 1 rate table of the double-float march in shared
+    // memory (gray rate only)
     constexpr bool kDf = kTable && sizeof(R) == 8;
-    __shared__ __align__(16) float rtab[kDf ? kRateSmem : 4];
-    if constexpr (kDf) {
+    __shared__ __align__(16) float rtab[(kDf && !kFreq) ? kRateSmem : 4];
+    if constexpr (kDf && !kFreq) {
         for (int i = threadIdx.x; i < kRateSmem; i += blockDim.x) {
             const int row = (i >> 2) % kRateIntervals, half = (i >> 2) / kRateIntervals;
             rtab[i] = kRateTable[row * kRateCoefs + 4 * half + (i & 3)];
@@ -1832,15 +1833,16 @@ __global__ void __launch_bounds__(256, (kTable && kSingle) ? TableOccupancy<R>::
                     V.rs = bs.rs;
                     V.tau_max = (R)bs.tau_max;
                     V.src_off = bs.src_off - A.src_base;
+                    if constexpr (kFreq) V.spec = A.spec;
                     if constexpr (kDf) {
-                        split = march_ray_table_df<kHash, false>(V, rtab, A.geo[l], A.err, l, si, pix, P, tau, se, dirs[pix], T, oP,
-                                                          otau);
+                        split = march_ray_table_df<kHash, kFreq>(V, rtab, A.geo[l], A.err, l, si, pix, P, tau, se,
+                                                                 dirs[pix], T, oP, otau);
                     } else if constexpr (kTable) {
-                        split = march_ray_table<float, kHash, false>(V, A.geo[l], A.err, l, si, pix, P, tau, cP, ctau, se, dirs[pix],
-                                                       T, oP, otau, ocP, octau);
+                        split = march_ray_table<float, kHash, kFreq>(V, A.geo[l], A.err, l, si, pix, P, tau, cP, ctau, se,
+                                                                     dirs[pix], T, oP, otau, ocP, octau);
                     } else {
-                        split = march_ray<R, kHash, false>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau, ocP,
-                                                    octau);
+                        split = march_ray<R, kHash, kFreq>(V, l, si, pix, P, tau, cP, ctau, se, dirs[pix], T, oP, otau,
+                                                           ocP, octau);
                     }
                 }
                 append_split<R>(split, si, pix, oP, otau, ocP, octau, A.buf[l + 1], &A.counts[sid], A.err);
@@ -1932,36 +1934,29 @@ void launch_geom_fill64(long long rq, int l, const int4* dirs, long long npix, i
     geom_fill64_kernel<<<(unsigned)grid, 256, 0, s>>>(rq, l, dirs, npix, n_cover, rs, row0, rows_total, ent, err);
 }
 
-template <class R, bool kSingle>
+template <class R, bool kSingle, bool kFreq>
 static const void* batch_kernel_pick(bool hash, bool table)
 {
-    if constexpr (sizeof(R) == 4) {
-        if (table)
-            return hash ? (const void*)batch_kernel<float, true, true, kSingle>
-                        : (const void*)batch_kernel<float, false, true, kSingle>;
-        return hash ? (const void*)batch_kernel<float, true, false, kSingle>
-                    : (const void*)batch_kernel<float, false, false, kSingle>;
-    } else {
-        if (table)
-            return hash ? (const void*)batch_kernel<double, true, true, kSingle>
-                        : (const void*)batch_kernel<double, false, true, kSingle>;
-        return hash ? (const void*)batch_kernel<double, true, false, kSingle>
-                    : (const void*)batch_kernel<double, false, false, kSingle>;
-    }
+    if (table)
+        return hash ? (const void*)batch_kernel<R, true, true, kSingle, kFreq>
+                    : (const void*)batch_kernel<R, false, true, kSingle, kFreq>;
+    return hash ? (const void*)batch_kernel<R, true, false, kSingle, kFreq>
+                : (const void*)batch_kernel<R, false, false, kSingle, kFreq>;
 }
 
 template <class R>
-static const void* batch_kernel_for(bool hash, bool table, bool single)
+static const void* batch_kernel_for(bool hash, bool table, bool single, bool freq)
 {
-    return single ? batch_kernel_pick<R, true>(hash, table) : batch_kernel_pick<R, false>(hash, table);
+    if (freq) return single ? batch_kernel_pick<R, true, true>(hash, table) : batch_kernel_pick<R, false, true>(hash, table);
+    return single ? batch_kernel_pick<R, true, false>(hash, table) : batch_kernel_pick<R, false, false>(hash, table);
 }
 
 template <class R>
 static cudaError_t launch_batch_impl(const BatchArgs<R>& a, int grid, int block, cudaStream_t s)
 {
     void* args[] = {const_cast<BatchArgs<R>*>(&a)};
-    return cudaLaunchCooperativeKernel(batch_kernel_for<R>(a.any_hash != 0, a.use_geo != 0, a.single != 0), dim3(grid),
-                                       dim3(block), args, 0, s);
+    return cudaLaunchCooperativeKernel(batch_kernel_for<R>(a.any_hash != 0, a.use_geo != 0, a.single != 0, a.freq != 0),
+                                       dim3(grid), dim3(block), args, 0, s);
 }
 
 cudaError_t launch_batch_f64(const BatchArgs<double>& a, int grid, int block, cudaStream_t s)
@@ -1975,14 +1970,14 @@ cudaError_t launch_batch_f32(const BatchArgs<float>& a, int grid, int block, cud
 }
 
 // Co-resident blocks per SM of the batch kernel variant (walking or table-driven, one solve or
-// many): the smaller of its two visit-hash instantiations, so that a cooperative launch sized by
-// it fits either.
-int batch_blocks_per_sm(int precision, int block, bool table, bool single)
+// many, gray or blackbody rate): the smaller of its two visit-hash instantiations, so that a
+// cooperative launch sized by it fits either.
+int batch_blocks_per_sm(int precision, int block, bool table, bool single, bool freq)
 {
     int best = 1 << 30;
     for (int hash = 0; hash < 2; ++hash) {
-        const void* k = precision == RT_FP32 ? batch_kernel_for<float>(hash, table, single)
-                                             : batch_kernel_for<double>(hash, table, single);
+        const void* k = precision == RT_FP32 ? batch_kernel_for<float>(hash, table, single, freq)
+                                             : batch_kernel_for<double>(hash, table, single, freq);
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0);
         best = std::min(best, nb);

@@ -139,6 +139,8 @@ struct BatchArgs {
     int single;                      // the launch holds one solve, given in `one`
     BatchSolve one;
     unsigned* err;
+    int freq;                        // every solve of the launch takes the blackbody rate of `spec`
+    SpecTable<R> spec;
 };
 
 // march.cu
@@ -146,7 +148,7 @@ int launch_march_f64(const MarchArgs<double>& a, int grid, int block, cudaStream
 int launch_march_f32(const MarchArgs<float>& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_batch_f64(const BatchArgs<double>& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_batch_f32(const BatchArgs<float>& a, int grid, int block, cudaStream_t s);
-int batch_blocks_per_sm(int precision, int block, bool table, bool single);
+int batch_blocks_per_sm(int precision, int block, bool table, bool single, bool freq);
 // The march of one level with its geometry from a table (FP32: g.ent; FP64: g.ent64).
 int launch_march_table_f32(const MarchArgs<float>& a, const GeomLevel& g, int grid, int block, cudaStream_t s);
 int launch_march_table_f64(const MarchArgs<double>& a, const GeomLevel& g, int grid, int block, cudaStream_t s);

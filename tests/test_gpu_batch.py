@@ -234,16 +234,19 @@ def test_batch_heavy_path_many_chunks(nyx, precision):
         s.close()
 
 
+@pytest.mark.parametrize("heavy_shift", [0, -1], ids=["light", "heavy"])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batch_blackbody_rate(nyx, precision):
-    """Eq. 1 integrated over a blackbody spectrum in the batched form (its heavy path): each solve
-    equal to rt_step (bookkeeping bit for bit, fields to the atomics' order) and, for one solve, to
-    the oracle's direct quadrature (FP64 1e-7; FP32 2e-5 of the FP64 oracle)."""
+def test_batch_blackbody_rate(nyx, precision, heavy_shift):
+    """Eq. 1 integrated over a blackbody spectrum in the batched form, through the persistent
+    kernel (light, the default before any run) and through the per-level launches (heavy): each
+    solve equal to rt_step (bookkeeping bit for bit, fields to the atomics' order) and, for one
+    solve, to the oracle's direct quadrature (FP64 1e-9; FP32 2e-6 of the FP64 oracle)."""
     ws = mixed_workloads(count=4, seed=23)
     kw = dict(spectrum=1, t_bb_K=1e5)
     solvers = [make_solver(nyx, w, precision, **kw) for w in ws]
     ref = [plain(nyx, s, w.n) for s, w in zip(solvers, ws)]
     b = nyx.Batch(solvers)
+    b.set_params(heavy_shift=heavy_shift)
     gs, hs, stats = run_batch(nyx, b, ws)
     tol = 1e-12 if precision == 0 else 1e-10
     for (gr, hr, sr), g, st in zip(ref, gs, stats):
@@ -256,7 +259,27 @@ def test_batch_blackbody_rate(nyx, precision):
     for k in BOOK:
         assert stats[0][k] == r["stats"][k], k
     r64 = r if precision == 0 else oracle.run_workload(w, n_th_cm3=n_th, precision=0, **kw)
-    assert relerr(gs[0].reshape(w.n, w.n, w.n), r64["gamma"]) < (1e-7 if precision == 0 else 2e-5)
+    assert relerr(gs[0].reshape(w.n, w.n, w.n), r64["gamma"]) < (1e-9 if precision == 0 else 2e-6)
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_mixes_rates(nyx, precision):
+    """Gray solves and blackbody solves at two temperatures in one batch: the persistent launches
+    hold one rate each, and every solve equals its own rt_step."""
+    ws = mixed_workloads(count=6, seed=29)
+    rates = [dict(), dict(spectrum=1, t_bb_K=1e5), dict(spectrum=1, t_bb_K=3e4)] * 2
+    solvers = [make_solver(nyx, w, precision, **kw) for w, kw in zip(ws, rates)]
+    ref = [plain(nyx, s, w.n) for s, w in zip(solvers, ws)]
+    b = nyx.Batch(solvers)
+    gs, hs, stats = run_batch(nyx, b, ws)
+    tol = 1e-12 if precision == 0 else 1e-10
+    for (gr, hr, sr), g, st in zip(ref, gs, stats):
+        for k in BOOK:
+            assert st[k] == sr[k], k
+        assert relerr(g, gr) < tol
     b.close()
     for s in solvers:
         s.close()

@@ -194,8 +194,9 @@ def test_pool_evicts_under_a_tight_budget(nyx):
 
 
 def test_blackbody_requests_are_served(nyx):
-    """Requests with Eq. 1 integrated over a blackbody spectrum go to the batch's heavy path:
-    each served result equals rt_step on the request alone and the oracle's bookkeeping."""
+    """Requests with Eq. 1 integrated over a blackbody spectrum are batched like gray ones (one rate
+    per persistent launch): each served result equals rt_step on the request alone and the oracle's
+    bookkeeping."""
     ws = requests(6, seed=61)
     srv = nyx.Server(precision=1, max_batch=8)
     kw = dict(spectrum=1, t_bb_K=1e5)
