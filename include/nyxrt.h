@@ -254,7 +254,8 @@ int64_t rt_geometry_table_bytes(int32_t device);
 /* Phi(tau) and the thin rate Psi(tau) = -dPhi/dtau of RT_SPECTRUM_BLACKBODY at
  * t_bb_K, from the library's own cubic pieces (the functions the FP64 march runs,
  * evaluated on the host; the FP32 march reads the same pieces rounded to float; for
- * checking). Returns RT_EINVAL for tau outside [0, 1e4] or t_bb_K <= 0. */
+ * checking). Returns RT_EINVAL for tau outside [0, 1e4] or t_bb_K <= 0, and
+ * RT_ENOMEM if host memory for the pieces ran out. */
 int rt_spectrum_eval(double t_bb_K, double tau, double* phi, double* psi);
 
 /* The fraction Phi(tau) - Phi(tau + dtau) of a ray's photons that a segment of
@@ -263,7 +264,8 @@ int rt_spectrum_eval(double t_bb_K, double tau, double* phi, double* psi);
  * piece within a piece, split at a node, node values across several pieces;
  * Eq. 1 over a blackbody spectrum, Sec. 2.5). *frac receives it. Returns
  * RT_EINVAL for tau outside [0, 1e4], dtau not in (0, 1e4], t_bb_K <= 0 or a
- * null pointer. For checking. */
+ * null pointer, and RT_ENOMEM if host memory for the pieces ran out. For
+ * checking. */
 int rt_spectrum_absorb(double t_bb_K, double tau, double dtau, double* frac);
 
 /* Text of the handle's last error ("" if none); for h == NULL, the last

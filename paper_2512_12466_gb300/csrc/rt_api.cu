@@ -21,6 +21,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -297,12 +298,19 @@ void spectrum_lin_build(double theta, SpecEntry& e)
         }
     };
     const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    // node q, q + nth, ... on thread q; a thread that cannot be started leaves its nodes to this one
     std::vector<std::thread> pool;
-    for (int q = 0; q < nth; ++q)
-        pool.emplace_back([&, q] {
-            for (int j = q; j <= J; j += nth) node(j);
-        });
+    int started = 0;
+    try {
+        for (; started < nth; ++started)
+            pool.emplace_back([&, started] {
+                for (int j = started; j <= J; j += nth) node(j);
+            });
+    } catch (const std::system_error&) {
+    }
     for (auto& t : pool) t.join();
+    for (int q = started; q < nth; ++q)
+        for (int j = q; j <= J; j += nth) node(j);
     e.lin_a.resize(J);
     e.lin_b.resize(J);
     for (int j = 0; j < J; ++j) {
@@ -319,9 +327,23 @@ void spectrum_lin_build(double theta, SpecEntry& e)
     e.psi_end = psi[J];
 }
 
+const SpecEntry* spectrum_entry_locked(int device, double t_bb, std::string& why);
+
+// The entry of (device, t_bb), built on first use; null (with `why`) if host or device memory ran
+// out. No exception leaves it.
 const SpecEntry* spectrum_entry(int device, double t_bb, std::string& why)
 {
     std::lock_guard<std::mutex> lk(g_spec_mu);
+    try {
+        return spectrum_entry_locked(device, t_bb, why);
+    } catch (const std::bad_alloc&) {
+        why = "host allocation of the spectrum table failed";
+        return nullptr;
+    }
+}
+
+const SpecEntry* spectrum_entry_locked(int device, double t_bb, std::string& why)
+{
     std::deque<SpecEntry>& list = g_spec[device];
     for (const SpecEntry& e : list)
         if (e.t_bb == t_bb) return &e;
@@ -374,10 +396,11 @@ const SpecEntry* spectrum_entry(int device, double t_bb, std::string& why)
 
 // Host evaluation of the pieces at t_bb (the host copy; entries are immutable once added): the same
 // functions the FP64 march runs.
-static void spec_eval_host(double t_bb, double tau, double* phi, double* psi)
+static bool spec_eval_host(double t_bb, double tau, double* phi, double* psi)
 {
     std::string why;
     const SpecEntry* e = spectrum_entry(-1, t_bb, why);
+    if (!e) return false;
     SpecTable<double> T;
     T.lin_a = e->lin_a.data();
     T.lin_b = e->lin_b.data();
@@ -388,13 +411,15 @@ static void spec_eval_host(double t_bb, double tau, double* phi, double* psi)
     T.psi_end = e->psi_end;
     *phi = nyx::lin_phi(T, tau);
     *psi = nyx::lin_psi(T, tau);
+    return true;
 }
 
 // One segment's absorbed fraction, as the FP64 march computes it (kap = 1, so ds = dtau).
-static void spec_absorb_host(double t_bb, double tau, double dtau, double* frac)
+static bool spec_absorb_host(double t_bb, double tau, double dtau, double* frac)
 {
     std::string why;
     const SpecEntry* e = spectrum_entry(-1, t_bb, why);
+    if (!e) return false;
     SpecTable<double> T;
     T.lin_a = e->lin_a.data();
     T.lin_b = e->lin_b.data();
@@ -405,6 +430,7 @@ static void spec_absorb_host(double t_bb, double tau, double dtau, double* frac)
     T.psi_end = e->psi_end;
     double per_kap;
     nyx::lin_absorb(T, tau, dtau, 1.0, dtau, *frac, per_kap);
+    return true;
 }
 
 int nyx::spectrum_table(int device, double t_bb, SpecTable<double>* d, SpecTable<float>* f, std::string& why)
@@ -1056,8 +1082,7 @@ int rt_add_sources(rt_handle* h, const int32_t* cell_ijk, const double* ndot, in
 int rt_spectrum_eval(double t_bb_K, double tau, double* phi, double* psi)
 {
     if (!phi || !psi || !(t_bb_K > 0) || !std::isfinite(t_bb_K) || !(tau >= 0) || !(tau <= kSpecTauHi)) return RT_EINVAL;
-    spec_eval_host(t_bb_K, tau, phi, psi);
-    return RT_OK;
+    return spec_eval_host(t_bb_K, tau, phi, psi) ? RT_OK : RT_ENOMEM;
 }
 
 int rt_spectrum_absorb(double t_bb_K, double tau, double dtau, double* frac)
@@ -1065,8 +1090,7 @@ int rt_spectrum_absorb(double t_bb_K, double tau, double dtau, double* frac)
     if (!frac || !(t_bb_K > 0) || !std::isfinite(t_bb_K) || !(tau >= 0) || !(tau <= kSpecTauHi) || !(dtau > 0) ||
         !(dtau <= kSpecTauHi))
         return RT_EINVAL;
-    spec_absorb_host(t_bb_K, tau, dtau, frac);
-    return RT_OK;
+    return spec_absorb_host(t_bb_K, tau, dtau, frac) ? RT_OK : RT_ENOMEM;
 }
 
 int64_t rt_geometry_table_bytes(int32_t device)
