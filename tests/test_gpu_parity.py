@@ -7,6 +7,7 @@ FP32 march (whose bookkeeping is compared bit-exactly with the oracle's FP32
 variant); the photon ledger closes to 1e-12 (FP64) / 1e-6 (FP32).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -635,8 +636,18 @@ def test_thin256_source_subset_parity(nyx):
     w.cells, w.ndot = w.cells[sub], w.ndot[sub]
     n_th = 0.01 * float(w.n_h.mean())
     ref64 = None
-    for prec in (0, 1):
-        ref, got = run_both(nyx, w, precision=prec, n_th_cm3=n_th)
+    # geometry tables live as long as the process: leave room for this box's above those that
+    # earlier tests built (the budget is read at every table build)
+    budget = os.environ.get("NYXRT_GEOMETRY_BUDGET_MB")
+    os.environ["NYXRT_GEOMETRY_BUDGET_MB"] = str((nyx.rt_geometry_table_bytes(0) >> 20) + 60000)
+    try:
+        runs = [run_both(nyx, w, precision=prec, n_th_cm3=n_th) for prec in (0, 1)]
+    finally:
+        if budget is None:
+            del os.environ["NYXRT_GEOMETRY_BUDGET_MB"]
+        else:
+            os.environ["NYXRT_GEOMETRY_BUDGET_MB"] = budget
+    for prec, (ref, got) in zip((0, 1), runs):
         st = got["stats"]
         assert_bookkeeping(st, ref["stats"])
         reached = [l for l, r in enumerate(st["rays"]) if r]
