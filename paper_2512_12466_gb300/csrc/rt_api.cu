@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -103,7 +104,8 @@ struct GeomTable {
     unsigned long long* row0; // row offset of each 32-pixel block (device)
     uint2* ent;               // FP32 entries, built on first use
     ulonglong2* ent64;        // FP64 entries, built on first use
-    bool failed32, failed64;  // that build was tried and did not fit (or failed)
+    size_t failed32, failed64;  // budget when that build was tried and did not fit or failed (0: never);
+                                // tried again once the budget is larger (the row offsets: never)
 };
 std::mutex g_geom_mu;
 std::map<int, std::vector<GeomTable>> g_geom;   // never shrinks; entries are updated in place
@@ -141,7 +143,7 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, long long r
     const long long nb = (npix + 31) / 32;
     if (!t) {
         // the rows of every 32-pixel block: counted once, shared by both precisions' entries
-        GeomTable c{rq, rs, level, n, false, 0ull, nullptr, nullptr, nullptr, false, false};
+        GeomTable c{rq, rs, level, n, false, 0ull, nullptr, nullptr, nullptr, 0, 0};
         // every ray reaches R_l inside the virtual grid of 2n - 1 cells when R_l + 1 < n; with periodic
         // boundaries the table runs to the travel-distance cutoff, fixed by rs alone
         c.complete = rs != 0 || std::ldexp((double)rq, level - kRadBits) + 2.0 < (double)n;
@@ -171,20 +173,21 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, long long r
         } else {
             cudaFree(c.row0);
             c.row0 = nullptr;
-            c.failed32 = c.failed64 = true;
+            c.failed32 = c.failed64 = SIZE_MAX;
         }
         list.push_back(c);
         t = &list.back();
     }
-    bool& failed = fp64 ? t->failed64 : t->failed32;
+    size_t& failed = fp64 ? t->failed64 : t->failed32;
     const bool have = fp64 ? t->ent64 != nullptr : t->ent != nullptr;
-    if (!have && !failed) {
+    const size_t budget = geometry_budget(device);
+    if (!have && (failed == 0 || (failed != SIZE_MAX && budget > failed))) {
         const size_t esz = fp64 ? sizeof(ulonglong2) : sizeof(uint2);
         const size_t bytes = (size_t)t->total * 32 * esz;
         void* ent = nullptr;
         unsigned* d_err = nullptr;
         unsigned herr = 0;
-        bool ok = g_geom_bytes[device] + bytes <= geometry_budget(device) &&
+        bool ok = g_geom_bytes[device] + bytes <= budget &&
                   cudaMalloc(&ent, std::max<size_t>(16, bytes)) == cudaSuccess &&
                   cudaMalloc(&d_err, sizeof(unsigned)) == cudaSuccess &&
                   cudaMemsetAsync(d_err, 0, sizeof(unsigned), s) == cudaSuccess;
@@ -205,7 +208,7 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, long long r
             g_geom_bytes[device] += bytes;
         } else {
             cudaFree(ent);
-            failed = true;
+            failed = std::max<size_t>(budget, 1);
         }
     }
     if (fp64 ? t->ent64 == nullptr : t->ent == nullptr) return false;
