@@ -104,8 +104,8 @@ struct GeomTable {
     unsigned long long* row0; // row offset of each 32-pixel block (device)
     uint2* ent;               // FP32 entries, built on first use
     ulonglong2* ent64;        // FP64 entries, built on first use
-    size_t failed32, failed64;  // budget when that build was tried and did not fit or failed (0: never);
-                                // tried again once the budget is larger (the row offsets: never)
+    size_t failed_rows, failed32, failed64;  // budget when that build was tried and did not fit or
+                                             // failed (0: never); tried again once the budget is larger
 };
 std::mutex g_geom_mu;
 std::map<int, std::vector<GeomTable>> g_geom;   // never shrinks; entries are updated in place
@@ -141,47 +141,53 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, long long r
         }
     const long long npix = 12LL << (2 * level);
     const long long nb = (npix + 31) / 32;
+    const size_t budget = geometry_budget(device);
     if (!t) {
-        // the rows of every 32-pixel block: counted once, shared by both precisions' entries
-        GeomTable c{rq, rs, level, n, false, 0ull, nullptr, nullptr, nullptr, 0, 0};
+        GeomTable c{rq, rs, level, n, false, 0ull, nullptr, nullptr, nullptr, 0, 0, 0};
         // every ray reaches R_l inside the virtual grid of 2n - 1 cells when R_l + 1 < n; with periodic
         // boundaries the table runs to the travel-distance cutoff, fixed by rs alone
         c.complete = rs != 0 || std::ldexp((double)rq, level - kRadBits) + 2.0 < (double)n;
+        list.push_back(c);
+        t = &list.back();
+    }
+    if (!t->row0 && (t->failed_rows == 0 || budget > t->failed_rows)) {
+        // the rows of every 32-pixel block: counted once, shared by both precisions' entries
         unsigned* d_rows = nullptr;
         std::vector<unsigned> rows((size_t)nb);
         std::vector<unsigned long long> off((size_t)nb);
         const size_t row0_bytes = sizeof(unsigned long long) * (size_t)nb;
-        bool ok = g_geom_bytes[device] + row0_bytes <= geometry_budget(device) &&
+        unsigned long long total = 0;
+        bool ok = g_geom_bytes[device] + row0_bytes <= budget &&
                   cudaMalloc(&d_rows, sizeof(unsigned) * (size_t)nb) == cudaSuccess;
         if (ok) {
-            launch_geom_count(rq, level, dirs_level, npix, n, rs, d_rows, s);
+            launch_geom_count(rq, level, dirs_level, npix, t->n_cover, rs, d_rows, s);
             ok = cudaMemcpyAsync(rows.data(), d_rows, sizeof(unsigned) * (size_t)nb, cudaMemcpyDeviceToHost, s) ==
                      cudaSuccess &&
                  cudaStreamSynchronize(s) == cudaSuccess;
         }
         for (long long b = 0; ok && b < nb; ++b) {
-            off[(size_t)b] = c.total;
-            c.total += rows[(size_t)b];
+            off[(size_t)b] = total;
+            total += rows[(size_t)b];
         }
-        ok = ok && cudaMalloc(&c.row0, row0_bytes) == cudaSuccess &&
-             cudaMemcpyAsync(c.row0, off.data(), row0_bytes, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+        unsigned long long* row0 = nullptr;
+        ok = ok && cudaMalloc(&row0, row0_bytes) == cudaSuccess &&
+             cudaMemcpyAsync(row0, off.data(), row0_bytes, cudaMemcpyHostToDevice, s) == cudaSuccess &&
              cudaStreamSynchronize(s) == cudaSuccess;
         cudaGetLastError();
         cudaFree(d_rows);
         if (ok) {
+            t->row0 = row0;
+            t->total = total;
             g_geom_bytes[device] += row0_bytes;
         } else {
-            cudaFree(c.row0);
-            c.row0 = nullptr;
-            c.failed32 = c.failed64 = SIZE_MAX;
+            cudaFree(row0);
+            t->failed_rows = std::max<size_t>(budget, 1);
         }
-        list.push_back(c);
-        t = &list.back();
     }
+    if (!t->row0) return false;
     size_t& failed = fp64 ? t->failed64 : t->failed32;
     const bool have = fp64 ? t->ent64 != nullptr : t->ent != nullptr;
-    const size_t budget = geometry_budget(device);
-    if (!have && (failed == 0 || (failed != SIZE_MAX && budget > failed))) {
+    if (!have && (failed == 0 || budget > failed)) {
         const size_t esz = fp64 ? sizeof(ulonglong2) : sizeof(uint2);
         const size_t bytes = (size_t)t->total * 32 * esz;
         void* ent = nullptr;
