@@ -90,7 +90,7 @@ namespace {
 
 // Geometry tables (FP32 march): one per (device, split radius, level, grid size covered). A
 // table is never freed while the process runs (handles on other streams may be reading it);
-// a larger grid gets a new one. Their total per device stays within a budget, by default a
+// a larger grid, or one more than a quarter smaller, gets a new one. Their total per device stays within a budget, by default a
 // quarter of the device's memory (NYXRT_GEOMETRY_BUDGET_MB overrides it): on a GB300 that holds
 // every level of a 256^3 box in both precisions (46 GB) beside those of a 128^3 box. A level that
 // does not fit is marched by walking its rays instead.
@@ -110,6 +110,17 @@ struct GeomTable {
 std::mutex g_geom_mu;
 std::map<int, std::vector<GeomTable>> g_geom;   // never shrinks; entries are updated in place
 std::map<int, size_t> g_geom_bytes;
+
+// With NYXRT_GEOMETRY_TRACE set, every table build writes one line to stderr: what was built, its
+// size, the budget and the outcome.
+void geometry_trace(const char* what, int level, int n_cover, size_t bytes, size_t used, size_t budget, const char* outcome)
+{
+    static const bool on = std::getenv("NYXRT_GEOMETRY_TRACE") != nullptr;
+    if (!on) return;
+    std::fprintf(stderr, "nyxrt-geometry %s level %d n_cover %d bytes %zu used %zu budget %zu: %s\n", what, level, n_cover,
+                 bytes, used, budget, outcome);
+    std::fflush(stderr);
+}
 
 size_t geometry_budget(int device)
 {
@@ -133,12 +144,15 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, long long r
 {
     std::lock_guard<std::mutex> lk(g_geom_mu);
     std::vector<GeomTable>& list = g_geom[device];
+    // the smallest table that covers grids of n cells: a complete one, or one built for n to n + n/4
+    // (a table for a much larger grid holds rows this grid never reads, up to 4x the bytes at 1024^3
+    // against 256^3, so a grid that small gets its own)
     GeomTable* t = nullptr;
     for (GeomTable& c : list)
-        if (c.rq == rq && c.rs == rs && c.level == level && (c.complete || c.n_cover >= n)) {
+        if (c.rq == rq && c.rs == rs && c.level == level &&
+            (c.complete || (c.n_cover >= n && c.n_cover <= n + n / 4)) &&
+            (!t || (!c.complete && (t->complete || c.n_cover < t->n_cover))))
             t = &c;
-            break;
-        }
     const long long npix = 12LL << (2 * level);
     const long long nb = (npix + 31) / 32;
     const size_t budget = geometry_budget(device);
@@ -175,6 +189,7 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, long long r
              cudaStreamSynchronize(s) == cudaSuccess;
         cudaGetLastError();
         cudaFree(d_rows);
+        geometry_trace("rows", level, t->n_cover, row0_bytes, g_geom_bytes[device], budget, ok ? "built" : "failed");
         if (ok) {
             t->row0 = row0;
             t->total = total;
@@ -193,10 +208,11 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, long long r
         void* ent = nullptr;
         unsigned* d_err = nullptr;
         unsigned herr = 0;
-        bool ok = g_geom_bytes[device] + bytes <= budget &&
-                  cudaMalloc(&ent, std::max<size_t>(16, bytes)) == cudaSuccess &&
+        const bool fits = g_geom_bytes[device] + bytes <= budget;
+        bool ok = fits && cudaMalloc(&ent, std::max<size_t>(16, bytes)) == cudaSuccess &&
                   cudaMalloc(&d_err, sizeof(unsigned)) == cudaSuccess &&
                   cudaMemsetAsync(d_err, 0, sizeof(unsigned), s) == cudaSuccess;
+        const bool allocated = ok;
         if (ok) {
             if (fp64)
                 launch_geom_fill64(rq, level, dirs_level, npix, t->n_cover, rs, t->row0, t->total,
@@ -208,6 +224,8 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, long long r
         }
         cudaGetLastError();
         cudaFree(d_err);
+        geometry_trace(fp64 ? "fp64 entries" : "fp32 entries", level, t->n_cover, bytes, g_geom_bytes[device], budget,
+                       ok ? "built" : (!fits ? "over budget" : (!allocated ? "allocation failed" : "fill error")));
         if (ok) {
             if (fp64) t->ent64 = static_cast<ulonglong2*>(ent);
             else t->ent = static_cast<uint2*>(ent);
