@@ -144,14 +144,13 @@ bool nyx::geometry_level(int device, long long rq, int level, int n, long long r
 {
     std::lock_guard<std::mutex> lk(g_geom_mu);
     std::vector<GeomTable>& list = g_geom[device];
-    // the smallest table that covers grids of n cells: a complete one, or one built for n to n + n/4
-    // (a table for a much larger grid holds rows this grid never reads, up to 4x the bytes at 1024^3
-    // against 256^3, so a grid that small gets its own)
+    // the smallest table that covers grids of n cells and was built for at most n + n/4: one built for
+    // a much larger grid, complete or not, holds rows this grid never reads (level 10 at 1024^3 is
+    // 38 GB in FP32, against 10 GB at 256^3), so a grid that small gets its own
     GeomTable* t = nullptr;
     for (GeomTable& c : list)
-        if (c.rq == rq && c.rs == rs && c.level == level &&
-            (c.complete || (c.n_cover >= n && c.n_cover <= n + n / 4)) &&
-            (!t || (!c.complete && (t->complete || c.n_cover < t->n_cover))))
+        if (c.rq == rq && c.rs == rs && c.level == level && (c.complete || c.n_cover >= n) &&
+            c.n_cover <= n + n / 4 && (!t || c.n_cover < t->n_cover))
             t = &c;
     const long long npix = 12LL << (2 * level);
     const long long nb = (npix + 31) / 32;
