@@ -1004,6 +1004,14 @@ struct TableEntry<double> {
     {
         return __longlong_as_double((long long)((e.y & ((1ull << 53) - 1ull)) + kDBase));
     }
+    // the same f as a double-float, straight from the code: f = (1 + m 2^-52) / 2 with m = code - 1
+    // (m = 2^52 is f = 1); head its leading 24 bits, tail the other 29 rounded to 24, as df_of(f)
+    __device__ __forceinline__ static dflt f_df(const E& e)
+    {
+        const unsigned long long m = (e.y & ((1ull << 53) - 1ull)) - 1ull;
+        return {__uint_as_float(0x3f000000u + (unsigned)(m >> 29)),
+                __fmul_rn(__uint2float_rn((unsigned)m & 0x1fffffffu), __uint_as_float(74u << 23))};   // 2^-53
+    }
 };
 
 // march_ray with the geometry read from the level's table (FP32 or FP64 physics).
@@ -1201,7 +1209,7 @@ __device__ __forceinline__ dflt rate_factor(const float* __restrict__ tab, const
     const float4 B = *reinterpret_cast<const float4*>(tab + 4 * (kRateIntervals + j));       // c2 c2' c3 c4
     // r = x - y0: the head difference is exact (Sterbenz, x / y0 in [2/3, 4/3] for j >= 1; y0 = 0
     // for j = 0); with x's tail it is renormalised, so that the cross terms below stay small
-    const float y0 = j ? __fmul_rn(__fadd_rn(__int2float_rn(j), 0.5f), 0.00390625f) : 0.f;
+    const float y0 = j ? __fmaf_rn(__int2float_rn(j), 0.00390625f, 0.001953125f) : 0.f;   // exact: (j + 1/2) 2^-8
     const dflt r = df_two_sum(__fsub_rn(x.h, y0), x.l);
     const float rh = r.h, rl = r.l;
     const float t = __fmaf_rn(B.w, rh, B.z);
@@ -1416,6 +1424,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
         // ---- Eq. 1: w = Q g ds, the segment's rate before the Eq. 5-8 share (double-float),
         // or its FP64 value wd for an opaque segment
         dflt w = {0.f, 0.f};
+        dflt ux = {0.f, 0.f};             // gray: the photons the segment absorbs, Q g dtau = kap w
         double wd = 0.0;
         const bool opaque = !kFreq && I::pos(kap) && !I::lt(dtau, 2.0);
         const double tau1 = I::add(tau, dtau);
@@ -1447,7 +1456,8 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
             if (I::pos(kap)) {
                 const dflt x = df_of(dtau);
                 const dflt u = df_mul(Q, rate_factor(rtab, x));
-                Q = df_sub(Q, df_mul(u, x));
+                ux = df_mul(u, x);
+                Q = df_sub(Q, ux);
                 w = df_mul(u, dsf);
             } else {
                 w = df_mul(Q, dsf);                       // optically thin limit
@@ -1475,30 +1485,47 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
                 keep_all = !elig && mode != RT_OVERLAP_NAIVE;   // naive threshold: the Eq. 5 share regardless
             }
         }
-        if (keep_all) {
-            dep = opaque ? scale2(wd, e_dep) : df_to_double_pos(w, e_seg);
-        } else {
-            const double fd = TE::f(e);
-            if (opaque) {
+        if (opaque) {
+            if (keep_all) {
+                dep = scale2(wd, e_dep);
+            } else {
+                const double fd = TE::f(e);
                 dep = scale2(fd * (squared ? fd * wd : wd), e_dep);
                 if (second) dep2 = scale2(((1.0 - fd) * wd) * (kap / I::mag(kn_raw)), e_dep);
-            } else {
-                const dflt f = df_of(fd);
-                const dflt fw = df_mul(f, w);
-                dep = df_to_double_pos(squared ? df_mul(f, fw) : fw, e_seg);
-                if (second && I::pos(kap)) {       // kap = 0 (an ionized cell) sends 0 to c'
+            }
+        } else {
+            // one path for every lane: f = 1 where the whole rate stays (1 w is w exactly)
+            const dflt f = keep_all ? dflt{1.f, 0.f} : TE::f_df(e);
+            const dflt fw = df_mul(f, w);
+            dep = df_to_double_pos(squared ? df_mul(f, fw) : fw, e_seg);
+            if (second && I::pos(kap)) {           // kap = 0 (an ionized cell) sends 0 to c'
+                // 1 - f, renormalised: the head difference is exact and at least f's tail, so a
+                // share near f = 1 keeps its relative precision through the products below
+                const dflt om = df_fast_two_sum(__fsub_rn(1.0f, f.h), -f.l);
+                int en;
+                const dflt mn = df_mant(I::mag(kn_raw), en);
+                // ux carries dtau's full double-float only from 2^-74 on (df_of keeps the head alone
+                // below), so thinner segments and the blackbody rate take the ratio kap / kap'
+                if (kFreq || I::lt(dtau, 0x1p-74)) {
                     // Eq. 8: (1 - f) w kap / kap', the ratio of the mantissas by a float reciprocal
                     // and one correction, the exponents applied when rounding to double
-                    int ek, en;
-                    const dflt mk = df_mant(kap, ek), mn = df_mant(I::mag(kn_raw), en);
+                    int ek;
+                    const dflt mk = df_mant(kap, ek);
                     const float r0 = __frcp_rn(mn.h);
                     const float q0 = __fmul_rn(mk.h, r0);
                     const float p = __fmul_rn(mn.h, q0);
                     const float pe = __fmaf_rn(mn.h, q0, -p);
                     const float rho = __fmaf_rn(-q0, mn.l, __fadd_rn(__fsub_rn(__fsub_rn(mk.h, p), pe), mk.l));
                     const dflt ratio = {q0, __fmul_rn(rho, r0)};
-                    const dflt om = {__fsub_rn(1.0f, f.h), -f.l};
                     dep2 = df_to_double_pos(df_mul(df_mul(om, w), ratio), e_seg + ek - en);
+                } else {
+                    // Eq. 8 from the absorbed photons: w kap = Q g dtau = ux, so the share is
+                    // (1 - f) ux / kap', by the reciprocal of kap''s mantissa with one correction
+                    // and its exponent applied when rounding to double
+                    dflt inv;
+                    inv.h = __frcp_rn(mn.h);
+                    inv.l = __fmul_rn(__fmaf_rn(-mn.l, inv.h, __fmaf_rn(-mn.h, inv.h, 1.0f)), inv.h);
+                    dep2 = df_to_double_pos(df_mul(df_mul(om, ux), inv), e_seg - en);
                 }
             }
         }

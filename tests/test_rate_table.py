@@ -4,7 +4,9 @@ one its generator derives, and the evaluation, replayed here operation by operat
 IEEE single precision (fused multiply-adds rounded once), must stay within 1e-14 of g
 relative, checked against 40-digit arithmetic (the tail additions of a double-float sum
 round at about 2^-48 of the value each), so that the march's deposits keep their 1e-12
-agreement with the FP64 oracle with room to spare."""
+agreement with the FP64 oracle with room to spare. The Eqs. 5-8 shares of each segment's
+rate (f from the geometry table's code, Eq. 8's (1 - f) w kap / kap') are replayed the
+same way against exact rationals."""
 import math
 import os
 import re
@@ -83,7 +85,7 @@ def rate_factor(rows, y: float):
     xh, xl = df_of(y)
     j = min(int(mul(xh, 256.0)), 511)
     c0h, c0l, c1h, c1l, c2h, c2l, c3, c4 = rows[j]
-    y0 = mul(add(float(j), 0.5), 0.00390625) if j else 0.0
+    y0 = fma(float(j), 0.00390625, 0.001953125) if j else 0.0
     rh, rl = two_sum(add(xh, -y0), xl)
     t = fma(c4, rh, c3)
     uh, ul = fast_two_sum(c2h, fma(rh, t, fma(rl, t, c2l)))
@@ -137,3 +139,86 @@ def test_closed_forms():
     assert abs(float(rate_factor(rows, 1.0)) - float(1 - mp.exp(-1))) < 5e-15
     y = 1e-6
     assert abs(float(rate_factor(rows, y)) - (1 - y / 2 + y * y / 6)) < 5e-16
+
+
+# ---- the Eqs. 5-8 shares of a segment's rate, as the FP64 table march evaluates them
+
+def df_mul(a, b):
+    p = mul(a[0], b[0])
+    e = fma(a[0], b[1], fma(a[0], b[0], -p))
+    return p, fma(a[1], b[0], e)
+
+
+def df_mant(x: float):
+    """A positive double as a double-float mantissa in [1, 2) and its exponent, as the kernel splits it."""
+    ex = math.frexp(x)[1] - 1
+    h, l = df_of(math.ldexp(x, -ex))
+    return (h, l), ex
+
+
+def f_of_code(code: int):
+    """The kernel's double-float f from a table entry's 53-bit code (bits of f less those of 1/2, plus 1)."""
+    m = code - 1
+    h = struct.unpack("<f", struct.pack("<I", 0x3F000000 + (m >> 29)))[0]
+    return h, mul(float(m & 0x1FFFFFFF), 2.0 ** -53)
+
+
+def frcp(x):
+    return round32(1 / Fraction(x))
+
+
+def val(a):
+    return Fraction(a[0]) + Fraction(a[1])
+
+
+def test_share_f_from_the_table_code():
+    # the entry stores f in [1/2, 1] as its bit pattern less that of 1/2, plus 1; the kernel reads
+    # it back as a double-float directly, which must be the head/tail split of that double
+    base = struct.unpack("<q", struct.pack("<d", 0.5))[0] - 1
+    rng = np.random.default_rng(31)
+    fs = [0.5, 1.0, np.nextafter(1.0, 0.0), np.nextafter(0.5, 1.0)] + list(rng.uniform(0.5, 1.0, 300))
+    for f in fs:
+        code = struct.unpack("<q", struct.pack("<d", float(f)))[0] - base
+        assert f_of_code(code) == df_of(float(f)), f
+
+
+def test_secondary_share_double_float():
+    """Eq. 8's share (1 - f) w kap / kap' of a segment whose rate is w = u ds (u = Q g, the
+    budget times the Eq. 1 factor), in the kernel's two forms: from the absorbed photons u dtau
+    over kap' (gray rate) and from the ratio of the mantissas of kap and kap' (the blackbody rate
+    and segments thinner than 2^-74). Against exact rationals, over f up to just below 1, where
+    1 - f must be renormalised to keep its precision, and kap' from 1e-3 to 1e3 of kap."""
+    rng = np.random.default_rng(77)
+    worst = {"ux": 0.0, "ratio": 0.0}
+    for _ in range(1500):
+        u = (round32(Fraction(float(rng.uniform(1, 2) * 2.0 ** 60))), round32(Fraction(float(rng.uniform(-1, 1) * 2.0 ** 36))))
+        kap = float(rng.uniform(1e-3, 3) * 10 ** rng.uniform(-8, 0))
+        kn = float(kap * 10 ** rng.uniform(-3, 3))
+        ds = float(rng.uniform(0.01, 1.7))
+        dtau = kap * ds                          # IEEE FP64, as the kernel's deciding product
+        f = float(1 - 10 ** rng.uniform(-15, -0.31))
+        fd = df_of(f)
+        om = fast_two_sum(add(1.0, -fd[0]), -fd[1])
+        mn, en = df_mant(kn)
+        exact = (1 - val(fd)) * val(u) * Fraction(dtau) / Fraction(kn)
+        if exact == 0:
+            continue
+        # gray: (1 - f) ux / kap', ux = u dtau
+        ux = df_mul(u, df_of(dtau))
+        ih = frcp(mn[0])
+        il = mul(fma(-mn[1], ih, fma(-mn[0], ih, 1.0)), ih)
+        got = val(df_mul(df_mul(om, ux), (ih, il))) / Fraction(2) ** en
+        worst["ux"] = max(worst["ux"], abs(float((got - exact) / exact)))
+        # ratio form: (1 - f) w (m_kap / m_kap') 2^(e_kap - e_kap')
+        w = df_mul(u, df_of(ds))
+        mk, ek = df_mant(kap)
+        r0 = frcp(mn[0])
+        q0 = mul(mk[0], r0)
+        p = mul(mn[0], q0)
+        pe = fma(mn[0], q0, -p)
+        rho = fma(-q0, mn[1], add(add(add(mk[0], -p), -pe), mk[1]))
+        got = val(df_mul(df_mul(om, w), (q0, mul(rho, r0)))) * Fraction(2) ** (ek - en)
+        exact_w = (1 - val(fd)) * val(u) * Fraction(ds) * Fraction(kap) / Fraction(kn)
+        worst["ratio"] = max(worst["ratio"], abs(float((got - exact_w) / exact_w)))
+    # double-float products round at about 2^-45 each; the deposit is then rounded to double
+    assert worst["ux"] < 2e-13 and worst["ratio"] < 2e-13, worst
