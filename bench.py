@@ -42,16 +42,18 @@ NOMINAL_HBM = 7900.0          # GB300 HBM3e nominal, for the second fraction bes
 L2_FLUSH_BYTES = 512 << 20
 
 
-# DRAM traffic of the FP32 march from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over
-# every march launch of one step of the same box with its first 64 sources, taken with
-# `python -m paper_2512_12466_gb300.profile_case --sources 64 --steps 1 --levels`), scaled to the full
-# workload by primary segments. Valid only for the kernel sources it was taken on.
-TRAFFIC_CAPTURE = {"kernel": "march_table_kernel", "bytes_per_segment": 8.781914413031373,
-                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "f377f4a644a2787a",
-                               "paper_2512_12466_gb300/csrc/rt_internal.h": "669971fcb157da7e"}}
+# DRAM traffic of the march from one ncu capture per precision (dram__bytes_read.sum +
+# dram__bytes_write.sum over every march launch of one step of the same box with its first 64
+# sources, taken with `python -m paper_2512_12466_gb300.profile_case --sources 64 --steps 1 --levels
+# [--precision fp64]`), scaled to the full workload by primary segments. Valid only for the kernel
+# sources it was taken on.
+TRAFFIC_CAPTURE = {"kernel": "march_table_kernel",
+                   "bytes_per_segment": {"fp32": 8.789734586064215, "fp64": 19.166941837002017},
+                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "785d932cedef44d9",
+                               "paper_2512_12466_gb300/csrc/rt_internal.h": "7b899d1021ce1758"}}
 
 
-def traffic_per_launch(segments_per_step: float, launches_per_step: float):
+def traffic_per_launch(segments_per_step: float, launches_per_step: float, precision: str = "fp32"):
     """Scaled DRAM bytes of the average march launch, or None once the kernel changed since the capture."""
     import hashlib
     for rel, h in TRAFFIC_CAPTURE["sources"].items():
@@ -60,7 +62,7 @@ def traffic_per_launch(segments_per_step: float, launches_per_step: float):
                 return None
         except OSError:
             return None
-    return TRAFFIC_CAPTURE["bytes_per_segment"] * segments_per_step / max(1.0, launches_per_step)
+    return TRAFFIC_CAPTURE["bytes_per_segment"][precision] * segments_per_step / max(1.0, launches_per_step)
 
 
 def atomic_peak():
@@ -775,6 +777,10 @@ def run_nyx(args, world, rank, local):
                      "algorithmic_bytes_per_launch": f32["achieved_gbs"] * 1e6 * f32["march_ms_per_step"]
                      / max(1, f32["march_launches_per_step"]),
                      "kernel": "march_table_kernel (FP32, geometry tables)", "peak_kind": peak_kind,
+                     # what the counters show binds this kernel: the algorithmic bytes above divide by
+                     # the HBM peak by convention, but kappa and Gamma of this box stay in L2
+                     "limiter": "L1/L2 throughput and load latency (ncu, one level-7 launch: L1 77%, L2 76% "
+                                "of peak, DRAM 6%); kappa and Gamma (25 MB) L2-resident on this box",
                      "march_ms_per_step": f32["march_ms_per_step"],
                      "march_launches_per_step": f32["march_launches_per_step"],
                      # the march's FP64 deposits (one per primary segment and per secondary deposit)
@@ -790,8 +796,13 @@ def run_nyx(args, world, rank, local):
         "fp64": {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "steps": f64["steps"],
                  "roofline": {"achieved": f64["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                               "frac": f64["achieved_gbs"] / hbm, "frac_nominal": f64["achieved_gbs"] / NOMINAL_HBM,
+                              "traffic": traffic_per_launch(f64["segments_per_step"], f64["march_launches_per_step"],
+                                                            "fp64"),
+                              "algorithmic_bytes_per_launch": f64["achieved_gbs"] * 1e6 * f64["march_ms_per_step"]
+                              / max(1, f64["march_launches_per_step"]),
                               "kernel": "march_table_kernel<double> (FP64, geometry tables, double-float)",
-                              "bound": "instruction issue of the double-float arithmetic (issue 70% active, 319 thread instructions per segment, FP64 pipe 30% in ncu)"}},
+                              "bound": "instruction issue of the double-float arithmetic (ncu, one level-7 launch: "
+                                       "issue 70% active, about 320 thread instructions per segment, FP64 pipe 30%)"}},
         "e2e": {"value": e2e_val, "unit": "segments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "clocks": f32["clocks"],

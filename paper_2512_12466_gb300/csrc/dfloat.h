@@ -55,12 +55,24 @@ __device__ __forceinline__ dflt df_scale(const dflt a, const int n)
     return {__fmul_rn(a.h, m), __fmul_rn(a.l, m)};
 }
 
-// a - b for a >= b >= 0: heads by Knuth's two-sum, tails added to its error, renormalised
-__device__ __forceinline__ dflt df_sub(const dflt a, const dflt b)
+// a - b where 0 <= b <= 7/8 a (a budget less a segment's share of it): the heads by Dekker's fast
+// two-sum, exact since |b.h| < |a.h|, the tails added to its error, renormalised
+__device__ __forceinline__ dflt df_sub_part(const dflt a, const dflt b)
 {
-    const dflt s = df_two_sum(a.h, -b.h);
+    const dflt s = df_fast_two_sum(a.h, -b.h);
     const float t = __fadd_rn(s.l, __fsub_rn(a.l, b.l));
     return df_fast_two_sum(s.h, t);
+}
+
+// 1 / x for x in [1, 2) as a double-float: the hardware's approximate reciprocal, one Newton step
+// r + r (1 - x r) for the head, and the residual (1 - x r) r for the tail (relative error below
+// about 2^-45)
+__device__ __forceinline__ dflt df_rcp12(const dflt x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x.h));
+    r = __fmaf_rn(r, __fmaf_rn(-x.h, r, 1.0f), r);
+    return {r, __fmul_rn(__fmaf_rn(-x.l, r, __fmaf_rn(-x.h, r, 1.0f)), r)};
 }
 
 // A positive normal double as a double-float mantissa in [1, 2) and its unbiased exponent:

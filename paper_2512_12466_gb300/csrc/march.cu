@@ -1457,7 +1457,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
                 const dflt x = df_of(dtau);
                 const dflt u = df_mul(Q, rate_factor(rtab, x));
                 ux = df_mul(u, x);
-                Q = df_sub(Q, ux);
+                Q = df_sub_part(Q, ux);           // ux = Q (1 - e^-dtau) < 7/8 Q below dtau = 2
                 w = df_mul(u, dsf);
             } else {
                 w = df_mul(Q, dsf);                       // optically thin limit
@@ -1520,12 +1520,9 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
                     dep2 = df_to_double_pos(df_mul(df_mul(om, w), ratio), e_seg + ek - en);
                 } else {
                     // Eq. 8 from the absorbed photons: w kap = Q g dtau = ux, so the share is
-                    // (1 - f) ux / kap', by the reciprocal of kap''s mantissa with one correction
-                    // and its exponent applied when rounding to double
-                    dflt inv;
-                    inv.h = __frcp_rn(mn.h);
-                    inv.l = __fmul_rn(__fmaf_rn(-mn.l, inv.h, __fmaf_rn(-mn.h, inv.h, 1.0f)), inv.h);
-                    dep2 = df_to_double_pos(df_mul(df_mul(om, ux), inv), e_seg - en);
+                    // (1 - f) ux / kap', by the double-float reciprocal of kap''s mantissa, its
+                    // exponent applied when rounding to double
+                    dep2 = df_to_double_pos(df_mul(df_mul(om, ux), df_rcp12(mn)), e_seg - en);
                 }
             }
         }

@@ -205,9 +205,12 @@ def test_secondary_share_double_float():
             continue
         # gray: (1 - f) ux / kap', ux = u dtau
         ux = df_mul(u, df_of(dtau))
-        ih = frcp(mn[0])
-        il = mul(fma(-mn[1], ih, fma(-mn[0], ih, 1.0)), ih)
-        got = val(df_mul(df_mul(om, ux), (ih, il))) / Fraction(2) ** en
+        # the hardware's approximate reciprocal, taken anywhere within 2^-22 of 1 / x, then one
+        # Newton step and the residual as the tail
+        r = round32(Fraction(1) / Fraction(mn[0]) * (1 + Fraction(float(rng.uniform(-1, 1))) / 2 ** 22))
+        r = fma(r, fma(-mn[0], r, 1.0), r)
+        inv = (r, mul(fma(-mn[1], r, fma(-mn[0], r, 1.0)), r))
+        got = val(df_mul(df_mul(om, ux), inv)) / Fraction(2) ** en
         worst["ux"] = max(worst["ux"], abs(float((got - exact) / exact)))
         # ratio form: (1 - f) w (m_kap / m_kap') 2^(e_kap - e_kap')
         w = df_mul(u, df_of(ds))
