@@ -802,7 +802,8 @@ def run_nyx(args, world, rank, local):
                               / max(1, f64["march_launches_per_step"]),
                               "kernel": "march_table_kernel<double> (FP64, geometry tables, double-float)",
                               "bound": "instruction issue of the double-float arithmetic (ncu, one level-7 launch: "
-                                       "issue 70% active, about 320 thread instructions per segment, FP64 pipe 30%)"}},
+                                       "issue 68% active, 322 thread instructions per segment at 25.3 of 32 lanes, "
+                                       "FP64 pipe 31%, DRAM 9%)"}},
         "e2e": {"value": e2e_val, "unit": "segments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "clocks": f32["clocks"],
