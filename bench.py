@@ -48,9 +48,10 @@ L2_FLUSH_BYTES = 512 << 20
 # [--precision fp64]`), scaled to the full workload by primary segments. Valid only for the kernel
 # sources it was taken on.
 TRAFFIC_CAPTURE = {"kernel": "march_table_kernel",
-                   "bytes_per_segment": {"fp32": 8.789734586064215, "fp64": 19.166941837002017},
-                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "785d932cedef44d9",
-                               "paper_2512_12466_gb300/csrc/rt_internal.h": "7b899d1021ce1758"}}
+                   "bytes_per_segment": {"fp32": 8.80868621095342, "fp64": 19.254816976037528},
+                   "sources": {"paper_2512_12466_gb300/csrc/march.cu": "e97eefbf436b7d8a",
+                               "paper_2512_12466_gb300/csrc/rt_internal.h": "7b899d1021ce1758",
+                               "paper_2512_12466_gb300/csrc/dfloat.h": "f46e607e6ba33980"}}
 
 
 def traffic_per_launch(segments_per_step: float, launches_per_step: float, precision: str = "fp32"):
@@ -803,7 +804,7 @@ def run_nyx(args, world, rank, local):
                               "kernel": "march_table_kernel<double> (FP64, geometry tables, double-float)",
                               "bound": "instruction issue of the double-float arithmetic (ncu, one level-7 launch: "
                                        "issue 68% active, 322 thread instructions per segment at 25.3 of 32 lanes, "
-                                       "FP64 pipe 31%, DRAM 9%)"}},
+                                       "FP64 pipe 31%, DRAM 9%, before the neighbour cell became selects)"}},
         "e2e": {"value": e2e_val, "unit": "segments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "clocks": f32["clocks"],

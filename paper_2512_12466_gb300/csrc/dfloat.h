@@ -104,6 +104,17 @@ __device__ __forceinline__ dflt df_of(const double x)
     return {h, l};
 }
 
+// df_of for a positive double in [2^-74, 2^127), without the range tests (segment lengths: the
+// integer traversal makes every segment longer than about 2^-46 cells)
+__device__ __forceinline__ dflt df_of_len(const double x)
+{
+    const long long b = __double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const int e = (int)(hw >> 20);
+    return {__uint_as_float(((unsigned)(e - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29)),
+            __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), __uint_as_float((unsigned)(e - 948) << 23))};
+}
+
 // x 2^e2 as a double, exactly: float to double by re-biasing the exponent and shifting the
 // mantissa (no FP64 instruction); zero and subnormal floats take the conversion.
 __device__ __forceinline__ double widen_scaled(const float x, const int e2)

@@ -1405,16 +1405,15 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
         const double knext = (steps && next_in) ? V.kap[ncell] : 0.0;
         const bool near = corr && ((fl >> 27) & 1u);
         int c2 = -1;
-        if (face && near) {
+        if (face) {                      // the cell across the nearest face, as selects on every lane
             const int ax = (int)((fl >> 28) & 3u);
             const int step = ((fl >> 30) & 1u) ? 1 : -1;
-            const int jc = pick3(ax, i0, i1, i2) + step;
-            if (periodic) {
-                const int jw = wrap1(jc, n);
-                c2 = cell + (jw - (jc - step)) * (ax == 0 ? 1 : (ax == 1 ? n : (int)nn));
-            } else if ((unsigned)jc < (unsigned)n) {
-                c2 = cell + step * (ax == 0 ? 1 : (ax == 1 ? n : (int)nn));
-            }
+            const int ia = pick3(ax, i0, i1, i2);
+            const int jc = ia + step;
+            const int stride = ax == 0 ? 1 : (ax == 1 ? n : (int)nn);
+            if (periodic) c2 = cell + (wrap1(jc, n) - ia) * stride;
+            else c2 = (unsigned)jc < (unsigned)n ? cell + step * stride : -1;
+            if (!near) c2 = -1;
         }
         const double kn_raw = c2 >= 0 ? V.kap[c2] : 0.0;
         // ---- the two deciding FP64 operations: dtau = kap ds here, tau += dtau below
@@ -1452,7 +1451,7 @@ __device__ __forceinline__ bool march_ray_table_df(const SolveView<double>& V, c
                 e_seg = e_dep + 64;
             }
         } else if (!opaque) {
-            const dflt dsf = df_of(ds);
+            const dflt dsf = df_of_len(ds);
             if (I::pos(kap)) {
                 const dflt x = df_of(dtau);
                 const dflt u = df_mul(Q, rate_factor(rtab, x));
