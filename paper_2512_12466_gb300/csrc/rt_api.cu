@@ -40,6 +40,7 @@ thread_local std::string g_create_error;
 // records.
 constexpr int64_t kMaxChildrenPerLaunch = int64_t(1) << 27;
 constexpr int kMarchBlock = 256;
+constexpr int kMarchBlocksPerSm = 12;
 
 struct DirTable {
     int level = -1;
@@ -662,7 +663,9 @@ int run_level(rt_handle* h, int level, int64_t nparents)
         a.st = h->d_st;
         const int64_t warps = (c1 - c0 + 31) / 32;
         const int64_t want = (warps + kMarchBlock / 32 - 1) / (kMarchBlock / 32);
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->sm_count * 8));
+        // grid-stride blocks of equal share: 12 per SM is a whole number of waves for the march
+        // kernels' 2, 3 and 4 resident blocks per SM, so no last wave runs an SM part-empty
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->sm_count * kMarchBlocksPerSm));
         // the level's geometry table for this precision (built once per device, outside the timed launch)
         GeomLevel gl;
         const bool table = !(h->cfg.flags & RT_FLAG_NO_GEOMETRY_TABLE) &&
