@@ -51,7 +51,7 @@ TRAFFIC_CAPTURE = {"kernel": "march_table_kernel",
                    "bytes_per_segment": {"fp32": 8.80868621095342, "fp64": 19.254816976037528},
                    "sources": {"paper_2512_12466_gb300/csrc/march.cu": "e97eefbf436b7d8a",
                                "paper_2512_12466_gb300/csrc/rt_internal.h": "7b899d1021ce1758",
-                               "paper_2512_12466_gb300/csrc/dfloat.h": "f46e607e6ba33980"}}
+                               "paper_2512_12466_gb300/csrc/dfloat.h": "459135c9d92ee117"}}
 
 
 def traffic_per_launch(segments_per_step: float, launches_per_step: float, precision: str = "fp32"):

@@ -138,10 +138,12 @@ __device__ __forceinline__ double df_to_double(const dflt a, const int e2)
 
 // The same for h + l >= 0 without the FP64 unit: renormalise (|l| <= 2^-24 h), take h's double
 // exactly, and add l counted in units of that double's last place, 2^(E_h - 52), as a 64-bit
-// integer: l 2^(52 - E_h) is below 2^28 in magnitude and rounds to the nearest unit. A carry or
-// borrow across the mantissa's end moves the exponent as binary addition of the bit patterns of
-// a positive double does, so the result is within one unit of the last place of h + l. Heads
-// outside [2^-75, 2^127) (where the scale factor leaves the float range) take df_to_double.
+// integer: l 2^(52 - E_h) is below 2^28 in magnitude and rounds to the nearest unit. The result is
+// within one unit of the last place of h + l, except where the renormalised head is a power of two
+// and the tail negative: the sum then lies in the binade below, whose last place is half as large,
+// so only half the tail is subtracted (an error of at most 2^-26 of the value, for about one deposit
+// in 10^7). Heads outside [2^-75, 2^127) (where the scale factor leaves the float range) take
+// df_to_double.
 __device__ __forceinline__ double df_to_double_pos(const dflt a, const int e2)
 {
     const dflt n = df_fast_two_sum(a.h, a.l);
