@@ -157,3 +157,28 @@ def test_pair_to_double():
         else:
             assert abs(Fraction(got) - exact) <= ulp(got), (h, lo, e2)
     assert corner >= 20
+
+
+def widen_scaled(x: float, e2: int) -> float:
+    """Float to double times 2^e2 by re-biasing the exponent and shifting the mantissa."""
+    u = fbits(x)
+    mag = u & 0x7FFFFFFF
+    if (mag - 0x00800000) & 0xFFFFFFFF < 0x7F000000:
+        hi = (((mag >> 3) + ((896 + e2) << 20)) | (u & 0x80000000)) & 0xFFFFFFFF
+        return bits_d((hi << 32) | ((u << 29) & 0xFFFFFFFF))
+    if mag == 0:
+        return 0.0
+    return bits_d(dbits(float(x)) + e2 * (1 << 52))
+
+
+def test_float_widening_is_exact():
+    # the FP32 march widens each deposit for its FP64 atomic by the same bit operations (e2 = 0), and
+    # the double-float fallback rounds its two widened parts: the result must be x 2^e2 exactly, for
+    # normal and subnormal floats of either sign
+    rng = np.random.default_rng(8)
+    xs = [f32(float(v) * s) for v, s in zip(10.0 ** rng.uniform(-37, 38, 3000), rng.choice([-1.0, 1.0], 3000))]
+    xs += [bits_f(v) for v in (1, 7, 0x007FFFFF, 0x00800000, 0x7F7FFFFF, 0x80000001, 0x80800000)]
+    for x in xs:
+        for e2 in (-300, -64, 0, 64, 300):
+            assert Fraction(widen_scaled(x, e2)) == Fraction(x) * Fraction(2) ** e2, (x, e2)
+    assert widen_scaled(0.0, 17) == 0.0
